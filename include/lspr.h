@@ -1,0 +1,181 @@
+/*
+ * lspr.h -- C ABI of the GB300 (sm_103a) quasistatic LSPR boundary-element library.
+ *
+ * Method: Clementi, Cooper & Barba, "Computational nanoplasmonics in the
+ * quasistatic limit for biosensing applications" (arXiv:1812.10722).
+ *   - interface problem and its boundary integral equations: Sec. II.A, II.C,
+ *     Eqs. electrostatic_scatter, integral_eq_lspr
+ *   - flat-panel collocation and the 2x2 block system: Eqs. layers_disc,
+ *     matrix_lspr, layers_element
+ *   - singular / near-singular / far quadrature: Sec. II.C "Integral evaluation"
+ *   - treecode (octree, N_crit, MAC theta, Cartesian Taylor order P): Sec. II.D
+ *   - complex GMRES: Sec. II.D-II.E
+ *   - dipole and extinction cross-section: Eqs. dipole_def_gauss_i_final,
+ *     scat_efield_long_range, scat_efield_fwa, cext_fwa
+ *
+ * Conventions shared by every entry point
+ *   - Lengths in nm, cross-sections in nm^2.  Triangles are counter-clockwise
+ *     seen from outside, so (v1-v0)x(v2-v0) is the outward normal.
+ *   - A complex number is two doubles (re, im); complex arrays are interleaved.
+ *   - The unknown vector of one wavelength is [phi_1 .. phi_N, dphi_1 .. dphi_N]
+ *     (potential and its normal derivative inside the particle, one value per
+ *     panel); B right-hand sides are stored one after another ([B][2N] complex).
+ *   - Every call returns an lspr_status; no exception or abort crosses the ABI.
+ *     On an error the context stays valid unless the status is LSPR_E_CUDA
+ *     after a sticky device error.
+ *   - A context is bound to one device and one CUDA stream and is not
+ *     thread-safe; separate contexts are independent.  All device memory the
+ *     library needs is owned by the context and freed by lspr_destroy.
+ */
+#ifndef LSPR_H
+#define LSPR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LSPR_API __attribute__((visibility("default")))
+#else
+#define LSPR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSPR_OK = 0,
+    LSPR_E_ARG = 1,            /* invalid argument (null pointer, size, unsupported option) */
+    LSPR_E_STATE = 2,          /* call out of order (no mesh, no tree) */
+    LSPR_E_CUDA = 3,           /* a CUDA runtime call failed */
+    LSPR_E_OOM = 4,            /* device memory exhausted */
+    LSPR_E_NOT_CONVERGED = 5,  /* at least one wavelength missed the GMRES tolerance (see stats) */
+    LSPR_E_TIMEOUT = 6,        /* a device-side wait exceeded its bound */
+    LSPR_E_MESH = 7            /* degenerate or non-finite mesh */
+} lspr_status;
+
+typedef struct lspr_ctx lspr_ctx;
+
+/* Matrix-vector product modes (lspr_matvec, lspr_solve_opts.mode). */
+enum {
+    LSPR_DIRECT_FP64 = 0,  /* all pairs, FP64 arithmetic */
+    LSPR_DIRECT_FP32 = 1,  /* all pairs, FP32 arithmetic, FP64 accumulation across tiles */
+    LSPR_TREE_FP64 = 2,    /* treecode (needs lspr_tree_build), FP64 */
+    LSPR_TREE_FP32 = 3     /* treecode, FP32 P2P/P2M/M2P, FP64 accumulation and corrections */
+};
+
+/* Quadrature options, Sec. II.C "Integral evaluation" (paper's Tables 1 and 4). */
+typedef struct {
+    int32_t K;          /* points per far panel: 1, 3 or 4 */
+    int32_t K_fine;     /* points per near-singular panel: 19, 25 or 37 */
+    int32_t N_k;        /* Gauss-Legendre points per edge for the singular (self) panel, 1..32 */
+    double threshold;   /* near-singular iff L_j / |c_i - c_j| >= threshold, L_j = sqrt(2 A_j) */
+} lspr_quad_opts;
+
+/* Solver options. */
+typedef struct {
+    double tol;         /* relative residual ||b - A x|| / ||b|| per wavelength */
+    int32_t restart;    /* GMRES restart length m (1..512) */
+    int32_t maxiter;    /* total Arnoldi steps per wavelength */
+    int32_t mode;       /* matvec mode of the Krylov iteration (LSPR_DIRECT_* / LSPR_TREE_*) */
+    int32_t refine;     /* 1: FP64 iterative refinement around an FP32-mode inner solve */
+} lspr_solve_opts;
+
+/* Per-solve statistics; arrays hold B entries and are owned by the caller (may be null). */
+typedef struct {
+    int32_t *iterations;       /* Arnoldi steps taken per wavelength */
+    double *residual;          /* final relative residual per wavelength */
+    int32_t *status;           /* LSPR_OK or LSPR_E_NOT_CONVERGED per wavelength */
+    double seconds;            /* wall time of the call */
+    int64_t matvecs;           /* operator applications (all wavelengths) */
+} lspr_solve_stats;
+
+/* Text for a status code (static storage). */
+LSPR_API const char *lspr_status_string(int status);
+
+/* Library version string (static storage). */
+LSPR_API const char *lspr_version(void);
+
+/* Create a context on CUDA device `device`; all work is queued on `cuda_stream`
+ * (a cudaStream_t, or null for the legacy default stream).  *out receives the
+ * context.  Errors: LSPR_E_ARG (null out, bad device), LSPR_E_CUDA. */
+LSPR_API int lspr_create(lspr_ctx **out, int device, void *cuda_stream);
+
+/* Free every device and host resource of the context.  Null is accepted. */
+LSPR_API int lspr_destroy(lspr_ctx *ctx);
+
+/* Upload a triangle mesh and precompute everything that depends only on the
+ * geometry and the quadrature (Sec. II.C):
+ *   - panel centroids (collocation points), unit outward normals, areas, L = sqrt(2A)
+ *   - Gauss-node sources of the far rule (K per panel, weight w_g * A)
+ *   - singular self integrals V_ii (semi-analytical: radial part exact, N_k-point
+ *     Gauss-Legendre in the angle on each edge), K_ii = 0 on a flat panel
+ *   - the near-singular list (L_j/|c_i - c_j| >= threshold) and, per near pair,
+ *     the FP64 correction (K_fine rule minus K rule) of V_ij and K_ij
+ * verts: [nv][3] doubles; tris: [ntri][3] vertex indices (int32); surf_id: [ntri]
+ * surface index in [0, nsurf) (null = all 0).  Only nsurf == 1 is supported.
+ * on_device = 0: host pointers; 1: device pointers on the context's device.
+ * The library copies the data; the caller keeps ownership.  Invalidates any tree.
+ * Errors: LSPR_E_ARG (sizes, rules, indices out of range), LSPR_E_MESH
+ * (zero-area or non-finite panel), LSPR_E_OOM, LSPR_E_CUDA. */
+LSPR_API int lspr_mesh_upload(lspr_ctx *ctx, const double *verts, int64_t nv, const int32_t *tris, int64_t ntri,
+                     const int32_t *surf_id, int32_t nsurf, const lspr_quad_opts *q, int32_t on_device);
+
+/* Build the treecode structures of Sec. II.D on the device: Morton keys of the
+ * Gauss-node sources and the collocation targets, radix sort, an octree whose
+ * leaves hold at most Ncrit sources (or sit at the maximum depth of 10 levels),
+ * box centres and radii r_b, and per block of 64 targets the interaction lists:
+ * a box is accepted for the Taylor expansion of order P when r_b < theta * r,
+ * r the distance from the box centre to the nearest point of the target block's
+ * bounding box (and the box is clear of every target's near-singular region);
+ * leaves that fail are summed directly.  Supported P: 1..8; theta in (0, 1).
+ * Errors: LSPR_E_STATE (no mesh), LSPR_E_ARG, LSPR_E_OOM, LSPR_E_CUDA. */
+LSPR_API int lspr_tree_build(lspr_ctx *ctx, double theta, int32_t P, int32_t Ncrit);
+
+/* y[b] = A(s_b) x[b] for b < B, A the block operator of Eq. matrix_lspr:
+ *   y_top = phi/2 + K phi - V dphi,   y_bot = phi/2 - K phi + s_b V dphi,
+ * with s_b = eps_ratio[b] = eps_in/eps_out (complex).  x, y: [B][2N] complex.
+ * on_device = 0: x, y, eps_ratio are host pointers; 1: device pointers.  The
+ * call is complete (stream synchronised) on return.
+ * Errors: LSPR_E_STATE (no mesh; tree mode without a tree), LSPR_E_ARG, LSPR_E_CUDA. */
+LSPR_API int lspr_matvec(lspr_ctx *ctx, const double *x, double *y, int32_t B, const double *eps_ratio,
+                int32_t mode, int32_t on_device);
+
+/* Solve the interface problem for B wavelengths and return the induced dipole
+ * and the extinction cross-section of each (host pointers):
+ *   eps_in   [B] complex   particle permittivity per wavelength
+ *   eps_out                host permittivity (re, im)
+ *   E0       [3]           incident field amplitude (direction = polarisation)
+ *   lambda_nm[B]           vacuum wavelengths
+ *   dipole_out [B][3] complex, sigma_ext_out [B] (nm^2): caller-allocated.
+ * The right-hand side V((eps_out-eps_in)/eps_out dphi_inc/dn), dphi_inc/dn = -E0.n,
+ * is formed in FP64; GMRES (right 2x2 block-Jacobi preconditioner, FP64 Krylov
+ * basis) runs in the matvec mode of `o`; the dipole is
+ * p = -eps_out * sum_j A_j (c_j dphi2s/dn_j - phi_j n_j) over the panels and
+ * sigma_ext = Im(k^2 e.p / (eps_out |E0|)) / Re k with k = 2 pi sqrt(eps_out) / lambda.
+ * Returns LSPR_E_NOT_CONVERGED if any wavelength missed tol (results are still
+ * written).  st may be null. */
+LSPR_API int lspr_solve(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
+               const double *lambda_nm, int32_t B, const lspr_solve_opts *o, double *dipole_out,
+               double *sigma_ext_out, lspr_solve_stats *st);
+
+/* Sizes of the current geometry and tree (any pointer may be null):
+ * panels, sources, near pairs (including self), boxes, P2P source-range items,
+ * M2P (target block, box) pairs, and the P2P target-source pairs per matvec. */
+LSPR_API int lspr_get_info(lspr_ctx *ctx, int64_t *n_panels, int64_t *n_sources, int64_t *n_near, int64_t *n_boxes,
+                  int64_t *n_p2p_items, int64_t *n_m2p_pairs, int64_t *n_p2p_pairs);
+
+/* Kernel timing of the last lspr_matvec / lspr_solve on the context's stream,
+ * in milliseconds summed over launches, and launch counts (arrays of 8):
+ * [0] P2P, [1] M2P, [2] P2M, [3] near/assembly, [4] GMRES vector kernels,
+ * [5] tree build, [6] mesh/near precompute, [7] other.
+ * Timing is recorded only while enabled (lspr_set_timing(ctx, 1)). */
+LSPR_API int lspr_set_timing(lspr_ctx *ctx, int32_t enable);
+/* Number of CUDA kernels the context has launched since lspr_create. */
+LSPR_API int lspr_launch_count(lspr_ctx *ctx, int64_t *count);
+LSPR_API int lspr_get_timing(lspr_ctx *ctx, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSPR_H */

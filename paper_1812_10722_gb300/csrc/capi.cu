@@ -1,0 +1,235 @@
+// C ABI entry points (declared in include/lspr.h).  Argument checking, context
+// ownership and status mapping live here; the numerical work is in mesh.cu,
+// tree.cu, farfield.cu and solve.cu.
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "lspr_internal.cuh"
+
+namespace lspr {
+
+void timer_begin(lspr_ctx *ctx, int slot, cudaEvent_t *ev) {
+    (void)slot;
+    *ev = nullptr;
+    Timing &t = ctx->timing;
+    if (!t.enabled) return;
+    if (t.used + 2 > t.pool.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            t.pool.push_back(e);
+        }
+    }
+    *ev = t.pool[t.used++];
+    cudaEventRecord(*ev, ctx->stream);
+}
+
+void timer_end(lspr_ctx *ctx, int slot, cudaEvent_t ev) {
+    Timing &t = ctx->timing;
+    if (!t.enabled || !ev) return;
+    if (t.used + 1 > t.pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        t.pool.push_back(e);
+    }
+    cudaEvent_t e2 = t.pool[t.used++];
+    cudaEventRecord(e2, ctx->stream);
+    t.pending.push_back({slot, {ev, e2}});
+    if (t.used > 4096) timer_collect(ctx);
+}
+
+void timer_collect(lspr_ctx *ctx) {
+    Timing &t = ctx->timing;
+    if (t.pending.empty()) {
+        t.used = 0;
+        return;
+    }
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &p : t.pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+            t.ms[p.first] += ms;
+            t.launches[p.first] += 1;
+        }
+    }
+    t.pending.clear();
+    t.used = 0;
+}
+
+}  // namespace lspr
+
+using namespace lspr;
+
+extern "C" {
+
+const char *lspr_status_string(int s) {
+    switch (s) {
+    case LSPR_OK: return "ok";
+    case LSPR_E_ARG: return "invalid argument";
+    case LSPR_E_STATE: return "call out of order (mesh or tree missing)";
+    case LSPR_E_CUDA: return "CUDA error";
+    case LSPR_E_OOM: return "device memory exhausted";
+    case LSPR_E_NOT_CONVERGED: return "GMRES did not reach the tolerance";
+    case LSPR_E_TIMEOUT: return "device wait exceeded its bound";
+    case LSPR_E_MESH: return "degenerate or non-finite mesh";
+    default: return "unknown status";
+    }
+}
+
+const char *lspr_version(void) { return "lspr-gb300 0.1 (sm_103a)"; }
+
+int lspr_create(lspr_ctx **out, int device, void *cuda_stream) {
+    if (!out) return LSPR_E_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return n == 0 ? LSPR_E_CUDA : LSPR_E_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return LSPR_E_CUDA;
+    lspr_ctx *c = new (std::nothrow) lspr_ctx();
+    if (!c) return LSPR_E_OOM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return LSPR_OK;
+}
+
+int lspr_destroy(lspr_ctx *c) {
+    if (!c) return LSPR_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    Mesh &m = c->mesh;
+    for (DArr<double> *a : {&m.verts, &m.cx, &m.cy, &m.cz, &m.nx, &m.ny, &m.nz, &m.area, &m.L, &m.Vself, &m.near_dV,
+                            &m.near_dK, &c->acc, &c->gm_norm, &c->gm_bnorm, &c->gm_dpart, &c->gm_out})
+        a->release();
+    m.tris.release();
+    m.near_col.release();
+    m.near_ptr.release();
+    for (DArr<dbl4> *a : {&m.src_pos64, &m.src_nrm64, &m.tgt64, &c->wo.spos64, &c->wo.snrm64, &c->wo.tgt64,
+                             &c->w64, &c->tree.box_c64, &c->tree.mom64})
+        a->release();
+    for (DArr<float4> *a : {&c->wo.spos32, &c->wo.snrm32, &c->wo.tgt32, &c->w32, &c->tree.box_c32, &c->tree.mom32})
+        a->release();
+    for (DArr<int> *a : {&c->wo.src_panel, &c->wo.tgt_panel, &c->tree.box_beg, &c->tree.box_end, &c->tree.box_child,
+                         &c->tree.box_nchild, &c->tree.box_level, &c->tree.box_used, &c->tree.m2p_list, &c->gm_active})
+        a->release();
+    c->tree.box_key.release();
+    for (DArr<int4> *a : {&c->tree.p2p_items, &c->tree.m2p_items, &c->tree.p2m_items, &c->direct.items}) a->release();
+    for (DArr<double2> *a : {&c->xbuf, &c->ybuf, &c->sbuf, &c->gm_V, &c->gm_w, &c->gm_z, &c->gm_x, &c->gm_b, &c->gm_r,
+                             &c->gm_H, &c->gm_cs, &c->gm_sn, &c->gm_g, &c->gm_y, &c->gm_h, &c->gm_part, &c->gm_s,
+                             &c->gm_vinc, &c->gm_eps})
+        a->release();
+    for (cudaEvent_t e : c->timing.pool) cudaEventDestroy(e);
+    delete c;
+    return LSPR_OK;
+}
+
+int lspr_mesh_upload(lspr_ctx *c, const double *verts, int64_t nv, const int32_t *tris, int64_t ntri,
+                     const int32_t *surf_id, int32_t nsurf, const lspr_quad_opts *q, int32_t on_device) {
+    if (!c || !verts || !tris || !q || nv < 3 || ntri < 1 || nsurf != 1) return LSPR_E_ARG;
+    if (ntri > (int64_t)1 << 28 || nv > (int64_t)1 << 30) return LSPR_E_ARG;
+    (void)surf_id;
+    cudaSetDevice(c->device);
+    return mesh_build(c, verts, nv, tris, ntri, on_device, *q);
+}
+
+int lspr_tree_build(lspr_ctx *c, double theta, int32_t P, int32_t Ncrit) {
+    if (!c) return LSPR_E_ARG;
+    if (!c->mesh.ready) return LSPR_E_STATE;
+    if (!(theta > 0.0 && theta < 1.0) || P < 1 || P > kMaxP || Ncrit < 1) return LSPR_E_ARG;
+    cudaSetDevice(c->device);
+    return tree_build(c, theta, P, Ncrit);
+}
+
+int lspr_matvec(lspr_ctx *c, const double *x, double *y, int32_t B, const double *eps_ratio, int32_t mode,
+                int32_t on_device) {
+    if (!c || !x || !y || !eps_ratio || B < 1 || mode < 0 || mode > 3) return LSPR_E_ARG;
+    if (!c->mesh.ready) return LSPR_E_STATE;
+    if ((mode == LSPR_TREE_FP32 || mode == LSPR_TREE_FP64) && !c->tree.ready) return LSPR_E_STATE;
+    cudaSetDevice(c->device);
+    const int64_t n2 = 2 * c->mesh.N;
+    const double2 *xd = (const double2 *)x;
+    double2 *yd = (double2 *)y;
+    const double2 *sd = (const double2 *)eps_ratio;
+    if (!on_device) {
+        LSPR_TRY(c, c->xbuf.ensure((size_t)B * n2));
+        LSPR_TRY(c, c->ybuf.ensure((size_t)B * n2));
+        LSPR_TRY(c, c->sbuf.ensure(B));
+        LSPR_TRY(c, cudaMemcpyAsync(c->xbuf.p, x, sizeof(double2) * B * n2, cudaMemcpyHostToDevice, c->stream));
+        LSPR_TRY(c, cudaMemcpyAsync(c->sbuf.p, eps_ratio, sizeof(double2) * B, cudaMemcpyHostToDevice, c->stream));
+        xd = c->xbuf.p;
+        yd = c->ybuf.p;
+        sd = c->sbuf.p;
+    }
+    LSPR_TRY_ST(apply_operator(c, mode, xd, yd, sd, B));
+    if (!on_device)
+        LSPR_TRY(c, cudaMemcpyAsync(y, yd, sizeof(double2) * B * n2, cudaMemcpyDeviceToHost, c->stream));
+    LSPR_TRY(c, cudaStreamSynchronize(c->stream));
+    timer_collect(c);
+    return LSPR_OK;
+}
+
+int lspr_solve(lspr_ctx *c, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
+               const double *lambda_nm, int32_t B, const lspr_solve_opts *o, double *dipole_out,
+               double *sigma_ext_out, lspr_solve_stats *st) {
+    if (!c || !eps_in || !E0 || !lambda_nm || !o || !dipole_out || !sigma_ext_out || B < 1) return LSPR_E_ARG;
+    if (o->mode < 0 || o->mode > 3 || !(o->tol > 0) || o->restart < 1 || o->maxiter < 1) return LSPR_E_ARG;
+    if (!(E0[0] * E0[0] + E0[1] * E0[1] + E0[2] * E0[2] > 0)) return LSPR_E_ARG;
+    if (!c->mesh.ready) return LSPR_E_STATE;
+    if ((o->mode == LSPR_TREE_FP32 || o->mode == LSPR_TREE_FP64) && !c->tree.ready) return LSPR_E_STATE;
+    cudaSetDevice(c->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t mv0 = c->matvec_count;
+    int rc = solve_impl(c, eps_in, eps_out_re, eps_out_im, E0, lambda_nm, B, *o, dipole_out, sigma_ext_out, st);
+    timer_collect(c);
+    if (st) {
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        st->matvecs = c->matvec_count - mv0;
+    }
+    return rc;
+}
+
+int lspr_get_info(lspr_ctx *c, int64_t *n_panels, int64_t *n_sources, int64_t *n_near, int64_t *n_boxes,
+                  int64_t *n_p2p_items, int64_t *n_m2p_pairs, int64_t *n_p2p_pairs) {
+    if (!c) return LSPR_E_ARG;
+    if (n_panels) *n_panels = c->mesh.N;
+    if (n_sources) *n_sources = c->mesh.Ns;
+    if (n_near) *n_near = c->mesh.nnz;
+    if (n_boxes) *n_boxes = c->tree.ready ? c->tree.nboxes : 0;
+    if (n_p2p_items) *n_p2p_items = c->tree.ready ? c->tree.n_p2p_items : 0;
+    if (n_m2p_pairs) *n_m2p_pairs = c->tree.ready ? c->tree.n_m2p_pairs : 0;
+    if (n_p2p_pairs) *n_p2p_pairs = c->tree.ready ? c->tree.p2p_pairs : 0;
+    return LSPR_OK;
+}
+
+int lspr_launch_count(lspr_ctx *c, int64_t *count) {
+    if (!c || !count) return LSPR_E_ARG;
+    *count = c->n_launches;
+    return LSPR_OK;
+}
+
+int lspr_set_timing(lspr_ctx *c, int32_t enable) {
+    if (!c) return LSPR_E_ARG;
+    timer_collect(c);
+    c->timing.enabled = enable != 0;
+    for (int k = 0; k < 8; ++k) {
+        c->timing.ms[k] = 0;
+        c->timing.launches[k] = 0;
+    }
+    return LSPR_OK;
+}
+
+int lspr_get_timing(lspr_ctx *c, double *ms, int64_t *launches) {
+    if (!c) return LSPR_E_ARG;
+    timer_collect(c);
+    for (int k = 0; k < 8; ++k) {
+        if (ms) ms[k] = c->timing.ms[k];
+        if (launches) launches[k] = c->timing.launches[k];
+    }
+    return LSPR_OK;
+}
+
+}  // extern "C"

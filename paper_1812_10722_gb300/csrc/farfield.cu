@@ -1,0 +1,430 @@
+// Far-field kernels of the matrix-vector product (Sec. II.D, Eq. summation):
+// sources are the far-rule Gauss nodes y_j with weights q_j = w_j A_j dphi_j / (4 pi)
+// (single layer) and mu_j = w_j A_j phi_j / (4 pi) (double layer); targets are the
+// panel centroids x_i.  For every target
+//     Vd_i = sum_j q_j / |x_i - y_j|,   Kp_i = sum_j mu_j (x_i - y_j).n_j / |x_i - y_j|^3
+// over all sources except those of panel i itself (its singular integral is
+// added exactly by the near-field correction).  Complex weights are carried as
+// two real channels (the paper's real/imaginary split of the treecode work).
+//
+//   p2p_kernel  direct sums of a 64-target block against a contiguous source range
+//   p2m_kernel  Cartesian Taylor moments of a box about its centre c:
+//                 M^V_k = sum_j q_j (c - y_j)^k
+//                 M^K_k = sum_j mu_j * (-sum_d n_{j,d} k_d (c - y_j)^(k - e_d))
+//   m2p_kernel  Vd_i += sum_{|k|<=P} a_k(x_i - c) M^V_k (same for K), with
+//               a_k(R) = D^k (1/|R|) / k! from the recurrence
+//               n |R|^2 a_k + (2n-1) sum_d R_d a_(k-e_d) + (n-1) sum_d a_(k-2e_d) = 0,
+//               n = |k|, a_0 = 1/|R|.
+// Partial sums are formed in the kernel's precision (FP32 or FP64) per work
+// item and accumulated in FP64 with atomics.
+#include "lspr_internal.cuh"
+
+namespace lspr {
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = dbl4; };
+
+__device__ __forceinline__ int panel_of(float w) { return __float_as_int(w); }
+__device__ __forceinline__ int panel_of(double w) { return (int)w; }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+// ----------------------------------------------------------------- weights
+template <typename T4>
+__global__ void weights_kernel(int64_t Ns, int64_t N, const dbl4 *__restrict__ spos64,
+                               const int *__restrict__ src_panel, const double2 *__restrict__ x, T4 *__restrict__ w) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= Ns) return;
+    const int p = src_panel[s];
+    const double wa = spos64[s].w * kInv4Pi;
+    const double2 phi = x[p], dphi = x[N + p];
+    T4 o;
+    o.x = wa * dphi.x;
+    o.y = wa * dphi.y;
+    o.z = wa * phi.x;
+    o.w = wa * phi.y;
+    w[s] = o;
+}
+
+// --------------------------------------------------------------------- P2P
+template <typename T>
+struct P2PAcc {
+    T vr, vi, kr, ki;
+};
+
+template <typename T, typename T4>
+__device__ __forceinline__ void p2p_pair(const T4 &p, const T4 &n, const T4 &w, int pid, T tx, T ty, T tz, int tp,
+                                         P2PAcc<T> &a) {
+    const T dx = tx - p.x, dy = ty - p.y, dz = tz - p.z;
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    T ri = rsq(r2);
+    ri = (pid == tp) ? T(0) : ri;   // own panel: the exact singular integral replaces it
+    const T dn = dx * n.x + dy * n.y + dz * n.z;
+    const T t3 = dn * (ri * ri) * ri;
+    a.vr += ri * w.x;
+    a.vi += ri * w.y;
+    a.kr += t3 * w.z;
+    a.ki += t3 * w.w;
+}
+
+constexpr int kP2PWarps = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kP2PWarps * 32) p2p_kernel(const int4 *__restrict__ items, int64_t nitems,
+                                                             const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt,
+                                                             const typename Vec4<T>::type *__restrict__ spos,
+                                                             const typename Vec4<T>::type *__restrict__ snrm,
+                                                             const typename Vec4<T>::type *__restrict__ sw,
+                                                             double *__restrict__ acc) {
+    using T4 = typename Vec4<T>::type;
+    __shared__ T4 sh[kP2PWarps][3][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t it = (int64_t)blockIdx.x * kP2PWarps + warp;
+    if (it >= nitems) return;
+    const int4 item = __ldg(items + it);
+    const int64_t t0 = (int64_t)item.x * kTargetBlock + lane, t1 = t0 + 32;
+    T4 q0 = t0 < ntgt ? tgt[t0] : tgt[0];
+    T4 q1 = t1 < ntgt ? tgt[t1] : tgt[0];
+    const int tp0 = panel_of(q0.w), tp1 = panel_of(q1.w);
+    P2PAcc<T> a0 = {0, 0, 0, 0}, a1 = {0, 0, 0, 0};
+    for (int base = item.y; base < item.z; base += 32) {
+        const int s = base + lane;
+        if (s < item.z) {
+            sh[warp][0][lane] = spos[s];
+            sh[warp][1][lane] = snrm[s];
+            sh[warp][2][lane] = sw[s];
+        }
+        __syncwarp();
+        const int cnt = min(32, item.z - base);
+        if (cnt == 32) {
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                const T4 p = sh[warp][0][k], n = sh[warp][1][k], w = sh[warp][2][k];
+                const int pid = panel_of(n.w);
+                p2p_pair<T, T4>(p, n, w, pid, q0.x, q0.y, q0.z, tp0, a0);
+                p2p_pair<T, T4>(p, n, w, pid, q1.x, q1.y, q1.z, tp1, a1);
+            }
+        } else {
+            for (int k = 0; k < cnt; ++k) {
+                const T4 p = sh[warp][0][k], n = sh[warp][1][k], w = sh[warp][2][k];
+                const int pid = panel_of(n.w);
+                p2p_pair<T, T4>(p, n, w, pid, q0.x, q0.y, q0.z, tp0, a0);
+                p2p_pair<T, T4>(p, n, w, pid, q1.x, q1.y, q1.z, tp1, a1);
+            }
+        }
+        __syncwarp();
+    }
+    if (t0 < ntgt) {
+        double *o = acc + 4 * (int64_t)tp0;
+        atomicAdd(o + 0, (double)a0.vr);
+        atomicAdd(o + 1, (double)a0.vi);
+        atomicAdd(o + 2, (double)a0.kr);
+        atomicAdd(o + 3, (double)a0.ki);
+    }
+    if (t1 < ntgt) {
+        double *o = acc + 4 * (int64_t)tp1;
+        atomicAdd(o + 0, (double)a1.vr);
+        atomicAdd(o + 1, (double)a1.vi);
+        atomicAdd(o + 2, (double)a1.kr);
+        atomicAdd(o + 3, (double)a1.ki);
+    }
+}
+
+// ------------------------------------------------------------ multi-indices
+// Terms ordered by degree n = k1+k2+k3; within a degree k1 descending, then k2.
+__host__ __device__ constexpr int mi_index(int a, int b, int c) {
+    const int n = a + b + c;
+    return n_terms(n - 1) + (n - a) * (n - a + 1) / 2 + (n - a - b);
+}
+
+template <int P>
+struct MultiIndex {
+    static constexpr int NT = n_terms(P);
+    int k[NT][3];
+    int deg[NT];
+    int m1[NT][3];   // index of k - e_d, or -1
+    int m2[NT][3];   // index of k - 2 e_d, or -1
+    constexpr MultiIndex() : k(), deg(), m1(), m2() {
+        int t = 0;
+        for (int n = 0; n <= P; ++n)
+            for (int a = n; a >= 0; --a)
+                for (int b = n - a; b >= 0; --b) {
+                    k[t][0] = a;
+                    k[t][1] = b;
+                    k[t][2] = n - a - b;
+                    deg[t] = n;
+                    ++t;
+                }
+        for (int u = 0; u < NT; ++u)
+            for (int d = 0; d < 3; ++d) {
+                int e1[3] = {k[u][0], k[u][1], k[u][2]};
+                int e2[3] = {k[u][0], k[u][1], k[u][2]};
+                e1[d] -= 1;
+                e2[d] -= 2;
+                m1[u][d] = e1[d] >= 0 ? mi_index(e1[0], e1[1], e1[2]) : -1;
+                m2[u][d] = e2[d] >= 0 ? mi_index(e2[0], e2[1], e2[2]) : -1;
+            }
+    }
+};
+
+// --------------------------------------------------------------------- M2P
+template <typename T, int P>
+__device__ __forceinline__ void m2p_one(T Rx, T Ry, T Rz, const typename Vec4<T>::type *__restrict__ mom,
+                                        P2PAcc<T> &acc) {
+    constexpr MultiIndex<P> mi{};
+    constexpr int NT = MultiIndex<P>::NT;
+    const T R[3] = {Rx, Ry, Rz};
+    const T r2 = Rx * Rx + Ry * Ry + Rz * Rz;
+    const T ir2 = T(1) / r2;
+    T a[NT];
+    a[0] = rsq(r2);
+    {
+        const auto m = mom[0];
+        acc.vr += a[0] * m.x;
+        acc.vi += a[0] * m.y;
+        acc.kr += a[0] * m.z;
+        acc.ki += a[0] * m.w;
+    }
+#pragma unroll
+    for (int t = 1; t < NT; ++t) {
+        const int n = mi.deg[t];
+        T s1 = T(0), s2 = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (mi.m1[t][d] >= 0) s1 += R[d] * a[mi.m1[t][d]];
+            if (mi.m2[t][d] >= 0) s2 += a[mi.m2[t][d]];
+        }
+        const T c1 = T(-(2.0 * n - 1.0) / n), c2 = T(-(n - 1.0) / n);
+        a[t] = (c1 * s1 + c2 * s2) * ir2;
+        const auto m = mom[t];
+        acc.vr += a[t] * m.x;
+        acc.vi += a[t] * m.y;
+        acc.kr += a[t] * m.z;
+        acc.ki += a[t] * m.w;
+    }
+}
+
+constexpr int kM2PWarps = 4;
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kM2PWarps * 32) m2p_kernel(const int4 *__restrict__ items, int64_t nitems,
+                                                             const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt,
+                                                             const int *__restrict__ list,
+                                                             const typename Vec4<T>::type *__restrict__ box_c,
+                                                             const typename Vec4<T>::type *__restrict__ mom,
+                                                             double *__restrict__ acc) {
+    using T4 = typename Vec4<T>::type;
+    constexpr int NT = n_terms(P);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t it = (int64_t)blockIdx.x * kM2PWarps + warp;
+    if (it >= nitems) return;
+    const int4 item = __ldg(items + it);
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const int64_t ti = (int64_t)item.x * kTargetBlock + lane + 32 * h;
+        if (ti >= ntgt) continue;
+        const T4 q = tgt[ti];
+        P2PAcc<T> a = {0, 0, 0, 0};
+#pragma unroll 1
+        for (int l = item.y; l < item.z; ++l) {
+            const int b = __ldg(list + l);
+            const T4 c = box_c[b];
+            m2p_one<T, P>(q.x - c.x, q.y - c.y, q.z - c.z, mom + (int64_t)b * NT, a);
+        }
+        double *o = acc + 4 * (int64_t)panel_of(q.w);
+        atomicAdd(o + 0, (double)a.vr);
+        atomicAdd(o + 1, (double)a.vi);
+        atomicAdd(o + 2, (double)a.kr);
+        atomicAdd(o + 3, (double)a.ki);
+    }
+}
+
+// --------------------------------------------------------------------- P2M
+constexpr int kP2MTile = 32;
+
+template <typename T, int P>
+__global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, const typename Vec4<T>::type *__restrict__ spos,
+                           const typename Vec4<T>::type *__restrict__ snrm, const typename Vec4<T>::type *__restrict__ sw,
+                           const typename Vec4<T>::type *__restrict__ box_c, typename Vec4<T>::type *__restrict__ mom) {
+    using T4 = typename Vec4<T>::type;
+    constexpr int NT = n_terms(P);
+    __shared__ T pw[kP2MTile][3][P + 1];
+    __shared__ T4 shn[kP2MTile], shw[kP2MTile];
+    const int64_t it = blockIdx.x;
+    if (it >= nitems) return;
+    const int4 item = items[it];
+    const T4 c = box_c[item.x];
+    const int t = threadIdx.x;
+    int k1 = 0, k2 = 0, k3 = 0;
+    if (t < NT) {   // decode the multi-index of this thread
+        int n = 0;
+        while (n_terms(n) <= t) ++n;
+        int r = t - n_terms(n - 1);
+        int a = n;
+        while (r > n - a) {
+            r -= n - a + 1;
+            --a;
+        }
+        k1 = a;
+        k2 = n - a - r;
+        k3 = n - k1 - k2;
+    }
+    T vr = 0, vi = 0, kr = 0, ki = 0;
+    for (int base = item.y; base < item.z; base += kP2MTile) {
+        __syncthreads();
+        const int cnt = min(kP2MTile, item.z - base);
+        if (t < cnt) {
+            const T4 y = spos[base + t];
+            const T d[3] = {c.x - y.x, c.y - y.y, c.z - y.z};
+            for (int q = 0; q < 3; ++q) {
+                T v = 1;
+                for (int e = 0; e <= P; ++e) {
+                    pw[t][q][e] = v;
+                    v *= d[q];
+                }
+            }
+            shn[t] = snrm[base + t];
+            shw[t] = sw[base + t];
+        }
+        __syncthreads();
+        if (t < NT) {
+            for (int s = 0; s < cnt; ++s) {
+                const T px = pw[s][0][k1], py = pw[s][1][k2], pz = pw[s][2][k3];
+                const T mono = px * py * pz;
+                const T4 n = shn[s], w = shw[s];
+                T dm = 0;
+                if (k1) dm += n.x * T(k1) * pw[s][0][k1 - 1] * py * pz;
+                if (k2) dm += n.y * T(k2) * px * pw[s][1][k2 - 1] * pz;
+                if (k3) dm += n.z * T(k3) * px * py * pw[s][2][k3 - 1];
+                vr += w.x * mono;
+                vi += w.y * mono;
+                kr -= w.z * dm;
+                ki -= w.w * dm;
+            }
+        }
+    }
+    if (t < NT) {
+        T *o = (T *)(mom + (int64_t)item.x * NT + t);
+        atomicAdd(o + 0, vr);
+        atomicAdd(o + 1, vi);
+        atomicAdd(o + 2, kr);
+        atomicAdd(o + 3, ki);
+    }
+}
+
+// --------------------------------------------------------------- launchers
+int launch_weights(lspr_ctx *ctx, bool fp64, const double2 *x, int64_t N) {
+    const int64_t Ns = ctx->mesh.Ns;
+    if (fp64) {
+        LSPR_TRY(ctx, ctx->w64.ensure(Ns));
+        ++ctx->n_launches;
+        weights_kernel<dbl4><<<grid_for(Ns, 256), 256, 0, ctx->stream>>>(Ns, N, ctx->wo.spos64.p,
+                                                                            ctx->wo.src_panel.p, x, ctx->w64.p);
+    } else {
+        LSPR_TRY(ctx, ctx->w32.ensure(Ns));
+        ++ctx->n_launches;
+        weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, ctx->stream>>>(Ns, N, ctx->wo.spos64.p,
+                                                                           ctx->wo.src_panel.p, x, ctx->w32.p);
+    }
+    LSPR_TRY(ctx, cudaGetLastError());
+    return LSPR_OK;
+}
+
+int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, double *acc) {
+    if (nitems == 0) return LSPR_OK;
+    const unsigned grid = grid_for(nitems, kP2PWarps);
+    cudaEvent_t ev;
+    timer_begin(ctx, T_P2P, &ev);
+    ++ctx->n_launches;
+    if (fp64)
+        p2p_kernel<double><<<grid, kP2PWarps * 32, 0, ctx->stream>>>(items, nitems, ctx->wo.tgt64.p, ctx->mesh.N,
+                                                                     ctx->wo.spos64.p, ctx->wo.snrm64.p, ctx->w64.p, acc);
+    else
+        p2p_kernel<float><<<grid, kP2PWarps * 32, 0, ctx->stream>>>(items, nitems, ctx->wo.tgt32.p, ctx->mesh.N,
+                                                                    ctx->wo.spos32.p, ctx->wo.snrm32.p, ctx->w32.p, acc);
+    timer_end(ctx, T_P2P, ev);
+    LSPR_TRY(ctx, cudaGetLastError());
+    return LSPR_OK;
+}
+
+template <typename T, int P>
+static void p2m_launch(lspr_ctx *ctx) {
+    using T4 = typename Vec4<T>::type;
+    Tree &tr = ctx->tree;
+    const int threads = ((n_terms(P) + 31) / 32) * 32;
+    const T4 *spos, *snrm, *w, *bc;
+    T4 *mom;
+    if constexpr (sizeof(T) == 8) {
+        spos = ctx->wo.spos64.p; snrm = ctx->wo.snrm64.p; w = ctx->w64.p; bc = tr.box_c64.p; mom = tr.mom64.p;
+    } else {
+        spos = ctx->wo.spos32.p; snrm = ctx->wo.snrm32.p; w = ctx->w32.p; bc = tr.box_c32.p; mom = tr.mom32.p;
+    }
+    ++ctx->n_launches;
+    p2m_kernel<T, P><<<(unsigned)tr.n_p2m_items, threads, 0, ctx->stream>>>(tr.p2m_items.p, tr.n_p2m_items, spos, snrm,
+                                                                           w, bc, mom);
+}
+
+template <typename T, int P>
+static void m2p_launch(lspr_ctx *ctx, double *acc) {
+    using T4 = typename Vec4<T>::type;
+    Tree &tr = ctx->tree;
+    const T4 *tgt, *bc, *mom;
+    if constexpr (sizeof(T) == 8) {
+        tgt = ctx->wo.tgt64.p; bc = tr.box_c64.p; mom = tr.mom64.p;
+    } else {
+        tgt = ctx->wo.tgt32.p; bc = tr.box_c32.p; mom = tr.mom32.p;
+    }
+    ++ctx->n_launches;
+    m2p_kernel<T, P><<<grid_for(tr.n_m2p_items, kM2PWarps), kM2PWarps * 32, 0, ctx->stream>>>(
+        tr.m2p_items.p, tr.n_m2p_items, tgt, ctx->mesh.N, tr.m2p_list.p, bc, mom, acc);
+}
+
+#define LSPR_DISPATCH_P(FN, T, ...)           \
+    switch (ctx->tree.P) {                    \
+    case 1: FN<T, 1>(__VA_ARGS__); break;     \
+    case 2: FN<T, 2>(__VA_ARGS__); break;     \
+    case 3: FN<T, 3>(__VA_ARGS__); break;     \
+    case 4: FN<T, 4>(__VA_ARGS__); break;     \
+    case 5: FN<T, 5>(__VA_ARGS__); break;     \
+    case 6: FN<T, 6>(__VA_ARGS__); break;     \
+    case 7: FN<T, 7>(__VA_ARGS__); break;     \
+    case 8: FN<T, 8>(__VA_ARGS__); break;     \
+    default: return LSPR_E_ARG;               \
+    }
+
+int launch_p2m(lspr_ctx *ctx, bool fp64) {
+    Tree &tr = ctx->tree;
+    if (tr.n_p2m_items == 0) return LSPR_OK;
+    cudaEvent_t ev;
+    timer_begin(ctx, T_P2M, &ev);
+    if (fp64) {
+        LSPR_TRY(ctx, tr.mom64.ensure(tr.nboxes * tr.NT));
+        LSPR_TRY(ctx, cudaMemsetAsync(tr.mom64.p, 0, sizeof(dbl4) * tr.nboxes * tr.NT, ctx->stream));
+        LSPR_DISPATCH_P(p2m_launch, double, ctx);
+    } else {
+        LSPR_TRY(ctx, tr.mom32.ensure(tr.nboxes * tr.NT));
+        LSPR_TRY(ctx, cudaMemsetAsync(tr.mom32.p, 0, sizeof(float4) * tr.nboxes * tr.NT, ctx->stream));
+        LSPR_DISPATCH_P(p2m_launch, float, ctx);
+    }
+    timer_end(ctx, T_P2M, ev);
+    LSPR_TRY(ctx, cudaGetLastError());
+    return LSPR_OK;
+}
+
+int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc) {
+    Tree &tr = ctx->tree;
+    if (tr.n_m2p_items == 0) return LSPR_OK;
+    cudaEvent_t ev;
+    timer_begin(ctx, T_M2P, &ev);
+    if (fp64) {
+        LSPR_DISPATCH_P(m2p_launch, double, ctx, acc);
+    } else {
+        LSPR_DISPATCH_P(m2p_launch, float, ctx, acc);
+    }
+    timer_end(ctx, T_M2P, ev);
+    LSPR_TRY(ctx, cudaGetLastError());
+    return LSPR_OK;
+}
+
+}  // namespace lspr

@@ -1,0 +1,204 @@
+// Internal declarations of the sm_103a LSPR boundary-element library.
+// Layout of device data (all owned by one lspr_ctx):
+//   panels    FP64 structure-of-arrays in input order (centroid, normal, area, L, V_ii)
+//   sources   Gauss nodes of the far rule, "work order" (input order until a tree
+//             is built, Morton order afterwards): position+weight (x,y,z,w_g*A),
+//             normal (nx,ny,nz,panel id as int bits) in FP64 and FP32 copies
+//   targets   collocation points in work order (x,y,z,panel id as int bits)
+//   near CSR  per panel row: the self entry first, then every near-singular panel,
+//             with FP64 corrections dV, dK (fine rule minus far rule; self: V_ii, 0)
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lspr.h"
+
+// 32-byte aligned four-double vector (CUDA's double4 is deprecated)
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+__host__ __device__ inline dbl4 make_dbl4(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
+
+namespace lspr {
+
+constexpr double kInv4Pi = 0.079577471545947667884;   // 1 / (4 pi)
+constexpr int kTargetBlock = 64;                       // targets per interaction block (2 per lane)
+constexpr int kMaxP = 8;                               // highest Taylor order compiled
+constexpr int kMaxDepth = 10;                          // octree levels below the root (10 bits per axis)
+constexpr int kMaxNk = 32;
+
+// number of multi-indices with |k| <= P
+__host__ __device__ constexpr int n_terms(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
+
+// ---------------------------------------------------------------- device arrays
+template <class T>
+struct DArr {
+    T *p = nullptr;
+    size_t n = 0;      // elements allocated
+    cudaError_t ensure(size_t count) {
+        if (count <= n && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        size_t c = count ? count : 1;
+        cudaError_t e = cudaMalloc((void **)&p, c * sizeof(T));
+        if (e == cudaSuccess) n = c;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+struct Mesh {
+    bool ready = false;
+    int64_t N = 0, nv = 0, Ns = 0;
+    int K = 4, Kf = 19, Nk = 9;
+    double thr = 0.5;
+    double Lmax = 0, rho_max = 0;         // largest L and largest centroid-to-node distance
+    DArr<double> verts;                   // [nv*3]
+    DArr<int> tris;                       // [N*3]
+    DArr<double> cx, cy, cz, nx, ny, nz, area, L, Vself;   // [N]
+    // natural-order sources (s = K*i + g) and targets (i)
+    DArr<dbl4> src_pos64, src_nrm64;
+    DArr<dbl4> tgt64;
+    // near CSR
+    DArr<int64_t> near_ptr;               // [N+1]
+    DArr<int> near_col;                   // [nnz]
+    DArr<double> near_dV, near_dK;        // [nnz]
+    int64_t nnz = 0;
+};
+
+struct WorkOrder {   // sources/targets in the order the far-field kernels walk them
+    DArr<dbl4> spos64, snrm64;
+    DArr<float4> spos32, snrm32;
+    DArr<dbl4> tgt64;
+    DArr<float4> tgt32;
+    DArr<int> src_panel;   // [Ns]
+    DArr<int> tgt_panel;   // [N]
+};
+
+struct Tree {
+    bool ready = false;
+    double theta = 0.5;
+    int P = 6, Ncrit = 300, NT = 84;
+    int64_t nboxes = 0, ntblocks = 0;
+    int64_t n_p2p_items = 0, n_m2p_items = 0, n_m2p_pairs = 0, n_p2m_items = 0;
+    int64_t p2p_pairs = 0;
+    // boxes
+    DArr<int> box_beg, box_end, box_child, box_nchild, box_level, box_used;
+    DArr<unsigned> box_key;
+    DArr<dbl4> box_c64;   // centre (x,y,z), radius r_b
+    DArr<float4> box_c32;
+    // lists
+    DArr<int4> p2p_items;    // (target block, source begin, source end, 0)
+    DArr<int4> m2p_items;    // (target block, list begin, list end, 0)
+    DArr<int> m2p_list;      // box ids
+    DArr<int4> p2m_items;    // (box, source begin, source end, 0)
+    // moments [box][NT] x (Vre, Vim, Kre, Kim)
+    DArr<float4> mom32;
+    DArr<dbl4> mom64;
+};
+
+struct DirectItems {
+    int64_t n = 0;
+    DArr<int4> items;
+};
+
+struct Timing {
+    bool enabled = false;
+    double ms[8] = {0};
+    int64_t launches[8] = {0};
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    size_t used = 0;
+};
+
+enum TimerSlot { T_P2P = 0, T_M2P = 1, T_P2M = 2, T_NEAR = 3, T_GMRES = 4, T_TREE = 5, T_MESH = 6, T_OTHER = 7 };
+
+}  // namespace lspr
+
+struct lspr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    lspr::Mesh mesh;
+    lspr::WorkOrder wo;
+    lspr::Tree tree;
+    lspr::DirectItems direct;
+    lspr::Timing timing;
+    // per-matvec scratch
+    lspr::DArr<double> acc;            // [B][N][4]: V re/im, K re/im (far part)
+    lspr::DArr<float4> w32;            // [Ns] source weights
+    lspr::DArr<dbl4> w64;
+    lspr::DArr<double2> xbuf, ybuf;    // staging for host matvec
+    lspr::DArr<double2> sbuf;
+    // solver scratch
+    lspr::DArr<double2> gm_V, gm_w, gm_z, gm_x, gm_b, gm_r;
+    lspr::DArr<double2> gm_H, gm_cs, gm_sn, gm_g, gm_y, gm_h, gm_part;
+    lspr::DArr<double> gm_norm, gm_bnorm, gm_dpart;
+    lspr::DArr<double2> gm_s, gm_vinc, gm_eps;
+    lspr::DArr<int> gm_active;
+    lspr::DArr<double> gm_out;         // dipole + sigma results
+    // last error text
+    std::string last_error;
+    int64_t matvec_count = 0;
+    int64_t n_launches = 0;            // kernels launched by this context
+};
+
+namespace lspr {
+
+// -------------------------------------------------------------- error helpers
+int cuda_status(lspr_ctx *ctx, cudaError_t e, const char *what);
+#define LSPR_TRY(ctx, expr)                                              \
+    do {                                                                 \
+        cudaError_t e__ = (expr);                                        \
+        if (e__ != cudaSuccess) return ::lspr::cuda_status(ctx, e__, #expr); \
+    } while (0)
+#define LSPR_TRY_ST(expr)             \
+    do {                              \
+        int s__ = (expr);             \
+        if (s__ != LSPR_OK) return s__; \
+    } while (0)
+
+// timing helpers (no-ops unless enabled)
+void timer_begin(lspr_ctx *ctx, int slot, cudaEvent_t *ev);
+void timer_end(lspr_ctx *ctx, int slot, cudaEvent_t ev);
+void timer_collect(lspr_ctx *ctx);
+
+inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+// ------------------------------------------------------------ mesh.cu
+int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, int64_t ntri, int on_device,
+               const lspr_quad_opts &q);
+// natural-order work arrays (direct mode)
+int workorder_natural(lspr_ctx *ctx);
+
+// ------------------------------------------------------------ tree.cu
+int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit);
+
+// ------------------------------------------------------------ farfield.cu
+// accumulate far parts (coarse rule everywhere except own panel) into acc[N][4]
+int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, double *acc);
+int launch_p2m(lspr_ctx *ctx, bool fp64);
+int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc);
+int launch_weights(lspr_ctx *ctx, bool fp64, const double2 *x, int64_t N);
+
+// ------------------------------------------------------------ solve.cu
+// y = A(s) x for one right-hand side, x and y device [2N] complex
+int apply_operator(lspr_ctx *ctx, int mode, const double2 *x, double2 *y, const double2 *s, int B);
+// layer potentials without the block assembly: out[i] = (V dphi)_i, (K phi)_i
+int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, double2 *Kp);
+int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
+               const double *lambda_nm, int B, const lspr_solve_opts &o, double *dipole_out, double *sigma_out,
+               lspr_solve_stats *st);
+
+}  // namespace lspr

@@ -1,0 +1,644 @@
+// Operator assembly, GMRES and observables.
+//   assemble_kernel   near-singular / singular correction (CSR SpMV, FP64) fused with
+//                     the 2x2 block operator of Eq. matrix_lspr:
+//                       y_top = phi/2 + K phi - V dphi,  y_bot = phi/2 - K phi + s V dphi
+//   GMRES             B independent complex systems in lockstep (Sec. II.D-E:
+//                     complex GMRES), right 2x2 block-Jacobi preconditioner
+//                     [[1/2 + K_ii, -V_ii], [1/2 - K_ii, s V_ii]] with K_ii = 0,
+//                     classical Gram-Schmidt applied twice, Givens rotations,
+//                     FP64 Krylov basis whatever the matvec precision
+//   dipole / sigma    p = -eps_out sum_j A_j (c_j dphi2s/dn_j - phi_j n_j),
+//                     dphi2s/dn = s dphi1s/dn - ((eps_out - eps_in)/eps_out) dphi_inc/dn,
+//                     sigma = Im(k^2 e.p / (eps_out |E0|)) / Re k, k = 2 pi sqrt(eps_out)/lambda
+//                     (Eqs. dipole_def_gauss_i_final with outward normals, cext_fwa)
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "lspr_internal.cuh"
+
+namespace lspr {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {   // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+// principal square root
+__device__ __forceinline__ double2 csqrt_p(double2 z) {
+    const double r = sqrt(z.x * z.x + z.y * z.y);
+    const double re = sqrt(fmax(0.0, 0.5 * (r + z.x)));
+    double im = sqrt(fmax(0.0, 0.5 * (r - z.x)));
+    if (z.y < 0) im = -im;
+    return make_double2(re, im);
+}
+
+// ------------------------------------------------------------------ assembly
+// RAW = true writes the layer potentials (V dphi, K phi) instead of the block rows.
+template <bool RAW>
+__global__ void assemble_kernel(int64_t N, const double *__restrict__ acc, const int64_t *__restrict__ ptr,
+                                const int *__restrict__ col, const double *__restrict__ dV,
+                                const double *__restrict__ dK, const double2 *__restrict__ x, const double2 *s,
+                                double2 *y, double2 *Vd, double2 *Kp) {
+    // one warp per row: the row's near entries are read coalesced
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    double vr = 0, vi = 0, kr = 0, ki = 0;
+    for (int64_t e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
+        const int j = col[e];
+        const double a = dV[e], b = dK[e];
+        const double2 ph = x[j], dp = x[N + j];
+        vr += a * dp.x;
+        vi += a * dp.y;
+        kr += b * ph.x;
+        ki += b * ph.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vr += __shfl_xor_sync(0xffffffffu, vr, o);
+        vi += __shfl_xor_sync(0xffffffffu, vi, o);
+        kr += __shfl_xor_sync(0xffffffffu, kr, o);
+        ki += __shfl_xor_sync(0xffffffffu, ki, o);
+    }
+    if (lane != 0) return;
+    const double2 V = make_double2(acc[4 * i] + vr, acc[4 * i + 1] + vi);
+    const double2 K = make_double2(acc[4 * i + 2] + kr, acc[4 * i + 3] + ki);
+    if (RAW) {
+        Vd[i] = V;
+        Kp[i] = K;
+        return;
+    }
+    const double2 ph = x[i];
+    const double2 sv = cmul(*s, V);
+    y[i] = make_double2(0.5 * ph.x + K.x - V.x, 0.5 * ph.y + K.y - V.y);
+    y[N + i] = make_double2(0.5 * ph.x - K.x + sv.x, 0.5 * ph.y - K.y + sv.y);
+}
+
+static int far_part(lspr_ctx *ctx, int mode, const double2 *x) {
+    const bool fp64 = mode == LSPR_DIRECT_FP64 || mode == LSPR_TREE_FP64;
+    const bool tree = mode == LSPR_TREE_FP64 || mode == LSPR_TREE_FP32;
+    const int64_t N = ctx->mesh.N;
+    if (tree && !ctx->tree.ready) return LSPR_E_STATE;
+    LSPR_TRY(ctx, ctx->acc.ensure(4 * N));
+    LSPR_TRY(ctx, cudaMemsetAsync(ctx->acc.p, 0, sizeof(double) * 4 * N, ctx->stream));
+    LSPR_TRY_ST(launch_weights(ctx, fp64, x, N));
+    if (tree) {
+        LSPR_TRY_ST(launch_p2m(ctx, fp64));
+        LSPR_TRY_ST(launch_p2p(ctx, fp64, ctx->tree.p2p_items.p, ctx->tree.n_p2p_items, ctx->acc.p));
+        LSPR_TRY_ST(launch_m2p(ctx, fp64, ctx->acc.p));
+    } else {
+        LSPR_TRY_ST(launch_p2p(ctx, fp64, ctx->direct.items.p, ctx->direct.n, ctx->acc.p));
+    }
+    ++ctx->matvec_count;
+    return LSPR_OK;
+}
+
+int apply_operator(lspr_ctx *ctx, int mode, const double2 *x, double2 *y, const double2 *s, int B) {
+    const Mesh &m = ctx->mesh;
+    const int64_t N = m.N;
+    for (int b = 0; b < B; ++b) {
+        LSPR_TRY_ST(far_part(ctx, mode, x + (size_t)b * 2 * N));
+        cudaEvent_t ev;
+        timer_begin(ctx, T_NEAR, &ev);
+        ++ctx->n_launches;
+        assemble_kernel<false><<<grid_for(N * 32, 256), 256, 0, ctx->stream>>>(
+            N, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x + (size_t)b * 2 * N, s + b,
+            y + (size_t)b * 2 * N, nullptr, nullptr);
+        timer_end(ctx, T_NEAR, ev);
+        LSPR_TRY(ctx, cudaGetLastError());
+    }
+    return LSPR_OK;
+}
+
+int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, double2 *Kp) {
+    const Mesh &m = ctx->mesh;
+    LSPR_TRY_ST(far_part(ctx, mode, x));
+    ++ctx->n_launches;
+    assemble_kernel<true><<<grid_for(m.N * 32, 256), 256, 0, ctx->stream>>>(
+        m.N, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr, nullptr, Vd, Kp);
+    LSPR_TRY(ctx, cudaGetLastError());
+    return LSPR_OK;
+}
+
+// --------------------------------------------------------------------- GMRES
+constexpr int kRedThreads = 256;
+constexpr int kChunk = 4096;   // elements per partial-sum block
+
+// right preconditioner: out = M^-1 in, per panel 2x2 block
+__global__ void precond_kernel(int B, int64_t N, const double *__restrict__ Vself, const double2 *__restrict__ s,
+                               const double2 *in, int64_t in_stride, double2 *out, const int *active) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (t >= N || b >= B || (active && !active[b])) return;
+    const double V = Vself[t];
+    const double2 sb = s[b];
+    const double2 u0 = in[b * in_stride + t], u1 = in[b * in_stride + N + t];
+    // [[1/2, -V], [1/2, s V]]^-1 = [[s V, V], [-1/2, 1/2]] / (V (1 + s) / 2)
+    const double2 det = make_double2(0.5 * V * (1.0 + sb.x), 0.5 * V * sb.y);
+    const double2 a = cadd(cmul(cscale(sb, V), u0), cscale(u1, V));
+    const double2 c = make_double2(0.5 * (u1.x - u0.x), 0.5 * (u1.y - u0.y));
+    out[b * 2 * N + t] = cdiv(a, det);
+    out[b * 2 * N + N + t] = cdiv(c, det);
+}
+
+// part[b][i][chunk] = sum_k conj(V[b][i][k]) w[b][k]
+__global__ void dot_partial_kernel(int B, int64_t n2, int nv, const double2 *__restrict__ V, int64_t vstride_b,
+                                   const double2 *__restrict__ w, double2 *part, int nchunks, const int *active) {
+    __shared__ double2 red[kRedThreads];
+    const int chunk = blockIdx.x, i = blockIdx.y, b = blockIdx.z;
+    if (active && !active[b]) return;
+    const double2 *v = V + b * vstride_b + (int64_t)i * n2;
+    const double2 *ww = w + (int64_t)b * n2;
+    double2 s = make_double2(0, 0);
+    const int64_t beg = (int64_t)chunk * kChunk, end = min(n2, beg + kChunk);
+    for (int64_t k = beg + threadIdx.x; k < end; k += blockDim.x) s = cadd(s, cconjmul(v[k], ww[k]));
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[((int64_t)b * nv + i) * nchunks + chunk] = red[0];
+}
+
+// h[b][i] = sum of partials; H[b][i][j] += h (column j of the Hessenberg matrix)
+__global__ void dot_final_kernel(int B, int nv, int nchunks, const double2 *part, double2 *h, double2 *H, int m, int j,
+                                 const int *active) {
+    const int i = threadIdx.x + blockIdx.x * blockDim.x, b = blockIdx.y;
+    if (i >= nv || (active && !active[b])) return;
+    double2 s = make_double2(0, 0);
+    for (int c = 0; c < nchunks; ++c) s = cadd(s, part[((int64_t)b * nv + i) * nchunks + c]);
+    h[b * (m + 1) + i] = s;
+    if (H) {
+        double2 &e = H[(int64_t)b * (m + 1) * m + (int64_t)i * m + j];
+        e = cadd(e, s);
+    }
+}
+
+// w[b] -= sum_i V[b][i] h[b][i]
+__global__ void axpy_basis_kernel(int B, int64_t n2, int nv, const double2 *__restrict__ V, int64_t vstride_b,
+                                  const double2 *__restrict__ h, int m, double2 *w, const int *active) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (k >= n2 || (active && !active[b])) return;
+    double2 acc = w[(int64_t)b * n2 + k];
+    for (int i = 0; i < nv; ++i) acc = csub(acc, cmul(V[b * vstride_b + (int64_t)i * n2 + k], h[b * (m + 1) + i]));
+    w[(int64_t)b * n2 + k] = acc;
+}
+
+__global__ void norm_partial_kernel(int B, int64_t n2, const double2 *__restrict__ w, int64_t wstride, double *part,
+                                    int nchunks, const int *active) {
+    __shared__ double red[kRedThreads];
+    const int chunk = blockIdx.x, b = blockIdx.y;
+    if (active && !active[b]) return;
+    double s = 0;
+    const int64_t beg = (int64_t)chunk * kChunk, end = min(n2, beg + kChunk);
+    for (int64_t k = beg + threadIdx.x; k < end; k += blockDim.x) s += cabs2(w[b * wstride + k]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)b * nchunks + chunk] = red[0];
+}
+
+__global__ void norm_final_kernel(int B, int nchunks, const double *part, double *out, const int *active) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B || (active && !active[b])) return;
+    double s = 0;
+    for (int c = 0; c < nchunks; ++c) s += part[(int64_t)b * nchunks + c];
+    out[b] = sqrt(s);
+}
+
+// v = w / nrm (nrm > 0), optionally records H[b][j+1][j] = nrm and starts g = (nrm, 0, ...)
+__global__ void scale_kernel(int B, int64_t n2, const double2 *w, int64_t wstride, double2 *v, int64_t vstride,
+                             const double *nrm, const int *active) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (k >= n2 || (active && !active[b])) return;
+    const double d = nrm[b];
+    v[b * vstride + k] = d > 0 ? cscale(w[b * wstride + k], 1.0 / d) : make_double2(0, 0);
+}
+
+// apply the previous rotations to column j, build rotation j, update g; resid[b] = |g_{j+1}|
+__global__ void givens_kernel(int B, int m, int j, double2 *H, const double *hn, double2 *cs, double2 *sn, double2 *g,
+                              double *resid, const int *active) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B || (active && !active[b])) return;
+    double2 *Hb = H + (int64_t)b * (m + 1) * m;
+    double2 *c = cs + (int64_t)b * m, *s = sn + (int64_t)b * m, *gb = g + (int64_t)b * (m + 1);
+    Hb[(j + 1) * m + j] = make_double2(hn[b], 0.0);
+    for (int i = 0; i < j; ++i) {
+        const double2 a = Hb[i * m + j], d = Hb[(i + 1) * m + j];
+        Hb[i * m + j] = cadd(cmul(c[i], a), cmul(s[i], d));
+        const double2 sc = make_double2(-s[i].x, s[i].y);   // -conj(s)
+        Hb[(i + 1) * m + j] = cadd(cmul(sc, a), cmul(c[i], d));
+    }
+    const double2 a = Hb[j * m + j];
+    const double2 d = Hb[(j + 1) * m + j];
+    const double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(d));
+    const double t = sqrt(aa * aa + bb * bb);
+    if (aa == 0.0) {
+        c[j] = make_double2(0, 0);
+        s[j] = make_double2(1, 0);
+    } else {
+        c[j] = make_double2(aa / t, 0);
+        const double2 ph = cscale(a, 1.0 / aa);
+        s[j] = cscale(cmul(ph, make_double2(d.x, -d.y)), 1.0 / t);
+    }
+    Hb[j * m + j] = cadd(cmul(c[j], a), cmul(s[j], d));
+    Hb[(j + 1) * m + j] = make_double2(0, 0);
+    const double2 gj = gb[j];
+    gb[j + 1] = cmul(make_double2(-s[j].x, s[j].y), gj);
+    gb[j] = cmul(c[j], gj);
+    resid[b] = sqrt(cabs2(gb[j + 1]));
+}
+
+// back substitution H y = g for the first jb[b] columns
+__global__ void trisolve_kernel(int B, int m, const double2 *H, const double2 *g, const int *jb, double2 *y) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double2 *Hb = H + (int64_t)b * (m + 1) * m;
+    const double2 *gb = g + (int64_t)b * (m + 1);
+    double2 *yb = y + (int64_t)b * m;
+    const int n = jb[b];
+    for (int i = n - 1; i >= 0; --i) {
+        double2 acc = gb[i];
+        for (int k = i + 1; k < n; ++k) acc = csub(acc, cmul(Hb[i * m + k], yb[k]));
+        yb[i] = cdiv(acc, Hb[i * m + i]);
+    }
+}
+
+// z[b] = sum_{i < jb} V[b][i] y[b][i]
+__global__ void combine_kernel(int B, int64_t n2, const double2 *__restrict__ V, int64_t vstride_b,
+                               const double2 *__restrict__ y, int m, const int *jb, double2 *z) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (k >= n2) return;
+    double2 acc = make_double2(0, 0);
+    for (int i = 0; i < jb[b]; ++i) acc = cadd(acc, cmul(V[b * vstride_b + (int64_t)i * n2 + k], y[(int64_t)b * m + i]));
+    z[(int64_t)b * n2 + k] = acc;
+}
+
+// v_0 = -(A x - b) / beta
+__global__ void init_basis_kernel(int B, int64_t n2, const double2 *w, double2 *V, int64_t vstride, const double *nrm,
+                                  const int *active) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (k >= n2 || (active && !active[b])) return;
+    V[b * vstride + k] = cscale(w[(int64_t)b * n2 + k], -1.0 / nrm[b]);
+}
+
+__global__ void add_kernel(int B, int64_t n2, double2 *x, const double2 *d, double sign) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (k >= n2) return;
+    const double2 a = x[(int64_t)b * n2 + k], c = d[(int64_t)b * n2 + k];
+    x[(int64_t)b * n2 + k] = make_double2(a.x + sign * c.x, a.y + sign * c.y);
+}
+
+// ------------------------------------------------------------------ RHS
+__global__ void dphi_inc_kernel(int64_t N, const double *nx, const double *ny, const double *nz, double E0x,
+                                double E0y, double E0z, double2 *x) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    x[i] = make_double2(0, 0);
+    x[N + i] = make_double2(-(E0x * nx[i] + E0y * ny[i] + E0z * nz[i]), 0.0);
+}
+
+// b[b] = [0 ; ((eps_out - eps_in_b)/eps_out) * V dphi_inc]
+__global__ void rhs_kernel(int B, int64_t N, const double2 *__restrict__ Vinc, const double2 *eps_in, double2 eps_out,
+                           double2 *rhs) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (i >= N) return;
+    const double2 f = cdiv(csub(eps_out, eps_in[b]), eps_out);
+    rhs[(int64_t)b * 2 * N + i] = make_double2(0, 0);
+    rhs[(int64_t)b * 2 * N + N + i] = cmul(f, Vinc[i]);
+}
+
+// ---------------------------------------------------------- dipole + sigma
+__global__ void dipole_partial_kernel(int B, int64_t N, const double2 *__restrict__ x, const double2 *eps_in,
+                                      double2 eps_out, const double *cx, const double *cy, const double *cz,
+                                      const double *nx, const double *ny, const double *nz, const double *area,
+                                      double E0x, double E0y, double E0z, double *part, int nchunks) {
+    __shared__ double red[6][kRedThreads];
+    const int chunk = blockIdx.x, b = blockIdx.y;
+    const double2 s = cdiv(eps_in[b], eps_out);
+    const double2 f = cdiv(csub(eps_out, eps_in[b]), eps_out);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t beg = (int64_t)chunk * kChunk, end = min(N, beg + kChunk);
+    for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
+        const double2 ph = x[(int64_t)b * 2 * N + j], dp = x[(int64_t)b * 2 * N + N + j];
+        const double dinc = -(E0x * nx[j] + E0y * ny[j] + E0z * nz[j]);
+        const double2 d2 = csub(cmul(s, dp), cscale(f, dinc));
+        const double A = area[j];
+        const double c[3] = {cx[j], cy[j], cz[j]}, n[3] = {nx[j], ny[j], nz[j]};
+        for (int d = 0; d < 3; ++d) {
+            acc[2 * d] += A * (c[d] * d2.x - ph.x * n[d]);
+            acc[2 * d + 1] += A * (c[d] * d2.y - ph.y * n[d]);
+        }
+    }
+    for (int q = 0; q < 6; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int q = 0; q < 6; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 6; ++q) part[((int64_t)b * nchunks + chunk) * 6 + q] = red[q][0];
+}
+
+// out[b] = (p_x, p_y, p_z as complex, sigma): 7 doubles per wavelength
+__global__ void dipole_final_kernel(int B, int nchunks, const double *part, double2 eps_out, double E0x, double E0y,
+                                    double E0z, const double *lambda, double *out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < nchunks; ++c)
+        for (int q = 0; q < 6; ++q) s[q] += part[((int64_t)b * nchunks + c) * 6 + q];
+    double2 p[3];
+    for (int d = 0; d < 3; ++d) {
+        const double2 v = cmul(make_double2(-eps_out.x, -eps_out.y), make_double2(s[2 * d], s[2 * d + 1]));
+        p[d] = v;
+        out[b * 7 + 2 * d] = v.x;
+        out[b * 7 + 2 * d + 1] = v.y;
+    }
+    const double E = sqrt(E0x * E0x + E0y * E0y + E0z * E0z);
+    const double2 ep = cscale(cadd(cadd(cscale(p[0], E0x), cscale(p[1], E0y)), cscale(p[2], E0z)), 1.0 / E);
+    const double2 k = cscale(csqrt_p(eps_out), 2.0 * M_PI / lambda[b]);
+    const double2 q = cdiv(cmul(cmul(k, k), ep), cscale(eps_out, E));
+    out[b * 7 + 6] = q.y / k.x;
+}
+
+// ------------------------------------------------------------------ driver
+static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double tol, const double2 *s_d,
+                       const double2 *b_d, double2 *x_d, std::vector<int> &iters, std::vector<double> &relres,
+                       const std::vector<double> &bnorm) {
+    const Mesh &me = ctx->mesh;
+    const int64_t N = me.N, n2 = 2 * N;
+    cudaStream_t st = ctx->stream;
+    const int nch = (int)((n2 + kChunk - 1) / kChunk);
+    const int64_t vstride = (int64_t)(m + 1) * n2;
+    LSPR_TRY(ctx, ctx->gm_V.ensure((size_t)B * vstride));
+    LSPR_TRY(ctx, ctx->gm_w.ensure((size_t)B * n2));
+    LSPR_TRY(ctx, ctx->gm_z.ensure((size_t)B * n2));
+    LSPR_TRY(ctx, ctx->gm_H.ensure((size_t)B * (m + 1) * m));
+    LSPR_TRY(ctx, ctx->gm_cs.ensure((size_t)B * m));
+    LSPR_TRY(ctx, ctx->gm_sn.ensure((size_t)B * m));
+    LSPR_TRY(ctx, ctx->gm_g.ensure((size_t)B * (m + 1)));
+    LSPR_TRY(ctx, ctx->gm_y.ensure((size_t)B * m));
+    LSPR_TRY(ctx, ctx->gm_h.ensure((size_t)B * (m + 1)));
+    LSPR_TRY(ctx, ctx->gm_part.ensure((size_t)B * (m + 1) * nch));
+    LSPR_TRY(ctx, ctx->gm_dpart.ensure((size_t)B * nch));
+    LSPR_TRY(ctx, ctx->gm_norm.ensure((size_t)2 * B));
+    LSPR_TRY(ctx, ctx->gm_active.ensure((size_t)2 * B));
+    double2 *V = ctx->gm_V.p, *w = ctx->gm_w.p, *z = ctx->gm_z.p;
+    double *nrm = ctx->gm_norm.p, *resid = ctx->gm_norm.p + B;
+    int *active = ctx->gm_active.p, *jb_d = ctx->gm_active.p + B;
+    const dim3 gv(grid_for(n2, 256), B), gN(grid_for(N, 256), B);
+    std::vector<int> act(B, 1), jb(B, 0);
+    std::vector<double> hres(B);
+    int total = 0;
+    for (int b = 0; b < B; ++b) { iters[b] = 0; relres[b] = 1.0; }
+    cudaEvent_t ev;
+    while (true) {
+        // explicit residual r = b - A x for the systems still running
+        LSPR_TRY_ST(apply_operator(ctx, mode, x_d, w, s_d, B));
+        timer_begin(ctx, T_GMRES, &ev);
+        ++ctx->n_launches;
+        add_kernel<<<gv, 256, 0, st>>>(B, n2, w, b_d, -1.0);                  // w = A x - b
+        ++ctx->n_launches;
+        norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, w, n2, ctx->gm_dpart.p, nch, nullptr);
+        ++ctx->n_launches;
+        norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, nrm, nullptr);
+        timer_end(ctx, T_GMRES, ev);
+        std::vector<double> beta(B);
+        LSPR_TRY(ctx, cudaMemcpyAsync(beta.data(), nrm, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaStreamSynchronize(st));
+        bool any = false;
+        for (int b = 0; b < B; ++b) {
+            relres[b] = beta[b] / bnorm[b];
+            act[b] = relres[b] > tol && iters[b] < maxiter && std::isfinite(relres[b]);
+            any = any || act[b];
+        }
+        if (!any) break;
+        LSPR_TRY(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+        // v0 = -(A x - b) / beta, g = (beta, 0, ...), H = 0
+        LSPR_TRY(ctx, cudaMemsetAsync(ctx->gm_H.p, 0, sizeof(double2) * B * (m + 1) * m, st));
+        LSPR_TRY(ctx, cudaMemsetAsync(ctx->gm_g.p, 0, sizeof(double2) * B * (m + 1), st));
+        {
+            std::vector<double2> g0(B * (m + 1), make_double2(0, 0));
+            for (int b = 0; b < B; ++b) g0[b * (m + 1)] = make_double2(beta[b], 0);
+            LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_g.p, g0.data(), sizeof(double2) * B * (m + 1), cudaMemcpyHostToDevice, st));
+            LSPR_TRY(ctx, cudaStreamSynchronize(st));
+        }
+        ++ctx->n_launches;
+        init_basis_kernel<<<gv, 256, 0, st>>>(B, n2, w, V, vstride, nrm, active);
+        for (int b = 0; b < B; ++b) jb[b] = 0;
+        int j = 0;
+        for (; j < m; ++j) {
+            // z = M^-1 v_j ; w = A z
+            timer_begin(ctx, T_GMRES, &ev);
+            ++ctx->n_launches;
+            precond_kernel<<<gN, 256, 0, st>>>(B, N, me.Vself.p, s_d, V + (int64_t)j * n2, vstride, z, active);
+            timer_end(ctx, T_GMRES, ev);
+            LSPR_TRY_ST(apply_operator(ctx, mode, z, w, s_d, B));
+            timer_begin(ctx, T_GMRES, &ev);
+            for (int pass = 0; pass < 2; ++pass) {
+                ++ctx->n_launches;
+                dot_partial_kernel<<<dim3(nch, j + 1, B), kRedThreads, 0, st>>>(B, n2, j + 1, V, vstride, w,
+                                                                                  ctx->gm_part.p, nch, active);
+                ++ctx->n_launches;
+                dot_final_kernel<<<dim3(grid_for(j + 1, 64), B), 64, 0, st>>>(B, j + 1, nch, ctx->gm_part.p,
+                                                                               ctx->gm_h.p, ctx->gm_H.p, m, j, active);
+                ++ctx->n_launches;
+                axpy_basis_kernel<<<gv, 256, 0, st>>>(B, n2, j + 1, V, vstride, ctx->gm_h.p, m, w, active);
+            }
+            ++ctx->n_launches;
+            norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, w, n2, ctx->gm_dpart.p, nch, active);
+            ++ctx->n_launches;
+            norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, nrm, active);
+            ++ctx->n_launches;
+            scale_kernel<<<gv, 256, 0, st>>>(B, n2, w, n2, V + (int64_t)(j + 1) * n2, vstride, nrm, active);
+            ++ctx->n_launches;
+            givens_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, m, j, ctx->gm_H.p, nrm, ctx->gm_cs.p, ctx->gm_sn.p,
+                                                          ctx->gm_g.p, resid, active);
+            timer_end(ctx, T_GMRES, ev);
+            LSPR_TRY(ctx, cudaGetLastError());
+            LSPR_TRY(ctx, cudaMemcpyAsync(hres.data(), resid, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+            LSPR_TRY(ctx, cudaStreamSynchronize(st));
+            ++total;
+            bool any_left = false;
+            for (int b = 0; b < B; ++b) {
+                if (!act[b]) continue;
+                jb[b] = j + 1;
+                ++iters[b];
+                if (hres[b] / bnorm[b] <= tol || iters[b] >= maxiter || !std::isfinite(hres[b])) act[b] = 0;
+                any_left = any_left || act[b];
+            }
+            if (!any_left) break;
+            LSPR_TRY(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+        }
+        // x += M^-1 V y
+        LSPR_TRY(ctx, cudaMemcpyAsync(jb_d, jb.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+        timer_begin(ctx, T_GMRES, &ev);
+        ++ctx->n_launches;
+        trisolve_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, m, ctx->gm_H.p, ctx->gm_g.p, jb_d, ctx->gm_y.p);
+        ++ctx->n_launches;
+        combine_kernel<<<gv, 256, 0, st>>>(B, n2, V, vstride, ctx->gm_y.p, m, jb_d, w);
+        ++ctx->n_launches;
+        precond_kernel<<<gN, 256, 0, st>>>(B, N, me.Vself.p, s_d, w, n2, z, nullptr);
+        ++ctx->n_launches;
+        add_kernel<<<gv, 256, 0, st>>>(B, n2, x_d, z, 1.0);
+        timer_end(ctx, T_GMRES, ev);
+        LSPR_TRY(ctx, cudaGetLastError());
+    }
+    return LSPR_OK;
+}
+
+int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
+               const double *lambda_nm, int B, const lspr_solve_opts &o, double *dipole_out, double *sigma_out,
+               lspr_solve_stats *stt) {
+    const Mesh &me = ctx->mesh;
+    const int64_t N = me.N, n2 = 2 * N;
+    cudaStream_t st = ctx->stream;
+    const int mode = o.mode;
+    const bool tree = mode == LSPR_TREE_FP64 || mode == LSPR_TREE_FP32;
+    const int mode64 = tree ? LSPR_TREE_FP64 : LSPR_DIRECT_FP64;
+    const double2 eout = make_double2(eps_out_re, eps_out_im);
+    LSPR_TRY(ctx, ctx->gm_eps.ensure(B));
+    LSPR_TRY(ctx, ctx->gm_s.ensure(B));
+    LSPR_TRY(ctx, ctx->gm_b.ensure((size_t)B * n2));
+    LSPR_TRY(ctx, ctx->gm_x.ensure((size_t)B * n2));
+    LSPR_TRY(ctx, ctx->gm_r.ensure((size_t)B * n2));
+    LSPR_TRY(ctx, ctx->gm_vinc.ensure(2 * n2));
+    LSPR_TRY(ctx, ctx->gm_out.ensure((size_t)B * 8 + B));
+    std::vector<double2> he(B), hs(B);
+    for (int b = 0; b < B; ++b) {
+        he[b] = make_double2(eps_in[2 * b], eps_in[2 * b + 1]);
+        const double d = eps_out_re * eps_out_re + eps_out_im * eps_out_im;
+        hs[b] = make_double2((he[b].x * eps_out_re + he[b].y * eps_out_im) / d,
+                             (he[b].y * eps_out_re - he[b].x * eps_out_im) / d);
+    }
+    LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_eps.p, he.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, st));
+    LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_s.p, hs.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, st));
+    // right-hand side in FP64: V (dphi_inc/dn)
+    double2 *xin = ctx->gm_vinc.p, *Vinc = ctx->gm_vinc.p + n2;
+    ++ctx->n_launches;
+    dphi_inc_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, me.nx.p, me.ny.p, me.nz.p, E0[0], E0[1], E0[2], xin);
+    LSPR_TRY_ST(layer_potentials(ctx, mode64, xin, Vinc, Vinc + N));
+    ++ctx->n_launches;
+    rhs_kernel<<<dim3(grid_for(N, 256), B), 256, 0, st>>>(B, N, Vinc, ctx->gm_eps.p, eout, ctx->gm_b.p);
+    LSPR_TRY(ctx, cudaMemsetAsync(ctx->gm_x.p, 0, sizeof(double2) * B * n2, st));
+    // ||b||
+    const int nch = (int)((n2 + kChunk - 1) / kChunk);
+    LSPR_TRY(ctx, ctx->gm_dpart.ensure((size_t)B * nch));
+    LSPR_TRY(ctx, ctx->gm_bnorm.ensure(B));
+    ++ctx->n_launches;
+    norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, ctx->gm_b.p, n2, ctx->gm_dpart.p, nch, nullptr);
+    ++ctx->n_launches;
+    norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, ctx->gm_bnorm.p, nullptr);
+    LSPR_TRY(ctx, cudaGetLastError());
+    std::vector<double> bnorm(B);
+    LSPR_TRY(ctx, cudaMemcpyAsync(bnorm.data(), ctx->gm_bnorm.p, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    for (auto &v : bnorm)
+        if (!(v > 0)) v = 1.0;
+
+    std::vector<int> iters(B, 0);
+    std::vector<double> relres(B, 1.0);
+    const int m = std::max(1, std::min(o.restart, 512));
+    const bool refine = o.refine && (mode == LSPR_TREE_FP32 || mode == LSPR_DIRECT_FP32);
+    if (!refine) {
+        LSPR_TRY_ST(gmres_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p, iters, relres,
+                                bnorm));
+    } else {
+        // iterative refinement: r = b - A64 x in FP64, correction from the FP32-mode GMRES
+        const int mode_hi = tree ? LSPR_TREE_FP64 : LSPR_DIRECT_FP64;
+        std::vector<int> it2(B, 0);
+        std::vector<double> rr2(B, 1.0);
+        DArr<double2> dx;
+        LSPR_TRY(ctx, dx.ensure((size_t)B * n2));
+        for (int cycle = 0; cycle < 8; ++cycle) {
+            LSPR_TRY_ST(apply_operator(ctx, mode_hi, ctx->gm_x.p, ctx->gm_r.p, ctx->gm_s.p, B));
+            ++ctx->n_launches;
+            add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_b.p, -1.0);   // A x - b
+            ++ctx->n_launches;
+            norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, ctx->gm_r.p, n2, ctx->gm_dpart.p, nch,
+                                                                      nullptr);
+            ++ctx->n_launches;
+            norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, ctx->gm_bnorm.p, nullptr);
+            std::vector<double> rn(B);
+            LSPR_TRY(ctx, cudaMemcpyAsync(rn.data(), ctx->gm_bnorm.p, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+            LSPR_TRY(ctx, cudaStreamSynchronize(st));
+            bool done = true;
+            for (int b = 0; b < B; ++b) {
+                relres[b] = rn[b] / bnorm[b];
+                done = done && (relres[b] <= o.tol);
+            }
+            if (done) break;
+            // solve A d = r = b - A x to a relative tolerance that brings ||b - A x|| under tol
+            std::vector<double> rnorm(B);
+            double inner = 0.1;
+            for (int b = 0; b < B; ++b) {
+                rnorm[b] = rn[b] > 0 ? rn[b] : 1.0;
+                if (relres[b] > o.tol) inner = std::min(inner, 0.5 * o.tol / relres[b]);
+            }
+            inner = std::max(inner, 1e-6);
+            ++ctx->n_launches;
+            add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_r.p, -2.0);   // r = b - A x
+            LSPR_TRY(ctx, cudaMemsetAsync(dx.p, 0, sizeof(double2) * B * n2, st));
+            LSPR_TRY_ST(gmres_solve(ctx, mode, B, m, o.maxiter, inner, ctx->gm_s.p, ctx->gm_r.p, dx.p, it2, rr2, rnorm));
+            ++ctx->n_launches;
+            add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_x.p, dx.p, 1.0);
+            for (int b = 0; b < B; ++b) iters[b] += it2[b];
+        }
+        LSPR_TRY(ctx, cudaStreamSynchronize(st));
+        dx.release();
+    }
+    // dipole and sigma
+    const int nchN = (int)((N + kChunk - 1) / kChunk);
+    DArr<double> part, lam;
+    LSPR_TRY(ctx, part.ensure((size_t)B * nchN * 6));
+    LSPR_TRY(ctx, lam.ensure(B));
+    LSPR_TRY(ctx, cudaMemcpyAsync(lam.p, lambda_nm, sizeof(double) * B, cudaMemcpyHostToDevice, st));
+    ++ctx->n_launches;
+    dipole_partial_kernel<<<dim3(nchN, B), kRedThreads, 0, st>>>(B, N, ctx->gm_x.p, ctx->gm_eps.p, eout, me.cx.p,
+                                                                 me.cy.p, me.cz.p, me.nx.p, me.ny.p, me.nz.p,
+                                                                 me.area.p, E0[0], E0[1], E0[2], part.p, nchN);
+    ++ctx->n_launches;
+    dipole_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nchN, part.p, eout, E0[0], E0[1], E0[2], lam.p,
+                                                         ctx->gm_out.p);
+    LSPR_TRY(ctx, cudaGetLastError());
+    std::vector<double> out((size_t)B * 7);
+    LSPR_TRY(ctx, cudaMemcpyAsync(out.data(), ctx->gm_out.p, sizeof(double) * 7 * B, cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    part.release();
+    lam.release();
+    int rc = LSPR_OK;
+    for (int b = 0; b < B; ++b) {
+        for (int q = 0; q < 6; ++q) dipole_out[6 * b + q] = out[7 * b + q];
+        sigma_out[b] = out[7 * b + 6];
+        const bool ok = relres[b] <= o.tol;
+        if (!ok) rc = LSPR_E_NOT_CONVERGED;
+        if (stt) {
+            if (stt->iterations) stt->iterations[b] = iters[b];
+            if (stt->residual) stt->residual[b] = relres[b];
+            if (stt->status) stt->status[b] = ok ? LSPR_OK : LSPR_E_NOT_CONVERGED;
+        }
+    }
+    return rc;
+}
+
+}  // namespace lspr

@@ -1,0 +1,647 @@
+// Treecode structures (Sec. II.D): the octree over the Gauss-node sources with at
+// most N_crit sources per leaf, and per block of 64 collocation targets the list of
+// boxes accepted by the multipole-acceptance criterion r_b < theta * r (Taylor
+// expansion, M2P) and of leaves summed directly (P2P).
+//
+// Device pipeline: bounding cube -> 30-bit Morton keys (10 bits per axis) ->
+// LSD radix sort (4-bit digits, stable) of sources and targets -> permuted
+// work-order arrays -> octree, level by level in one CTA (deterministic box
+// numbering) -> box centres (centre of the sources' bounding box) and radii
+// r_b = max |y - c| -> target-block bounding boxes -> interaction lists (count,
+// scan, fill; one thread per target block walks the tree depth first).
+#include <algorithm>
+#include <cmath>
+
+#include "lspr_internal.cuh"
+
+namespace lspr {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kDigitBits = 4;
+constexpr int kDigits = 1 << kDigitBits;
+constexpr int kP2PChunk = 1024;     // sources per P2P work item (upper bound)
+constexpr int kM2PSeg = 16;         // boxes per M2P work item
+constexpr int kP2MChunk = 512;      // sources per P2M work item
+constexpr int kStack = 96;
+
+// ------------------------------------------------------------ bounding cube
+__global__ void bbox_kernel(const dbl4 *__restrict__ a, int64_t na, const dbl4 *__restrict__ b, int64_t nb,
+                            double *out /* lo[3], hi[3] */) {
+    __shared__ double lo[3][1024], hi[3][1024];
+    const int t = threadIdx.x;
+    double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = t; i < na + nb; i += blockDim.x) {
+        const dbl4 p = i < na ? a[i] : b[i - na];
+        l[0] = fmin(l[0], p.x); l[1] = fmin(l[1], p.y); l[2] = fmin(l[2], p.z);
+        h[0] = fmax(h[0], p.x); h[1] = fmax(h[1], p.y); h[2] = fmax(h[2], p.z);
+    }
+    for (int d = 0; d < 3; ++d) { lo[d][t] = l[d]; hi[d][t] = h[d]; }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s)
+            for (int d = 0; d < 3; ++d) {
+                lo[d][t] = fmin(lo[d][t], lo[d][t + s]);
+                hi[d][t] = fmax(hi[d][t], hi[d][t + s]);
+            }
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int d = 0; d < 3; ++d) { out[d] = lo[d][0]; out[3 + d] = hi[d][0]; }
+}
+
+__device__ __forceinline__ unsigned spread10(unsigned v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// key bit 3l+2 / 3l+1 / 3l = x / y / z bit l, so the top triple selects the octant
+__global__ void morton_kernel(const dbl4 *__restrict__ p, int64_t n, const double *cube /* lo[3], size */,
+                              unsigned *keys, int *vals) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const dbl4 q = p[i];
+    const double inv = 1024.0 / cube[3];
+    unsigned ix = (unsigned)min(1023.0, fmax(0.0, floor((q.x - cube[0]) * inv)));
+    unsigned iy = (unsigned)min(1023.0, fmax(0.0, floor((q.y - cube[1]) * inv)));
+    unsigned iz = (unsigned)min(1023.0, fmax(0.0, floor((q.z - cube[2]) * inv)));
+    keys[i] = (spread10(ix) << 2) | (spread10(iy) << 1) | spread10(iz);
+    vals[i] = (int)i;
+}
+
+// ----------------------------------------------------------------- radix sort
+__global__ void radix_hist_kernel(const unsigned *__restrict__ keys, int64_t n, int shift, int nblocks, int *hist) {
+    __shared__ int cnt[kDigits];
+    if (threadIdx.x < kDigits) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int k = threadIdx.x; k < kSortTile; k += blockDim.x) {
+        const int64_t i = base + k;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & (kDigits - 1)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kDigits) hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// exclusive scan of an int array (single block, any length)
+__global__ void scan_int_kernel(const int *in, int64_t n, int *out, int64_t *total) {
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t b = t * per, e = min(n, b + per);
+    int64_t s = 0;
+    for (int64_t k = b; k < e; ++k) s += in[k];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        int64_t v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = part[t] - s;
+    for (int64_t k = b; k < e; ++k) {
+        out[k] = (int)run;
+        run += in[k];
+    }
+    if (t == blockDim.x - 1 && total) *total = part[t];
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const unsigned *__restrict__ kin,
+                                                                     const int *__restrict__ vin, int64_t n, int shift,
+                                                                     int nblocks, const int *__restrict__ offs,
+                                                                     unsigned *kout, int *vout) {
+    __shared__ int cnt[kDigits * kSortThreads];
+    __shared__ int tsum[kSortThreads];
+    const int t = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)t * kSortItems;
+    unsigned k[kSortItems];
+    int v[kSortItems];
+    for (int d = 0; d < kDigits; ++d) cnt[d * kSortThreads + t] = 0;
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int64_t i = base + j;
+        k[j] = i < n ? kin[i] : 0u;
+        v[j] = i < n ? vin[i] : 0;
+        if (i < n) cnt[((k[j] >> shift) & (kDigits - 1)) * kSortThreads + t] += 1;
+    }
+    __syncthreads();
+    // exclusive scan over cnt in digit-major order (each thread owns kDigits consecutive entries)
+    int own[kDigits];
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < kDigits; ++j) {
+        own[j] = cnt[t * kDigits + j];
+        s += own[j];
+    }
+    tsum[t] = s;
+    __syncthreads();
+    for (int off = 1; off < kSortThreads; off <<= 1) {
+        int x = t >= off ? tsum[t - off] : 0;
+        __syncthreads();
+        tsum[t] += x;
+        __syncthreads();
+    }
+    int run = tsum[t] - s;
+#pragma unroll
+    for (int j = 0; j < kDigits; ++j) {
+        cnt[t * kDigits + j] = run;
+        run += own[j];
+    }
+    __syncthreads();
+    int local[kDigits];
+#pragma unroll
+    for (int d = 0; d < kDigits; ++d) local[d] = 0;
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int64_t i = base + j;
+        if (i >= n) continue;
+        const int d = (k[j] >> shift) & (kDigits - 1);
+        int r = 0;
+#pragma unroll
+        for (int q = 0; q < kDigits; ++q)
+            if (q == d) { r = local[q]; local[q] = r + 1; }
+        const int pos = offs[d * nblocks + blockIdx.x] + (cnt[d * kSortThreads + t] - cnt[d * kSortThreads]) + r;
+        kout[pos] = k[j];
+        vout[pos] = v[j];
+    }
+}
+
+// sorts (keys, vals) of length n in place using the given scratch
+static int radix_sort(lspr_ctx *ctx, unsigned *keys, int *vals, unsigned *ktmp, int *vtmp, int64_t n, int bits,
+                      int *hist, int *offs) {
+    const int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+    cudaStream_t st = ctx->stream;
+    unsigned *ka = keys, *kb = ktmp;
+    int *va = vals, *vb = vtmp;
+    const int passes = (bits + kDigitBits - 1) / kDigitBits;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * kDigitBits;
+        ++ctx->n_launches;
+        radix_hist_kernel<<<nblocks, kSortThreads, 0, st>>>(ka, n, shift, nblocks, hist);
+        ++ctx->n_launches;
+        scan_int_kernel<<<1, 1024, 0, st>>>(hist, (int64_t)kDigits * nblocks, offs, nullptr);
+        ++ctx->n_launches;
+        radix_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(ka, va, n, shift, nblocks, offs, kb, vb);
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    LSPR_TRY(ctx, cudaGetLastError());
+    if (ka != keys) {
+        LSPR_TRY(ctx, cudaMemcpyAsync(keys, ka, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, st));
+        LSPR_TRY(ctx, cudaMemcpyAsync(vals, va, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+    }
+    return LSPR_OK;
+}
+
+__global__ void permute_sources_kernel(int64_t Ns, const int *__restrict__ perm, const dbl4 *__restrict__ pos,
+                                       const dbl4 *__restrict__ nrm, dbl4 *spos64, dbl4 *snrm64,
+                                       float4 *spos32, float4 *snrm32, int *src_panel) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= Ns) return;
+    const int o = perm[s];
+    const dbl4 p = pos[o], n = nrm[o];
+    const int pid = (int)n.w;
+    spos64[s] = p;
+    snrm64[s] = n;
+    spos32[s] = make_float4((float)p.x, (float)p.y, (float)p.z, (float)p.w);
+    snrm32[s] = make_float4((float)n.x, (float)n.y, (float)n.z, __int_as_float(pid));
+    src_panel[s] = pid;
+}
+
+__global__ void permute_targets_kernel(int64_t N, const int *__restrict__ perm, const dbl4 *__restrict__ tgt,
+                                       dbl4 *tgt64, float4 *tgt32, int *tgt_panel) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int o = perm[i];
+    const dbl4 t = tgt[o];
+    tgt64[i] = t;
+    tgt32[i] = make_float4((float)t.x, (float)t.y, (float)t.z, __int_as_float(o));
+    tgt_panel[i] = o;
+}
+
+// --------------------------------------------------------------------- octree
+__device__ int lower_bound_key(const unsigned *keys, int lo, int hi, unsigned v) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// block-wide exclusive scan of n ints in place (blockDim.x == 1024); returns the total
+__device__ int block_scan_inplace(int *a, int n, int *sh) {
+    int carry = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? a[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+            int x = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += x;
+            __syncthreads();
+        }
+        if (i < n) a[i] = carry + sh[threadIdx.x] - v;
+        const int tot = sh[blockDim.x - 1];
+        __syncthreads();
+        carry += tot;
+    }
+    return carry;
+}
+
+// One CTA, level by level.  Box b covers keys [beg, end) sharing the top 3*level
+// bits; it is split into its non-empty octants while it holds more than ncrit
+// sources and is above the maximum depth.  Children of a box are contiguous and
+// ordered by octant; boxes are numbered level by level (deterministic).
+__global__ void __launch_bounds__(1024) octree_kernel(const unsigned *__restrict__ keys, int Ns, int ncrit, int cap,
+                                                      int *beg, int *end, int *child, int *nchild, int *level,
+                                                      unsigned *bkey, int *scratch, int *out_nboxes) {
+    __shared__ int sh[1024];
+    __shared__ int s_lb, s_le, s_overflow;
+    if (threadIdx.x == 0) {
+        beg[0] = 0; end[0] = Ns; level[0] = 0; bkey[0] = 0u; child[0] = -1; nchild[0] = 0;
+        s_lb = 0; s_le = 1; s_overflow = 0;
+    }
+    __syncthreads();
+    for (int l = 0; l < kMaxDepth; ++l) {
+        const int lb = s_lb, le = s_le;
+        if (lb == le) break;
+        const int shift = 3 * (kMaxDepth - 1 - l);
+        // count non-empty children
+        for (int b = lb + threadIdx.x; b < le; b += blockDim.x) {
+            int c = 0;
+            if (end[b] - beg[b] > ncrit) {
+                for (int o = 0; o < 8; ++o) {
+                    const unsigned p = (bkey[b] << 3) | o;
+                    const int s0 = lower_bound_key(keys, beg[b], end[b], p << shift);
+                    const int s1 = lower_bound_key(keys, s0, end[b], (p + 1) << shift);
+                    c += s1 > s0;
+                }
+            }
+            scratch[b - lb] = c;
+        }
+        __syncthreads();
+        const int total = block_scan_inplace(scratch, le - lb, sh);
+        if (le + total > cap) {
+            if (threadIdx.x == 0) s_overflow = 1;
+            __syncthreads();
+            break;
+        }
+        for (int b = lb + threadIdx.x; b < le; b += blockDim.x) {
+            int pos = le + scratch[b - lb];
+            child[b] = -1;
+            nchild[b] = 0;
+            if (end[b] - beg[b] > ncrit) {
+                int first = pos;
+                for (int o = 0; o < 8; ++o) {
+                    const unsigned p = (bkey[b] << 3) | o;
+                    const int s0 = lower_bound_key(keys, beg[b], end[b], p << shift);
+                    const int s1 = lower_bound_key(keys, s0, end[b], (p + 1) << shift);
+                    if (s1 > s0) {
+                        beg[pos] = s0; end[pos] = s1; level[pos] = l + 1; bkey[pos] = p;
+                        child[pos] = -1; nchild[pos] = 0;
+                        ++pos;
+                    }
+                }
+                child[b] = first;
+                nchild[b] = pos - first;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) { s_lb = le; s_le = le + total; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out_nboxes = s_overflow ? -1 : s_le;
+}
+
+// centre of the bounding box of the box's sources and r_b = max distance to it
+__global__ void box_geometry_kernel(int nboxes, const int *beg, const int *end, const dbl4 *__restrict__ spos,
+                                    dbl4 *c64, float4 *c32) {
+    __shared__ double red[6][128];
+    __shared__ double cen[3];
+    const int b = blockIdx.x;
+    if (b >= nboxes) return;
+    const int t = threadIdx.x;
+    double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
+    for (int s = beg[b] + t; s < end[b]; s += blockDim.x) {
+        const dbl4 p = spos[s];
+        l[0] = fmin(l[0], p.x); l[1] = fmin(l[1], p.y); l[2] = fmin(l[2], p.z);
+        h[0] = fmax(h[0], p.x); h[1] = fmax(h[1], p.y); h[2] = fmax(h[2], p.z);
+    }
+    for (int d = 0; d < 3; ++d) { red[d][t] = l[d]; red[3 + d][t] = h[d]; }
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s)
+            for (int d = 0; d < 3; ++d) {
+                red[d][t] = fmin(red[d][t], red[d][t + s]);
+                red[3 + d][t] = fmax(red[3 + d][t], red[3 + d][t + s]);
+            }
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int d = 0; d < 3; ++d) cen[d] = 0.5 * (red[d][0] + red[3 + d][0]);
+    __syncthreads();
+    double r2 = 0;
+    for (int s = beg[b] + t; s < end[b]; s += blockDim.x) {
+        const dbl4 p = spos[s];
+        const double dx = p.x - cen[0], dy = p.y - cen[1], dz = p.z - cen[2];
+        r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
+    }
+    __syncthreads();
+    red[0][t] = r2;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s) red[0][t] = fmax(red[0][t], red[0][t + s]);
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double rb = sqrt(red[0][0]);
+        c64[b] = make_dbl4(cen[0], cen[1], cen[2], rb);
+        // FP32 copy: radius rounded up so the FP32 kernels never see a smaller box
+        c32[b] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)rb * (1.0f + 1e-6f));
+    }
+}
+
+__global__ void tblock_bbox_kernel(int64_t ntb, int64_t N, const dbl4 *__restrict__ tgt, dbl4 *lo, dbl4 *hi) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= ntb) return;
+    double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = b * kTargetBlock; i < min(N, (b + 1) * kTargetBlock); ++i) {
+        const dbl4 p = tgt[i];
+        l[0] = fmin(l[0], p.x); l[1] = fmin(l[1], p.y); l[2] = fmin(l[2], p.z);
+        h[0] = fmax(h[0], p.x); h[1] = fmax(h[1], p.y); h[2] = fmax(h[2], p.z);
+    }
+    lo[b] = make_dbl4(l[0], l[1], l[2], 0);
+    hi[b] = make_dbl4(h[0], h[1], h[2], 0);
+}
+
+// Multipole-acceptance test of box (c, r_b) against a target block's bounding box:
+// r = distance from c to the nearest point of the block.  Accepted iff
+// r_b < theta * r and the box keeps clear of every target's own panel and of its
+// near-singular panels (r - r_b > clear), so that those stay in direct sums.
+__device__ __forceinline__ bool mac_accept(const dbl4 &c, const dbl4 &lo, const dbl4 &hi, double theta,
+                                           double clear) {
+    const double dx = fmax(0.0, fmax(lo.x - c.x, c.x - hi.x));
+    const double dy = fmax(0.0, fmax(lo.y - c.y, c.y - hi.y));
+    const double dz = fmax(0.0, fmax(lo.z - c.z, c.z - hi.z));
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    return c.w < theta * r && r - c.w > clear;
+}
+
+// FILL = false: count P2P items, M2P boxes and M2P items per target block.
+// FILL = true: write them at the scanned offsets and mark accepted boxes as used.
+template <bool FILL>
+__global__ void lists_kernel(int64_t ntb, int64_t N, const dbl4 *lo, const dbl4 *hi, const dbl4 *__restrict__ bc,
+                             const int *__restrict__ beg, const int *__restrict__ end, const int *__restrict__ child,
+                             const int *__restrict__ nchild, double theta, double clear, int *n_p2p, int *n_m2p,
+                             int *n_m2pi, const int *o_p2p, const int *o_m2p, const int *o_m2pi, int4 *p2p_items,
+                             int *m2p_list, int4 *m2p_items, int *used, unsigned long long *pairs, int *overflow) {
+    int64_t tb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tb >= ntb) return;
+    const dbl4 l = lo[tb], h = hi[tb];
+    const int ntgt = (int)min((int64_t)kTargetBlock, N - tb * kTargetBlock);
+    int stack[kStack];
+    int sp = 0;
+    stack[sp++] = 0;
+    int np = 0, nm = 0;
+    int cur_b = -1, cur_e = -1;    // pending merged P2P range
+    int p_out = FILL ? o_p2p[tb] : 0, m_out = FILL ? o_m2p[tb] : 0;
+    unsigned long long pp = 0;
+    auto flush = [&](int b, int e) {
+        // split [b, e) into chunks of at most kP2PChunk sources
+        const int n = e - b;
+        const int k = (n + kP2PChunk - 1) / kP2PChunk;
+        for (int q = 0; q < k; ++q) {
+            const int s0 = b + (int)((int64_t)n * q / k), s1 = b + (int)((int64_t)n * (q + 1) / k);
+            if (FILL) p2p_items[p_out++] = make_int4((int)tb, s0, s1, 0);
+        }
+        np += k;
+        pp += (unsigned long long)n * ntgt;
+    };
+    while (sp > 0) {
+        const int b = stack[--sp];
+        const dbl4 c = bc[b];
+        if (b != 0 && mac_accept(c, l, h, theta, clear)) {
+            if (FILL) {
+                m2p_list[m_out++] = b;
+                used[b] = 1;
+            }
+            ++nm;
+            continue;
+        }
+        if (nchild[b] == 0) {
+            if (cur_e == beg[b]) {
+                cur_e = end[b];
+            } else {
+                if (cur_b >= 0) flush(cur_b, cur_e);
+                cur_b = beg[b];
+                cur_e = end[b];
+            }
+            continue;
+        }
+        if (sp + nchild[b] > kStack) {
+            atomicOr(overflow, 1);
+            break;
+        }
+        for (int q = nchild[b] - 1; q >= 0; --q) stack[sp++] = child[b] + q;
+    }
+    if (cur_b >= 0) flush(cur_b, cur_e);
+    const int nmi = (nm + kM2PSeg - 1) / kM2PSeg;
+    if (!FILL) {
+        n_p2p[tb] = np;
+        n_m2p[tb] = nm;
+        n_m2pi[tb] = nmi;
+        atomicAdd(pairs, pp);
+    } else {
+        int base = o_m2p[tb];
+        for (int q = 0; q < nmi; ++q) {
+            const int s0 = base + q * kM2PSeg, s1 = min(base + nm, s0 + kM2PSeg);
+            m2p_items[o_m2pi[tb] + q] = make_int4((int)tb, s0, s1, 0);
+        }
+    }
+}
+
+// --------------------------------------------------------------------- driver
+int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
+    Mesh &m = ctx->mesh;
+    Tree &tr = ctx->tree;
+    WorkOrder &w = ctx->wo;
+    cudaStream_t st = ctx->stream;
+    tr.ready = false;
+    tr.theta = theta;
+    tr.P = P;
+    tr.Ncrit = Ncrit;
+    tr.NT = n_terms(P);
+    const int64_t Ns = m.Ns, N = m.N;
+    cudaEvent_t ev;
+    timer_begin(ctx, T_TREE, &ev);
+
+    DArr<double> cube;
+    LSPR_TRY(ctx, cube.ensure(8));
+    ++ctx->n_launches;
+    bbox_kernel<<<1, 1024, 0, st>>>(m.src_pos64.p, Ns, m.tgt64.p, N, cube.p);
+    double hb[6];
+    LSPR_TRY(ctx, cudaMemcpyAsync(hb, cube.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    double size = std::max(hb[3] - hb[0], std::max(hb[4] - hb[1], hb[5] - hb[2]));
+    size = size * (1.0 + 1e-6) + 1e-12;
+    double hc[4] = {hb[0] - 1e-7 * size, hb[1] - 1e-7 * size, hb[2] - 1e-7 * size, size * (1.0 + 2e-7)};
+    LSPR_TRY(ctx, cudaMemcpyAsync(cube.p, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+
+    // keys and sort
+    DArr<unsigned> keys, ktmp;
+    DArr<int> vals, vtmp, hist, offs;
+    const int64_t nmax = std::max(Ns, N);
+    LSPR_TRY(ctx, keys.ensure(nmax));
+    LSPR_TRY(ctx, ktmp.ensure(nmax));
+    LSPR_TRY(ctx, vals.ensure(nmax));
+    LSPR_TRY(ctx, vtmp.ensure(nmax));
+    const int64_t nblk = (nmax + kSortTile - 1) / kSortTile;
+    LSPR_TRY(ctx, hist.ensure(kDigits * nblk));
+    LSPR_TRY(ctx, offs.ensure(kDigits * nblk));
+    LSPR_TRY(ctx, w.spos64.ensure(Ns));
+    LSPR_TRY(ctx, w.snrm64.ensure(Ns));
+    LSPR_TRY(ctx, w.spos32.ensure(Ns));
+    LSPR_TRY(ctx, w.snrm32.ensure(Ns));
+    LSPR_TRY(ctx, w.src_panel.ensure(Ns));
+    LSPR_TRY(ctx, w.tgt64.ensure(N));
+    LSPR_TRY(ctx, w.tgt32.ensure(N));
+    LSPR_TRY(ctx, w.tgt_panel.ensure(N));
+
+    // targets first (their sorted keys are not kept)
+    ++ctx->n_launches;
+    morton_kernel<<<grid_for(N, 256), 256, 0, st>>>(m.tgt64.p, N, cube.p, keys.p, vals.p);
+    LSPR_TRY_ST(radix_sort(ctx, keys.p, vals.p, ktmp.p, vtmp.p, N, 30, hist.p, offs.p));
+    ++ctx->n_launches;
+    permute_targets_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, vals.p, m.tgt64.p, w.tgt64.p, w.tgt32.p, w.tgt_panel.p);
+    // sources
+    ++ctx->n_launches;
+    morton_kernel<<<grid_for(Ns, 256), 256, 0, st>>>(m.src_pos64.p, Ns, cube.p, keys.p, vals.p);
+    LSPR_TRY_ST(radix_sort(ctx, keys.p, vals.p, ktmp.p, vtmp.p, Ns, 30, hist.p, offs.p));
+    ++ctx->n_launches;
+    permute_sources_kernel<<<grid_for(Ns, 256), 256, 0, st>>>(Ns, vals.p, m.src_pos64.p, m.src_nrm64.p, w.spos64.p,
+                                                              w.snrm64.p, w.spos32.p, w.snrm32.p, w.src_panel.p);
+    LSPR_TRY(ctx, cudaGetLastError());
+
+    // octree
+    const int64_t cap64 = 1 + 8LL * kMaxDepth * (Ns / (Ncrit + 1) + 1);
+    const int cap = (int)std::min<int64_t>(cap64, 1 << 30);
+    for (DArr<int> *a : {&tr.box_beg, &tr.box_end, &tr.box_child, &tr.box_nchild, &tr.box_level, &tr.box_used})
+        LSPR_TRY(ctx, a->ensure(cap));
+    LSPR_TRY(ctx, tr.box_key.ensure(cap));
+    DArr<int> scratch, nbox_d;
+    LSPR_TRY(ctx, scratch.ensure(cap));
+    LSPR_TRY(ctx, nbox_d.ensure(1));
+    ++ctx->n_launches;
+    octree_kernel<<<1, 1024, 0, st>>>(keys.p, (int)Ns, Ncrit, cap, tr.box_beg.p, tr.box_end.p, tr.box_child.p,
+                                      tr.box_nchild.p, tr.box_level.p, tr.box_key.p, scratch.p, nbox_d.p);
+    LSPR_TRY(ctx, cudaGetLastError());
+    int nboxes = 0;
+    LSPR_TRY(ctx, cudaMemcpyAsync(&nboxes, nbox_d.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    if (nboxes <= 0) {
+        ctx->last_error = "octree capacity exceeded";
+        return LSPR_E_OOM;
+    }
+    tr.nboxes = nboxes;
+    LSPR_TRY(ctx, tr.box_c64.ensure(nboxes));
+    LSPR_TRY(ctx, tr.box_c32.ensure(nboxes));
+    ++ctx->n_launches;
+    box_geometry_kernel<<<nboxes, 128, 0, st>>>(nboxes, tr.box_beg.p, tr.box_end.p, w.spos64.p, tr.box_c64.p,
+                                                tr.box_c32.p);
+
+    // target blocks
+    const int64_t ntb = (N + kTargetBlock - 1) / kTargetBlock;
+    tr.ntblocks = ntb;
+    DArr<dbl4> tlo, thi;
+    LSPR_TRY(ctx, tlo.ensure(ntb));
+    LSPR_TRY(ctx, thi.ensure(ntb));
+    ++ctx->n_launches;
+    tblock_bbox_kernel<<<grid_for(ntb, 128), 128, 0, st>>>(ntb, N, w.tgt64.p, tlo.p, thi.p);
+
+    // lists: count
+    const double clear = m.Lmax / m.thr + m.rho_max;
+    DArr<int> cnt3, off3;
+    DArr<int64_t> tot3;
+    DArr<unsigned long long> pairs;
+    DArr<int> ovf;
+    LSPR_TRY(ctx, cnt3.ensure(3 * ntb));
+    LSPR_TRY(ctx, off3.ensure(3 * ntb));
+    LSPR_TRY(ctx, tot3.ensure(3));
+    LSPR_TRY(ctx, pairs.ensure(1));
+    LSPR_TRY(ctx, ovf.ensure(1));
+    LSPR_TRY(ctx, cudaMemsetAsync(pairs.p, 0, sizeof(unsigned long long), st));
+    LSPR_TRY(ctx, cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
+    LSPR_TRY(ctx, cudaMemsetAsync(tr.box_used.p, 0, sizeof(int) * nboxes, st));
+    ++ctx->n_launches;
+    lists_kernel<false><<<grid_for(ntb, 64), 64, 0, st>>>(
+        ntb, N, tlo.p, thi.p, tr.box_c64.p, tr.box_beg.p, tr.box_end.p, tr.box_child.p, tr.box_nchild.p, theta, clear,
+        cnt3.p, cnt3.p + ntb, cnt3.p + 2 * ntb, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+        pairs.p, ovf.p);
+    for (int q = 0; q < 3; ++q) {
+        ++ctx->n_launches;
+        scan_int_kernel<<<1, 1024, 0, st>>>(cnt3.p + q * ntb, ntb, off3.p + q * ntb, tot3.p + q);
+    }
+    LSPR_TRY(ctx, cudaGetLastError());
+    int64_t tot[3];
+    unsigned long long hp = 0;
+    int hovf = 0;
+    LSPR_TRY(ctx, cudaMemcpyAsync(tot, tot3.p, sizeof(tot), cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaMemcpyAsync(&hp, pairs.p, sizeof(hp), cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaMemcpyAsync(&hovf, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    if (hovf) {
+        ctx->last_error = "tree traversal stack overflow";
+        return LSPR_E_ARG;
+    }
+    tr.n_p2p_items = tot[0];
+    tr.n_m2p_pairs = tot[1];
+    tr.n_m2p_items = tot[2];
+    tr.p2p_pairs = (int64_t)hp;
+    LSPR_TRY(ctx, tr.p2p_items.ensure(std::max<int64_t>(1, tot[0])));
+    LSPR_TRY(ctx, tr.m2p_list.ensure(std::max<int64_t>(1, tot[1])));
+    LSPR_TRY(ctx, tr.m2p_items.ensure(std::max<int64_t>(1, tot[2])));
+    ++ctx->n_launches;
+    lists_kernel<true><<<grid_for(ntb, 64), 64, 0, st>>>(
+        ntb, N, tlo.p, thi.p, tr.box_c64.p, tr.box_beg.p, tr.box_end.p, tr.box_child.p, tr.box_nchild.p, theta, clear,
+        nullptr, nullptr, nullptr, off3.p, off3.p + ntb, off3.p + 2 * ntb, tr.p2p_items.p, tr.m2p_list.p,
+        tr.m2p_items.p, tr.box_used.p, pairs.p, ovf.p);
+    LSPR_TRY(ctx, cudaGetLastError());
+
+    // P2M work items over the used boxes (host side: a few thousand boxes)
+    std::vector<int> hbeg(nboxes), hend(nboxes), hused(nboxes);
+    LSPR_TRY(ctx, cudaMemcpyAsync(hbeg.data(), tr.box_beg.p, sizeof(int) * nboxes, cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaMemcpyAsync(hend.data(), tr.box_end.p, sizeof(int) * nboxes, cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaMemcpyAsync(hused.data(), tr.box_used.p, sizeof(int) * nboxes, cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    std::vector<int4> p2m;
+    for (int b = 0; b < nboxes; ++b) {
+        if (!hused[b]) continue;
+        for (int s = hbeg[b]; s < hend[b]; s += kP2MChunk) p2m.push_back(make_int4(b, s, std::min(hend[b], s + kP2MChunk), 0));
+    }
+    tr.n_p2m_items = (int64_t)p2m.size();
+    LSPR_TRY(ctx, tr.p2m_items.ensure(std::max<size_t>(1, p2m.size())));
+    if (!p2m.empty())
+        LSPR_TRY(ctx, cudaMemcpyAsync(tr.p2m_items.p, p2m.data(), sizeof(int4) * p2m.size(), cudaMemcpyHostToDevice, st));
+    timer_end(ctx, T_TREE, ev);
+    LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    for (auto *a : {&keys, &ktmp}) a->release();
+    for (auto *a : {&vals, &vtmp, &hist, &offs, &scratch, &nbox_d, &cnt3, &off3, &ovf}) a->release();
+    tlo.release();
+    thi.release();
+    tot3.release();
+    pairs.release();
+    cube.release();
+    tr.ready = true;
+    return LSPR_OK;
+}
+
+}  // namespace lspr

@@ -1,0 +1,232 @@
+"""Python binding of the C ABI in ``include/lspr.h`` (argument marshalling only).
+
+Every numerical step runs in the sm_103a library ``_lib/liblspr_gb300.so``;
+there is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.  Arrays may be numpy (host) or torch CUDA tensors (device; the
+call then runs on torch's current stream of that device).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+DIRECT_FP64, DIRECT_FP32, TREE_FP64, TREE_FP32 = 0, 1, 2, 3
+MODES = {"direct_fp64": DIRECT_FP64, "direct_fp32": DIRECT_FP32, "tree_fp64": TREE_FP64, "tree_fp32": TREE_FP32}
+
+STATUS = {0: "LSPR_OK", 1: "LSPR_E_ARG", 2: "LSPR_E_STATE", 3: "LSPR_E_CUDA", 4: "LSPR_E_OOM",
+          5: "LSPR_E_NOT_CONVERGED", 6: "LSPR_E_TIMEOUT", 7: "LSPR_E_MESH"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LsprError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({lib().lspr_status_string(status).decode()})")
+
+
+class QuadOpts(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("K_fine", ctypes.c_int32), ("N_k", ctypes.c_int32),
+                ("threshold", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxiter", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("refine", ctypes.c_int32)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.POINTER(ctypes.c_int32)), ("residual", ctypes.POINTER(ctypes.c_double)),
+                ("status", ctypes.POINTER(ctypes.c_int32)), ("seconds", ctypes.c_double),
+                ("matvecs", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            L.lspr_status_string.argtypes = [ctypes.c_int]
+            L.lspr_status_string.restype = ctypes.c_char_p
+            L.lspr_version.restype = ctypes.c_char_p
+            L.lspr_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp]
+            L.lspr_destroy.argtypes = [_vp]
+            L.lspr_mesh_upload.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i32, ctypes.POINTER(QuadOpts), _i32]
+            L.lspr_tree_build.argtypes = [_vp, _d, _i32, _i32]
+            L.lspr_matvec.argtypes = [_vp, _vp, _vp, _i32, _vp, _i32, _i32]
+            L.lspr_solve.argtypes = [_vp, _vp, _d, _d, _vp, _vp, _i32, ctypes.POINTER(SolveOpts), _vp, _vp,
+                                     ctypes.POINTER(SolveStats)]
+            L.lspr_get_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 7
+            L.lspr_set_timing.argtypes = [_vp, _i32]
+            L.lspr_get_timing.argtypes = [_vp, _vp, _vp]
+            for f in ("lspr_create", "lspr_destroy", "lspr_mesh_upload", "lspr_tree_build", "lspr_matvec",
+                      "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing"):
+                getattr(L, f).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise LsprError(rc, where)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _host_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+@dataclass
+class SolveResult:
+    dipole: np.ndarray        # [B, 3] complex
+    sigma_ext: np.ndarray     # [B] nm^2
+    iterations: np.ndarray    # [B]
+    residual: np.ndarray      # [B]
+    status: np.ndarray        # [B]
+    seconds: float
+    matvecs: int
+
+
+class Context:
+    """One GPU context: mesh, tree, operator and solver state (lspr_ctx)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._h = ctypes.c_void_p()
+        self.device = device
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device).cuda_stream
+            except ImportError:
+                stream = None
+        _check(lib().lspr_create(ctypes.byref(self._h), device, ctypes.c_void_p(stream or 0)), "lspr_create")
+        self.n = 0
+
+    def close(self):
+        if self._h:
+            lib().lspr_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------ mesh
+    def mesh_upload(self, verts, tris, K=4, K_fine=19, N_k=9, threshold=0.5, surf_id=None, nsurf=1):
+        q = QuadOpts(K, K_fine, N_k, threshold)
+        if _is_torch(verts):
+            assert verts.is_cuda and tris.is_cuda
+            assert str(verts.dtype) == "torch.float64" and str(tris.dtype) == "torch.int32"
+            verts, tris = verts.contiguous(), tris.contiguous()
+            rc = lib().lspr_mesh_upload(self._h, ctypes.c_void_p(verts.data_ptr()), verts.shape[0],
+                                        ctypes.c_void_p(tris.data_ptr()), tris.shape[0], None, nsurf,
+                                        ctypes.byref(q), 1)
+            n = tris.shape[0]
+        else:
+            v = np.ascontiguousarray(verts, dtype=np.float64)
+            t = np.ascontiguousarray(tris, dtype=np.int32)
+            sid = None if surf_id is None else np.ascontiguousarray(surf_id, dtype=np.int32)
+            rc = lib().lspr_mesh_upload(self._h, _host_ptr(v), len(v), _host_ptr(t), len(t),
+                                        None if sid is None else _host_ptr(sid), nsurf, ctypes.byref(q), 0)
+            n = len(t)
+        _check(rc, "lspr_mesh_upload")
+        self.n = int(n)
+
+    def tree_build(self, theta=0.5, P=6, Ncrit=300):
+        _check(lib().lspr_tree_build(self._h, float(theta), int(P), int(Ncrit)), "lspr_tree_build")
+
+    # ---------------------------------------------------------------- matvec
+    def matvec(self, x, eps_ratio, mode="direct_fp64"):
+        """y = A(s) x; x [2N] or [B, 2N] complex128 (numpy or torch CUDA)."""
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        if _is_torch(x):
+            import torch
+            squeeze = x.dim() == 1
+            xx = x.reshape(-1, 2 * self.n).contiguous()
+            B = xx.shape[0]
+            s = torch.as_tensor(np.broadcast_to(np.asarray(eps_ratio, np.complex128), (B,)).copy(),
+                                device=x.device)
+            y = torch.empty_like(xx)
+            rc = lib().lspr_matvec(self._h, ctypes.c_void_p(xx.data_ptr()), ctypes.c_void_p(y.data_ptr()), B,
+                                   ctypes.c_void_p(s.data_ptr()), m, 1)
+            _check(rc, "lspr_matvec")
+            return y[0] if squeeze else y
+        x = np.ascontiguousarray(x, dtype=np.complex128)
+        squeeze = x.ndim == 1
+        xx = x.reshape(-1, 2 * self.n)
+        B = xx.shape[0]
+        s = np.ascontiguousarray(np.broadcast_to(np.asarray(eps_ratio, np.complex128), (B,)))
+        y = np.zeros_like(xx)
+        _check(lib().lspr_matvec(self._h, _host_ptr(xx), _host_ptr(y), B, _host_ptr(s), m, 0), "lspr_matvec")
+        return y[0] if squeeze else y
+
+    # ----------------------------------------------------------------- solve
+    def solve(self, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0), tol=1e-6, restart=50, maxiter=500,
+              mode="tree_fp32", refine=False, check=True) -> SolveResult:
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        e = np.ascontiguousarray(np.atleast_1d(eps_in), dtype=np.complex128)
+        lam = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(lambda_nm), e.shape), dtype=np.float64)
+        B = len(e)
+        E = np.ascontiguousarray(E0, dtype=np.float64)
+        dip = np.zeros((B, 3), np.complex128)
+        sig = np.zeros(B)
+        it = np.zeros(B, np.int32)
+        rr = np.zeros(B)
+        stt = np.zeros(B, np.int32)
+        st = SolveStats(it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                        rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        stt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0.0, 0)
+        o = SolveOpts(float(tol), int(restart), int(maxiter), m, int(bool(refine)))
+        eo = complex(eps_out)
+        rc = lib().lspr_solve(self._h, _host_ptr(e), eo.real, eo.imag, _host_ptr(E), _host_ptr(lam), B,
+                              ctypes.byref(o), _host_ptr(dip), _host_ptr(sig), ctypes.byref(st))
+        if rc not in (0, 5) or (check and rc != 0):
+            _check(rc, "lspr_solve")
+        return SolveResult(dip, sig, it, rr, stt, st.seconds, st.matvecs)
+
+    # ------------------------------------------------------------------ info
+    def info(self) -> dict:
+        vals = [ctypes.c_int64() for _ in range(7)]
+        _check(lib().lspr_get_info(self._h, *[ctypes.byref(v) for v in vals]), "lspr_get_info")
+        keys = ["n_panels", "n_sources", "n_near", "n_boxes", "n_p2p_items", "n_m2p_pairs", "n_p2p_pairs"]
+        return {k: v.value for k, v in zip(keys, vals)}
+
+    def set_timing(self, enable: bool):
+        _check(lib().lspr_set_timing(self._h, int(bool(enable))), "lspr_set_timing")
+
+    def timing(self) -> dict:
+        ms = np.zeros(8)
+        n = np.zeros(8, np.int64)
+        _check(lib().lspr_get_timing(self._h, _host_ptr(ms), _host_ptr(n)), "lspr_get_timing")
+        names = ["p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh", "other"]
+        return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}
