@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark of the quasistatic LSPR boundary-element hot path on GB300.
+
+Metric: wavelength solves per second (lambda-solves/s) at sigma_ext error <= 1e-4
+relative to the plain FP64 solve; the matvec rate (G-interactions/s: one
+(target, source Gauss node, wavelength) evaluation of G and dG/dn on complex
+data) is reported alongside.
+
+One step = the whole hot path for one batch of synthetic input: mesh upload and
+panel/near-singular precompute, Morton sort + octree + interaction lists, FP64
+right-hand side, GMRES with the treecode matvec, dipole and sigma_ext.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload sphere20480]
+  python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
+
+Multi-GPU: wavelengths and geometries are independent, so N ranks run N
+independent replicas of the step (weak scaling, no data-path collective); the
+barrier and max-over-ranks timing use torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1812_10722_gb300 import inputs as I  # noqa: E402
+
+WORKLOADS = {
+    # 20480-panel silver sphere, single wavelength, treecode P=6 theta=0.5 Ncrit=300, FP32 matvec, GMRES 1e-6
+    "sphere20480": dict(sub=5, R=10.0, lam=[380.0], mode="tree_fp32", tol=1e-6, theta=0.5, P=6, Ncrit=300,
+                        K=4, K_fine=19, N_k=9, restart=50, refine=True),
+    # the same with the plain FP64 treecode (baseline of the mixed-precision form)
+    "sphere20480_fp64": dict(sub=5, R=10.0, lam=[380.0], mode="tree_fp64", tol=1e-6, theta=0.5, P=6, Ncrit=300,
+                             K=4, K_fine=19, N_k=9, restart=50, refine=False),
+    # 1280-panel sphere, direct FP64 matvec, GMRES 1e-8
+    "sphere1280": dict(sub=3, R=10.0, lam=[380.0], mode="direct_fp64", tol=1e-8, theta=0.5, P=6, Ncrit=300,
+                       K=4, K_fine=19, N_k=9, restart=100, refine=False),
+    # 81920-panel sphere, 64 wavelengths over 350-420 nm in one batched solve
+    "sphere81920_sweep64": dict(sub=6, R=10.0, lam=list(I.wavelengths(350, 420, 64)), mode="tree_fp32", tol=1e-6,
+                                theta=0.5, P=6, Ncrit=300, K=4, K_fine=19, N_k=9, restart=50, refine=True),
+}
+
+L2_BYTES = 129 * 2 ** 20
+P2P_FLOPS = 24          # per (target, source) pair: see the design doc (FMA = 2 flops)
+P2P_FP32_INSTR = 16     # FP32-pipe instructions per pair
+
+
+def m2p_flops(P: int) -> int:
+    """FP32 flops per (target, box) M2P evaluation of the recurrence + 4-channel dot (FMA = 2)."""
+    terms = [(a, b, n - a - b) for n in range(P + 1) for a in range(n, -1, -1) for b in range(n - a, -1, -1)]
+    f = 3 + 5 + 1 + 8   # R components, r^2, 1/r^2, first term dot
+    for k in terms[1:]:
+        m1 = sum(1 for d in range(3) if k[d] >= 1)
+        m2 = sum(1 for d in range(3) if k[d] >= 2)
+        f += 2 * m1 + m2 + 3 + 8
+    return f
+
+
+def fp32_peak_tflops(mhz: float) -> float:
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+# ----------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ our GPU arm
+def run_ours(args, wl, rank, world, local_rank):
+    import torch
+    from paper_1812_10722_gb300 import lspr
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    verts, tris = I.icosphere(wl["sub"], wl["R"])
+    lam = np.asarray(wl["lam"], float)
+    eps = I.drude_eps(lam)
+    em = I.EPS_WATER
+    B = len(lam)
+    v_d = torch.as_tensor(verts, device=dev)
+    t_d = torch.as_tensor(tris, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = lspr.Context(local_rank, stream.cuda_stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(host: bool):
+        if host:
+            ctx.mesh_upload(verts, tris, wl["K"], wl["K_fine"], wl["N_k"])
+        else:
+            ctx.mesh_upload(v_d, t_d, wl["K"], wl["K_fine"], wl["N_k"])
+        if wl["mode"].startswith("tree"):
+            ctx.tree_build(wl["theta"], wl["P"], wl["Ncrit"])
+        return ctx.solve(eps, em, lam, tol=wl["tol"], restart=wl["restart"], maxiter=2000, mode=wl["mode"],
+                         refine=wl["refine"])
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step(False)
+    barrier()
+    # ---- timed region: inputs resident in HBM, L2 flushed between steps
+    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
+    sampler.start()
+    ctx.set_timing(True)
+    n0 = ctx_launches(ctx)
+    total_ms = 0.0
+    iters = []
+    sig = None
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = step(False)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        iters.append(int(r.iterations.max()))
+        sig = r.sigma_ext
+    launches = ctx_launches(ctx) - n0
+    ktime = ctx.timing()
+    ctx.set_timing(False)
+    clocks = sampler.stop()
+    barrier()
+    info = ctx.info()
+    t_max = total_ms
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = B * args.steps * world / (t_max / 1e3)
+
+    # ---- accuracy: the same step with the plain FP64 treecode (same P, theta) and the oracle's stored value
+    acc = {}
+    if wl["mode"] == "tree_fp32":
+        r64 = ctx.solve(eps, em, lam, tol=min(wl["tol"], 1e-8), restart=wl["restart"], maxiter=2000,
+                        mode="tree_fp64")
+        acc["sigma_rel_err_vs_fp64_treecode"] = float(np.max(np.abs(sig - r64.sigma_ext) / r64.sigma_ext))
+    gold = os.path.join(ROOT, "tests", "golden", f"sphere{info['n_panels']}_l380.json")
+    if B == 1 and lam[0] == 380.0 and os.path.exists(gold):
+        with open(gold) as f:
+            g = json.load(f)
+        acc["sigma_rel_err_vs_oracle"] = float(abs(sig[0] - g["sigma_ext_nm2"]) / g["sigma_ext_nm2"])
+
+    # ---- end to end through the public API with host buffers
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = step(True)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    h2d = verts.nbytes + tris.nbytes + eps.astype(np.complex128).nbytes + lam.nbytes + 24
+    d2h = B * (3 * 16 + 8)
+
+    # ---- roofline of the dominant kernel (CUDA events around every launch in the timed region)
+    peaks = load_peaks()
+    mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    kernels = {}
+    matvecs_per_step = None
+    for name in ("p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh"):
+        ms, n = ktime[name]
+        if n:
+            kernels[name] = {"ms_total": round(ms, 4), "launches": n, "ms_per_launch": ms / n,
+                             "share_of_step": round(ms / total_ms, 4)}
+    pairs = info["n_p2p_pairs"] if wl["mode"].startswith("tree") else info["n_panels"] * info["n_sources"]
+    roof = None
+    dom = max((k for k in kernels if k in ("p2p", "m2p", "p2m", "near_assembly", "gmres")),
+              key=lambda k: kernels[k]["ms_total"], default=None)
+    fp32 = wl["mode"].endswith("fp32")
+    peak_fp32 = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    if "p2p" in kernels:
+        k = kernels["p2p"]
+        k["algorithmic_tflops"] = pairs * P2P_FLOPS / (k["ms_per_launch"] * 1e-3) / 1e12
+        k["pairs_per_launch"] = pairs
+    if "m2p" in kernels:
+        k = kernels["m2p"]
+        k["algorithmic_tflops"] = info["n_m2p_pairs"] * kernel_targets(info) * m2p_flops(wl["P"]) / (
+            k["ms_per_launch"] * 1e-3) / 1e12
+    if dom in ("p2p", "m2p") and fp32:
+        a = kernels[dom]["algorithmic_tflops"]
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 3), "peak": round(peak_fp32, 2),
+                "unit": "TFLOP/s", "frac": round(a / peak_fp32, 4), "traffic": None,
+                "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 flops x 2070 MHz (derived, no measured FP32 peak)"}
+    elif dom is not None:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": None, "traffic": None, "peak_note": "of measured"}
+    g_int = pairs * B * (sum(iters) / len(iters) + 2) / (total_ms / args.steps / 1e3)
+
+    out = {
+        "metric": "lambda-solves/s at sigma_ext rel err <= 1e-4 vs plain FP64 (treecode GMRES)",
+        "value": round(value, 4), "unit": "lambda-solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
+        "data": "synthetic (icosphere, Drude silver in water)",
+        "config": {"workload": args.workload, "panels": info["n_panels"], "sources": info["n_sources"],
+                   "wavelengths": B, "mode": wl["mode"], "theta": wl["theta"], "P": wl["P"], "Ncrit": wl["Ncrit"],
+                   "K": wl["K"], "K_fine": wl["K_fine"], "N_k": wl["N_k"], "gmres_tol": wl["tol"],
+                   "restart": wl["restart"], "l2": "flushed between steps (258 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(B * args.steps * world / e2e_s, 4), "unit": "lambda-solves/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "matvec_g_interactions_per_s": round(g_int / 1e9, 3),
+        "gmres_iterations": iters[-1],
+        "sigma_ext_nm2": float(sig[0]),
+        "accuracy": acc,
+        "kernels": kernels,
+        "tree": {"boxes": info["n_boxes"], "p2p_pairs_per_matvec": info["n_p2p_pairs"],
+                 "m2p_box_target_blocks": info["n_m2p_pairs"], "near_entries": info["n_near"]},
+        "clocks": clocks,
+    }
+    ctx.close()
+    return out, iters
+
+
+def kernel_targets(info) -> int:
+    return 64   # targets per interaction block
+
+
+def ctx_launches(ctx) -> int:
+    return ctx.launch_count()
+
+
+# --------------------------------------------------------- oracle (CPU) timings
+def oracle_sample(wl, iters_hint: int, reps: int = 1):
+    """Time the oracle's matrix-free matvec at full size and extrapolate one
+    lambda-solve as (GMRES iterations + 2) matvecs (explicit residual and RHS)."""
+    import oracle
+    verts, tris = I.icosphere(wl["sub"], wl["R"])
+    n = len(tris)
+    s = I.drude_eps(wl["lam"][0]) / I.EPS_WATER
+    x = I.random_complex(2 * n, seed=0)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.matvec(verts, tris, x, s, K=wl["K"], K_fine=wl["K_fine"])
+        times.append(time.perf_counter() - t0)
+    t_mv = float(np.median(times))
+    t_solve = (iters_hint + 2) * t_mv
+    return t_mv, t_solve
+
+
+def oracle_iterations_hint(wl):
+    gold = os.path.join(ROOT, "tests", "golden", f"sphere{len(I.icosphere(wl['sub'], wl['R'])[1])}_l380.json")
+    try:
+        with open(gold) as f:
+            return int(json.load(f)["gmres_iterations"])
+    except OSError:
+        return 30
+
+
+def run_reference(args, wl):
+    import oracle
+    oracle.build()
+    it = oracle_iterations_hint(wl)
+    for _ in range(args.warmup):
+        oracle_sample(wl, it)
+    t = 0.0
+    for _ in range(args.steps):
+        t_mv, t_solve = oracle_sample(wl, it)
+        t += t_solve
+    value = len(wl["lam"]) * args.steps / t if len(wl["lam"]) == 1 else args.steps / t
+    cores = os.cpu_count()
+    return {
+        "impl": "reference", "metric": "lambda-solves/s at sigma_ext rel err <= 1e-4 vs plain FP64 (treecode GMRES)",
+        "value": value, "unit": "lambda-solves/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (icosphere, Drude silver in water)",
+        "config": {"workload": args.workload, "panels": len(I.icosphere(wl["sub"], wl["R"])[1]),
+                   "wavelengths": 1, "mode": "oracle direct FP64 (plain CPU)"},
+        "cpu_baseline": {"value": value, "unit": "lambda-solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one full-size oracle matvec per step, lambda-solve extrapolated as "
+                                   f"({it} GMRES iterations + 2) matvecs"},
+        "e2e": {"value": value, "unit": "lambda-solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere20480", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, wl)))
+        return
+
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out, iters = run_ours(args, wl, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_mv, t_solve = oracle_sample(wl, iters[-1])
+        out["cpu_baseline"] = {"value": 1.0 / t_solve,
+                               "unit": "lambda-solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": f"one full-size oracle matvec ({t_mv:.2f} s) on the host cores; one "
+                                         f"lambda-solve extrapolated as ({iters[-1]} GMRES iterations + 2) matvecs"}
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

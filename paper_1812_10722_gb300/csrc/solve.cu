@@ -564,45 +564,58 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
         LSPR_TRY_ST(gmres_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p, iters, relres,
                                 bnorm));
     } else {
-        // iterative refinement: r = b - A64 x in FP64, correction from the FP32-mode GMRES
+        // Iterative refinement: the residual r = b - A x is formed with the FP64 operator of
+        // the same kind (tree or direct); the correction solves A d = r with the FP32-mode
+        // GMRES to a tolerance well above the FP32 noise floor (>= 1e-4 relative to ||r||).
         const int mode_hi = tree ? LSPR_TREE_FP64 : LSPR_DIRECT_FP64;
         std::vector<int> it2(B, 0);
-        std::vector<double> rr2(B, 1.0);
+        std::vector<double> rr2(B, 1.0), rn(B, 0.0);
         DArr<double2> dx;
         LSPR_TRY(ctx, dx.ensure((size_t)B * n2));
-        for (int cycle = 0; cycle < 8; ++cycle) {
-            LSPR_TRY_ST(apply_operator(ctx, mode_hi, ctx->gm_x.p, ctx->gm_r.p, ctx->gm_s.p, B));
-            ++ctx->n_launches;
-            add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_b.p, -1.0);   // A x - b
-            ++ctx->n_launches;
-            norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, ctx->gm_r.p, n2, ctx->gm_dpart.p, nch,
-                                                                      nullptr);
-            ++ctx->n_launches;
-            norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, ctx->gm_bnorm.p, nullptr);
-            std::vector<double> rn(B);
-            LSPR_TRY(ctx, cudaMemcpyAsync(rn.data(), ctx->gm_bnorm.p, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
-            LSPR_TRY(ctx, cudaStreamSynchronize(st));
+        const int max_cycles = 12;
+        int used = 0;
+        for (int cycle = 0;; ++cycle) {
+            if (cycle == 0) {   // x = 0: r = b
+                LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_r.p, ctx->gm_b.p, sizeof(double2) * B * n2,
+                                              cudaMemcpyDeviceToDevice, st));
+                for (int b = 0; b < B; ++b) rn[b] = bnorm[b];
+            } else {
+                LSPR_TRY_ST(apply_operator(ctx, mode_hi, ctx->gm_x.p, ctx->gm_r.p, ctx->gm_s.p, B));
+                ++ctx->n_launches;
+                add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_b.p, -1.0);
+                ++ctx->n_launches;
+                norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, ctx->gm_r.p, n2, ctx->gm_dpart.p,
+                                                                          nch, nullptr);
+                ++ctx->n_launches;
+                norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, ctx->gm_bnorm.p, nullptr);
+                LSPR_TRY(ctx, cudaMemcpyAsync(rn.data(), ctx->gm_bnorm.p, sizeof(double) * B, cudaMemcpyDeviceToHost,
+                                              st));
+                LSPR_TRY(ctx, cudaStreamSynchronize(st));
+                ++ctx->n_launches;   // r = b - A x
+                add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_r.p, -2.0);
+            }
             bool done = true;
+            double worst = 0.0;
             for (int b = 0; b < B; ++b) {
                 relres[b] = rn[b] / bnorm[b];
                 done = done && (relres[b] <= o.tol);
+                worst = std::max(worst, relres[b]);
             }
-            if (done) break;
-            // solve A d = r = b - A x to a relative tolerance that brings ||b - A x|| under tol
+            if (done || cycle == max_cycles || used >= o.maxiter || !std::isfinite(worst)) break;
+            const double inner = std::min(0.5, std::max(1e-4, 0.3 * o.tol / worst));
             std::vector<double> rnorm(B);
-            double inner = 0.1;
-            for (int b = 0; b < B; ++b) {
-                rnorm[b] = rn[b] > 0 ? rn[b] : 1.0;
-                if (relres[b] > o.tol) inner = std::min(inner, 0.5 * o.tol / relres[b]);
-            }
-            inner = std::max(inner, 1e-6);
-            ++ctx->n_launches;
-            add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_r.p, -2.0);   // r = b - A x
+            for (int b = 0; b < B; ++b) rnorm[b] = rn[b] > 0 ? rn[b] : 1.0;
             LSPR_TRY(ctx, cudaMemsetAsync(dx.p, 0, sizeof(double2) * B * n2, st));
-            LSPR_TRY_ST(gmres_solve(ctx, mode, B, m, o.maxiter, inner, ctx->gm_s.p, ctx->gm_r.p, dx.p, it2, rr2, rnorm));
+            LSPR_TRY_ST(gmres_solve(ctx, mode, B, m, std::max(1, o.maxiter - used), inner, ctx->gm_s.p, ctx->gm_r.p,
+                                    dx.p, it2, rr2, rnorm));
             ++ctx->n_launches;
             add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_x.p, dx.p, 1.0);
-            for (int b = 0; b < B; ++b) iters[b] += it2[b];
+            int mx = 0;
+            for (int b = 0; b < B; ++b) {
+                iters[b] += it2[b];
+                mx = std::max(mx, it2[b]);
+            }
+            used += mx;
         }
         LSPR_TRY(ctx, cudaStreamSynchronize(st));
         dx.release();

@@ -76,9 +76,10 @@ def lib():
                                      ctypes.POINTER(SolveStats)]
             L.lspr_get_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 7
             L.lspr_set_timing.argtypes = [_vp, _i32]
+            L.lspr_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
             L.lspr_get_timing.argtypes = [_vp, _vp, _vp]
             for f in ("lspr_create", "lspr_destroy", "lspr_mesh_upload", "lspr_tree_build", "lspr_matvec",
-                      "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing"):
+                      "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing", "lspr_launch_count"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -220,6 +221,11 @@ class Context:
         _check(lib().lspr_get_info(self._h, *[ctypes.byref(v) for v in vals]), "lspr_get_info")
         keys = ["n_panels", "n_sources", "n_near", "n_boxes", "n_p2p_items", "n_m2p_pairs", "n_p2p_pairs"]
         return {k: v.value for k, v in zip(keys, vals)}
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64(0)
+        _check(lib().lspr_launch_count(self._h, ctypes.byref(n)), "lspr_launch_count")
+        return n.value
 
     def set_timing(self, enable: bool):
         _check(lib().lspr_set_timing(self._h, int(bool(enable))), "lspr_set_timing")
