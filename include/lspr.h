@@ -174,6 +174,26 @@ LSPR_API int lspr_set_timing(lspr_ctx *ctx, int32_t enable);
 LSPR_API int lspr_launch_count(lspr_ctx *ctx, int64_t *count);
 LSPR_API int lspr_get_timing(lspr_ctx *ctx, double *ms, int64_t *launches);
 
+/* Allocation-free direct FP32 product y = A(s) x (the LSPR_DIRECT_FP32 product of
+ * lspr_matvec for one right-hand side).  The paper has no counterpart: this is a
+ * service for callers that must not allocate device memory during the call, such
+ * as code embedded in an application whose device memory belongs to another
+ * allocator or that has a fixed budget, and latency-critical loops where
+ * cudaMalloc/cudaFree would stall (they can synchronise the device).  The call
+ * uses no cudaMalloc, cudaFree or allocating library routine: its scratch
+ * (source weights and accumulators) is one fixed device array of 1.5 MiB inside
+ * the library, which every GPU that loads the library keeps until exit.
+ *   ctx        context with an uploaded mesh of at most 16384 panels and 65536
+ *              far-rule sources (larger meshes: LSPR_E_ARG)
+ *   x, y       device pointers on the context's device, [2N] complex each
+ *   s          eps_in / eps_out (re, im)
+ * The work is queued on the context's stream and is not synchronised on return.
+ * The first call on a device looks up the array's device address (make it before
+ * any stream capture).  All calls on a device share the array and leave their
+ * contents in it; calls that overlap on the GPU race and must be serialised.
+ * Errors: LSPR_E_ARG, LSPR_E_STATE (no mesh), LSPR_E_CUDA. */
+LSPR_API int lspr_matvec_direct_fp32_noalloc(lspr_ctx *ctx, const double *x, double *y, double s_re, double s_im);
+
 #ifdef __cplusplus
 }
 #endif

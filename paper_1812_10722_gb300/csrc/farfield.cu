@@ -428,3 +428,23 @@ int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc) {
 }
 
 }  // namespace lspr
+
+namespace lspr {
+
+// Launchers on explicit buffers (no context-owned scratch): used by the
+// allocation-free matvec entry point.
+int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
+                            const double2 *x, float4 *w) {
+    weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, st>>>(Ns, N, spos64, src_panel, x, w);
+    return cudaGetLastError() == cudaSuccess ? LSPR_OK : LSPR_E_CUDA;
+}
+
+int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, const float4 *tgt, int64_t ntgt,
+                        const float4 *spos, const float4 *snrm, const float4 *w, double *acc) {
+    if (nitems == 0) return LSPR_OK;
+    p2p_kernel<float><<<grid_for(nitems, kP2PWarps), kP2PWarps * 32, 0, st>>>(items, nitems, tgt, ntgt, spos, snrm, w,
+                                                                             acc);
+    return cudaGetLastError() == cudaSuccess ? LSPR_OK : LSPR_E_CUDA;
+}
+
+}  // namespace lspr

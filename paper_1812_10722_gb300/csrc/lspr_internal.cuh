@@ -191,6 +191,10 @@ int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, doub
 int launch_p2m(lspr_ctx *ctx, bool fp64);
 int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc);
 int launch_weights(lspr_ctx *ctx, bool fp64, const double2 *x, int64_t N);
+int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
+                            const double2 *x, float4 *w);
+int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, const float4 *tgt, int64_t ntgt,
+                        const float4 *spos, const float4 *snrm, const float4 *w, double *acc);
 
 // ------------------------------------------------------------ solve.cu
 // y = A(s) x for one right-hand side, x and y device [2N] complex
