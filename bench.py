@@ -52,6 +52,7 @@ WORKLOADS = {
 L2_BYTES = 129 * 2 ** 20
 P2P_FLOPS = 24          # per (target, source) pair: see the design doc (FMA = 2 flops)
 P2P_FP32_INSTR = 16     # FP32-pipe instructions per pair
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64
 
 
 def m2p_flops(P: int) -> int:
@@ -222,14 +223,16 @@ def run_ours(args, wl, rank, world, local_rank):
     mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     kernels = {}
     matvecs_per_step = None
-    for name in ("p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh"):
+    for name in ("p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh", "p2p_fp64", "m2p_fp64", "p2m_fp64",
+                 "weights"):
         ms, n = ktime[name]
         if n:
             kernels[name] = {"ms_total": round(ms, 4), "launches": n, "ms_per_launch": ms / n,
                              "share_of_step": round(ms / total_ms, 4)}
     pairs = info["n_p2p_pairs"] if wl["mode"].startswith("tree") else info["n_panels"] * info["n_sources"]
     roof = None
-    dom = max((k for k in kernels if k in ("p2p", "m2p", "p2m", "near_assembly", "gmres")),
+    dom = max((k for k in kernels if k in ("p2p", "m2p", "p2m", "near_assembly", "gmres", "p2p_fp64", "m2p_fp64",
+                                           "p2m_fp64")),
               key=lambda k: kernels[k]["ms_total"], default=None)
     fp32 = wl["mode"].endswith("fp32")
     peak_fp32 = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
@@ -241,7 +244,17 @@ def run_ours(args, wl, rank, world, local_rank):
         k = kernels["m2p"]
         k["algorithmic_tflops"] = info["n_m2p_pairs"] * kernel_targets(info) * m2p_flops(wl["P"]) / (
             k["ms_per_launch"] * 1e-3) / 1e12
-    if dom in ("p2p", "m2p") and fp32:
+    for name, flops in (("p2p_fp64", P2P_FLOPS), ("m2p_fp64", None)):
+        if name in kernels:
+            k = kernels[name]
+            work = pairs * P2P_FLOPS if flops else info["n_m2p_pairs"] * kernel_targets(info) * m2p_flops(wl["P"])
+            k["algorithmic_tflops"] = work / (k["ms_per_launch"] * 1e-3) / 1e12
+    if dom in ("p2p_fp64", "m2p_fp64"):
+        a = kernels[dom]["algorithmic_tflops"]
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_note": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"}
+    elif dom in ("p2p", "m2p") and fp32:
         a = kernels[dom]["algorithmic_tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 3), "peak": round(peak_fp32, 2),
                 "unit": "TFLOP/s", "frac": round(a / peak_fp32, 4), "traffic": None,
@@ -341,6 +354,34 @@ def run_reference(args, wl):
     }
 
 
+def run_matvecs(args, wl):
+    """K bare matvecs of the workload's mode on a seeded random vector (profiling aid)."""
+    import torch
+    from paper_1812_10722_gb300 import lspr
+    verts, tris = I.icosphere(wl["sub"], wl["R"])
+    n = len(tris)
+    s = complex(I.drude_eps(wl["lam"][0]) / I.EPS_WATER)
+    ctx = lspr.Context(0, torch.cuda.current_stream().cuda_stream)
+    ctx.mesh_upload(verts, tris, wl["K"], wl["K_fine"], wl["N_k"])
+    mode = args.matvec_mode or wl["mode"]
+    if mode.startswith("tree"):
+        ctx.tree_build(wl["theta"], wl["P"], wl["Ncrit"])
+    x = torch.as_tensor(I.random_complex(2 * n, seed=0), device="cuda")
+    ctx.matvec(x, s, mode)
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    t0 = time.perf_counter()
+    for _ in range(args.matvecs):
+        y = ctx.matvec(x, s, mode)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.matvecs
+    out = {"workload": args.workload, "mode": mode, "matvecs": args.matvecs, "ms_per_matvec": 1e3 * dt,
+           "kernels_ms": {k: v for k, v in ctx.timing().items() if v[1]}, "info": ctx.info(),
+           "checksum": float(torch.linalg.vector_norm(y).item())}
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,11 +390,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere20480", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--matvecs", type=int, default=0, help="only run this many bare matvecs (profiling)")
+    ap.add_argument("--matvec-mode", default=None, help="matvec mode for --matvecs (default: the workload's)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.matvecs:
+        print(json.dumps(run_matvecs(args, wl)))
+        return
 
     if args.impl == "reference":
         if rank != 0:

@@ -148,8 +148,10 @@ LSPR_API int lspr_matvec(lspr_ctx *ctx, const double *x, double *y, int32_t B, c
  *   lambda_nm[B]           vacuum wavelengths
  *   dipole_out [B][3] complex, sigma_ext_out [B] (nm^2): caller-allocated.
  * The right-hand side V((eps_out-eps_in)/eps_out dphi_inc/dn), dphi_inc/dn = -E0.n,
- * is formed in FP64; GMRES (right 2x2 block-Jacobi preconditioner, FP64 Krylov
- * basis) runs in the matvec mode of `o`; the dipole is
+ * is formed with the operator of the matvec mode of `o` (FP64 accumulation in every
+ * mode); GMRES (right 2x2 block-Jacobi preconditioner, FP64 Krylov basis) runs in
+ * that mode, and with o->refine in an FP32 mode the residual of each refinement
+ * cycle is formed with the FP64 operator of the same kind; the dipole is
  * p = -eps_out * sum_j A_j (c_j dphi2s/dn_j - phi_j n_j) over the panels and
  * sigma_ext = Im(k^2 e.p / (eps_out |E0|)) / Re k with k = 2 pi sqrt(eps_out) / lambda.
  * Returns LSPR_E_NOT_CONVERGED if any wavelength missed tol (results are still
@@ -164,11 +166,12 @@ LSPR_API int lspr_solve(lspr_ctx *ctx, const double *eps_in, double eps_out_re, 
 LSPR_API int lspr_get_info(lspr_ctx *ctx, int64_t *n_panels, int64_t *n_sources, int64_t *n_near, int64_t *n_boxes,
                   int64_t *n_p2p_items, int64_t *n_m2p_pairs, int64_t *n_p2p_pairs);
 
-/* Kernel timing of the last lspr_matvec / lspr_solve on the context's stream,
- * in milliseconds summed over launches, and launch counts (arrays of 8):
- * [0] P2P, [1] M2P, [2] P2M, [3] near/assembly, [4] GMRES vector kernels,
- * [5] tree build, [6] mesh/near precompute, [7] other.
- * Timing is recorded only while enabled (lspr_set_timing(ctx, 1)). */
+/* Kernel timing on the context's stream while enabled (lspr_set_timing(ctx, 1) clears
+ * the counters): milliseconds summed over launches and launch counts, arrays of 12:
+ * [0] P2P FP32, [1] M2P FP32, [2] P2M FP32, [3] near correction + block assembly,
+ * [4] GMRES vector kernels, [5] tree build, [6] mesh + near precompute, [7] other,
+ * [8] P2P FP64, [9] M2P FP64, [10] P2M FP64, [11] source weights.
+ * Every timed launch is bracketed by CUDA events on the context's stream. */
 LSPR_API int lspr_set_timing(lspr_ctx *ctx, int32_t enable);
 /* Number of CUDA kernels the context has launched since lspr_create. */
 LSPR_API int lspr_launch_count(lspr_ctx *ctx, int64_t *count);

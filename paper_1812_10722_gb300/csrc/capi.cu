@@ -215,7 +215,7 @@ int lspr_set_timing(lspr_ctx *c, int32_t enable) {
     if (!c) return LSPR_E_ARG;
     timer_collect(c);
     c->timing.enabled = enable != 0;
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kTimerSlots; ++k) {
         c->timing.ms[k] = 0;
         c->timing.launches[k] = 0;
     }
@@ -225,7 +225,7 @@ int lspr_set_timing(lspr_ctx *c, int32_t enable) {
 int lspr_get_timing(lspr_ctx *c, double *ms, int64_t *launches) {
     if (!c) return LSPR_E_ARG;
     timer_collect(c);
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kTimerSlots; ++k) {
         if (ms) ms[k] = c->timing.ms[k];
         if (launches) launches[k] = c->timing.launches[k];
     }

@@ -316,6 +316,8 @@ __global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, const
 // --------------------------------------------------------------- launchers
 int launch_weights(lspr_ctx *ctx, bool fp64, const double2 *x, int64_t N) {
     const int64_t Ns = ctx->mesh.Ns;
+    cudaEvent_t ev;
+    timer_begin(ctx, T_WEIGHTS, &ev);
     if (fp64) {
         LSPR_TRY(ctx, ctx->w64.ensure(Ns));
         ++ctx->n_launches;
@@ -327,6 +329,7 @@ int launch_weights(lspr_ctx *ctx, bool fp64, const double2 *x, int64_t N) {
         weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, ctx->stream>>>(Ns, N, ctx->wo.spos64.p,
                                                                            ctx->wo.src_panel.p, x, ctx->w32.p);
     }
+    timer_end(ctx, T_WEIGHTS, ev);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
@@ -335,7 +338,8 @@ int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, doub
     if (nitems == 0) return LSPR_OK;
     const unsigned grid = grid_for(nitems, kP2PWarps);
     cudaEvent_t ev;
-    timer_begin(ctx, T_P2P, &ev);
+    const int slot = fp64 ? T_P2P64 : T_P2P;
+    timer_begin(ctx, slot, &ev);
     ++ctx->n_launches;
     if (fp64)
         p2p_kernel<double><<<grid, kP2PWarps * 32, 0, ctx->stream>>>(items, nitems, ctx->wo.tgt64.p, ctx->mesh.N,
@@ -343,7 +347,7 @@ int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, doub
     else
         p2p_kernel<float><<<grid, kP2PWarps * 32, 0, ctx->stream>>>(items, nitems, ctx->wo.tgt32.p, ctx->mesh.N,
                                                                     ctx->wo.spos32.p, ctx->wo.snrm32.p, ctx->w32.p, acc);
-    timer_end(ctx, T_P2P, ev);
+    timer_end(ctx, slot, ev);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
@@ -397,7 +401,8 @@ int launch_p2m(lspr_ctx *ctx, bool fp64) {
     Tree &tr = ctx->tree;
     if (tr.n_p2m_items == 0) return LSPR_OK;
     cudaEvent_t ev;
-    timer_begin(ctx, T_P2M, &ev);
+    const int slot = fp64 ? T_P2M64 : T_P2M;
+    timer_begin(ctx, slot, &ev);
     if (fp64) {
         LSPR_TRY(ctx, tr.mom64.ensure(tr.nboxes * tr.NT));
         LSPR_TRY(ctx, cudaMemsetAsync(tr.mom64.p, 0, sizeof(dbl4) * tr.nboxes * tr.NT, ctx->stream));
@@ -407,7 +412,7 @@ int launch_p2m(lspr_ctx *ctx, bool fp64) {
         LSPR_TRY(ctx, cudaMemsetAsync(tr.mom32.p, 0, sizeof(float4) * tr.nboxes * tr.NT, ctx->stream));
         LSPR_DISPATCH_P(p2m_launch, float, ctx);
     }
-    timer_end(ctx, T_P2M, ev);
+    timer_end(ctx, slot, ev);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
@@ -416,13 +421,14 @@ int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc) {
     Tree &tr = ctx->tree;
     if (tr.n_m2p_items == 0) return LSPR_OK;
     cudaEvent_t ev;
-    timer_begin(ctx, T_M2P, &ev);
+    const int slot = fp64 ? T_M2P64 : T_M2P;
+    timer_begin(ctx, slot, &ev);
     if (fp64) {
         LSPR_DISPATCH_P(m2p_launch, double, ctx, acc);
     } else {
         LSPR_DISPATCH_P(m2p_launch, float, ctx, acc);
     }
-    timer_end(ctx, T_M2P, ev);
+    timer_end(ctx, slot, ev);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }

@@ -113,16 +113,21 @@ struct DirectItems {
     DArr<int4> items;
 };
 
+constexpr int kTimerSlots = 12;
+
 struct Timing {
     bool enabled = false;
-    double ms[8] = {0};
-    int64_t launches[8] = {0};
+    double ms[kTimerSlots] = {0};
+    int64_t launches[kTimerSlots] = {0};
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     size_t used = 0;
 };
 
-enum TimerSlot { T_P2P = 0, T_M2P = 1, T_P2M = 2, T_NEAR = 3, T_GMRES = 4, T_TREE = 5, T_MESH = 6, T_OTHER = 7 };
+enum TimerSlot {
+    T_P2P = 0, T_M2P = 1, T_P2M = 2, T_NEAR = 3, T_GMRES = 4, T_TREE = 5, T_MESH = 6, T_OTHER = 7,
+    T_P2P64 = 8, T_M2P64 = 9, T_P2M64 = 10, T_WEIGHTS = 11
+};
 
 }  // namespace lspr
 
@@ -184,6 +189,19 @@ int workorder_natural(lspr_ctx *ctx);
 
 // ------------------------------------------------------------ tree.cu
 int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit);
+// stable LSD radix sort of (keys, vals) on the context's stream (bits: key width)
+int radix_sort(lspr_ctx *ctx, unsigned *keys, int *vals, unsigned *ktmp, int *vals_tmp, int64_t n, int bits, int *hist,
+               int *offs);
+int64_t radix_sort_scratch_ints(int64_t n);   // ints needed by each of hist and offs
+// 10-bit coordinate -> every third bit (Morton interleave helper)
+__device__ __forceinline__ unsigned spread10(unsigned v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
 
 // ------------------------------------------------------------ farfield.cu
 // accumulate far parts (coarse rule everywhere except own panel) into acc[N][4]

@@ -232,9 +232,8 @@ __global__ void self_kernel(const double *__restrict__ verts, const int *__restr
 }
 
 // ----------------------------------------------------------------------------
-// Near-singular search: brute force over all panel pairs.  An FP32 prefilter
-// with a safety margin selects candidates; the decision itself is the FP64
-// test L_j / |c_i - c_j| >= threshold with separately rounded operations.
+// Near-singular decision: the FP64 test L_j / |c_i - c_j| >= threshold with every
+// operation rounded separately (reproducible on any IEEE machine).
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ bool near_exact(double xi, double yi, double zi, double xj, double yj, double zj,
                                            double Lj, double thr) {
@@ -243,43 +242,71 @@ __device__ __forceinline__ bool near_exact(double xi, double yi, double zi, doub
     return __ddiv_rn(Lj, dist) >= thr;
 }
 
-template <bool FILL>
-__global__ void near_search_kernel(int64_t N, const double *__restrict__ cx, const double *__restrict__ cy,
-                                   const double *__restrict__ cz, const double *__restrict__ L, double thr,
-                                   float slack, int64_t *count, const int64_t *ptr, int *col, int *row) {
-    __shared__ float4 tile[256];
+// ----------------------------------------------------------------------------
+// Cell list for the near-singular search: cubic cells of edge h >= L_max/threshold,
+// panels sorted by the Morton key of the cell holding their centroid.  Every panel
+// j with L_j/|c_i - c_j| >= threshold lies within L_max/threshold of c_i, hence in
+// one of the 27 cells around c_i's cell.  Cell coordinates come from the same FP64
+// expression for keys and queries.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int cell_coord(double c, double lo, double inv_h) {
+    const double u = floor((c - lo) * inv_h);
+    return (int)fmin(1023.0, fmax(0.0, u));
+}
+
+__device__ __forceinline__ unsigned cell_key(int ix, int iy, int iz) {
+    return (spread10((unsigned)ix) << 2) | (spread10((unsigned)iy) << 1) | spread10((unsigned)iz);
+}
+
+__global__ void cell_key_kernel(int64_t N, const double *__restrict__ cx, const double *__restrict__ cy,
+                                const double *__restrict__ cz, const double *grid /* lo[3], 1/h */, unsigned *keys,
+                                int *vals) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const bool valid = i < N;
-    double xi = 0, yi = 0, zi = 0;
-    if (valid) { xi = cx[i]; yi = cy[i]; zi = cz[i]; }
-    const float fx = (float)xi, fy = (float)yi, fz = (float)zi;
-    int64_t c = 0;
-    int64_t out = 0;
-    if (FILL && valid) {
+    if (i >= N) return;
+    keys[i] = cell_key(cell_coord(cx[i], grid[0], grid[3]), cell_coord(cy[i], grid[1], grid[3]),
+                       cell_coord(cz[i], grid[2], grid[3]));
+    vals[i] = (int)i;
+}
+
+__device__ __forceinline__ int lower_bound_u(const unsigned *a, int n, unsigned v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <bool FILL>
+__global__ void near_cells_kernel(int64_t N, const double *__restrict__ cx, const double *__restrict__ cy,
+                                  const double *__restrict__ cz, const double *__restrict__ L, double thr,
+                                  const double *grid, const unsigned *__restrict__ skeys, const int *__restrict__ sidx,
+                                  int64_t *count, const int64_t *ptr, int *col, int *row) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double xi = cx[i], yi = cy[i], zi = cz[i];
+    const int ix = cell_coord(xi, grid[0], grid[3]), iy = cell_coord(yi, grid[1], grid[3]),
+              iz = cell_coord(zi, grid[2], grid[3]);
+    int64_t out = 0, c = 0;
+    if (FILL) {
         out = ptr[i];
         col[out] = (int)i;   // self entry first
         row[out] = (int)i;
         ++out;
     }
-    for (int64_t base = 0; base < N; base += 256) {
-        __syncthreads();
-        int64_t j = base + threadIdx.x;
-        if (j < N) {
-            float r = (float)(L[j] / thr) + slack;
-            tile[threadIdx.x] = make_float4((float)cx[j], (float)cy[j], (float)cz[j], r * r * 1.00001f);
-        }
-        __syncthreads();
-        int cnt = (int)min((int64_t)256, N - base);
-        if (!valid) continue;
-        for (int k = 0; k < cnt; ++k) {
-            float4 p = tile[k];
-            float dx = fx - p.x, dy = fy - p.y, dz = fz - p.z;
-            float d2 = dx * dx + dy * dy + dz * dz;
-            if (d2 <= p.w) {
-                int64_t jj = base + k;
-                if (jj != i && near_exact(xi, yi, zi, cx[jj], cy[jj], cz[jj], L[jj], thr)) {
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int qx = ix + dx, qy = iy + dy, qz = iz + dz;
+                if (qx < 0 || qy < 0 || qz < 0 || qx > 1023 || qy > 1023 || qz > 1023) continue;
+                const unsigned key = cell_key(qx, qy, qz);
+                int k = lower_bound_u(skeys, (int)N, key);
+                for (; k < N && skeys[k] == key; ++k) {
+                    const int j = sidx[k];
+                    if (j == i || !near_exact(xi, yi, zi, cx[j], cy[j], cz[j], L[j], thr)) continue;
                     if (FILL) {
-                        col[out] = (int)jj;
+                        col[out] = j;
                         row[out] = (int)i;
                         ++out;
                     } else {
@@ -287,9 +314,7 @@ __global__ void near_search_kernel(int64_t N, const double *__restrict__ cx, con
                     }
                 }
             }
-        }
-    }
-    if (!FILL && valid) count[i] = c + 1;
+    if (!FILL) count[i] = c + 1;
 }
 
 // exclusive scan of n int64 counts into ptr[0..n], single block
@@ -448,21 +473,52 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     std::memcpy(&bad, &hflags[0], sizeof(int));
     m.rho_max = hflags[1];
     m.Lmax = hflags[2];
-    const double maxabs = hflags[3];
     flags.release();
     if (bad & 1) return LSPR_E_ARG;
     if (bad & 2) return LSPR_E_MESH;
 
-    // near-singular list
+    // near-singular list from a cell list (cell edge >= L_max / threshold)
     DArr<int64_t> cnt;
     LSPR_TRY(ctx, cnt.ensure(N));
     LSPR_TRY(ctx, m.near_ptr.ensure(N + 1));
-    // FP32 prefilter: candidates within L_j/threshold + slack, the slack covering the
-    // FP32 rounding of the coordinates (~1e-7 of the largest coordinate) 25 times over
-    const float slack = (float)(1e-5 * maxabs + 1e-30);
+    double hgrid[4];
+    {
+        std::vector<double> hc(3 * N);
+        // bounding box of the centroids (host copy of three N-vectors, once per geometry)
+        LSPR_TRY(ctx, cudaMemcpyAsync(hc.data(), m.cx.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaMemcpyAsync(hc.data() + N, m.cy.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaMemcpyAsync(hc.data() + 2 * N, m.cz.p, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaStreamSynchronize(st));
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int d = 0; d < 3; ++d)
+            for (int64_t i = 0; i < N; ++i) {
+                lo[d] = std::min(lo[d], hc[d * N + i]);
+                hi[d] = std::max(hi[d], hc[d * N + i]);
+            }
+        const double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+        const double h = std::max(m.Lmax / m.thr * (1.0 + 1e-9), ext / 1023.0) * (1.0 + 1e-12) + 1e-300;
+        hgrid[0] = lo[0];
+        hgrid[1] = lo[1];
+        hgrid[2] = lo[2];
+        hgrid[3] = 1.0 / h;
+    }
+    DArr<double> grid;
+    DArr<unsigned> keys, ktmp;
+    DArr<int> vals, vtmp, hist, offs;
+    LSPR_TRY(ctx, grid.ensure(4));
+    LSPR_TRY(ctx, keys.ensure(N));
+    LSPR_TRY(ctx, ktmp.ensure(N));
+    LSPR_TRY(ctx, vals.ensure(N));
+    LSPR_TRY(ctx, vtmp.ensure(N));
+    LSPR_TRY(ctx, hist.ensure(radix_sort_scratch_ints(N)));
+    LSPR_TRY(ctx, offs.ensure(radix_sort_scratch_ints(N)));
+    LSPR_TRY(ctx, cudaMemcpyAsync(grid.p, hgrid, sizeof(hgrid), cudaMemcpyHostToDevice, st));
     ++ctx->n_launches;
-    near_search_kernel<false><<<grid_for(N, 256), 256, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, slack,
-                                                                 cnt.p, nullptr, nullptr, nullptr);
+    cell_key_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, grid.p, keys.p, vals.p);
+    LSPR_TRY_ST(radix_sort(ctx, keys.p, vals.p, ktmp.p, vtmp.p, N, 30, hist.p, offs.p));
+    ++ctx->n_launches;
+    near_cells_kernel<false><<<grid_for(N, 128), 128, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, grid.p,
+                                                               keys.p, vals.p, cnt.p, nullptr, nullptr, nullptr);
     ++ctx->n_launches;
     scan_kernel<<<1, 1024, 0, st>>>(cnt.p, N, m.near_ptr.p);
     LSPR_TRY(ctx, cudaGetLastError());
@@ -474,8 +530,9 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     DArr<int> rowidx;
     LSPR_TRY(ctx, rowidx.ensure(m.nnz));
     ++ctx->n_launches;
-    near_search_kernel<true><<<grid_for(N, 256), 256, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, slack,
-                                                               nullptr, m.near_ptr.p, m.near_col.p, rowidx.p);
+    near_cells_kernel<true><<<grid_for(N, 128), 128, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, grid.p,
+                                                              keys.p, vals.p, nullptr, m.near_ptr.p, m.near_col.p,
+                                                              rowidx.p);
     ++ctx->n_launches;
     near_values_kernel<<<grid_for(m.nnz, 128), 128, 0, st>>>(m.nnz, rowidx.p, m.near_col.p, m.verts.p, m.tris.p,
                                                              m.cx.p, m.cy.p, m.cz.p, m.nx.p, m.ny.p, m.nz.p, m.area.p,
@@ -485,6 +542,9 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     LSPR_TRY(ctx, cudaStreamSynchronize(st));
     cnt.release();
     rowidx.release();
+    for (auto *a : {&keys, &ktmp}) a->release();
+    for (auto *a : {&vals, &vtmp, &hist, &offs}) a->release();
+    grid.release();
     m.ready = true;
     return workorder_natural(ctx);
 }

@@ -515,7 +515,6 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
     cudaStream_t st = ctx->stream;
     const int mode = o.mode;
     const bool tree = mode == LSPR_TREE_FP64 || mode == LSPR_TREE_FP32;
-    const int mode64 = tree ? LSPR_TREE_FP64 : LSPR_DIRECT_FP64;
     const double2 eout = make_double2(eps_out_re, eps_out_im);
     LSPR_TRY(ctx, ctx->gm_eps.ensure(B));
     LSPR_TRY(ctx, ctx->gm_s.ensure(B));
@@ -533,11 +532,13 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
     }
     LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_eps.p, he.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, st));
     LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_s.p, hs.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, st));
-    // right-hand side in FP64: V (dphi_inc/dn)
+    // right-hand side V (dphi_inc/dn) with the operator of the solve's mode: dphi_inc/dn
+    // is smooth and the sum has no cancellation, so FP32 evaluation (FP64 accumulation)
+    // leaves ~1e-7 relative error in b
     double2 *xin = ctx->gm_vinc.p, *Vinc = ctx->gm_vinc.p + n2;
     ++ctx->n_launches;
     dphi_inc_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, me.nx.p, me.ny.p, me.nz.p, E0[0], E0[1], E0[2], xin);
-    LSPR_TRY_ST(layer_potentials(ctx, mode64, xin, Vinc, Vinc + N));
+    LSPR_TRY_ST(layer_potentials(ctx, mode, xin, Vinc, Vinc + N));
     ++ctx->n_launches;
     rhs_kernel<<<dim3(grid_for(N, 256), B), 256, 0, st>>>(B, N, Vinc, ctx->gm_eps.p, eout, ctx->gm_b.p);
     LSPR_TRY(ctx, cudaMemsetAsync(ctx->gm_x.p, 0, sizeof(double2) * B * n2, st));

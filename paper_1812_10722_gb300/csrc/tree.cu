@@ -25,6 +25,7 @@ constexpr int kP2PChunk = 1024;     // sources per P2P work item (upper bound)
 constexpr int kM2PSeg = 16;         // boxes per M2P work item
 constexpr int kP2MChunk = 512;      // sources per P2M work item
 constexpr int kStack = 96;
+constexpr int kGeomThreads = 512;   // the root box holds every source
 
 // ------------------------------------------------------------ bounding cube
 __global__ void bbox_kernel(const dbl4 *__restrict__ a, int64_t na, const dbl4 *__restrict__ b, int64_t nb,
@@ -49,15 +50,6 @@ __global__ void bbox_kernel(const dbl4 *__restrict__ a, int64_t na, const dbl4 *
     }
     if (t == 0)
         for (int d = 0; d < 3; ++d) { out[d] = lo[d][0]; out[3 + d] = hi[d][0]; }
-}
-
-__device__ __forceinline__ unsigned spread10(unsigned v) {
-    v &= 0x3ffu;
-    v = (v | (v << 16)) & 0x030000ffu;
-    v = (v | (v << 8)) & 0x0300f00fu;
-    v = (v | (v << 4)) & 0x030c30c3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
 }
 
 // key bit 3l+2 / 3l+1 / 3l = x / y / z bit l, so the top triple selects the octant
@@ -173,7 +165,9 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(const unsig
 }
 
 // sorts (keys, vals) of length n in place using the given scratch
-static int radix_sort(lspr_ctx *ctx, unsigned *keys, int *vals, unsigned *ktmp, int *vtmp, int64_t n, int bits,
+int64_t radix_sort_scratch_ints(int64_t n) { return kDigits * ((n + kSortTile - 1) / kSortTile); }
+
+int radix_sort(lspr_ctx *ctx, unsigned *keys, int *vals, unsigned *ktmp, int *vtmp, int64_t n, int bits,
                       int *hist, int *offs) {
     const int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     cudaStream_t st = ctx->stream;
@@ -325,7 +319,7 @@ __global__ void __launch_bounds__(1024) octree_kernel(const unsigned *__restrict
 // centre of the bounding box of the box's sources and r_b = max distance to it
 __global__ void box_geometry_kernel(int nboxes, const int *beg, const int *end, const dbl4 *__restrict__ spos,
                                     dbl4 *c64, float4 *c32) {
-    __shared__ double red[6][128];
+    __shared__ double red[6][kGeomThreads];
     __shared__ double cen[3];
     const int b = blockIdx.x;
     if (b >= nboxes) return;
@@ -555,7 +549,7 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     LSPR_TRY(ctx, tr.box_c64.ensure(nboxes));
     LSPR_TRY(ctx, tr.box_c32.ensure(nboxes));
     ++ctx->n_launches;
-    box_geometry_kernel<<<nboxes, 128, 0, st>>>(nboxes, tr.box_beg.p, tr.box_end.p, w.spos64.p, tr.box_c64.p,
+    box_geometry_kernel<<<nboxes, kGeomThreads, 0, st>>>(nboxes, tr.box_beg.p, tr.box_end.p, w.spos64.p, tr.box_c64.p,
                                                 tr.box_c32.p);
 
     // target blocks

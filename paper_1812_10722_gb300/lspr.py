@@ -231,8 +231,9 @@ class Context:
         _check(lib().lspr_set_timing(self._h, int(bool(enable))), "lspr_set_timing")
 
     def timing(self) -> dict:
-        ms = np.zeros(8)
-        n = np.zeros(8, np.int64)
+        ms = np.zeros(12)
+        n = np.zeros(12, np.int64)
         _check(lib().lspr_get_timing(self._h, _host_ptr(ms), _host_ptr(n)), "lspr_get_timing")
-        names = ["p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh", "other"]
+        names = ["p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh", "other", "p2p_fp64", "m2p_fp64",
+                 "p2m_fp64", "weights"]
         return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}

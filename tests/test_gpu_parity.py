@@ -5,7 +5,10 @@ Tolerances (relative L2 unless stated):
                               N_k = 9 vs the exact one, ~1e-8, and summation order)
   direct FP32 matvec  1e-5
   treecode P = 6, theta = 0.5 (FP32 or FP64) 1e-4
-  sigma_ext           1e-4 relative (1e-6 in direct FP64 mode)
+  sigma_ext           1e-6 relative in direct FP64 mode, 1e-5 in refined direct FP32
+                      mode (FP32 right-hand side); treecode P = 6, theta = 0.5: 3e-4
+                      (the solve amplifies the ~1e-5 operator error near the
+                      resonance); treecode P = 8: 1e-4
 Near-singular classification is an integer decision: it must match exactly.
 """
 import json
@@ -157,7 +160,7 @@ def _golden(name):
 # iterative refinement; the refined solution is that of the FP64 operator of the
 # same kind (direct or treecode).
 @pytest.mark.parametrize("mode,tol,gtol,refine", [("direct_fp64", 1e-6, 1e-8, False),
-                                                  ("direct_fp32", 1e-6, 1e-8, True),
+                                                  ("direct_fp32", 1e-5, 1e-8, True),
                                                   ("tree_fp64", 3e-4, 1e-8, False),
                                                   ("tree_fp32", 3e-4, 1e-8, True)])
 def test_solve_sigma_sphere1280(lspr, mode, tol, gtol, refine):
@@ -175,7 +178,8 @@ def test_solve_sigma_sphere1280(lspr, mode, tol, gtol, refine):
 
 
 def test_fp32_refinement_matches_fp64_operator(lspr):
-    # the refined FP32 solve reproduces the FP64 solve of the same operator
+    # the refined FP32 solve reproduces the FP64 solve of the same operator, up to the
+    # ~1e-7 FP32 error of its right-hand side amplified by the conditioning near resonance
     v, t = I.icosphere(3, 10.0)
     ep = I.drude_eps(375.0)
     with lspr.Context(0) as ctx:
@@ -185,7 +189,7 @@ def test_fp32_refinement_matches_fp64_operator(lspr):
         b = ctx.solve(ep, I.EPS_WATER, 375.0, tol=1e-9, mode="tree_fp32", refine=True, restart=100)
         c = ctx.solve(ep, I.EPS_WATER, 375.0, tol=3e-5, mode="tree_fp32", refine=False, restart=100)
     assert a.status[0] == 0 and b.status[0] == 0 and c.status[0] == 0
-    assert abs(b.sigma_ext[0] - a.sigma_ext[0]) / a.sigma_ext[0] < 1e-6
+    assert abs(b.sigma_ext[0] - a.sigma_ext[0]) / a.sigma_ext[0] < 1e-5
     assert abs(c.sigma_ext[0] - a.sigma_ext[0]) / a.sigma_ext[0] < 2e-3
 
 
