@@ -92,6 +92,10 @@ typedef struct {
 /* Text for a status code (static storage). */
 LSPR_API const char *lspr_status_string(int status);
 
+/* Text of the last CUDA or argument error recorded by the context ("" if none);
+ * valid until the next call on the context. */
+LSPR_API const char *lspr_last_error(lspr_ctx *ctx);
+
 /* Library version string (static storage). */
 LSPR_API const char *lspr_version(void);
 

@@ -9,7 +9,11 @@
 
 namespace lspr {
 
-void timer_begin(lspr_ctx *ctx, int slot, cudaEvent_t *ev) {
+void timer_begin(lspr_ctx *ctx, int slot, cudaEvent_t *ev) { timer_begin_on(ctx, slot, ev, ctx->stream); }
+
+void timer_end(lspr_ctx *ctx, int slot, cudaEvent_t ev) { timer_end_on(ctx, slot, ev, ctx->stream); }
+
+void timer_begin_on(lspr_ctx *ctx, int slot, cudaEvent_t *ev, cudaStream_t st) {
     (void)slot;
     *ev = nullptr;
     Timing &t = ctx->timing;
@@ -22,10 +26,10 @@ void timer_begin(lspr_ctx *ctx, int slot, cudaEvent_t *ev) {
         }
     }
     *ev = t.pool[t.used++];
-    cudaEventRecord(*ev, ctx->stream);
+    cudaEventRecord(*ev, st);
 }
 
-void timer_end(lspr_ctx *ctx, int slot, cudaEvent_t ev) {
+void timer_end_on(lspr_ctx *ctx, int slot, cudaEvent_t ev, cudaStream_t st) {
     Timing &t = ctx->timing;
     if (!t.enabled || !ev) return;
     if (t.used + 1 > t.pool.size()) {
@@ -34,7 +38,7 @@ void timer_end(lspr_ctx *ctx, int slot, cudaEvent_t ev) {
         t.pool.push_back(e);
     }
     cudaEvent_t e2 = t.pool[t.used++];
-    cudaEventRecord(e2, ctx->stream);
+    cudaEventRecord(e2, st);
     t.pending.push_back({slot, {ev, e2}});
     if (t.used > 4096) timer_collect(ctx);
 }
@@ -46,6 +50,7 @@ void timer_collect(lspr_ctx *ctx) {
         return;
     }
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
     for (auto &p : t.pending) {
         float ms = 0;
         if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
@@ -79,6 +84,8 @@ const char *lspr_status_string(int s) {
 
 const char *lspr_version(void) { return "lspr-gb300 0.1 (sm_103a)"; }
 
+const char *lspr_last_error(lspr_ctx *c) { return c ? c->last_error.c_str() : ""; }
+
 int lspr_create(lspr_ctx **out, int device, void *cuda_stream) {
     if (!out) return LSPR_E_ARG;
     *out = nullptr;
@@ -93,6 +100,12 @@ int lspr_create(lspr_ctx **out, int device, void *cuda_stream) {
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        lspr_destroy(c);
+        return LSPR_E_CUDA;
+    }
     *out = c;
     return LSPR_OK;
 }
@@ -123,6 +136,15 @@ int lspr_destroy(lspr_ctx *c) {
                              &c->gm_vinc, &c->gm_eps})
         a->release();
     for (cudaEvent_t e : c->timing.pool) cudaEventDestroy(e);
+    c->counters.release();
+    c->wo.tgt_pos.release();
+    c->wo.src_tblock.release();
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
     delete c;
     return LSPR_OK;
 }

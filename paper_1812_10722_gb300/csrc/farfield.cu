@@ -17,6 +17,8 @@
 //               n = |k|, a_0 = 1/|R|.
 // Partial sums are formed in the kernel's precision (FP32 or FP64) per work
 // item and accumulated in FP64 with atomics.
+#include <algorithm>
+
 #include "lspr_internal.cuh"
 
 namespace lspr {
@@ -53,13 +55,15 @@ struct P2PAcc {
     T vr, vi, kr, ki;
 };
 
-template <typename T, typename T4>
+// One (target, source) pair.  CHECK: the item may hold sources of the target's own
+// panel, whose far-rule terms are skipped (the exact singular integral replaces them).
+template <typename T, typename T4, bool CHECK>
 __device__ __forceinline__ void p2p_pair(const T4 &p, const T4 &n, const T4 &w, int pid, T tx, T ty, T tz, int tp,
                                          P2PAcc<T> &a) {
     const T dx = tx - p.x, dy = ty - p.y, dz = tz - p.z;
     const T r2 = dx * dx + dy * dy + dz * dz;
     T ri = rsq(r2);
-    ri = (pid == tp) ? T(0) : ri;   // own panel: the exact singular integral replaces it
+    if (CHECK) ri = (pid == tp) ? T(0) : ri;
     const T dn = dx * n.x + dy * n.y + dz * n.z;
     const T t3 = dn * (ri * ri) * ri;
     a.vr += ri * w.x;
@@ -70,65 +74,94 @@ __device__ __forceinline__ void p2p_pair(const T4 &p, const T4 &n, const T4 &w, 
 
 constexpr int kP2PWarps = 8;
 
-template <typename T>
+// Sources [beg, end) against the lane's two targets; the warp stages 32 sources at a
+// time in its shared-memory slice and every lane reads them by broadcast.
+template <typename T, typename T4, bool CHECK>
+__device__ __forceinline__ void p2p_range(int beg, int end, int lane, T4 (*sh)[32], const T4 *__restrict__ spos,
+                                          const T4 *__restrict__ snrm, const T4 *__restrict__ sw, const T4 &q0,
+                                          const T4 &q1, int tp0, int tp1, P2PAcc<T> &a0, P2PAcc<T> &a1) {
+    for (int base = beg; base < end; base += 32) {
+        const int s = base + lane;
+        if (s < end) {
+            sh[0][lane] = spos[s];
+            sh[1][lane] = snrm[s];
+            sh[2][lane] = sw[s];
+        }
+        __syncwarp();
+        const int cnt = min(32, end - base);
+        if (cnt == 32) {
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                const T4 p = sh[0][k], n = sh[1][k], w = sh[2][k];
+                const int pid = panel_of(n.w);
+                p2p_pair<T, T4, CHECK>(p, n, w, pid, q0.x, q0.y, q0.z, tp0, a0);
+                p2p_pair<T, T4, CHECK>(p, n, w, pid, q1.x, q1.y, q1.z, tp1, a1);
+            }
+        } else {
+            for (int k = 0; k < cnt; ++k) {
+                const T4 p = sh[0][k], n = sh[1][k], w = sh[2][k];
+                const int pid = panel_of(n.w);
+                p2p_pair<T, T4, CHECK>(p, n, w, pid, q0.x, q0.y, q0.z, tp0, a0);
+                p2p_pair<T, T4, CHECK>(p, n, w, pid, q1.x, q1.y, q1.z, tp1, a1);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void atomic_add4(double *o, double a, double b, double c, double d) {
+    atomicAdd(o + 0, a);
+    atomicAdd(o + 1, b);
+    atomicAdd(o + 2, c);
+    atomicAdd(o + 3, d);
+}
+
+// Work items (target block, source begin, source end, own-panel flag), one per warp.
+// DYNAMIC: a persistent grid whose warps take items from an atomic counter.
+template <typename T, bool DYNAMIC>
 __global__ void __launch_bounds__(kP2PWarps * 32) p2p_kernel(const int4 *__restrict__ items, int64_t nitems,
                                                              const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt,
                                                              const typename Vec4<T>::type *__restrict__ spos,
                                                              const typename Vec4<T>::type *__restrict__ snrm,
                                                              const typename Vec4<T>::type *__restrict__ sw,
-                                                             double *__restrict__ acc) {
+                                                             double *__restrict__ acc, int *counter) {
     using T4 = typename Vec4<T>::type;
     __shared__ T4 sh[kP2PWarps][3][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t it = (int64_t)blockIdx.x * kP2PWarps + warp;
+    int64_t it = (int64_t)blockIdx.x * kP2PWarps + warp;
+    while (true) {
+        if (DYNAMIC) {
+            int v = 0;
+            if (lane == 0) v = atomicAdd(counter, 1);
+            it = __shfl_sync(0xffffffffu, v, 0);
+        }
+        if (it >= nitems) return;
+        const int4 item = __ldg(items + it);
+        const int64_t t0 = (int64_t)item.x * kTargetBlock + lane, t1 = t0 + 32;
+        const T4 q0 = t0 < ntgt ? tgt[t0] : tgt[0];
+        const T4 q1 = t1 < ntgt ? tgt[t1] : tgt[0];
+        const int tp0 = panel_of(q0.w), tp1 = panel_of(q1.w);
+        P2PAcc<T> a0 = {0, 0, 0, 0}, a1 = {0, 0, 0, 0};
+        if (item.w)
+            p2p_range<T, T4, true>(item.y, item.z, lane, sh[warp], spos, snrm, sw, q0, q1, tp0, tp1, a0, a1);
+        else
+            p2p_range<T, T4, false>(item.y, item.z, lane, sh[warp], spos, snrm, sw, q0, q1, tp0, tp1, a0, a1);
+        if (t0 < ntgt) atomic_add4(acc + 4 * (int64_t)tp0, a0.vr, a0.vi, a0.kr, a0.ki);
+        if (t1 < ntgt) atomic_add4(acc + 4 * (int64_t)tp1, a1.vr, a1.vi, a1.kr, a1.ki);
+        if (!DYNAMIC) return;
+    }
+}
+
+// item.w = 1 iff some source of [item.y, item.z) belongs to a panel of the item's target block
+__global__ void item_flags_kernel(int4 *items, int64_t nitems, const int *__restrict__ src_tblock) {
+    const int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (it >= nitems) return;
-    const int4 item = __ldg(items + it);
-    const int64_t t0 = (int64_t)item.x * kTargetBlock + lane, t1 = t0 + 32;
-    T4 q0 = t0 < ntgt ? tgt[t0] : tgt[0];
-    T4 q1 = t1 < ntgt ? tgt[t1] : tgt[0];
-    const int tp0 = panel_of(q0.w), tp1 = panel_of(q1.w);
-    P2PAcc<T> a0 = {0, 0, 0, 0}, a1 = {0, 0, 0, 0};
-    for (int base = item.y; base < item.z; base += 32) {
-        const int s = base + lane;
-        if (s < item.z) {
-            sh[warp][0][lane] = spos[s];
-            sh[warp][1][lane] = snrm[s];
-            sh[warp][2][lane] = sw[s];
-        }
-        __syncwarp();
-        const int cnt = min(32, item.z - base);
-        if (cnt == 32) {
-#pragma unroll 8
-            for (int k = 0; k < 32; ++k) {
-                const T4 p = sh[warp][0][k], n = sh[warp][1][k], w = sh[warp][2][k];
-                const int pid = panel_of(n.w);
-                p2p_pair<T, T4>(p, n, w, pid, q0.x, q0.y, q0.z, tp0, a0);
-                p2p_pair<T, T4>(p, n, w, pid, q1.x, q1.y, q1.z, tp1, a1);
-            }
-        } else {
-            for (int k = 0; k < cnt; ++k) {
-                const T4 p = sh[warp][0][k], n = sh[warp][1][k], w = sh[warp][2][k];
-                const int pid = panel_of(n.w);
-                p2p_pair<T, T4>(p, n, w, pid, q0.x, q0.y, q0.z, tp0, a0);
-                p2p_pair<T, T4>(p, n, w, pid, q1.x, q1.y, q1.z, tp1, a1);
-            }
-        }
-        __syncwarp();
-    }
-    if (t0 < ntgt) {
-        double *o = acc + 4 * (int64_t)tp0;
-        atomicAdd(o + 0, (double)a0.vr);
-        atomicAdd(o + 1, (double)a0.vi);
-        atomicAdd(o + 2, (double)a0.kr);
-        atomicAdd(o + 3, (double)a0.ki);
-    }
-    if (t1 < ntgt) {
-        double *o = acc + 4 * (int64_t)tp1;
-        atomicAdd(o + 0, (double)a1.vr);
-        atomicAdd(o + 1, (double)a1.vi);
-        atomicAdd(o + 2, (double)a1.kr);
-        atomicAdd(o + 3, (double)a1.ki);
-    }
+    int4 item = items[it];
+    int hit = 0;
+    for (int s = item.y + lane; s < item.z; s += 32) hit |= src_tblock[s] == item.x;
+    hit = __any_sync(0xffffffffu, hit);
+    if (lane == 0) items[it].w = hit;
 }
 
 // ------------------------------------------------------------ multi-indices
@@ -176,9 +209,9 @@ __device__ __forceinline__ void m2p_one(T Rx, T Ry, T Rz, const typename Vec4<T>
     constexpr int NT = MultiIndex<P>::NT;
     const T R[3] = {Rx, Ry, Rz};
     const T r2 = Rx * Rx + Ry * Ry + Rz * Rz;
-    const T ir2 = T(1) / r2;
     T a[NT];
     a[0] = rsq(r2);
+    const T ir2 = a[0] * a[0];
     {
         const auto m = mom[0];
         acc.vr += a[0] * m.x;
@@ -207,36 +240,45 @@ __device__ __forceinline__ void m2p_one(T Rx, T Ry, T Rz, const typename Vec4<T>
 
 constexpr int kM2PWarps = 4;
 
-template <typename T, int P>
+// Work items (target block, list begin, list end): each lane evaluates the boxes'
+// expansions at its two targets; a box's moments are staged in the warp's shared slice.
+template <typename T, int P, bool DYNAMIC>
 __global__ void __launch_bounds__(kM2PWarps * 32) m2p_kernel(const int4 *__restrict__ items, int64_t nitems,
                                                              const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt,
                                                              const int *__restrict__ list,
                                                              const typename Vec4<T>::type *__restrict__ box_c,
                                                              const typename Vec4<T>::type *__restrict__ mom,
-                                                             double *__restrict__ acc) {
+                                                             double *__restrict__ acc, int *counter) {
     using T4 = typename Vec4<T>::type;
     constexpr int NT = n_terms(P);
+    __shared__ T4 sm[kM2PWarps][NT];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t it = (int64_t)blockIdx.x * kM2PWarps + warp;
-    if (it >= nitems) return;
-    const int4 item = __ldg(items + it);
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        const int64_t ti = (int64_t)item.x * kTargetBlock + lane + 32 * h;
-        if (ti >= ntgt) continue;
-        const T4 q = tgt[ti];
-        P2PAcc<T> a = {0, 0, 0, 0};
+    int64_t it = (int64_t)blockIdx.x * kM2PWarps + warp;
+    while (true) {
+        if (DYNAMIC) {
+            int v = 0;
+            if (lane == 0) v = atomicAdd(counter, 1);
+            it = __shfl_sync(0xffffffffu, v, 0);
+        }
+        if (it >= nitems) return;
+        const int4 item = __ldg(items + it);
+        const int64_t t0 = (int64_t)item.x * kTargetBlock + lane, t1 = t0 + 32;
+        const T4 q0 = t0 < ntgt ? tgt[t0] : tgt[0];
+        const T4 q1 = t1 < ntgt ? tgt[t1] : tgt[0];
+        P2PAcc<T> a0 = {0, 0, 0, 0}, a1 = {0, 0, 0, 0};
 #pragma unroll 1
         for (int l = item.y; l < item.z; ++l) {
             const int b = __ldg(list + l);
             const T4 c = box_c[b];
-            m2p_one<T, P>(q.x - c.x, q.y - c.y, q.z - c.z, mom + (int64_t)b * NT, a);
+            __syncwarp();
+            for (int t = lane; t < NT; t += 32) sm[warp][t] = mom[(int64_t)b * NT + t];
+            __syncwarp();
+            m2p_one<T, P>(q0.x - c.x, q0.y - c.y, q0.z - c.z, sm[warp], a0);
+            m2p_one<T, P>(q1.x - c.x, q1.y - c.y, q1.z - c.z, sm[warp], a1);
         }
-        double *o = acc + 4 * (int64_t)panel_of(q.w);
-        atomicAdd(o + 0, (double)a.vr);
-        atomicAdd(o + 1, (double)a.vi);
-        atomicAdd(o + 2, (double)a.kr);
-        atomicAdd(o + 3, (double)a.ki);
+        if (t0 < ntgt) atomic_add4(acc + 4 * (int64_t)panel_of(q0.w), a0.vr, a0.vi, a0.kr, a0.ki);
+        if (t1 < ntgt) atomic_add4(acc + 4 * (int64_t)panel_of(q1.w), a1.vr, a1.vi, a1.kr, a1.ki);
+        if (!DYNAMIC) return;
     }
 }
 
@@ -334,20 +376,48 @@ int launch_weights(lspr_ctx *ctx, bool fp64, const double2 *x, int64_t N) {
     return LSPR_OK;
 }
 
-int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, double *acc) {
+// persistent-grid size: resident blocks per SM x SMs (queried once per kernel instance)
+template <class K>
+static unsigned persistent_grid(lspr_ctx *ctx, K kernel, int threads, int *cache) {
+    if (*cache <= 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        *cache = per_sm;
+    }
+    return (unsigned)(*cache * std::max(1, ctx->num_sms));
+}
+
+int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, double *acc, cudaStream_t st,
+               int *counter) {
     if (nitems == 0) return LSPR_OK;
-    const unsigned grid = grid_for(nitems, kP2PWarps);
+    static int occ32 = 0, occ64 = 0;
     cudaEvent_t ev;
     const int slot = fp64 ? T_P2P64 : T_P2P;
-    timer_begin(ctx, slot, &ev);
+    timer_begin_on(ctx, slot, &ev, st);
     ++ctx->n_launches;
-    if (fp64)
-        p2p_kernel<double><<<grid, kP2PWarps * 32, 0, ctx->stream>>>(items, nitems, ctx->wo.tgt64.p, ctx->mesh.N,
-                                                                     ctx->wo.spos64.p, ctx->wo.snrm64.p, ctx->w64.p, acc);
-    else
-        p2p_kernel<float><<<grid, kP2PWarps * 32, 0, ctx->stream>>>(items, nitems, ctx->wo.tgt32.p, ctx->mesh.N,
-                                                                    ctx->wo.spos32.p, ctx->wo.snrm32.p, ctx->w32.p, acc);
-    timer_end(ctx, slot, ev);
+    if (fp64) {
+        const unsigned grid = std::min<unsigned>(grid_for(nitems, kP2PWarps),
+                                                 persistent_grid(ctx, p2p_kernel<double, true>, kP2PWarps * 32, &occ64));
+        p2p_kernel<double, true><<<grid, kP2PWarps * 32, 0, st>>>(items, nitems, ctx->wo.tgt64.p, ctx->mesh.N,
+                                                                  ctx->wo.spos64.p, ctx->wo.snrm64.p, ctx->w64.p, acc,
+                                                                  counter);
+    } else {
+        const unsigned grid = std::min<unsigned>(grid_for(nitems, kP2PWarps),
+                                                 persistent_grid(ctx, p2p_kernel<float, true>, kP2PWarps * 32, &occ32));
+        p2p_kernel<float, true><<<grid, kP2PWarps * 32, 0, st>>>(items, nitems, ctx->wo.tgt32.p, ctx->mesh.N,
+                                                                 ctx->wo.spos32.p, ctx->wo.snrm32.p, ctx->w32.p, acc,
+                                                                 counter);
+    }
+    timer_end_on(ctx, slot, ev, st);
+    LSPR_TRY(ctx, cudaGetLastError());
+    return LSPR_OK;
+}
+
+int launch_item_flags(lspr_ctx *ctx, int4 *items, int64_t nitems) {
+    if (nitems == 0) return LSPR_OK;
+    ++ctx->n_launches;
+    item_flags_kernel<<<grid_for(nitems * 32, 256), 256, 0, ctx->stream>>>(items, nitems, ctx->wo.src_tblock.p);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
@@ -370,8 +440,9 @@ static void p2m_launch(lspr_ctx *ctx) {
 }
 
 template <typename T, int P>
-static void m2p_launch(lspr_ctx *ctx, double *acc) {
+static void m2p_launch(lspr_ctx *ctx, double *acc, int *counter) {
     using T4 = typename Vec4<T>::type;
+    static int occ = 0;
     Tree &tr = ctx->tree;
     const T4 *tgt, *bc, *mom;
     if constexpr (sizeof(T) == 8) {
@@ -379,9 +450,10 @@ static void m2p_launch(lspr_ctx *ctx, double *acc) {
     } else {
         tgt = ctx->wo.tgt32.p; bc = tr.box_c32.p; mom = tr.mom32.p;
     }
-    ++ctx->n_launches;
-    m2p_kernel<T, P><<<grid_for(tr.n_m2p_items, kM2PWarps), kM2PWarps * 32, 0, ctx->stream>>>(
-        tr.m2p_items.p, tr.n_m2p_items, tgt, ctx->mesh.N, tr.m2p_list.p, bc, mom, acc);
+    const unsigned grid = std::min<unsigned>(grid_for(tr.n_m2p_items, kM2PWarps),
+                                             persistent_grid(ctx, m2p_kernel<T, P, true>, kM2PWarps * 32, &occ));
+    m2p_kernel<T, P, true><<<grid, kM2PWarps * 32, 0, ctx->stream>>>(tr.m2p_items.p, tr.n_m2p_items, tgt, ctx->mesh.N,
+                                                                    tr.m2p_list.p, bc, mom, acc, counter);
 }
 
 #define LSPR_DISPATCH_P(FN, T, ...)           \
@@ -417,16 +489,16 @@ int launch_p2m(lspr_ctx *ctx, bool fp64) {
     return LSPR_OK;
 }
 
-int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc) {
+int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc, int *counter) {
     Tree &tr = ctx->tree;
     if (tr.n_m2p_items == 0) return LSPR_OK;
     cudaEvent_t ev;
     const int slot = fp64 ? T_M2P64 : T_M2P;
     timer_begin(ctx, slot, &ev);
     if (fp64) {
-        LSPR_DISPATCH_P(m2p_launch, double, ctx, acc);
+        LSPR_DISPATCH_P(m2p_launch, double, ctx, acc, counter);
     } else {
-        LSPR_DISPATCH_P(m2p_launch, float, ctx, acc);
+        LSPR_DISPATCH_P(m2p_launch, float, ctx, acc, counter);
     }
     timer_end(ctx, slot, ev);
     LSPR_TRY(ctx, cudaGetLastError());
@@ -448,8 +520,8 @@ int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *
 int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, const float4 *tgt, int64_t ntgt,
                         const float4 *spos, const float4 *snrm, const float4 *w, double *acc) {
     if (nitems == 0) return LSPR_OK;
-    p2p_kernel<float><<<grid_for(nitems, kP2PWarps), kP2PWarps * 32, 0, st>>>(items, nitems, tgt, ntgt, spos, snrm, w,
-                                                                             acc);
+    p2p_kernel<float, false><<<grid_for(nitems, kP2PWarps), kP2PWarps * 32, 0, st>>>(items, nitems, tgt, ntgt, spos,
+                                                                                    snrm, w, acc, nullptr);
     return cudaGetLastError() == cudaSuccess ? LSPR_OK : LSPR_E_CUDA;
 }
 

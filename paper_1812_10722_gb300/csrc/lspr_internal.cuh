@@ -84,6 +84,8 @@ struct WorkOrder {   // sources/targets in the order the far-field kernels walk 
     DArr<float4> tgt32;
     DArr<int> src_panel;   // [Ns]
     DArr<int> tgt_panel;   // [N]
+    DArr<int> tgt_pos;     // [N] work-order position of each panel's target
+    DArr<int> src_tblock;  // [Ns] target block holding the source's own panel
 };
 
 struct Tree {
@@ -134,6 +136,9 @@ enum TimerSlot {
 struct lspr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;       // second stream: P2P overlaps P2M -> M2P
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    lspr::DArr<int> counters;          // work-item counters of the persistent kernels
     int num_sms = 0;
     lspr::Mesh mesh;
     lspr::WorkOrder wo;
@@ -177,6 +182,8 @@ int cuda_status(lspr_ctx *ctx, cudaError_t e, const char *what);
 // timing helpers (no-ops unless enabled)
 void timer_begin(lspr_ctx *ctx, int slot, cudaEvent_t *ev);
 void timer_end(lspr_ctx *ctx, int slot, cudaEvent_t ev);
+void timer_begin_on(lspr_ctx *ctx, int slot, cudaEvent_t *ev, cudaStream_t st);
+void timer_end_on(lspr_ctx *ctx, int slot, cudaEvent_t ev, cudaStream_t st);
 void timer_collect(lspr_ctx *ctx);
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
@@ -205,9 +212,12 @@ __device__ __forceinline__ unsigned spread10(unsigned v) {
 
 // ------------------------------------------------------------ farfield.cu
 // accumulate far parts (coarse rule everywhere except own panel) into acc[N][4]
-int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, double *acc);
+int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, double *acc, cudaStream_t st,
+               int *counter);
 int launch_p2m(lspr_ctx *ctx, bool fp64);
-int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc);
+int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc, int *counter);
+// item.w = 1 where a P2P item may contain sources of its own target block's panels
+int launch_item_flags(lspr_ctx *ctx, int4 *items, int64_t nitems);
 int launch_weights(lspr_ctx *ctx, bool fp64, const double2 *x, int64_t N);
 int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
                             const double2 *x, float4 *w);

@@ -386,7 +386,8 @@ __global__ void near_values_kernel(int64_t nnz, const int *row, const int *col, 
 
 __global__ void natural_order_kernel(int64_t N, int K, const dbl4 *pos, const dbl4 *nrm, const dbl4 *tgt,
                                      dbl4 *spos64, dbl4 *snrm64, float4 *spos32, float4 *snrm32,
-                                     dbl4 *tgt64, float4 *tgt32, int *src_panel, int *tgt_panel) {
+                                     dbl4 *tgt64, float4 *tgt32, int *src_panel, int *tgt_panel, int *tgt_pos,
+                                     int *src_tblock) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= N * K) return;
     dbl4 p = pos[s], n = nrm[s];
@@ -396,11 +397,13 @@ __global__ void natural_order_kernel(int64_t N, int K, const dbl4 *pos, const db
     spos32[s] = make_float4((float)p.x, (float)p.y, (float)p.z, (float)p.w);
     snrm32[s] = make_float4((float)n.x, (float)n.y, (float)n.z, __int_as_float(pid));
     src_panel[s] = pid;
+    src_tblock[s] = pid / kTargetBlock;
     if (s % K == 0) {
         dbl4 t = tgt[pid];
         tgt64[pid] = t;
         tgt32[pid] = make_float4((float)t.x, (float)t.y, (float)t.z, __int_as_float(pid));
         tgt_panel[pid] = pid;
+        tgt_pos[pid] = pid;
     }
 }
 
@@ -561,14 +564,17 @@ int workorder_natural(lspr_ctx *ctx) {
     LSPR_TRY(ctx, w.tgt32.ensure(m.N));
     LSPR_TRY(ctx, w.src_panel.ensure(m.Ns));
     LSPR_TRY(ctx, w.tgt_panel.ensure(m.N));
+    LSPR_TRY(ctx, w.tgt_pos.ensure(m.N));
+    LSPR_TRY(ctx, w.src_tblock.ensure(m.Ns));
     ++ctx->n_launches;
     natural_order_kernel<<<grid_for(m.Ns, 256), 256, 0, st>>>(m.N, m.K, m.src_pos64.p, m.src_nrm64.p, m.tgt64.p,
                                                               w.spos64.p, w.snrm64.p, w.spos32.p, w.snrm32.p,
-                                                              w.tgt64.p, w.tgt32.p, w.src_panel.p, w.tgt_panel.p);
+                                                              w.tgt64.p, w.tgt32.p, w.src_panel.p, w.tgt_panel.p,
+                                                              w.tgt_pos.p, w.src_tblock.p);
     LSPR_TRY(ctx, cudaGetLastError());
     // direct-mode work items: every target block against source chunks
     const int64_t ntb = (m.N + kTargetBlock - 1) / kTargetBlock;
-    const int64_t chunk = 2048;
+    const int64_t chunk = 512;
     const int64_t nch = (m.Ns + chunk - 1) / chunk;
     std::vector<int4> items;
     items.reserve(ntb * nch);
@@ -579,6 +585,7 @@ int workorder_natural(lspr_ctx *ctx) {
     LSPR_TRY(ctx, ctx->direct.items.ensure(items.size()));
     LSPR_TRY(ctx, cudaMemcpyAsync(ctx->direct.items.p, items.data(), sizeof(int4) * items.size(),
                                   cudaMemcpyHostToDevice, ctx->stream));
+    LSPR_TRY_ST(launch_item_flags(ctx, ctx->direct.items.p, ctx->direct.n));
     LSPR_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return LSPR_OK;
 }

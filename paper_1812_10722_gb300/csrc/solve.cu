@@ -88,14 +88,23 @@ static int far_part(lspr_ctx *ctx, int mode, const double2 *x) {
     const int64_t N = ctx->mesh.N;
     if (tree && !ctx->tree.ready) return LSPR_E_STATE;
     LSPR_TRY(ctx, ctx->acc.ensure(4 * N));
+    LSPR_TRY(ctx, ctx->counters.ensure(8));
     LSPR_TRY(ctx, cudaMemsetAsync(ctx->acc.p, 0, sizeof(double) * 4 * N, ctx->stream));
+    LSPR_TRY(ctx, cudaMemsetAsync(ctx->counters.p, 0, sizeof(int) * 8, ctx->stream));
     LSPR_TRY_ST(launch_weights(ctx, fp64, x, N));
     if (tree) {
+        // P2P on the side stream overlaps P2M -> M2P on the main stream; both add into acc
+        LSPR_TRY(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
+        LSPR_TRY(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+        LSPR_TRY_ST(launch_p2p(ctx, fp64, ctx->tree.p2p_items.p, ctx->tree.n_p2p_items, ctx->acc.p, ctx->side,
+                               ctx->counters.p));
+        LSPR_TRY(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
         LSPR_TRY_ST(launch_p2m(ctx, fp64));
-        LSPR_TRY_ST(launch_p2p(ctx, fp64, ctx->tree.p2p_items.p, ctx->tree.n_p2p_items, ctx->acc.p));
-        LSPR_TRY_ST(launch_m2p(ctx, fp64, ctx->acc.p));
+        LSPR_TRY_ST(launch_m2p(ctx, fp64, ctx->acc.p, ctx->counters.p + 1));
+        LSPR_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     } else {
-        LSPR_TRY_ST(launch_p2p(ctx, fp64, ctx->direct.items.p, ctx->direct.n, ctx->acc.p));
+        LSPR_TRY_ST(launch_p2p(ctx, fp64, ctx->direct.items.p, ctx->direct.n, ctx->acc.p, ctx->stream,
+                               ctx->counters.p));
     }
     ++ctx->matvec_count;
     return LSPR_OK;
@@ -229,38 +238,54 @@ __global__ void scale_kernel(int B, int64_t n2, const double2 *w, int64_t wstrid
     v[b * vstride + k] = d > 0 ? cscale(w[b * wstride + k], 1.0 / d) : make_double2(0, 0);
 }
 
-// apply the previous rotations to column j, build rotation j, update g; resid[b] = |g_{j+1}|
+// apply the previous rotations to column j, build rotation j, update g; resid[b] = |g_{j+1}|.
+// One block per system: the column and the rotations are staged in shared memory and
+// one thread applies the (sequential) rotations.
+constexpr int kMaxRestart = 512;
 __global__ void givens_kernel(int B, int m, int j, double2 *H, const double *hn, double2 *cs, double2 *sn, double2 *g,
                               double *resid, const int *active) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double2 col[kMaxRestart + 1], c[kMaxRestart], s[kMaxRestart];
+    const int b = blockIdx.x;
     if (b >= B || (active && !active[b])) return;
     double2 *Hb = H + (int64_t)b * (m + 1) * m;
-    double2 *c = cs + (int64_t)b * m, *s = sn + (int64_t)b * m, *gb = g + (int64_t)b * (m + 1);
-    Hb[(j + 1) * m + j] = make_double2(hn[b], 0.0);
-    for (int i = 0; i < j; ++i) {
-        const double2 a = Hb[i * m + j], d = Hb[(i + 1) * m + j];
-        Hb[i * m + j] = cadd(cmul(c[i], a), cmul(s[i], d));
-        const double2 sc = make_double2(-s[i].x, s[i].y);   // -conj(s)
-        Hb[(i + 1) * m + j] = cadd(cmul(sc, a), cmul(c[i], d));
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        col[i] = Hb[i * m + j];
+        if (i < j) {
+            c[i] = cs[(int64_t)b * m + i];
+            s[i] = sn[(int64_t)b * m + i];
+        }
     }
-    const double2 a = Hb[j * m + j];
-    const double2 d = Hb[(j + 1) * m + j];
-    const double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(d));
-    const double t = sqrt(aa * aa + bb * bb);
-    if (aa == 0.0) {
-        c[j] = make_double2(0, 0);
-        s[j] = make_double2(1, 0);
-    } else {
-        c[j] = make_double2(aa / t, 0);
-        const double2 ph = cscale(a, 1.0 / aa);
-        s[j] = cscale(cmul(ph, make_double2(d.x, -d.y)), 1.0 / t);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        col[j + 1] = make_double2(hn[b], 0.0);
+        for (int i = 0; i < j; ++i) {
+            const double2 a = col[i], d = col[i + 1];
+            col[i] = cadd(cmul(c[i], a), cmul(s[i], d));
+            col[i + 1] = cadd(cmul(make_double2(-s[i].x, s[i].y), a), cmul(c[i], d));   // -conj(s)
+        }
+        const double2 a = col[j], d = col[j + 1];
+        const double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(d));
+        const double t = sqrt(aa * aa + bb * bb);
+        double2 cj, sj;
+        if (aa == 0.0) {
+            cj = make_double2(0, 0);
+            sj = make_double2(1, 0);
+        } else {
+            cj = make_double2(aa / t, 0);
+            sj = cscale(cmul(cscale(a, 1.0 / aa), make_double2(d.x, -d.y)), 1.0 / t);
+        }
+        col[j] = cadd(cmul(cj, a), cmul(sj, d));
+        col[j + 1] = make_double2(0, 0);
+        cs[(int64_t)b * m + j] = cj;
+        sn[(int64_t)b * m + j] = sj;
+        double2 *gb = g + (int64_t)b * (m + 1);
+        const double2 gj = gb[j];
+        gb[j + 1] = cmul(make_double2(-sj.x, sj.y), gj);
+        gb[j] = cmul(cj, gj);
+        resid[b] = sqrt(cabs2(gb[j + 1]));
     }
-    Hb[j * m + j] = cadd(cmul(c[j], a), cmul(s[j], d));
-    Hb[(j + 1) * m + j] = make_double2(0, 0);
-    const double2 gj = gb[j];
-    gb[j + 1] = cmul(make_double2(-s[j].x, s[j].y), gj);
-    gb[j] = cmul(c[j], gj);
-    resid[b] = sqrt(cabs2(gb[j + 1]));
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hb[i * m + j] = col[i];
 }
 
 // back substitution H y = g for the first jb[b] columns
@@ -472,7 +497,7 @@ static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, doubl
             ++ctx->n_launches;
             scale_kernel<<<gv, 256, 0, st>>>(B, n2, w, n2, V + (int64_t)(j + 1) * n2, vstride, nrm, active);
             ++ctx->n_launches;
-            givens_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, m, j, ctx->gm_H.p, nrm, ctx->gm_cs.p, ctx->gm_sn.p,
+            givens_kernel<<<B, 64, 0, st>>>(B, m, j, ctx->gm_H.p, nrm, ctx->gm_cs.p, ctx->gm_sn.p,
                                                           ctx->gm_g.p, resid, active);
             timer_end(ctx, T_GMRES, ev);
             LSPR_TRY(ctx, cudaGetLastError());
@@ -559,7 +584,7 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
 
     std::vector<int> iters(B, 0);
     std::vector<double> relres(B, 1.0);
-    const int m = std::max(1, std::min(o.restart, 512));
+    const int m = std::max(1, std::min(o.restart, kMaxRestart));
     const bool refine = o.refine && (mode == LSPR_TREE_FP32 || mode == LSPR_DIRECT_FP32);
     if (!refine) {
         LSPR_TRY_ST(gmres_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p, iters, relres,

@@ -21,7 +21,7 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kDigitBits = 4;
 constexpr int kDigits = 1 << kDigitBits;
-constexpr int kP2PChunk = 1024;     // sources per P2P work item (upper bound)
+constexpr int kP2PChunk = 256;      // sources per P2P work item (upper bound)
 constexpr int kM2PSeg = 16;         // boxes per M2P work item
 constexpr int kP2MChunk = 512;      // sources per P2M work item
 constexpr int kStack = 96;
@@ -209,7 +209,7 @@ __global__ void permute_sources_kernel(int64_t Ns, const int *__restrict__ perm,
 }
 
 __global__ void permute_targets_kernel(int64_t N, const int *__restrict__ perm, const dbl4 *__restrict__ tgt,
-                                       dbl4 *tgt64, float4 *tgt32, int *tgt_panel) {
+                                       dbl4 *tgt64, float4 *tgt32, int *tgt_panel, int *tgt_pos) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int o = perm[i];
@@ -217,6 +217,14 @@ __global__ void permute_targets_kernel(int64_t N, const int *__restrict__ perm, 
     tgt64[i] = t;
     tgt32[i] = make_float4((float)t.x, (float)t.y, (float)t.z, __int_as_float(o));
     tgt_panel[i] = o;
+    tgt_pos[o] = (int)i;
+}
+
+__global__ void src_tblock_kernel(int64_t Ns, const int *__restrict__ src_panel, const int *__restrict__ tgt_pos,
+                                  int *src_tblock) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= Ns) return;
+    src_tblock[s] = tgt_pos[src_panel[s]] / kTargetBlock;
 }
 
 // --------------------------------------------------------------------- octree
@@ -509,13 +517,16 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     LSPR_TRY(ctx, w.tgt64.ensure(N));
     LSPR_TRY(ctx, w.tgt32.ensure(N));
     LSPR_TRY(ctx, w.tgt_panel.ensure(N));
+    LSPR_TRY(ctx, w.tgt_pos.ensure(N));
+    LSPR_TRY(ctx, w.src_tblock.ensure(Ns));
 
     // targets first (their sorted keys are not kept)
     ++ctx->n_launches;
     morton_kernel<<<grid_for(N, 256), 256, 0, st>>>(m.tgt64.p, N, cube.p, keys.p, vals.p);
     LSPR_TRY_ST(radix_sort(ctx, keys.p, vals.p, ktmp.p, vtmp.p, N, 30, hist.p, offs.p));
     ++ctx->n_launches;
-    permute_targets_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, vals.p, m.tgt64.p, w.tgt64.p, w.tgt32.p, w.tgt_panel.p);
+    permute_targets_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, vals.p, m.tgt64.p, w.tgt64.p, w.tgt32.p, w.tgt_panel.p,
+                                                              w.tgt_pos.p);
     // sources
     ++ctx->n_launches;
     morton_kernel<<<grid_for(Ns, 256), 256, 0, st>>>(m.src_pos64.p, Ns, cube.p, keys.p, vals.p);
@@ -523,7 +534,11 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     ++ctx->n_launches;
     permute_sources_kernel<<<grid_for(Ns, 256), 256, 0, st>>>(Ns, vals.p, m.src_pos64.p, m.src_nrm64.p, w.spos64.p,
                                                               w.snrm64.p, w.spos32.p, w.snrm32.p, w.src_panel.p);
+    ++ctx->n_launches;
+    src_tblock_kernel<<<grid_for(Ns, 256), 256, 0, st>>>(Ns, w.src_panel.p, w.tgt_pos.p, w.src_tblock.p);
     LSPR_TRY(ctx, cudaGetLastError());
+    // the direct-mode items now address the Morton work order: refresh their own-panel flags
+    LSPR_TRY_ST(launch_item_flags(ctx, ctx->direct.items.p, ctx->direct.n));
 
     // octree
     const int64_t cap64 = 1 + 8LL * kMaxDepth * (Ns / (Ncrit + 1) + 1);
@@ -609,6 +624,7 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
         nullptr, nullptr, nullptr, off3.p, off3.p + ntb, off3.p + 2 * ntb, tr.p2p_items.p, tr.m2p_list.p,
         tr.m2p_items.p, tr.box_used.p, pairs.p, ovf.p);
     LSPR_TRY(ctx, cudaGetLastError());
+    LSPR_TRY_ST(launch_item_flags(ctx, tr.p2p_items.p, tr.n_p2p_items));
 
     // P2M work items over the used boxes (host side: a few thousand boxes)
     std::vector<int> hbeg(nboxes), hend(nboxes), hused(nboxes);

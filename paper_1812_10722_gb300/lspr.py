@@ -29,9 +29,10 @@ _lib = None
 
 
 class LsprError(RuntimeError):
-    def __init__(self, status: int, where: str):
+    def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
-        super().__init__(f"{where}: {STATUS.get(status, status)} ({lib().lspr_status_string(status).decode()})")
+        msg = f"{where}: {STATUS.get(status, status)} ({lib().lspr_status_string(status).decode()})"
+        super().__init__(msg + (f": {detail}" if detail else ""))
 
 
 class QuadOpts(ctypes.Structure):
@@ -67,6 +68,8 @@ def lib():
             L.lspr_status_string.argtypes = [ctypes.c_int]
             L.lspr_status_string.restype = ctypes.c_char_p
             L.lspr_version.restype = ctypes.c_char_p
+            L.lspr_last_error.argtypes = [_vp]
+            L.lspr_last_error.restype = ctypes.c_char_p
             L.lspr_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, _vp]
             L.lspr_destroy.argtypes = [_vp]
             L.lspr_mesh_upload.argtypes = [_vp, _vp, _i64, _vp, _i64, _vp, _i32, ctypes.POINTER(QuadOpts), _i32]
@@ -85,9 +88,10 @@ def lib():
     return _lib
 
 
-def _check(rc: int, where: str):
+def _check(rc: int, where: str, handle=None):
     if rc != 0:
-        raise LsprError(rc, where)
+        detail = lib().lspr_last_error(handle).decode() if handle else ""
+        raise LsprError(rc, where, detail)
 
 
 def _is_torch(a) -> bool:
@@ -160,11 +164,11 @@ class Context:
             rc = lib().lspr_mesh_upload(self._h, _host_ptr(v), len(v), _host_ptr(t), len(t),
                                         None if sid is None else _host_ptr(sid), nsurf, ctypes.byref(q), 0)
             n = len(t)
-        _check(rc, "lspr_mesh_upload")
+        _check(rc, "lspr_mesh_upload", self._h)
         self.n = int(n)
 
     def tree_build(self, theta=0.5, P=6, Ncrit=300):
-        _check(lib().lspr_tree_build(self._h, float(theta), int(P), int(Ncrit)), "lspr_tree_build")
+        _check(lib().lspr_tree_build(self._h, float(theta), int(P), int(Ncrit)), "lspr_tree_build", self._h)
 
     # ---------------------------------------------------------------- matvec
     def matvec(self, x, eps_ratio, mode="direct_fp64"):
@@ -180,7 +184,7 @@ class Context:
             y = torch.empty_like(xx)
             rc = lib().lspr_matvec(self._h, ctypes.c_void_p(xx.data_ptr()), ctypes.c_void_p(y.data_ptr()), B,
                                    ctypes.c_void_p(s.data_ptr()), m, 1)
-            _check(rc, "lspr_matvec")
+            _check(rc, "lspr_matvec", self._h)
             return y[0] if squeeze else y
         x = np.ascontiguousarray(x, dtype=np.complex128)
         squeeze = x.ndim == 1
@@ -188,7 +192,7 @@ class Context:
         B = xx.shape[0]
         s = np.ascontiguousarray(np.broadcast_to(np.asarray(eps_ratio, np.complex128), (B,)))
         y = np.zeros_like(xx)
-        _check(lib().lspr_matvec(self._h, _host_ptr(xx), _host_ptr(y), B, _host_ptr(s), m, 0), "lspr_matvec")
+        _check(lib().lspr_matvec(self._h, _host_ptr(xx), _host_ptr(y), B, _host_ptr(s), m, 0), "lspr_matvec", self._h)
         return y[0] if squeeze else y
 
     # ----------------------------------------------------------------- solve
@@ -212,28 +216,28 @@ class Context:
         rc = lib().lspr_solve(self._h, _host_ptr(e), eo.real, eo.imag, _host_ptr(E), _host_ptr(lam), B,
                               ctypes.byref(o), _host_ptr(dip), _host_ptr(sig), ctypes.byref(st))
         if rc not in (0, 5) or (check and rc != 0):
-            _check(rc, "lspr_solve")
+            _check(rc, "lspr_solve", self._h)
         return SolveResult(dip, sig, it, rr, stt, st.seconds, st.matvecs)
 
     # ------------------------------------------------------------------ info
     def info(self) -> dict:
         vals = [ctypes.c_int64() for _ in range(7)]
-        _check(lib().lspr_get_info(self._h, *[ctypes.byref(v) for v in vals]), "lspr_get_info")
+        _check(lib().lspr_get_info(self._h, *[ctypes.byref(v) for v in vals]), "lspr_get_info", self._h)
         keys = ["n_panels", "n_sources", "n_near", "n_boxes", "n_p2p_items", "n_m2p_pairs", "n_p2p_pairs"]
         return {k: v.value for k, v in zip(keys, vals)}
 
     def launch_count(self) -> int:
         n = ctypes.c_int64(0)
-        _check(lib().lspr_launch_count(self._h, ctypes.byref(n)), "lspr_launch_count")
+        _check(lib().lspr_launch_count(self._h, ctypes.byref(n)), "lspr_launch_count", self._h)
         return n.value
 
     def set_timing(self, enable: bool):
-        _check(lib().lspr_set_timing(self._h, int(bool(enable))), "lspr_set_timing")
+        _check(lib().lspr_set_timing(self._h, int(bool(enable))), "lspr_set_timing", self._h)
 
     def timing(self) -> dict:
         ms = np.zeros(12)
         n = np.zeros(12, np.int64)
-        _check(lib().lspr_get_timing(self._h, _host_ptr(ms), _host_ptr(n)), "lspr_get_timing")
+        _check(lib().lspr_get_timing(self._h, _host_ptr(ms), _host_ptr(n)), "lspr_get_timing", self._h)
         names = ["p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh", "other", "p2p_fp64", "m2p_fp64",
                  "p2m_fp64", "weights"]
         return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}
