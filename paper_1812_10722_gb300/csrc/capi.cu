@@ -130,6 +130,7 @@ int lspr_destroy(lspr_ctx *c) {
                          &c->tree.box_nchild, &c->tree.box_level, &c->tree.box_used, &c->tree.m2p_list, &c->gm_active})
         a->release();
     c->tree.box_key.release();
+    c->tree.box_parent.release();
     for (DArr<int4> *a : {&c->tree.p2p_items, &c->tree.m2p_items, &c->tree.p2m_items, &c->direct.items}) a->release();
     for (DArr<double2> *a : {&c->xbuf, &c->ybuf, &c->sbuf, &c->gm_V, &c->gm_w, &c->gm_z, &c->gm_x, &c->gm_b, &c->gm_r,
                              &c->gm_H, &c->gm_cs, &c->gm_sn, &c->gm_g, &c->gm_y, &c->gm_h, &c->gm_part, &c->gm_s,

@@ -8,7 +8,8 @@
 // two real channels (the paper's real/imaginary split of the treecode work).
 //
 //   p2p_kernel  direct sums of a 64-target block against a contiguous source range
-//   p2m_kernel  Cartesian Taylor moments of a box about its centre c:
+//   p2m_kernel  Cartesian Taylor moments of a leaf about its centre c, shifted into
+//               every accepted ancestor box:
 //                 M^V_k = sum_j q_j (c - y_j)^k
 //                 M^K_k = sum_j mu_j * (-sum_d n_{j,d} k_d (c - y_j)^(k - e_d))
 //   m2p_kernel  Vd_i += sum_{|k|<=P} a_k(x_i - c) M^V_k (same for K), with
@@ -30,7 +31,14 @@ template <> struct Vec4<double> { using type = dbl4; };
 __device__ __forceinline__ int panel_of(float w) { return __float_as_int(w); }
 __device__ __forceinline__ int panel_of(double w) { return (int)w; }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+// FP64 1/sqrt(x): the FP32 reciprocal square root as the seed and one Newton-Raphson
+// step y <- y + y (1 - x y^2) / 2; a seed error e leaves ~1.5 e^2 (~2e-14 relative).
+// Used for squared distances, which stay far inside the FP32 range.
+__device__ __forceinline__ double rsq(double x) {
+    const double y = (double)rsqrtf((float)x);
+    const double h = fma(-x * y, y, 1.0);
+    return fma(0.5 * y, h, y);
+}
 
 // ----------------------------------------------------------------- weights
 template <typename T4>
@@ -285,13 +293,22 @@ __global__ void __launch_bounds__(kM2PWarps * 32) m2p_kernel(const int4 *__restr
 // --------------------------------------------------------------------- P2M
 constexpr int kP2MTile = 32;
 
+// binomial coefficients C(n, r), n, r <= kMaxP
+__constant__ float c_binom[kMaxP + 1][kMaxP + 1] = {
+    {1, 0, 0, 0, 0, 0, 0, 0, 0},     {1, 1, 0, 0, 0, 0, 0, 0, 0},     {1, 2, 1, 0, 0, 0, 0, 0, 0},
+    {1, 3, 3, 1, 0, 0, 0, 0, 0},     {1, 4, 6, 4, 1, 0, 0, 0, 0},     {1, 5, 10, 10, 5, 1, 0, 0, 0},
+    {1, 6, 15, 20, 15, 6, 1, 0, 0},  {1, 7, 21, 35, 35, 21, 7, 1, 0}, {1, 8, 28, 56, 70, 56, 28, 8, 1}};
+
 template <typename T, int P>
 __global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, const typename Vec4<T>::type *__restrict__ spos,
                            const typename Vec4<T>::type *__restrict__ snrm, const typename Vec4<T>::type *__restrict__ sw,
-                           const typename Vec4<T>::type *__restrict__ box_c, typename Vec4<T>::type *__restrict__ mom) {
+                           const typename Vec4<T>::type *__restrict__ box_c, const int *__restrict__ parent,
+                           const int *__restrict__ used, typename Vec4<T>::type *__restrict__ mom) {
     using T4 = typename Vec4<T>::type;
     constexpr int NT = n_terms(P);
     __shared__ T pw[kP2MTile][3][P + 1];
+    __shared__ T4 lm[NT];
+    __shared__ T dpw[3][P + 1];
     __shared__ T4 shn[kP2MTile], shw[kP2MTile];
     const int64_t it = blockIdx.x;
     if (it >= nitems) return;
@@ -346,12 +363,54 @@ __global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, const
             }
         }
     }
+    // the chunk's moments about its leaf centre: added to the leaf if it is accepted by some
+    // target block, and shifted into every accepted ancestor (upward pass folded in):
+    //   M_k(a) = sum_{l <= k} C(k, l) (a - c)^(k - l) M_l(c),  C(k, l) = prod_d binom(k_d, l_d),
+    // valid for both moment kinds since (a - y)^k = ((a - c) + (c - y))^k.
     if (t < NT) {
-        T *o = (T *)(mom + (int64_t)item.x * NT + t);
-        atomicAdd(o + 0, vr);
-        atomicAdd(o + 1, vi);
-        atomicAdd(o + 2, kr);
-        atomicAdd(o + 3, ki);
+        T4 o;
+        o.x = vr; o.y = vi; o.z = kr; o.w = ki;
+        lm[t] = o;
+        if (used[item.x]) {
+            T *g = (T *)(mom + (int64_t)item.x * NT + t);
+            atomicAdd(g + 0, vr);
+            atomicAdd(g + 1, vi);
+            atomicAdd(g + 2, kr);
+            atomicAdd(g + 3, ki);
+        }
+    }
+    for (int A = parent[item.x]; A >= 0; A = parent[A]) {
+        if (!used[A]) continue;
+        __syncthreads();
+        if (t < 3) {
+            const T4 ca = box_c[A];
+            const T delta = t == 0 ? ca.x - c.x : (t == 1 ? ca.y - c.y : ca.z - c.z);
+            T v = 1;
+            for (int e = 0; e <= P; ++e) {
+                dpw[t][e] = v;
+                v *= delta;
+            }
+        }
+        __syncthreads();
+        if (t < NT) {
+            T sr = 0, si = 0, skr = 0, ski = 0;
+            for (int l1 = 0; l1 <= k1; ++l1)
+                for (int l2 = 0; l2 <= k2; ++l2)
+                    for (int l3 = 0; l3 <= k3; ++l3) {
+                        const T coef = T(c_binom[k1][l1] * c_binom[k2][l2] * c_binom[k3][l3]) * dpw[0][k1 - l1] *
+                                       dpw[1][k2 - l2] * dpw[2][k3 - l3];
+                        const T4 m = lm[mi_index(l1, l2, l3)];
+                        sr += coef * m.x;
+                        si += coef * m.y;
+                        skr += coef * m.z;
+                        ski += coef * m.w;
+                    }
+            T *g = (T *)(mom + (int64_t)A * NT + t);
+            atomicAdd(g + 0, sr);
+            atomicAdd(g + 1, si);
+            atomicAdd(g + 2, skr);
+            atomicAdd(g + 3, ski);
+        }
     }
 }
 
@@ -436,7 +495,7 @@ static void p2m_launch(lspr_ctx *ctx) {
     }
     ++ctx->n_launches;
     p2m_kernel<T, P><<<(unsigned)tr.n_p2m_items, threads, 0, ctx->stream>>>(tr.p2m_items.p, tr.n_p2m_items, spos, snrm,
-                                                                           w, bc, mom);
+                                                                           w, bc, tr.box_parent.p, tr.box_used.p, mom);
 }
 
 template <typename T, int P>

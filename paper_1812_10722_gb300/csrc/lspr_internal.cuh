@@ -104,7 +104,8 @@ struct Tree {
     DArr<int4> p2p_items;    // (target block, source begin, source end, 0)
     DArr<int4> m2p_items;    // (target block, list begin, list end, 0)
     DArr<int> m2p_list;      // box ids
-    DArr<int4> p2m_items;    // (box, source begin, source end, 0)
+    DArr<int4> p2m_items;    // (leaf, source begin, source end, 0): leaves under an accepted box
+    DArr<int> box_parent;    // parent box (-1 for the root)
     // moments [box][NT] x (Vre, Vim, Kre, Kim)
     DArr<float4> mom32;
     DArr<dbl4> mom64;

@@ -278,43 +278,59 @@ __device__ __forceinline__ int lower_bound_u(const unsigned *a, int n, unsigned 
     return lo;
 }
 
+// One warp per target: lane c < 27 searches neighbour cell c and tests its panels; the
+// row is laid out as the self entry, then the hits of cell 0, 1, ... in sorted order.
 template <bool FILL>
 __global__ void near_cells_kernel(int64_t N, const double *__restrict__ cx, const double *__restrict__ cy,
                                   const double *__restrict__ cz, const double *__restrict__ L, double thr,
                                   const double *grid, const unsigned *__restrict__ skeys, const int *__restrict__ sidx,
                                   int64_t *count, const int64_t *ptr, int *col, int *row) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= N) return;
     const double xi = cx[i], yi = cy[i], zi = cz[i];
     const int ix = cell_coord(xi, grid[0], grid[3]), iy = cell_coord(yi, grid[1], grid[3]),
               iz = cell_coord(zi, grid[2], grid[3]);
-    int64_t out = 0, c = 0;
-    if (FILL) {
-        out = ptr[i];
+    int k0 = 0, k1 = 0;
+    if (lane < 27) {
+        const int qx = ix + lane % 3 - 1, qy = iy + (lane / 3) % 3 - 1, qz = iz + lane / 9 - 1;
+        if (qx >= 0 && qy >= 0 && qz >= 0 && qx <= 1023 && qy <= 1023 && qz <= 1023) {
+            const unsigned key = cell_key(qx, qy, qz);
+            k0 = lower_bound_u(skeys, (int)N, key);
+            k1 = k0;
+            while (k1 < N && skeys[k1] == key) ++k1;
+        }
+    }
+    int c = 0;
+    for (int k = k0; k < k1; ++k) {
+        const int j = sidx[k];
+        c += (j != i && near_exact(xi, yi, zi, cx[j], cy[j], cz[j], L[j], thr));
+    }
+    // inclusive warp scan of the per-lane hit counts
+    int inc = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    if (!FILL) {
+        if (lane == 0) count[i] = total + 1;
+        return;
+    }
+    int64_t out = ptr[i];
+    if (lane == 0) {
         col[out] = (int)i;   // self entry first
         row[out] = (int)i;
-        ++out;
     }
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int qx = ix + dx, qy = iy + dy, qz = iz + dz;
-                if (qx < 0 || qy < 0 || qz < 0 || qx > 1023 || qy > 1023 || qz > 1023) continue;
-                const unsigned key = cell_key(qx, qy, qz);
-                int k = lower_bound_u(skeys, (int)N, key);
-                for (; k < N && skeys[k] == key; ++k) {
-                    const int j = sidx[k];
-                    if (j == i || !near_exact(xi, yi, zi, cx[j], cy[j], cz[j], L[j], thr)) continue;
-                    if (FILL) {
-                        col[out] = j;
-                        row[out] = (int)i;
-                        ++out;
-                    } else {
-                        ++c;
-                    }
-                }
-            }
-    if (!FILL) count[i] = c + 1;
+    out += 1 + (inc - c);
+    for (int k = k0; k < k1; ++k) {
+        const int j = sidx[k];
+        if (j != i && near_exact(xi, yi, zi, cx[j], cy[j], cz[j], L[j], thr)) {
+            col[out] = j;
+            row[out] = (int)i;
+            ++out;
+        }
+    }
 }
 
 // exclusive scan of n int64 counts into ptr[0..n], single block
@@ -520,7 +536,7 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     cell_key_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, grid.p, keys.p, vals.p);
     LSPR_TRY_ST(radix_sort(ctx, keys.p, vals.p, ktmp.p, vtmp.p, N, 30, hist.p, offs.p));
     ++ctx->n_launches;
-    near_cells_kernel<false><<<grid_for(N, 128), 128, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, grid.p,
+    near_cells_kernel<false><<<grid_for(N * 32, 128), 128, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, grid.p,
                                                                keys.p, vals.p, cnt.p, nullptr, nullptr, nullptr);
     ++ctx->n_launches;
     scan_kernel<<<1, 1024, 0, st>>>(cnt.p, N, m.near_ptr.p);
@@ -533,7 +549,7 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     DArr<int> rowidx;
     LSPR_TRY(ctx, rowidx.ensure(m.nnz));
     ++ctx->n_launches;
-    near_cells_kernel<true><<<grid_for(N, 128), 128, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, grid.p,
+    near_cells_kernel<true><<<grid_for(N * 32, 128), 128, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, grid.p,
                                                               keys.p, vals.p, nullptr, m.near_ptr.p, m.near_col.p,
                                                               rowidx.p);
     ++ctx->n_launches;
@@ -550,6 +566,14 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     grid.release();
     m.ready = true;
     return workorder_natural(ctx);
+}
+
+// item i = (target block i mod ntb, source chunk i / ntb): consecutive warps share a chunk
+__global__ void direct_items_kernel(int4 *items, int64_t ntb, int64_t nch, int64_t chunk, int64_t Ns) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ntb * nch) return;
+    const int64_t c = i / ntb, tb = i - c * ntb;
+    items[i] = make_int4((int)tb, (int)(c * chunk), (int)min(Ns, (c + 1) * chunk), 0);
 }
 
 int workorder_natural(lspr_ctx *ctx) {
@@ -576,15 +600,10 @@ int workorder_natural(lspr_ctx *ctx) {
     const int64_t ntb = (m.N + kTargetBlock - 1) / kTargetBlock;
     const int64_t chunk = 512;
     const int64_t nch = (m.Ns + chunk - 1) / chunk;
-    std::vector<int4> items;
-    items.reserve(ntb * nch);
-    for (int64_t c = 0; c < nch; ++c)
-        for (int64_t tb = 0; tb < ntb; ++tb)
-            items.push_back(make_int4((int)tb, (int)(c * chunk), (int)std::min(m.Ns, (c + 1) * chunk), 0));
-    ctx->direct.n = (int64_t)items.size();
-    LSPR_TRY(ctx, ctx->direct.items.ensure(items.size()));
-    LSPR_TRY(ctx, cudaMemcpyAsync(ctx->direct.items.p, items.data(), sizeof(int4) * items.size(),
-                                  cudaMemcpyHostToDevice, ctx->stream));
+    ctx->direct.n = ntb * nch;
+    LSPR_TRY(ctx, ctx->direct.items.ensure(ctx->direct.n));
+    ++ctx->n_launches;
+    direct_items_kernel<<<grid_for(ctx->direct.n, 256), 256, 0, st>>>(ctx->direct.items.p, ntb, nch, chunk, m.Ns);
     LSPR_TRY_ST(launch_item_flags(ctx, ctx->direct.items.p, ctx->direct.n));
     LSPR_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return LSPR_OK;

@@ -42,33 +42,37 @@ __device__ __forceinline__ double2 csqrt_p(double2 z) {
 
 // ------------------------------------------------------------------ assembly
 // RAW = true writes the layer potentials (V dphi, K phi) instead of the block rows.
+// kRowLanes lanes per row read the row's near entries coalesced (rows hold ~25 entries).
+constexpr int kRowLanes = 8;
 template <bool RAW>
 __global__ void assemble_kernel(int64_t N, const double *__restrict__ acc, const int64_t *__restrict__ ptr,
                                 const int *__restrict__ col, const double *__restrict__ dV,
                                 const double *__restrict__ dK, const double2 *__restrict__ x, const double2 *s,
                                 double2 *y, double2 *Vd, double2 *Kp) {
-    // one warp per row: the row's near entries are read coalesced
-    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (i >= N) return;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = g / kRowLanes;
+    const int lane = (int)(g % kRowLanes);
+    const bool valid = i < N;
     double vr = 0, vi = 0, kr = 0, ki = 0;
-    for (int64_t e = ptr[i] + lane; e < ptr[i + 1]; e += 32) {
-        const int j = col[e];
-        const double a = dV[e], b = dK[e];
-        const double2 ph = x[j], dp = x[N + j];
-        vr += a * dp.x;
-        vi += a * dp.y;
-        kr += b * ph.x;
-        ki += b * ph.y;
+    if (valid) {
+        for (int64_t e = ptr[i] + lane; e < ptr[i + 1]; e += kRowLanes) {
+            const int j = col[e];
+            const double a = dV[e], b = dK[e];
+            const double2 ph = x[j], dp = x[N + j];
+            vr += a * dp.x;
+            vi += a * dp.y;
+            kr += b * ph.x;
+            ki += b * ph.y;
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        vr += __shfl_xor_sync(0xffffffffu, vr, o);
-        vi += __shfl_xor_sync(0xffffffffu, vi, o);
-        kr += __shfl_xor_sync(0xffffffffu, kr, o);
-        ki += __shfl_xor_sync(0xffffffffu, ki, o);
+    for (int o = kRowLanes / 2; o > 0; o >>= 1) {
+        vr += __shfl_xor_sync(0xffffffffu, vr, o, kRowLanes);
+        vi += __shfl_xor_sync(0xffffffffu, vi, o, kRowLanes);
+        kr += __shfl_xor_sync(0xffffffffu, kr, o, kRowLanes);
+        ki += __shfl_xor_sync(0xffffffffu, ki, o, kRowLanes);
     }
-    if (lane != 0) return;
+    if (!valid || lane != 0) return;
     const double2 V = make_double2(acc[4 * i] + vr, acc[4 * i + 1] + vi);
     const double2 K = make_double2(acc[4 * i + 2] + kr, acc[4 * i + 3] + ki);
     if (RAW) {
@@ -118,7 +122,7 @@ int apply_operator(lspr_ctx *ctx, int mode, const double2 *x, double2 *y, const 
         cudaEvent_t ev;
         timer_begin(ctx, T_NEAR, &ev);
         ++ctx->n_launches;
-        assemble_kernel<false><<<grid_for(N * 32, 256), 256, 0, ctx->stream>>>(
+        assemble_kernel<false><<<grid_for(N * kRowLanes, 256), 256, 0, ctx->stream>>>(
             N, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x + (size_t)b * 2 * N, s + b,
             y + (size_t)b * 2 * N, nullptr, nullptr);
         timer_end(ctx, T_NEAR, ev);
@@ -131,7 +135,7 @@ int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, dou
     const Mesh &m = ctx->mesh;
     LSPR_TRY_ST(far_part(ctx, mode, x));
     ++ctx->n_launches;
-    assemble_kernel<true><<<grid_for(m.N * 32, 256), 256, 0, ctx->stream>>>(
+    assemble_kernel<true><<<grid_for(m.N * kRowLanes, 256), 256, 0, ctx->stream>>>(
         m.N, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr, nullptr, Vd, Kp);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
@@ -139,7 +143,7 @@ int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, dou
 
 // --------------------------------------------------------------------- GMRES
 constexpr int kRedThreads = 256;
-constexpr int kChunk = 4096;   // elements per partial-sum block
+constexpr int kChunk = 1024;   // elements per partial-sum block
 
 // right preconditioner: out = M^-1 in, per panel 2x2 block
 __global__ void precond_kernel(int B, int64_t N, const double *__restrict__ Vself, const double2 *__restrict__ s,

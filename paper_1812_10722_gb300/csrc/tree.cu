@@ -25,31 +25,42 @@ constexpr int kP2PChunk = 256;      // sources per P2P work item (upper bound)
 constexpr int kM2PSeg = 16;         // boxes per M2P work item
 constexpr int kP2MChunk = 512;      // sources per P2M work item
 constexpr int kStack = 96;
-constexpr int kGeomThreads = 512;   // the root box holds every source
+constexpr int kGeomThreads = 256;
 
 // ------------------------------------------------------------ bounding cube
-__global__ void bbox_kernel(const dbl4 *__restrict__ a, int64_t na, const dbl4 *__restrict__ b, int64_t nb,
-                            double *out /* lo[3], hi[3] */) {
-    __shared__ double lo[3][1024], hi[3][1024];
+// two stages: kBoxBlocks blocks reduce slices of the points into part[block][6], then one
+// block reduces the partials into out = (lo[3], hi[3])
+constexpr int kBoxBlocks = 128;
+__global__ void bbox_partial_kernel(const dbl4 *__restrict__ a, int64_t na, const dbl4 *__restrict__ b, int64_t nb,
+                                    double *part) {
+    __shared__ double red[6][256];
     const int t = threadIdx.x;
     double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
-    for (int64_t i = t; i < na + nb; i += blockDim.x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + t; i < na + nb; i += (int64_t)gridDim.x * blockDim.x) {
         const dbl4 p = i < na ? a[i] : b[i - na];
         l[0] = fmin(l[0], p.x); l[1] = fmin(l[1], p.y); l[2] = fmin(l[2], p.z);
         h[0] = fmax(h[0], p.x); h[1] = fmax(h[1], p.y); h[2] = fmax(h[2], p.z);
     }
-    for (int d = 0; d < 3; ++d) { lo[d][t] = l[d]; hi[d][t] = h[d]; }
+    for (int d = 0; d < 3; ++d) { red[d][t] = l[d]; red[3 + d][t] = h[d]; }
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (t < s)
             for (int d = 0; d < 3; ++d) {
-                lo[d][t] = fmin(lo[d][t], lo[d][t + s]);
-                hi[d][t] = fmax(hi[d][t], hi[d][t + s]);
+                red[d][t] = fmin(red[d][t], red[d][t + s]);
+                red[3 + d][t] = fmax(red[3 + d][t], red[3 + d][t + s]);
             }
         __syncthreads();
     }
     if (t == 0)
-        for (int d = 0; d < 3; ++d) { out[d] = lo[d][0]; out[3 + d] = hi[d][0]; }
+        for (int q = 0; q < 6; ++q) part[blockIdx.x * 6 + q] = red[q][0];
+}
+
+__global__ void bbox_final_kernel(const double *part, int nparts, double *out) {
+    const int q = threadIdx.x;
+    if (q >= 6) return;
+    double v = q < 3 ? 1e300 : -1e300;
+    for (int k = 0; k < nparts; ++k) v = q < 3 ? fmin(v, part[k * 6 + q]) : fmax(v, part[k * 6 + q]);
+    out[q] = v;
 }
 
 // key bit 3l+2 / 3l+1 / 3l = x / y / z bit l, so the top triple selects the octant
@@ -324,51 +335,58 @@ __global__ void __launch_bounds__(1024) octree_kernel(const unsigned *__restrict
     if (threadIdx.x == 0) *out_nboxes = s_overflow ? -1 : s_le;
 }
 
-// centre of the bounding box of the box's sources and r_b = max distance to it
-__global__ void box_geometry_kernel(int nboxes, const int *beg, const int *end, const dbl4 *__restrict__ spos,
+// Centre of the bounding box of the box's sources and r_b = max distance to it, from
+// the FP32 source copies (FP64 min/max would run on the narrow FP64 pipe of a single
+// block for the root).  The radius is enlarged to cover the FP32 rounding of the
+// coordinates (<= 2^-24 |y| each) and of the distance itself, so it bounds the true one.
+__global__ void box_geometry_kernel(int nboxes, const int *beg, const int *end, const float4 *__restrict__ spos,
                                     dbl4 *c64, float4 *c32) {
-    __shared__ double red[6][kGeomThreads];
-    __shared__ double cen[3];
+    __shared__ float red[6][kGeomThreads];
+    __shared__ float cen[3];
     const int b = blockIdx.x;
     if (b >= nboxes) return;
     const int t = threadIdx.x;
-    double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
+    float l[3] = {3e38f, 3e38f, 3e38f}, h[3] = {-3e38f, -3e38f, -3e38f};
     for (int s = beg[b] + t; s < end[b]; s += blockDim.x) {
-        const dbl4 p = spos[s];
-        l[0] = fmin(l[0], p.x); l[1] = fmin(l[1], p.y); l[2] = fmin(l[2], p.z);
-        h[0] = fmax(h[0], p.x); h[1] = fmax(h[1], p.y); h[2] = fmax(h[2], p.z);
+        const float4 p = spos[s];
+        l[0] = fminf(l[0], p.x); l[1] = fminf(l[1], p.y); l[2] = fminf(l[2], p.z);
+        h[0] = fmaxf(h[0], p.x); h[1] = fmaxf(h[1], p.y); h[2] = fmaxf(h[2], p.z);
     }
     for (int d = 0; d < 3; ++d) { red[d][t] = l[d]; red[3 + d][t] = h[d]; }
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (t < s)
             for (int d = 0; d < 3; ++d) {
-                red[d][t] = fmin(red[d][t], red[d][t + s]);
-                red[3 + d][t] = fmax(red[3 + d][t], red[3 + d][t + s]);
+                red[d][t] = fminf(red[d][t], red[d][t + s]);
+                red[3 + d][t] = fmaxf(red[3 + d][t], red[3 + d][t + s]);
             }
         __syncthreads();
     }
     if (t == 0)
-        for (int d = 0; d < 3; ++d) cen[d] = 0.5 * (red[d][0] + red[3 + d][0]);
+        for (int d = 0; d < 3; ++d) cen[d] = 0.5f * (red[d][0] + red[3 + d][0]);
     __syncthreads();
-    double r2 = 0;
+    float r2 = 0.f, ymax = 0.f;
     for (int s = beg[b] + t; s < end[b]; s += blockDim.x) {
-        const dbl4 p = spos[s];
-        const double dx = p.x - cen[0], dy = p.y - cen[1], dz = p.z - cen[2];
-        r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
+        const float4 p = spos[s];
+        const float dx = p.x - cen[0], dy = p.y - cen[1], dz = p.z - cen[2];
+        r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+        ymax = fmaxf(ymax, fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z))));
     }
     __syncthreads();
     red[0][t] = r2;
+    red[1][t] = ymax;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (t < s) red[0][t] = fmax(red[0][t], red[0][t + s]);
+        if (t < s) {
+            red[0][t] = fmaxf(red[0][t], red[0][t + s]);
+            red[1][t] = fmaxf(red[1][t], red[1][t + s]);
+        }
         __syncthreads();
     }
     if (t == 0) {
-        const double rb = sqrt(red[0][0]);
+        const double rb = (double)sqrtf(red[0][0]) * (1.0 + 1e-6) + 4e-7 * (double)red[1][0];
         c64[b] = make_dbl4(cen[0], cen[1], cen[2], rb);
-        // FP32 copy: radius rounded up so the FP32 kernels never see a smaller box
-        c32[b] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)rb * (1.0f + 1e-6f));
+        c32[b] = make_float4(cen[0], cen[1], cen[2], (float)(rb * (1.0 + 1e-6)));
     }
 }
 
@@ -398,48 +416,52 @@ __device__ __forceinline__ bool mac_accept(const dbl4 &c, const dbl4 &lo, const 
     return c.w < theta * r && r - c.w > clear;
 }
 
+// One warp per target block walks the tree depth first.  A popped box is known to be
+// rejected by the MAC: a leaf becomes a direct (P2P) source range, merged with the
+// previous range when contiguous; for an internal box the lanes test its children in
+// parallel, accepted children join the block's M2P list and rejected ones are pushed in
+// reverse octant order, so leaves come out in Morton order.
 // FILL = false: count P2P items, M2P boxes and M2P items per target block.
 // FILL = true: write them at the scanned offsets and mark accepted boxes as used.
+constexpr int kListWarps = 4;
 template <bool FILL>
-__global__ void lists_kernel(int64_t ntb, int64_t N, const dbl4 *lo, const dbl4 *hi, const dbl4 *__restrict__ bc,
-                             const int *__restrict__ beg, const int *__restrict__ end, const int *__restrict__ child,
-                             const int *__restrict__ nchild, double theta, double clear, int *n_p2p, int *n_m2p,
-                             int *n_m2pi, const int *o_p2p, const int *o_m2p, const int *o_m2pi, int4 *p2p_items,
-                             int *m2p_list, int4 *m2p_items, int *used, unsigned long long *pairs, int *overflow) {
-    int64_t tb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kListWarps * 32) lists_kernel(
+    int64_t ntb, int64_t N, const dbl4 *lo, const dbl4 *hi, const dbl4 *__restrict__ bc,
+    const int *__restrict__ beg, const int *__restrict__ end, const int *__restrict__ child,
+    const int *__restrict__ nchild, double theta, double clear, int *n_p2p, int *n_m2p, int *n_m2pi,
+    const int *o_p2p, const int *o_m2p, const int *o_m2pi, int4 *p2p_items, int *m2p_list, int4 *m2p_items,
+    int *used, unsigned long long *pairs, int *overflow) {
+    __shared__ int stk[kListWarps][kStack];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tb = (int64_t)blockIdx.x * kListWarps + warp;
     if (tb >= ntb) return;
+    int *stack = stk[warp];
     const dbl4 l = lo[tb], h = hi[tb];
     const int ntgt = (int)min((int64_t)kTargetBlock, N - tb * kTargetBlock);
-    int stack[kStack];
-    int sp = 0;
-    stack[sp++] = 0;
+    if (lane == 0) stack[0] = 0;
+    __syncwarp();
+    int sp = 1;
     int np = 0, nm = 0;
-    int cur_b = -1, cur_e = -1;    // pending merged P2P range
+    int cur_b = -1, cur_e = -1;   // pending merged P2P range
     int p_out = FILL ? o_p2p[tb] : 0, m_out = FILL ? o_m2p[tb] : 0;
     unsigned long long pp = 0;
-    auto flush = [&](int b, int e) {
-        // split [b, e) into chunks of at most kP2PChunk sources
-        const int n = e - b;
+    auto flush = [&](int b0, int e0) {
+        const int n = e0 - b0;
         const int k = (n + kP2PChunk - 1) / kP2PChunk;
         for (int q = 0; q < k; ++q) {
-            const int s0 = b + (int)((int64_t)n * q / k), s1 = b + (int)((int64_t)n * (q + 1) / k);
-            if (FILL) p2p_items[p_out++] = make_int4((int)tb, s0, s1, 0);
+            const int s0 = b0 + (int)((int64_t)n * q / k), s1 = b0 + (int)((int64_t)n * (q + 1) / k);
+            if (FILL && lane == 0) p2p_items[p_out] = make_int4((int)tb, s0, s1, 0);
+            ++p_out;
         }
         np += k;
         pp += (unsigned long long)n * ntgt;
     };
+    bool ovf = false;
     while (sp > 0) {
         const int b = stack[--sp];
-        const dbl4 c = bc[b];
-        if (b != 0 && mac_accept(c, l, h, theta, clear)) {
-            if (FILL) {
-                m2p_list[m_out++] = b;
-                used[b] = 1;
-            }
-            ++nm;
-            continue;
-        }
-        if (nchild[b] == 0) {
+        __syncwarp();
+        const int nc = nchild[b];
+        if (nc == 0) {
             if (cur_e == beg[b]) {
                 cur_e = end[b];
             } else {
@@ -449,21 +471,44 @@ __global__ void lists_kernel(int64_t ntb, int64_t N, const dbl4 *lo, const dbl4 
             }
             continue;
         }
-        if (sp + nchild[b] > kStack) {
-            atomicOr(overflow, 1);
+        int ch = -1;
+        bool acc = false, push = false;
+        if (lane < nc) {
+            ch = child[b] + lane;
+            acc = mac_accept(bc[ch], l, h, theta, clear);
+            push = !acc;
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, acc), pm = __ballot_sync(0xffffffffu, push);
+        const unsigned below = (1u << lane) - 1u;
+        if (FILL && acc) {
+            m2p_list[m_out + __popc(am & below)] = ch;
+            used[ch] = 1;
+        }
+        m_out += __popc(am);
+        nm += __popc(am);
+        const int npush = __popc(pm);
+        if (sp + npush > kStack) {
+            ovf = true;
             break;
         }
-        for (int q = nchild[b] - 1; q >= 0; --q) stack[sp++] = child[b] + q;
+        if (push) stack[sp + npush - 1 - __popc(pm & below)] = ch;
+        __syncwarp();
+        sp += npush;
+    }
+    if (ovf) {
+        if (lane == 0) atomicOr(overflow, 1);
+        return;
     }
     if (cur_b >= 0) flush(cur_b, cur_e);
     const int nmi = (nm + kM2PSeg - 1) / kM2PSeg;
+    if (lane != 0) return;
     if (!FILL) {
         n_p2p[tb] = np;
         n_m2p[tb] = nm;
         n_m2pi[tb] = nmi;
         atomicAdd(pairs, pp);
     } else {
-        int base = o_m2p[tb];
+        const int base = o_m2p[tb];
         for (int q = 0; q < nmi; ++q) {
             const int s0 = base + q * kM2PSeg, s1 = min(base + nm, s0 + kM2PSeg);
             m2p_items[o_m2pi[tb] + q] = make_int4((int)tb, s0, s1, 0);
@@ -487,9 +532,11 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     timer_begin(ctx, T_TREE, &ev);
 
     DArr<double> cube;
-    LSPR_TRY(ctx, cube.ensure(8));
+    LSPR_TRY(ctx, cube.ensure(8 + 6 * kBoxBlocks));
     ++ctx->n_launches;
-    bbox_kernel<<<1, 1024, 0, st>>>(m.src_pos64.p, Ns, m.tgt64.p, N, cube.p);
+    bbox_partial_kernel<<<kBoxBlocks, 256, 0, st>>>(m.src_pos64.p, Ns, m.tgt64.p, N, cube.p + 8);
+    ++ctx->n_launches;
+    bbox_final_kernel<<<1, 32, 0, st>>>(cube.p + 8, kBoxBlocks, cube.p);
     double hb[6];
     LSPR_TRY(ctx, cudaMemcpyAsync(hb, cube.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
     LSPR_TRY(ctx, cudaStreamSynchronize(st));
@@ -564,7 +611,7 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     LSPR_TRY(ctx, tr.box_c64.ensure(nboxes));
     LSPR_TRY(ctx, tr.box_c32.ensure(nboxes));
     ++ctx->n_launches;
-    box_geometry_kernel<<<nboxes, kGeomThreads, 0, st>>>(nboxes, tr.box_beg.p, tr.box_end.p, w.spos64.p, tr.box_c64.p,
+    box_geometry_kernel<<<nboxes, kGeomThreads, 0, st>>>(nboxes, tr.box_beg.p, tr.box_end.p, w.spos32.p, tr.box_c64.p,
                                                 tr.box_c32.p);
 
     // target blocks
@@ -591,7 +638,7 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     LSPR_TRY(ctx, cudaMemsetAsync(ovf.p, 0, sizeof(int), st));
     LSPR_TRY(ctx, cudaMemsetAsync(tr.box_used.p, 0, sizeof(int) * nboxes, st));
     ++ctx->n_launches;
-    lists_kernel<false><<<grid_for(ntb, 64), 64, 0, st>>>(
+    lists_kernel<false><<<grid_for(ntb, kListWarps), kListWarps * 32, 0, st>>>(
         ntb, N, tlo.p, thi.p, tr.box_c64.p, tr.box_beg.p, tr.box_end.p, tr.box_child.p, tr.box_nchild.p, theta, clear,
         cnt3.p, cnt3.p + ntb, cnt3.p + 2 * ntb, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
         pairs.p, ovf.p);
@@ -619,28 +666,43 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     LSPR_TRY(ctx, tr.m2p_list.ensure(std::max<int64_t>(1, tot[1])));
     LSPR_TRY(ctx, tr.m2p_items.ensure(std::max<int64_t>(1, tot[2])));
     ++ctx->n_launches;
-    lists_kernel<true><<<grid_for(ntb, 64), 64, 0, st>>>(
+    lists_kernel<true><<<grid_for(ntb, kListWarps), kListWarps * 32, 0, st>>>(
         ntb, N, tlo.p, thi.p, tr.box_c64.p, tr.box_beg.p, tr.box_end.p, tr.box_child.p, tr.box_nchild.p, theta, clear,
         nullptr, nullptr, nullptr, off3.p, off3.p + ntb, off3.p + 2 * ntb, tr.p2p_items.p, tr.m2p_list.p,
         tr.m2p_items.p, tr.box_used.p, pairs.p, ovf.p);
     LSPR_TRY(ctx, cudaGetLastError());
     LSPR_TRY_ST(launch_item_flags(ctx, tr.p2p_items.p, tr.n_p2p_items));
 
-    // P2M work items over the used boxes (host side: a few thousand boxes)
-    std::vector<int> hbeg(nboxes), hend(nboxes), hused(nboxes);
+    // P2M work: the leaves with an accepted box among themselves or their ancestors; each
+    // leaf chunk's moments are shifted into every accepted ancestor inside the P2M kernel
+    // (host side: a few thousand boxes).
+    std::vector<int> hbeg(nboxes), hend(nboxes), hused(nboxes), hch(nboxes), hnch(nboxes), hpar(nboxes, -1);
     LSPR_TRY(ctx, cudaMemcpyAsync(hbeg.data(), tr.box_beg.p, sizeof(int) * nboxes, cudaMemcpyDeviceToHost, st));
     LSPR_TRY(ctx, cudaMemcpyAsync(hend.data(), tr.box_end.p, sizeof(int) * nboxes, cudaMemcpyDeviceToHost, st));
     LSPR_TRY(ctx, cudaMemcpyAsync(hused.data(), tr.box_used.p, sizeof(int) * nboxes, cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaMemcpyAsync(hch.data(), tr.box_child.p, sizeof(int) * nboxes, cudaMemcpyDeviceToHost, st));
+    LSPR_TRY(ctx, cudaMemcpyAsync(hnch.data(), tr.box_nchild.p, sizeof(int) * nboxes, cudaMemcpyDeviceToHost, st));
     LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    std::vector<char> under(nboxes, 0);   // the box or an ancestor is accepted
+    for (int b = 0; b < nboxes; ++b) {    // children are numbered after their parent
+        under[b] = under[b] || hused[b];
+        for (int c = 0; c < hnch[b]; ++c) {
+            hpar[hch[b] + c] = b;
+            under[hch[b] + c] = under[b];
+        }
+    }
     std::vector<int4> p2m;
     for (int b = 0; b < nboxes; ++b) {
-        if (!hused[b]) continue;
-        for (int s = hbeg[b]; s < hend[b]; s += kP2MChunk) p2m.push_back(make_int4(b, s, std::min(hend[b], s + kP2MChunk), 0));
+        if (!under[b] || hnch[b] != 0) continue;
+        for (int s0 = hbeg[b]; s0 < hend[b]; s0 += kP2MChunk)
+            p2m.push_back(make_int4(b, s0, std::min(hend[b], s0 + kP2MChunk), 0));
     }
     tr.n_p2m_items = (int64_t)p2m.size();
     LSPR_TRY(ctx, tr.p2m_items.ensure(std::max<size_t>(1, p2m.size())));
     if (!p2m.empty())
         LSPR_TRY(ctx, cudaMemcpyAsync(tr.p2m_items.p, p2m.data(), sizeof(int4) * p2m.size(), cudaMemcpyHostToDevice, st));
+    LSPR_TRY(ctx, tr.box_parent.ensure(nboxes));
+    LSPR_TRY(ctx, cudaMemcpyAsync(tr.box_parent.p, hpar.data(), sizeof(int) * nboxes, cudaMemcpyHostToDevice, st));
     timer_end(ctx, T_TREE, ev);
     LSPR_TRY(ctx, cudaStreamSynchronize(st));
     for (auto *a : {&keys, &ktmp}) a->release();

@@ -147,7 +147,9 @@ def test_batched_matvec_and_device_pointers(lspr, oracle):
         y_dev = ctx.matvec(torch.as_tensor(x, device="cuda"), s, "tree_fp32").cpu().numpy()
     for b in range(3):
         assert _rel(y_host[b], yo[b]) < 1e-4
-    assert np.allclose(y_dev, y_host, rtol=0, atol=1e-9 * np.abs(y_host).max())
+    # same product through device pointers; the FP32 far field accumulates with atomics
+    # in a run-dependent order, so the two agree to FP32 rounding, not bit for bit
+    assert _rel(y_dev, y_host) < 1e-6
 
 
 def _golden(name):
