@@ -44,6 +44,9 @@ WORKLOADS = {
     # 1280-panel sphere, direct FP64 matvec, GMRES 1e-8
     "sphere1280": dict(sub=3, R=10.0, lam=[380.0], mode="direct_fp64", tol=1e-8, theta=0.5, P=6, Ncrit=300,
                        K=4, K_fine=19, N_k=9, restart=100, refine=False),
+    # 20480-panel sphere, 16 wavelengths over 350-420 nm in one batched solve
+    "sphere20480_sweep16": dict(sub=5, R=10.0, lam=list(I.wavelengths(350, 420, 16)), mode="tree_fp32", tol=1e-6,
+                                theta=0.5, P=6, Ncrit=300, K=4, K_fine=19, N_k=9, restart=50, refine=True),
     # 81920-panel sphere, 64 wavelengths over 350-420 nm in one batched solve
     "sphere81920_sweep64": dict(sub=6, R=10.0, lam=list(I.wavelengths(350, 420, 64)), mode="tree_fp32", tol=1e-6,
                                 theta=0.5, P=6, Ncrit=300, K=4, K_fine=19, N_k=9, restart=50, refine=True),
@@ -224,15 +227,16 @@ def run_ours(args, wl, rank, world, local_rank):
     kernels = {}
     matvecs_per_step = None
     for name in ("p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh", "p2p_fp64", "m2p_fp64", "p2m_fp64",
-                 "weights"):
+                 "weights", "p2p_ff", "m2p_ff", "p2m_ff"):
         ms, n = ktime[name]
         if n:
             kernels[name] = {"ms_total": round(ms, 4), "launches": n, "ms_per_launch": ms / n,
                              "share_of_step": round(ms / total_ms, 4)}
     pairs = info["n_p2p_pairs"] if wl["mode"].startswith("tree") else info["n_panels"] * info["n_sources"]
     roof = None
-    dom = max((k for k in kernels if k in ("p2p", "m2p", "p2m", "near_assembly", "gmres", "p2p_fp64", "m2p_fp64",
-                                           "p2m_fp64")),
+    # dominant single kernel: the far-field evaluations (the "gmres" slot groups many small
+    # vector kernels, and P2M's event time overlaps the concurrent P2P on the side stream)
+    dom = max((k for k in kernels if k in ("p2p", "m2p", "p2p_fp64", "m2p_fp64", "p2p_ff", "m2p_ff")),
               key=lambda k: kernels[k]["ms_total"], default=None)
     fp32 = wl["mode"].endswith("fp32")
     peak_fp32 = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
@@ -244,7 +248,7 @@ def run_ours(args, wl, rank, world, local_rank):
         k = kernels["m2p"]
         k["algorithmic_tflops"] = info["n_m2p_pairs"] * kernel_targets(info) * m2p_flops(wl["P"]) / (
             k["ms_per_launch"] * 1e-3) / 1e12
-    for name, flops in (("p2p_fp64", P2P_FLOPS), ("m2p_fp64", None)):
+    for name, flops in (("p2p_fp64", P2P_FLOPS), ("m2p_fp64", None), ("p2p_ff", P2P_FLOPS), ("m2p_ff", None)):
         if name in kernels:
             k = kernels[name]
             work = pairs * P2P_FLOPS if flops else info["n_m2p_pairs"] * kernel_targets(info) * m2p_flops(wl["P"])
@@ -259,6 +263,11 @@ def run_ours(args, wl, rank, world, local_rank):
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 3), "peak": round(peak_fp32, 2),
                 "unit": "TFLOP/s", "frac": round(a / peak_fp32, 4), "traffic": None,
                 "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 flops x 2070 MHz (derived, no measured FP32 peak)"}
+    elif dom in ("p2p_ff", "m2p_ff"):
+        a = kernels[dom]["algorithmic_tflops"]
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s (FP64-equivalent)", "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_note": "float-float kernel replacing FP64; peak is the nominal FP64 1.25 TFLOP/s"}
     elif dom is not None:
         roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                 "frac": None, "traffic": None, "peak_note": "of measured"}
@@ -390,10 +399,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere20480", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--restart", type=int, default=None, help="override the workload's GMRES restart length")
     ap.add_argument("--matvecs", type=int, default=0, help="only run this many bare matvecs (profiling)")
     ap.add_argument("--matvec-mode", default=None, help="matvec mode for --matvecs (default: the workload's)")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.restart:
+        wl["restart"] = args.restart
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -60,7 +60,9 @@ enum {
     LSPR_DIRECT_FP64 = 0,  /* all pairs, FP64 arithmetic */
     LSPR_DIRECT_FP32 = 1,  /* all pairs, FP32 arithmetic, FP64 accumulation across tiles */
     LSPR_TREE_FP64 = 2,    /* treecode (needs lspr_tree_build), FP64 */
-    LSPR_TREE_FP32 = 3     /* treecode, FP32 P2P/P2M/M2P, FP64 accumulation and corrections */
+    LSPR_TREE_FP32 = 3,    /* treecode, FP32 P2P/P2M/M2P, FP64 accumulation and corrections */
+    LSPR_DIRECT_FF = 4,    /* all pairs, float-float arithmetic (hi + lo FP32 pair, ~48 bits) */
+    LSPR_TREE_FF = 5       /* treecode in float-float arithmetic */
 };
 
 /* Quadrature options, Sec. II.C "Integral evaluation" (paper's Tables 1 and 4). */
@@ -77,7 +79,8 @@ typedef struct {
     int32_t restart;    /* GMRES restart length m (1..512) */
     int32_t maxiter;    /* total Arnoldi steps per wavelength */
     int32_t mode;       /* matvec mode of the Krylov iteration (LSPR_DIRECT_* / LSPR_TREE_*) */
-    int32_t refine;     /* 1: FP64 iterative refinement around an FP32-mode inner solve */
+    int32_t refine;     /* FP32 modes only: 0 plain solve; 1 iterative refinement with the residual
+                           in float-float arithmetic; 2 the same with a native FP64 residual */
 } lspr_solve_opts;
 
 /* Per-solve statistics; arrays hold B entries and are owned by the caller (may be null). */
@@ -171,11 +174,12 @@ LSPR_API int lspr_get_info(lspr_ctx *ctx, int64_t *n_panels, int64_t *n_sources,
                   int64_t *n_p2p_items, int64_t *n_m2p_pairs, int64_t *n_p2p_pairs);
 
 /* Kernel timing on the context's stream while enabled (lspr_set_timing(ctx, 1) clears
- * the counters): milliseconds summed over launches and launch counts, arrays of 12:
+ * the counters): milliseconds summed over launches and launch counts, arrays of 16:
  * [0] P2P FP32, [1] M2P FP32, [2] P2M FP32, [3] near correction + block assembly,
  * [4] GMRES vector kernels, [5] tree build, [6] mesh + near precompute, [7] other,
- * [8] P2P FP64, [9] M2P FP64, [10] P2M FP64, [11] source weights.
- * Every timed launch is bracketed by CUDA events on the context's stream. */
+ * [8] P2P FP64, [9] M2P FP64, [10] P2M FP64, [11] source weights,
+ * [12] P2P float-float, [13] M2P float-float, [14] P2M float-float, [15] unused.
+ * Every timed launch is bracketed by CUDA events on the stream it runs on. */
 LSPR_API int lspr_set_timing(lspr_ctx *ctx, int32_t enable);
 /* Number of CUDA kernels the context has launched since lspr_create. */
 LSPR_API int lspr_launch_count(lspr_ctx *ctx, int64_t *count);

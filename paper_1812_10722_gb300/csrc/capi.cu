@@ -138,6 +138,8 @@ int lspr_destroy(lspr_ctx *c) {
         a->release();
     for (cudaEvent_t e : c->timing.pool) cudaEventDestroy(e);
     c->counters.release();
+    for (DArr<ff4> *a : {&c->wo.spos_ff, &c->wo.snrm_ff, &c->wo.tgt_ff, &c->tree.mom_ff, &c->tree.box_c_ff, &c->w_ff})
+        a->release();
     c->wo.tgt_pos.release();
     c->wo.src_tblock.release();
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -169,9 +171,9 @@ int lspr_tree_build(lspr_ctx *c, double theta, int32_t P, int32_t Ncrit) {
 
 int lspr_matvec(lspr_ctx *c, const double *x, double *y, int32_t B, const double *eps_ratio, int32_t mode,
                 int32_t on_device) {
-    if (!c || !x || !y || !eps_ratio || B < 1 || mode < 0 || mode > 3) return LSPR_E_ARG;
+    if (!c || !x || !y || !eps_ratio || B < 1 || mode < 0 || mode > 5) return LSPR_E_ARG;
     if (!c->mesh.ready) return LSPR_E_STATE;
-    if ((mode == LSPR_TREE_FP32 || mode == LSPR_TREE_FP64) && !c->tree.ready) return LSPR_E_STATE;
+    if (mode_tree(mode) && !c->tree.ready) return LSPR_E_STATE;
     cudaSetDevice(c->device);
     const int64_t n2 = 2 * c->mesh.N;
     const double2 *xd = (const double2 *)x;
@@ -199,10 +201,11 @@ int lspr_solve(lspr_ctx *c, const double *eps_in, double eps_out_re, double eps_
                const double *lambda_nm, int32_t B, const lspr_solve_opts *o, double *dipole_out,
                double *sigma_ext_out, lspr_solve_stats *st) {
     if (!c || !eps_in || !E0 || !lambda_nm || !o || !dipole_out || !sigma_ext_out || B < 1) return LSPR_E_ARG;
-    if (o->mode < 0 || o->mode > 3 || !(o->tol > 0) || o->restart < 1 || o->maxiter < 1) return LSPR_E_ARG;
+    if (o->mode < 0 || o->mode > 5 || !(o->tol > 0) || o->restart < 1 || o->maxiter < 1) return LSPR_E_ARG;
+    if (o->refine < 0 || o->refine > 2) return LSPR_E_ARG;
     if (!(E0[0] * E0[0] + E0[1] * E0[1] + E0[2] * E0[2] > 0)) return LSPR_E_ARG;
     if (!c->mesh.ready) return LSPR_E_STATE;
-    if ((o->mode == LSPR_TREE_FP32 || o->mode == LSPR_TREE_FP64) && !c->tree.ready) return LSPR_E_STATE;
+    if (mode_tree(o->mode) && !c->tree.ready) return LSPR_E_STATE;
     cudaSetDevice(c->device);
     const auto t0 = std::chrono::steady_clock::now();
     const int64_t mv0 = c->matvec_count;

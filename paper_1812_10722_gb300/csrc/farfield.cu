@@ -7,6 +7,12 @@
 // added exactly by the near-field correction).  Complex weights are carried as
 // two real channels (the paper's real/imaginary split of the treecode work).
 //
+// Several right-hand sides (wavelengths) share one geometry: the kernels generate G,
+// dG/dn (P2P), the monomials (P2M) or the Taylor coefficients (M2P) once per pair,
+// source or (target, box) and apply them to a chunk of NB right-hand sides.
+// Layouts for B right-hand sides: weights [source][B], accumulators [panel][B][4],
+// moments [box][term][B].
+//
 //   p2p_kernel  direct sums of a 64-target block against a contiguous source range
 //   p2m_kernel  Cartesian Taylor moments of a leaf about its centre c, shifted into
 //               every accepted ancestor box:
@@ -20,6 +26,7 @@
 // item and accumulated in FP64 with atomics.
 #include <algorithm>
 
+#include "ffloat.cuh"
 #include "lspr_internal.cuh"
 
 namespace lspr {
@@ -27,9 +34,18 @@ namespace lspr {
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = dbl4; };
+template <> struct Vec4<ffloat> { using type = ff4; };
+
+// moments accumulate with atomics: FP32/FP64 in place, float-float through an FP64 buffer
+template <typename T> struct MomAcc { using type = typename Vec4<T>::type; using scalar = T; };
+template <> struct MomAcc<ffloat> { using type = dbl4; using scalar = double; };
+__device__ __forceinline__ void acc_add(float *g, float v) { atomicAdd(g, v); }
+__device__ __forceinline__ void acc_add(double *g, double v) { atomicAdd(g, v); }
+__device__ __forceinline__ void acc_add(double *g, const ffloat &v) { atomicAdd(g, (double)v); }
 
 __device__ __forceinline__ int panel_of(float w) { return __float_as_int(w); }
 __device__ __forceinline__ int panel_of(double w) { return (int)w; }
+__device__ __forceinline__ int panel_of(const ffloat &w) { return __float_as_int(w.hi); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 // FP64 1/sqrt(x): the FP32 reciprocal square root as the seed and one Newton-Raphson
 // step y <- y + y (1 - x y^2) / 2; a seed error e leaves ~1.5 e^2 (~2e-14 relative).
@@ -40,81 +56,14 @@ __device__ __forceinline__ double rsq(double x) {
     return fma(0.5 * y, h, y);
 }
 
-// ----------------------------------------------------------------- weights
 template <typename T4>
-__global__ void weights_kernel(int64_t Ns, int64_t N, const dbl4 *__restrict__ spos64,
-                               const int *__restrict__ src_panel, const double2 *__restrict__ x, T4 *__restrict__ w) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= Ns) return;
-    const int p = src_panel[s];
-    const double wa = spos64[s].w * kInv4Pi;
-    const double2 phi = x[p], dphi = x[N + p];
-    T4 o;
-    o.x = wa * dphi.x;
-    o.y = wa * dphi.y;
-    o.z = wa * phi.x;
-    o.w = wa * phi.y;
-    w[s] = o;
-}
-
-// --------------------------------------------------------------------- P2P
-template <typename T>
-struct P2PAcc {
-    T vr, vi, kr, ki;
-};
-
-// One (target, source) pair.  CHECK: the item may hold sources of the target's own
-// panel, whose far-rule terms are skipped (the exact singular integral replaces them).
-template <typename T, typename T4, bool CHECK>
-__device__ __forceinline__ void p2p_pair(const T4 &p, const T4 &n, const T4 &w, int pid, T tx, T ty, T tz, int tp,
-                                         P2PAcc<T> &a) {
-    const T dx = tx - p.x, dy = ty - p.y, dz = tz - p.z;
-    const T r2 = dx * dx + dy * dy + dz * dz;
-    T ri = rsq(r2);
-    if (CHECK) ri = (pid == tp) ? T(0) : ri;
-    const T dn = dx * n.x + dy * n.y + dz * n.z;
-    const T t3 = dn * (ri * ri) * ri;
-    a.vr += ri * w.x;
-    a.vi += ri * w.y;
-    a.kr += t3 * w.z;
-    a.ki += t3 * w.w;
-}
-
-constexpr int kP2PWarps = 8;
-
-// Sources [beg, end) against the lane's two targets; the warp stages 32 sources at a
-// time in its shared-memory slice and every lane reads them by broadcast.
-template <typename T, typename T4, bool CHECK>
-__device__ __forceinline__ void p2p_range(int beg, int end, int lane, T4 (*sh)[32], const T4 *__restrict__ spos,
-                                          const T4 *__restrict__ snrm, const T4 *__restrict__ sw, const T4 &q0,
-                                          const T4 &q1, int tp0, int tp1, P2PAcc<T> &a0, P2PAcc<T> &a1) {
-    for (int base = beg; base < end; base += 32) {
-        const int s = base + lane;
-        if (s < end) {
-            sh[0][lane] = spos[s];
-            sh[1][lane] = snrm[s];
-            sh[2][lane] = sw[s];
-        }
-        __syncwarp();
-        const int cnt = min(32, end - base);
-        if (cnt == 32) {
-#pragma unroll 8
-            for (int k = 0; k < 32; ++k) {
-                const T4 p = sh[0][k], n = sh[1][k], w = sh[2][k];
-                const int pid = panel_of(n.w);
-                p2p_pair<T, T4, CHECK>(p, n, w, pid, q0.x, q0.y, q0.z, tp0, a0);
-                p2p_pair<T, T4, CHECK>(p, n, w, pid, q1.x, q1.y, q1.z, tp1, a1);
-            }
-        } else {
-            for (int k = 0; k < cnt; ++k) {
-                const T4 p = sh[0][k], n = sh[1][k], w = sh[2][k];
-                const int pid = panel_of(n.w);
-                p2p_pair<T, T4, CHECK>(p, n, w, pid, q0.x, q0.y, q0.z, tp0, a0);
-                p2p_pair<T, T4, CHECK>(p, n, w, pid, q1.x, q1.y, q1.z, tp1, a1);
-            }
-        }
-        __syncwarp();
-    }
+__device__ __forceinline__ T4 zero4() {
+    T4 z;
+    z.x = 0;
+    z.y = 0;
+    z.z = 0;
+    z.w = 0;
+    return z;
 }
 
 __device__ __forceinline__ void atomic_add4(double *o, double a, double b, double c, double d) {
@@ -124,38 +73,131 @@ __device__ __forceinline__ void atomic_add4(double *o, double a, double b, doubl
     atomicAdd(o + 3, d);
 }
 
-// Work items (target block, source begin, source end, own-panel flag), one per warp.
-// DYNAMIC: a persistent grid whose warps take items from an atomic counter.
-template <typename T, bool DYNAMIC>
-__global__ void __launch_bounds__(kP2PWarps * 32) p2p_kernel(const int4 *__restrict__ items, int64_t nitems,
-                                                             const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt,
-                                                             const typename Vec4<T>::type *__restrict__ spos,
-                                                             const typename Vec4<T>::type *__restrict__ snrm,
-                                                             const typename Vec4<T>::type *__restrict__ sw,
-                                                             double *__restrict__ acc, int *counter) {
+// right-hand sides per chunk: 1 for a single wavelength, else 8 (FP32) or 4 (FP64)
+template <typename T>
+constexpr int batch_chunk(int B) { return B <= 1 ? 1 : (sizeof(T) == 4 ? 8 : 4); }   // float-float: 8 bytes
+
+// ----------------------------------------------------------------- weights
+// w[s][b] = w_s A_s / (4 pi) * (dphi_b, phi_b) at the source's panel; x is [B][2N] complex
+template <typename T4>
+__global__ void weights_kernel(int64_t Ns, int64_t N, int B, const dbl4 *__restrict__ spos64,
+                               const int *__restrict__ src_panel, const double2 *__restrict__ x, T4 *__restrict__ w) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= Ns * B) return;
+    const int64_t s = g / B;
+    const int b = (int)(g - s * B);
+    const int p = src_panel[s];
+    const double wa = spos64[s].w * kInv4Pi;
+    const double2 phi = x[(int64_t)b * 2 * N + p], dphi = x[(int64_t)b * 2 * N + N + p];
+    T4 o;
+    o.x = wa * dphi.x;
+    o.y = wa * dphi.y;
+    o.z = wa * phi.x;
+    o.w = wa * phi.y;
+    w[g] = o;
+}
+
+// --------------------------------------------------------------------- P2P
+constexpr int p2p_warps(int NB) { return NB > 1 ? 4 : 8; }
+
+// Sources [beg, end) against the lane's two targets for right-hand sides [b0, b0 + nb):
+// the warp stages 32 sources (position, normal, NB weights) in its shared slice and every
+// lane reads them by broadcast; G and dG/dn are formed once per pair.
+// CHECK: the range may hold sources of a target's own panel, whose far-rule terms are
+// skipped (the exact singular integral replaces them).
+template <typename T, typename T4, int NB, bool CHECK>
+__device__ __forceinline__ void p2p_range(int beg, int end, int lane, int B, int b0, int nb, T4 (*sh)[32],
+                                          T4 (*shw)[NB], const T4 *__restrict__ spos, const T4 *__restrict__ snrm,
+                                          const T4 *__restrict__ sw, const T4 &q0, const T4 &q1, int tp0, int tp1,
+                                          T (&a0)[NB][4], T (&a1)[NB][4]) {
+    for (int base = beg; base < end; base += 32) {
+        const int s = base + lane;
+        if (s < end) {
+            sh[0][lane] = spos[s];
+            sh[1][lane] = snrm[s];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) shw[lane][k] = k < nb ? sw[(int64_t)s * B + b0 + k] : zero4<T4>();
+        }
+        __syncwarp();
+        const int cnt = min(32, end - base);
+#pragma unroll 4
+        for (int kk = 0; kk < cnt; ++kk) {
+            const T4 p = sh[0][kk], n = sh[1][kk];
+            const int pid = panel_of(n.w);
+            const T dx0 = q0.x - p.x, dy0 = q0.y - p.y, dz0 = q0.z - p.z;
+            const T dx1 = q1.x - p.x, dy1 = q1.y - p.y, dz1 = q1.z - p.z;
+            T r0 = rsq(dx0 * dx0 + dy0 * dy0 + dz0 * dz0);
+            T r1 = rsq(dx1 * dx1 + dy1 * dy1 + dz1 * dz1);
+            if (CHECK) {
+                r0 = (pid == tp0) ? T(0) : r0;
+                r1 = (pid == tp1) ? T(0) : r1;
+            }
+            const T t0 = (dx0 * n.x + dy0 * n.y + dz0 * n.z) * (r0 * r0) * r0;
+            const T t1 = (dx1 * n.x + dy1 * n.y + dz1 * n.z) * (r1 * r1) * r1;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const T4 w = shw[kk][k];
+                a0[k][0] += r0 * w.x;
+                a0[k][1] += r0 * w.y;
+                a0[k][2] += t0 * w.z;
+                a0[k][3] += t0 * w.w;
+                a1[k][0] += r1 * w.x;
+                a1[k][1] += r1 * w.y;
+                a1[k][2] += t1 * w.z;
+                a1[k][3] += t1 * w.w;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Work units: (item, right-hand-side chunk), item = (target block, source begin, source
+// end, own-panel flag); one per warp.  DYNAMIC: a persistent grid whose warps take units
+// from an atomic counter.  acc is [panel][B][4].
+template <typename T, int NB, bool DYNAMIC>
+__global__ void __launch_bounds__(p2p_warps(NB) * 32)
+    p2p_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B,
+               const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt,
+               const typename Vec4<T>::type *__restrict__ spos, const typename Vec4<T>::type *__restrict__ snrm,
+               const typename Vec4<T>::type *__restrict__ sw, double *__restrict__ acc, int *counter) {
     using T4 = typename Vec4<T>::type;
-    __shared__ T4 sh[kP2PWarps][3][32];
+    constexpr int W = p2p_warps(NB);
+    __shared__ T4 sh[W][2][32];
+    __shared__ T4 shw[W][32][NB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t it = (int64_t)blockIdx.x * kP2PWarps + warp;
+    const int64_t units = nitems * nbc;
+    int64_t it = (int64_t)blockIdx.x * W + warp;
     while (true) {
         if (DYNAMIC) {
             int v = 0;
             if (lane == 0) v = atomicAdd(counter, 1);
             it = __shfl_sync(0xffffffffu, v, 0);
         }
-        if (it >= nitems) return;
-        const int4 item = __ldg(items + it);
+        if (it >= units) return;
+        const int64_t ii = it / nbc;
+        const int b0 = (int)(it - ii * nbc) * NB, nb = min(NB, B - b0);
+        const int4 item = __ldg(items + ii);
         const int64_t t0 = (int64_t)item.x * kTargetBlock + lane, t1 = t0 + 32;
         const T4 q0 = t0 < ntgt ? tgt[t0] : tgt[0];
         const T4 q1 = t1 < ntgt ? tgt[t1] : tgt[0];
         const int tp0 = panel_of(q0.w), tp1 = panel_of(q1.w);
-        P2PAcc<T> a0 = {0, 0, 0, 0}, a1 = {0, 0, 0, 0};
+        T a0[NB][4], a1[NB][4];
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a0[k][c] = a1[k][c] = T(0);
         if (item.w)
-            p2p_range<T, T4, true>(item.y, item.z, lane, sh[warp], spos, snrm, sw, q0, q1, tp0, tp1, a0, a1);
+            p2p_range<T, T4, NB, true>(item.y, item.z, lane, B, b0, nb, sh[warp], shw[warp], spos, snrm, sw, q0, q1,
+                                       tp0, tp1, a0, a1);
         else
-            p2p_range<T, T4, false>(item.y, item.z, lane, sh[warp], spos, snrm, sw, q0, q1, tp0, tp1, a0, a1);
-        if (t0 < ntgt) atomic_add4(acc + 4 * (int64_t)tp0, a0.vr, a0.vi, a0.kr, a0.ki);
-        if (t1 < ntgt) atomic_add4(acc + 4 * (int64_t)tp1, a1.vr, a1.vi, a1.kr, a1.ki);
+            p2p_range<T, T4, NB, false>(item.y, item.z, lane, B, b0, nb, sh[warp], shw[warp], spos, snrm, sw, q0,
+                                        q1, tp0, tp1, a0, a1);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            if (k >= nb) break;
+            if (t0 < ntgt) atomic_add4(acc + 4 * ((int64_t)tp0 * B + b0 + k), a0[k][0], a0[k][1], a0[k][2], a0[k][3]);
+            if (t1 < ntgt) atomic_add4(acc + 4 * ((int64_t)tp1 * B + b0 + k), a1[k][0], a1[k][1], a1[k][2], a1[k][3]);
+        }
         if (!DYNAMIC) return;
     }
 }
@@ -209,10 +251,26 @@ struct MultiIndex {
     }
 };
 
+// decode the multi-index of term t
+__device__ __forceinline__ void mi_decode(int t, int &k1, int &k2, int &k3) {
+    int n = 0;
+    while (n_terms(n) <= t) ++n;
+    int r = t - n_terms(n - 1), a = n;
+    while (r > n - a) {
+        r -= n - a + 1;
+        --a;
+    }
+    k1 = a;
+    k2 = n - a - r;
+    k3 = n - k1 - k2;
+}
+
 // --------------------------------------------------------------------- M2P
-template <typename T, int P>
+// One target against one box: the coefficients a_k(R) are generated by the recurrence
+// and contracted with the box's moments of NB right-hand sides, mom[k * NB + j].
+template <typename T, int P, int NB>
 __device__ __forceinline__ void m2p_one(T Rx, T Ry, T Rz, const typename Vec4<T>::type *__restrict__ mom,
-                                        P2PAcc<T> &acc) {
+                                        T (&acc)[NB][4]) {
     constexpr MultiIndex<P> mi{};
     constexpr int NT = MultiIndex<P>::NT;
     const T R[3] = {Rx, Ry, Rz};
@@ -220,12 +278,13 @@ __device__ __forceinline__ void m2p_one(T Rx, T Ry, T Rz, const typename Vec4<T>
     T a[NT];
     a[0] = rsq(r2);
     const T ir2 = a[0] * a[0];
-    {
-        const auto m = mom[0];
-        acc.vr += a[0] * m.x;
-        acc.vi += a[0] * m.y;
-        acc.kr += a[0] * m.z;
-        acc.ki += a[0] * m.w;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const auto m = mom[j];
+        acc[j][0] += a[0] * m.x;
+        acc[j][1] += a[0] * m.y;
+        acc[j][2] += a[0] * m.z;
+        acc[j][3] += a[0] * m.w;
     }
 #pragma unroll
     for (int t = 1; t < NT; ++t) {
@@ -238,54 +297,106 @@ __device__ __forceinline__ void m2p_one(T Rx, T Ry, T Rz, const typename Vec4<T>
         }
         const T c1 = T(-(2.0 * n - 1.0) / n), c2 = T(-(n - 1.0) / n);
         a[t] = (c1 * s1 + c2 * s2) * ir2;
-        const auto m = mom[t];
-        acc.vr += a[t] * m.x;
-        acc.vi += a[t] * m.y;
-        acc.kr += a[t] * m.z;
-        acc.ki += a[t] * m.w;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const auto m = mom[t * NB + j];
+            acc[j][0] += a[t] * m.x;
+            acc[j][1] += a[t] * m.y;
+            acc[j][2] += a[t] * m.z;
+            acc[j][3] += a[t] * m.w;
+        }
     }
 }
 
-constexpr int kM2PWarps = 4;
+// warps per block such that the staged moments of every warp fit in 46 KB
+template <typename T, int P, int NB>
+constexpr int m2p_warps() {
+    constexpr int per = n_terms(P) * NB * (int)sizeof(typename Vec4<T>::type);
+    constexpr int w = 46000 / per;
+    return w < 1 ? 1 : (w > 4 ? 4 : w);
+}
 
-// Work items (target block, list begin, list end): each lane evaluates the boxes'
-// expansions at its two targets; a box's moments are staged in the warp's shared slice.
-template <typename T, int P, bool DYNAMIC>
-__global__ void __launch_bounds__(kM2PWarps * 32) m2p_kernel(const int4 *__restrict__ items, int64_t nitems,
-                                                             const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt,
-                                                             const int *__restrict__ list,
-                                                             const typename Vec4<T>::type *__restrict__ box_c,
-                                                             const typename Vec4<T>::type *__restrict__ mom,
-                                                             double *__restrict__ acc, int *counter) {
+// Work units: (item, right-hand-side chunk), item = (target block, list begin, list end):
+// each lane evaluates the listed boxes' expansions at its two targets; a box's moments
+// for the chunk are staged in the warp's shared slice.
+template <typename T, int P, int NB, bool DYNAMIC>
+__global__ void __launch_bounds__(m2p_warps<T, P, NB>() * 32)
+    m2p_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B,
+               const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt, const int *__restrict__ list,
+               const typename Vec4<T>::type *__restrict__ box_c, const typename Vec4<T>::type *__restrict__ mom,
+               double *__restrict__ acc, int *counter) {
     using T4 = typename Vec4<T>::type;
     constexpr int NT = n_terms(P);
-    __shared__ T4 sm[kM2PWarps][NT];
+    constexpr int W = m2p_warps<T, P, NB>();
+    __shared__ T4 sm[W][NT * NB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t it = (int64_t)blockIdx.x * kM2PWarps + warp;
+    const int64_t units = nitems * nbc;
+    int64_t it = (int64_t)blockIdx.x * W + warp;
     while (true) {
         if (DYNAMIC) {
             int v = 0;
             if (lane == 0) v = atomicAdd(counter, 1);
             it = __shfl_sync(0xffffffffu, v, 0);
         }
-        if (it >= nitems) return;
-        const int4 item = __ldg(items + it);
+        if (it >= units) return;
+        const int64_t ii = it / nbc;
+        const int b0 = (int)(it - ii * nbc) * NB, nb = min(NB, B - b0);
+        const int4 item = __ldg(items + ii);
         const int64_t t0 = (int64_t)item.x * kTargetBlock + lane, t1 = t0 + 32;
         const T4 q0 = t0 < ntgt ? tgt[t0] : tgt[0];
         const T4 q1 = t1 < ntgt ? tgt[t1] : tgt[0];
-        P2PAcc<T> a0 = {0, 0, 0, 0}, a1 = {0, 0, 0, 0};
+        if constexpr (NB == 1) {
+            // both targets per staged box; the non-unrolled loop over the two targets keeps
+            // the compiler from interleaving their recurrences (register pressure)
+            T a0[1][4] = {{0, 0, 0, 0}}, a1[1][4] = {{0, 0, 0, 0}};
 #pragma unroll 1
-        for (int l = item.y; l < item.z; ++l) {
-            const int b = __ldg(list + l);
-            const T4 c = box_c[b];
-            __syncwarp();
-            for (int t = lane; t < NT; t += 32) sm[warp][t] = mom[(int64_t)b * NT + t];
-            __syncwarp();
-            m2p_one<T, P>(q0.x - c.x, q0.y - c.y, q0.z - c.z, sm[warp], a0);
-            m2p_one<T, P>(q1.x - c.x, q1.y - c.y, q1.z - c.z, sm[warp], a1);
+            for (int l = item.y; l < item.z; ++l) {
+                const int b = __ldg(list + l);
+                const T4 c = box_c[b];
+                __syncwarp();
+                for (int t = lane; t < NT; t += 32) sm[warp][t] = mom[((int64_t)b * NT + t) * B + b0];
+                __syncwarp();
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 0) m2p_one<T, P, 1>(q0.x - c.x, q0.y - c.y, q0.z - c.z, sm[warp], a0);
+                    else m2p_one<T, P, 1>(q1.x - c.x, q1.y - c.y, q1.z - c.z, sm[warp], a1);
+                }
+            }
+            if (t0 < ntgt)
+                atomic_add4(acc + 4 * ((int64_t)panel_of(q0.w) * B + b0), a0[0][0], a0[0][1], a0[0][2], a0[0][3]);
+            if (t1 < ntgt)
+                atomic_add4(acc + 4 * ((int64_t)panel_of(q1.w) * B + b0), a1[0][0], a1[0][1], a1[0][2], a1[0][3]);
+        } else {
+            // one target at a time keeps one accumulator set (NB x 4) and one recurrence live
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const T4 q = h ? q1 : q0;
+                T a[NB][4];
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) a[j][c] = T(0);
+#pragma unroll 1
+                for (int l = item.y; l < item.z; ++l) {
+                    const int b = __ldg(list + l);
+                    const T4 c = box_c[b];
+                    __syncwarp();
+                    for (int q2 = lane; q2 < NT * NB; q2 += 32) {
+                        const int t = q2 / NB, j = q2 - t * NB;
+                        sm[warp][q2] = j < nb ? mom[((int64_t)b * NT + t) * B + b0 + j] : zero4<T4>();
+                    }
+                    __syncwarp();
+                    m2p_one<T, P, NB>(q.x - c.x, q.y - c.y, q.z - c.z, sm[warp], a);
+                }
+                const int64_t ti = h ? t1 : t0;
+                if (ti < ntgt) {
+                    const int64_t tp = panel_of(q.w);
+#pragma unroll
+                    for (int j = 0; j < NB; ++j)
+                        if (j < nb) atomic_add4(acc + 4 * (tp * B + b0 + j), a[j][0], a[j][1], a[j][2], a[j][3]);
+                }
+            }
         }
-        if (t0 < ntgt) atomic_add4(acc + 4 * (int64_t)panel_of(q0.w), a0.vr, a0.vi, a0.kr, a0.ki);
-        if (t1 < ntgt) atomic_add4(acc + 4 * (int64_t)panel_of(q1.w), a1.vr, a1.vi, a1.kr, a1.ki);
         if (!DYNAMIC) return;
     }
 }
@@ -299,37 +410,39 @@ __constant__ float c_binom[kMaxP + 1][kMaxP + 1] = {
     {1, 3, 3, 1, 0, 0, 0, 0, 0},     {1, 4, 6, 4, 1, 0, 0, 0, 0},     {1, 5, 10, 10, 5, 1, 0, 0, 0},
     {1, 6, 15, 20, 15, 6, 1, 0, 0},  {1, 7, 21, 35, 35, 21, 7, 1, 0}, {1, 8, 28, 56, 70, 56, 28, 8, 1}};
 
-template <typename T, int P>
-__global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, const typename Vec4<T>::type *__restrict__ spos,
+// One block per work unit (leaf chunk, right-hand-side chunk), one thread per term k.
+// The chunk's moments about the leaf centre c are added to the leaf if some target block
+// accepted it, and shifted into every accepted ancestor a (upward pass folded in):
+//   M_k(a) = sum_{l <= k} C(k, l) (a - c)^(k - l) M_l(c),  C(k, l) = prod_d binom(k_d, l_d),
+// valid for both moment kinds since (a - y)^k = ((a - c) + (c - y))^k.
+template <typename T, int P, int NB>
+__global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B,
+                           const typename Vec4<T>::type *__restrict__ spos,
                            const typename Vec4<T>::type *__restrict__ snrm, const typename Vec4<T>::type *__restrict__ sw,
                            const typename Vec4<T>::type *__restrict__ box_c, const int *__restrict__ parent,
-                           const int *__restrict__ used, typename Vec4<T>::type *__restrict__ mom) {
+                           const int *__restrict__ used, typename MomAcc<T>::type *__restrict__ mom) {
+    using S = typename MomAcc<T>::scalar;
     using T4 = typename Vec4<T>::type;
     constexpr int NT = n_terms(P);
     __shared__ T pw[kP2MTile][3][P + 1];
-    __shared__ T4 lm[NT];
+    __shared__ T4 shn[kP2MTile];
+    __shared__ T4 shw[kP2MTile][NB];
+    __shared__ T4 lm[NT][NB];
     __shared__ T dpw[3][P + 1];
-    __shared__ T4 shn[kP2MTile], shw[kP2MTile];
-    const int64_t it = blockIdx.x;
-    if (it >= nitems) return;
-    const int4 item = items[it];
+    const int64_t u = blockIdx.x;
+    if (u >= nitems * nbc) return;
+    const int64_t ii = u / nbc;
+    const int b0 = (int)(u - ii * nbc) * NB, nb = min(NB, B - b0);
+    const int4 item = items[ii];
     const T4 c = box_c[item.x];
     const int t = threadIdx.x;
     int k1 = 0, k2 = 0, k3 = 0;
-    if (t < NT) {   // decode the multi-index of this thread
-        int n = 0;
-        while (n_terms(n) <= t) ++n;
-        int r = t - n_terms(n - 1);
-        int a = n;
-        while (r > n - a) {
-            r -= n - a + 1;
-            --a;
-        }
-        k1 = a;
-        k2 = n - a - r;
-        k3 = n - k1 - k2;
-    }
-    T vr = 0, vi = 0, kr = 0, ki = 0;
+    if (t < NT) mi_decode(t, k1, k2, k3);
+    T acc[NB][4];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][q] = T(0);
     for (int base = item.y; base < item.z; base += kP2MTile) {
         __syncthreads();
         const int cnt = min(kP2MTile, item.z - base);
@@ -344,39 +457,44 @@ __global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, const
                 }
             }
             shn[t] = snrm[base + t];
-            shw[t] = sw[base + t];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) shw[t][j] = j < nb ? sw[(int64_t)(base + t) * B + b0 + j] : zero4<T4>();
         }
         __syncthreads();
         if (t < NT) {
             for (int s = 0; s < cnt; ++s) {
                 const T px = pw[s][0][k1], py = pw[s][1][k2], pz = pw[s][2][k3];
                 const T mono = px * py * pz;
-                const T4 n = shn[s], w = shw[s];
+                const T4 n = shn[s];
                 T dm = 0;
                 if (k1) dm += n.x * T(k1) * pw[s][0][k1 - 1] * py * pz;
                 if (k2) dm += n.y * T(k2) * px * pw[s][1][k2 - 1] * pz;
                 if (k3) dm += n.z * T(k3) * px * py * pw[s][2][k3 - 1];
-                vr += w.x * mono;
-                vi += w.y * mono;
-                kr -= w.z * dm;
-                ki -= w.w * dm;
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const T4 w = shw[s][j];
+                    acc[j][0] += w.x * mono;
+                    acc[j][1] += w.y * mono;
+                    acc[j][2] -= w.z * dm;
+                    acc[j][3] -= w.w * dm;
+                }
             }
         }
     }
-    // the chunk's moments about its leaf centre: added to the leaf if it is accepted by some
-    // target block, and shifted into every accepted ancestor (upward pass folded in):
-    //   M_k(a) = sum_{l <= k} C(k, l) (a - c)^(k - l) M_l(c),  C(k, l) = prod_d binom(k_d, l_d),
-    // valid for both moment kinds since (a - y)^k = ((a - c) + (c - y))^k.
     if (t < NT) {
-        T4 o;
-        o.x = vr; o.y = vi; o.z = kr; o.w = ki;
-        lm[t] = o;
-        if (used[item.x]) {
-            T *g = (T *)(mom + (int64_t)item.x * NT + t);
-            atomicAdd(g + 0, vr);
-            atomicAdd(g + 1, vi);
-            atomicAdd(g + 2, kr);
-            atomicAdd(g + 3, ki);
+        const bool own = used[item.x] != 0;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            T4 o;
+            o.x = acc[j][0]; o.y = acc[j][1]; o.z = acc[j][2]; o.w = acc[j][3];
+            lm[t][j] = o;
+            if (own && j < nb) {
+                S *g = (S *)(mom + ((int64_t)item.x * NT + t) * B + b0 + j);
+                acc_add(g + 0, acc[j][0]);
+                acc_add(g + 1, acc[j][1]);
+                acc_add(g + 2, acc[j][2]);
+                acc_add(g + 3, acc[j][3]);
+            }
         }
     }
     for (int A = parent[item.x]; A >= 0; A = parent[A]) {
@@ -393,44 +511,96 @@ __global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, const
         }
         __syncthreads();
         if (t < NT) {
-            T sr = 0, si = 0, skr = 0, ski = 0;
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[j][q] = T(0);
             for (int l1 = 0; l1 <= k1; ++l1)
                 for (int l2 = 0; l2 <= k2; ++l2)
                     for (int l3 = 0; l3 <= k3; ++l3) {
                         const T coef = T(c_binom[k1][l1] * c_binom[k2][l2] * c_binom[k3][l3]) * dpw[0][k1 - l1] *
                                        dpw[1][k2 - l2] * dpw[2][k3 - l3];
-                        const T4 m = lm[mi_index(l1, l2, l3)];
-                        sr += coef * m.x;
-                        si += coef * m.y;
-                        skr += coef * m.z;
-                        ski += coef * m.w;
+                        const int li = mi_index(l1, l2, l3);
+#pragma unroll
+                        for (int j = 0; j < NB; ++j) {
+                            const T4 m = lm[li][j];
+                            acc[j][0] += coef * m.x;
+                            acc[j][1] += coef * m.y;
+                            acc[j][2] += coef * m.z;
+                            acc[j][3] += coef * m.w;
+                        }
                     }
-            T *g = (T *)(mom + (int64_t)A * NT + t);
-            atomicAdd(g + 0, sr);
-            atomicAdd(g + 1, si);
-            atomicAdd(g + 2, skr);
-            atomicAdd(g + 3, ski);
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                if (j >= nb) break;
+                S *g = (S *)(mom + ((int64_t)A * NT + t) * B + b0 + j);
+                acc_add(g + 0, acc[j][0]);
+                acc_add(g + 1, acc[j][1]);
+                acc_add(g + 2, acc[j][2]);
+                acc_add(g + 3, acc[j][3]);
+            }
         }
     }
 }
 
+// FP64 -> float-float copies (moments accumulated in FP64, geometry)
+__global__ void to_ff_kernel(int64_t n, const dbl4 *__restrict__ a, ff4 *__restrict__ b, int id_in_w) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const dbl4 v = a[i];
+    ff4 o;
+    o.x = ffloat(v.x);
+    o.y = ffloat(v.y);
+    o.z = ffloat(v.z);
+    o.w = id_in_w ? ffloat(__int_as_float((int)v.w), 0.f) : ffloat(v.w);
+    b[i] = o;
+}
+
 // --------------------------------------------------------------- launchers
-int launch_weights(lspr_ctx *ctx, bool fp64, const double2 *x, int64_t N) {
+int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, int64_t N, int B) {
     const int64_t Ns = ctx->mesh.Ns;
+    const unsigned grid = grid_for(Ns * B, 256);
     cudaEvent_t ev;
     timer_begin(ctx, T_WEIGHTS, &ev);
-    if (fp64) {
-        LSPR_TRY(ctx, ctx->w64.ensure(Ns));
-        ++ctx->n_launches;
-        weights_kernel<dbl4><<<grid_for(Ns, 256), 256, 0, ctx->stream>>>(Ns, N, ctx->wo.spos64.p,
-                                                                            ctx->wo.src_panel.p, x, ctx->w64.p);
+    ++ctx->n_launches;
+    if (prec == PREC_F64) {
+        LSPR_TRY(ctx, ctx->w64.ensure(Ns * B));
+        weights_kernel<dbl4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x,
+                                                            ctx->w64.p);
+    } else if (prec == PREC_FF) {
+        LSPR_TRY(ctx, ctx->w_ff.ensure(Ns * B));
+        weights_kernel<ff4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x,
+                                                           ctx->w_ff.p);
     } else {
-        LSPR_TRY(ctx, ctx->w32.ensure(Ns));
-        ++ctx->n_launches;
-        weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, ctx->stream>>>(Ns, N, ctx->wo.spos64.p,
-                                                                           ctx->wo.src_panel.p, x, ctx->w32.p);
+        LSPR_TRY(ctx, ctx->w32.ensure(Ns * B));
+        weights_kernel<float4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x,
+                                                              ctx->w32.p);
     }
     timer_end(ctx, T_WEIGHTS, ev);
+    LSPR_TRY(ctx, cudaGetLastError());
+    return LSPR_OK;
+}
+
+// float-float copies of the work-order geometry (after every change of work order)
+int launch_ff_geometry(lspr_ctx *ctx) {
+    const Mesh &m = ctx->mesh;
+    WorkOrder &w = ctx->wo;
+    LSPR_TRY(ctx, w.spos_ff.ensure(m.Ns));
+    LSPR_TRY(ctx, w.snrm_ff.ensure(m.Ns));
+    LSPR_TRY(ctx, w.tgt_ff.ensure(m.N));
+    ctx->n_launches += 3;
+    to_ff_kernel<<<grid_for(m.Ns, 256), 256, 0, ctx->stream>>>(m.Ns, w.spos64.p, w.spos_ff.p, 0);
+    to_ff_kernel<<<grid_for(m.Ns, 256), 256, 0, ctx->stream>>>(m.Ns, w.snrm64.p, w.snrm_ff.p, 1);
+    to_ff_kernel<<<grid_for(m.N, 256), 256, 0, ctx->stream>>>(m.N, w.tgt64.p, w.tgt_ff.p, 1);
+    LSPR_TRY(ctx, cudaGetLastError());
+    return LSPR_OK;
+}
+
+int launch_ff_boxes(lspr_ctx *ctx) {
+    Tree &tr = ctx->tree;
+    LSPR_TRY(ctx, tr.box_c_ff.ensure(tr.nboxes));
+    ++ctx->n_launches;
+    to_ff_kernel<<<grid_for(tr.nboxes, 256), 256, 0, ctx->stream>>>(tr.nboxes, tr.box_c64.p, tr.box_c_ff.p, 0);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
@@ -447,26 +617,67 @@ static unsigned persistent_grid(lspr_ctx *ctx, K kernel, int threads, int *cache
     return (unsigned)(*cache * std::max(1, ctx->num_sms));
 }
 
-int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, double *acc, cudaStream_t st,
-               int *counter) {
+// per-precision views of the context's geometry and scratch
+template <typename T> struct Views;
+template <> struct Views<float> {
+    static const float4 *tgt(lspr_ctx *c) { return c->wo.tgt32.p; }
+    static const float4 *spos(lspr_ctx *c) { return c->wo.spos32.p; }
+    static const float4 *snrm(lspr_ctx *c) { return c->wo.snrm32.p; }
+    static const float4 *w(lspr_ctx *c) { return c->w32.p; }
+    static const float4 *bc(lspr_ctx *c) { return c->tree.box_c32.p; }
+    static const float4 *mom(lspr_ctx *c) { return c->tree.mom32.p; }
+    static float4 *mom_acc(lspr_ctx *c) { return c->tree.mom32.p; }
+};
+template <> struct Views<double> {
+    static const dbl4 *tgt(lspr_ctx *c) { return c->wo.tgt64.p; }
+    static const dbl4 *spos(lspr_ctx *c) { return c->wo.spos64.p; }
+    static const dbl4 *snrm(lspr_ctx *c) { return c->wo.snrm64.p; }
+    static const dbl4 *w(lspr_ctx *c) { return c->w64.p; }
+    static const dbl4 *bc(lspr_ctx *c) { return c->tree.box_c64.p; }
+    static const dbl4 *mom(lspr_ctx *c) { return c->tree.mom64.p; }
+    static dbl4 *mom_acc(lspr_ctx *c) { return c->tree.mom64.p; }
+};
+template <> struct Views<ffloat> {
+    static const ff4 *tgt(lspr_ctx *c) { return c->wo.tgt_ff.p; }
+    static const ff4 *spos(lspr_ctx *c) { return c->wo.spos_ff.p; }
+    static const ff4 *snrm(lspr_ctx *c) { return c->wo.snrm_ff.p; }
+    static const ff4 *w(lspr_ctx *c) { return c->w_ff.p; }
+    static const ff4 *bc(lspr_ctx *c) { return c->tree.box_c_ff.p; }
+    static const ff4 *mom(lspr_ctx *c) { return c->tree.mom_ff.p; }
+    static dbl4 *mom_acc(lspr_ctx *c) { return c->tree.mom64.p; }
+};
+
+template <typename T, int NB>
+static void p2p_launch(lspr_ctx *ctx, const int4 *items, int64_t nitems, int B, double *acc, cudaStream_t st,
+                       int *counter) {
+    static int occ = 0;
+    constexpr int W = p2p_warps(NB);
+    const int nbc = (B + NB - 1) / NB;
+    const unsigned grid = std::min<unsigned>(grid_for(nitems * nbc, W),
+                                             persistent_grid(ctx, p2p_kernel<T, NB, true>, W * 32, &occ));
+    p2p_kernel<T, NB, true><<<grid, W * 32, 0, st>>>(items, nitems, nbc, B, Views<T>::tgt(ctx), ctx->mesh.N,
+                                                      Views<T>::spos(ctx), Views<T>::snrm(ctx), Views<T>::w(ctx),
+                                                      acc, counter);
+}
+
+static int slot_of(int prec, int f32, int f64, int ff) { return prec == PREC_F64 ? f64 : (prec == PREC_FF ? ff : f32); }
+
+int launch_p2p(lspr_ctx *ctx, int prec, const int4 *items, int64_t nitems, double *acc, cudaStream_t st,
+               int *counter, int B) {
     if (nitems == 0) return LSPR_OK;
-    static int occ32 = 0, occ64 = 0;
     cudaEvent_t ev;
-    const int slot = fp64 ? T_P2P64 : T_P2P;
+    const int slot = slot_of(prec, T_P2P, T_P2P64, T_P2PFF);
     timer_begin_on(ctx, slot, &ev, st);
     ++ctx->n_launches;
-    if (fp64) {
-        const unsigned grid = std::min<unsigned>(grid_for(nitems, kP2PWarps),
-                                                 persistent_grid(ctx, p2p_kernel<double, true>, kP2PWarps * 32, &occ64));
-        p2p_kernel<double, true><<<grid, kP2PWarps * 32, 0, st>>>(items, nitems, ctx->wo.tgt64.p, ctx->mesh.N,
-                                                                  ctx->wo.spos64.p, ctx->wo.snrm64.p, ctx->w64.p, acc,
-                                                                  counter);
+    if (prec == PREC_F64) {
+        if (B == 1) p2p_launch<double, 1>(ctx, items, nitems, B, acc, st, counter);
+        else p2p_launch<double, batch_chunk<double>(2)>(ctx, items, nitems, B, acc, st, counter);
+    } else if (prec == PREC_FF) {
+        if (B == 1) p2p_launch<ffloat, 1>(ctx, items, nitems, B, acc, st, counter);
+        else p2p_launch<ffloat, batch_chunk<ffloat>(2)>(ctx, items, nitems, B, acc, st, counter);
     } else {
-        const unsigned grid = std::min<unsigned>(grid_for(nitems, kP2PWarps),
-                                                 persistent_grid(ctx, p2p_kernel<float, true>, kP2PWarps * 32, &occ32));
-        p2p_kernel<float, true><<<grid, kP2PWarps * 32, 0, st>>>(items, nitems, ctx->wo.tgt32.p, ctx->mesh.N,
-                                                                 ctx->wo.spos32.p, ctx->wo.snrm32.p, ctx->w32.p, acc,
-                                                                 counter);
+        if (B == 1) p2p_launch<float, 1>(ctx, items, nitems, B, acc, st, counter);
+        else p2p_launch<float, batch_chunk<float>(2)>(ctx, items, nitems, B, acc, st, counter);
     }
     timer_end_on(ctx, slot, ev, st);
     LSPR_TRY(ctx, cudaGetLastError());
@@ -481,106 +692,107 @@ int launch_item_flags(lspr_ctx *ctx, int4 *items, int64_t nitems) {
     return LSPR_OK;
 }
 
-template <typename T, int P>
-static void p2m_launch(lspr_ctx *ctx) {
-    using T4 = typename Vec4<T>::type;
+template <typename T, int P, int NB>
+static void p2m_launch(lspr_ctx *ctx, int B) {
     Tree &tr = ctx->tree;
     const int threads = ((n_terms(P) + 31) / 32) * 32;
-    const T4 *spos, *snrm, *w, *bc;
-    T4 *mom;
-    if constexpr (sizeof(T) == 8) {
-        spos = ctx->wo.spos64.p; snrm = ctx->wo.snrm64.p; w = ctx->w64.p; bc = tr.box_c64.p; mom = tr.mom64.p;
-    } else {
-        spos = ctx->wo.spos32.p; snrm = ctx->wo.snrm32.p; w = ctx->w32.p; bc = tr.box_c32.p; mom = tr.mom32.p;
-    }
-    ++ctx->n_launches;
-    p2m_kernel<T, P><<<(unsigned)tr.n_p2m_items, threads, 0, ctx->stream>>>(tr.p2m_items.p, tr.n_p2m_items, spos, snrm,
-                                                                           w, bc, tr.box_parent.p, tr.box_used.p, mom);
+    const int nbc = (B + NB - 1) / NB;
+    p2m_kernel<T, P, NB><<<(unsigned)(tr.n_p2m_items * nbc), threads, 0, ctx->stream>>>(
+        tr.p2m_items.p, tr.n_p2m_items, nbc, B, Views<T>::spos(ctx), Views<T>::snrm(ctx), Views<T>::w(ctx),
+        Views<T>::bc(ctx), tr.box_parent.p, tr.box_used.p, Views<T>::mom_acc(ctx));
 }
 
-template <typename T, int P>
-static void m2p_launch(lspr_ctx *ctx, double *acc, int *counter) {
-    using T4 = typename Vec4<T>::type;
+template <typename T, int P, int NB>
+static void m2p_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     static int occ = 0;
     Tree &tr = ctx->tree;
-    const T4 *tgt, *bc, *mom;
-    if constexpr (sizeof(T) == 8) {
-        tgt = ctx->wo.tgt64.p; bc = tr.box_c64.p; mom = tr.mom64.p;
-    } else {
-        tgt = ctx->wo.tgt32.p; bc = tr.box_c32.p; mom = tr.mom32.p;
-    }
-    const unsigned grid = std::min<unsigned>(grid_for(tr.n_m2p_items, kM2PWarps),
-                                             persistent_grid(ctx, m2p_kernel<T, P, true>, kM2PWarps * 32, &occ));
-    m2p_kernel<T, P, true><<<grid, kM2PWarps * 32, 0, ctx->stream>>>(tr.m2p_items.p, tr.n_m2p_items, tgt, ctx->mesh.N,
-                                                                    tr.m2p_list.p, bc, mom, acc, counter);
+    constexpr int W = m2p_warps<T, P, NB>();
+    const int nbc = (B + NB - 1) / NB;
+    const unsigned grid = std::min<unsigned>(grid_for(tr.n_m2p_items * nbc, W),
+                                             persistent_grid(ctx, m2p_kernel<T, P, NB, true>, W * 32, &occ));
+    m2p_kernel<T, P, NB, true><<<grid, W * 32, 0, ctx->stream>>>(tr.m2p_items.p, tr.n_m2p_items, nbc, B,
+                                                                  Views<T>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p,
+                                                                  Views<T>::bc(ctx), Views<T>::mom(ctx), acc, counter);
 }
 
-#define LSPR_DISPATCH_P(FN, T, ...)           \
-    switch (ctx->tree.P) {                    \
-    case 1: FN<T, 1>(__VA_ARGS__); break;     \
-    case 2: FN<T, 2>(__VA_ARGS__); break;     \
-    case 3: FN<T, 3>(__VA_ARGS__); break;     \
-    case 4: FN<T, 4>(__VA_ARGS__); break;     \
-    case 5: FN<T, 5>(__VA_ARGS__); break;     \
-    case 6: FN<T, 6>(__VA_ARGS__); break;     \
-    case 7: FN<T, 7>(__VA_ARGS__); break;     \
-    case 8: FN<T, 8>(__VA_ARGS__); break;     \
-    default: return LSPR_E_ARG;               \
-    }
+// dispatch over the compiled Taylor orders and over single / chunked right-hand sides
+#define LSPR_DISPATCH_P(FN, T, B, ...)                                                      \
+    do {                                                                                    \
+        constexpr int NBB = batch_chunk<T>(2);                                              \
+        switch (ctx->tree.P) {                                                              \
+        case 1: if ((B) == 1) FN<T, 1, 1>(__VA_ARGS__); else FN<T, 1, NBB>(__VA_ARGS__); break; \
+        case 2: if ((B) == 1) FN<T, 2, 1>(__VA_ARGS__); else FN<T, 2, NBB>(__VA_ARGS__); break; \
+        case 3: if ((B) == 1) FN<T, 3, 1>(__VA_ARGS__); else FN<T, 3, NBB>(__VA_ARGS__); break; \
+        case 4: if ((B) == 1) FN<T, 4, 1>(__VA_ARGS__); else FN<T, 4, NBB>(__VA_ARGS__); break; \
+        case 5: if ((B) == 1) FN<T, 5, 1>(__VA_ARGS__); else FN<T, 5, NBB>(__VA_ARGS__); break; \
+        case 6: if ((B) == 1) FN<T, 6, 1>(__VA_ARGS__); else FN<T, 6, NBB>(__VA_ARGS__); break; \
+        case 7: if ((B) == 1) FN<T, 7, 1>(__VA_ARGS__); else FN<T, 7, NBB>(__VA_ARGS__); break; \
+        case 8: if ((B) == 1) FN<T, 8, 1>(__VA_ARGS__); else FN<T, 8, NBB>(__VA_ARGS__); break; \
+        default: return LSPR_E_ARG;                                                         \
+        }                                                                                   \
+    } while (0)
 
-int launch_p2m(lspr_ctx *ctx, bool fp64) {
+int launch_p2m(lspr_ctx *ctx, int prec, int B) {
     Tree &tr = ctx->tree;
     if (tr.n_p2m_items == 0) return LSPR_OK;
+    const int64_t nm = tr.nboxes * tr.NT * B;
     cudaEvent_t ev;
-    const int slot = fp64 ? T_P2M64 : T_P2M;
+    const int slot = slot_of(prec, T_P2M, T_P2M64, T_P2MFF);
     timer_begin(ctx, slot, &ev);
-    if (fp64) {
-        LSPR_TRY(ctx, tr.mom64.ensure(tr.nboxes * tr.NT));
-        LSPR_TRY(ctx, cudaMemsetAsync(tr.mom64.p, 0, sizeof(dbl4) * tr.nboxes * tr.NT, ctx->stream));
-        LSPR_DISPATCH_P(p2m_launch, double, ctx);
+    ++ctx->n_launches;
+    if (prec == PREC_F32) {
+        LSPR_TRY(ctx, tr.mom32.ensure(nm));
+        LSPR_TRY(ctx, cudaMemsetAsync(tr.mom32.p, 0, sizeof(float4) * nm, ctx->stream));
+        LSPR_DISPATCH_P(p2m_launch, float, B, ctx, B);
     } else {
-        LSPR_TRY(ctx, tr.mom32.ensure(tr.nboxes * tr.NT));
-        LSPR_TRY(ctx, cudaMemsetAsync(tr.mom32.p, 0, sizeof(float4) * tr.nboxes * tr.NT, ctx->stream));
-        LSPR_DISPATCH_P(p2m_launch, float, ctx);
+        LSPR_TRY(ctx, tr.mom64.ensure(nm));
+        LSPR_TRY(ctx, cudaMemsetAsync(tr.mom64.p, 0, sizeof(dbl4) * nm, ctx->stream));
+        if (prec == PREC_F64) {
+            LSPR_DISPATCH_P(p2m_launch, double, B, ctx, B);
+        } else {
+            LSPR_DISPATCH_P(p2m_launch, ffloat, B, ctx, B);
+            LSPR_TRY(ctx, tr.mom_ff.ensure(nm));
+            ++ctx->n_launches;
+            to_ff_kernel<<<grid_for(nm, 256), 256, 0, ctx->stream>>>(nm, tr.mom64.p, tr.mom_ff.p, 0);
+        }
     }
     timer_end(ctx, slot, ev);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
 
-int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc, int *counter) {
+int launch_m2p(lspr_ctx *ctx, int prec, double *acc, int *counter, int B) {
     Tree &tr = ctx->tree;
     if (tr.n_m2p_items == 0) return LSPR_OK;
     cudaEvent_t ev;
-    const int slot = fp64 ? T_M2P64 : T_M2P;
+    const int slot = slot_of(prec, T_M2P, T_M2P64, T_M2PFF);
     timer_begin(ctx, slot, &ev);
-    if (fp64) {
-        LSPR_DISPATCH_P(m2p_launch, double, ctx, acc, counter);
+    ++ctx->n_launches;
+    if (prec == PREC_F64) {
+        LSPR_DISPATCH_P(m2p_launch, double, B, ctx, acc, counter, B);
+    } else if (prec == PREC_FF) {
+        LSPR_DISPATCH_P(m2p_launch, ffloat, B, ctx, acc, counter, B);
     } else {
-        LSPR_DISPATCH_P(m2p_launch, float, ctx, acc, counter);
+        LSPR_DISPATCH_P(m2p_launch, float, B, ctx, acc, counter, B);
     }
     timer_end(ctx, slot, ev);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
 
-}  // namespace lspr
-
-namespace lspr {
-
-// Launchers on explicit buffers (no context-owned scratch): used by the
-// allocation-free matvec entry point.
+// Launchers on explicit buffers (no context-owned scratch), one right-hand side: used
+// by the allocation-free matvec entry point.
 int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
                             const double2 *x, float4 *w) {
-    weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, st>>>(Ns, N, spos64, src_panel, x, w);
+    weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, st>>>(Ns, N, 1, spos64, src_panel, x, w);
     return cudaGetLastError() == cudaSuccess ? LSPR_OK : LSPR_E_CUDA;
 }
 
 int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, const float4 *tgt, int64_t ntgt,
                         const float4 *spos, const float4 *snrm, const float4 *w, double *acc) {
     if (nitems == 0) return LSPR_OK;
-    p2p_kernel<float, false><<<grid_for(nitems, kP2PWarps), kP2PWarps * 32, 0, st>>>(items, nitems, tgt, ntgt, spos,
-                                                                                    snrm, w, acc, nullptr);
+    p2p_kernel<float, 1, false><<<grid_for(nitems, p2p_warps(1)), p2p_warps(1) * 32, 0, st>>>(
+        items, nitems, 1, 1, tgt, ntgt, spos, snrm, w, acc, nullptr);
     return cudaGetLastError() == cudaSuccess ? LSPR_OK : LSPR_E_CUDA;
 }
 

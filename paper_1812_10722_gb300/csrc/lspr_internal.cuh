@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "ffloat.cuh"
 #include "lspr.h"
 
 // 32-byte aligned four-double vector (CUDA's double4 is deprecated)
@@ -26,6 +27,15 @@ struct __align__(32) dbl4 {
 __host__ __device__ inline dbl4 make_dbl4(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
 
 namespace lspr {
+
+// arithmetic of the far-field kernels
+enum Prec { PREC_F32 = 0, PREC_F64 = 1, PREC_FF = 2 };
+inline int mode_prec(int mode) {
+    return (mode == LSPR_DIRECT_FP64 || mode == LSPR_TREE_FP64) ? PREC_F64
+           : (mode == LSPR_DIRECT_FF || mode == LSPR_TREE_FF)   ? PREC_FF
+                                                                : PREC_F32;
+}
+inline bool mode_tree(int mode) { return mode == LSPR_TREE_FP64 || mode == LSPR_TREE_FP32 || mode == LSPR_TREE_FF; }
 
 constexpr double kInv4Pi = 0.079577471545947667884;   // 1 / (4 pi)
 constexpr int kTargetBlock = 64;                       // targets per interaction block (2 per lane)
@@ -84,6 +94,7 @@ struct WorkOrder {   // sources/targets in the order the far-field kernels walk 
     DArr<float4> tgt32;
     DArr<int> src_panel;   // [Ns]
     DArr<int> tgt_panel;   // [N]
+    DArr<ff4> spos_ff, snrm_ff, tgt_ff;   // float-float copies
     DArr<int> tgt_pos;     // [N] work-order position of each panel's target
     DArr<int> src_tblock;  // [Ns] target block holding the source's own panel
 };
@@ -108,7 +119,8 @@ struct Tree {
     DArr<int> box_parent;    // parent box (-1 for the root)
     // moments [box][NT] x (Vre, Vim, Kre, Kim)
     DArr<float4> mom32;
-    DArr<dbl4> mom64;
+    DArr<dbl4> mom64;        // FP64 moments; also the accumulation buffer of the float-float ones
+    DArr<ff4> mom_ff, box_c_ff;
 };
 
 struct DirectItems {
@@ -116,7 +128,7 @@ struct DirectItems {
     DArr<int4> items;
 };
 
-constexpr int kTimerSlots = 12;
+constexpr int kTimerSlots = 16;
 
 struct Timing {
     bool enabled = false;
@@ -129,7 +141,7 @@ struct Timing {
 
 enum TimerSlot {
     T_P2P = 0, T_M2P = 1, T_P2M = 2, T_NEAR = 3, T_GMRES = 4, T_TREE = 5, T_MESH = 6, T_OTHER = 7,
-    T_P2P64 = 8, T_M2P64 = 9, T_P2M64 = 10, T_WEIGHTS = 11
+    T_P2P64 = 8, T_M2P64 = 9, T_P2M64 = 10, T_WEIGHTS = 11, T_P2PFF = 12, T_M2PFF = 13, T_P2MFF = 14
 };
 
 }  // namespace lspr
@@ -150,6 +162,7 @@ struct lspr_ctx {
     lspr::DArr<double> acc;            // [B][N][4]: V re/im, K re/im (far part)
     lspr::DArr<float4> w32;            // [Ns] source weights
     lspr::DArr<dbl4> w64;
+    lspr::DArr<ff4> w_ff;
     lspr::DArr<double2> xbuf, ybuf;    // staging for host matvec
     lspr::DArr<double2> sbuf;
     // solver scratch
@@ -213,13 +226,17 @@ __device__ __forceinline__ unsigned spread10(unsigned v) {
 
 // ------------------------------------------------------------ farfield.cu
 // accumulate far parts (coarse rule everywhere except own panel) into acc[N][4]
-int launch_p2p(lspr_ctx *ctx, bool fp64, const int4 *items, int64_t nitems, double *acc, cudaStream_t st,
-               int *counter);
-int launch_p2m(lspr_ctx *ctx, bool fp64);
-int launch_m2p(lspr_ctx *ctx, bool fp64, double *acc, int *counter);
+// B right-hand sides: weights [source][B], accumulators acc [panel][B][4]
+int launch_p2p(lspr_ctx *ctx, int prec, const int4 *items, int64_t nitems, double *acc, cudaStream_t st,
+               int *counter, int B);
+int launch_p2m(lspr_ctx *ctx, int prec, int B);
+int launch_m2p(lspr_ctx *ctx, int prec, double *acc, int *counter, int B);
+// float-float copies of the work-order geometry / box centres
+int launch_ff_geometry(lspr_ctx *ctx);
+int launch_ff_boxes(lspr_ctx *ctx);
 // item.w = 1 where a P2P item may contain sources of its own target block's panels
 int launch_item_flags(lspr_ctx *ctx, int4 *items, int64_t nitems);
-int launch_weights(lspr_ctx *ctx, bool fp64, const double2 *x, int64_t N);
+int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, int64_t N, int B);
 int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
                             const double2 *x, float4 *w);
 int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, const float4 *tgt, int64_t ntgt,

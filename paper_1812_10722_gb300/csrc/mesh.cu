@@ -259,10 +259,11 @@ __device__ __forceinline__ unsigned cell_key(int ix, int iy, int iz) {
 }
 
 __global__ void cell_key_kernel(int64_t N, const double *__restrict__ cx, const double *__restrict__ cy,
-                                const double *__restrict__ cz, const double *grid /* lo[3], 1/h */, unsigned *keys,
-                                int *vals) {
+                                const double *__restrict__ cz, const double *__restrict__ L, double thr,
+                                const double *grid /* lo[3], 1/h */, unsigned *keys, int *vals, float4 *cf) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
+    cf[i] = make_float4((float)cx[i], (float)cy[i], (float)cz[i], (float)(L[i] / thr));
     keys[i] = cell_key(cell_coord(cx[i], grid[0], grid[3]), cell_coord(cy[i], grid[1], grid[3]),
                        cell_coord(cz[i], grid[2], grid[3]));
     vals[i] = (int)i;
@@ -278,17 +279,35 @@ __device__ __forceinline__ int lower_bound_u(const unsigned *a, int n, unsigned 
     return lo;
 }
 
+// Near decision from FP32 copies when the FP32 distance is clearly inside or outside
+// L_j/threshold, else the exact FP64 test.  band bounds |d32 - d| + |r32 - r|: FP32
+// rounding of the coordinates (2^-24 |c| each) and of the arithmetic.
+__device__ __forceinline__ bool near_decide(const float4 &fi, const float4 &fj, float band, double xi, double yi,
+                                            double zi, int j, const double *__restrict__ cx,
+                                            const double *__restrict__ cy, const double *__restrict__ cz,
+                                            const double *__restrict__ L, double thr) {
+    const float dx = fi.x - fj.x, dy = fi.y - fj.y, dz = fi.z - fj.z;
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    const float r = fj.w, lo = fmaxf(r - band, 0.f), hi = r + band;
+    if (d2 < lo * lo) return true;
+    if (d2 > hi * hi) return false;
+    return near_exact(xi, yi, zi, cx[j], cy[j], cz[j], L[j], thr);
+}
+
 // One warp per target: lane c < 27 searches neighbour cell c and tests its panels; the
 // row is laid out as the self entry, then the hits of cell 0, 1, ... in sorted order.
 template <bool FILL>
 __global__ void near_cells_kernel(int64_t N, const double *__restrict__ cx, const double *__restrict__ cy,
                                   const double *__restrict__ cz, const double *__restrict__ L, double thr,
                                   const double *grid, const unsigned *__restrict__ skeys, const int *__restrict__ sidx,
-                                  int64_t *count, const int64_t *ptr, int *col, int *row) {
+                                  const float4 *__restrict__ cf, int64_t *count, const int64_t *ptr, int *col,
+                                  int *row) {
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (i >= N) return;
     const double xi = cx[i], yi = cy[i], zi = cz[i];
+    const float4 fi = cf[i];
+    const float cmax = (float)grid[4];
     const int ix = cell_coord(xi, grid[0], grid[3]), iy = cell_coord(yi, grid[1], grid[3]),
               iz = cell_coord(zi, grid[2], grid[3]);
     int k0 = 0, k1 = 0;
@@ -304,7 +323,9 @@ __global__ void near_cells_kernel(int64_t N, const double *__restrict__ cx, cons
     int c = 0;
     for (int k = k0; k < k1; ++k) {
         const int j = sidx[k];
-        c += (j != i && near_exact(xi, yi, zi, cx[j], cy[j], cz[j], L[j], thr));
+        if (j == i) continue;
+        const float4 fj = cf[j];
+        c += near_decide(fi, fj, 1e-6f * fj.w + 5e-7f * cmax, xi, yi, zi, j, cx, cy, cz, L, thr);
     }
     // inclusive warp scan of the per-lane hit counts
     int inc = c;
@@ -325,7 +346,9 @@ __global__ void near_cells_kernel(int64_t N, const double *__restrict__ cx, cons
     out += 1 + (inc - c);
     for (int k = k0; k < k1; ++k) {
         const int j = sidx[k];
-        if (j != i && near_exact(xi, yi, zi, cx[j], cy[j], cz[j], L[j], thr)) {
+        if (j == i) continue;
+        const float4 fj = cf[j];
+        if (near_decide(fi, fj, 1e-6f * fj.w + 5e-7f * cmax, xi, yi, zi, j, cx, cy, cz, L, thr)) {
             col[out] = j;
             row[out] = (int)i;
             ++out;
@@ -500,7 +523,7 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     DArr<int64_t> cnt;
     LSPR_TRY(ctx, cnt.ensure(N));
     LSPR_TRY(ctx, m.near_ptr.ensure(N + 1));
-    double hgrid[4];
+    double hgrid[5];
     {
         std::vector<double> hc(3 * N);
         // bounding box of the centroids (host copy of three N-vectors, once per geometry)
@@ -520,11 +543,16 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
         hgrid[1] = lo[1];
         hgrid[2] = lo[2];
         hgrid[3] = 1.0 / h;
+        hgrid[4] = std::max(std::max(std::fabs(lo[0]), std::fabs(hi[0])),
+                            std::max(std::max(std::fabs(lo[1]), std::fabs(hi[1])),
+                                     std::max(std::fabs(lo[2]), std::fabs(hi[2]))));
     }
     DArr<double> grid;
     DArr<unsigned> keys, ktmp;
     DArr<int> vals, vtmp, hist, offs;
-    LSPR_TRY(ctx, grid.ensure(4));
+    LSPR_TRY(ctx, grid.ensure(5));
+    DArr<float4> cf;
+    LSPR_TRY(ctx, cf.ensure(N));
     LSPR_TRY(ctx, keys.ensure(N));
     LSPR_TRY(ctx, ktmp.ensure(N));
     LSPR_TRY(ctx, vals.ensure(N));
@@ -533,11 +561,12 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     LSPR_TRY(ctx, offs.ensure(radix_sort_scratch_ints(N)));
     LSPR_TRY(ctx, cudaMemcpyAsync(grid.p, hgrid, sizeof(hgrid), cudaMemcpyHostToDevice, st));
     ++ctx->n_launches;
-    cell_key_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, grid.p, keys.p, vals.p);
+    cell_key_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, grid.p, keys.p,
+                                                      vals.p, cf.p);
     LSPR_TRY_ST(radix_sort(ctx, keys.p, vals.p, ktmp.p, vtmp.p, N, 30, hist.p, offs.p));
     ++ctx->n_launches;
     near_cells_kernel<false><<<grid_for(N * 32, 128), 128, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, grid.p,
-                                                               keys.p, vals.p, cnt.p, nullptr, nullptr, nullptr);
+                                                               keys.p, vals.p, cf.p, cnt.p, nullptr, nullptr, nullptr);
     ++ctx->n_launches;
     scan_kernel<<<1, 1024, 0, st>>>(cnt.p, N, m.near_ptr.p);
     LSPR_TRY(ctx, cudaGetLastError());
@@ -550,7 +579,7 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     LSPR_TRY(ctx, rowidx.ensure(m.nnz));
     ++ctx->n_launches;
     near_cells_kernel<true><<<grid_for(N * 32, 128), 128, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, grid.p,
-                                                              keys.p, vals.p, nullptr, m.near_ptr.p, m.near_col.p,
+                                                              keys.p, vals.p, cf.p, nullptr, m.near_ptr.p, m.near_col.p,
                                                               rowidx.p);
     ++ctx->n_launches;
     near_values_kernel<<<grid_for(m.nnz, 128), 128, 0, st>>>(m.nnz, rowidx.p, m.near_col.p, m.verts.p, m.tris.p,
@@ -564,6 +593,7 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     for (auto *a : {&keys, &ktmp}) a->release();
     for (auto *a : {&vals, &vtmp, &hist, &offs}) a->release();
     grid.release();
+    cf.release();
     m.ready = true;
     return workorder_natural(ctx);
 }
@@ -605,6 +635,7 @@ int workorder_natural(lspr_ctx *ctx) {
     ++ctx->n_launches;
     direct_items_kernel<<<grid_for(ctx->direct.n, 256), 256, 0, st>>>(ctx->direct.items.p, ntb, nch, chunk, m.Ns);
     LSPR_TRY_ST(launch_item_flags(ctx, ctx->direct.items.p, ctx->direct.n));
+    LSPR_TRY_ST(launch_ff_geometry(ctx));
     LSPR_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return LSPR_OK;
 }

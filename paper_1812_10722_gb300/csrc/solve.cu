@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <complex>
 
 #include "lspr_internal.cuh"
 
@@ -42,27 +43,32 @@ __device__ __forceinline__ double2 csqrt_p(double2 z) {
 
 // ------------------------------------------------------------------ assembly
 // RAW = true writes the layer potentials (V dphi, K phi) instead of the block rows.
-// kRowLanes lanes per row read the row's near entries coalesced (rows hold ~25 entries).
+// kRowLanes lanes per (row, right-hand side) read the row's near entries coalesced
+// (rows hold ~25 entries); groups are ordered row-major so the B right-hand sides of a
+// row reuse its CSR entries from cache.  acc is [panel][B][4], x and y are [B][2N].
 constexpr int kRowLanes = 8;
 template <bool RAW>
-__global__ void assemble_kernel(int64_t N, const double *__restrict__ acc, const int64_t *__restrict__ ptr,
+__global__ void assemble_kernel(int64_t N, int B, const double *__restrict__ acc, const int64_t *__restrict__ ptr,
                                 const int *__restrict__ col, const double *__restrict__ dV,
                                 const double *__restrict__ dK, const double2 *__restrict__ x, const double2 *s,
                                 double2 *y, double2 *Vd, double2 *Kp) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t i = g / kRowLanes;
+    const int64_t grp = g / kRowLanes;
     const int lane = (int)(g % kRowLanes);
+    const int64_t i = grp / B;
+    const int b = (int)(grp - i * B);
     const bool valid = i < N;
+    const double2 *xb = x + (int64_t)b * 2 * N;
     double vr = 0, vi = 0, kr = 0, ki = 0;
     if (valid) {
         for (int64_t e = ptr[i] + lane; e < ptr[i + 1]; e += kRowLanes) {
             const int j = col[e];
-            const double a = dV[e], b = dK[e];
-            const double2 ph = x[j], dp = x[N + j];
+            const double a = dV[e], c = dK[e];
+            const double2 ph = xb[j], dp = xb[N + j];
             vr += a * dp.x;
             vi += a * dp.y;
-            kr += b * ph.x;
-            ki += b * ph.y;
+            kr += c * ph.x;
+            ki += c * ph.y;
         }
     }
 #pragma unroll
@@ -73,70 +79,70 @@ __global__ void assemble_kernel(int64_t N, const double *__restrict__ acc, const
         ki += __shfl_xor_sync(0xffffffffu, ki, o, kRowLanes);
     }
     if (!valid || lane != 0) return;
-    const double2 V = make_double2(acc[4 * i] + vr, acc[4 * i + 1] + vi);
-    const double2 K = make_double2(acc[4 * i + 2] + kr, acc[4 * i + 3] + ki);
+    const double *ai = acc + 4 * (i * B + b);
+    const double2 V = make_double2(ai[0] + vr, ai[1] + vi);
+    const double2 K = make_double2(ai[2] + kr, ai[3] + ki);
     if (RAW) {
-        Vd[i] = V;
-        Kp[i] = K;
+        Vd[(int64_t)b * N + i] = V;
+        Kp[(int64_t)b * N + i] = K;
         return;
     }
-    const double2 ph = x[i];
-    const double2 sv = cmul(*s, V);
-    y[i] = make_double2(0.5 * ph.x + K.x - V.x, 0.5 * ph.y + K.y - V.y);
-    y[N + i] = make_double2(0.5 * ph.x - K.x + sv.x, 0.5 * ph.y - K.y + sv.y);
+    const double2 ph = xb[i];
+    const double2 sv = cmul(s[b], V);
+    double2 *yb = y + (int64_t)b * 2 * N;
+    yb[i] = make_double2(0.5 * ph.x + K.x - V.x, 0.5 * ph.y + K.y - V.y);
+    yb[N + i] = make_double2(0.5 * ph.x - K.x + sv.x, 0.5 * ph.y - K.y + sv.y);
 }
 
-static int far_part(lspr_ctx *ctx, int mode, const double2 *x) {
-    const bool fp64 = mode == LSPR_DIRECT_FP64 || mode == LSPR_TREE_FP64;
-    const bool tree = mode == LSPR_TREE_FP64 || mode == LSPR_TREE_FP32;
+// far-field parts of B right-hand sides x [B][2N] into ctx->acc [panel][B][4]
+static int far_part(lspr_ctx *ctx, int mode, const double2 *x, int B) {
+    const int prec = mode_prec(mode);
+    const bool tree = mode_tree(mode);
     const int64_t N = ctx->mesh.N;
     if (tree && !ctx->tree.ready) return LSPR_E_STATE;
-    LSPR_TRY(ctx, ctx->acc.ensure(4 * N));
+    LSPR_TRY(ctx, ctx->acc.ensure(4 * N * B));
     LSPR_TRY(ctx, ctx->counters.ensure(8));
-    LSPR_TRY(ctx, cudaMemsetAsync(ctx->acc.p, 0, sizeof(double) * 4 * N, ctx->stream));
+    LSPR_TRY(ctx, cudaMemsetAsync(ctx->acc.p, 0, sizeof(double) * 4 * N * B, ctx->stream));
     LSPR_TRY(ctx, cudaMemsetAsync(ctx->counters.p, 0, sizeof(int) * 8, ctx->stream));
-    LSPR_TRY_ST(launch_weights(ctx, fp64, x, N));
+    LSPR_TRY_ST(launch_weights(ctx, prec, x, N, B));
     if (tree) {
         // P2P on the side stream overlaps P2M -> M2P on the main stream; both add into acc
         LSPR_TRY(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
         LSPR_TRY(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-        LSPR_TRY_ST(launch_p2p(ctx, fp64, ctx->tree.p2p_items.p, ctx->tree.n_p2p_items, ctx->acc.p, ctx->side,
-                               ctx->counters.p));
+        LSPR_TRY_ST(launch_p2p(ctx, prec, ctx->tree.p2p_items.p, ctx->tree.n_p2p_items, ctx->acc.p, ctx->side,
+                               ctx->counters.p, B));
         LSPR_TRY(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
-        LSPR_TRY_ST(launch_p2m(ctx, fp64));
-        LSPR_TRY_ST(launch_m2p(ctx, fp64, ctx->acc.p, ctx->counters.p + 1));
+        LSPR_TRY_ST(launch_p2m(ctx, prec, B));
+        LSPR_TRY_ST(launch_m2p(ctx, prec, ctx->acc.p, ctx->counters.p + 1, B));
         LSPR_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     } else {
-        LSPR_TRY_ST(launch_p2p(ctx, fp64, ctx->direct.items.p, ctx->direct.n, ctx->acc.p, ctx->stream,
-                               ctx->counters.p));
+        LSPR_TRY_ST(launch_p2p(ctx, prec, ctx->direct.items.p, ctx->direct.n, ctx->acc.p, ctx->stream,
+                               ctx->counters.p, B));
     }
-    ++ctx->matvec_count;
+    ctx->matvec_count += B;
     return LSPR_OK;
 }
 
 int apply_operator(lspr_ctx *ctx, int mode, const double2 *x, double2 *y, const double2 *s, int B) {
     const Mesh &m = ctx->mesh;
     const int64_t N = m.N;
-    for (int b = 0; b < B; ++b) {
-        LSPR_TRY_ST(far_part(ctx, mode, x + (size_t)b * 2 * N));
-        cudaEvent_t ev;
-        timer_begin(ctx, T_NEAR, &ev);
-        ++ctx->n_launches;
-        assemble_kernel<false><<<grid_for(N * kRowLanes, 256), 256, 0, ctx->stream>>>(
-            N, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x + (size_t)b * 2 * N, s + b,
-            y + (size_t)b * 2 * N, nullptr, nullptr);
-        timer_end(ctx, T_NEAR, ev);
-        LSPR_TRY(ctx, cudaGetLastError());
-    }
+    LSPR_TRY_ST(far_part(ctx, mode, x, B));
+    cudaEvent_t ev;
+    timer_begin(ctx, T_NEAR, &ev);
+    ++ctx->n_launches;
+    assemble_kernel<false><<<grid_for(N * B * kRowLanes, 256), 256, 0, ctx->stream>>>(
+        N, B, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, s, y, nullptr, nullptr);
+    timer_end(ctx, T_NEAR, ev);
+    LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
 
 int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, double2 *Kp) {
     const Mesh &m = ctx->mesh;
-    LSPR_TRY_ST(far_part(ctx, mode, x));
+    LSPR_TRY_ST(far_part(ctx, mode, x, 1));
     ++ctx->n_launches;
     assemble_kernel<true><<<grid_for(m.N * kRowLanes, 256), 256, 0, ctx->stream>>>(
-        m.N, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr, nullptr, Vd, Kp);
+        m.N, 1, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr, nullptr, Vd, Kp);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
@@ -182,18 +188,17 @@ __global__ void dot_partial_kernel(int B, int64_t n2, int nv, const double2 *__r
     if (threadIdx.x == 0) part[((int64_t)b * nv + i) * nchunks + chunk] = red[0];
 }
 
-// h[b][i] = sum of partials; H[b][i][j] += h (column j of the Hessenberg matrix)
-__global__ void dot_final_kernel(int B, int nv, int nchunks, const double2 *part, double2 *h, double2 *H, int m, int j,
-                                 const int *active) {
+// h[b][i] = sum of partials; hcol[b][i] = h (first pass) or += h (second pass): the
+// Hessenberg column of this Arnoldi step, contiguous for the copy to the host
+__global__ void dot_final_kernel(int B, int nv, int nchunks, const double2 *part, double2 *h, double2 *hcol, int m,
+                                 int accumulate, const int *active) {
     const int i = threadIdx.x + blockIdx.x * blockDim.x, b = blockIdx.y;
     if (i >= nv || (active && !active[b])) return;
     double2 s = make_double2(0, 0);
     for (int c = 0; c < nchunks; ++c) s = cadd(s, part[((int64_t)b * nv + i) * nchunks + c]);
     h[b * (m + 1) + i] = s;
-    if (H) {
-        double2 &e = H[(int64_t)b * (m + 1) * m + (int64_t)i * m + j];
-        e = cadd(e, s);
-    }
+    double2 &e = hcol[b * (m + 1) + i];
+    e = accumulate ? cadd(e, s) : s;
 }
 
 // w[b] -= sum_i V[b][i] h[b][i]
@@ -242,70 +247,7 @@ __global__ void scale_kernel(int B, int64_t n2, const double2 *w, int64_t wstrid
     v[b * vstride + k] = d > 0 ? cscale(w[b * wstride + k], 1.0 / d) : make_double2(0, 0);
 }
 
-// apply the previous rotations to column j, build rotation j, update g; resid[b] = |g_{j+1}|.
-// One block per system: the column and the rotations are staged in shared memory and
-// one thread applies the (sequential) rotations.
 constexpr int kMaxRestart = 512;
-__global__ void givens_kernel(int B, int m, int j, double2 *H, const double *hn, double2 *cs, double2 *sn, double2 *g,
-                              double *resid, const int *active) {
-    __shared__ double2 col[kMaxRestart + 1], c[kMaxRestart], s[kMaxRestart];
-    const int b = blockIdx.x;
-    if (b >= B || (active && !active[b])) return;
-    double2 *Hb = H + (int64_t)b * (m + 1) * m;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        col[i] = Hb[i * m + j];
-        if (i < j) {
-            c[i] = cs[(int64_t)b * m + i];
-            s[i] = sn[(int64_t)b * m + i];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        col[j + 1] = make_double2(hn[b], 0.0);
-        for (int i = 0; i < j; ++i) {
-            const double2 a = col[i], d = col[i + 1];
-            col[i] = cadd(cmul(c[i], a), cmul(s[i], d));
-            col[i + 1] = cadd(cmul(make_double2(-s[i].x, s[i].y), a), cmul(c[i], d));   // -conj(s)
-        }
-        const double2 a = col[j], d = col[j + 1];
-        const double aa = sqrt(cabs2(a)), bb = sqrt(cabs2(d));
-        const double t = sqrt(aa * aa + bb * bb);
-        double2 cj, sj;
-        if (aa == 0.0) {
-            cj = make_double2(0, 0);
-            sj = make_double2(1, 0);
-        } else {
-            cj = make_double2(aa / t, 0);
-            sj = cscale(cmul(cscale(a, 1.0 / aa), make_double2(d.x, -d.y)), 1.0 / t);
-        }
-        col[j] = cadd(cmul(cj, a), cmul(sj, d));
-        col[j + 1] = make_double2(0, 0);
-        cs[(int64_t)b * m + j] = cj;
-        sn[(int64_t)b * m + j] = sj;
-        double2 *gb = g + (int64_t)b * (m + 1);
-        const double2 gj = gb[j];
-        gb[j + 1] = cmul(make_double2(-sj.x, sj.y), gj);
-        gb[j] = cmul(cj, gj);
-        resid[b] = sqrt(cabs2(gb[j + 1]));
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hb[i * m + j] = col[i];
-}
-
-// back substitution H y = g for the first jb[b] columns
-__global__ void trisolve_kernel(int B, int m, const double2 *H, const double2 *g, const int *jb, double2 *y) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
-    const double2 *Hb = H + (int64_t)b * (m + 1) * m;
-    const double2 *gb = g + (int64_t)b * (m + 1);
-    double2 *yb = y + (int64_t)b * m;
-    const int n = jb[b];
-    for (int i = n - 1; i >= 0; --i) {
-        double2 acc = gb[i];
-        for (int k = i + 1; k < n; ++k) acc = csub(acc, cmul(Hb[i * m + k], yb[k]));
-        yb[i] = cdiv(acc, Hb[i * m + i]);
-    }
-}
 
 // z[b] = sum_{i < jb} V[b][i] y[b][i]
 __global__ void combine_kernel(int B, int64_t n2, const double2 *__restrict__ V, int64_t vstride_b,
@@ -411,9 +353,16 @@ __global__ void dipole_final_kernel(int B, int nchunks, const double *part, doub
 }
 
 // ------------------------------------------------------------------ driver
+// Restarted GMRES(m) for B systems in lockstep.  The device holds the Krylov basis and
+// does every O(N) operation (preconditioner, matvec, two classical Gram-Schmidt passes,
+// norm, scaling); after each step the new Hessenberg column (m + 2 complex values per
+// system) is copied to the host, which applies the Givens rotations in FP64, tracks the
+// residual estimate |g_{j+1}| and, at the end of a cycle, solves the small triangular
+// system for the update coefficients.
 static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double tol, const double2 *s_d,
                        const double2 *b_d, double2 *x_d, std::vector<int> &iters, std::vector<double> &relres,
                        const std::vector<double> &bnorm) {
+    typedef std::complex<double> cd;
     const Mesh &me = ctx->mesh;
     const int64_t N = me.N, n2 = 2 * N;
     cudaStream_t st = ctx->stream;
@@ -422,23 +371,21 @@ static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, doubl
     LSPR_TRY(ctx, ctx->gm_V.ensure((size_t)B * vstride));
     LSPR_TRY(ctx, ctx->gm_w.ensure((size_t)B * n2));
     LSPR_TRY(ctx, ctx->gm_z.ensure((size_t)B * n2));
-    LSPR_TRY(ctx, ctx->gm_H.ensure((size_t)B * (m + 1) * m));
-    LSPR_TRY(ctx, ctx->gm_cs.ensure((size_t)B * m));
-    LSPR_TRY(ctx, ctx->gm_sn.ensure((size_t)B * m));
-    LSPR_TRY(ctx, ctx->gm_g.ensure((size_t)B * (m + 1)));
     LSPR_TRY(ctx, ctx->gm_y.ensure((size_t)B * m));
-    LSPR_TRY(ctx, ctx->gm_h.ensure((size_t)B * (m + 1)));
+    LSPR_TRY(ctx, ctx->gm_h.ensure((size_t)2 * B * (m + 1)));   // per-pass h, then the column
     LSPR_TRY(ctx, ctx->gm_part.ensure((size_t)B * (m + 1) * nch));
     LSPR_TRY(ctx, ctx->gm_dpart.ensure((size_t)B * nch));
     LSPR_TRY(ctx, ctx->gm_norm.ensure((size_t)2 * B));
     LSPR_TRY(ctx, ctx->gm_active.ensure((size_t)2 * B));
     double2 *V = ctx->gm_V.p, *w = ctx->gm_w.p, *z = ctx->gm_z.p;
-    double *nrm = ctx->gm_norm.p, *resid = ctx->gm_norm.p + B;
+    double2 *hpass = ctx->gm_h.p, *hcol = ctx->gm_h.p + (size_t)B * (m + 1);
+    double *nrm = ctx->gm_norm.p;
     int *active = ctx->gm_active.p, *jb_d = ctx->gm_active.p + B;
     const dim3 gv(grid_for(n2, 256), B), gN(grid_for(N, 256), B);
     std::vector<int> act(B, 1), jb(B, 0);
-    std::vector<double> hres(B);
-    int total = 0;
+    std::vector<cd> H((size_t)B * (m + 1) * m), cs((size_t)B * m), sn((size_t)B * m), g((size_t)B * (m + 1));
+    std::vector<cd> col((size_t)B * (m + 1)), y((size_t)B * m);
+    std::vector<double> hn(B);
     for (int b = 0; b < B; ++b) { iters[b] = 0; relres[b] = 1.0; }
     cudaEvent_t ev;
     while (true) {
@@ -463,20 +410,13 @@ static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, doubl
         }
         if (!any) break;
         LSPR_TRY(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-        // v0 = -(A x - b) / beta, g = (beta, 0, ...), H = 0
-        LSPR_TRY(ctx, cudaMemsetAsync(ctx->gm_H.p, 0, sizeof(double2) * B * (m + 1) * m, st));
-        LSPR_TRY(ctx, cudaMemsetAsync(ctx->gm_g.p, 0, sizeof(double2) * B * (m + 1), st));
-        {
-            std::vector<double2> g0(B * (m + 1), make_double2(0, 0));
-            for (int b = 0; b < B; ++b) g0[b * (m + 1)] = make_double2(beta[b], 0);
-            LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_g.p, g0.data(), sizeof(double2) * B * (m + 1), cudaMemcpyHostToDevice, st));
-            LSPR_TRY(ctx, cudaStreamSynchronize(st));
-        }
+        // v0 = -(A x - b) / beta, g = (beta, 0, ...)
+        std::fill(g.begin(), g.end(), cd(0, 0));
+        for (int b = 0; b < B; ++b) g[(size_t)b * (m + 1)] = cd(beta[b], 0);
         ++ctx->n_launches;
         init_basis_kernel<<<gv, 256, 0, st>>>(B, n2, w, V, vstride, nrm, active);
         for (int b = 0; b < B; ++b) jb[b] = 0;
-        int j = 0;
-        for (; j < m; ++j) {
+        for (int j = 0; j < m; ++j) {
             // z = M^-1 v_j ; w = A z
             timer_begin(ctx, T_GMRES, &ev);
             ++ctx->n_launches;
@@ -489,10 +429,10 @@ static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, doubl
                 dot_partial_kernel<<<dim3(nch, j + 1, B), kRedThreads, 0, st>>>(B, n2, j + 1, V, vstride, w,
                                                                                   ctx->gm_part.p, nch, active);
                 ++ctx->n_launches;
-                dot_final_kernel<<<dim3(grid_for(j + 1, 64), B), 64, 0, st>>>(B, j + 1, nch, ctx->gm_part.p,
-                                                                               ctx->gm_h.p, ctx->gm_H.p, m, j, active);
+                dot_final_kernel<<<dim3(grid_for(j + 1, 64), B), 64, 0, st>>>(B, j + 1, nch, ctx->gm_part.p, hpass,
+                                                                               hcol, m, pass, active);
                 ++ctx->n_launches;
-                axpy_basis_kernel<<<gv, 256, 0, st>>>(B, n2, j + 1, V, vstride, ctx->gm_h.p, m, w, active);
+                axpy_basis_kernel<<<gv, 256, 0, st>>>(B, n2, j + 1, V, vstride, hpass, m, w, active);
             }
             ++ctx->n_launches;
             norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, w, n2, ctx->gm_dpart.p, nch, active);
@@ -500,30 +440,58 @@ static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, doubl
             norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, nrm, active);
             ++ctx->n_launches;
             scale_kernel<<<gv, 256, 0, st>>>(B, n2, w, n2, V + (int64_t)(j + 1) * n2, vstride, nrm, active);
-            ++ctx->n_launches;
-            givens_kernel<<<B, 64, 0, st>>>(B, m, j, ctx->gm_H.p, nrm, ctx->gm_cs.p, ctx->gm_sn.p,
-                                                          ctx->gm_g.p, resid, active);
             timer_end(ctx, T_GMRES, ev);
             LSPR_TRY(ctx, cudaGetLastError());
-            LSPR_TRY(ctx, cudaMemcpyAsync(hres.data(), resid, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+            LSPR_TRY(ctx, cudaMemcpyAsync(col.data(), hcol, sizeof(double2) * B * (m + 1), cudaMemcpyDeviceToHost, st));
+            LSPR_TRY(ctx, cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
             LSPR_TRY(ctx, cudaStreamSynchronize(st));
-            ++total;
             bool any_left = false;
             for (int b = 0; b < B; ++b) {
                 if (!act[b]) continue;
+                cd *Hb = &H[(size_t)b * (m + 1) * m], *c = &cs[(size_t)b * m], *sg = &sn[(size_t)b * m];
+                cd *gb = &g[(size_t)b * (m + 1)];
+                for (int i = 0; i <= j; ++i) Hb[(size_t)i * m + j] = col[(size_t)b * (m + 1) + i];
+                Hb[(size_t)(j + 1) * m + j] = cd(hn[b], 0);
+                for (int i = 0; i < j; ++i) {   // previous rotations on column j
+                    const cd a0 = Hb[(size_t)i * m + j], d0 = Hb[(size_t)(i + 1) * m + j];
+                    Hb[(size_t)i * m + j] = c[i] * a0 + sg[i] * d0;
+                    Hb[(size_t)(i + 1) * m + j] = -std::conj(sg[i]) * a0 + c[i] * d0;
+                }
+                const cd a0 = Hb[(size_t)j * m + j], d0 = Hb[(size_t)(j + 1) * m + j];
+                const double aa = std::abs(a0), t = std::sqrt(aa * aa + std::norm(d0));
+                if (aa == 0.0) {
+                    c[j] = 0.0;
+                    sg[j] = 1.0;
+                } else {
+                    c[j] = aa / t;
+                    sg[j] = (a0 / aa) * std::conj(d0) / t;
+                }
+                Hb[(size_t)j * m + j] = c[j] * a0 + sg[j] * d0;
+                Hb[(size_t)(j + 1) * m + j] = 0.0;
+                gb[j + 1] = -std::conj(sg[j]) * gb[j];
+                gb[j] = c[j] * gb[j];
+                const double res = std::abs(gb[j + 1]);
                 jb[b] = j + 1;
                 ++iters[b];
-                if (hres[b] / bnorm[b] <= tol || iters[b] >= maxiter || !std::isfinite(hres[b])) act[b] = 0;
+                if (res / bnorm[b] <= tol || iters[b] >= maxiter || !std::isfinite(res)) act[b] = 0;
                 any_left = any_left || act[b];
             }
             if (!any_left) break;
             LSPR_TRY(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
         }
-        // x += M^-1 V y
+        // y = R^-1 g (back substitution on the host), x += M^-1 V y
+        for (int b = 0; b < B; ++b) {
+            const cd *Hb = &H[(size_t)b * (m + 1) * m], *gb = &g[(size_t)b * (m + 1)];
+            cd *yb = &y[(size_t)b * m];
+            for (int i = jb[b] - 1; i >= 0; --i) {
+                cd acc = gb[i];
+                for (int k = i + 1; k < jb[b]; ++k) acc -= Hb[(size_t)i * m + k] * yb[k];
+                yb[i] = acc / Hb[(size_t)i * m + i];
+            }
+        }
         LSPR_TRY(ctx, cudaMemcpyAsync(jb_d, jb.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+        LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_y.p, y.data(), sizeof(double2) * B * m, cudaMemcpyHostToDevice, st));
         timer_begin(ctx, T_GMRES, &ev);
-        ++ctx->n_launches;
-        trisolve_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, m, ctx->gm_H.p, ctx->gm_g.p, jb_d, ctx->gm_y.p);
         ++ctx->n_launches;
         combine_kernel<<<gv, 256, 0, st>>>(B, n2, V, vstride, ctx->gm_y.p, m, jb_d, w);
         ++ctx->n_launches;
@@ -532,6 +500,8 @@ static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, doubl
         add_kernel<<<gv, 256, 0, st>>>(B, n2, x_d, z, 1.0);
         timer_end(ctx, T_GMRES, ev);
         LSPR_TRY(ctx, cudaGetLastError());
+        // the host vectors y, jb must outlive the copies above
+        LSPR_TRY(ctx, cudaStreamSynchronize(st));
     }
     return LSPR_OK;
 }
@@ -543,7 +513,7 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
     const int64_t N = me.N, n2 = 2 * N;
     cudaStream_t st = ctx->stream;
     const int mode = o.mode;
-    const bool tree = mode == LSPR_TREE_FP64 || mode == LSPR_TREE_FP32;
+    const bool tree = mode_tree(mode);
     const double2 eout = make_double2(eps_out_re, eps_out_im);
     LSPR_TRY(ctx, ctx->gm_eps.ensure(B));
     LSPR_TRY(ctx, ctx->gm_s.ensure(B));
@@ -594,10 +564,14 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
         LSPR_TRY_ST(gmres_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p, iters, relres,
                                 bnorm));
     } else {
-        // Iterative refinement: the residual r = b - A x is formed with the FP64 operator of
-        // the same kind (tree or direct); the correction solves A d = r with the FP32-mode
-        // GMRES to a tolerance well above the FP32 noise floor (>= 1e-4 relative to ||r||).
-        const int mode_hi = tree ? LSPR_TREE_FP64 : LSPR_DIRECT_FP64;
+        // Iterative refinement: the residual r = b - A x is formed with a high-precision
+        // operator of the same kind (tree or direct); the correction solves A d = r with the
+        // FP32-mode GMRES to a tolerance well above the FP32 noise floor (>= 1e-4 relative
+        // to ||r||).
+        // refine == 2: native FP64 residual; otherwise float-float (about 48 significant bits
+        // at a fraction of the cost of FP64 on this GPU)
+        const int mode_hi = o.refine == 2 ? (tree ? LSPR_TREE_FP64 : LSPR_DIRECT_FP64)
+                                          : (tree ? LSPR_TREE_FF : LSPR_DIRECT_FF);
         std::vector<int> it2(B, 0);
         std::vector<double> rr2(B, 1.0), rn(B, 0.0);
         DArr<double2> dx;

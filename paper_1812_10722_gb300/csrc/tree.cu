@@ -586,6 +586,7 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     LSPR_TRY(ctx, cudaGetLastError());
     // the direct-mode items now address the Morton work order: refresh their own-panel flags
     LSPR_TRY_ST(launch_item_flags(ctx, ctx->direct.items.p, ctx->direct.n));
+    LSPR_TRY_ST(launch_ff_geometry(ctx));
 
     // octree
     const int64_t cap64 = 1 + 8LL * kMaxDepth * (Ns / (Ncrit + 1) + 1);
@@ -613,6 +614,7 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     ++ctx->n_launches;
     box_geometry_kernel<<<nboxes, kGeomThreads, 0, st>>>(nboxes, tr.box_beg.p, tr.box_end.p, w.spos32.p, tr.box_c64.p,
                                                 tr.box_c32.p);
+    LSPR_TRY_ST(launch_ff_boxes(ctx));
 
     // target blocks
     const int64_t ntb = (N + kTargetBlock - 1) / kTargetBlock;

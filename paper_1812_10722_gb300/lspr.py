@@ -18,8 +18,9 @@ from . import build as _build
 
 LIB_PATH = _build.LIB
 
-DIRECT_FP64, DIRECT_FP32, TREE_FP64, TREE_FP32 = 0, 1, 2, 3
-MODES = {"direct_fp64": DIRECT_FP64, "direct_fp32": DIRECT_FP32, "tree_fp64": TREE_FP64, "tree_fp32": TREE_FP32}
+DIRECT_FP64, DIRECT_FP32, TREE_FP64, TREE_FP32, DIRECT_FF, TREE_FF = 0, 1, 2, 3, 4, 5
+MODES = {"direct_fp64": DIRECT_FP64, "direct_fp32": DIRECT_FP32, "tree_fp64": TREE_FP64, "tree_fp32": TREE_FP32,
+         "direct_ff": DIRECT_FF, "tree_ff": TREE_FF}
 
 STATUS = {0: "LSPR_OK", 1: "LSPR_E_ARG", 2: "LSPR_E_STATE", 3: "LSPR_E_CUDA", 4: "LSPR_E_OOM",
           5: "LSPR_E_NOT_CONVERGED", 6: "LSPR_E_TIMEOUT", 7: "LSPR_E_MESH"}
@@ -211,7 +212,8 @@ class Context:
         st = SolveStats(it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                         rr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                         stt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 0.0, 0)
-        o = SolveOpts(float(tol), int(restart), int(maxiter), m, int(bool(refine)))
+        # refine: False/0 plain, True/1 float-float residual, 2 native FP64 residual
+        o = SolveOpts(float(tol), int(restart), int(maxiter), m, int(refine))
         eo = complex(eps_out)
         rc = lib().lspr_solve(self._h, _host_ptr(e), eo.real, eo.imag, _host_ptr(E), _host_ptr(lam), B,
                               ctypes.byref(o), _host_ptr(dip), _host_ptr(sig), ctypes.byref(st))
@@ -235,9 +237,9 @@ class Context:
         _check(lib().lspr_set_timing(self._h, int(bool(enable))), "lspr_set_timing", self._h)
 
     def timing(self) -> dict:
-        ms = np.zeros(12)
-        n = np.zeros(12, np.int64)
+        ms = np.zeros(16)
+        n = np.zeros(16, np.int64)
         _check(lib().lspr_get_timing(self._h, _host_ptr(ms), _host_ptr(n)), "lspr_get_timing", self._h)
         names = ["p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh", "other", "p2p_fp64", "m2p_fp64",
-                 "p2m_fp64", "weights"]
+                 "p2m_fp64", "weights", "p2p_ff", "m2p_ff", "p2m_ff", "unused"]
         return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}

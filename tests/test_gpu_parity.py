@@ -290,3 +290,68 @@ def test_full_size_sampled_rows_and_sigma(lspr, oracle):
     if os.path.exists(gold):
         g = _golden("sphere20480_l380.json")
         assert abs(r.sigma_ext[0] - g["sigma_ext_nm2"]) / g["sigma_ext_nm2"] < 1e-3
+
+
+@pytest.mark.parametrize("mode,tol", [("direct_fp64", 1e-6), ("direct_fp32", 1e-5), ("tree_fp64", 1e-4),
+                                      ("tree_fp32", 1e-4)])
+def test_batched_matvec_ragged_chunks(lspr, oracle, mode, tol):
+    # 11 right-hand sides: one full and one partial chunk of 8 (FP32) or 4 (FP64)
+    v, t = _ragged_mesh()
+    n = len(t)
+    lam = I.wavelengths(350, 420, 11)
+    s = I.drude_eps(lam) / I.EPS_WATER
+    x = I.random_complex(2 * n, seed=17, batch=11)
+    yo = oracle.matvec(v, t, x, s)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        ctx.tree_build(0.5, 6, 64)
+        y = ctx.matvec(x, s, mode)
+        y1 = ctx.matvec(x[5], s[5], mode)
+    for b in range(11):
+        assert _rel(y[b], yo[b]) < tol, b
+    assert _rel(y[5], y1) < 1e-6     # a batched column equals the single-RHS product
+
+
+def test_batched_solve_equals_single(lspr):
+    v, t = I.icosphere(3, 10.0)
+    lam = I.wavelengths(360, 400, 6)
+    ep = I.drude_eps(lam)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        ctx.tree_build(0.5, 6, 64)
+        rb = ctx.solve(ep, I.EPS_WATER, lam, tol=1e-9, mode="tree_fp32", refine=True, restart=60)
+        singles = [ctx.solve(ep[b], I.EPS_WATER, lam[b], tol=1e-9, mode="tree_fp32", refine=True,
+                             restart=60).sigma_ext[0] for b in range(len(lam))]
+    assert np.all(rb.status == 0)
+    assert np.max(np.abs(rb.sigma_ext - np.array(singles)) / np.array(singles)) < 1e-6
+
+
+@pytest.mark.parametrize("name", ["sphere1280", "ragged1235"])
+@pytest.mark.parametrize("kind,ncrit", [("direct", 300), ("tree", 32), ("tree", 300)])
+def test_float_float_operator_matches_fp64(lspr, name, kind, ncrit):
+    # float-float (hi + lo FP32 pairs) evaluation of the same operator: ~1e-13 per term
+    v, t = MESHES[name]()
+    n = len(t)
+    lam = I.wavelengths(360, 400, 5)
+    s = I.drude_eps(lam) / I.EPS_WATER
+    x = I.random_complex(2 * n, seed=23, batch=5)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        ctx.tree_build(0.5, 6, ncrit)
+        y64 = ctx.matvec(x, s, f"{kind}_fp64")
+        yff = ctx.matvec(x, s, f"{kind}_ff")
+        y1 = ctx.matvec(x[0], s[0], f"{kind}_ff")
+    assert _rel(yff, y64) < 1e-11
+    assert _rel(y1, y64[0]) < 1e-11
+
+
+def test_refinement_residual_float_float_vs_fp64(lspr):
+    v, t = I.icosphere(3, 10.0)
+    ep = I.drude_eps(380.0)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        ctx.tree_build(0.5, 6, 64)
+        a = ctx.solve(ep, I.EPS_WATER, 380.0, tol=1e-10, mode="tree_fp32", refine=1, restart=100)
+        b = ctx.solve(ep, I.EPS_WATER, 380.0, tol=1e-10, mode="tree_fp32", refine=2, restart=100)
+    assert a.status[0] == 0 and b.status[0] == 0 and a.residual[0] <= 1e-10
+    assert abs(a.sigma_ext[0] - b.sigma_ext[0]) / b.sigma_ext[0] < 1e-8
