@@ -1,0 +1,16 @@
+// P2M and M2P launches of every compiled Taylor order, double arithmetic.
+#include "farfield.cuh"
+
+namespace lspr {
+
+int p2m_orders_f64(lspr_ctx *ctx, int B) {
+    LSPR_DISPATCH_P(p2m_launch, double, B, ctx, B);
+    return LSPR_OK;
+}
+
+int m2p_orders_f64(lspr_ctx *ctx, double *acc, int *counter, int B) {
+    LSPR_DISPATCH_P(m2p_launch, double, B, ctx, acc, counter, B);
+    return LSPR_OK;
+}
+
+}  // namespace lspr

@@ -355,3 +355,21 @@ def test_refinement_residual_float_float_vs_fp64(lspr):
         b = ctx.solve(ep, I.EPS_WATER, 380.0, tol=1e-10, mode="tree_fp32", refine=2, restart=100)
     assert a.status[0] == 0 and b.status[0] == 0 and a.residual[0] <= 1e-10
     assert abs(a.sigma_ext[0] - b.sigma_ext[0]) / b.sigma_ext[0] < 1e-8
+
+
+@pytest.mark.parametrize("P", [1, 3, 8])
+def test_float_float_operator_every_order(lspr, P):
+    # the float-float M2P walks a term table for every order: ff = FP64 at P = 1, 3, 8
+    v, t = MESHES["ragged1235"]()
+    n = len(t)
+    lam = I.wavelengths(360, 400, 5)
+    s = I.drude_eps(lam) / I.EPS_WATER
+    x = I.random_complex(2 * n, seed=29, batch=5)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        ctx.tree_build(0.5, P, 32)
+        y64 = ctx.matvec(x, s, "tree_fp64")
+        yff = ctx.matvec(x, s, "tree_ff")
+        y1 = ctx.matvec(x[2], s[2], "tree_ff")
+    assert _rel(yff, y64) < 1e-11
+    assert _rel(y1, y64[2]) < 1e-11
