@@ -114,41 +114,12 @@ int lspr_destroy(lspr_ctx *c) {
     if (!c) return LSPR_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    Mesh &m = c->mesh;
-    for (DArr<double> *a : {&m.verts, &m.cx, &m.cy, &m.cz, &m.nx, &m.ny, &m.nz, &m.area, &m.L, &m.Vself, &m.near_dV,
-                            &m.near_dK, &c->acc, &c->gm_norm, &c->gm_bnorm, &c->gm_dpart, &c->gm_out})
-        a->release();
-    m.tris.release();
-    m.near_col.release();
-    m.near_ptr.release();
-    for (DArr<dbl4> *a : {&m.src_pos64, &m.src_nrm64, &m.tgt64, &c->wo.spos64, &c->wo.snrm64, &c->wo.tgt64,
-                             &c->w64, &c->tree.box_c64, &c->tree.mom64})
-        a->release();
-    for (DArr<float4> *a : {&c->wo.spos32, &c->wo.snrm32, &c->wo.tgt32, &c->w32, &c->tree.box_c32, &c->tree.mom32})
-        a->release();
-    for (DArr<int> *a : {&c->wo.src_panel, &c->wo.tgt_panel, &c->tree.box_beg, &c->tree.box_end, &c->tree.box_child,
-                         &c->tree.box_nchild, &c->tree.box_level, &c->tree.box_used, &c->tree.m2p_list, &c->gm_active})
-        a->release();
-    c->tree.box_key.release();
-    c->tree.box_parent.release();
-    for (DArr<int4> *a : {&c->tree.p2p_items, &c->tree.m2p_items, &c->tree.p2m_items, &c->direct.items}) a->release();
-    for (DArr<double2> *a : {&c->xbuf, &c->ybuf, &c->sbuf, &c->gm_V, &c->gm_w, &c->gm_z, &c->gm_x, &c->gm_b, &c->gm_r,
-                             &c->gm_H, &c->gm_cs, &c->gm_sn, &c->gm_g, &c->gm_y, &c->gm_h, &c->gm_part, &c->gm_s,
-                             &c->gm_vinc, &c->gm_eps})
-        a->release();
+    if (c->side) cudaStreamSynchronize(c->side);
     for (cudaEvent_t e : c->timing.pool) cudaEventDestroy(e);
-    c->counters.release();
-    for (DArr<ff4> *a : {&c->wo.spos_ff, &c->wo.snrm_ff, &c->wo.tgt_ff, &c->tree.mom_ff, &c->tree.box_c_ff, &c->w_ff})
-        a->release();
-    c->wo.tgt_pos.release();
-    c->wo.src_tblock.release();
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
-    if (c->side) {
-        cudaStreamSynchronize(c->side);
-        cudaStreamDestroy(c->side);
-    }
-    delete c;
+    for (cudaEvent_t e : {c->ev_fork, c->ev_join})
+        if (e) cudaEventDestroy(e);
+    if (c->side) cudaStreamDestroy(c->side);
+    delete c;   // device arrays free themselves
     return LSPR_OK;
 }
 

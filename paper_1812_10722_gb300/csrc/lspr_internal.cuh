@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -47,10 +48,18 @@ constexpr int kMaxNk = 32;
 __host__ __device__ constexpr int n_terms(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
 
 // ---------------------------------------------------------------- device arrays
+// Counts device allocations made through DArr: captured CUDA graphs embed buffer
+// addresses and are re-recorded when this number has changed since their recording.
+inline std::atomic<uint64_t> g_alloc_generation{0};
+
 template <class T>
 struct DArr {
     T *p = nullptr;
     size_t n = 0;      // elements allocated
+    DArr() = default;
+    DArr(const DArr &) = delete;
+    DArr &operator=(const DArr &) = delete;
+    ~DArr() { release(); }
     cudaError_t ensure(size_t count) {
         if (count <= n && p) return cudaSuccess;
         if (p) cudaFree(p);
@@ -59,6 +68,7 @@ struct DArr {
         size_t c = count ? count : 1;
         cudaError_t e = cudaMalloc((void **)&p, c * sizeof(T));
         if (e == cudaSuccess) n = c;
+        ++g_alloc_generation;
         return e;
     }
     void release() {
@@ -67,6 +77,27 @@ struct DArr {
         n = 0;
     }
 };
+
+// Typed view of a context-owned scratch buffer: the temporaries of the mesh and tree
+// builds reuse device memory from call to call instead of allocating and freeing it
+// (cudaFree synchronises the device).  Temporaries that are live at the same time use
+// different slots.
+template <class T>
+struct Tmp {
+    DArr<unsigned char> *buf;
+    T *p = nullptr;
+    size_t n = 0;
+    explicit Tmp(DArr<unsigned char> &b) : buf(&b) {}
+    cudaError_t ensure(size_t count) {
+        const cudaError_t e = buf->ensure((count ? count : 1) * sizeof(T));
+        if (e == cudaSuccess) {
+            p = (T *)buf->p;
+            n = count;
+        }
+        return e;
+    }
+};
+constexpr int kScratchSlots = 16;
 
 struct Mesh {
     bool ready = false;
@@ -172,6 +203,9 @@ struct lspr_ctx {
     lspr::DArr<double2> gm_s, gm_vinc, gm_eps;
     lspr::DArr<int> gm_active;
     lspr::DArr<double> gm_out;         // dipole + sigma results
+    lspr::DArr<double2> gm_dx;         // refinement correction
+    lspr::DArr<double> gm_dippart, gm_lambda;
+    lspr::DArr<unsigned char> scratch[lspr::kScratchSlots];   // see lspr::Tmp
     // last error text
     std::string last_error;
     int64_t matvec_count = 0;

@@ -493,7 +493,7 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     LSPR_TRY(ctx, m.tgt64.ensure(N));
 
     // scratch: [0] bad flag (int), [1] rho_max, [2] L_max, [3] largest |coordinate| of a centroid
-    DArr<double> flags;
+    Tmp<double> flags(ctx->scratch[0]);
     LSPR_TRY(ctx, flags.ensure(4));
     LSPR_TRY(ctx, cudaMemsetAsync(flags.p, 0, 4 * sizeof(double), st));
     cudaEvent_t ev;
@@ -515,12 +515,11 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     std::memcpy(&bad, &hflags[0], sizeof(int));
     m.rho_max = hflags[1];
     m.Lmax = hflags[2];
-    flags.release();
     if (bad & 1) return LSPR_E_ARG;
     if (bad & 2) return LSPR_E_MESH;
 
     // near-singular list from a cell list (cell edge >= L_max / threshold)
-    DArr<int64_t> cnt;
+    Tmp<int64_t> cnt(ctx->scratch[1]);
     LSPR_TRY(ctx, cnt.ensure(N));
     LSPR_TRY(ctx, m.near_ptr.ensure(N + 1));
     double hgrid[5];
@@ -547,11 +546,11 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
                             std::max(std::max(std::fabs(lo[1]), std::fabs(hi[1])),
                                      std::max(std::fabs(lo[2]), std::fabs(hi[2]))));
     }
-    DArr<double> grid;
-    DArr<unsigned> keys, ktmp;
-    DArr<int> vals, vtmp, hist, offs;
+    Tmp<double> grid(ctx->scratch[2]);
+    Tmp<unsigned> keys(ctx->scratch[3]), ktmp(ctx->scratch[4]);
+    Tmp<int> vals(ctx->scratch[5]), vtmp(ctx->scratch[6]), hist(ctx->scratch[7]), offs(ctx->scratch[8]);
     LSPR_TRY(ctx, grid.ensure(5));
-    DArr<float4> cf;
+    Tmp<float4> cf(ctx->scratch[9]);
     LSPR_TRY(ctx, cf.ensure(N));
     LSPR_TRY(ctx, keys.ensure(N));
     LSPR_TRY(ctx, ktmp.ensure(N));
@@ -575,7 +574,7 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     LSPR_TRY(ctx, m.near_col.ensure(m.nnz));
     LSPR_TRY(ctx, m.near_dV.ensure(m.nnz));
     LSPR_TRY(ctx, m.near_dK.ensure(m.nnz));
-    DArr<int> rowidx;
+    Tmp<int> rowidx(ctx->scratch[10]);
     LSPR_TRY(ctx, rowidx.ensure(m.nnz));
     ++ctx->n_launches;
     near_cells_kernel<true><<<grid_for(N * 32, 128), 128, 0, st>>>(N, m.cx.p, m.cy.p, m.cz.p, m.L.p, m.thr, grid.p,
@@ -588,12 +587,6 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     LSPR_TRY(ctx, cudaGetLastError());
     timer_end(ctx, T_MESH, ev);
     LSPR_TRY(ctx, cudaStreamSynchronize(st));
-    cnt.release();
-    rowidx.release();
-    for (auto *a : {&keys, &ktmp}) a->release();
-    for (auto *a : {&vals, &vtmp, &hist, &offs}) a->release();
-    grid.release();
-    cf.release();
     m.ready = true;
     return workorder_natural(ctx);
 }

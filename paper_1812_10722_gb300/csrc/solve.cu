@@ -574,7 +574,7 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
                                           : (tree ? LSPR_TREE_FF : LSPR_DIRECT_FF);
         std::vector<int> it2(B, 0);
         std::vector<double> rr2(B, 1.0), rn(B, 0.0);
-        DArr<double2> dx;
+        DArr<double2> &dx = ctx->gm_dx;
         LSPR_TRY(ctx, dx.ensure((size_t)B * n2));
         const int max_cycles = 12;
         int used = 0;
@@ -622,11 +622,10 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
             used += mx;
         }
         LSPR_TRY(ctx, cudaStreamSynchronize(st));
-        dx.release();
     }
     // dipole and sigma
     const int nchN = (int)((N + kChunk - 1) / kChunk);
-    DArr<double> part, lam;
+    DArr<double> &part = ctx->gm_dippart, &lam = ctx->gm_lambda;
     LSPR_TRY(ctx, part.ensure((size_t)B * nchN * 6));
     LSPR_TRY(ctx, lam.ensure(B));
     LSPR_TRY(ctx, cudaMemcpyAsync(lam.p, lambda_nm, sizeof(double) * B, cudaMemcpyHostToDevice, st));
@@ -641,8 +640,6 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
     std::vector<double> out((size_t)B * 7);
     LSPR_TRY(ctx, cudaMemcpyAsync(out.data(), ctx->gm_out.p, sizeof(double) * 7 * B, cudaMemcpyDeviceToHost, st));
     LSPR_TRY(ctx, cudaStreamSynchronize(st));
-    part.release();
-    lam.release();
     int rc = LSPR_OK;
     for (int b = 0; b < B; ++b) {
         for (int q = 0; q < 6; ++q) dipole_out[6 * b + q] = out[7 * b + q];

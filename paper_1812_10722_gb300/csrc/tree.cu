@@ -531,7 +531,7 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     cudaEvent_t ev;
     timer_begin(ctx, T_TREE, &ev);
 
-    DArr<double> cube;
+    Tmp<double> cube(ctx->scratch[0]);
     LSPR_TRY(ctx, cube.ensure(8 + 6 * kBoxBlocks));
     ++ctx->n_launches;
     bbox_partial_kernel<<<kBoxBlocks, 256, 0, st>>>(m.src_pos64.p, Ns, m.tgt64.p, N, cube.p + 8);
@@ -546,8 +546,8 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     LSPR_TRY(ctx, cudaMemcpyAsync(cube.p, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
 
     // keys and sort
-    DArr<unsigned> keys, ktmp;
-    DArr<int> vals, vtmp, hist, offs;
+    Tmp<unsigned> keys(ctx->scratch[1]), ktmp(ctx->scratch[2]);
+    Tmp<int> vals(ctx->scratch[3]), vtmp(ctx->scratch[4]), hist(ctx->scratch[5]), offs(ctx->scratch[6]);
     const int64_t nmax = std::max(Ns, N);
     LSPR_TRY(ctx, keys.ensure(nmax));
     LSPR_TRY(ctx, ktmp.ensure(nmax));
@@ -594,7 +594,7 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     for (DArr<int> *a : {&tr.box_beg, &tr.box_end, &tr.box_child, &tr.box_nchild, &tr.box_level, &tr.box_used})
         LSPR_TRY(ctx, a->ensure(cap));
     LSPR_TRY(ctx, tr.box_key.ensure(cap));
-    DArr<int> scratch, nbox_d;
+    Tmp<int> scratch(ctx->scratch[7]), nbox_d(ctx->scratch[8]);
     LSPR_TRY(ctx, scratch.ensure(cap));
     LSPR_TRY(ctx, nbox_d.ensure(1));
     ++ctx->n_launches;
@@ -619,7 +619,7 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     // target blocks
     const int64_t ntb = (N + kTargetBlock - 1) / kTargetBlock;
     tr.ntblocks = ntb;
-    DArr<dbl4> tlo, thi;
+    Tmp<dbl4> tlo(ctx->scratch[9]), thi(ctx->scratch[10]);
     LSPR_TRY(ctx, tlo.ensure(ntb));
     LSPR_TRY(ctx, thi.ensure(ntb));
     ++ctx->n_launches;
@@ -627,10 +627,10 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
 
     // lists: count
     const double clear = m.Lmax / m.thr + m.rho_max;
-    DArr<int> cnt3, off3;
-    DArr<int64_t> tot3;
-    DArr<unsigned long long> pairs;
-    DArr<int> ovf;
+    Tmp<int> cnt3(ctx->scratch[11]), off3(ctx->scratch[12]);
+    Tmp<int64_t> tot3(ctx->scratch[13]);
+    Tmp<unsigned long long> pairs(ctx->scratch[14]);
+    Tmp<int> ovf(ctx->scratch[15]);
     LSPR_TRY(ctx, cnt3.ensure(3 * ntb));
     LSPR_TRY(ctx, off3.ensure(3 * ntb));
     LSPR_TRY(ctx, tot3.ensure(3));
@@ -707,13 +707,6 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     LSPR_TRY(ctx, cudaMemcpyAsync(tr.box_parent.p, hpar.data(), sizeof(int) * nboxes, cudaMemcpyHostToDevice, st));
     timer_end(ctx, T_TREE, ev);
     LSPR_TRY(ctx, cudaStreamSynchronize(st));
-    for (auto *a : {&keys, &ktmp}) a->release();
-    for (auto *a : {&vals, &vtmp, &hist, &offs, &scratch, &nbox_d, &cnt3, &off3, &ovf}) a->release();
-    tlo.release();
-    thi.release();
-    tot3.release();
-    pairs.release();
-    cube.release();
     tr.ready = true;
     return LSPR_OK;
 }
