@@ -185,6 +185,19 @@ LSPR_API int lspr_set_timing(lspr_ctx *ctx, int32_t enable);
 LSPR_API int lspr_launch_count(lspr_ctx *ctx, int64_t *count);
 LSPR_API int lspr_get_timing(lspr_ctx *ctx, double *ms, int64_t *launches);
 
+/* GMRES of lspr_solve runs each Arnoldi cycle as one CUDA graph launch: a graph
+ * loop whose body is one Arnoldi step (preconditioner, product, two Gram-Schmidt
+ * passes, Givens rotation and stop test on the device), so the host takes part once
+ * per restart cycle instead of once per step.  The graph of a configuration (buffer
+ * sizes, mode, B, restart) is recorded on first use and reused, also across mesh and
+ * tree rebuilds of the same sizes.  lspr_set_graphs(ctx, 0) selects host-driven cycles
+ * (same arithmetic); kernel timing (lspr_set_timing) also uses them, since timing
+ * events cannot sit inside a graph loop.  If recording fails the context falls back
+ * to host-driven cycles. */
+LSPR_API int lspr_set_graphs(lspr_ctx *ctx, int32_t enable);
+/* Graph cycles launched and graphs recorded since lspr_create (either pointer may be null). */
+LSPR_API int lspr_graph_stats(lspr_ctx *ctx, int64_t *cycles, int64_t *recordings);
+
 /* Allocation-free direct FP32 product y = A(s) x (the LSPR_DIRECT_FP32 product of
  * lspr_matvec for one right-hand side).  The paper has no counterpart: this is a
  * service for callers that must not allocate device memory during the call, such

@@ -115,10 +115,13 @@ int lspr_destroy(lspr_ctx *c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     if (c->side) cudaStreamSynchronize(c->side);
+    if (c->gstream) cudaStreamSynchronize(c->gstream);
+    for (GraphCache &g : c->gcache) g.reset();
     for (cudaEvent_t e : c->timing.pool) cudaEventDestroy(e);
-    for (cudaEvent_t e : {c->ev_fork, c->ev_join})
+    for (cudaEvent_t e : {c->ev_fork, c->ev_join, c->ev_g0, c->ev_g1})
         if (e) cudaEventDestroy(e);
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     delete c;   // device arrays free themselves
     return LSPR_OK;
 }
@@ -205,6 +208,19 @@ int lspr_get_info(lspr_ctx *c, int64_t *n_panels, int64_t *n_sources, int64_t *n
 int lspr_launch_count(lspr_ctx *c, int64_t *count) {
     if (!c || !count) return LSPR_E_ARG;
     *count = c->n_launches;
+    return LSPR_OK;
+}
+
+int lspr_set_graphs(lspr_ctx *c, int32_t enable) {
+    if (!c) return LSPR_E_ARG;
+    c->use_graphs = enable != 0;
+    return LSPR_OK;
+}
+
+int lspr_graph_stats(lspr_ctx *c, int64_t *cycles, int64_t *recordings) {
+    if (!c) return LSPR_E_ARG;
+    if (cycles) *cycles = c->graph_cycles;
+    if (recordings) *recordings = c->graph_recordings;
     return LSPR_OK;
 }
 

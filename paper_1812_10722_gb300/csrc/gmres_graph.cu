@@ -1,0 +1,607 @@
+// Restarted GMRES(m) (Sec. II.D-E: complex GMRES) with device-driven Arnoldi cycles.
+//
+// One cycle of B systems in lockstep is one CUDA graph launch:
+//   init        v_0 = r / beta, g = beta e_1
+//   while node  (the body is one Arnoldi step; the last kernel of the body decides, on
+//               the device, whether another step follows)
+//                 z = M^-1 v_j                      (v_j = w / ||w|| formed here, j > 0)
+//                 w = A z                           (the far field, near SpMV and block rows)
+//                 two classical Gram-Schmidt passes h = V^H w, w -= V h
+//                 ||w||, Givens rotation of the new Hessenberg column, residual
+//                 estimate |g_{j+1}|, per-system stop test
+//   back substitution R y = g, x += M^-1 V y
+// so the host only takes part once per cycle (explicit residual and stop decision).
+// Inner products reduce over blocks with a last-block ticket instead of a second launch.
+// The arithmetic is that of the host-driven GMRES in solve.cu: FP64 Krylov basis,
+// right 2x2 block-Jacobi preconditioner, CGS2, the same rotation convention.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "cplx.cuh"
+#include "lspr_internal.cuh"
+
+namespace lspr {
+namespace {
+
+constexpr int kT = 256;                 // threads per block of the vector kernels
+constexpr int kPer = 4;                 // elements per thread of the inner-product kernel
+constexpr int kDotChunk = kT * kPer;    // elements per inner-product block
+constexpr int kMaxWarpsSmall = 16;      // warps of the per-system (rotation, back substitution) kernels
+
+struct Arn {
+    int B, m, nch, nblk;
+    int64_t N, n2, vstride;
+    double2 *V, *w, *z, *x;
+    const double2 *b, *s;
+    const double *Vself;
+    double2 *h, *hcol, *part, *H, *sn, *g, *y;
+    double *npart, *nrm, *cs, *res;
+    const double *bn, *par;
+    unsigned *tick;
+    int *jdev, *active, *jb, *iters;
+    cudaGraphConditionalHandle cond;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double2 warp_sum2(double2 v) { return make_double2(warp_sum(v.x), warp_sum(v.y)); }
+
+// sum over a block of kT threads, valid in warp 0
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) t = warp_sum(threadIdx.x < kT / 32 ? sh[threadIdx.x] : 0.0);
+    return t;
+}
+
+// true in every thread of the block that arrives last among `count` blocks on ticket *t
+// (the partial results written before the call are visible to it)
+__device__ __forceinline__ bool last_block(unsigned *t, unsigned count) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(t, 1u) == count - 1;
+    __syncthreads();
+    return last;
+}
+
+// final sum of the squared-norm partials of system b into nrm[b] (last block only)
+__device__ __forceinline__ void norm_final(const Arn &a, int b, double *sh) {
+    double t = 0.0;
+    for (int c = threadIdx.x; c < a.nblk; c += kT) t += __ldcg(a.npart + (int64_t)b * a.nblk + c);
+    t = block_sum(t, sh);
+    if (threadIdx.x == 0) {
+        a.nrm[b] = sqrt(t);
+        a.tick[a.B + b] = 0;
+    }
+}
+
+// w = A x - b (w holds A x on entry; x_zero: x = 0 and w = -b), nrm[b] = ||w||
+__global__ void __launch_bounds__(kT) arn_resid_kernel(Arn a, int x_zero) {
+    __shared__ double sh[kT / 32];
+    const int b = blockIdx.y;
+    const int64_t k = blockIdx.x * (int64_t)kT + threadIdx.x;
+    double q = 0.0;
+    if (k < a.n2) {
+        const int64_t o = (int64_t)b * a.n2 + k;
+        const double2 bb = a.b[o];
+        const double2 v = x_zero ? make_double2(-bb.x, -bb.y) : csub(a.w[o], bb);
+        a.w[o] = v;
+        q = cabs2(v);
+    }
+    q = block_sum(q, sh);
+    if (threadIdx.x == 0) a.npart[(int64_t)b * a.nblk + blockIdx.x] = q;
+    if (last_block(a.tick + a.B + b, a.nblk)) norm_final(a, b, sh);
+}
+
+// v_0 = -w / beta for the running systems (w = A x - b); cycle state reset
+__global__ void __launch_bounds__(kT) arn_init_kernel(Arn a) {
+    const int b = blockIdx.y;
+    const int64_t k = blockIdx.x * (int64_t)kT + threadIdx.x;
+    const bool act = a.active[b] != 0;
+    if (act && k < a.n2) a.V[(int64_t)b * a.vstride + k] = cscale(a.w[(int64_t)b * a.n2 + k], -1.0 / a.nrm[b]);
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i <= a.m; i += kT)
+            a.g[(int64_t)b * (a.m + 1) + i] = make_double2(i == 0 && act ? a.nrm[b] : 0.0, 0.0);
+        if (threadIdx.x == 0) {
+            a.jb[b] = 0;
+            a.tick[b] = 0;
+            a.tick[a.B + b] = 0;
+            if (b == 0) *a.jdev = 0;
+        }
+    }
+}
+
+// v_j = w / ||w|| (j > 0; v_0 comes from the init kernel), z = M^-1 v_j
+__global__ void __launch_bounds__(kT) arn_precond_kernel(Arn a) {
+    const int b = blockIdx.y;
+    const int64_t t = blockIdx.x * (int64_t)kT + threadIdx.x;
+    if (t >= a.N || !a.active[b]) return;
+    const int j = *a.jdev;
+    double2 *Vj = a.V + (int64_t)b * a.vstride + (int64_t)j * a.n2;
+    double2 u0, u1;
+    if (j == 0) {
+        u0 = Vj[t];
+        u1 = Vj[a.N + t];
+    } else {
+        const double d = a.nrm[b];
+        const double inv = d > 0 ? 1.0 / d : 0.0;
+        const double2 *wb = a.w + (int64_t)b * a.n2;
+        u0 = cscale(wb[t], inv);
+        u1 = cscale(wb[a.N + t], inv);
+        Vj[t] = u0;
+        Vj[a.N + t] = u1;
+    }
+    double2 o0, o1;
+    block_jacobi(a.Vself[t], a.s[b], u0, u1, o0, o1);
+    a.z[(int64_t)b * a.n2 + t] = o0;
+    a.z[(int64_t)b * a.n2 + a.N + t] = o1;
+}
+
+// One classical Gram-Schmidt pass, first half: h_i = <v_i, w> for i <= j.  Each block
+// forms the partial products of its chunk for every basis vector; the last block of the
+// system sums the chunks into h and into the Hessenberg column (hcol = h on pass 0,
+// hcol += h on pass 1).
+__global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
+    __shared__ double2 red[kT / 32][32];
+    const int b = blockIdx.y, chunk = blockIdx.x;
+    if (!a.active[b]) return;
+    const int nv = *a.jdev + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)chunk * kDotChunk + threadIdx.x;
+    const double2 *wb = a.w + (int64_t)b * a.n2;
+    const double2 *Vb = a.V + (int64_t)b * a.vstride;
+    double2 wr[kPer];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const int64_t k = base + r * kT;
+        wr[r] = k < a.n2 ? wb[k] : make_double2(0.0, 0.0);
+    }
+    double2 *pb = a.part + (int64_t)b * (a.m + 1) * a.nch;
+    for (int i0 = 0; i0 < nv; i0 += 32) {
+        const int cnt = min(32, nv - i0);
+        for (int ii = 0; ii < cnt; ++ii) {
+            const double2 *v = Vb + (int64_t)(i0 + ii) * a.n2;
+            double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const int64_t k = base + r * kT;
+                if (k < a.n2) s = cadd(s, cconjmul(v[k], wr[r]));
+            }
+            s = warp_sum2(s);
+            if (lane == 0) red[warp][ii] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int q = 0; q < kT / 32; ++q) t = cadd(t, red[q][threadIdx.x]);
+            pb[(int64_t)(i0 + threadIdx.x) * a.nch + chunk] = t;
+        }
+        __syncthreads();
+    }
+    if (!last_block(a.tick + b, a.nch)) return;
+    // rows i = warp + 8 u: lanes stride over the chunks
+    for (int i0 = warp; i0 < nv; i0 += 4 * (kT / 32)) {
+        double2 t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            t[u] = make_double2(0.0, 0.0);
+            const int i = i0 + u * (kT / 32);
+            if (i < nv)
+                for (int c = lane; c < a.nch; c += 32) t[u] = cadd(t[u], __ldcg(pb + (int64_t)i * a.nch + c));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * (kT / 32);
+            const double2 sum = warp_sum2(t[u]);
+            if (lane == 0 && i < nv) {
+                a.h[(int64_t)b * (a.m + 1) + i] = sum;
+                double2 &e = a.hcol[(int64_t)b * (a.m + 1) + i];
+                e = pass ? cadd(e, sum) : sum;
+            }
+        }
+    }
+    if (threadIdx.x == 0) a.tick[b] = 0;
+}
+
+// Second half of a pass: w -= sum_{i <= j} v_i h_i; with_norm (second pass): ||w||
+// into nrm[b] (partials per block, the last block sums them)
+__global__ void __launch_bounds__(kT) arn_axpy_kernel(Arn a, int with_norm) {
+    __shared__ double sh[kT / 32];
+    const int b = blockIdx.y;
+    if (!a.active[b]) return;
+    const int nv = *a.jdev + 1;
+    const int64_t k = blockIdx.x * (int64_t)kT + threadIdx.x;
+    const double2 *hb = a.h + (int64_t)b * (a.m + 1);
+    double q = 0.0;
+    if (k < a.n2) {
+        const double2 *Vb = a.V + (int64_t)b * a.vstride + k;
+        double2 acc = a.w[(int64_t)b * a.n2 + k];
+        for (int i = 0; i < nv; ++i) acc = csub(acc, cmul(Vb[(int64_t)i * a.n2], hb[i]));
+        a.w[(int64_t)b * a.n2 + k] = acc;
+        q = cabs2(acc);
+    }
+    if (!with_norm) return;
+    q = block_sum(q, sh);
+    if (threadIdx.x == 0) a.npart[(int64_t)b * a.nblk + blockIdx.x] = q;
+    if (last_block(a.tick + a.B + b, a.nblk)) norm_final(a, b, sh);
+}
+
+// shared memory of the rotation kernel per warp: column (m+1), sines (m), cosines (m)
+inline size_t tail_smem_per_warp(int m) { return (size_t)(3 * m + 1) * sizeof(double2); }
+
+// End of an Arnoldi step, one warp per system: the new Hessenberg column (hcol, ||w||)
+// is rotated by the previous Givens rotations, a new rotation zeroes its subdiagonal,
+// g is rotated, |g_{j+1}| is the residual estimate and decides whether the system keeps
+// running.  The block then advances j and sets the loop condition: another step runs
+// while a system is running and j < m.
+__global__ void arn_tail_kernel(Arn a) {
+    extern __shared__ double2 dsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int m = a.m, j = *a.jdev;
+    double2 *col = dsm + (size_t)warp * (3 * m + 1);
+    double2 *snw = col + m + 1;
+    double2 *csw = snw + m;
+    const double tol = a.par[0];
+    const int maxit = (int)a.par[1];
+    int any = 0;
+    for (int b = warp; b < a.B; b += nw) {
+        if (!a.active[b]) continue;   // warp-uniform
+        const double2 *hc = a.hcol + (int64_t)b * (m + 1);
+        for (int i = lane; i <= j; i += 32) col[i] = hc[i];
+        for (int i = lane; i < j; i += 32) {
+            snw[i] = a.sn[(int64_t)b * m + i];
+            csw[i] = make_double2(a.cs[(int64_t)b * m + i], 0.0);
+        }
+        __syncwarp();
+        int act = 0;
+        if (lane == 0) {
+            double2 *Hb = a.H + (int64_t)b * (m + 1) * m;
+            double2 a0 = col[0];
+            for (int i = 0; i < j; ++i) {   // previous rotations, carrying row i+1
+                const double c = csw[i].x;
+                const double2 sg = snw[i], d0 = col[i + 1];
+                Hb[(int64_t)i * m + j] = cadd(cscale(a0, c), cmul(sg, d0));
+                a0 = csub(cscale(d0, c), cmul(cconj(sg), a0));
+            }
+            const double hn = a.nrm[b];   // subdiagonal entry ||w||, real
+            const double aa = sqrt(cabs2(a0)), t = sqrt(aa * aa + hn * hn);
+            double c;
+            double2 sg;
+            if (aa == 0.0) {
+                c = 0.0;
+                sg = make_double2(1.0, 0.0);
+            } else {
+                c = aa / t;
+                sg = cscale(a0, hn / (aa * t));
+            }
+            Hb[(int64_t)j * m + j] = cadd(cscale(a0, c), cscale(sg, hn));
+            a.cs[(int64_t)b * m + j] = c;
+            a.sn[(int64_t)b * m + j] = sg;
+            double2 *gb = a.g + (int64_t)b * (m + 1);
+            const double2 gj = gb[j];
+            gb[j + 1] = cmul(make_double2(-sg.x, sg.y), gj);   // -conj(s) g_j
+            gb[j] = cscale(gj, c);
+            const double r = sqrt(cabs2(gb[j + 1]));
+            a.res[b] = r;
+            a.jb[b] = j + 1;
+            const int it = ++a.iters[b];
+            act = (r / a.bn[b] > tol) && it < maxit && isfinite(r);
+            a.active[b] = act;
+        }
+        any |= __shfl_sync(0xffffffffu, act, 0);
+        __syncwarp();
+    }
+    const int go = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        *a.jdev = j + 1;
+        cudaGraphSetConditional(a.cond, (go && j + 1 < m) ? 1u : 0u);
+    }
+}
+
+// R y = g by back substitution (one warp per system), y into a.y
+__global__ void arn_backsub_kernel(Arn a) {
+    extern __shared__ double2 ysm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int m = a.m;
+    double2 *ys = ysm + (size_t)warp * m;
+    for (int b = warp; b < a.B; b += nw) {
+        const int n = a.jb[b];
+        const double2 *Hb = a.H + (int64_t)b * (m + 1) * m, *gb = a.g + (int64_t)b * (m + 1);
+        for (int i = n - 1; i >= 0; --i) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int k = i + 1 + lane; k < n; k += 32) s = cadd(s, cmul(Hb[(int64_t)i * m + k], ys[k]));
+            s = warp_sum2(s);
+            if (lane == 0) ys[i] = cdiv(csub(gb[i], s), Hb[(int64_t)i * m + i]);
+            __syncwarp();
+        }
+        for (int i = lane; i < n; i += 32) a.y[(int64_t)b * m + i] = ys[i];
+        __syncwarp();
+    }
+}
+
+// x += M^-1 sum_{i < jb} v_i y_i
+__global__ void __launch_bounds__(kT) arn_update_kernel(Arn a) {
+    const int b = blockIdx.y;
+    const int64_t t = blockIdx.x * (int64_t)kT + threadIdx.x;
+    const int n = a.jb[b];
+    if (t >= a.N || n == 0) return;
+    const double2 *Vb = a.V + (int64_t)b * a.vstride, *yb = a.y + (int64_t)b * a.m;
+    double2 u0 = make_double2(0.0, 0.0), u1 = make_double2(0.0, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double2 yi = yb[i];
+        u0 = cadd(u0, cmul(Vb[(int64_t)i * a.n2 + t], yi));
+        u1 = cadd(u1, cmul(Vb[(int64_t)i * a.n2 + a.N + t], yi));
+    }
+    double2 o0, o1;
+    block_jacobi(a.Vself[t], a.s[b], u0, u1, o0, o1);
+    double2 *xb = a.x + (int64_t)b * a.n2;
+    xb[t] = cadd(xb[t], o0);
+    xb[a.N + t] = cadd(xb[a.N + t], o1);
+}
+
+int small_kernel_warps(int B, int m) {
+    const int by_smem = (int)(45000 / tail_smem_per_warp(m));
+    return std::max(1, std::min({B, kMaxWarpsSmall, by_smem}));
+}
+
+// Records one Arnoldi cycle into gc: [init] -> while{step} -> [back substitution, update].
+// Launches go to ctx->gstream (ctx->stream is redirected there while recording so that
+// the operator's launchers record into the graph too).  Kernel counts of the recording
+// are kept in gc and removed from the context's counters.
+int capture_cycle(lspr_ctx *ctx, int mode, const Arn &a0, GraphCache &gc) {
+    gc.reset();
+    cudaStream_t cs = ctx->gstream, saved = ctx->stream;
+    const int64_t l0 = ctx->n_launches, mv0 = ctx->matvec_count;
+    const int nw = small_kernel_warps(a0.B, a0.m);
+    const dim3 gv(grid_for(a0.n2, kT), a0.B), gN(grid_for(a0.N, kT), a0.B);
+    cudaGraph_t g = nullptr;
+    bool capturing = false;
+    auto fail = [&](int code) {
+        if (capturing) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(cs, &tmp);
+        }
+        cudaGetLastError();
+        ctx->stream = saved;
+        ctx->n_launches = l0;
+        ctx->matvec_count = mv0;
+        if (g) cudaGraphDestroy(g);
+        return code;
+    };
+#define CAP_TRY(expr)                                                      \
+    do {                                                                   \
+        cudaError_t e__ = (expr);                                          \
+        if (e__ != cudaSuccess) return fail(cuda_status(ctx, e__, #expr)); \
+    } while (0)
+    CAP_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    CAP_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    Arn a = a0;
+    a.cond = h;
+    ctx->stream = cs;
+    // head: v_0 and the cycle state
+    CAP_TRY(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    arn_init_kernel<<<gv, kT, 0, cs>>>(a);
+    CAP_TRY(cudaGetLastError());
+    CAP_TRY(cudaStreamEndCapture(cs, &g));
+    capturing = false;
+    cudaGraphNode_t head = nullptr;
+    size_t nn = 1;
+    CAP_TRY(cudaGraphGetNodes(g, &head, &nn));
+    // the loop over Arnoldi steps
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t loop = nullptr;
+    CAP_TRY(cudaGraphAddNode(&loop, g, &head, nullptr, 1, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    const int64_t l1 = ctx->n_launches;
+    CAP_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    arn_precond_kernel<<<gN, kT, 0, cs>>>(a);
+    ++ctx->n_launches;
+    const int rc = apply_operator(ctx, mode, a.z, a.w, a.s, a.B);
+    if (rc != LSPR_OK) return fail(rc);
+    for (int pass = 0; pass < 2; ++pass) {
+        arn_dot_kernel<<<dim3(a.nch, a.B), kT, 0, cs>>>(a, pass);
+        arn_axpy_kernel<<<gv, kT, 0, cs>>>(a, pass);
+        ctx->n_launches += 2;
+    }
+    arn_tail_kernel<<<1, 32 * nw, nw * tail_smem_per_warp(a.m), cs>>>(a);
+    ++ctx->n_launches;
+    CAP_TRY(cudaGetLastError());
+    CAP_TRY(cudaStreamEndCapture(cs, &body));
+    capturing = false;
+    const int64_t l2 = ctx->n_launches;
+    // tail: x += M^-1 V y
+    CAP_TRY(cudaStreamBeginCaptureToGraph(cs, g, &loop, nullptr, 1, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    arn_backsub_kernel<<<1, 32 * nw, nw * a.m * sizeof(double2), cs>>>(a);
+    arn_update_kernel<<<gN, kT, 0, cs>>>(a);
+    CAP_TRY(cudaGetLastError());
+    CAP_TRY(cudaStreamEndCapture(cs, &g));
+    capturing = false;
+    cudaGraphExec_t exec = nullptr;
+    CAP_TRY(cudaGraphInstantiate(&exec, g, 0));
+#undef CAP_TRY
+    ctx->stream = saved;
+    ctx->n_launches = l0;
+    ctx->matvec_count = mv0;
+    gc.graph = g;
+    gc.exec = exec;
+    gc.per_step = l2 - l1;
+    gc.outer = 3;   // init, back substitution, update
+    return LSPR_OK;
+}
+
+}  // namespace
+
+int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double tol, const double2 *s_d,
+                      const double2 *b_d, double2 *x_d, bool x_zero, bool trust_estimate, std::vector<int> &iters,
+                      std::vector<double> &relres, const std::vector<double> &bnorm) {
+    if (!ctx->use_graphs || ctx->timing.enabled || B < 1 || m < 1) return LSPR_E_STATE;
+    const Mesh &me = ctx->mesh;
+    const int64_t N = me.N, n2 = 2 * N;
+    cudaStream_t st = ctx->stream;
+    if (!ctx->gstream) {
+        LSPR_TRY(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+        LSPR_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_g0, cudaEventDisableTiming));
+        LSPR_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_g1, cudaEventDisableTiming));
+    }
+    ArnoldiBufs &ab = ctx->arn;
+    const int nch = (int)((n2 + kDotChunk - 1) / kDotChunk), nblk = (int)grid_for(n2, kT);
+    const int64_t vstride = (int64_t)(m + 1) * n2;
+    LSPR_TRY(ctx, ctx->gm_V.ensure((size_t)B * vstride));
+    LSPR_TRY(ctx, ctx->gm_w.ensure((size_t)B * n2));
+    LSPR_TRY(ctx, ctx->gm_z.ensure((size_t)B * n2));
+    LSPR_TRY(ctx, ab.h.ensure((size_t)B * (m + 1)));
+    LSPR_TRY(ctx, ab.hcol.ensure((size_t)B * (m + 1)));
+    LSPR_TRY(ctx, ab.part.ensure((size_t)B * (m + 1) * nch));
+    LSPR_TRY(ctx, ab.npart.ensure((size_t)B * nblk));
+    LSPR_TRY(ctx, ab.nrm.ensure(B));
+    LSPR_TRY(ctx, ab.H.ensure((size_t)B * (m + 1) * m));
+    LSPR_TRY(ctx, ab.cs.ensure((size_t)B * m));
+    LSPR_TRY(ctx, ab.sn.ensure((size_t)B * m));
+    LSPR_TRY(ctx, ab.g.ensure((size_t)B * (m + 1)));
+    LSPR_TRY(ctx, ab.y.ensure((size_t)B * m));
+    LSPR_TRY(ctx, ab.res.ensure(B));
+    LSPR_TRY(ctx, ab.bn.ensure(B));
+    LSPR_TRY(ctx, ab.par.ensure(2));
+    LSPR_TRY(ctx, ab.tick.ensure(2 * (size_t)B));
+    LSPR_TRY(ctx, ab.ctl.ensure(1 + 3 * (size_t)B));
+    Arn a;
+    a.B = B;
+    a.m = m;
+    a.nch = nch;
+    a.nblk = nblk;
+    a.N = N;
+    a.n2 = n2;
+    a.vstride = vstride;
+    a.V = ctx->gm_V.p;
+    a.w = ctx->gm_w.p;
+    a.z = ctx->gm_z.p;
+    a.x = x_d;
+    a.b = b_d;
+    a.s = s_d;
+    a.Vself = me.Vself.p;
+    a.h = ab.h.p;
+    a.hcol = ab.hcol.p;
+    a.part = ab.part.p;
+    a.H = ab.H.p;
+    a.sn = ab.sn.p;
+    a.g = ab.g.p;
+    a.y = ab.y.p;
+    a.npart = ab.npart.p;
+    a.nrm = ab.nrm.p;
+    a.cs = ab.cs.p;
+    a.res = ab.res.p;
+    a.bn = ab.bn.p;
+    a.par = ab.par.p;
+    a.tick = ab.tick.p;
+    a.jdev = ab.ctl.p;
+    a.active = ab.ctl.p + 1;
+    a.jb = ab.ctl.p + 1 + B;
+    a.iters = ab.ctl.p + 1 + 2 * B;
+    a.cond = 0;
+    // per-call parameters live in device memory, so one recorded graph serves every call
+    const double par[2] = {tol, (double)std::max(1, maxiter)};
+    LSPR_TRY(ctx, cudaMemcpyAsync(ab.bn.p, bnorm.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
+    LSPR_TRY(ctx, cudaMemcpyAsync(ab.par.p, par, sizeof(par), cudaMemcpyHostToDevice, st));
+    LSPR_TRY(ctx, cudaMemsetAsync(ab.ctl.p, 0, sizeof(int) * (1 + 3 * (size_t)B), st));
+    LSPR_TRY(ctx, cudaMemsetAsync(ab.tick.p, 0, sizeof(unsigned) * 2 * (size_t)B, st));
+    for (int b = 0; b < B; ++b) {
+        iters[b] = 0;
+        relres[b] = 1.0;
+    }
+    std::vector<int> act(B), ctl(1 + 3 * (size_t)B);
+    std::vector<double> est(B), beta(B);
+    const dim3 gv(grid_for(n2, kT), B);
+    static uint64_t clock = 0;
+    bool first = true;
+    while (true) {
+        // explicit residual w = A x - b and beta = ||w|| (x = 0 on entry: w = -b)
+        const bool skip_mv = first && x_zero;
+        if (!skip_mv) LSPR_TRY_ST(apply_operator(ctx, mode, x_d, a.w, s_d, B));
+        ++ctx->n_launches;
+        arn_resid_kernel<<<gv, kT, 0, st>>>(a, skip_mv ? 1 : 0);
+        LSPR_TRY(ctx, cudaGetLastError());
+        LSPR_TRY(ctx, cudaMemcpyAsync(beta.data(), a.nrm, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaStreamSynchronize(st));
+        first = false;
+        bool any = false;
+        for (int b = 0; b < B; ++b) {
+            relres[b] = beta[b] / bnorm[b];
+            act[b] = relres[b] > tol && iters[b] < maxiter && std::isfinite(relres[b]);
+            any = any || act[b];
+        }
+        if (!any) break;
+        LSPR_TRY(ctx, cudaMemcpyAsync(a.active, act.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+        // The graph recorded for this configuration.  Recorded launches hold buffer
+        // addresses (unchanged while no buffer is reallocated: the allocation count) and
+        // sizes that set grids and loop bounds (the counts below); a geometry or tree
+        // rebuilt with the same sizes reuses the graph, since the kernels read the new
+        // contents from the same buffers.
+        const Tree &tr = ctx->tree;
+        uint64_t key[24] = {g_alloc_generation.load(), (uint64_t)mode, (uint64_t)B, (uint64_t)m,
+                            (uint64_t)(uintptr_t)x_d, (uint64_t)(uintptr_t)b_d, (uint64_t)(uintptr_t)s_d,
+                            (uint64_t)N, (uint64_t)me.Ns, (uint64_t)me.nnz, (uint64_t)tr.ready, (uint64_t)tr.P,
+                            (uint64_t)tr.NT, (uint64_t)tr.nboxes, (uint64_t)tr.n_p2p_items,
+                            (uint64_t)tr.n_m2p_items, (uint64_t)tr.n_p2m_items, (uint64_t)ctx->direct.n,
+                            (uint64_t)(uintptr_t)ctx->gm_V.p, (uint64_t)ctx->num_sms, 0, 0, 0, 0};
+        GraphCache *gc = nullptr;
+        for (GraphCache &c : ctx->gcache)
+            if (c.exec && std::equal(key, key + 24, c.key)) gc = &c;
+        if (!gc) {
+            gc = &ctx->gcache[0];
+            for (GraphCache &c : ctx->gcache)
+                if (c.use < gc->use) gc = &c;
+            // the operator's buffers must exist before recording (no allocation inside a graph)
+            if (skip_mv) LSPR_TRY_ST(apply_operator(ctx, mode, b_d, a.z, s_d, B));
+            LSPR_TRY(ctx, cudaStreamSynchronize(st));
+            if (capture_cycle(ctx, mode, a, *gc) != LSPR_OK) {
+                ctx->use_graphs = false;   // the caller falls back to host-driven cycles
+                return LSPR_E_STATE;
+            }
+            ++ctx->graph_recordings;
+            key[0] = g_alloc_generation.load();   // buffers the recording itself sized
+            std::copy(key, key + 24, gc->key);
+        }
+        gc->use = ++clock;
+        LSPR_TRY(ctx, cudaEventRecord(ctx->ev_g0, st));
+        LSPR_TRY(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_g0, 0));
+        LSPR_TRY(ctx, cudaGraphLaunch(gc->exec, ctx->gstream));
+        LSPR_TRY(ctx, cudaEventRecord(ctx->ev_g1, ctx->gstream));
+        LSPR_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_g1, 0));
+        LSPR_TRY(ctx, cudaMemcpyAsync(ctl.data(), ab.ctl.p, sizeof(int) * ctl.size(), cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaMemcpyAsync(est.data(), a.res, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaStreamSynchronize(st));
+        ++ctx->graph_cycles;
+        const int steps = ctl[0];
+        ctx->n_launches += gc->outer + gc->per_step * steps;
+        ctx->matvec_count += (int64_t)B * steps;
+        bool all_met = true;
+        for (int b = 0; b < B; ++b) {
+            iters[b] = ctl[1 + 2 * B + b];
+            if (act[b]) {
+                const double r = est[b] / bnorm[b];
+                if (!(r <= tol) && iters[b] < maxiter) all_met = false;
+                relres[b] = r;
+            }
+        }
+        if (trust_estimate && all_met) break;
+    }
+    return LSPR_OK;
+}
+
+}  // namespace lspr

@@ -159,6 +159,43 @@ struct DirectItems {
     DArr<int4> items;
 };
 
+// An instantiated Arnoldi-cycle graph and what it was recorded for
+struct GraphCache {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t key[24] = {0};
+    uint64_t use = 0;        // last use, for replacement
+    int64_t per_step = 0;    // kernels launched per Arnoldi step (body of the loop)
+    int64_t outer = 0;       // kernels launched once per cycle
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        use = 0;
+    }
+    ~GraphCache() { reset(); }
+};
+
+// device state of the Arnoldi cycles of B systems with restart length m
+struct ArnoldiBufs {
+    DArr<double2> h;        // [B][m+1]  coefficients of one Gram-Schmidt pass
+    DArr<double2> hcol;     // [B][m+1]  Hessenberg column being built
+    DArr<double2> part;     // [B][m+1][chunks] partial inner products
+    DArr<double> npart;     // [B][blocks] partial squared norms
+    DArr<double> nrm;       // [B] norm of the new basis vector / of the residual
+    DArr<double2> H;        // [B][m+1][m] rotated Hessenberg matrix (R)
+    DArr<double> cs;        // [B][m] Givens cosines
+    DArr<double2> sn;       // [B][m] Givens sines
+    DArr<double2> g;        // [B][m+1] rotated right-hand side beta e_1
+    DArr<double2> y;        // [B][m] update coefficients
+    DArr<double> res;       // [B] residual estimate |g_{j+1}|
+    DArr<double> bn;        // [B] reference norm of the relative residual
+    DArr<double> par;       // [2] tolerance, iteration limit
+    DArr<unsigned> tick;    // [2B] last-block tickets
+    DArr<int> ctl;          // [1 + 3B] current column j, active[B], jb[B], iters[B]
+};
+
 constexpr int kTimerSlots = 16;
 
 struct Timing {
@@ -206,6 +243,13 @@ struct lspr_ctx {
     lspr::DArr<double2> gm_dx;         // refinement correction
     lspr::DArr<double> gm_dippart, gm_lambda;
     lspr::DArr<unsigned char> scratch[lspr::kScratchSlots];   // see lspr::Tmp
+    // device-driven Arnoldi cycles (a CUDA graph per configuration, gmres_graph.cu)
+    bool use_graphs = true;
+    cudaStream_t gstream = nullptr;    // private recording/launch stream
+    cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;
+    lspr::GraphCache gcache[2];
+    lspr::ArnoldiBufs arn;
+    int64_t graph_cycles = 0, graph_recordings = 0;
     // last error text
     std::string last_error;
     int64_t matvec_count = 0;
@@ -284,5 +328,17 @@ int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, dou
 int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
                const double *lambda_nm, int B, const lspr_solve_opts &o, double *dipole_out, double *sigma_out,
                lspr_solve_stats *st);
+
+// ------------------------------------------------------------ gmres_graph.cu
+// Restarted GMRES(m) for B systems A(s_b) x_b = b_b whose Arnoldi cycles each run as one
+// CUDA graph launch (a device-side loop over the steps).  x_zero: x holds zeros on entry
+// (the first residual is b without a matrix-vector product).  trust_estimate: return
+// after a cycle whose recurrence residual estimates meet tol, without the explicit
+// residual (for inner solves whose caller forms the residual itself).  iters/relres
+// receive the steps taken and the last relative residual (explicit or estimated) per
+// system.  Returns LSPR_E_STATE when graphs cannot be used (the caller falls back).
+int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double tol, const double2 *s_d,
+                      const double2 *b_d, double2 *x_d, bool x_zero, bool trust_estimate, std::vector<int> &iters,
+                      std::vector<double> &relres, const std::vector<double> &bnorm);
 
 }  // namespace lspr

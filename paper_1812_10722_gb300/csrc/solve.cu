@@ -16,22 +16,11 @@
 #include <cmath>
 #include <complex>
 
+#include "cplx.cuh"
 #include "lspr_internal.cuh"
 
 namespace lspr {
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {   // conj(a) * b
-    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-    const double d = b.x * b.x + b.y * b.y;
-    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
-}
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 // principal square root
 __device__ __forceinline__ double2 csqrt_p(double2 z) {
     const double r = sqrt(z.x * z.x + z.y * z.y);
@@ -157,15 +146,10 @@ __global__ void precond_kernel(int B, int64_t N, const double *__restrict__ Vsel
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (t >= N || b >= B || (active && !active[b])) return;
-    const double V = Vself[t];
-    const double2 sb = s[b];
-    const double2 u0 = in[b * in_stride + t], u1 = in[b * in_stride + N + t];
-    // [[1/2, -V], [1/2, s V]]^-1 = [[s V, V], [-1/2, 1/2]] / (V (1 + s) / 2)
-    const double2 det = make_double2(0.5 * V * (1.0 + sb.x), 0.5 * V * sb.y);
-    const double2 a = cadd(cmul(cscale(sb, V), u0), cscale(u1, V));
-    const double2 c = make_double2(0.5 * (u1.x - u0.x), 0.5 * (u1.y - u0.y));
-    out[b * 2 * N + t] = cdiv(a, det);
-    out[b * 2 * N + N + t] = cdiv(c, det);
+    double2 o0, o1;
+    block_jacobi(Vself[t], s[b], in[b * in_stride + t], in[b * in_stride + N + t], o0, o1);
+    out[b * 2 * N + t] = o0;
+    out[b * 2 * N + N + t] = o1;
 }
 
 // part[b][i][chunk] = sum_k conj(V[b][i][k]) w[b][k]
@@ -561,8 +545,12 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
     const int m = std::max(1, std::min(o.restart, kMaxRestart));
     const bool refine = o.refine && (mode == LSPR_TREE_FP32 || mode == LSPR_DIRECT_FP32);
     if (!refine) {
-        LSPR_TRY_ST(gmres_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p, iters, relres,
-                                bnorm));
+        int rc = gmres_graph_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p, true,
+                                   false, iters, relres, bnorm);
+        if (rc == LSPR_E_STATE)
+            rc = gmres_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p, iters, relres,
+                             bnorm);
+        LSPR_TRY_ST(rc);
     } else {
         // Iterative refinement: the residual r = b - A x is formed with a high-precision
         // operator of the same kind (tree or direct); the correction solves A d = r with the
@@ -610,8 +598,14 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
             std::vector<double> rnorm(B);
             for (int b = 0; b < B; ++b) rnorm[b] = rn[b] > 0 ? rn[b] : 1.0;
             LSPR_TRY(ctx, cudaMemsetAsync(dx.p, 0, sizeof(double2) * B * n2, st));
-            LSPR_TRY_ST(gmres_solve(ctx, mode, B, m, std::max(1, o.maxiter - used), inner, ctx->gm_s.p, ctx->gm_r.p,
-                                    dx.p, it2, rr2, rnorm));
+            // the caller forms the next residual in high precision: the inner solve may
+            // stop on its recurrence estimate
+            int rc = gmres_graph_solve(ctx, mode, B, m, std::max(1, o.maxiter - used), inner, ctx->gm_s.p,
+                                       ctx->gm_r.p, dx.p, true, true, it2, rr2, rnorm);
+            if (rc == LSPR_E_STATE)
+                rc = gmres_solve(ctx, mode, B, m, std::max(1, o.maxiter - used), inner, ctx->gm_s.p, ctx->gm_r.p,
+                                 dx.p, it2, rr2, rnorm);
+            LSPR_TRY_ST(rc);
             ++ctx->n_launches;
             add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_x.p, dx.p, 1.0);
             int mx = 0;

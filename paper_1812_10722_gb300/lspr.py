@@ -82,8 +82,11 @@ def lib():
             L.lspr_set_timing.argtypes = [_vp, _i32]
             L.lspr_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
             L.lspr_get_timing.argtypes = [_vp, _vp, _vp]
+            L.lspr_set_graphs.argtypes = [_vp, _i32]
+            L.lspr_graph_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
             for f in ("lspr_create", "lspr_destroy", "lspr_mesh_upload", "lspr_tree_build", "lspr_matvec",
-                      "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing", "lspr_launch_count"):
+                      "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing", "lspr_launch_count",
+                      "lspr_set_graphs", "lspr_graph_stats"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -232,6 +235,15 @@ class Context:
         n = ctypes.c_int64(0)
         _check(lib().lspr_launch_count(self._h, ctypes.byref(n)), "lspr_launch_count", self._h)
         return n.value
+
+    def set_graphs(self, enable: bool):
+        """Arnoldi cycles as CUDA graph launches (default) or host-driven."""
+        _check(lib().lspr_set_graphs(self._h, int(bool(enable))), "lspr_set_graphs", self._h)
+
+    def graph_stats(self) -> dict:
+        c, r = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().lspr_graph_stats(self._h, ctypes.byref(c), ctypes.byref(r)), "lspr_graph_stats", self._h)
+        return {"cycles": c.value, "recordings": r.value}
 
     def set_timing(self, enable: bool):
         _check(lib().lspr_set_timing(self._h, int(bool(enable))), "lspr_set_timing", self._h)

@@ -373,3 +373,45 @@ def test_float_float_operator_every_order(lspr, P):
         y1 = ctx.matvec(x[2], s[2], "tree_ff")
     assert _rel(yff, y64) < 1e-11
     assert _rel(y1, y64[2]) < 1e-11
+
+
+@pytest.mark.parametrize("mode,refine,B,restart", [("direct_fp64", 0, 1, 50), ("direct_fp64", 0, 3, 12),
+                                                   ("tree_fp32", 1, 1, 50), ("tree_fp32", 1, 4, 16),
+                                                   ("tree_fp64", 0, 2, 10)])
+def test_graph_cycles_match_host_cycles(lspr, mode, refine, B, restart):
+    # Arnoldi cycles as device-driven graph loops give the host-driven cycles' result;
+    # short restarts exercise several cycles, and the recorded graph is reused
+    v, t = MESHES["sphere1280"]()
+    lam = I.wavelengths(395, 420, B)
+    ep = I.drude_eps(lam)
+    kw = dict(tol=1e-9, mode=mode, refine=refine, restart=restart, maxiter=3000)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        ctx.tree_build(0.5, 6, 64)
+        ctx.set_graphs(False)
+        h = ctx.solve(ep, I.EPS_WATER, lam, **kw)
+        assert ctx.graph_stats()["cycles"] == 0
+        ctx.set_graphs(True)
+        g = ctx.solve(ep, I.EPS_WATER, lam, **kw)
+        ctx.mesh_upload(v, t)            # same sizes: the recorded graph stays valid
+        ctx.tree_build(0.5, 6, 64)
+        g2 = ctx.solve(ep, I.EPS_WATER, lam, **kw)
+        st = ctx.graph_stats()
+    assert np.all(h.status == 0) and np.all(g.status == 0) and np.all(g2.status == 0)
+    assert st["cycles"] > 0 and st["recordings"] <= 2
+    assert np.max(np.abs(g.sigma_ext - h.sigma_ext) / np.abs(h.sigma_ext)) < 1e-7
+    # repeat: FP32 atomics make the far field's summation order vary from run to run
+    assert np.max(np.abs(g2.sigma_ext - g.sigma_ext) / np.abs(g.sigma_ext)) < 1e-7
+    if not refine:   # same arithmetic, same stopping rule
+        assert np.all(np.abs(g.iterations - h.iterations) <= 1)
+
+
+def test_graph_cycles_respect_iteration_limit(lspr):
+    v, t = MESHES["protein512"]()
+    ep = I.drude_eps(380.0)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        r = ctx.solve(ep, I.EPS_WATER, 380.0, tol=1e-14, mode="direct_fp64", restart=4, maxiter=10,
+                      check=False)
+        assert ctx.graph_stats()["cycles"] >= 3
+    assert r.iterations[0] == 10 and r.status[0] != 0
