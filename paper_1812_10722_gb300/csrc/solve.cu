@@ -557,7 +557,13 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
         // FP32-mode GMRES to a tolerance well above the FP32 noise floor (>= 1e-4 relative
         // to ||r||).
         // refine == 2: native FP64 residual; otherwise float-float (about 48 significant bits
-        // at a fraction of the cost of FP64 on this GPU)
+        // at a fraction of the cost of FP64 on this GPU).
+        // Once the residual is small (||r|| <= kUpdateRatio tol ||b||), the next residual is
+        // updated instead, r <- r - A d with the FP32 operator: the update differs from the
+        // high-precision residual by (A_hi - A_32) d, whose norm is at most the FP32
+        // operator's relative error (<= 1e-5 measured bound, ~5e-7 typical) times
+        // ||A d|| ~ ||r||, i.e. <= 1e-2 tol ||b||.
+        constexpr double kUpdateRatio = 1e3;
         const int mode_hi = o.refine == 2 ? (tree ? LSPR_TREE_FP64 : LSPR_DIRECT_FP64)
                                           : (tree ? LSPR_TREE_FF : LSPR_DIRECT_FF);
         std::vector<int> it2(B, 0);
@@ -566,31 +572,37 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
         LSPR_TRY(ctx, dx.ensure((size_t)B * n2));
         const int max_cycles = 12;
         int used = 0;
+        bool updated = false;   // r already holds the updated residual of the current x
+        auto norm_of_r = [&]() -> int {
+            ++ctx->n_launches;
+            norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, ctx->gm_r.p, n2, ctx->gm_dpart.p, nch,
+                                                                      nullptr);
+            ++ctx->n_launches;
+            norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, ctx->gm_bnorm.p, nullptr);
+            LSPR_TRY(ctx, cudaGetLastError());
+            LSPR_TRY(ctx, cudaMemcpyAsync(rn.data(), ctx->gm_bnorm.p, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+            LSPR_TRY(ctx, cudaStreamSynchronize(st));
+            return LSPR_OK;
+        };
         for (int cycle = 0;; ++cycle) {
             if (cycle == 0) {   // x = 0: r = b
                 LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_r.p, ctx->gm_b.p, sizeof(double2) * B * n2,
                                               cudaMemcpyDeviceToDevice, st));
                 for (int b = 0; b < B; ++b) rn[b] = bnorm[b];
-            } else {
+            } else if (!updated) {
                 LSPR_TRY_ST(apply_operator(ctx, mode_hi, ctx->gm_x.p, ctx->gm_r.p, ctx->gm_s.p, B));
-                ++ctx->n_launches;
+                ++ctx->n_launches;   // r = b - A x
                 add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_b.p, -1.0);
                 ++ctx->n_launches;
-                norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, ctx->gm_r.p, n2, ctx->gm_dpart.p,
-                                                                          nch, nullptr);
-                ++ctx->n_launches;
-                norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, ctx->gm_bnorm.p, nullptr);
-                LSPR_TRY(ctx, cudaMemcpyAsync(rn.data(), ctx->gm_bnorm.p, sizeof(double) * B, cudaMemcpyDeviceToHost,
-                                              st));
-                LSPR_TRY(ctx, cudaStreamSynchronize(st));
-                ++ctx->n_launches;   // r = b - A x
                 add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_r.p, -2.0);
+                LSPR_TRY_ST(norm_of_r());
             }
-            bool done = true;
+            bool done = true, small = cycle > 0;
             double worst = 0.0;
             for (int b = 0; b < B; ++b) {
                 relres[b] = rn[b] / bnorm[b];
                 done = done && (relres[b] <= o.tol);
+                small = small && (relres[b] <= kUpdateRatio * o.tol);
                 worst = std::max(worst, relres[b]);
             }
             if (done || cycle == max_cycles || used >= o.maxiter || !std::isfinite(worst)) break;
@@ -598,8 +610,8 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
             std::vector<double> rnorm(B);
             for (int b = 0; b < B; ++b) rnorm[b] = rn[b] > 0 ? rn[b] : 1.0;
             LSPR_TRY(ctx, cudaMemsetAsync(dx.p, 0, sizeof(double2) * B * n2, st));
-            // the caller forms the next residual in high precision: the inner solve may
-            // stop on its recurrence estimate
+            // the caller forms the next residual itself: the inner solve may stop on its
+            // recurrence estimate
             int rc = gmres_graph_solve(ctx, mode, B, m, std::max(1, o.maxiter - used), inner, ctx->gm_s.p,
                                        ctx->gm_r.p, dx.p, true, true, it2, rr2, rnorm);
             if (rc == LSPR_E_STATE)
@@ -614,6 +626,14 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
                 mx = std::max(mx, it2[b]);
             }
             used += mx;
+            updated = small;
+            if (updated) {   // r <- r - A_32 d (gm_z is free between GMRES calls)
+                LSPR_TRY(ctx, ctx->gm_z.ensure((size_t)B * n2));
+                LSPR_TRY_ST(apply_operator(ctx, mode, dx.p, ctx->gm_z.p, ctx->gm_s.p, B));
+                ++ctx->n_launches;
+                add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_z.p, -1.0);
+                LSPR_TRY_ST(norm_of_r());
+            }
         }
         LSPR_TRY(ctx, cudaStreamSynchronize(st));
     }
