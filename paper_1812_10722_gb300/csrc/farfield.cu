@@ -31,14 +31,19 @@
 namespace lspr {
 
 // ----------------------------------------------------------------- weights
-// w[s][b] = w_s A_s / (4 pi) * (dphi_b, phi_b) at the source's panel; x is [B][2N] complex
+// w[s][slot] = w_s A_s / (4 pi) * (dphi_b, phi_b) at the source's panel, b = map[slot]
+// (identity without a map; only the first *nact slots are formed when nact is given);
+// x is [B][2N] complex
 template <typename T4>
 __global__ void weights_kernel(int64_t Ns, int64_t N, int B, const dbl4 *__restrict__ spos64,
-                               const int *__restrict__ src_panel, const double2 *__restrict__ x, T4 *__restrict__ w) {
+                               const int *__restrict__ src_panel, const double2 *__restrict__ x, T4 *__restrict__ w,
+                               const int *map, const int *nact) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= Ns * B) return;
     const int64_t s = g / B;
-    const int b = (int)(g - s * B);
+    const int slot = (int)(g - s * B);
+    if (nact && slot >= *nact) return;
+    const int b = map ? map[slot] : slot;
     const int p = src_panel[s];
     const double wa = spos64[s].w * kInv4Pi;
     const double2 phi = x[(int64_t)b * 2 * N + p], dphi = x[(int64_t)b * 2 * N + N + p];
@@ -85,15 +90,15 @@ int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, int64_t N, int B) 
     if (prec == PREC_F64) {
         LSPR_TRY(ctx, ctx->w64.ensure(Ns * B));
         weights_kernel<dbl4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x,
-                                                            ctx->w64.p);
+                                                            ctx->w64.p, ctx->rhs_map, ctx->rhs_nact);
     } else if (prec == PREC_FF) {
         LSPR_TRY(ctx, ctx->w_ff.ensure(Ns * B));
         weights_kernel<ff4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x,
-                                                           ctx->w_ff.p);
+                                                           ctx->w_ff.p, ctx->rhs_map, ctx->rhs_nact);
     } else {
         LSPR_TRY(ctx, ctx->w32.ensure(Ns * B));
         weights_kernel<float4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x,
-                                                              ctx->w32.p);
+                                                              ctx->w32.p, ctx->rhs_map, ctx->rhs_nact);
     }
     timer_end(ctx, T_WEIGHTS, ev);
     LSPR_TRY(ctx, cudaGetLastError());
@@ -208,7 +213,7 @@ int launch_m2p(lspr_ctx *ctx, int prec, double *acc, int *counter, int B) {
 // by the allocation-free matvec entry point.
 int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
                             const double2 *x, float4 *w) {
-    weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, st>>>(Ns, N, 1, spos64, src_panel, x, w);
+    weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, st>>>(Ns, N, 1, spos64, src_panel, x, w, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? LSPR_OK : LSPR_E_CUDA;
 }
 
@@ -216,7 +221,7 @@ int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, cons
                         const float4 *spos, const float4 *snrm, const float4 *w, double *acc) {
     if (nitems == 0) return LSPR_OK;
     p2p_kernel<float, 1, false><<<grid_for(nitems, p2p_warps(1)), p2p_warps(1) * 32, 0, st>>>(
-        items, nitems, 1, 1, tgt, ntgt, spos, snrm, w, acc, nullptr);
+        items, nitems, 1, 1, tgt, ntgt, spos, snrm, w, acc, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? LSPR_OK : LSPR_E_CUDA;
 }
 

@@ -118,12 +118,15 @@ __global__ void __launch_bounds__(p2p_warps(NB) * 32)
     p2p_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B,
                const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt,
                const typename Vec4<T>::type *__restrict__ spos, const typename Vec4<T>::type *__restrict__ snrm,
-               const typename Vec4<T>::type *__restrict__ sw, double *__restrict__ acc, int *counter) {
+               const typename Vec4<T>::type *__restrict__ sw, double *__restrict__ acc, int *counter,
+               const int *nact) {
     using T4 = typename Vec4<T>::type;
     constexpr int W = p2p_warps(NB);
     __shared__ T4 sh[W][2][32];
     __shared__ T4 shw[W][32][NB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Bact = nact ? *nact : B;   // right-hand sides in use (the first Bact slots)
+    nbc = (Bact + NB - 1) / NB;
     const int64_t units = nitems * nbc;
     int64_t it = (int64_t)blockIdx.x * W + warp;
     while (true) {
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(p2p_warps(NB) * 32)
         }
         if (it >= units) return;
         const int64_t ii = it / nbc;
-        const int b0 = (int)(it - ii * nbc) * NB, nb = min(NB, B - b0);
+        const int b0 = (int)(it - ii * nbc) * NB, nb = min(NB, Bact - b0);
         const int4 item = __ldg(items + ii);
         const int64_t t0 = (int64_t)item.x * kTargetBlock + lane, t1 = t0 + 32;
         const T4 q0 = t0 < ntgt ? tgt[t0] : tgt[0];
@@ -271,12 +274,14 @@ __global__ void __launch_bounds__(m2p_warps<T, P, NB>() * 32)
     m2p_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B,
                const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt, const int *__restrict__ list,
                const typename Vec4<T>::type *__restrict__ box_c, const typename Vec4<T>::type *__restrict__ mom,
-               double *__restrict__ acc, int *counter) {
+               double *__restrict__ acc, int *counter, const int *nact) {
     using T4 = typename Vec4<T>::type;
     constexpr int NT = n_terms(P);
     constexpr int W = m2p_warps<T, P, NB>();
     __shared__ T4 sm[W][NT * NB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Bact = nact ? *nact : B;   // right-hand sides in use (the first Bact slots)
+    nbc = (Bact + NB - 1) / NB;
     const int64_t units = nitems * nbc;
     int64_t it = (int64_t)blockIdx.x * W + warp;
     while (true) {
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(m2p_warps<T, P, NB>() * 32)
         }
         if (it >= units) return;
         const int64_t ii = it / nbc;
-        const int b0 = (int)(it - ii * nbc) * NB, nb = min(NB, B - b0);
+        const int b0 = (int)(it - ii * nbc) * NB, nb = min(NB, Bact - b0);
         const int4 item = __ldg(items + ii);
         const int64_t t0 = (int64_t)item.x * kTargetBlock + lane, t1 = t0 + 32;
         const T4 q0 = t0 < ntgt ? tgt[t0] : tgt[0];
@@ -367,7 +372,8 @@ __global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, int n
                            const typename Vec4<T>::type *__restrict__ spos,
                            const typename Vec4<T>::type *__restrict__ snrm, const typename Vec4<T>::type *__restrict__ sw,
                            const typename Vec4<T>::type *__restrict__ box_c, const int *__restrict__ parent,
-                           const int *__restrict__ used, typename MomAcc<T>::type *__restrict__ mom) {
+                           const int *__restrict__ used, typename MomAcc<T>::type *__restrict__ mom,
+                           const int *nact) {
     using S = typename MomAcc<T>::scalar;
     using T4 = typename Vec4<T>::type;
     constexpr int NT = n_terms(P);
@@ -379,7 +385,10 @@ __global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, int n
     const int64_t u = blockIdx.x;
     if (u >= nitems * nbc) return;
     const int64_t ii = u / nbc;
-    const int b0 = (int)(u - ii * nbc) * NB, nb = min(NB, B - b0);
+    const int b0 = (int)(u - ii * nbc) * NB;
+    const int Bact = nact ? *nact : B;   // right-hand sides in use (the first Bact slots)
+    if (b0 >= Bact) return;
+    const int nb = min(NB, Bact - b0);
     const int4 item = items[ii];
     const T4 c = box_c[item.x];
     const int t = threadIdx.x;
@@ -542,7 +551,7 @@ static void p2p_launch(lspr_ctx *ctx, const int4 *items, int64_t nitems, int B, 
                                              persistent_grid(ctx, p2p_kernel<T, NB, true>, W * 32, &occ));
     p2p_kernel<T, NB, true><<<grid, W * 32, 0, st>>>(items, nitems, nbc, B, Views<T>::tgt(ctx), ctx->mesh.N,
                                                       Views<T>::spos(ctx), Views<T>::snrm(ctx), Views<T>::w(ctx),
-                                                      acc, counter);
+                                                      acc, counter, ctx->rhs_nact);
 }
 
 template <typename T, int P, int NB>
@@ -552,7 +561,7 @@ static void p2m_launch(lspr_ctx *ctx, int B) {
     const int nbc = (B + NB - 1) / NB;
     p2m_kernel<T, P, NB><<<(unsigned)(tr.n_p2m_items * nbc), threads, 0, ctx->stream>>>(
         tr.p2m_items.p, tr.n_p2m_items, nbc, B, Views<T>::spos(ctx), Views<T>::snrm(ctx), Views<T>::w(ctx),
-        Views<T>::bc(ctx), tr.box_parent.p, tr.box_used.p, Views<T>::mom_acc(ctx));
+        Views<T>::bc(ctx), tr.box_parent.p, tr.box_used.p, Views<T>::mom_acc(ctx), ctx->rhs_nact);
 }
 
 template <typename T, int P, int NB>
@@ -565,7 +574,8 @@ static void m2p_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
                                              persistent_grid(ctx, m2p_kernel<T, P, NB, true>, W * 32, &occ));
     m2p_kernel<T, P, NB, true><<<grid, W * 32, 0, ctx->stream>>>(tr.m2p_items.p, tr.n_m2p_items, nbc, B,
                                                                   Views<T>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p,
-                                                                  Views<T>::bc(ctx), Views<T>::mom(ctx), acc, counter);
+                                                                  Views<T>::bc(ctx), Views<T>::mom(ctx), acc, counter,
+                                                                  ctx->rhs_nact);
 }
 
 // dispatch over the compiled Taylor orders and over single / chunked right-hand sides

@@ -57,12 +57,15 @@ template <int NB>
 __global__ void __launch_bounds__(kFfM2PWarps * 32)
     m2p_ff_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B, int NT, int W,
                   const ff4 *__restrict__ tgt, int64_t ntgt, const int *__restrict__ list,
-                  const ff4 *__restrict__ box_c, const ff4 *__restrict__ mom, double *__restrict__ acc, int *counter) {
+                  const ff4 *__restrict__ box_c, const ff4 *__restrict__ mom, double *__restrict__ acc, int *counter,
+                  const int *nact) {
     extern __shared__ __align__(16) unsigned char ff_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp >= W) return;
     ff4 *sm = (ff4 *)(ff_smem + (size_t)warp * ff_m2p_smem_per_warp(NT, NB));
     ffloat *sa = (ffloat *)(sm + NT * NB);   // sa[t * 32 + lane]
+    const int Bact = nact ? *nact : B;   // right-hand sides in use (the first Bact slots)
+    nbc = (Bact + NB - 1) / NB;
     const int64_t units = nitems * nbc;
     while (true) {
         int v = 0;
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(kFfM2PWarps * 32)
         const int64_t it = __shfl_sync(0xffffffffu, v, 0);
         if (it >= units) return;
         const int64_t ii = it / nbc;
-        const int b0 = (int)(it - ii * nbc) * NB, nb = min(NB, B - b0);
+        const int b0 = (int)(it - ii * nbc) * NB, nb = min(NB, Bact - b0);
         const int4 item = __ldg(items + ii);
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
@@ -163,7 +166,7 @@ int m2p_ff_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
                                                       (int64_t)occ * std::max(1, ctx->num_sms));
     m2p_ff_kernel<NB><<<grid, kFfM2PWarps * 32, smem, ctx->stream>>>(
         tr.m2p_items.p, tr.n_m2p_items, nbc, B, NT, W, Views<ffloat>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p,
-        Views<ffloat>::bc(ctx), Views<ffloat>::mom(ctx), acc, counter);
+        Views<ffloat>::bc(ctx), Views<ffloat>::mom(ctx), acc, counter, ctx->rhs_nact);
     return LSPR_OK;
 }
 

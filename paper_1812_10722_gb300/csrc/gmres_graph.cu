@@ -40,8 +40,24 @@ struct Arn {
     const double *bn, *par;
     unsigned *tick;
     int *jdev, *active, *jb, *iters;
+    int *rmap;   // [2B + 1]: slot -> system, system -> slot (-1: not running), running count
     cudaGraphConditionalHandle cond;
 };
+
+// packs the running systems into the first slots (single thread)
+__device__ __forceinline__ void pack_running(const Arn &a) {
+    int n = 0;
+    for (int b = 0; b < a.B; ++b) {
+        if (a.active[b]) {
+            a.rmap[n] = b;
+            a.rmap[a.B + b] = n++;
+        } else {
+            a.rmap[a.B + b] = -1;
+        }
+    }
+    for (int q = n; q < a.B; ++q) a.rmap[q] = 0;
+    a.rmap[2 * a.B] = n;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -113,7 +129,10 @@ __global__ void __launch_bounds__(kT) arn_init_kernel(Arn a) {
             a.jb[b] = 0;
             a.tick[b] = 0;
             a.tick[a.B + b] = 0;
-            if (b == 0) *a.jdev = 0;
+            if (b == 0) {
+                *a.jdev = 0;
+                pack_running(a);
+            }
         }
     }
 }
@@ -301,6 +320,7 @@ __global__ void arn_tail_kernel(Arn a) {
     }
     const int go = __syncthreads_or(any);
     if (threadIdx.x == 0) {
+        pack_running(a);
         *a.jdev = j + 1;
         cudaGraphSetConditional(a.cond, (go && j + 1 < m) ? 1u : 0u);
     }
@@ -411,7 +431,12 @@ int capture_cycle(lspr_ctx *ctx, int mode, const Arn &a0, GraphCache &gc) {
     capturing = true;
     arn_precond_kernel<<<gN, kT, 0, cs>>>(a);
     ++ctx->n_launches;
+    // the product works on the running systems only, packed into the first slots
+    ctx->rhs_map = a.rmap;
+    ctx->rhs_inv = a.rmap + a.B;
+    ctx->rhs_nact = a.rmap + 2 * a.B;
     const int rc = apply_operator(ctx, mode, a.z, a.w, a.s, a.B);
+    ctx->rhs_map = ctx->rhs_inv = ctx->rhs_nact = nullptr;
     if (rc != LSPR_OK) return fail(rc);
     for (int pass = 0; pass < 2; ++pass) {
         arn_dot_kernel<<<dim3(a.nch, a.B), kT, 0, cs>>>(a, pass);
@@ -480,6 +505,7 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     LSPR_TRY(ctx, ab.par.ensure(2));
     LSPR_TRY(ctx, ab.tick.ensure(2 * (size_t)B));
     LSPR_TRY(ctx, ab.ctl.ensure(1 + 3 * (size_t)B));
+    LSPR_TRY(ctx, ab.rmap.ensure(2 * (size_t)B + 1));
     Arn a;
     a.B = B;
     a.m = m;
@@ -513,6 +539,7 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     a.active = ab.ctl.p + 1;
     a.jb = ab.ctl.p + 1 + B;
     a.iters = ab.ctl.p + 1 + 2 * B;
+    a.rmap = ab.rmap.p;
     a.cond = 0;
     // per-call parameters live in device memory, so one recorded graph serves every call
     const double par[2] = {tol, (double)std::max(1, maxiter)};
@@ -589,9 +616,9 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
         ++ctx->graph_cycles;
         const int steps = ctl[0];
         ctx->n_launches += gc->outer + gc->per_step * steps;
-        ctx->matvec_count += (int64_t)B * steps;
         bool all_met = true;
         for (int b = 0; b < B; ++b) {
+            ctx->matvec_count += ctl[1 + 2 * B + b] - iters[b];   // products of the running systems only
             iters[b] = ctl[1 + 2 * B + b];
             if (act[b]) {
                 const double r = est[b] / bnorm[b];

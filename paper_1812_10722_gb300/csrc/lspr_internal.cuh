@@ -194,6 +194,7 @@ struct ArnoldiBufs {
     DArr<double> par;       // [2] tolerance, iteration limit
     DArr<unsigned> tick;    // [2B] last-block tickets
     DArr<int> ctl;          // [1 + 3B] current column j, active[B], jb[B], iters[B]
+    DArr<int> rmap;         // [2B + 1] running systems packed first: slot -> b, b -> slot, count
 };
 
 constexpr int kTimerSlots = 16;
@@ -249,6 +250,10 @@ struct lspr_ctx {
     cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;
     lspr::GraphCache gcache[2];
     lspr::ArnoldiBufs arn;
+    // right-hand sides in use while recording an Arnoldi step (null: all B): slot -> system
+    // map, system -> slot map (-1: converged), and the count; the far-field kernels work on
+    // the first *rhs_nact slots only
+    const int *rhs_map = nullptr, *rhs_inv = nullptr, *rhs_nact = nullptr;
     int64_t graph_cycles = 0, graph_recordings = 0;
     // last error text
     std::string last_error;

@@ -40,13 +40,16 @@ template <bool RAW>
 __global__ void assemble_kernel(int64_t N, int B, const double *__restrict__ acc, const int64_t *__restrict__ ptr,
                                 const int *__restrict__ col, const double *__restrict__ dV,
                                 const double *__restrict__ dK, const double2 *__restrict__ x, const double2 *s,
-                                double2 *y, double2 *Vd, double2 *Kp) {
+                                double2 *y, double2 *Vd, double2 *Kp, const int *inv) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t grp = g / kRowLanes;
     const int lane = (int)(g % kRowLanes);
     const int64_t i = grp / B;
     const int b = (int)(grp - i * B);
-    const bool valid = i < N;
+    // the far part of system b sits in slot inv[b] of acc (identity without a map); rows
+    // of converged systems (slot -1) are left untouched
+    const int slot = i < N ? (inv ? inv[b] : b) : -1;
+    const bool valid = i < N && slot >= 0;
     const double2 *xb = x + (int64_t)b * 2 * N;
     double vr = 0, vi = 0, kr = 0, ki = 0;
     if (valid) {
@@ -68,7 +71,7 @@ __global__ void assemble_kernel(int64_t N, int B, const double *__restrict__ acc
         ki += __shfl_xor_sync(0xffffffffu, ki, o, kRowLanes);
     }
     if (!valid || lane != 0) return;
-    const double *ai = acc + 4 * (i * B + b);
+    const double *ai = acc + 4 * (i * B + slot);
     const double2 V = make_double2(ai[0] + vr, ai[1] + vi);
     const double2 K = make_double2(ai[2] + kr, ai[3] + ki);
     if (RAW) {
@@ -120,7 +123,8 @@ int apply_operator(lspr_ctx *ctx, int mode, const double2 *x, double2 *y, const 
     timer_begin(ctx, T_NEAR, &ev);
     ++ctx->n_launches;
     assemble_kernel<false><<<grid_for(N * B * kRowLanes, 256), 256, 0, ctx->stream>>>(
-        N, B, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, s, y, nullptr, nullptr);
+        N, B, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, s, y, nullptr, nullptr,
+        ctx->rhs_inv);
     timer_end(ctx, T_NEAR, ev);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
@@ -131,7 +135,8 @@ int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, dou
     LSPR_TRY_ST(far_part(ctx, mode, x, 1));
     ++ctx->n_launches;
     assemble_kernel<true><<<grid_for(m.N * kRowLanes, 256), 256, 0, ctx->stream>>>(
-        m.N, 1, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr, nullptr, Vd, Kp);
+        m.N, 1, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr, nullptr, Vd, Kp,
+        nullptr);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
