@@ -403,13 +403,17 @@ def run_matvecs(args, wl):
     from paper_1812_10722_gb300 import lspr
     verts, tris = I.icosphere(wl["sub"], wl["R"])
     n = len(tris)
-    s = complex(I.drude_eps(wl["lam"][0]) / I.EPS_WATER)
+    lam = np.asarray(wl["lam"], float)
+    s = I.drude_eps(lam) / I.EPS_WATER   # one product over the workload's B right-hand sides
     ctx = lspr.Context(0, torch.cuda.current_stream().cuda_stream)
     ctx.mesh_upload(verts, tris, wl["K"], wl["K_fine"], wl["N_k"])
     mode = args.matvec_mode or wl["mode"]
     if mode.startswith("tree"):
         ctx.tree_build(wl["theta"], wl["P"], wl["Ncrit"])
-    x = torch.as_tensor(I.random_complex(2 * n, seed=0), device="cuda")
+    x = torch.as_tensor(I.random_complex(2 * n, seed=0, batch=len(lam)) if len(lam) > 1
+                        else I.random_complex(2 * n, seed=0), device="cuda")
+    if len(lam) == 1:
+        s = complex(s[0])
     ctx.matvec(x, s, mode)
     torch.cuda.synchronize()
     ctx.set_timing(True)

@@ -353,6 +353,126 @@ __global__ void __launch_bounds__(m2p_warps<T, P, NB>() * 32)
     }
 }
 
+// ------------------------------------------------------- M2P, several right-hand sides
+// With NB right-hand sides the contraction (4 NB channels per coefficient) outweighs the
+// recurrence, so a (target block, box) pair is handled as a small matrix product:
+//   phase 1  each of 64 threads generates the coefficients a_k of one target into shared
+//            memory, coef[k][target];
+//   phase 2  C[target][channel] += sum_k coef[k][target] M[k][channel], each thread owning a
+//            4-target x (CH/4)-channel tile of C in registers (CH = 4 NB channels).
+// The tile stays in registers over all boxes of the work unit; one block of 64 threads
+// works on one unit at a time.
+constexpr int kM2PGemmThreads = 64;
+
+template <typename T, int P>
+__device__ __forceinline__ void m2p_coeffs(T Rx, T Ry, T Rz, T *__restrict__ out) {   // out[k * 64]
+    constexpr MultiIndex<P> mi{};
+    constexpr int NT = MultiIndex<P>::NT;
+    const T R[3] = {Rx, Ry, Rz};
+    T a[NT];
+    a[0] = rsq(Rx * Rx + Ry * Ry + Rz * Rz);
+    const T ir2 = a[0] * a[0];
+    out[0] = a[0];
+#pragma unroll
+    for (int t = 1; t < NT; ++t) {
+        const int n = mi.deg[t];
+        T s1 = T(0), s2 = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (mi.m1[t][d] >= 0) s1 += R[d] * a[mi.m1[t][d]];
+            if (mi.m2[t][d] >= 0) s2 += a[mi.m2[t][d]];
+        }
+        const T c1 = T(-(2.0 * n - 1.0) / n), c2 = T(-(n - 1.0) / n);
+        a[t] = (c1 * s1 + c2 * s2) * ir2;
+        out[t * kM2PGemmThreads] = a[t];
+    }
+}
+
+template <typename T, int P, int NB>
+__host__ __device__ constexpr size_t m2p_gemm_smem() {
+    return (size_t)n_terms(P) * (kM2PGemmThreads + 4 * NB) * sizeof(T);
+}
+
+template <typename T, int P, int NB>
+__global__ void __launch_bounds__(kM2PGemmThreads)
+    m2p_gemm_kernel(const int4 *__restrict__ items, int64_t nitems, int B,
+                    const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt, const int *__restrict__ list,
+                    const typename Vec4<T>::type *__restrict__ box_c, const typename Vec4<T>::type *__restrict__ mom,
+                    double *__restrict__ acc, int *counter, const int *nact) {
+    using T4 = typename Vec4<T>::type;
+    constexpr int NT = n_terms(P);
+    constexpr int CH = 4 * NB;           // channels of a right-hand-side chunk
+    constexpr int CPT = CH / 4;          // channels per thread (4 channel groups)
+    extern __shared__ __align__(16) unsigned char gemm_smem[];
+    T *coef = (T *)gemm_smem;            // [NT][64]
+    T *ms = coef + NT * kM2PGemmThreads; // [NT][CH]
+    __shared__ int64_t unit_s;
+    const int tid = threadIdx.x;
+    const int tg = tid & 15, cg = tid >> 4;   // targets 4 tg .. 4 tg + 3, channels CPT cg ..
+    const int Bact = nact ? *nact : B;
+    const int nbc = (Bact + NB - 1) / NB;
+    const int64_t units = nitems * nbc;
+    while (true) {
+        __syncthreads();   // the previous unit's readers are done with unit_s and the buffers
+        if (tid == 0) unit_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t it = unit_s;
+        if (it >= units) return;
+        const int64_t ii = it / nbc;
+        const int b0 = (int)(it - ii * nbc) * NB, nb = min(NB, Bact - b0);
+        const int4 item = __ldg(items + ii);
+        const int64_t tb = (int64_t)item.x * kTargetBlock;
+        const int64_t ti = tb + tid;
+        const T4 q = ti < ntgt ? tgt[ti] : tgt[0];
+        T c[4][CPT];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) c[i][j] = T(0);
+#pragma unroll 1
+        for (int l = item.y; l < item.z; ++l) {
+            const int b = __ldg(list + l);
+            const T4 bc = box_c[b];
+            __syncthreads();   // phase 2 of the previous box is done with coef and ms
+            for (int q2 = tid; q2 < NT * NB; q2 += kM2PGemmThreads) {
+                const int t = q2 / NB, j = q2 - t * NB;
+                const T4 m = j < nb ? mom[((int64_t)b * NT + t) * B + b0 + j] : zero4<T4>();
+                T *d = ms + t * CH + 4 * j;
+                d[0] = m.x;
+                d[1] = m.y;
+                d[2] = m.z;
+                d[3] = m.w;
+            }
+            m2p_coeffs<T, P>(q.x - bc.x, q.y - bc.y, q.z - bc.z, coef + tid);
+            __syncthreads();
+#pragma unroll 2
+            for (int k = 0; k < NT; ++k) {
+                T a4[4], m8[CPT];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a4[i] = coef[k * kM2PGemmThreads + 4 * tg + i];
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) m8[j] = ms[k * CH + CPT * cg + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) c[i][j] += a4[i] * m8[j];
+            }
+        }
+        // channel CPT cg + j = component (CPT cg + j) % 4 of right-hand side b0 + (CPT cg + j) / 4
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t t = tb + 4 * tg + i;
+            if (t >= ntgt) continue;
+            const int64_t tp = panel_of(tgt[t].w);
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                const int ch = CPT * cg + j, r = ch >> 2;
+                if (r < nb) atomicAdd(acc + 4 * (tp * B + b0 + r) + (ch & 3), (double)c[i][j]);
+            }
+        }
+    }
+}
+
 // --------------------------------------------------------------------- P2M
 constexpr int kP2MTile = 32;
 
@@ -568,6 +688,24 @@ template <typename T, int P, int NB>
 static void m2p_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     static int occ = 0;
     Tree &tr = ctx->tree;
+    if constexpr (NB > 1) {
+        constexpr size_t smem = m2p_gemm_smem<T, P, NB>();
+        if (occ <= 0) {
+            cudaFuncSetAttribute(m2p_gemm_kernel<T, P, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2p_gemm_kernel<T, P, NB>, kM2PGemmThreads,
+                                                              smem) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            occ = per_sm;
+        }
+        const int nbc = (B + NB - 1) / NB;
+        const unsigned grid = (unsigned)std::min<int64_t>(tr.n_m2p_items * nbc, (int64_t)occ * std::max(1, ctx->num_sms));
+        m2p_gemm_kernel<T, P, NB><<<grid, kM2PGemmThreads, smem, ctx->stream>>>(
+            tr.m2p_items.p, tr.n_m2p_items, B, Views<T>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p, Views<T>::bc(ctx),
+            Views<T>::mom(ctx), acc, counter, ctx->rhs_nact);
+        return;
+    }
     constexpr int W = m2p_warps<T, P, NB>();
     const int nbc = (B + NB - 1) / NB;
     const unsigned grid = std::min<unsigned>(grid_for(tr.n_m2p_items * nbc, W),
