@@ -36,8 +36,8 @@ namespace lspr {
 // x is [B][2N] complex
 template <typename T4>
 __global__ void weights_kernel(int64_t Ns, int64_t N, int B, const dbl4 *__restrict__ spos64,
-                               const int *__restrict__ src_panel, const double2 *__restrict__ x, T4 *__restrict__ w,
-                               const int *map, const int *nact) {
+                               const int *__restrict__ src_panel, const double2 *__restrict__ x,
+                               const double2 *__restrict__ xt, T4 *__restrict__ w, const int *map, const int *nact) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= Ns * B) return;
     const int64_t s = g / B;
@@ -46,7 +46,9 @@ __global__ void weights_kernel(int64_t Ns, int64_t N, int B, const dbl4 *__restr
     const int b = map ? map[slot] : slot;
     const int p = src_panel[s];
     const double wa = spos64[s].w * kInv4Pi;
-    const double2 phi = x[(int64_t)b * 2 * N + p], dphi = x[(int64_t)b * 2 * N + N + p];
+    // x [B][2N], or its transposed copy xt [2N][B] when given
+    const double2 phi = xt ? xt[(int64_t)p * B + b] : x[(int64_t)b * 2 * N + p];
+    const double2 dphi = xt ? xt[(N + p) * B + b] : x[(int64_t)b * 2 * N + N + p];
     T4 o;
     o.x = wa * dphi.x;
     o.y = wa * dphi.y;
@@ -81,7 +83,7 @@ __global__ void to_ff_kernel(int64_t n, const dbl4 *__restrict__ a, ff4 *__restr
 }
 
 // --------------------------------------------------------------- launchers
-int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, int64_t N, int B) {
+int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt, int64_t N, int B) {
     const int64_t Ns = ctx->mesh.Ns;
     const unsigned grid = grid_for(Ns * B, 256);
     cudaEvent_t ev;
@@ -89,15 +91,15 @@ int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, int64_t N, int B) 
     ++ctx->n_launches;
     if (prec == PREC_F64) {
         LSPR_TRY(ctx, ctx->w64.ensure(Ns * B));
-        weights_kernel<dbl4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x,
+        weights_kernel<dbl4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x, xt,
                                                             ctx->w64.p, ctx->rhs_map, ctx->rhs_nact);
     } else if (prec == PREC_FF) {
         LSPR_TRY(ctx, ctx->w_ff.ensure(Ns * B));
-        weights_kernel<ff4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x,
+        weights_kernel<ff4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x, xt,
                                                            ctx->w_ff.p, ctx->rhs_map, ctx->rhs_nact);
     } else {
         LSPR_TRY(ctx, ctx->w32.ensure(Ns * B));
-        weights_kernel<float4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x,
+        weights_kernel<float4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x, xt,
                                                               ctx->w32.p, ctx->rhs_map, ctx->rhs_nact);
     }
     timer_end(ctx, T_WEIGHTS, ev);
@@ -213,7 +215,8 @@ int launch_m2p(lspr_ctx *ctx, int prec, double *acc, int *counter, int B) {
 // by the allocation-free matvec entry point.
 int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
                             const double2 *x, float4 *w) {
-    weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, st>>>(Ns, N, 1, spos64, src_panel, x, w, nullptr, nullptr);
+    weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, st>>>(Ns, N, 1, spos64, src_panel, x, nullptr, w, nullptr,
+                                                               nullptr);
     return cudaGetLastError() == cudaSuccess ? LSPR_OK : LSPR_E_CUDA;
 }
 

@@ -233,6 +233,7 @@ struct lspr_ctx {
     lspr::DArr<dbl4> w64;
     lspr::DArr<ff4> w_ff;
     lspr::DArr<double2> xbuf, ybuf;    // staging for host matvec
+    lspr::DArr<double2> xt;            // [2N][B] transposed right-hand sides of a product
     lspr::DArr<double2> sbuf;
     // solver scratch
     lspr::DArr<double2> gm_V, gm_w, gm_z, gm_x, gm_b, gm_r;
@@ -319,7 +320,8 @@ int launch_ff_geometry(lspr_ctx *ctx);
 int launch_ff_boxes(lspr_ctx *ctx);
 // item.w = 1 where a P2P item may contain sources of its own target block's panels
 int launch_item_flags(lspr_ctx *ctx, int4 *items, int64_t nitems);
-int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, int64_t N, int B);
+// xt: x transposed to [2N][B] (B > 1), or null
+int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt, int64_t N, int B);
 int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
                             const double2 *x, float4 *w);
 int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, const float4 *tgt, int64_t ntgt,

@@ -86,7 +86,64 @@ __global__ void assemble_kernel(int64_t N, int B, const double *__restrict__ acc
     yb[N + i] = make_double2(0.5 * ph.x - K.x + sv.x, 0.5 * ph.y - K.y + sv.y);
 }
 
-// far-field parts of B right-hand sides x [B][2N] into ctx->acc [panel][B][4]
+// Several right-hand sides: x [B][2N] is transposed to xt [2N][B] once per product, so
+// that the gathers of the near-field SpMV and of the source weights read the B values of
+// a panel contiguously (32 x 32 tiles through shared memory, both sides coalesced).
+__global__ void transpose_kernel(int B, int64_t n2, const double2 *__restrict__ x, double2 *__restrict__ xt) {
+    __shared__ double2 tile[32][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    const int b0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {   // rows b, columns k
+        const int b = b0 + r;
+        const int64_t k = k0 + threadIdx.x;
+        if (b < B && k < n2) tile[r][threadIdx.x] = x[(int64_t)b * n2 + k];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {   // rows k, columns b
+        const int64_t k = k0 + r;
+        const int b = b0 + threadIdx.x;
+        if (b < B && k < n2) xt[k * B + b] = tile[threadIdx.x][r];
+    }
+}
+
+// The block rows for several right-hand sides from xt [2N][B]: L lanes per row (a power
+// of two, L <= 32), lane r handling b = r, r + L, ...; the row's CSR entries are read by
+// all lanes of the group (one transaction) and the gathers of x are contiguous in b.
+__global__ void assemble_rhs_kernel(int64_t N, int B, int L, const double *__restrict__ acc,
+                                    const int64_t *__restrict__ ptr, const int *__restrict__ col,
+                                    const double *__restrict__ dV, const double *__restrict__ dK,
+                                    const double2 *__restrict__ xt, const double2 *s, double2 *y, const int *inv) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = g / L;
+    const int r = (int)(g - i * L);
+    if (i >= N) return;
+    const int64_t e0 = ptr[i], e1 = ptr[i + 1];
+    for (int b = r; b < B; b += L) {
+        const int slot = inv ? inv[b] : b;
+        if (slot < 0) continue;   // converged system: row left untouched
+        double vr = 0, vi = 0, kr = 0, ki = 0;
+        for (int64_t e = e0; e < e1; ++e) {
+            const int64_t j = col[e];
+            const double a = dV[e], c = dK[e];
+            const double2 ph = xt[j * B + b], dp = xt[(N + j) * B + b];
+            vr += a * dp.x;
+            vi += a * dp.y;
+            kr += c * ph.x;
+            ki += c * ph.y;
+        }
+        const double *ai = acc + 4 * (i * B + slot);
+        const double2 V = make_double2(ai[0] + vr, ai[1] + vi);
+        const double2 K = make_double2(ai[2] + kr, ai[3] + ki);
+        const double2 ph = xt[i * B + b];
+        const double2 sv = cmul(s[b], V);
+        double2 *yb = y + (int64_t)b * 2 * N;
+        yb[i] = make_double2(0.5 * ph.x + K.x - V.x, 0.5 * ph.y + K.y - V.y);
+        yb[N + i] = make_double2(0.5 * ph.x - K.x + sv.x, 0.5 * ph.y - K.y + sv.y);
+    }
+}
+
+// far-field parts of B right-hand sides x [B][2N] into ctx->acc [panel][B][4]; with B > 1
+// the transposed copy xt of x is formed first (the block assembly reads it too)
 static int far_part(lspr_ctx *ctx, int mode, const double2 *x, int B) {
     const int prec = mode_prec(mode);
     const bool tree = mode_tree(mode);
@@ -96,7 +153,15 @@ static int far_part(lspr_ctx *ctx, int mode, const double2 *x, int B) {
     LSPR_TRY(ctx, ctx->counters.ensure(8));
     LSPR_TRY(ctx, cudaMemsetAsync(ctx->acc.p, 0, sizeof(double) * 4 * N * B, ctx->stream));
     LSPR_TRY(ctx, cudaMemsetAsync(ctx->counters.p, 0, sizeof(int) * 8, ctx->stream));
-    LSPR_TRY_ST(launch_weights(ctx, prec, x, N, B));
+    const double2 *xt = nullptr;
+    if (B > 1) {
+        LSPR_TRY(ctx, ctx->xt.ensure((size_t)B * 2 * N));
+        ++ctx->n_launches;
+        transpose_kernel<<<dim3(grid_for(2 * N, 32), grid_for(B, 32)), dim3(32, 8), 0, ctx->stream>>>(B, 2 * N, x,
+                                                                                                   ctx->xt.p);
+        xt = ctx->xt.p;
+    }
+    LSPR_TRY_ST(launch_weights(ctx, prec, x, xt, N, B));
     if (tree) {
         // P2P on the side stream overlaps P2M -> M2P on the main stream; both add into acc
         LSPR_TRY(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
@@ -122,9 +187,17 @@ int apply_operator(lspr_ctx *ctx, int mode, const double2 *x, double2 *y, const 
     cudaEvent_t ev;
     timer_begin(ctx, T_NEAR, &ev);
     ++ctx->n_launches;
-    assemble_kernel<false><<<grid_for(N * B * kRowLanes, 256), 256, 0, ctx->stream>>>(
-        N, B, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, s, y, nullptr, nullptr,
-        ctx->rhs_inv);
+    if (B == 1) {
+        assemble_kernel<false><<<grid_for(N * kRowLanes, 256), 256, 0, ctx->stream>>>(
+            N, B, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, s, y, nullptr, nullptr,
+            ctx->rhs_inv);
+    } else {
+        int L = 1;
+        while (L < B && L < 32) L *= 2;
+        assemble_rhs_kernel<<<grid_for(N * L, 256), 256, 0, ctx->stream>>>(N, B, L, ctx->acc.p, m.near_ptr.p,
+                                                                          m.near_col.p, m.near_dV.p, m.near_dK.p,
+                                                                          ctx->xt.p, s, y, ctx->rhs_inv);
+    }
     timer_end(ctx, T_NEAR, ev);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
