@@ -157,8 +157,11 @@ LSPR_API int lspr_matvec(lspr_ctx *ctx, const double *x, double *y, int32_t B, c
  * The right-hand side V((eps_out-eps_in)/eps_out dphi_inc/dn), dphi_inc/dn = -E0.n,
  * is formed with the operator of the matvec mode of `o` (FP64 accumulation in every
  * mode); GMRES (right 2x2 block-Jacobi preconditioner, FP64 Krylov basis) runs in
- * that mode, and with o->refine in an FP32 mode the residual of each refinement
- * cycle is formed with the FP64 operator of the same kind; the dipole is
+ * that mode, and with o->refine in an FP32 mode the residual of a refinement cycle
+ * is formed with the float-float (refine 1) or FP64 (refine 2) operator of the same
+ * kind, or, once it is below 1e3 tol ||b||, updated with the FP32 product of the last
+ * correction (the update's deviation from the high-precision residual is at most the
+ * FP32 operator's relative error times the previous residual); the dipole is
  * p = -eps_out * sum_j A_j (c_j dphi2s/dn_j - phi_j n_j) over the panels and
  * sigma_ext = Im(k^2 e.p / (eps_out |E0|)) / Re k with k = 2 pi sqrt(eps_out) / lambda.
  * Returns LSPR_E_NOT_CONVERGED if any wavelength missed tol (results are still
@@ -166,6 +169,37 @@ LSPR_API int lspr_matvec(lspr_ctx *ctx, const double *x, double *y, int32_t B, c
 LSPR_API int lspr_solve(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
                const double *lambda_nm, int32_t B, const lspr_solve_opts *o, double *dipole_out,
                double *sigma_ext_out, lspr_solve_stats *st);
+
+/* Autotuner of the treecode parameters (theta, P, Ncrit) for the current mesh: every
+ * candidate of a fixed grid (P 4..8, theta 0.3..0.6, Ncrit 128/256/512) is built and
+ * solved for the given wavelengths, its sigma_ext compared with a reference solve
+ * (treecode P = 8, theta = 0.3, whose own deviation from the direct FP64 solution is
+ * ~2e-6 on the sphere workloads), and the fastest candidate whose largest relative
+ * sigma_ext deviation stays within half of target_rel_err is chosen; its tree is left
+ * built in the context.  Solve times are CUDA-event times on the context's stream.
+ * If no candidate qualifies, the reference parameters are chosen.  Errors as
+ * lspr_solve (a candidate whose solve does not converge is skipped). */
+typedef struct {
+    double target_rel_err;   /* allowed sigma_ext deviation from the FP64 solution, e.g. 1e-4 */
+    double tol;              /* GMRES tolerance of the tuning solves */
+    int32_t restart;         /* GMRES restart of the tuning solves */
+    int32_t mode;            /* tree matvec mode timed (LSPR_TREE_FP32 or LSPR_TREE_FP64) */
+    int32_t refine;          /* refinement of the timed solves (as lspr_solve_opts.refine) */
+} lspr_tune_opts;
+
+typedef struct {
+    double theta;            /* chosen parameters */
+    int32_t P, Ncrit;
+    double rel_err;          /* largest sigma_ext deviation of the choice from the reference */
+    double ms;               /* solve time of the choice (all wavelengths) */
+    double ref_ms;           /* solve time of the reference parameters */
+    int32_t candidates;      /* candidates built and solved */
+    int32_t qualified;       /* candidates within the accuracy bound */
+} lspr_tune_result;
+
+LSPR_API int lspr_autotune(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im,
+                           const double *E0, const double *lambda_nm, int32_t B, const lspr_tune_opts *o,
+                           lspr_tune_result *res);
 
 /* Sizes of the current geometry and tree (any pointer may be null):
  * panels, sources, near pairs (including self), boxes, P2P source-range items,

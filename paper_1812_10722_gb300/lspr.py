@@ -83,10 +83,12 @@ def lib():
             L.lspr_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
             L.lspr_get_timing.argtypes = [_vp, _vp, _vp]
             L.lspr_set_graphs.argtypes = [_vp, _i32]
+            L.lspr_autotune.argtypes = [_vp, _vp, _d, _d, _vp, _vp, _i32, ctypes.POINTER(TuneOpts),
+                                        ctypes.POINTER(TuneResult)]
             L.lspr_graph_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
             for f in ("lspr_create", "lspr_destroy", "lspr_mesh_upload", "lspr_tree_build", "lspr_matvec",
                       "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing", "lspr_launch_count",
-                      "lspr_set_graphs", "lspr_graph_stats"):
+                      "lspr_set_graphs", "lspr_graph_stats", "lspr_autotune"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -104,6 +106,17 @@ def _is_torch(a) -> bool:
 
 def _host_ptr(a: np.ndarray):
     return ctypes.c_void_p(a.ctypes.data)
+
+
+class TuneOpts(ctypes.Structure):
+    _fields_ = [("target_rel_err", ctypes.c_double), ("tol", ctypes.c_double), ("restart", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("refine", ctypes.c_int32)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double), ("P", ctypes.c_int32), ("Ncrit", ctypes.c_int32),
+                ("rel_err", ctypes.c_double), ("ms", ctypes.c_double), ("ref_ms", ctypes.c_double),
+                ("candidates", ctypes.c_int32), ("qualified", ctypes.c_int32)]
 
 
 @dataclass
@@ -235,6 +248,21 @@ class Context:
         n = ctypes.c_int64(0)
         _check(lib().lspr_launch_count(self._h, ctypes.byref(n)), "lspr_launch_count", self._h)
         return n.value
+
+    def autotune(self, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0), target_rel_err=1e-4, tol=1e-6,
+                 restart=50, mode="tree_fp32", refine=1) -> dict:
+        """Fastest (theta, P, Ncrit) whose sigma_ext stays within target_rel_err / 2 of the
+        reference treecode solve; the chosen tree is left built."""
+        eps = np.ascontiguousarray(np.atleast_1d(np.asarray(eps_in, np.complex128)))
+        lam = np.ascontiguousarray(np.atleast_1d(np.asarray(lambda_nm, np.float64)))
+        e0 = np.ascontiguousarray(np.asarray(E0, np.float64))
+        eo = complex(eps_out)
+        o = TuneOpts(float(target_rel_err), float(tol), int(restart), MODES[mode] if isinstance(mode, str) else int(mode),
+                     int(refine))
+        r = TuneResult()
+        _check(lib().lspr_autotune(self._h, _host_ptr(eps), eo.real, eo.imag, _host_ptr(e0), _host_ptr(lam),
+                                   len(lam), ctypes.byref(o), ctypes.byref(r)), "lspr_autotune", self._h)
+        return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def set_graphs(self, enable: bool):
         """Arnoldi cycles as CUDA graph launches (default) or host-driven."""

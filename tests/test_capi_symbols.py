@@ -64,3 +64,23 @@ def test_header_compiles_as_c(tmp_path):
     r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-c",
                         str(src), "-o", str(tmp_path / "t.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_binding_structs_match_header(tmp_path):
+    # the ctypes mirrors of the option/result structs have the header's layout
+    from paper_1812_10722_gb300 import lspr
+    names = {"lspr_quad_opts": lspr.QuadOpts, "lspr_solve_opts": lspr.SolveOpts,
+             "lspr_solve_stats": lspr.SolveStats, "lspr_tune_opts": lspr.TuneOpts,
+             "lspr_tune_result": lspr.TuneResult}
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "lspr.h"\nint main(void) {\n' +
+                   "".join(f'    printf("{n} %zu\\n", sizeof({n}));\n' for n in names) + "    return 0;\n}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for line in out.split("\n"):
+        if line:
+            n, size = line.split()
+            assert ctypes.sizeof(names[n]) == int(size), n
+    r = lspr.SolveResult(None, None, None, None, None, 0.0, 0)   # a plain record
+    assert r.seconds == 0.0

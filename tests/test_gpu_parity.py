@@ -415,3 +415,19 @@ def test_graph_cycles_respect_iteration_limit(lspr):
                       check=False)
         assert ctx.graph_stats()["cycles"] >= 3
     assert r.iterations[0] == 10 and r.status[0] != 0
+
+
+def test_autotune_meets_sigma_bound(lspr):
+    # the autotuner's choice, built in the context, reproduces the FP64 oracle's sigma_ext
+    # within the requested bound
+    v, t = I.icosphere(3, 10.0)
+    g = _golden("sphere1280_l380.json")["sigma_ext_nm2"]
+    ep = I.drude_eps(380.0)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        r = ctx.autotune(ep, I.EPS_WATER, 380.0, target_rel_err=1e-4, tol=1e-8)
+        s = ctx.solve(ep, I.EPS_WATER, 380.0, tol=1e-8, mode="tree_fp32", refine=True)
+    assert r["candidates"] == 60 and r["qualified"] >= 1 and r["rel_err"] <= 5e-5
+    assert 4 <= r["P"] <= 8 and r["theta"] in (0.3, 0.4, 0.5, 0.6) and r["Ncrit"] in (128, 256, 512)
+    assert r["ms"] <= r["ref_ms"]
+    assert abs(s.sigma_ext[0] - g) / g < 1e-4
