@@ -459,6 +459,47 @@ def run_matvecs(args, wl):
     return out
 
 
+def run_profile(args, wl):
+    """Profiling aid: W untimed steps, then K steps inside an NVTX range "timed" (for
+    ncu --nvtx --nvtx-include timed/), nothing else; the treecode parameters come from
+    --tree (no autotuning)."""
+    import torch
+    from paper_1812_10722_gb300 import lspr
+    verts, tris = I.icosphere(wl["sub"], wl["R"])
+    lam = np.asarray(wl["lam"], float)
+    eps = I.drude_eps(lam)
+    v_d = torch.as_tensor(verts, device="cuda")
+    t_d = torch.as_tensor(tris, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = lspr.Context(0, stream.cuda_stream)
+    if args.no_graphs:
+        ctx.set_graphs(False)   # ncu does not profile the kernels inside a graph's loop
+
+    def step():
+        ctx.mesh_upload(v_d, t_d, wl["K"], wl["K_fine"], wl["N_k"])
+        if wl["mode"].startswith("tree"):
+            ctx.tree_build(wl["theta"], wl["P"], wl["Ncrit"])
+        return ctx.solve(eps, I.EPS_WATER, lam, tol=wl["tol"], restart=wl["restart"], maxiter=2000,
+                         mode=wl["mode"], refine=wl["refine"])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        r = step()
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    e1.synchronize()
+    out = {"workload": args.workload, "tree": [wl["theta"], wl["P"], wl["Ncrit"]], "steps": args.steps,
+           "ms_per_step": e0.elapsed_time(e1) / args.steps, "iterations": int(r.iterations.max()),
+           "matvecs": int(r.matvecs), "launches": ctx.launch_count()}
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,6 +511,9 @@ def main():
     ap.add_argument("--restart", type=int, default=None, help="override the workload's GMRES restart length")
     ap.add_argument("--matvecs", type=int, default=0, help="only run this many bare matvecs (profiling)")
     ap.add_argument("--matvec-mode", default=None, help="matvec mode for --matvecs (default: the workload's)")
+    ap.add_argument("--tree", default=None, help="THETA,P,NCRIT: fixed treecode parameters (no autotuning)")
+    ap.add_argument("--profile", action="store_true", help="only the steps, in an NVTX range 'timed' (profiling)")
+    ap.add_argument("--no-graphs", action="store_true", help="host-driven Arnoldi cycles (profiling)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.restart:
@@ -478,8 +522,14 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
+    if args.tree:
+        th, P, nc = args.tree.split(",")
+        wl.update(theta=float(th), P=int(P), Ncrit=int(nc), autotune=False)
     if args.matvecs:
         print(json.dumps(run_matvecs(args, wl)))
+        return
+    if args.profile:
+        print(json.dumps(run_profile(args, wl)))
         return
 
     if args.impl == "reference":

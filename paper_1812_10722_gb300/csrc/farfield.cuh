@@ -25,7 +25,14 @@ static __device__ __forceinline__ void acc_add(double *g, const ffloat &v) { ato
 static __device__ __forceinline__ int panel_of(float w) { return __float_as_int(w); }
 static __device__ __forceinline__ int panel_of(double w) { return (int)w; }
 static __device__ __forceinline__ int panel_of(const ffloat &w) { return __float_as_int(w.hi); }
-static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+// FP32 1/sqrt(x): the hardware approximation with denormal inputs flushed (squared
+// distances here are far above the denormal range), which spares the denormal fix-up
+// instructions that rsqrtf carries without -ftz
+static __device__ __forceinline__ float rsq(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 // FP64 1/sqrt(x): the FP32 reciprocal square root as the seed and one Newton-Raphson
 // step y <- y + y (1 - x y^2) / 2; a seed error e leaves ~1.5 e^2 (~2e-14 relative).
 // Used for squared distances, which stay far inside the FP32 range.
