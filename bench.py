@@ -76,10 +76,10 @@ P2P_GEN_FLOPS = 16      # per (target, source) pair, generation of G and dG/dn (
 P2P_FP32_INSTR = 16     # FP32-pipe instructions per pair
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64
 # DRAM bytes (read + write) per launch of the current kernels, from the ncu captures summarised in
-# profiles/{m2p,p2p}_fp32_sphere20480.md and profiles/m2p_ff_sphere20480.md (dram__bytes.sum.per_second
-# x gpu__time_duration.sum); None for workloads that were not captured
-NCU_TRAFFIC = {("sphere20480", "m2p"): 2.828e6, ("sphere20480", "p2p"): 5.029e6,
-               ("sphere20480", "m2p_ff"): 5.138e6}
+# profiles/{p2p,m2p,p2m}_fp32_sphere20480.md (dram__bytes.sum.per_second x gpu__time_duration.sum), keyed by
+# workload, kernel and treecode parameters (theta, P, Ncrit); None where no capture matches
+NCU_TRAFFIC = {("sphere20480", "p2p", 0.4, 5, 256): 5.048e6, ("sphere20480", "m2p", 0.4, 5, 256): 2.410e6,
+               ("sphere20480", "p2m", 0.4, 5, 256): 5.097e6}
 
 
 def m2p_flops(P: int, B: int = 1) -> int:
@@ -316,17 +316,17 @@ def run_ours(args, wl, rank, world, local_rank):
     if dom in ("p2p_fp64", "m2p_fp64"):
         a = kernels[dom]["algorithmic_tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom)),
+                "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom, wl["theta"], wl["P"], wl["Ncrit"])),
                 "peak_note": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"}
     elif dom in ("p2p", "m2p") and fp32:
         a = kernels[dom]["algorithmic_tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 3), "peak": round(peak_fp32, 2),
-                "unit": "TFLOP/s", "frac": round(a / peak_fp32, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom)),
+                "unit": "TFLOP/s", "frac": round(a / peak_fp32, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom, wl["theta"], wl["P"], wl["Ncrit"])),
                 "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 flops x 2070 MHz (derived, no measured FP32 peak)"}
     elif dom in ("p2p_ff", "m2p_ff"):
         a = kernels[dom]["algorithmic_tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 4), "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s (FP64-equivalent)", "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom)),
+                "unit": "TFLOP/s (FP64-equivalent)", "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom, wl["theta"], wl["P"], wl["Ncrit"])),
                 "peak_note": "float-float kernel replacing FP64; peak is the nominal FP64 1.25 TFLOP/s"}
     elif dom is not None:
         roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
