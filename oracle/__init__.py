@@ -79,6 +79,17 @@ def lib():
             L.oracle_solve.argtypes = [_dp, _ip, _i64, _i, _i, _d, _i, _dp, _d, _d, _dp, _dp, _d, _i,
                                        _i, _dp, _dp, _intp, _i]
             L.oracle_solve.restype = _i
+            L.oracle_matvec_multi.argtypes = [_dp, _ip, _ip, _i64, _i, _i, _i, _d, _i, _dp, _dp, _dp, _i]
+            L.oracle_matvec_multi.restype = _i
+            L.oracle_rhs_multi.argtypes = [_dp, _ip, _ip, _i64, _i, _i, _i, _d, _i, _dp, _d, _d, _dp, _dp, _i]
+            L.oracle_rhs_multi.restype = _i
+            L.oracle_gmres_multi.argtypes = [_dp, _ip, _ip, _i64, _i, _i, _i, _d, _dp, _dp, _dp, _d, _i, _i,
+                                             _intp, _dp, _i]
+            L.oracle_gmres_multi.restype = _i
+            L.oracle_dipole_surface.argtypes = [_dp, _ip, _ip, _i64, _i, _dp, _d, _d, _d, _d, _dp, _dp]
+            L.oracle_solve_multi.argtypes = [_dp, _ip, _ip, _i64, _i, _i, _i, _d, _i, _dp, _d, _d, _dp, _dp, _d,
+                                             _i, _i, _dp, _dp, _intp, _i]
+            L.oracle_solve_multi.restype = _i
             _lib = L
     return _lib
 
@@ -245,4 +256,100 @@ def solve(verts, tris, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0), tol=1e-8,
     bad = lib().oracle_solve(_ptr(v), _ptr(t, _ip), n, K, K_fine, threshold, B, _ptr(e.view(np.float64)),
                              e2.real, e2.imag, _ptr(E), _ptr(lam), tol, restart, maxiter,
                              _ptr(dip.view(np.float64)), _ptr(sig), its.ctypes.data_as(_intp), nthreads)
+    return dip, sig, its, bad
+
+
+# ------------------------------------------------------- several surfaces
+# Eqs. integral_eq_lspr_system / matrix_multi: surfaces t = 0..S-1 (surf[i] = surface of
+# panel i) with permittivities eps_t in one host eps_out; surface 0 is the particle whose
+# sigma_ext is reported.
+
+
+def _surf(surf, n):
+    sf = np.ascontiguousarray(surf, dtype=np.int32)
+    if sf.shape != (n,):
+        raise ValueError("surf must hold one surface index per panel")
+    return sf, int(sf.max()) + 1
+
+
+def matvec_multi(verts, tris, surf, x, s, K=4, K_fine=19, threshold=0.5, nthreads=0):
+    """y = A(s) x of several surfaces; x [2n] or [B,2n]; s [S] or [B,S] (eps_t/eps_out)."""
+    v, t, n = _mesh(verts, tris)
+    sf, S = _surf(surf, n)
+    x = _c128(x)
+    squeeze = x.ndim == 1
+    x2 = x.reshape(-1, 2 * n)
+    B = x2.shape[0]
+    s = _c128(np.broadcast_to(np.asarray(s, np.complex128).reshape(-1, S), (B, S)))
+    y = np.zeros_like(x2)
+    rc = lib().oracle_matvec_multi(_ptr(v), _ptr(t, _ip), _ptr(sf, _ip), n, S, K, K_fine, threshold, B,
+                                   _ptr(s.view(np.float64)), _ptr(x2.view(np.float64)), _ptr(y.view(np.float64)),
+                                   nthreads)
+    if rc:
+        raise RuntimeError(f"oracle_matvec_multi failed ({rc})")
+    return y[0] if squeeze else y
+
+
+def rhs_multi(verts, tris, surf, eps_in, eps_out, E0=(0.0, 0.0, 1.0), K=4, K_fine=19, threshold=0.5,
+              nthreads=0):
+    """Right-hand side of several surfaces, [B,2n] for eps_in of shape [S] or [B,S]."""
+    v, t, n = _mesh(verts, tris)
+    sf, S = _surf(surf, n)
+    e = _c128(np.asarray(eps_in, np.complex128).reshape(-1, S))
+    B = e.shape[0]
+    b = np.zeros((B, 2 * n), np.complex128)
+    eo = complex(eps_out)
+    rc = lib().oracle_rhs_multi(_ptr(v), _ptr(t, _ip), _ptr(sf, _ip), n, S, K, K_fine, threshold, B,
+                                _ptr(e.view(np.float64)), eo.real, eo.imag, _ptr(_f64(E0)), _ptr(b.view(np.float64)),
+                                nthreads)
+    if rc:
+        raise RuntimeError(f"oracle_rhs_multi failed ({rc})")
+    return b
+
+
+def gmres_multi(verts, tris, surf, b, s, tol=1e-8, restart=100, maxiter=1000, K=4, K_fine=19, threshold=0.5,
+                nthreads=0):
+    """GMRES of several surfaces for one wavelength, s [S]; returns (x, iters, relres, ok)."""
+    v, t, n = _mesh(verts, tris)
+    sf, S = _surf(surf, n)
+    b = _c128(b)
+    x = np.zeros(2 * n, np.complex128)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0)
+    s = _c128(np.asarray(s, np.complex128).reshape(S))
+    st = lib().oracle_gmres_multi(_ptr(v), _ptr(t, _ip), _ptr(sf, _ip), n, S, K, K_fine, threshold,
+                                  _ptr(s.view(np.float64)), _ptr(b.view(np.float64)), _ptr(x.view(np.float64)),
+                                  tol, restart, maxiter, ctypes.byref(it), ctypes.byref(rr), nthreads)
+    return x, it.value, rr.value, st == 0
+
+
+def dipole_surface(verts, tris, surf, x, surface, eps_in, eps_out, E0=(0.0, 0.0, 1.0)):
+    """Dipole moment of the panels of one surface (eps_in: that surface's permittivity)."""
+    v, t, n = _mesh(verts, tris)
+    sf, _ = _surf(surf, n)
+    x = _c128(x)
+    p = np.zeros(3, np.complex128)
+    e1, e2 = complex(eps_in), complex(eps_out)
+    lib().oracle_dipole_surface(_ptr(v), _ptr(t, _ip), _ptr(sf, _ip), n, int(surface), _ptr(x.view(np.float64)),
+                                e1.real, e1.imag, e2.real, e2.imag, _ptr(_f64(E0)), _ptr(p.view(np.float64)))
+    return p
+
+
+def solve_multi(verts, tris, surf, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0), tol=1e-8, restart=100,
+                maxiter=1000, K=4, K_fine=19, threshold=0.5, nthreads=0):
+    """Several surfaces: RHS + GMRES + dipole and sigma_ext of surface 0 per wavelength;
+    eps_in [B,S]; returns (dipoles [B,3], sigma [B], iters [B], n_bad)."""
+    v, t, n = _mesh(verts, tris)
+    sf, S = _surf(surf, n)
+    e = _c128(np.asarray(eps_in, np.complex128).reshape(-1, S))
+    lam = _f64(np.atleast_1d(lambda_nm))
+    B = e.shape[0]
+    dip = np.zeros((B, 3), np.complex128)
+    sig = np.zeros(B)
+    its = np.zeros(B, dtype=np.int32)
+    e2 = complex(eps_out)
+    bad = lib().oracle_solve_multi(_ptr(v), _ptr(t, _ip), _ptr(sf, _ip), n, S, K, K_fine, threshold, B,
+                                   _ptr(e.view(np.float64)), e2.real, e2.imag, _ptr(_f64(E0)), _ptr(lam), tol,
+                                   restart, maxiter, _ptr(dip.view(np.float64)), _ptr(sig), its.ctypes.data_as(_intp),
+                                   nthreads)
     return dip, sig, its, bad

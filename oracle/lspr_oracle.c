@@ -18,6 +18,9 @@
  *       * far: K-point rule
  *   - the 2x2 block operator of one interface                  [Eq. matrix_lspr]
  *   - its right-hand side V((eps2-eps1)/eps2 dphi_inc/dn)       [Eq. matrix_lspr]
+ *   - the operator of several closed interfaces in one host (a particle
+ *     and analyte surfaces), its right-hand side and the dipole of one
+ *     surface                                                    [Eqs. integral_eq_lspr_system, matrix_multi]
  *   - complex GMRES (restarted, right block-Jacobi preconditioner) and a
  *     dense complex LU with partial pivoting for small systems  [Sec. II.D]
  *   - the dipole moment from boundary data                      [Eq. dipole_def_gauss_i_final]
@@ -40,6 +43,18 @@
  *     L_j / dist >= threshold, L_j = sqrt(2 A_j); evaluated with every
  *     operation rounded separately (build with -ffp-contract=off) so that the
  *     classification is reproducible bit for bit.
+ *
+ *   - several surfaces t = 0..S-1 with permittivities eps_t in one host eps_out:
+ *     on every surface the unknowns are phi (= phi_s on both sides) and the
+ *     interior normal derivative dphi/dn of the scattered potential; the
+ *     interior row of a panel on surface s holds that surface's layer
+ *     potentials only, the exterior row those of every surface, each
+ *     surface's single layer weighted by s_t = eps_t/eps_out:
+ *       top_i = phi_i/2 + (K phi)_{s} - (V dphi)_{s}
+ *       bot_i = phi_i/2 - sum_t (K phi)_t + sum_t s_t (V dphi)_t
+ *     with right-hand side bot_i = sum_t ((eps_out - eps_t)/eps_out)(V dphi_inc/dn)_t
+ *     (one surface: Eq. matrix_lspr).  The cross-section is that of surface 0,
+ *     the particle, whose dipole uses eps_0.
  *
  * Complex arrays cross the C ABI as interleaved (re, im) doubles.
  */
@@ -232,7 +247,11 @@ typedef struct {
     double bary[37 * 3], w[37];       /* far rule */
     double baryf[37 * 3], wf[37];     /* near-singular rule */
     double threshold;
+    const int32_t *surf;              /* surface of each panel (NULL: all surface 0) */
+    int S;                            /* number of surfaces */
 } mesh_t;
+
+static int surf_of(const mesh_t *m, int64_t i) { return m->surf ? m->surf[i] : 0; }
 
 static int mesh_init(mesh_t *m, const double *verts, const int32_t *tris, int64_t n,
                      int K, int Kf, double threshold)
@@ -243,6 +262,8 @@ static int mesh_init(mesh_t *m, const double *verts, const int32_t *tris, int64_
     m->K = K;
     m->Kf = Kf;
     m->threshold = threshold;
+    m->surf = NULL;
+    m->S = 1;
     if (oracle_quad_rule(K, m->bary, m->w) != K) return -1;
     if (oracle_quad_rule(Kf, m->baryf, m->wf) != Kf) return -1;
     m->pan = (panel_t *)malloc(sizeof(panel_t) * (size_t)(n > 0 ? n : 1));
@@ -329,37 +350,49 @@ int64_t oracle_near_pairs(const double *verts, const int32_t *tris, int64_t n, d
 }
 
 /* ------------------------------------------------------------------------- */
-/* Operator of one interface, Eq. matrix_lspr, applied matrix-free.          */
-/*   x = [phi (n) ; dphi/dn (n)], s = eps_in/eps_out                          */
-/*   y_top = phi/2 + K phi - V dphi                                           */
-/*   y_bot = phi/2 - K phi + s V dphi                                         */
+/* Operator of the interfaces, Eqs. matrix_lspr / matrix_multi, matrix-free. */
+/*   x = [phi (n) ; dphi/dn (n)], s[b][t] = eps_t/eps_out of wavelength b     */
+/*   y_top = phi/2 + (K phi)_self - (V dphi)_self                             */
+/*   y_bot = phi/2 - sum_t (K phi)_t + sum_t s_t (V dphi)_t                    */
+/* (one surface: y_bot = phi/2 - K phi + s V dphi).                           */
 /* ------------------------------------------------------------------------- */
 static void apply_operator(const mesh_t *m, int B, const cplx *s, const cplx *x, cplx *y)
 {
     const int64_t n = m->n;
+    const int S = m->S;
 #pragma omp parallel
     {
-        cplx *kv = (cplx *)malloc(sizeof(cplx) * 2 * (size_t)B);
+        /* per wavelength and source surface: kp[b][t] = (K phi)_t, vd[b][t] = (V dphi)_t */
+        cplx *kp = (cplx *)malloc(sizeof(cplx) * (size_t)B * S);
+        cplx *vd = (cplx *)malloc(sizeof(cplx) * (size_t)B * S);
 #pragma omp for schedule(dynamic, 8)
         for (int64_t i = 0; i < n; ++i) {
-            for (int b = 0; b < 2 * B; ++b) kv[b] = 0.0;   /* kv[2b] = (K phi)_i, kv[2b+1] = (V dphi)_i */
+            for (int q = 0; q < B * S; ++q) kp[q] = vd[q] = 0.0;
             for (int64_t j = 0; j < n; ++j) {
                 double V, Kd;
                 entry(m, i, j, &V, &Kd);
+                const int t = surf_of(m, j);
                 for (int b = 0; b < B; ++b) {
                     const cplx *xb = x + (size_t)b * 2 * n;
-                    kv[2 * b] += Kd * xb[j];
-                    kv[2 * b + 1] += V * xb[n + j];
+                    kp[b * S + t] += Kd * xb[j];
+                    vd[b * S + t] += V * xb[n + j];
                 }
             }
+            const int si = surf_of(m, i);
             for (int b = 0; b < B; ++b) {
                 const cplx *xb = x + (size_t)b * 2 * n;
                 cplx *yb = y + (size_t)b * 2 * n;
-                yb[i] = 0.5 * xb[i] + kv[2 * b] - kv[2 * b + 1];
-                yb[n + i] = 0.5 * xb[i] - kv[2 * b] + s[b] * kv[2 * b + 1];
+                cplx kall = 0.0, vall = 0.0;
+                for (int t = 0; t < S; ++t) {
+                    kall += kp[b * S + t];
+                    vall += s[b * S + t] * vd[b * S + t];
+                }
+                yb[i] = 0.5 * xb[i] + kp[b * S + si] - vd[b * S + si];
+                yb[n + i] = 0.5 * xb[i] - kall + vall;
             }
         }
-        free(kv);
+        free(kp);
+        free(vd);
     }
 }
 
@@ -385,6 +418,49 @@ int oracle_matvec(const double *verts, const int32_t *tris, int64_t n, int K, in
     return 0;
 }
 
+/* Several surfaces: surf [n] surface of each panel (0..S-1); s: [B][S] complex. */
+int oracle_matvec_multi(const double *verts, const int32_t *tris, const int32_t *surf, int64_t n, int S,
+                        int K, int Kf, double threshold, int B, const double *s, const double *x, double *y,
+                        int nthreads)
+{
+    mesh_t m;
+    set_threads(nthreads);
+    int rc = mesh_init(&m, verts, tris, n, K, Kf, threshold);
+    if (rc) return rc;
+    m.surf = surf;
+    m.S = S;
+    apply_operator(&m, B, (const cplx *)s, (const cplx *)x, (cplx *)y);
+    mesh_free(&m);
+    return 0;
+}
+
+/* Right-hand side: top 0, bottom sum_t ((eps_out - eps_t)/eps_out) (V dphi_inc/dn)_t,
+ * dphi_inc/dn = -E0.n (one surface: Eq. matrix_lspr).  e1: [B][S] complex. */
+static void rhs_impl(const mesh_t *m, int B, const cplx *e1, cplx e2, const double *E0, cplx *b)
+{
+    const int64_t n = m->n;
+    const int S = m->S;
+    double *vinc = (double *)malloc(sizeof(double) * (size_t)n * S);   /* [i][t] */
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int t = 0; t < S; ++t) vinc[i * S + t] = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double V, Kd;
+            entry(m, i, j, &V, &Kd);
+            double dphi_inc = -(E0[0] * m->pan[j].n[0] + E0[1] * m->pan[j].n[1] + E0[2] * m->pan[j].n[2]);
+            vinc[i * S + surf_of(m, j)] += V * dphi_inc;
+        }
+    }
+    for (int bb = 0; bb < B; ++bb)
+        for (int64_t i = 0; i < n; ++i) {
+            cplx acc = 0.0;
+            for (int t = 0; t < S; ++t) acc += ((e2 - e1[bb * S + t]) / e2) * vinc[i * S + t];
+            b[(size_t)bb * 2 * n + i] = 0.0;
+            b[(size_t)bb * 2 * n + n + i] = acc;
+        }
+    free(vinc);
+}
+
 /* Right-hand side of Eq. matrix_lspr: top 0, bottom V((eps2-eps1)/eps2 dphi_inc/dn),
  * dphi_inc/dn = -E0.n.  b: [B][2n]; eps_in: [B] complex; eps_out complex (re, im). */
 int oracle_rhs(const double *verts, const int32_t *tris, int64_t n, int K, int Kf, double threshold,
@@ -395,27 +471,23 @@ int oracle_rhs(const double *verts, const int32_t *tris, int64_t n, int K, int K
     set_threads(nthreads);
     int rc = mesh_init(&m, verts, tris, n, K, Kf, threshold);
     if (rc) return rc;
-    const cplx *e1 = (const cplx *)eps_in;
-    cplx e2 = eps_out_re + I * eps_out_im;
-    cplx *b = (cplx *)bout;
-    double *vinc = (double *)malloc(sizeof(double) * (size_t)n);
-#pragma omp parallel for schedule(dynamic, 8)
-    for (int64_t i = 0; i < n; ++i) {
-        double acc = 0.0;
-        for (int64_t j = 0; j < n; ++j) {
-            double V, Kd;
-            entry(&m, i, j, &V, &Kd);
-            double dphi_inc = -(E0[0] * m.pan[j].n[0] + E0[1] * m.pan[j].n[1] + E0[2] * m.pan[j].n[2]);
-            acc += V * dphi_inc;
-        }
-        vinc[i] = acc;
-    }
-    for (int bb = 0; bb < B; ++bb)
-        for (int64_t i = 0; i < n; ++i) {
-            b[(size_t)bb * 2 * n + i] = 0.0;
-            b[(size_t)bb * 2 * n + n + i] = ((e2 - e1[bb]) / e2) * vinc[i];
-        }
-    free(vinc);
+    rhs_impl(&m, B, (const cplx *)eps_in, eps_out_re + I * eps_out_im, E0, (cplx *)bout);
+    mesh_free(&m);
+    return 0;
+}
+
+/* The same for several surfaces: eps_in [B][S] complex. */
+int oracle_rhs_multi(const double *verts, const int32_t *tris, const int32_t *surf, int64_t n, int S, int K,
+                     int Kf, double threshold, int B, const double *eps_in, double eps_out_re,
+                     double eps_out_im, const double *E0, double *bout, int nthreads)
+{
+    mesh_t m;
+    set_threads(nthreads);
+    int rc = mesh_init(&m, verts, tris, n, K, Kf, threshold);
+    if (rc) return rc;
+    m.surf = surf;
+    m.S = S;
+    rhs_impl(&m, B, (const cplx *)eps_in, eps_out_re + I * eps_out_im, E0, (cplx *)bout);
     mesh_free(&m);
     return 0;
 }
@@ -473,12 +545,13 @@ static double vnorm(const cplx *v, int64_t n)
     return sqrt(s);
 }
 
-static void precond(const mesh_t *m, const double *Vii, cplx s, const cplx *u, cplx *x)
+static void precond(const mesh_t *m, const double *Vii, const cplx *s, const cplx *u, cplx *x)
 {
     const int64_t n = m->n;
     for (int64_t i = 0; i < n; ++i) {
-        /* [[a, b], [c, d]] = [[1/2, -V], [1/2, s V]] (K_ii = 0 on flat panels) */
-        cplx a = 0.5, bq = -Vii[i], c = 0.5, d = s * Vii[i];
+        /* [[a, b], [c, d]] = [[1/2, -V], [1/2, s V]] (K_ii = 0 on flat panels), s of the
+         * panel's surface */
+        cplx a = 0.5, bq = -Vii[i], c = 0.5, d = s[surf_of(m, i)] * Vii[i];
         cplx det = a * d - bq * c;
         cplx u0 = u[i], u1 = u[n + i];
         x[i] = (d * u0 - bq * u1) / det;
@@ -486,16 +559,13 @@ static void precond(const mesh_t *m, const double *Vii, cplx s, const cplx *u, c
     }
 }
 
-int oracle_gmres(const double *verts, const int32_t *tris, int64_t n, int K, int Kf, double threshold,
-                 double s_re, double s_im, const double *bin, double *xout, double tol, int restart,
-                 int maxiter, int *iters_out, double *relres_out, int nthreads)
+/* GMRES(restart) for one wavelength, s[t] = eps_t/eps_out per surface */
+static int gmres_impl(mesh_t *mp, const cplx *s, const double *bin, double *xout, double tol, int restart,
+                      int maxiter, int *iters_out, double *relres_out)
 {
-    mesh_t m;
-    set_threads(nthreads);
-    int rc = mesh_init(&m, verts, tris, n, K, Kf, threshold);
-    if (rc) return rc;
+    mesh_t m = *mp;
+    const int64_t n = m.n;
     const int64_t N2 = 2 * n;
-    const cplx s = s_re + I * s_im;
     const cplx *b = (const cplx *)bin;
     cplx *x = (cplx *)xout;
     double *Vii = (double *)malloc(sizeof(double) * (size_t)n);
@@ -517,7 +587,7 @@ int oracle_gmres(const double *verts, const int32_t *tris, int64_t n, int K, int
     int status = 1;
     while (1) {
         /* explicit residual r = b - A x */
-        apply_operator(&m, 1, &s, x, w);
+        apply_operator(&m, 1, s, x, w);
         for (int64_t i = 0; i < N2; ++i) w[i] = b[i] - w[i];
         double beta = vnorm(w, N2);
         relres = beta / bnorm;
@@ -530,7 +600,7 @@ int oracle_gmres(const double *verts, const int32_t *tris, int64_t n, int K, int
         for (; j < mr && it < maxiter; ++j) {
             cplx *vj = Vb + (size_t)j * N2, *vn = Vb + (size_t)(j + 1) * N2;
             precond(&m, Vii, s, vj, z);
-            apply_operator(&m, 1, &s, z, w);
+            apply_operator(&m, 1, s, z, w);
             /* modified Gram-Schmidt, applied twice */
             for (int pass = 0; pass < 2; ++pass)
                 for (int i = 0; i <= j; ++i) {
@@ -585,8 +655,37 @@ int oracle_gmres(const double *verts, const int32_t *tris, int64_t n, int K, int
     if (iters_out) *iters_out = it;
     if (relres_out) *relres_out = relres;
     free(Vb); free(H); free(cs); free(sn); free(g); free(yv); free(w); free(z); free(Vii);
-    mesh_free(&m);
     return status;
+}
+
+int oracle_gmres(const double *verts, const int32_t *tris, int64_t n, int K, int Kf, double threshold,
+                 double s_re, double s_im, const double *bin, double *xout, double tol, int restart,
+                 int maxiter, int *iters_out, double *relres_out, int nthreads)
+{
+    mesh_t m;
+    set_threads(nthreads);
+    int rc = mesh_init(&m, verts, tris, n, K, Kf, threshold);
+    if (rc) return rc;
+    const cplx s = s_re + I * s_im;
+    int st = gmres_impl(&m, &s, bin, xout, tol, restart, maxiter, iters_out, relres_out);
+    mesh_free(&m);
+    return st;
+}
+
+/* Several surfaces: s [S] complex (eps_t/eps_out of one wavelength). */
+int oracle_gmres_multi(const double *verts, const int32_t *tris, const int32_t *surf, int64_t n, int S, int K,
+                       int Kf, double threshold, const double *s, const double *bin, double *xout, double tol,
+                       int restart, int maxiter, int *iters_out, double *relres_out, int nthreads)
+{
+    mesh_t m;
+    set_threads(nthreads);
+    int rc = mesh_init(&m, verts, tris, n, K, Kf, threshold);
+    if (rc) return rc;
+    m.surf = surf;
+    m.S = S;
+    int st = gmres_impl(&m, (const cplx *)s, bin, xout, tol, restart, maxiter, iters_out, relres_out);
+    mesh_free(&m);
+    return st;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -605,6 +704,30 @@ void oracle_dipole(const double *verts, const int32_t *tris, int64_t n, int64_t 
     cplx e1 = eps_in_re + I * eps_in_im, e2 = eps_out_re + I * eps_out_im;
     cplx p[3] = {0, 0, 0};
     for (int64_t j = p0; j < p1; ++j) {
+        panel_t pj;
+        make_panel(verts, tris, j, &pj);
+        double dinc = -(E0[0] * pj.n[0] + E0[1] * pj.n[1] + E0[2] * pj.n[2]);
+        cplx d2 = (e1 / e2) * x[n + j] - ((e2 - e1) / e2) * dinc;
+        for (int d = 0; d < 3; ++d) p[d] += pj.area * (pj.c[d] * d2 - x[j] * pj.n[d]);
+    }
+    for (int d = 0; d < 3; ++d) {
+        cplx v = -e2 * p[d];
+        pout[2 * d] = creal(v);
+        pout[2 * d + 1] = cimag(v);
+    }
+}
+
+/* Dipole moment of the panels of surface `surface` (the formula of oracle_dipole with
+ * that surface's eps). */
+void oracle_dipole_surface(const double *verts, const int32_t *tris, const int32_t *surf, int64_t n,
+                           int surface, const double *xin, double eps_in_re, double eps_in_im,
+                           double eps_out_re, double eps_out_im, const double *E0, double *pout)
+{
+    const cplx *x = (const cplx *)xin;
+    cplx e1 = eps_in_re + I * eps_in_im, e2 = eps_out_re + I * eps_out_im;
+    cplx p[3] = {0, 0, 0};
+    for (int64_t j = 0; j < n; ++j) {
+        if (surf[j] != surface) continue;
         panel_t pj;
         make_panel(verts, tris, j, &pj);
         double dinc = -(E0[0] * pj.n[0] + E0[1] * pj.n[1] + E0[2] * pj.n[2]);
@@ -669,5 +792,44 @@ int oracle_solve(const double *verts, const int32_t *tris, int64_t n, int K, int
     }
     free(b);
     free(x);
+    return bad;
+}
+
+/* Several surfaces, one wavelength after another: RHS, GMRES, dipole of surface 0
+ * (the particle) and its sigma_ext.  eps_in: [B][S] complex.  Returns the number of
+ * wavelengths that did not converge. */
+int oracle_solve_multi(const double *verts, const int32_t *tris, const int32_t *surf, int64_t n, int S, int K,
+                       int Kf, double threshold, int B, const double *eps_in, double eps_out_re,
+                       double eps_out_im, const double *E0, const double *lambda_nm, double tol, int restart,
+                       int maxiter, double *dip_out, double *sigma_out, int *iters_out, int nthreads)
+{
+    const int64_t N2 = 2 * n;
+    double *b = (double *)malloc(sizeof(double) * 2 * (size_t)N2);
+    double *x = (double *)malloc(sizeof(double) * 2 * (size_t)N2);
+    double *s = (double *)malloc(sizeof(double) * 2 * (size_t)S);
+    int bad = 0;
+    const cplx e2 = eps_out_re + I * eps_out_im;
+    for (int bb = 0; bb < B; ++bb) {
+        const double *e1 = eps_in + 2 * (size_t)S * bb;
+        oracle_rhs_multi(verts, tris, surf, n, S, K, Kf, threshold, 1, e1, eps_out_re, eps_out_im, E0, b,
+                         nthreads);
+        for (int t = 0; t < S; ++t) {
+            cplx st = (e1[2 * t] + I * e1[2 * t + 1]) / e2;
+            s[2 * t] = creal(st);
+            s[2 * t + 1] = cimag(st);
+        }
+        int it = 0;
+        double rr = 0;
+        int st = oracle_gmres_multi(verts, tris, surf, n, S, K, Kf, threshold, s, b, x, tol, restart, maxiter,
+                                    &it, &rr, nthreads);
+        if (st) ++bad;
+        if (iters_out) iters_out[bb] = it;
+        oracle_dipole_surface(verts, tris, surf, n, 0, x, e1[0], e1[1], eps_out_re, eps_out_im, E0,
+                              dip_out + 6 * bb);
+        sigma_out[bb] = oracle_sigma_ext(dip_out + 6 * bb, eps_out_re, eps_out_im, E0, lambda_nm[bb]);
+    }
+    free(b);
+    free(x);
+    free(s);
     return bad;
 }

@@ -151,6 +151,67 @@ def protein_like(subdivisions: int = 6, axes=(7.0, 4.0, 4.0), lmax: int = 8,
     return np.ascontiguousarray(v), _orient_outward(v, t.astype(np.int64)).astype(np.int32)
 
 
+# Rotations that take a surface whose long axis is x to a placement axis: first x -> +z;
+# the -z copy is the 180-degree rotation of the +z one about y, and +-x, +-y are 90-degree
+# rotations of the +z placement (the sensor arrangements of Sec. III).
+_TO_Z = np.array([[0.0, 0.0, -1.0], [0.0, 1.0, 0.0], [1.0, 0.0, 0.0]])
+_FROM_Z = {
+    "+z": np.eye(3),
+    "-z": np.diag([-1.0, 1.0, -1.0]),
+    "+x": np.array([[0.0, 0.0, 1.0], [0.0, 1.0, 0.0], [-1.0, 0.0, 0.0]]),
+    "-x": np.array([[0.0, 0.0, -1.0], [0.0, 1.0, 0.0], [1.0, 0.0, 0.0]]),
+    "+y": np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 1.0], [0.0, -1.0, 0.0]]),
+    "-y": np.array([[1.0, 0.0, 0.0], [0.0, 0.0, -1.0], [0.0, 1.0, 0.0]]),
+}
+_AXIS = {"+z": (0, 0, 1), "-z": (0, 0, -1), "+x": (1, 0, 0), "-x": (-1, 0, 0), "+y": (0, 1, 0), "-y": (0, -1, 0)}
+
+
+def place_analyte(verts: np.ndarray, axis: str, gap: float, R: float) -> np.ndarray:
+    """Rotate a surface centred at the origin (long axis x) onto `axis` and move it along
+    that axis until its closest vertex lies `gap` nm outside the sphere of radius R."""
+    v = verts @ (_FROM_Z[axis] @ _TO_Z).T
+    u = np.asarray(_AXIS[axis], float)
+
+    def clearance(d):
+        return np.min(np.linalg.norm(v + d * u, axis=1)) - R
+
+    lo, hi = 0.0, R + gap + 2.0 * np.max(np.linalg.norm(v, axis=1))
+    for _ in range(200):   # clearance grows with d once the surface is outside the sphere
+        mid = 0.5 * (lo + hi)
+        if clearance(mid) < gap:
+            lo = mid
+        else:
+            hi = mid
+    return np.ascontiguousarray(v + hi * u)
+
+
+def sensor_geometry(sphere_sub: int = 6, R: float = 10.0, analytes=(("+z", 1.0), ("-z", 1.0)),
+                    analyte_sub: int = 6, axes=(7.0, 4.0, 4.0), seed0: int = 1812):
+    """Sphere (surface 0) plus protein-like analytes (surfaces 1, 2, ...) at the given
+    (axis, gap) placements; analyte k is drawn with seed seed0 + k.  Returns (verts, tris, surf)."""
+    vs, ts = icosphere(sphere_sub, R)
+    parts_v, parts_t, surf = [vs], [ts], [np.zeros(len(ts), np.int32)]
+    off = len(vs)
+    for k, (axis, gap) in enumerate(analytes):
+        va, ta = protein_like(analyte_sub, axes, seed=seed0 + k)
+        va = place_analyte(va, axis, gap, R)
+        parts_v.append(va)
+        parts_t.append(ta + off)
+        surf.append(np.full(len(ta), k + 1, np.int32))
+        off += len(va)
+    return (np.ascontiguousarray(np.concatenate(parts_v)), np.ascontiguousarray(np.concatenate(parts_t), np.int32),
+            np.concatenate(surf))
+
+
+def two_spheres(subdivisions: int, R: float, distance: float):
+    """Two equal spheres, surface 0 at the origin and surface 1 centred at (0, 0, distance)."""
+    v, t = icosphere(subdivisions, R)
+    v1 = v + np.array([0.0, 0.0, distance])
+    return (np.ascontiguousarray(np.concatenate([v, v1])),
+            np.ascontiguousarray(np.concatenate([t, t + len(v)]), np.int32),
+            np.concatenate([np.zeros(len(t), np.int32), np.ones(len(t), np.int32)]))
+
+
 def drude_eps(lambda_nm, eps_inf=DRUDE_AG["eps_inf"], wp=DRUDE_AG["wp"], gamma=DRUDE_AG["gamma"]):
     """Drude permittivity eps_inf - wp^2/(w^2 + i*gamma*w), w = 1239.84198/lambda eV."""
     w = HC_EV_NM / np.asarray(lambda_nm, dtype=np.float64)
