@@ -119,7 +119,9 @@ LSPR_API int lspr_destroy(lspr_ctx *ctx);
  *   - the near-singular list (L_j/|c_i - c_j| >= threshold) and, per near pair,
  *     the FP64 correction (K_fine rule minus K rule) of V_ij and K_ij
  * verts: [nv][3] doubles; tris: [ntri][3] vertex indices (int32); surf_id: [ntri]
- * surface index in [0, nsurf) (null = all 0).  Only nsurf == 1 is supported.
+ * surface index in [0, nsurf), 1 <= nsurf <= 16 (may be null when nsurf == 1).
+ * Surfaces are closed and disjoint (Eq. integral_eq_lspr_system): surface 0 is the
+ * particle whose dipole gives sigma_ext, the others analytes in the same host.
  * on_device = 0: host pointers; 1: device pointers on the context's device.
  * The library copies the data; the caller keeps ownership.  Invalidates any tree.
  * Errors: LSPR_E_ARG (sizes, rules, indices out of range), LSPR_E_MESH
@@ -141,6 +143,10 @@ LSPR_API int lspr_tree_build(lspr_ctx *ctx, double theta, int32_t P, int32_t Ncr
 /* y[b] = A(s_b) x[b] for b < B, A the block operator of Eq. matrix_lspr:
  *   y_top = phi/2 + K phi - V dphi,   y_bot = phi/2 - K phi + s_b V dphi,
  * with s_b = eps_ratio[b] = eps_in/eps_out (complex).  x, y: [B][2N] complex.
+ * Several surfaces (Eq. matrix_multi): for panel i on surface s,
+ *   y_top = phi/2 + (K phi)_s - (V dphi)_s,
+ *   y_bot = phi/2 - sum_t (K phi)_t + sum_t s_bt (V dphi)_t,
+ * (.)_t the layer potential of surface t's panels, eps_ratio [B][nsurf] complex.
  * on_device = 0: x, y, eps_ratio are host pointers; 1: device pointers.  The
  * call is complete (stream synchronised) on return.
  * Errors: LSPR_E_STATE (no mesh; tree mode without a tree), LSPR_E_ARG, LSPR_E_CUDA. */
@@ -149,7 +155,7 @@ LSPR_API int lspr_matvec(lspr_ctx *ctx, const double *x, double *y, int32_t B, c
 
 /* Solve the interface problem for B wavelengths and return the induced dipole
  * and the extinction cross-section of each (host pointers):
- *   eps_in   [B] complex   particle permittivity per wavelength
+ *   eps_in   [B][nsurf] complex  permittivity of every surface per wavelength
  *   eps_out                host permittivity (re, im)
  *   E0       [3]           incident field amplitude (direction = polarisation)
  *   lambda_nm[B]           vacuum wavelengths
@@ -249,7 +255,7 @@ LSPR_API int lspr_graph_stats(lspr_ctx *ctx, int64_t *cycles, int64_t *recording
  * The first call on a device looks up the array's device address (make it before
  * any stream capture).  All calls on a device share the array and leave their
  * contents in it; calls that overlap on the GPU race and must be serialised.
- * Errors: LSPR_E_ARG, LSPR_E_STATE (no mesh), LSPR_E_CUDA. */
+ * Errors: LSPR_E_ARG, LSPR_E_STATE (no mesh, or a mesh of several surfaces), LSPR_E_CUDA. */
 LSPR_API int lspr_matvec_direct_fp32_noalloc(lspr_ctx *ctx, const double *x, double *y, double s_re, double s_im);
 
 #ifdef __cplusplus

@@ -128,11 +128,11 @@ int lspr_destroy(lspr_ctx *c) {
 
 int lspr_mesh_upload(lspr_ctx *c, const double *verts, int64_t nv, const int32_t *tris, int64_t ntri,
                      const int32_t *surf_id, int32_t nsurf, const lspr_quad_opts *q, int32_t on_device) {
-    if (!c || !verts || !tris || !q || nv < 3 || ntri < 1 || nsurf != 1) return LSPR_E_ARG;
+    if (!c || !verts || !tris || !q || nv < 3 || ntri < 1 || nsurf < 1 || nsurf > kMaxSurfaces) return LSPR_E_ARG;
+    if (nsurf > 1 && !surf_id) return LSPR_E_ARG;
     if (ntri > (int64_t)1 << 28 || nv > (int64_t)1 << 30) return LSPR_E_ARG;
-    (void)surf_id;
     cudaSetDevice(c->device);
-    return mesh_build(c, verts, nv, tris, ntri, on_device, *q);
+    return mesh_build(c, verts, nv, tris, ntri, nsurf > 1 ? surf_id : nullptr, nsurf, on_device, *q);
 }
 
 int lspr_tree_build(lspr_ctx *c, double theta, int32_t P, int32_t Ncrit) {
@@ -156,9 +156,11 @@ int lspr_matvec(lspr_ctx *c, const double *x, double *y, int32_t B, const double
     if (!on_device) {
         LSPR_TRY(c, c->xbuf.ensure((size_t)B * n2));
         LSPR_TRY(c, c->ybuf.ensure((size_t)B * n2));
-        LSPR_TRY(c, c->sbuf.ensure(B));
+        const int S = c->mesh.S;   // eps_ratio is [B][S]
+        LSPR_TRY(c, c->sbuf.ensure((size_t)B * S));
         LSPR_TRY(c, cudaMemcpyAsync(c->xbuf.p, x, sizeof(double2) * B * n2, cudaMemcpyHostToDevice, c->stream));
-        LSPR_TRY(c, cudaMemcpyAsync(c->sbuf.p, eps_ratio, sizeof(double2) * B, cudaMemcpyHostToDevice, c->stream));
+        LSPR_TRY(c, cudaMemcpyAsync(c->sbuf.p, eps_ratio, sizeof(double2) * B * S, cudaMemcpyHostToDevice,
+                                    c->stream));
         xd = c->xbuf.p;
         yd = c->ybuf.p;
         sd = c->sbuf.p;

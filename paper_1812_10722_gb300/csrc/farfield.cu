@@ -35,16 +35,26 @@ namespace lspr {
 // (identity without a map; only the first *nact slots are formed when nact is given);
 // x is [B][2N] complex
 template <typename T4>
-__global__ void weights_kernel(int64_t Ns, int64_t N, int B, const dbl4 *__restrict__ spos64,
-                               const int *__restrict__ src_panel, const double2 *__restrict__ x,
-                               const double2 *__restrict__ xt, T4 *__restrict__ w, const int *map, const int *nact) {
+// Several surfaces (S > 1): channel set slot = b * S + t carries the weights of the sources
+// of surface t only (zero elsewhere), so that each surface's layer potentials come out
+// separately; BS = B * S sets per source.
+__global__ void weights_kernel(int64_t Ns, int64_t N, int B, int S, const dbl4 *__restrict__ spos64,
+                               const int *__restrict__ src_panel, const int *__restrict__ surf,
+                               const double2 *__restrict__ x, const double2 *__restrict__ xt, T4 *__restrict__ w,
+                               const int *map, const int *nact) {
+    const int BS = B * S;
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= Ns * B) return;
-    const int64_t s = g / B;
-    const int slot = (int)(g - s * B);
+    if (g >= Ns * BS) return;
+    const int64_t s = g / BS;
+    const int slot = (int)(g - s * BS);
     if (nact && slot >= *nact) return;
-    const int b = map ? map[slot] : slot;
     const int p = src_panel[s];
+    const int bs = map ? map[slot] : slot;
+    const int b = bs / S;
+    if (S > 1 && surf[p] != bs - b * S) {
+        w[g] = zero4<T4>();
+        return;
+    }
     const double wa = spos64[s].w * kInv4Pi;
     // x [B][2N], or its transposed copy xt [2N][B] when given
     const double2 phi = xt ? xt[(int64_t)p * B + b] : x[(int64_t)b * 2 * N + p];
@@ -83,23 +93,24 @@ __global__ void to_ff_kernel(int64_t n, const dbl4 *__restrict__ a, ff4 *__restr
 }
 
 // --------------------------------------------------------------- launchers
-int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt, int64_t N, int B) {
+int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt, int64_t N, int B, int S) {
     const int64_t Ns = ctx->mesh.Ns;
-    const unsigned grid = grid_for(Ns * B, 256);
+    const int BS = B * S;
+    const unsigned grid = grid_for(Ns * BS, 256);
     cudaEvent_t ev;
     timer_begin(ctx, T_WEIGHTS, &ev);
     ++ctx->n_launches;
     if (prec == PREC_F64) {
-        LSPR_TRY(ctx, ctx->w64.ensure(Ns * B));
-        weights_kernel<dbl4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x, xt,
+        LSPR_TRY(ctx, ctx->w64.ensure(Ns * BS));
+        weights_kernel<dbl4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, S, ctx->wo.spos64.p, ctx->wo.src_panel.p, ctx->mesh.surf.p, x, xt,
                                                             ctx->w64.p, ctx->rhs_map, ctx->rhs_nact);
     } else if (prec == PREC_FF) {
-        LSPR_TRY(ctx, ctx->w_ff.ensure(Ns * B));
-        weights_kernel<ff4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x, xt,
+        LSPR_TRY(ctx, ctx->w_ff.ensure(Ns * BS));
+        weights_kernel<ff4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, S, ctx->wo.spos64.p, ctx->wo.src_panel.p, ctx->mesh.surf.p, x, xt,
                                                            ctx->w_ff.p, ctx->rhs_map, ctx->rhs_nact);
     } else {
-        LSPR_TRY(ctx, ctx->w32.ensure(Ns * B));
-        weights_kernel<float4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, ctx->wo.spos64.p, ctx->wo.src_panel.p, x, xt,
+        LSPR_TRY(ctx, ctx->w32.ensure(Ns * BS));
+        weights_kernel<float4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, S, ctx->wo.spos64.p, ctx->wo.src_panel.p, ctx->mesh.surf.p, x, xt,
                                                               ctx->w32.p, ctx->rhs_map, ctx->rhs_nact);
     }
     timer_end(ctx, T_WEIGHTS, ev);
@@ -215,7 +226,7 @@ int launch_m2p(lspr_ctx *ctx, int prec, double *acc, int *counter, int B) {
 // by the allocation-free matvec entry point.
 int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
                             const double2 *x, float4 *w) {
-    weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, st>>>(Ns, N, 1, spos64, src_panel, x, nullptr, w, nullptr,
+    weights_kernel<float4><<<grid_for(Ns, 256), 256, 0, st>>>(Ns, N, 1, 1, spos64, src_panel, nullptr, x, nullptr, w, nullptr,
                                                                nullptr);
     return cudaGetLastError() == cudaSuccess ? LSPR_OK : LSPR_E_CUDA;
 }

@@ -35,6 +35,8 @@ struct Arn {
     double2 *V, *w, *z, *x;
     const double2 *b, *s;
     const double *Vself;
+    const int *surf;   // surface of each panel; s is [B][S]
+    int S;
     double2 *h, *hcol, *part, *H, *sn, *g, *y;
     double *npart, *nrm, *cs, *res;
     const double *bn, *par;
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(kT) arn_precond_kernel(Arn a) {
         Vj[a.N + t] = u1;
     }
     double2 o0, o1;
-    block_jacobi(a.Vself[t], a.s[b], u0, u1, o0, o1);
+    block_jacobi(a.Vself[t], a.s[b * a.S + a.surf[t]], u0, u1, o0, o1);
     a.z[(int64_t)b * a.n2 + t] = o0;
     a.z[(int64_t)b * a.n2 + a.N + t] = o1;
 }
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(kT) arn_update_kernel(Arn a) {
         u1 = cadd(u1, cmul(Vb[(int64_t)i * a.n2 + a.N + t], yi));
     }
     double2 o0, o1;
-    block_jacobi(a.Vself[t], a.s[b], u0, u1, o0, o1);
+    block_jacobi(a.Vself[t], a.s[b * a.S + a.surf[t]], u0, u1, o0, o1);
     double2 *xb = a.x + (int64_t)b * a.n2;
     xb[t] = cadd(xb[t], o0);
     xb[a.N + t] = cadd(xb[a.N + t], o1);
@@ -431,10 +433,13 @@ int capture_cycle(lspr_ctx *ctx, int mode, const Arn &a0, GraphCache &gc) {
     capturing = true;
     arn_precond_kernel<<<gN, kT, 0, cs>>>(a);
     ++ctx->n_launches;
-    // the product works on the running systems only, packed into the first slots
-    ctx->rhs_map = a.rmap;
-    ctx->rhs_inv = a.rmap + a.B;
-    ctx->rhs_nact = a.rmap + 2 * a.B;
+    // the product works on the running systems only, packed into the first slots (one
+    // surface; with several, the channel sets are (system, surface) pairs and all run)
+    if (a.S == 1) {
+        ctx->rhs_map = a.rmap;
+        ctx->rhs_inv = a.rmap + a.B;
+        ctx->rhs_nact = a.rmap + 2 * a.B;
+    }
     const int rc = apply_operator(ctx, mode, a.z, a.w, a.s, a.B);
     ctx->rhs_map = ctx->rhs_inv = ctx->rhs_nact = nullptr;
     if (rc != LSPR_OK) return fail(rc);
@@ -521,6 +526,8 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     a.b = b_d;
     a.s = s_d;
     a.Vself = me.Vself.p;
+    a.surf = me.surf.p;
+    a.S = me.S;
     a.h = ab.h.p;
     a.hcol = ab.hcol.p;
     a.part = ab.part.p;
@@ -585,7 +592,7 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
                             (uint64_t)N, (uint64_t)me.Ns, (uint64_t)me.nnz, (uint64_t)tr.ready, (uint64_t)tr.P,
                             (uint64_t)tr.NT, (uint64_t)tr.nboxes, (uint64_t)tr.n_p2p_items,
                             (uint64_t)tr.n_m2p_items, (uint64_t)tr.n_p2m_items, (uint64_t)ctx->direct.n,
-                            (uint64_t)(uintptr_t)ctx->gm_V.p, (uint64_t)ctx->num_sms, 0, 0, 0, 0};
+                            (uint64_t)(uintptr_t)ctx->gm_V.p, (uint64_t)ctx->num_sms, (uint64_t)me.S, 0, 0, 0};
         GraphCache *gc = nullptr;
         for (GraphCache &c : ctx->gcache)
             if (c.exec && std::equal(key, key + 24, c.key)) gc = &c;

@@ -43,6 +43,7 @@ constexpr int kTargetBlock = 64;                       // targets per interactio
 constexpr int kMaxP = 8;                               // highest Taylor order compiled
 constexpr int kMaxDepth = 10;                          // octree levels below the root (10 bits per axis)
 constexpr int kMaxNk = 32;
+constexpr int kMaxSurfaces = 16;                       // particle + analyte surfaces
 
 // number of multi-indices with |k| <= P
 __host__ __device__ constexpr int n_terms(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
@@ -108,6 +109,8 @@ struct Mesh {
     DArr<double> verts;                   // [nv*3]
     DArr<int> tris;                       // [N*3]
     DArr<double> cx, cy, cz, nx, ny, nz, area, L, Vself;   // [N]
+    int S = 1;                            // surfaces (surface 0: the particle)
+    DArr<int> surf;                       // [N] surface of each panel
     // natural-order sources (s = K*i + g) and targets (i)
     DArr<dbl4> src_pos64, src_nrm64;
     DArr<dbl4> tgt64;
@@ -287,7 +290,9 @@ void timer_collect(lspr_ctx *ctx);
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
 // ------------------------------------------------------------ mesh.cu
-int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, int64_t ntri, int on_device,
+// surf: [ntri] surface index of each panel in [0, nsurf) (null: one surface)
+int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, int64_t ntri, const int *surf,
+               int nsurf, int on_device,
                const lspr_quad_opts &q);
 // natural-order work arrays (direct mode)
 int workorder_natural(lspr_ctx *ctx);
@@ -321,7 +326,8 @@ int launch_ff_boxes(lspr_ctx *ctx);
 // item.w = 1 where a P2P item may contain sources of its own target block's panels
 int launch_item_flags(lspr_ctx *ctx, int4 *items, int64_t nitems);
 // xt: x transposed to [2N][B] (B > 1), or null
-int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt, int64_t N, int B);
+// S > 1 surfaces: B x S channel sets, weights of set (b, t) masked to the sources of surface t
+int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt, int64_t N, int B, int S);
 int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
                             const double2 *x, float4 *w);
 int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, const float4 *tgt, int64_t ntgt,
@@ -331,6 +337,7 @@ int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, cons
 // y = A(s) x for one right-hand side, x and y device [2N] complex
 int apply_operator(lspr_ctx *ctx, int mode, const double2 *x, double2 *y, const double2 *s, int B);
 // layer potentials without the block assembly: out[i] = (V dphi)_i, (K phi)_i
+// per source surface t (S of them): Vd[t * N + i] = (V dphi)_t, Kp[t * N + i] = (K phi)_t
 int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, double2 *Kp);
 int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
                const double *lambda_nm, int B, const lspr_solve_opts &o, double *dipole_out, double *sigma_out,

@@ -456,8 +456,14 @@ int cuda_status(lspr_ctx *ctx, cudaError_t e, const char *what) {
     return LSPR_E_CUDA;
 }
 
-int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, int64_t N, int on_device,
-               const lspr_quad_opts &q) {
+// flags[0] |= 1 for a surface index outside [0, S)
+__global__ void surf_check_kernel(int64_t N, int S, const int *__restrict__ surf, int *flag) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N && (surf[i] < 0 || surf[i] >= S)) atomicOr(flag, 1);
+}
+
+int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, int64_t N, const int *surf,
+               int nsurf, int on_device, const lspr_quad_opts &q) {
     Mesh &m = ctx->mesh;
     cudaStream_t st = ctx->stream;
     m.ready = false;
@@ -496,6 +502,15 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     Tmp<double> flags(ctx->scratch[0]);
     LSPR_TRY(ctx, flags.ensure(4));
     LSPR_TRY(ctx, cudaMemsetAsync(flags.p, 0, 4 * sizeof(double), st));
+    m.S = nsurf;
+    LSPR_TRY(ctx, m.surf.ensure(N));
+    if (surf) {
+        LSPR_TRY(ctx, cudaMemcpyAsync(m.surf.p, surf, sizeof(int) * N, kind, st));
+        ++ctx->n_launches;
+        surf_check_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, nsurf, m.surf.p, (int *)flags.p);
+    } else {
+        LSPR_TRY(ctx, cudaMemsetAsync(m.surf.p, 0, sizeof(int) * N, st));
+    }
     cudaEvent_t ev;
     timer_begin(ctx, T_MESH, &ev);
     ++ctx->n_launches;

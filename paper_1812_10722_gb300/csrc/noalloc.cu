@@ -92,6 +92,10 @@ extern "C" int lspr_matvec_direct_fp32_noalloc(lspr_ctx *c, const double *x, dou
     if (!c || !x || !y) return LSPR_E_ARG;
     if (!c->mesh.ready) return LSPR_E_STATE;
     const Mesh &m = c->mesh;
+    if (m.S != 1) {
+        c->last_error = "lspr_matvec_direct_fp32_noalloc: one surface only";
+        return LSPR_E_STATE;
+    }
     if (m.N > kNoAllocMaxPanels || m.Ns > kNoAllocMaxSources) {
         c->last_error = "lspr_matvec_direct_fp32_noalloc: mesh exceeds the fixed scratch (16384 panels, 65536 sources)";
         return LSPR_E_ARG;

@@ -142,16 +142,76 @@ __global__ void assemble_rhs_kernel(int64_t N, int B, int L, const double *__res
     }
 }
 
-// far-field parts of B right-hand sides x [B][2N] into ctx->acc [panel][B][4]; with B > 1
-// the transposed copy xt of x is formed first (the block assembly reads it too)
+// Several surfaces, Eq. matrix_multi: the block rows of panel i on surface s for channel
+// sets (b, t) of the far field (acc [panel][B S][4]) and the near corrections, the latter
+// split by the source panel's surface t:
+//   y_top = phi/2 + (K phi)_s - (V dphi)_s,  y_bot = phi/2 - sum_t (K phi)_t + sum_t s_bt (V dphi)_t
+// One thread per (row, right-hand side); s is [B][S].  RAW: write the layer potentials per
+// source surface instead, Vd[t][i] = (V dphi)_t and Kp[t][i] = (K phi)_t (B = 1).
+template <bool RAW>
+__global__ void assemble_surf_kernel(int64_t N, int B, int S, const int *__restrict__ surf,
+                                     const double *__restrict__ acc, const int64_t *__restrict__ ptr,
+                                     const int *__restrict__ col, const double *__restrict__ dV,
+                                     const double *__restrict__ dK, const double2 *__restrict__ x,
+                                     const double2 *__restrict__ s, double2 *y, double2 *Vd, double2 *Kp) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= N * B) return;
+    const int64_t i = g / B;
+    const int b = (int)(g - i * B);
+    const int si = surf[i];
+    const double2 *xb = x + (int64_t)b * 2 * N;
+    double2 Ks = make_double2(0, 0), Vs = make_double2(0, 0), Ka = make_double2(0, 0), Vw = make_double2(0, 0);
+    for (int t = 0; t < S; ++t) {
+        const double *a = acc + 4 * ((i * B + b) * S + t);
+        double2 V = make_double2(a[0], a[1]), K = make_double2(a[2], a[3]);
+        if (RAW) {   // near corrections of surface t added below
+            Vd[(int64_t)t * N + i] = V;
+            Kp[(int64_t)t * N + i] = K;
+            continue;
+        }
+        Ka = cadd(Ka, K);
+        Vw = cadd(Vw, cmul(s[b * S + t], V));
+        if (t == si) {
+            Ks = K;
+            Vs = V;
+        }
+    }
+    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) {
+        const int j = col[e];
+        const int t = surf[j];
+        const double2 dv = cscale(xb[N + j], dV[e]), dk = cscale(xb[j], dK[e]);
+        if (RAW) {
+            Vd[(int64_t)t * N + i] = cadd(Vd[(int64_t)t * N + i], dv);
+            Kp[(int64_t)t * N + i] = cadd(Kp[(int64_t)t * N + i], dk);
+            continue;
+        }
+        Ka = cadd(Ka, dk);
+        Vw = cadd(Vw, cmul(s[b * S + t], dv));
+        if (t == si) {
+            Ks = cadd(Ks, dk);
+            Vs = cadd(Vs, dv);
+        }
+    }
+    if (RAW) return;
+    const double2 ph = xb[i];
+    double2 *yb = y + (int64_t)b * 2 * N;
+    yb[i] = make_double2(0.5 * ph.x + Ks.x - Vs.x, 0.5 * ph.y + Ks.y - Vs.y);
+    yb[N + i] = make_double2(0.5 * ph.x - Ka.x + Vw.x, 0.5 * ph.y - Ka.y + Vw.y);
+}
+
+// far-field parts of B right-hand sides x [B][2N] into ctx->acc [panel][B S][4] (S surfaces:
+// channel set b S + t holds the potentials of surface t's sources); with B > 1 the
+// transposed copy xt of x is formed first (the block assembly reads it too)
 static int far_part(lspr_ctx *ctx, int mode, const double2 *x, int B) {
     const int prec = mode_prec(mode);
     const bool tree = mode_tree(mode);
     const int64_t N = ctx->mesh.N;
+    const int S = ctx->mesh.S;
+    const int BS = B * S;
     if (tree && !ctx->tree.ready) return LSPR_E_STATE;
-    LSPR_TRY(ctx, ctx->acc.ensure(4 * N * B));
+    LSPR_TRY(ctx, ctx->acc.ensure(4 * N * BS));
     LSPR_TRY(ctx, ctx->counters.ensure(8));
-    LSPR_TRY(ctx, cudaMemsetAsync(ctx->acc.p, 0, sizeof(double) * 4 * N * B, ctx->stream));
+    LSPR_TRY(ctx, cudaMemsetAsync(ctx->acc.p, 0, sizeof(double) * 4 * N * BS, ctx->stream));
     LSPR_TRY(ctx, cudaMemsetAsync(ctx->counters.p, 0, sizeof(int) * 8, ctx->stream));
     const double2 *xt = nullptr;
     if (B > 1) {
@@ -161,20 +221,20 @@ static int far_part(lspr_ctx *ctx, int mode, const double2 *x, int B) {
                                                                                                    ctx->xt.p);
         xt = ctx->xt.p;
     }
-    LSPR_TRY_ST(launch_weights(ctx, prec, x, xt, N, B));
+    LSPR_TRY_ST(launch_weights(ctx, prec, x, xt, N, B, S));
     if (tree) {
         // P2P on the side stream overlaps P2M -> M2P on the main stream; both add into acc
         LSPR_TRY(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
         LSPR_TRY(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
         LSPR_TRY_ST(launch_p2p(ctx, prec, ctx->tree.p2p_items.p, ctx->tree.n_p2p_items, ctx->acc.p, ctx->side,
-                               ctx->counters.p, B));
+                               ctx->counters.p, BS));
         LSPR_TRY(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
-        LSPR_TRY_ST(launch_p2m(ctx, prec, B));
-        LSPR_TRY_ST(launch_m2p(ctx, prec, ctx->acc.p, ctx->counters.p + 1, B));
+        LSPR_TRY_ST(launch_p2m(ctx, prec, BS));
+        LSPR_TRY_ST(launch_m2p(ctx, prec, ctx->acc.p, ctx->counters.p + 1, BS));
         LSPR_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     } else {
         LSPR_TRY_ST(launch_p2p(ctx, prec, ctx->direct.items.p, ctx->direct.n, ctx->acc.p, ctx->stream,
-                               ctx->counters.p, B));
+                               ctx->counters.p, BS));
     }
     ctx->matvec_count += B;
     return LSPR_OK;
@@ -187,7 +247,11 @@ int apply_operator(lspr_ctx *ctx, int mode, const double2 *x, double2 *y, const 
     cudaEvent_t ev;
     timer_begin(ctx, T_NEAR, &ev);
     ++ctx->n_launches;
-    if (B == 1) {
+    if (m.S > 1) {
+        assemble_surf_kernel<false><<<grid_for(N * B, 128), 128, 0, ctx->stream>>>(
+            N, B, m.S, m.surf.p, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, s, y, nullptr,
+            nullptr);
+    } else if (B == 1) {
         assemble_kernel<false><<<grid_for(N * kRowLanes, 256), 256, 0, ctx->stream>>>(
             N, B, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, s, y, nullptr, nullptr,
             ctx->rhs_inv);
@@ -207,9 +271,14 @@ int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, dou
     const Mesh &m = ctx->mesh;
     LSPR_TRY_ST(far_part(ctx, mode, x, 1));
     ++ctx->n_launches;
-    assemble_kernel<true><<<grid_for(m.N * kRowLanes, 256), 256, 0, ctx->stream>>>(
-        m.N, 1, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr, nullptr, Vd, Kp,
-        nullptr);
+    if (m.S > 1)
+        assemble_surf_kernel<true><<<grid_for(m.N, 128), 128, 0, ctx->stream>>>(
+            m.N, 1, m.S, m.surf.p, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr,
+            nullptr, Vd, Kp);
+    else
+        assemble_kernel<true><<<grid_for(m.N * kRowLanes, 256), 256, 0, ctx->stream>>>(
+            m.N, 1, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr, nullptr, Vd, Kp,
+            nullptr);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
@@ -218,14 +287,16 @@ int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, dou
 constexpr int kRedThreads = 256;
 constexpr int kChunk = 1024;   // elements per partial-sum block
 
-// right preconditioner: out = M^-1 in, per panel 2x2 block
+// right preconditioner: out = M^-1 in, per panel 2x2 block with the s of the panel's surface
+// (s is [B][S])
 __global__ void precond_kernel(int B, int64_t N, const double *__restrict__ Vself, const double2 *__restrict__ s,
-                               const double2 *in, int64_t in_stride, double2 *out, const int *active) {
+                               int S, const int *__restrict__ surf, const double2 *in, int64_t in_stride, double2 *out,
+                               const int *active) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (t >= N || b >= B || (active && !active[b])) return;
     double2 o0, o1;
-    block_jacobi(Vself[t], s[b], in[b * in_stride + t], in[b * in_stride + N + t], o0, o1);
+    block_jacobi(Vself[t], s[b * S + surf[t]], in[b * in_stride + t], in[b * in_stride + N + t], o0, o1);
     out[b * 2 * N + t] = o0;
     out[b * 2 * N + N + t] = o1;
 }
@@ -348,29 +419,36 @@ __global__ void dphi_inc_kernel(int64_t N, const double *nx, const double *ny, c
     x[N + i] = make_double2(-(E0x * nx[i] + E0y * ny[i] + E0z * nz[i]), 0.0);
 }
 
-// b[b] = [0 ; ((eps_out - eps_in_b)/eps_out) * V dphi_inc]
-__global__ void rhs_kernel(int B, int64_t N, const double2 *__restrict__ Vinc, const double2 *eps_in, double2 eps_out,
-                           double2 *rhs) {
+// b[b] = [0 ; sum_t ((eps_out - eps_bt)/eps_out) (V dphi_inc)_t], Vinc [S][N], eps_in [B][S]
+__global__ void rhs_kernel(int B, int S, int64_t N, const double2 *__restrict__ Vinc, const double2 *eps_in,
+                           double2 eps_out, double2 *rhs) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (i >= N) return;
-    const double2 f = cdiv(csub(eps_out, eps_in[b]), eps_out);
+    double2 acc = make_double2(0, 0);
+    for (int t = 0; t < S; ++t) {
+        const double2 f = cdiv(csub(eps_out, eps_in[b * S + t]), eps_out);
+        acc = cadd(acc, cmul(f, Vinc[(int64_t)t * N + i]));
+    }
     rhs[(int64_t)b * 2 * N + i] = make_double2(0, 0);
-    rhs[(int64_t)b * 2 * N + N + i] = cmul(f, Vinc[i]);
+    rhs[(int64_t)b * 2 * N + N + i] = acc;
 }
 
 // ---------------------------------------------------------- dipole + sigma
-__global__ void dipole_partial_kernel(int B, int64_t N, const double2 *__restrict__ x, const double2 *eps_in,
+// dipole of surface 0 (the particle; eps_in [B][S], its permittivity eps_in[b][0])
+__global__ void dipole_partial_kernel(int B, int S, int64_t N, const int *__restrict__ surf,
+                                      const double2 *__restrict__ x, const double2 *eps_in,
                                       double2 eps_out, const double *cx, const double *cy, const double *cz,
                                       const double *nx, const double *ny, const double *nz, const double *area,
                                       double E0x, double E0y, double E0z, double *part, int nchunks) {
     __shared__ double red[6][kRedThreads];
     const int chunk = blockIdx.x, b = blockIdx.y;
-    const double2 s = cdiv(eps_in[b], eps_out);
-    const double2 f = cdiv(csub(eps_out, eps_in[b]), eps_out);
+    const double2 s = cdiv(eps_in[b * S], eps_out);
+    const double2 f = cdiv(csub(eps_out, eps_in[b * S]), eps_out);
     double acc[6] = {0, 0, 0, 0, 0, 0};
     const int64_t beg = (int64_t)chunk * kChunk, end = min(N, beg + kChunk);
     for (int64_t j = beg + threadIdx.x; j < end; j += blockDim.x) {
+        if (surf[j] != 0) continue;
         const double2 ph = x[(int64_t)b * 2 * N + j], dp = x[(int64_t)b * 2 * N + N + j];
         const double dinc = -(E0x * nx[j] + E0y * ny[j] + E0z * nz[j]);
         const double2 d2 = csub(cmul(s, dp), cscale(f, dinc));
@@ -482,7 +560,8 @@ static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, doubl
             // z = M^-1 v_j ; w = A z
             timer_begin(ctx, T_GMRES, &ev);
             ++ctx->n_launches;
-            precond_kernel<<<gN, 256, 0, st>>>(B, N, me.Vself.p, s_d, V + (int64_t)j * n2, vstride, z, active);
+            precond_kernel<<<gN, 256, 0, st>>>(B, N, me.Vself.p, s_d, me.S, me.surf.p, V + (int64_t)j * n2, vstride, z,
+                                                active);
             timer_end(ctx, T_GMRES, ev);
             LSPR_TRY_ST(apply_operator(ctx, mode, z, w, s_d, B));
             timer_begin(ctx, T_GMRES, &ev);
@@ -557,7 +636,7 @@ static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, doubl
         ++ctx->n_launches;
         combine_kernel<<<gv, 256, 0, st>>>(B, n2, V, vstride, ctx->gm_y.p, m, jb_d, w);
         ++ctx->n_launches;
-        precond_kernel<<<gN, 256, 0, st>>>(B, N, me.Vself.p, s_d, w, n2, z, nullptr);
+        precond_kernel<<<gN, 256, 0, st>>>(B, N, me.Vself.p, s_d, me.S, me.surf.p, w, n2, z, nullptr);
         ++ctx->n_launches;
         add_kernel<<<gv, 256, 0, st>>>(B, n2, x_d, z, 1.0);
         timer_end(ctx, T_GMRES, ev);
@@ -577,31 +656,32 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
     const int mode = o.mode;
     const bool tree = mode_tree(mode);
     const double2 eout = make_double2(eps_out_re, eps_out_im);
-    LSPR_TRY(ctx, ctx->gm_eps.ensure(B));
-    LSPR_TRY(ctx, ctx->gm_s.ensure(B));
+    const int S = me.S;   // eps_in is [B][S]
+    LSPR_TRY(ctx, ctx->gm_eps.ensure((size_t)B * S));
+    LSPR_TRY(ctx, ctx->gm_s.ensure((size_t)B * S));
     LSPR_TRY(ctx, ctx->gm_b.ensure((size_t)B * n2));
     LSPR_TRY(ctx, ctx->gm_x.ensure((size_t)B * n2));
     LSPR_TRY(ctx, ctx->gm_r.ensure((size_t)B * n2));
-    LSPR_TRY(ctx, ctx->gm_vinc.ensure(2 * n2));
+    LSPR_TRY(ctx, ctx->gm_vinc.ensure(n2 + 2 * (size_t)S * N));
     LSPR_TRY(ctx, ctx->gm_out.ensure((size_t)B * 8 + B));
-    std::vector<double2> he(B), hs(B);
-    for (int b = 0; b < B; ++b) {
-        he[b] = make_double2(eps_in[2 * b], eps_in[2 * b + 1]);
+    std::vector<double2> he((size_t)B * S), hs((size_t)B * S);
+    for (int q = 0; q < B * S; ++q) {
+        he[q] = make_double2(eps_in[2 * q], eps_in[2 * q + 1]);
         const double d = eps_out_re * eps_out_re + eps_out_im * eps_out_im;
-        hs[b] = make_double2((he[b].x * eps_out_re + he[b].y * eps_out_im) / d,
-                             (he[b].y * eps_out_re - he[b].x * eps_out_im) / d);
+        hs[q] = make_double2((he[q].x * eps_out_re + he[q].y * eps_out_im) / d,
+                             (he[q].y * eps_out_re - he[q].x * eps_out_im) / d);
     }
-    LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_eps.p, he.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, st));
-    LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_s.p, hs.data(), sizeof(double2) * B, cudaMemcpyHostToDevice, st));
+    LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_eps.p, he.data(), sizeof(double2) * B * S, cudaMemcpyHostToDevice, st));
+    LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_s.p, hs.data(), sizeof(double2) * B * S, cudaMemcpyHostToDevice, st));
     // right-hand side V (dphi_inc/dn) with the operator of the solve's mode: dphi_inc/dn
     // is smooth and the sum has no cancellation, so FP32 evaluation (FP64 accumulation)
     // leaves ~1e-7 relative error in b
     double2 *xin = ctx->gm_vinc.p, *Vinc = ctx->gm_vinc.p + n2;
     ++ctx->n_launches;
     dphi_inc_kernel<<<grid_for(N, 256), 256, 0, st>>>(N, me.nx.p, me.ny.p, me.nz.p, E0[0], E0[1], E0[2], xin);
-    LSPR_TRY_ST(layer_potentials(ctx, mode, xin, Vinc, Vinc + N));
+    LSPR_TRY_ST(layer_potentials(ctx, mode, xin, Vinc, Vinc + (size_t)S * N));
     ++ctx->n_launches;
-    rhs_kernel<<<dim3(grid_for(N, 256), B), 256, 0, st>>>(B, N, Vinc, ctx->gm_eps.p, eout, ctx->gm_b.p);
+    rhs_kernel<<<dim3(grid_for(N, 256), B), 256, 0, st>>>(B, S, N, Vinc, ctx->gm_eps.p, eout, ctx->gm_b.p);
     LSPR_TRY(ctx, cudaMemsetAsync(ctx->gm_x.p, 0, sizeof(double2) * B * n2, st));
     // ||b||
     const int nch = (int)((n2 + kChunk - 1) / kChunk);
@@ -722,7 +802,8 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
     LSPR_TRY(ctx, lam.ensure(B));
     LSPR_TRY(ctx, cudaMemcpyAsync(lam.p, lambda_nm, sizeof(double) * B, cudaMemcpyHostToDevice, st));
     ++ctx->n_launches;
-    dipole_partial_kernel<<<dim3(nchN, B), kRedThreads, 0, st>>>(B, N, ctx->gm_x.p, ctx->gm_eps.p, eout, me.cx.p,
+    dipole_partial_kernel<<<dim3(nchN, B), kRedThreads, 0, st>>>(B, me.S, N, me.surf.p, ctx->gm_x.p, ctx->gm_eps.p,
+                                                                 eout, me.cx.p,
                                                                  me.cy.p, me.cz.p, me.nx.p, me.ny.p, me.nz.p,
                                                                  me.area.p, E0[0], E0[1], E0[2], part.p, nchN);
     ++ctx->n_launches;

@@ -164,25 +164,42 @@ class Context:
         self.close()
 
     # ------------------------------------------------------------------ mesh
-    def mesh_upload(self, verts, tris, K=4, K_fine=19, N_k=9, threshold=0.5, surf_id=None, nsurf=1):
+    def mesh_upload(self, verts, tris, K=4, K_fine=19, N_k=9, threshold=0.5, surf_id=None, nsurf=None):
+        """Panels and quadrature (host numpy or CUDA torch arrays).  surf_id: surface of
+        each panel (surface 0 = the particle); nsurf defaults to max(surf_id) + 1."""
         q = QuadOpts(K, K_fine, N_k, threshold)
         if _is_torch(verts):
             assert verts.is_cuda and tris.is_cuda
             assert str(verts.dtype) == "torch.float64" and str(tris.dtype) == "torch.int32"
             verts, tris = verts.contiguous(), tris.contiguous()
+            sid = None if surf_id is None else surf_id.contiguous()
+            if sid is not None:
+                assert sid.is_cuda and str(sid.dtype) == "torch.int32"
+            ns = nsurf or (1 if sid is None else int(sid.max().item()) + 1)
             rc = lib().lspr_mesh_upload(self._h, ctypes.c_void_p(verts.data_ptr()), verts.shape[0],
-                                        ctypes.c_void_p(tris.data_ptr()), tris.shape[0], None, nsurf,
+                                        ctypes.c_void_p(tris.data_ptr()), tris.shape[0],
+                                        None if sid is None else ctypes.c_void_p(sid.data_ptr()), ns,
                                         ctypes.byref(q), 1)
             n = tris.shape[0]
         else:
             v = np.ascontiguousarray(verts, dtype=np.float64)
             t = np.ascontiguousarray(tris, dtype=np.int32)
             sid = None if surf_id is None else np.ascontiguousarray(surf_id, dtype=np.int32)
+            ns = nsurf or (1 if sid is None else int(sid.max()) + 1)
             rc = lib().lspr_mesh_upload(self._h, _host_ptr(v), len(v), _host_ptr(t), len(t),
-                                        None if sid is None else _host_ptr(sid), nsurf, ctypes.byref(q), 0)
+                                        None if sid is None else _host_ptr(sid), ns, ctypes.byref(q), 0)
             n = len(t)
         _check(rc, "lspr_mesh_upload", self._h)
         self.n = int(n)
+        self.nsurf = int(ns)
+
+    def _per_surface(self, a, B):
+        """[B, S] complex array from a scalar, [S], [B] (one surface) or [B, S] input."""
+        a = np.asarray(a, np.complex128)
+        S = getattr(self, "nsurf", 1)
+        if S == 1:
+            return np.ascontiguousarray(np.broadcast_to(a.reshape(-1), (B,)).reshape(B, 1))
+        return np.ascontiguousarray(np.broadcast_to(a.reshape(-1, S), (B, S)))
 
     def tree_build(self, theta=0.5, P=6, Ncrit=300):
         _check(lib().lspr_tree_build(self._h, float(theta), int(P), int(Ncrit)), "lspr_tree_build", self._h)
@@ -196,8 +213,7 @@ class Context:
             squeeze = x.dim() == 1
             xx = x.reshape(-1, 2 * self.n).contiguous()
             B = xx.shape[0]
-            s = torch.as_tensor(np.broadcast_to(np.asarray(eps_ratio, np.complex128), (B,)).copy(),
-                                device=x.device)
+            s = torch.as_tensor(self._per_surface(eps_ratio, B).copy(), device=x.device)
             y = torch.empty_like(xx)
             rc = lib().lspr_matvec(self._h, ctypes.c_void_p(xx.data_ptr()), ctypes.c_void_p(y.data_ptr()), B,
                                    ctypes.c_void_p(s.data_ptr()), m, 1)
@@ -207,7 +223,7 @@ class Context:
         squeeze = x.ndim == 1
         xx = x.reshape(-1, 2 * self.n)
         B = xx.shape[0]
-        s = np.ascontiguousarray(np.broadcast_to(np.asarray(eps_ratio, np.complex128), (B,)))
+        s = self._per_surface(eps_ratio, B)
         y = np.zeros_like(xx)
         _check(lib().lspr_matvec(self._h, _host_ptr(xx), _host_ptr(y), B, _host_ptr(s), m, 0), "lspr_matvec", self._h)
         return y[0] if squeeze else y
@@ -215,10 +231,15 @@ class Context:
     # ----------------------------------------------------------------- solve
     def solve(self, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0), tol=1e-6, restart=50, maxiter=500,
               mode="tree_fp32", refine=False, check=True) -> SolveResult:
+        """eps_in: [B] (one surface) or [B, S] / [S] (several surfaces: permittivity of every
+        surface per wavelength; sigma_ext and the dipole are surface 0's)."""
         m = MODES[mode] if isinstance(mode, str) else int(mode)
-        e = np.ascontiguousarray(np.atleast_1d(eps_in), dtype=np.complex128)
-        lam = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(lambda_nm), e.shape), dtype=np.float64)
-        B = len(e)
+        S = getattr(self, "nsurf", 1)
+        lam1 = np.atleast_1d(np.asarray(lambda_nm, np.float64))
+        ea = np.asarray(eps_in, np.complex128)
+        B = max(len(lam1), ea.size // S)
+        e = self._per_surface(ea, B)
+        lam = np.ascontiguousarray(np.broadcast_to(lam1, (B,)), dtype=np.float64)
         E = np.ascontiguousarray(E0, dtype=np.float64)
         dip = np.zeros((B, 3), np.complex128)
         sig = np.zeros(B)

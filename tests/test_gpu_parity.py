@@ -431,3 +431,64 @@ def test_autotune_meets_sigma_bound(lspr):
     assert 4 <= r["P"] <= 8 and r["theta"] in (0.3, 0.4, 0.5, 0.6) and r["Ncrit"] in (128, 256, 512)
     assert r["ms"] <= r["ref_ms"]
     assert abs(s.sigma_ext[0] - g) / g < 1e-4
+
+
+def _sensor_small():
+    # sphere (surface 0) and two analytes at 0.5 and 1 nm: cross-surface near-singular pairs
+    # (the analytes' skinny panels need N_k = 24 for the semi-analytical self integral to
+    # match the exact one to ~1e-8)
+    return I.sensor_geometry(2, 10.0, analytes=(("+z", 0.5), ("-x", 1.0)), analyte_sub=2)
+
+
+@pytest.mark.parametrize("mode,tol", [("direct_fp64", 1e-6), ("direct_fp32", 1e-5), ("direct_ff", 1e-6),
+                                      ("tree_fp64", 1e-4), ("tree_fp32", 1e-4)])
+def test_multi_surface_matvec(lspr, oracle, mode, tol):
+    # Eq. matrix_multi: self-surface interior rows, all-surface exterior rows with s_t weights
+    v, t, surf = _sensor_small()
+    n = len(t)
+    lam = I.wavelengths(360, 400, 3)
+    s = np.stack([I.drude_eps(lam) / I.EPS_WATER, np.full(3, 2.25 / I.EPS_WATER),
+                  np.array([1.8, 2.0, 2.6]) / I.EPS_WATER + 0.01j], axis=1)
+    x = I.random_complex(2 * n, seed=31, batch=3)
+    yo = oracle.matvec_multi(v, t, surf, x, s)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t, N_k=24, surf_id=surf)
+        ctx.tree_build(0.5, 6, 32)
+        y = ctx.matvec(x, s, mode)
+        y1 = ctx.matvec(x[1], s[1], mode)
+    for b in range(3):
+        assert _rel(y[b], yo[b]) < tol, b
+    assert _rel(y1, yo[1]) < tol
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_multi_surface_solve(lspr, oracle, graphs):
+    v, t, surf = _sensor_small()
+    lam = np.array([370.0, 390.0])
+    eps = np.stack([I.drude_eps(lam), np.full(2, 2.25), np.full(2, 2.0 + 0.05j)], axis=1)
+    dref, sref, _, bad = oracle.solve_multi(v, t, surf, eps, I.EPS_WATER, lam, tol=1e-10)
+    assert bad == 0
+    with lspr.Context(0) as ctx:
+        ctx.set_graphs(graphs)
+        ctx.mesh_upload(v, t, N_k=24, surf_id=surf)
+        r = ctx.solve(eps, I.EPS_WATER, lam, tol=1e-10, mode="direct_fp64", restart=100, maxiter=2000)
+        ctx.tree_build(0.3, 8, 32)
+        rt = ctx.solve(eps, I.EPS_WATER, lam, tol=1e-8, mode="tree_fp32", refine=True, restart=60, maxiter=2000)
+        r1 = ctx.solve(eps[1], I.EPS_WATER, lam[1], tol=1e-8, mode="tree_fp32", refine=True, restart=60,
+                       maxiter=2000)
+    assert np.all(r.status == 0) and np.all(rt.status == 0)
+    assert np.max(np.abs(r.sigma_ext - sref) / sref) < 1e-6
+    assert np.max(np.abs(r.dipole - dref)) < 1e-6 * np.max(np.abs(dref))
+    assert np.max(np.abs(rt.sigma_ext - sref) / sref) < 1e-4
+    assert abs(r1.sigma_ext[0] - rt.sigma_ext[1]) / rt.sigma_ext[1] < 1e-6
+
+
+def test_multi_surface_upload_errors(lspr):
+    v, t, surf = _sensor_small()
+    bad = surf.copy()
+    bad[5] = 7
+    with lspr.Context(0) as ctx:
+        with pytest.raises(lspr.LsprError):
+            ctx.mesh_upload(v, t, surf_id=bad, nsurf=3)
+        ctx.mesh_upload(v, t, N_k=24, surf_id=surf)
+        assert ctx.nsurf == 3
