@@ -52,6 +52,11 @@ WORKLOADS = {
     "sphere20480_sweep16": dict(sub=5, R=10.0, lam=list(I.wavelengths(350, 420, 16)), mode="tree_fp32", tol=1e-6,
                                 theta=0.5, P=6, Ncrit=300, K=4, K_fine=19, N_k=9, restart=50, refine=True,
                                 autotune=True),
+    # sensor-analyte: 81920-panel sphere plus two 32768-panel protein-like analytes (eps 2.25) at 1 nm on
+    # +-z, 32 wavelengths over 370-400 nm in one batched solve; the resonance shift against the bare sphere
+    "sensor_c4": dict(sub=6, R=10.0, lam=list(I.wavelengths(370, 400, 32)), mode="tree_fp32", tol=1e-6,
+                      theta=0.5, P=6, Ncrit=300, K=4, K_fine=19, N_k=9, restart=50, refine=True, autotune=True,
+                      analytes=(("+z", 1.0), ("-z", 1.0)), analyte_sub=6, eps_analyte=2.25, tune_lams=1),
     # 81920-panel sphere, 64 wavelengths over 350-420 nm in one batched solve
     "sphere81920_sweep64": dict(sub=6, R=10.0, lam=list(I.wavelengths(350, 420, 64)), mode="tree_fp32", tol=1e-6,
                                 theta=0.5, P=6, Ncrit=300, K=4, K_fine=19, N_k=9, restart=50, refine=True,
@@ -59,16 +64,44 @@ WORKLOADS = {
 }
 
 
-def tuning_wavelengths(lam: np.ndarray) -> np.ndarray:
+def tuning_wavelengths(lam: np.ndarray, count: int = 4) -> np.ndarray:
     """Wavelengths the autotuner checks: the one nearest the sphere's dipole resonance
-    (smallest |eps + 2 eps_m|, where the solve amplifies operator errors most) and up to
-    three more spread over the sweep."""
+    (smallest |eps + 2 eps_m|, where the solve amplifies operator errors most) and, with
+    count 4, three more spread over the sweep."""
     lam = np.asarray(lam, float)
+    k = int(np.argmin(np.abs(I.drude_eps(lam) + 2 * I.EPS_WATER)))
+    if count == 1:
+        return lam[k:k + 1]
     if len(lam) <= 4:
         return lam
-    k = int(np.argmin(np.abs(I.drude_eps(lam) + 2 * I.EPS_WATER)))
     pick = {k, 0, len(lam) // 2, len(lam) - 1}
     return lam[sorted(pick)]
+
+
+def workload_geometry(wl):
+    """(verts, tris, surf or None) of a workload: the sphere, or the sphere plus analytes."""
+    if wl.get("analytes"):
+        return I.sensor_geometry(wl["sub"], wl["R"], wl["analytes"], wl["analyte_sub"])
+    v, t = I.icosphere(wl["sub"], wl["R"])
+    return v, t, None
+
+
+def workload_eps(wl, lam):
+    """[B] or [B, S] permittivities: Drude silver for the sphere, eps_analyte for analytes."""
+    e = I.drude_eps(np.asarray(lam, float))
+    if not wl.get("analytes"):
+        return e
+    S = 1 + len(wl["analytes"])
+    out = np.full((len(e), S), complex(wl["eps_analyte"]), np.complex128)
+    out[:, 0] = e
+    return out
+
+
+def resonance_peak(lam, sigma):
+    """Wavelength of the largest sigma_ext from a parabola through the 3 samples around it."""
+    k = int(np.clip(np.argmax(sigma), 1, len(sigma) - 2))
+    a, b, _ = np.polyfit(lam[k - 1:k + 2], sigma[k - 1:k + 2], 2)
+    return float(-b / (2 * a))
 
 
 L2_BYTES = 129 * 2 ** 20
@@ -164,33 +197,35 @@ def run_ours(args, wl, rank, world, local_rank):
     from paper_1812_10722_gb300 import lspr
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    verts, tris = I.icosphere(wl["sub"], wl["R"])
+    verts, tris, surf = workload_geometry(wl)
     lam = np.asarray(wl["lam"], float)
-    eps = I.drude_eps(lam)
+    eps = workload_eps(wl, lam)
     em = I.EPS_WATER
     B = len(lam)
     v_d = torch.as_tensor(verts, device=dev)
     t_d = torch.as_tensor(tris, device=dev)
+    s_d = None if surf is None else torch.as_tensor(surf, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = lspr.Context(local_rank, stream.cuda_stream)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     tune = None
     if wl.get("autotune") and wl["mode"].startswith("tree"):
         # once per geometry, before the timed region: treecode parameters under the sigma_ext bound
-        ctx.mesh_upload(v_d, t_d, wl["K"], wl["K_fine"], wl["N_k"])
-        lt = tuning_wavelengths(lam)
+        ctx.mesh_upload(v_d, t_d, wl["K"], wl["K_fine"], wl["N_k"], surf_id=s_d)
+        lt = tuning_wavelengths(lam, wl.get("tune_lams", 4))
         t0 = time.perf_counter()
-        tune = ctx.autotune(I.drude_eps(lt), em, lt, target_rel_err=1e-4, tol=min(wl["tol"], 1e-8),
-                            restart=wl["restart"], mode=wl["mode"], refine=1 if wl["refine"] else 0)
+        tune = ctx.autotune(workload_eps(wl, lt), em, lt, target_rel_err=1e-4, tol=min(wl["tol"], 1e-8),
+                            restart=wl["restart"], mode=wl["mode"], refine=1 if wl["refine"] else 0,
+                            coarse=len(tris) > 100000)
         tune["seconds"] = round(time.perf_counter() - t0, 2)
         tune["wavelengths"] = [float(x) for x in lt]
         wl["theta"], wl["P"], wl["Ncrit"] = tune["theta"], tune["P"], tune["Ncrit"]
 
     def step(host: bool):
         if host:
-            ctx.mesh_upload(verts, tris, wl["K"], wl["K_fine"], wl["N_k"])
+            ctx.mesh_upload(verts, tris, wl["K"], wl["K_fine"], wl["N_k"], surf_id=surf)
         else:
-            ctx.mesh_upload(v_d, t_d, wl["K"], wl["K_fine"], wl["N_k"])
+            ctx.mesh_upload(v_d, t_d, wl["K"], wl["K_fine"], wl["N_k"], surf_id=s_d)
         if wl["mode"].startswith("tree"):
             ctx.tree_build(wl["theta"], wl["P"], wl["Ncrit"])
         return ctx.solve(eps, em, lam, tol=wl["tol"], restart=wl["restart"], maxiter=2000, mode=wl["mode"],
@@ -258,9 +293,22 @@ def run_ours(args, wl, rank, world, local_rank):
     # ---- accuracy: the same step with the plain FP64 treecode (same P, theta) and the oracle's stored value
     acc = {}
     if wl["mode"] == "tree_fp32":
-        r64 = ctx.solve(eps, em, lam, tol=min(wl["tol"], 1e-8), restart=wl["restart"], maxiter=2000,
+        # large batches: the wavelength nearest the resonance (the FP64 treecode is ~30x slower)
+        ka = [int(np.argmin(np.abs(I.drude_eps(lam) + 2 * em)))] if B > 4 else list(range(B))
+        r64 = ctx.solve(eps[ka], em, lam[ka], tol=min(wl["tol"], 1e-8), restart=wl["restart"], maxiter=2000,
                         mode="tree_fp64")
-        acc["sigma_rel_err_vs_fp64_treecode"] = float(np.max(np.abs(sig - r64.sigma_ext) / r64.sigma_ext))
+        acc["sigma_rel_err_vs_fp64_treecode"] = float(np.max(np.abs(sig[ka] - r64.sigma_ext) / r64.sigma_ext))
+        acc["checked_wavelengths_nm"] = [float(lam[k]) for k in ka]
+    if wl.get("analytes"):
+        # resonance shift: the same sweep on the bare sphere, peaks from parabolic fits
+        vb, tb = I.icosphere(wl["sub"], wl["R"])
+        ctx.mesh_upload(vb, tb, wl["K"], wl["K_fine"], wl["N_k"])
+        ctx.tree_build(wl["theta"], wl["P"], wl["Ncrit"])
+        rb = ctx.solve(I.drude_eps(lam), em, lam, tol=wl["tol"], restart=wl["restart"], maxiter=2000,
+                       mode=wl["mode"], refine=wl["refine"])
+        acc["resonance"] = {"peak_nm": resonance_peak(lam, sig), "bare_sphere_peak_nm": resonance_peak(lam, rb.sigma_ext),
+                            "shift_nm": resonance_peak(lam, sig) - resonance_peak(lam, rb.sigma_ext),
+                            "peak_sigma_nm2": float(np.max(sig)), "bare_peak_sigma_nm2": float(np.max(rb.sigma_ext))}
     gold = os.path.join(ROOT, "tests", "golden", f"sphere{info['n_panels']}_l380.json")
     if B == 1 and lam[0] == 380.0 and os.path.exists(gold):
         with open(gold) as f:
@@ -278,7 +326,8 @@ def run_ours(args, wl, rank, world, local_rank):
         tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(tt.item())
-    h2d = verts.nbytes + tris.nbytes + eps.astype(np.complex128).nbytes + lam.nbytes + 24
+    h2d = verts.nbytes + tris.nbytes + eps.astype(np.complex128).nbytes + lam.nbytes + 24 + (
+        0 if surf is None else surf.nbytes)
     d2h = B * (3 * 16 + 8)
 
     # ---- roofline of the dominant kernel (CUDA events around every launch in the timed region)
@@ -339,7 +388,9 @@ def run_ours(args, wl, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
         "data": "synthetic (icosphere, Drude silver in water)",
-        "config": {"workload": args.workload, "panels": info["n_panels"], "sources": info["n_sources"],
+        "config": {"workload": args.workload, "panels": len(tris), "sources": len(tris) * wl["K"],
+                   "surfaces": 1 if surf is None else int(surf.max()) + 1,
+                   "analytes": None if surf is None else [list(a) for a in wl["analytes"]],
                    "wavelengths": B, "mode": wl["mode"], "theta": wl["theta"], "P": wl["P"], "Ncrit": wl["Ncrit"],
                    "K": wl["K"], "K_fine": wl["K_fine"], "N_k": wl["N_k"], "gmres_tol": wl["tol"],
                    "restart": wl["restart"], "l2": "flushed between steps (258 MiB write)",
@@ -378,8 +429,16 @@ def oracle_sample(wl, iters_hint: int, reps: int = 1):
     """Time the oracle's matrix-free matvec at full size and extrapolate one
     lambda-solve as (GMRES iterations + 2) matvecs (explicit residual and RHS)."""
     import oracle
-    verts, tris = I.icosphere(wl["sub"], wl["R"])
+    verts, tris, surf = workload_geometry(wl)
     n = len(tris)
+    if n > 40000:
+        # too large for a full product in the time budget: the matrix entries of a block of
+        # rows (the product's cost), scaled to all n rows
+        rows = 256
+        t0 = time.perf_counter()
+        oracle.entries(verts, tris, K=wl["K"], K_fine=wl["K_fine"], rows=(0, rows))
+        t_mv = (time.perf_counter() - t0) * n / rows
+        return t_mv, (iters_hint + 2) * t_mv, f"the oracle's matrix entries of {rows} of {n} rows, scaled to a product"
     s = I.drude_eps(wl["lam"][0]) / I.EPS_WATER
     x = I.random_complex(2 * n, seed=0)
     times = []
@@ -389,7 +448,7 @@ def oracle_sample(wl, iters_hint: int, reps: int = 1):
         times.append(time.perf_counter() - t0)
     t_mv = float(np.median(times))
     t_solve = (iters_hint + 2) * t_mv
-    return t_mv, t_solve
+    return t_mv, t_solve, "one full-size oracle matvec"
 
 
 def oracle_iterations_hint(wl):
@@ -409,7 +468,7 @@ def run_reference(args, wl):
         oracle_sample(wl, it)
     t = 0.0
     for _ in range(args.steps):
-        t_mv, t_solve = oracle_sample(wl, it)
+        t_mv, t_solve, sample = oracle_sample(wl, it)
         t += t_solve
     value = len(wl["lam"]) * args.steps / t if len(wl["lam"]) == 1 else args.steps / t
     cores = os.cpu_count()
@@ -418,10 +477,10 @@ def run_reference(args, wl):
         "value": value, "unit": "lambda-solves/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (icosphere, Drude silver in water)",
-        "config": {"workload": args.workload, "panels": len(I.icosphere(wl["sub"], wl["R"])[1]),
+        "config": {"workload": args.workload, "panels": len(workload_geometry(wl)[1]),
                    "wavelengths": 1, "mode": "oracle direct FP64 (plain CPU)"},
         "cpu_baseline": {"value": value, "unit": "lambda-solves/s", "cores": cores, "kind": "oracle",
-                         "sample": f"one full-size oracle matvec per step, lambda-solve extrapolated as "
+                         "sample": f"{sample} per step, lambda-solve extrapolated as "
                                    f"({it} GMRES iterations + 2) matvecs"},
         "e2e": {"value": value, "unit": "lambda-solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -544,10 +603,10 @@ def main():
         torch.distributed.init_process_group("nccl")
     out, iters = run_ours(args, wl, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_mv, t_solve = oracle_sample(wl, iters[-1])
+        t_mv, t_solve, sample = oracle_sample(wl, iters[-1])
         out["cpu_baseline"] = {"value": 1.0 / t_solve,
                                "unit": "lambda-solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                               "sample": f"one full-size oracle matvec ({t_mv:.2f} s) on the host cores; one "
+                               "sample": f"{sample} ({t_mv:.2f} s) on the host cores; one "
                                          f"lambda-solve extrapolated as ({iters[-1]} GMRES iterations + 2) matvecs"}
     if world > 1:
         import torch

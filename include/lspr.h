@@ -177,7 +177,7 @@ LSPR_API int lspr_solve(lspr_ctx *ctx, const double *eps_in, double eps_out_re, 
                double *sigma_ext_out, lspr_solve_stats *st);
 
 /* Autotuner of the treecode parameters (theta, P, Ncrit) for the current mesh: every
- * candidate of a fixed grid (P 4..8, theta 0.3..0.6, Ncrit 128/256/512) is built and
+ * candidate of a fixed grid (P 4..8, theta 0.3..0.6, Ncrit 128/256/512, or the coarse grid) is built and
  * solved for the given wavelengths, its sigma_ext compared with a reference solve
  * (treecode P = 8, theta = 0.3, whose own deviation from the direct FP64 solution is
  * ~2e-6 on the sphere workloads), and the fastest candidate whose largest relative
@@ -191,6 +191,8 @@ typedef struct {
     int32_t restart;         /* GMRES restart of the tuning solves */
     int32_t mode;            /* tree matvec mode timed (LSPR_TREE_FP32 or LSPR_TREE_FP64) */
     int32_t refine;          /* refinement of the timed solves (as lspr_solve_opts.refine) */
+    int32_t grid;            /* 0: the full grid (60 candidates); 1: a coarse grid for large meshes
+                                (P 5..7, theta 0.4/0.5, Ncrit 256/512: 12 candidates) */
 } lspr_tune_opts;
 
 typedef struct {

@@ -53,7 +53,7 @@ int lspr_autotune(lspr_ctx *c, const double *eps_in, double eps_out_re, double e
     if (!c || !eps_in || !E0 || !lambda_nm || !o || !res || B < 1) return LSPR_E_ARG;
     if (!(o->target_rel_err > 0) || !(o->tol > 0) || o->restart < 1) return LSPR_E_ARG;
     if (o->mode != LSPR_TREE_FP32 && o->mode != LSPR_TREE_FP64 && o->mode != LSPR_TREE_FF) return LSPR_E_ARG;
-    if (o->refine < 0 || o->refine > 2) return LSPR_E_ARG;
+    if (o->refine < 0 || o->refine > 2 || o->grid < 0 || o->grid > 1) return LSPR_E_ARG;
     if (!c->mesh.ready) return LSPR_E_STATE;
     cudaSetDevice(c->device);
     lspr_solve_opts so;
@@ -72,10 +72,17 @@ int lspr_autotune(lspr_ctx *c, const double *eps_in, double eps_out_re, double e
     Trial best = ref;
     double best_ms = ref_ms, best_err = 0.0;
     int n = 0, ok = 0;
-    for (int P = 4; P <= kMaxP; ++P)
-        for (double theta : {0.3, 0.4, 0.5, 0.6})
-            for (int Ncrit : {128, 256, 512}) {
-                const Trial t = {theta, P, Ncrit};
+    std::vector<Trial> grid;
+    if (o->grid == 0) {
+        for (int P = 4; P <= kMaxP; ++P)
+            for (double theta : {0.3, 0.4, 0.5, 0.6})
+                for (int Ncrit : {128, 256, 512}) grid.push_back({theta, P, Ncrit});
+    } else {
+        for (int P = 5; P <= 7; ++P)
+            for (double theta : {0.4, 0.5})
+                for (int Ncrit : {256, 512}) grid.push_back({theta, P, Ncrit});
+    }
+    for (const Trial &t : grid) {
                 if (t.theta == ref.theta && t.P == ref.P && t.Ncrit == ref.Ncrit) continue;
                 std::vector<double> s;
                 double ms = 0.0;

@@ -49,8 +49,10 @@ __global__ void weights_kernel(int64_t Ns, int64_t N, int B, int S, const dbl4 *
     const int slot = (int)(g - s * BS);
     if (nact && slot >= *nact) return;
     const int p = src_panel[s];
-    const int bs = map ? map[slot] : slot;
-    const int b = bs / S;
+    // set slot = k S + t: surface t of the k-th running system (map: k -> system)
+    const int k = slot / S, t = slot - k * S;
+    const int b = map ? map[k] : k;
+    const int bs = b * S + t;
     if (S > 1 && surf[p] != bs - b * S) {
         w[g] = zero4<T4>();
         return;

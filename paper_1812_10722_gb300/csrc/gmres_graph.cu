@@ -42,7 +42,8 @@ struct Arn {
     const double *bn, *par;
     unsigned *tick;
     int *jdev, *active, *jb, *iters;
-    int *rmap;   // [2B + 1]: slot -> system, system -> slot (-1: not running), running count
+    int *rmap;   // [2B + 2]: slot -> system, system -> slot (-1: not running), running count,
+                 // channel sets in use (running count x surfaces)
     cudaGraphConditionalHandle cond;
 };
 
@@ -59,6 +60,7 @@ __device__ __forceinline__ void pack_running(const Arn &a) {
     }
     for (int q = n; q < a.B; ++q) a.rmap[q] = 0;
     a.rmap[2 * a.B] = n;
+    a.rmap[2 * a.B + 1] = n * a.S;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -433,13 +435,11 @@ int capture_cycle(lspr_ctx *ctx, int mode, const Arn &a0, GraphCache &gc) {
     capturing = true;
     arn_precond_kernel<<<gN, kT, 0, cs>>>(a);
     ++ctx->n_launches;
-    // the product works on the running systems only, packed into the first slots (one
-    // surface; with several, the channel sets are (system, surface) pairs and all run)
-    if (a.S == 1) {
-        ctx->rhs_map = a.rmap;
-        ctx->rhs_inv = a.rmap + a.B;
-        ctx->rhs_nact = a.rmap + 2 * a.B;
-    }
+    // the product works on the running systems only, packed into the first slots (with
+    // several surfaces, the S channel sets of a system follow each other)
+    ctx->rhs_map = a.rmap;
+    ctx->rhs_inv = a.rmap + a.B;
+    ctx->rhs_nact = a.rmap + 2 * a.B + 1;
     const int rc = apply_operator(ctx, mode, a.z, a.w, a.s, a.B);
     ctx->rhs_map = ctx->rhs_inv = ctx->rhs_nact = nullptr;
     if (rc != LSPR_OK) return fail(rc);
@@ -510,7 +510,7 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     LSPR_TRY(ctx, ab.par.ensure(2));
     LSPR_TRY(ctx, ab.tick.ensure(2 * (size_t)B));
     LSPR_TRY(ctx, ab.ctl.ensure(1 + 3 * (size_t)B));
-    LSPR_TRY(ctx, ab.rmap.ensure(2 * (size_t)B + 1));
+    LSPR_TRY(ctx, ab.rmap.ensure(2 * (size_t)B + 2));
     Arn a;
     a.B = B;
     a.m = m;

@@ -197,7 +197,7 @@ struct ArnoldiBufs {
     DArr<double> par;       // [2] tolerance, iteration limit
     DArr<unsigned> tick;    // [2B] last-block tickets
     DArr<int> ctl;          // [1 + 3B] current column j, active[B], jb[B], iters[B]
-    DArr<int> rmap;         // [2B + 1] running systems packed first: slot -> b, b -> slot, count
+    DArr<int> rmap;         // [2B + 2] running systems packed first: slot -> b, b -> slot, count, sets
 };
 
 constexpr int kTimerSlots = 16;
@@ -255,8 +255,8 @@ struct lspr_ctx {
     lspr::GraphCache gcache[2];
     lspr::ArnoldiBufs arn;
     // right-hand sides in use while recording an Arnoldi step (null: all B): slot -> system
-    // map, system -> slot map (-1: converged), and the count; the far-field kernels work on
-    // the first *rhs_nact slots only
+    // map, system -> slot map (-1: converged), and the number of channel sets in use (running
+    // systems x surfaces); the far-field kernels work on the first *rhs_nact sets only
     const int *rhs_map = nullptr, *rhs_inv = nullptr, *rhs_nact = nullptr;
     int64_t graph_cycles = 0, graph_recordings = 0;
     // last error text

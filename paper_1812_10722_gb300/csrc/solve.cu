@@ -153,16 +153,21 @@ __global__ void assemble_surf_kernel(int64_t N, int B, int S, const int *__restr
                                      const double *__restrict__ acc, const int64_t *__restrict__ ptr,
                                      const int *__restrict__ col, const double *__restrict__ dV,
                                      const double *__restrict__ dK, const double2 *__restrict__ x,
-                                     const double2 *__restrict__ s, double2 *y, double2 *Vd, double2 *Kp) {
+                                     const double2 *__restrict__ s, double2 *y, double2 *Vd, double2 *Kp,
+                                     const int *inv) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= N * B) return;
     const int64_t i = g / B;
     const int b = (int)(g - i * B);
+    // the far part of system b sits in sets k S .. k S + S - 1, k = inv[b] (identity without
+    // a map); rows of converged systems (k = -1) are left untouched
+    const int k = inv ? inv[b] : b;
+    if (k < 0) return;
     const int si = surf[i];
     const double2 *xb = x + (int64_t)b * 2 * N;
     double2 Ks = make_double2(0, 0), Vs = make_double2(0, 0), Ka = make_double2(0, 0), Vw = make_double2(0, 0);
     for (int t = 0; t < S; ++t) {
-        const double *a = acc + 4 * ((i * B + b) * S + t);
+        const double *a = acc + 4 * ((i * B + k) * S + t);
         double2 V = make_double2(a[0], a[1]), K = make_double2(a[2], a[3]);
         if (RAW) {   // near corrections of surface t added below
             Vd[(int64_t)t * N + i] = V;
@@ -250,7 +255,7 @@ int apply_operator(lspr_ctx *ctx, int mode, const double2 *x, double2 *y, const 
     if (m.S > 1) {
         assemble_surf_kernel<false><<<grid_for(N * B, 128), 128, 0, ctx->stream>>>(
             N, B, m.S, m.surf.p, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, s, y, nullptr,
-            nullptr);
+            nullptr, ctx->rhs_inv);
     } else if (B == 1) {
         assemble_kernel<false><<<grid_for(N * kRowLanes, 256), 256, 0, ctx->stream>>>(
             N, B, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, s, y, nullptr, nullptr,
@@ -274,7 +279,7 @@ int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, dou
     if (m.S > 1)
         assemble_surf_kernel<true><<<grid_for(m.N, 128), 128, 0, ctx->stream>>>(
             m.N, 1, m.S, m.surf.p, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr,
-            nullptr, Vd, Kp);
+            nullptr, Vd, Kp, nullptr);
     else
         assemble_kernel<true><<<grid_for(m.N * kRowLanes, 256), 256, 0, ctx->stream>>>(
             m.N, 1, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_dV.p, m.near_dK.p, x, nullptr, nullptr, Vd, Kp,

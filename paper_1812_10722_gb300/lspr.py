@@ -110,7 +110,7 @@ def _host_ptr(a: np.ndarray):
 
 class TuneOpts(ctypes.Structure):
     _fields_ = [("target_rel_err", ctypes.c_double), ("tol", ctypes.c_double), ("restart", ctypes.c_int32),
-                ("mode", ctypes.c_int32), ("refine", ctypes.c_int32)]
+                ("mode", ctypes.c_int32), ("refine", ctypes.c_int32), ("grid", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -271,7 +271,7 @@ class Context:
         return n.value
 
     def autotune(self, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0), target_rel_err=1e-4, tol=1e-6,
-                 restart=50, mode="tree_fp32", refine=1) -> dict:
+                 restart=50, mode="tree_fp32", refine=1, coarse=False) -> dict:
         """Fastest (theta, P, Ncrit) whose sigma_ext stays within target_rel_err / 2 of the
         reference treecode solve; the chosen tree is left built."""
         eps = np.ascontiguousarray(np.atleast_1d(np.asarray(eps_in, np.complex128)))
@@ -279,7 +279,7 @@ class Context:
         e0 = np.ascontiguousarray(np.asarray(E0, np.float64))
         eo = complex(eps_out)
         o = TuneOpts(float(target_rel_err), float(tol), int(restart), MODES[mode] if isinstance(mode, str) else int(mode),
-                     int(refine))
+                     int(refine), int(bool(coarse)))
         r = TuneResult()
         _check(lib().lspr_autotune(self._h, _host_ptr(eps), eo.real, eo.imag, _host_ptr(e0), _host_ptr(lam),
                                    len(lam), ctypes.byref(o), ctypes.byref(r)), "lspr_autotune", self._h)
