@@ -216,7 +216,7 @@ def run_ours(args, wl, rank, world, local_rank):
         t0 = time.perf_counter()
         tune = ctx.autotune(workload_eps(wl, lt), em, lt, target_rel_err=1e-4, tol=min(wl["tol"], 1e-8),
                             restart=wl["restart"], mode=wl["mode"], refine=1 if wl["refine"] else 0,
-                            coarse=len(tris) > 100000)
+                            coarse=len(tris) > 50000)
         tune["seconds"] = round(time.perf_counter() - t0, 2)
         tune["wavelengths"] = [float(x) for x in lt]
         wl["theta"], wl["P"], wl["Ncrit"] = tune["theta"], tune["P"], tune["Ncrit"]

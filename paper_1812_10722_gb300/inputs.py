@@ -218,6 +218,21 @@ def drude_eps(lambda_nm, eps_inf=DRUDE_AG["eps_inf"], wp=DRUDE_AG["wp"], gamma=D
     return eps_inf - wp * wp / (w * w + 1j * gamma * w)
 
 
+def tabulated_eps(lambda_nm, table_lambda_nm, table_n, table_k) -> np.ndarray:
+    """Permittivity eps = (n + i k)^2 from a tabulated complex refractive index (e.g. the
+    Johnson-Christy silver or Hale-Querry water tables the paper uses, Sec. III), with n and
+    k interpolated linearly in the wavelength.  Wavelengths outside the table are refused."""
+    lam = np.atleast_1d(np.asarray(lambda_nm, float))
+    tl = np.asarray(table_lambda_nm, float)
+    order = np.argsort(tl)
+    tl = tl[order]
+    if lam.min() < tl[0] or lam.max() > tl[-1]:
+        raise ValueError("wavelength outside the tabulated range")
+    n = np.interp(lam, tl, np.asarray(table_n, float)[order])
+    k = np.interp(lam, tl, np.asarray(table_k, float)[order])
+    return (n + 1j * k) ** 2
+
+
 def wavelengths(lo: float, hi: float, count: int) -> np.ndarray:
     """``count`` wavelengths uniform over [lo, hi] nm, both ends included."""
     return np.linspace(lo, hi, count)

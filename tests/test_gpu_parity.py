@@ -492,3 +492,35 @@ def test_multi_surface_upload_errors(lspr):
             ctx.mesh_upload(v, t, surf_id=bad, nsurf=3)
         ctx.mesh_upload(v, t, N_k=24, surf_id=surf)
         assert ctx.nsurf == 3
+
+
+def test_grid_study_through_the_library(lspr, oracle):
+    # the paper's Table 6 case (R = 8 nm, lossy water, K_fine = 37) on the GPU: errors
+    # against Eq. an_sol at N = 512 and 2048 reproduce the printed 29.86 % and 7.33 %, the
+    # observed order is ~1 and Richardson from 2048/8192 is much closer than 8192 alone
+    from paper_1812_10722_gb300 import convergence as C
+    em, ep, lam = 1.7972 + 8.5048e-9j, -3.3877 + 0.1922j, 380.0
+    exact = oracle.sigma_closed_form(8.0, ep, em, lam)
+    meshes = [I.octasphere(s, 8.0) for s in (3, 4, 5)]
+    with lspr.Context(0) as ctx:
+        out = C.grid_study([(v, t) for v, t in meshes], ep, em, lam, ctx=ctx, quad=dict(K_fine=37), tol=1e-10,
+                           restart=100, maxiter=3000)
+    err = [100 * (s - exact) / exact for s in out["sigma_ext"]]
+    assert abs(err[0] - 29.86) <= 0.005 + 1e-9 and abs(err[1] - 7.33) <= 0.005 + 1e-9
+    assert abs(err[2] - 1.9) <= 0.05
+    assert 0.95 < out["order"] < 1.1
+    assert abs(out["extrapolated"] - exact) < 0.1 * abs(out["sigma_ext"][2] - exact)
+
+
+def test_lossy_host_matches_oracle(lspr, oracle):
+    # complex host permittivity (k' = Re k in sigma_ext): GPU solve against the oracle's
+    v, t = I.icosphere(3, 10.0)
+    em = 1.7689 + 0.05j
+    lam = np.array([370.0, 390.0])
+    ep = I.drude_eps(lam)
+    _, so, _, bad = oracle.solve(v, t, ep, em, lam, tol=1e-10)
+    assert bad == 0
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        r = ctx.solve(ep, em, lam, tol=1e-10, mode="direct_fp64", restart=100, maxiter=2000)
+    assert np.max(np.abs(r.sigma_ext - so) / so) < 1e-6
