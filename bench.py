@@ -495,6 +495,8 @@ def run_matvecs(args, wl):
     lam = np.asarray(wl["lam"], float)
     s = I.drude_eps(lam) / I.EPS_WATER   # one product over the workload's B right-hand sides
     ctx = lspr.Context(0, torch.cuda.current_stream().cuda_stream)
+    if args.no_tc:
+        ctx.set_tensor_cores(False)
     ctx.mesh_upload(verts, tris, wl["K"], wl["K_fine"], wl["N_k"])
     mode = args.matvec_mode or wl["mode"]
     if mode.startswith("tree"):
@@ -533,6 +535,8 @@ def run_profile(args, wl):
     ctx = lspr.Context(0, stream.cuda_stream)
     if args.no_graphs:
         ctx.set_graphs(False)   # ncu does not profile the kernels inside a graph's loop
+    if args.no_tc:
+        ctx.set_tensor_cores(False)
 
     def step():
         ctx.mesh_upload(v_d, t_d, wl["K"], wl["K_fine"], wl["N_k"])
@@ -573,6 +577,7 @@ def main():
     ap.add_argument("--tree", default=None, help="THETA,P,NCRIT: fixed treecode parameters (no autotuning)")
     ap.add_argument("--profile", action="store_true", help="only the steps, in an NVTX range 'timed' (profiling)")
     ap.add_argument("--no-graphs", action="store_true", help="host-driven Arnoldi cycles (profiling)")
+    ap.add_argument("--no-tc", action="store_true", help="FP32 M2P on the CUDA cores, not tcgen05")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.restart:

@@ -237,6 +237,16 @@ LSPR_API int lspr_get_timing(lspr_ctx *ctx, double *ms, int64_t *launches);
  * events cannot sit inside a graph loop.  If recording fails the context falls back
  * to host-driven cycles. */
 LSPR_API int lspr_set_graphs(lspr_ctx *ctx, int32_t enable);
+/* The FP32 M2P of several right-hand sides (B >= 2) runs on the tensor cores
+ * (tcgen05, TF32 operands split into high and low parts, three products per term block,
+ * FP32 accumulation in tensor memory) by default; lspr_set_tensor_cores(ctx, 0) selects the
+ * FP32-pipe kernel of the same sums. */
+LSPR_API int lspr_set_tensor_cores(lspr_ctx *ctx, int32_t enable);
+/* Bounded waits inside device kernels that ran out since lspr_create (the tensor-core
+ * M2P's pipeline barriers, about one second each): a kernel whose wait runs out stops its
+ * block, frees its resources and counts here, and the product it computed is incomplete.
+ * Synchronises the context's stream.  LSPR_E_ARG: null pointer. */
+LSPR_API int lspr_device_errors(lspr_ctx *ctx, int32_t *count);
 /* Graph cycles launched and graphs recorded since lspr_create (either pointer may be null). */
 LSPR_API int lspr_graph_stats(lspr_ctx *ctx, int64_t *cycles, int64_t *recordings);
 

@@ -219,6 +219,21 @@ int lspr_set_graphs(lspr_ctx *c, int32_t enable) {
     return LSPR_OK;
 }
 
+int lspr_set_tensor_cores(lspr_ctx *c, int32_t enable) {
+    if (!c) return LSPR_E_ARG;
+    c->use_tensor_cores = enable != 0;
+    return LSPR_OK;
+}
+
+int lspr_device_errors(lspr_ctx *c, int32_t *count) {
+    if (!c || !count) return LSPR_E_ARG;
+    *count = 0;
+    if (!c->dev_err.p) return LSPR_OK;
+    LSPR_TRY(c, cudaStreamSynchronize(c->stream));
+    LSPR_TRY(c, cudaMemcpy(count, c->dev_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return LSPR_OK;
+}
+
 int lspr_graph_stats(lspr_ctx *c, int64_t *cycles, int64_t *recordings) {
     if (!c) return LSPR_E_ARG;
     if (cycles) *cycles = c->graph_cycles;

@@ -9,6 +9,10 @@ int p2m_orders_f32(lspr_ctx *ctx, int B) {
 }
 
 int m2p_orders_f32(lspr_ctx *ctx, double *acc, int *counter, int B) {
+    if (B > 1 && ctx->use_tensor_cores) {
+        const int rc = m2p_tc_launch(ctx, acc, counter, B);
+        if (rc != LSPR_E_STATE) return rc;
+    }
     LSPR_DISPATCH_P(m2p_launch, float, B, ctx, acc, counter, B);
     return LSPR_OK;
 }

@@ -250,6 +250,9 @@ struct lspr_ctx {
     lspr::DArr<unsigned char> scratch[lspr::kScratchSlots];   // see lspr::Tmp
     // device-driven Arnoldi cycles (a CUDA graph per configuration, gmres_graph.cu)
     bool use_graphs = true;
+    bool use_tensor_cores = true;      // FP32 M2P of several right-hand sides on tcgen05
+    lspr::DArr<unsigned char> tc_img;  // split moments in tensor-core operand layout
+    lspr::DArr<int> dev_err;           // bounded device waits that ran out (never reset)
     cudaStream_t gstream = nullptr;    // private recording/launch stream
     cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;
     lspr::GraphCache gcache[2];

@@ -83,12 +83,15 @@ def lib():
             L.lspr_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
             L.lspr_get_timing.argtypes = [_vp, _vp, _vp]
             L.lspr_set_graphs.argtypes = [_vp, _i32]
+            L.lspr_set_tensor_cores.argtypes = [_vp, _i32]
             L.lspr_autotune.argtypes = [_vp, _vp, _d, _d, _vp, _vp, _i32, ctypes.POINTER(TuneOpts),
                                         ctypes.POINTER(TuneResult)]
             L.lspr_graph_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+            L.lspr_device_errors.argtypes = [_vp, ctypes.POINTER(_i32)]
             for f in ("lspr_create", "lspr_destroy", "lspr_mesh_upload", "lspr_tree_build", "lspr_matvec",
                       "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing", "lspr_launch_count",
-                      "lspr_set_graphs", "lspr_graph_stats", "lspr_autotune"):
+                      "lspr_set_graphs", "lspr_graph_stats", "lspr_autotune", "lspr_set_tensor_cores",
+                      "lspr_device_errors"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -288,6 +291,16 @@ class Context:
     def set_graphs(self, enable: bool):
         """Arnoldi cycles as CUDA graph launches (default) or host-driven."""
         _check(lib().lspr_set_graphs(self._h, int(bool(enable))), "lspr_set_graphs", self._h)
+
+    def set_tensor_cores(self, enable: bool):
+        """FP32 M2P of several right-hand sides on the tensor cores (default) or the FP32 pipe."""
+        _check(lib().lspr_set_tensor_cores(self._h, int(bool(enable))), "lspr_set_tensor_cores", self._h)
+
+    def device_errors(self) -> int:
+        """Bounded device waits that ran out since the context was created (0 when healthy)."""
+        n = ctypes.c_int32(0)
+        _check(lib().lspr_device_errors(self._h, ctypes.byref(n)), "lspr_device_errors", self._h)
+        return n.value
 
     def graph_stats(self) -> dict:
         c, r = ctypes.c_int64(0), ctypes.c_int64(0)
