@@ -40,6 +40,8 @@ inline bool mode_tree(int mode) { return mode == LSPR_TREE_FP64 || mode == LSPR_
 
 constexpr double kInv4Pi = 0.079577471545947667884;   // 1 / (4 pi)
 constexpr int kTargetBlock = 64;                       // targets per interaction block (2 per lane)
+constexpr int kTcGroup = 4;        // target blocks per tensor-core M2P group (256 targets)
+constexpr int kTcGroupSeg = 24;    // boxes per tensor-core M2P work unit at most
 constexpr int kMaxP = 8;                               // highest Taylor order compiled
 constexpr int kMaxDepth = 10;                          // octree levels below the root (10 bits per axis)
 constexpr int kMaxNk = 32;
@@ -149,6 +151,12 @@ struct Tree {
     DArr<int4> p2p_items;    // (target block, source begin, source end, 0)
     DArr<int4> m2p_items;    // (target block, list begin, list end, 0)
     DArr<int> m2p_list;      // box ids
+    // the M2P lists of groups of kTcGroup consecutive target blocks (tensor-core M2P): the
+    // union of the blocks' lists, sorted by box, with a mask of the blocks that accepted each
+    // box, cut into segments
+    DArr<int4> tc_items;     // (group, list begin, list end, 0)
+    DArr<int2> tc_list;      // (box id, block mask)
+    int64_t n_tc_items = 0, n_tc_pairs = 0;
     DArr<int4> p2m_items;    // (leaf, source begin, source end, 0): leaves under an accepted box
     DArr<int> box_parent;    // parent box (-1 for the root)
     // moments [box][NT] x (Vre, Vim, Kre, Kim)

@@ -1,28 +1,30 @@
 // M2P of several right-hand sides on the fifth-generation tensor cores (tcgen05).
 //
-// For a (64-target block, box) pair the contraction over the Taylor terms is a matrix
-// product, D[channel][target] += sum_k M[k][channel] a_k[target]: channels (4 per right-hand
-// side: V re, V im, K re, K im) are the MMA's M dimension, the 64 targets its N, the terms its
-// K.  Both operands are split into TF32 high and low parts and the product is taken as
-// A_hi B_hi + A_hi B_lo + A_lo B_hi (3xTF32, FP32 accumulation in tensor memory).
+// The contraction over the Taylor terms is a matrix product per box b,
+//   D[channel][target] += sum_k M_k(b)[channel] a_k(target - c_b),
+// with the channels (4 per right-hand side: V re, V im, K re, K im) as the MMA's M dimension,
+// the targets as its N and the terms as its K.  A tcgen05 MMA costs the same time whatever
+// its shape, so N is made as wide as the instruction allows: a work unit is a group of four
+// consecutive 64-target blocks (N = 256) and walks the sorted union of their M2P lists; the
+// coefficients of a block that did not accept a box are zero, so every block still receives
+// exactly the boxes its own acceptance test chose.  M = 64 channels (16 right-hand sides)
+// or 128 (32).  Both operands are split into TF32 high and low parts and the product is
+// taken as A_hi B_hi + A_hi B_lo + A_lo B_hi (3xTF32, FP32 accumulation in tensor memory).
 //
 // Two kernels per product:
 //   - tc_image_kernel writes, once per product, the split moments of every box in the
 //     operand layout of one pipeline stage (K-major 8x16-byte core matrices, no swizzle),
 //     so that staging A is a single bulk copy;
 //   - m2p_tc_kernel is persistent and warp-specialised.  The terms of each (unit, box) are
-//     cut into chunks of 32, one pipeline stage each; the NS stages in shared memory form two
-//     rings, one per generator group (a stage with a single writer per part is reused in
-//     order, so a parity wait can never be two phases ahead):
-//       warp 4 (one lane) fetches work units, publishes them in a small ring, and streams
+//     cut into chunks of 16, one pipeline stage each (a ring of NS stages in shared memory):
+//       warps 0-7 (one thread per target of the group) compute the coefficients a_k by the
+//         recurrence of m2p_kernel and write the split B part of each stage; at the end of a
+//         unit they drain its accumulator (tcgen05.ld) into the FP64 accumulators;
+//       warp 8 (one lane) fetches work units, publishes them in a small ring, and streams
 //         each stage's A part with cp.async.bulk;
-//       warps 0-1 and 2-3 are two generator groups that take alternate boxes: one thread per
-//         target computes the coefficients a_k by the recurrence of m2p_kernel and writes the
-//         split B part of each stage;
-//       warp 5 (one lane) issues the MMAs of each stage once both parts are in, and commits
-//         to the stage's "empty" barrier and, at the end of a unit, to an accumulator barrier;
-//       warps 6-9 drain the accumulator of a finished unit (tcgen05.ld) into the FP64
-//         accumulators while the next unit accumulates into the second TMEM buffer.
+//       warp 9 (one lane) issues the MMAs of each stage once both parts are in, commits to
+//         the stage's "empty" barrier and, at the end of a unit, to an accumulator barrier
+//         (two accumulators of 256 columns alternate between units).
 // Every wait is bounded (about a second): one that runs out raises an abort flag that the
 // other roles see, the block drains its bulk copies and MMAs in flight, frees its tensor
 // memory and returns, and the context's device error count records it.
@@ -32,17 +34,16 @@ namespace lspr {
 
 namespace {
 
-constexpr int kKC = 32;                        // terms per pipeline stage (four MMA K steps)
-constexpr int kTcN = 64;                       // targets per work unit (the MMA's N)
-constexpr int kTcM = 128;                      // MMA rows
+constexpr int kKC = 16;                        // terms per pipeline stage (two MMA K steps)
+constexpr int kTcN = kTcGroup * kTargetBlock;  // targets per work unit (the MMA's N)
 constexpr int kChunkSBO = (kKC / 4) * 128;     // bytes per 8-row group of a stage operand
-constexpr int kGenWarps = 4;                   // two groups of two warps
-constexpr int kProdWarp = kGenWarps, kMmaWarp = kGenWarps + 1, kEpiWarp0 = kGenWarps + 2;
-constexpr int kEpiWarps = 4;
-constexpr int kTcThreads = 32 * (kEpiWarp0 + kEpiWarps);
+constexpr int kGenWarps = kTcN / 32;           // one thread per target
+constexpr int kProdWarp = kGenWarps, kMmaWarp = kGenWarps + 1;
+constexpr int kTcThreads = 32 * (kGenWarps + 2);
 constexpr int kUnitRing = 4;
-constexpr int kRingConsumers = kGenWarps + 1 + kEpiWarps;   // lane 0 of each consumer warp
+constexpr int kRingConsumers = kGenWarps + 1;  // lane 0 of each consumer warp
 constexpr uint32_t kTmemCols = 2 * kTcN;       // two accumulators
+static_assert(kTmemCols <= 512 && kTcN <= 256, "one MMA spans the group");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -56,46 +57,8 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
-// instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N and M
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                            ((uint32_t)(kTcM >> 4) << 24);
-
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-// Stage geometry for order P and RC right-hand sides per unit.  With RC = 16 the MMA's rows
-// 64..127 read the next part of the stage (A_lo after A_hi, B_hi after A_lo); those rows of
-// the product are discarded, and each row of the product depends on its own row of A only.
-template <int P, int RC>
-struct TcShape {
-    static constexpr int NT = n_terms(P);
-    static constexpr int NKC = (NT + kKC - 1) / kKC;
-    static constexpr int ROWS = 4 * RC;
-    static constexpr int A_CH = (ROWS / 8) * kChunkSBO;   // one split part of A per stage
-    static constexpr int B_CH = (kTcN / 8) * kChunkSBO;   // one split part of B per stage
-    static constexpr int STAGE = 2 * A_CH + 2 * B_CH;     // A_hi | A_lo | B_hi | B_lo
-    static constexpr int NS = (192 * 1024) / STAGE;
-    static constexpr int SMEM = NS * STAGE;
-    static_assert(ROWS == 64 || ROWS == kTcM, "unit of 16 or 32 right-hand sides");
-    static_assert(NS % 2 == 0 && NS >= 2, "half of the stages per generator group");
-    static_assert(ROWS == kTcM || B_CH >= (kTcM - ROWS) / 8 * kChunkSBO, "MMA rows stay inside the stage");
-};
-
-// byte offset of (row r, term k) inside one split part of a stage operand
-__device__ __forceinline__ int core_off(int r, int k) {
-    return (r >> 3) * kChunkSBO + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
-}
-
-// Stage of chunk kc of the gb-th box of the block (boxes counted over all its units): the
-// generator group gb & 1 owns stages [g NS/2, (g+1) NS/2) and fills them in order, so that
-// every stage has one writer of each part and its uses come in order; use = how many times
-// the stage was filled before.
-template <int NS, int NKC>
-__device__ __forceinline__ int stage_of(int64_t gb, int kc, int64_t &use) {
-    constexpr int H = NS / 2;
-    const int64_t k = (gb >> 1) * NKC + kc;
-    use = k / H;
-    return (int)(gb & 1) * H + (int)(k - use * H);
-}
 
 __device__ __forceinline__ uint64_t now_ns() {
     uint64_t t;
@@ -142,14 +105,59 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(d),
-                 "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+                 "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+
+// instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N and M
+constexpr uint32_t idesc_tf32(int m, int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// Stage geometry for order P and RC right-hand sides per unit: M = 4 RC accumulator rows.
+// With M = 64 row m sits in TMEM lane 32 (m / 16) + m % 16 (16 rows per lane quarter), with
+// M = 128 in lane m.
+template <int P, int RC>
+struct TcShape {
+    static constexpr int NT = n_terms(P);
+    static constexpr int NKC = (NT + kKC - 1) / kKC;
+    static constexpr int ROWS = 4 * RC;
+    static constexpr int RQ = ROWS / 4;                    // accumulator rows per lane quarter
+    static constexpr uint32_t IDESC = idesc_tf32(ROWS, kTcN);
+    static constexpr int A_CH = (ROWS / 8) * kChunkSBO;   // one split part of A per stage
+    static constexpr int B_CH = (kTcN / 8) * kChunkSBO;   // one split part of B per stage
+    static constexpr int STAGE = 2 * A_CH + 2 * B_CH;     // A_hi | A_lo | B_hi | B_lo
+    static constexpr int NS = (200 * 1024) / STAGE;
+    static constexpr int SMEM = NS * STAGE;
+    static_assert(ROWS == 64 || ROWS == 128, "unit of 16 or 32 right-hand sides");
+    static_assert(NS >= 2, "at least two stages");
+};
+
+// byte offset of (row r, term k) inside one split part of a stage operand
+__device__ __forceinline__ int core_off(int r, int k) {
+    return (r >> 3) * kChunkSBO + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
+// every lane waits; the verdict is made uniform over the warp (the callers then take
+// .sync.aligned steps or warp syncs together)
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    const bool ok = bar_wait(bar, parity, abort_flag);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// wait for a phase that completes by itself (copies or MMAs in flight), bounded, whatever
+// the abort flag says
+__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = now_ns();
+    while (!bar_try(bar, parity) && now_ns() - t0 < 1000000000ull) {
+    }
 }
 
 // The split moments of every box in stage layout: image[((box * nrc + rc) * NKC + kc)] holds
-// A_hi then A_lo of right-hand sides rc*RC.. and terms kc*32..; rows of right-hand sides at
+// A_hi then A_lo of right-hand sides rc*RC.. and terms kc*16..; rows of right-hand sides at
 // or beyond the active count and terms beyond NT are zero.  One thread per 16 bytes of A_hi.
 template <int P, int RC>
 __global__ void tc_image_kernel(int64_t nbox, int B, int nrc, const float4 *__restrict__ mom,
@@ -183,25 +191,10 @@ __global__ void tc_image_kernel(int64_t nbox, int B, int nrc, const float4 *__re
     }
 }
 
-// every lane waits; the verdict is made uniform over the warp (the callers then take
-// .sync.aligned steps or warp syncs together)
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-    const bool ok = bar_wait(bar, parity, abort_flag);
-    return __all_sync(0xffffffffu, ok);
-}
-
-// wait for a phase that completes by itself (copies or MMAs in flight), bounded, whatever
-// the abort flag says
-__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity) {
-    const uint64_t t0 = now_ns();
-    while (!bar_try(bar, parity) && now_ns() - t0 < 1000000000ull) {
-    }
-}
-
 template <int P, int RC>
 __global__ void __launch_bounds__(kTcThreads, 1)
     m2p_tc_kernel(const int4 *__restrict__ items, int64_t nitems, int B, int nrc, const float4 *__restrict__ tgt,
-                  int64_t ntgt, const int *__restrict__ list, const float4 *__restrict__ box_c,
+                  int64_t ntgt, const int2 *__restrict__ list, const float4 *__restrict__ box_c,
                   const unsigned char *__restrict__ img, double *__restrict__ acc, int *counter, int *error,
                   const int *nact) {
     using S = TcShape<P, RC>;
@@ -222,7 +215,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             bar_init(smem_addr(&acc_full[a]), 1);
-            bar_init(smem_addr(&acc_empty[a]), kEpiWarps);
+            bar_init(smem_addr(&acc_empty[a]), kGenWarps);
         }
         for (int r = 0; r < kUnitRing; ++r) {
             bar_init(smem_addr(&ring_full[r]), 1);
@@ -248,10 +241,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == kProdWarp) {
         // ---- producer: work units and the A part of every stage
         if (lane == 0) {
-            int64_t gb = 0;        // boxes streamed so far
-            int64_t last[NS];      // last use armed per stage (-1: none)
-#pragma unroll
-            for (int s = 0; s < NS; ++s) last[s] = -1;
+            int64_t seq = 0;   // stages armed so far
             for (int uc = 0;; ++uc) {
                 const int slot = uc % kUnitRing;
                 if (uc >= kUnitRing &&
@@ -265,12 +255,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int rc = (int)(u - ii * nbc);
                 const int4 item = __ldg(items + ii);
                 bool ok = true;
-                for (int l = item.y; l < item.z && ok; ++l, ++gb) {
-                    const unsigned char *src = img + ((int64_t)__ldg(list + l) * nrc + rc) * NKC * (2 * S::A_CH);
-                    for (int kc = 0; kc < NKC; ++kc) {
-                        int64_t use;
-                        const int s = stage_of<NS, NKC>(gb, kc, use);
-                        if (use > 0 && !bar_wait(smem_addr(&empty_s[s]), (uint32_t)(use - 1) & 1u, &abort_s)) {
+                for (int l = item.y; l < item.z && ok; ++l) {
+                    const unsigned char *src = img + ((int64_t)__ldg(&list[l].x) * nrc + rc) * NKC * (2 * S::A_CH);
+                    for (int kc = 0; kc < NKC; ++kc, ++seq) {
+                        const int s = (int)(seq % NS);
+                        if (seq >= NS &&
+                            !bar_wait(smem_addr(&empty_s[s]), (uint32_t)((seq / NS) - 1) & 1u, &abort_s)) {
                             ok = false;
                             break;
                         }
@@ -283,86 +273,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 sbase + (uint32_t)(s * S::STAGE)),
                             "l"(src + (int64_t)kc * 2 * S::A_CH), "r"(2 * S::A_CH), "r"(fb)
                             : "memory");
-                        last[s] = use;
                     }
                 }
                 if (!ok) break;
             }
-            // copies may still be in flight into the last use of each stage
-#pragma unroll
-            for (int s = 0; s < NS; ++s)
-                if (last[s] >= 0) drain_wait(smem_addr(&full_a[s]), (uint32_t)last[s] & 1u);
-        }
-    } else if (warp < kGenWarps) {
-        // ---- generators: group g takes the boxes of parity g (counted over all units)
-        const int g = warp >> 1, tg = tid - kTcN * g;   // target row 0..63
-        int64_t gb = 0;
-        for (int uc = 0;; ++uc) {
-            const int slot = uc % kUnitRing;
-            if (!warp_wait(smem_addr(&ring_full[slot]), (uint32_t)(uc / kUnitRing) & 1u, &abort_s)) break;
-            const int64_t u = ring[slot];
-            if (u >= units) break;
-            const int4 item = __ldg(items + u / nbc);
-            const int64_t ti = (int64_t)item.x * kTargetBlock + tg;
-            const float4 q = ti < ntgt ? tgt[ti] : tgt[0];
-            bool ok = true;
-            for (int l = item.y; l < item.z; ++l, ++gb) {
-                if ((int)(gb & 1) != g) continue;
-                const float4 c = box_c[__ldg(list + l)];
-                constexpr MultiIndex<P> mi{};
-                const float R[3] = {q.x - c.x, q.y - c.y, q.z - c.z};
-                float a[NT];
-                a[0] = rsq(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
-                const float ir2 = a[0] * a[0];
-#pragma unroll
-                for (int t = 1; t < NT; ++t) {
-                    const int n = mi.deg[t];
-                    float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        if (mi.m1[t][d] >= 0) s1 += R[d] * a[mi.m1[t][d]];
-                        if (mi.m2[t][d] >= 0) s2 += a[mi.m2[t][d]];
-                    }
-                    const float c1 = (float)(-(2.0 * n - 1.0) / n), c2 = (float)(-(n - 1.0) / n);
-                    a[t] = (c1 * s1 + c2 * s2) * ir2;
-                }
-#pragma unroll
-                for (int kc = 0; kc < NKC; ++kc) {
-                    int64_t use;
-                    const int s = stage_of<NS, NKC>(gb, kc, use);
-                    if (use > 0 && !warp_wait(smem_addr(&empty_s[s]), (uint32_t)(use - 1) & 1u, &abort_s)) {
-                        ok = false;
-                        break;
-                    }
-                    unsigned char *bh = tc_smem + s * S::STAGE + 2 * S::A_CH, *bl = bh + S::B_CH;
-                    // four terms per 16-byte store: the eight lanes of a quarter warp fill one
-                    // core matrix, free of bank conflicts
-#pragma unroll
-                    for (int t4 = 0; t4 < kKC / 4; ++t4) {
-                        float v[4];
-#pragma unroll
-                        for (int w = 0; w < 4; ++w) {
-                            const int t = kc * kKC + 4 * t4 + w;
-                            v[w] = t < NT ? a[t < NT ? t : 0] : 0.f;
-                        }
-                        const float4 hi = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
-                        *(float4 *)(bh + core_off(tg, 4 * t4)) = hi;
-                        *(float4 *)(bl + core_off(tg, 4 * t4)) =
-                            make_float4(v[0] - hi.x, v[1] - hi.y, v[2] - hi.z, v[3] - hi.w);
-                    }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bar_arrive(smem_addr(&full_b[s]));
-                }
-                if (!ok) break;
-            }
-            if (!ok) break;
-            __syncwarp();
-            if (lane == 0) bar_arrive(smem_addr(&ring_empty[slot]));
+            // the copies of the last NS armed stages may still be in flight
+            for (int64_t k = seq > NS ? seq - NS : 0; k < seq; ++k)
+                drain_wait(smem_addr(&full_a[k % NS]), (uint32_t)(k / NS) & 1u);
         }
     } else if (warp == kMmaWarp) {
         // ---- MMA issue: one lane
         if (lane == 0) {
-            int64_t gb = 0;
+            int64_t seq = 0;
             int nu = 0;   // non-empty units so far (accumulator = nu & 1)
             for (int uc = 0;; ++uc) {
                 const int slot = uc % kUnitRing;
@@ -377,11 +299,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t d = tmem + (uint32_t)(ab * kTcN);
                     bool ok = true;
-                    for (int l = item.y; l < item.z && ok; ++l, ++gb) {
-                        for (int kc = 0; kc < NKC; ++kc) {
-                            int64_t use;
-                            const int s = stage_of<NS, NKC>(gb, kc, use);
-                            const uint32_t par = (uint32_t)use & 1u;
+                    for (int l = item.y; l < item.z && ok; ++l) {
+                        for (int kc = 0; kc < NKC; ++kc, ++seq) {
+                            const int s = (int)(seq % NS);
+                            const uint32_t par = (uint32_t)(seq / NS) & 1u;
                             if (!bar_wait(smem_addr(&full_a[s]), par, &abort_s) ||
                                 !bar_wait(smem_addr(&full_b[s]), par, &abort_s)) {
                                 ok = false;
@@ -396,9 +317,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 const uint64_t dal = umma_desc(st + S::A_CH + off, 128, kChunkSBO);
                                 const uint64_t dbh = umma_desc(st + 2 * S::A_CH + off, 128, kChunkSBO);
                                 const uint64_t dbl = umma_desc(st + 2 * S::A_CH + S::B_CH + off, 128, kChunkSBO);
-                                tc_mma(d, dah, dbh, (l == item.y && kc == 0 && ks == 0) ? 0u : 1u);
-                                tc_mma(d, dah, dbl, 1u);
-                                tc_mma(d, dal, dbh, 1u);
+                                tc_mma(d, dah, dbh, S::IDESC, (l == item.y && kc == 0 && ks == 0) ? 0u : 1u);
+                                tc_mma(d, dah, dbl, S::IDESC, 1u);
+                                tc_mma(d, dal, dbh, S::IDESC, 1u);
                             }
                             tc_commit(smem_addr(&empty_s[s]));
                         }
@@ -414,8 +335,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             drain_wait(smem_addr(&drain), 0u);
         }
     } else {
-        // ---- epilogue: warp w reads lanes 32 (w % 4).. of the accumulator
-        const int qd = warp & 3;
+        // ---- generators (one thread per target of the group), then the unit's epilogue
+        const int blk = tid / kTargetBlock;   // block of the group this thread's target is in
+        int64_t seq = 0;
         int nu = 0;
         for (int uc = 0;; ++uc) {
             const int slot = uc % kUnitRing;
@@ -425,33 +347,98 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int64_t ii = u / nbc;
             const int b0 = (int)(u - ii * nbc) * RC, nb = min(RC, Bact - b0);
             const int4 item = __ldg(items + ii);
+            const int64_t tbase = (int64_t)item.x * kTcN;   // first target of the group
+            const int64_t ti = tbase + tid;
+            const bool live = ti < ntgt;
+            const float4 q = live ? tgt[ti] : tgt[0];
+            bool ok = true;
+            for (int l = item.y; l < item.z; ++l) {
+                const int2 e = __ldg(list + l);
+                const bool on = live && ((e.y >> blk) & 1);   // uniform over the warp but for the tail
+                float a[NT];
+                if (on) {
+                    const float4 c = box_c[e.x];
+                    constexpr MultiIndex<P> mi{};
+                    const float R[3] = {q.x - c.x, q.y - c.y, q.z - c.z};
+                    a[0] = rsq(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+                    const float ir2 = a[0] * a[0];
+#pragma unroll
+                    for (int t = 1; t < NT; ++t) {
+                        const int n = mi.deg[t];
+                        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            if (mi.m1[t][d] >= 0) s1 += R[d] * a[mi.m1[t][d]];
+                            if (mi.m2[t][d] >= 0) s2 += a[mi.m2[t][d]];
+                        }
+                        const float c1 = (float)(-(2.0 * n - 1.0) / n), c2 = (float)(-(n - 1.0) / n);
+                        a[t] = (c1 * s1 + c2 * s2) * ir2;
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) a[t] = 0.f;
+                }
+#pragma unroll
+                for (int kc = 0; kc < NKC; ++kc) {
+                    const int s = (int)(seq % NS);
+                    if (seq >= NS && !warp_wait(smem_addr(&empty_s[s]), (uint32_t)((seq / NS) - 1) & 1u, &abort_s)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *bh = tc_smem + s * S::STAGE + 2 * S::A_CH, *bl = bh + S::B_CH;
+                    // four terms per 16-byte store: the eight lanes of a quarter warp fill one
+                    // core matrix, free of bank conflicts
+#pragma unroll
+                    for (int t4 = 0; t4 < kKC / 4; ++t4) {
+                        float v[4];
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            const int t = kc * kKC + 4 * t4 + w;
+                            v[w] = t < NT ? a[t < NT ? t : 0] : 0.f;
+                        }
+                        const float4 hi = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
+                        *(float4 *)(bh + core_off(tid, 4 * t4)) = hi;
+                        *(float4 *)(bl + core_off(tid, 4 * t4)) =
+                            make_float4(v[0] - hi.x, v[1] - hi.y, v[2] - hi.z, v[3] - hi.w);
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bar_arrive(smem_addr(&full_b[s]));
+                    ++seq;
+                }
+                if (!ok) break;
+            }
+            if (!ok) break;
             if (item.y < item.z) {
-                const int ab = nu & 1;
+                // epilogue: warp w reads lane quarter w % 4 (rows RQ (w % 4)..) and columns
+                // 128 (w / 4).. of the unit's accumulator
+                const int ab = nu & 1, qd = warp & 3, half = warp >> 2;
                 if (!warp_wait(smem_addr(&acc_full[ab]), (uint32_t)(nu >> 1) & 1u, &abort_s)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                if (32 * qd < 4 * nb) {
-                    const int64_t tb = (int64_t)item.x * kTargetBlock;
-                    const int pa = tb + lane < ntgt ? panel_of(tgt[tb + lane].w) : -1;
-                    const int pb = tb + 32 + lane < ntgt ? panel_of(tgt[tb + 32 + lane].w) : -1;
-                    const int m = 32 * qd + lane, j = m >> 2, cpt = m & 3;
+                if (S::RQ * qd < 4 * nb) {
+                    const int m = S::RQ * qd + lane, j = lane < S::RQ ? m >> 2 : RC, cpt = m & 3;
 #pragma unroll 1
-                    for (int c0 = 0; c0 < kTcN; c0 += 16) {
-                        uint32_t v[16];
-                        const uint32_t addr = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(ab * kTcN + c0);
-                        asm volatile(
-                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-                            "%15}, [%16];"
-                            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                              "=r"(v[14]), "=r"(v[15])
-                            : "r"(addr));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    for (int c0 = 0; c0 < kTcN / 2; c0 += 32) {
+                        const int64_t tc = tbase + half * (kTcN / 2) + c0 + lane;   // this lane's column's target
+                        const int pc = tc < ntgt ? panel_of(tgt[tc].w) : -1;
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) {
-                            const int col = c0 + x;
-                            const int p = __shfl_sync(0xffffffffu, col < 32 ? pa : pb, col & 31);
-                            if (j < nb && p >= 0)
-                                atomicAdd(acc + 4 * ((int64_t)p * B + b0 + j) + cpt, (double)__uint_as_float(v[x]));
+                        for (int h16 = 0; h16 < 32; h16 += 16) {
+                            uint32_t v[16];
+                            const uint32_t addr = tmem + ((uint32_t)(32 * qd) << 16) +
+                                                  (uint32_t)(ab * kTcN + half * (kTcN / 2) + c0 + h16);
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                                "%14,%15}, [%16];"
+                                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                                  "=r"(v[14]), "=r"(v[15])
+                                : "r"(addr));
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                            for (int x = 0; x < 16; ++x) {
+                                const int p = __shfl_sync(0xffffffffu, pc, h16 + x);
+                                if (j < nb && p >= 0)
+                                    atomicAdd(acc + 4 * ((int64_t)p * B + b0 + j) + cpt, (double)__uint_as_float(v[x]));
+                            }
                         }
                     }
                 }
@@ -476,24 +463,27 @@ int tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     using S = TcShape<P, RC>;
     static int smem_set = 0;
     Tree &tr = ctx->tree;
+    if (tr.n_tc_items == 0) return LSPR_OK;
     const int nrc = (B + RC - 1) / RC;
     const int64_t segs = tr.nboxes * nrc * S::NKC * (S::A_CH / 16);
     LSPR_TRY(ctx, ctx->tc_img.ensure((size_t)segs * 32));
+    if (!ctx->dev_err.p) {
+        LSPR_TRY(ctx, ctx->dev_err.ensure(1));
+        LSPR_TRY(ctx, cudaMemsetAsync(ctx->dev_err.p, 0, sizeof(int), ctx->stream));
+    }
     if (!smem_set) {
         LSPR_TRY(ctx, cudaFuncSetAttribute(m2p_tc_kernel<P, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
         smem_set = 1;
     }
     ++ctx->n_launches;   // the image; the caller counts the M2P launch
-    const unsigned gi = (unsigned)std::max<int64_t>(1, std::min<int64_t>((segs + 255) / 256, 8 * std::max(1, ctx->num_sms)));
+    const unsigned gi =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((segs + 255) / 256, 8 * std::max(1, ctx->num_sms)));
     tc_image_kernel<P, RC><<<gi, 256, 0, ctx->stream>>>(tr.nboxes, B, nrc, Views<float>::mom(ctx), ctx->tc_img.p,
                                                          ctx->rhs_nact);
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tr.n_m2p_items * nrc, std::max(1, ctx->num_sms)));
-    if (!ctx->dev_err.p) {
-        LSPR_TRY(ctx, ctx->dev_err.ensure(1));
-        LSPR_TRY(ctx, cudaMemsetAsync(ctx->dev_err.p, 0, sizeof(int), ctx->stream));
-    }
+    const unsigned grid =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(tr.n_tc_items * nrc, std::max(1, ctx->num_sms)));
     m2p_tc_kernel<P, RC><<<grid, kTcThreads, S::SMEM, ctx->stream>>>(
-        tr.m2p_items.p, tr.n_m2p_items, B, nrc, Views<float>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p,
+        tr.tc_items.p, tr.n_tc_items, B, nrc, Views<float>::tgt(ctx), ctx->mesh.N, tr.tc_list.p,
         Views<float>::bc(ctx), ctx->tc_img.p, acc, counter, ctx->dev_err.p, ctx->rhs_nact);
     return LSPR_OK;
 }

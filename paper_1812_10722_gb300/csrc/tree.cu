@@ -703,6 +703,50 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
     LSPR_TRY(ctx, tr.p2m_items.ensure(std::max<size_t>(1, p2m.size())));
     if (!p2m.empty())
         LSPR_TRY(ctx, cudaMemcpyAsync(tr.p2m_items.p, p2m.data(), sizeof(int4) * p2m.size(), cudaMemcpyHostToDevice, st));
+    // M2P lists of groups of kTcGroup consecutive target blocks (tensor-core M2P): per group
+    // the sorted union of its blocks' lists with the mask of accepting blocks, cut into
+    // segments of at most kTcGroupSeg boxes (host side: one pass over the pairs)
+    std::vector<int> hlist((size_t)tot[1]);
+    std::vector<int4> hitems((size_t)tot[2]);
+    if (tot[1] > 0) {
+        LSPR_TRY(ctx, cudaMemcpyAsync(hlist.data(), tr.m2p_list.p, sizeof(int) * tot[1], cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaMemcpyAsync(hitems.data(), tr.m2p_items.p, sizeof(int4) * tot[2], cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    }
+    std::vector<int2> glist;
+    std::vector<int4> gitems;
+    {
+        const int64_t ngroups = (ntb + kTcGroup - 1) / kTcGroup;
+        std::vector<std::vector<int2>> per(ngroups);   // (box, mask) entries of each group
+        for (const int4 &it : hitems) {
+            const int64_t g = it.x / kTcGroup;
+            const int bit = 1 << (int)(it.x % kTcGroup);
+            for (int l = it.y; l < it.z; ++l) per[g].push_back(make_int2(hlist[l], bit));
+        }
+        for (int64_t g = 0; g < ngroups; ++g) {
+            std::vector<int2> &v = per[g];
+            if (v.empty()) continue;
+            std::sort(v.begin(), v.end(), [](const int2 &a, const int2 &b) { return a.x < b.x; });
+            const int64_t start = (int64_t)glist.size();
+            for (const int2 &e : v) {
+                if ((int64_t)glist.size() > start && glist.back().x == e.x)
+                    glist.back().y |= e.y;
+                else
+                    glist.push_back(e);
+            }
+            const int64_t n = (int64_t)glist.size() - start, k = (n + kTcGroupSeg - 1) / kTcGroupSeg;
+            for (int64_t q = 0; q < k; ++q)
+                gitems.push_back(make_int4((int)g, (int)(start + n * q / k), (int)(start + n * (q + 1) / k), 0));
+        }
+    }
+    tr.n_tc_pairs = (int64_t)glist.size();
+    tr.n_tc_items = (int64_t)gitems.size();
+    LSPR_TRY(ctx, tr.tc_list.ensure(std::max<size_t>(1, glist.size())));
+    LSPR_TRY(ctx, tr.tc_items.ensure(std::max<size_t>(1, gitems.size())));
+    if (!glist.empty()) {
+        LSPR_TRY(ctx, cudaMemcpyAsync(tr.tc_list.p, glist.data(), sizeof(int2) * glist.size(), cudaMemcpyHostToDevice, st));
+        LSPR_TRY(ctx, cudaMemcpyAsync(tr.tc_items.p, gitems.data(), sizeof(int4) * gitems.size(), cudaMemcpyHostToDevice, st));
+    }
     LSPR_TRY(ctx, tr.box_parent.ensure(nboxes));
     LSPR_TRY(ctx, cudaMemcpyAsync(tr.box_parent.p, hpar.data(), sizeof(int) * nboxes, cudaMemcpyHostToDevice, st));
     timer_end(ctx, T_TREE, ev);

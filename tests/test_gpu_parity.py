@@ -559,6 +559,26 @@ def test_tensor_core_m2p_matches_fp32_pipe(lspr, oracle, P, B):
         assert max(_rel(ytc[b], yo[b]) for b in range(3)) < 1e-4
 
 
+@pytest.mark.parametrize("B", [3, 24])
+def test_tensor_core_m2p_partial_group(lspr, B):
+    # 320 panels = five target blocks: the second group of four holds one block, and the
+    # targets beyond the mesh get zero coefficients and no accumulation
+    v, t = I.icosphere(2, 10.0)
+    n = len(t)
+    lam = I.wavelengths(350, 420, B)
+    s = I.drude_eps(lam) / I.EPS_WATER
+    x = I.random_complex(2 * n, seed=41, batch=B)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        ctx.tree_build(0.6, 4, 16)
+        ytc = ctx.matvec(x, s, "tree_fp32")
+        assert ctx.device_errors() == 0
+        ctx.set_tensor_cores(False)
+        yfp = ctx.matvec(x, s, "tree_fp32")
+    for b in range(B):
+        assert _rel(ytc[b], yfp[b]) < 1e-5, b
+
+
 def test_tensor_core_solve(lspr):
     v, t = I.icosphere(3, 10.0)
     lam = I.wavelengths(360, 400, 12)
