@@ -7,9 +7,11 @@
 // its shape, so N is made as wide as the instruction allows: a work unit is a group of four
 // consecutive 64-target blocks (N = 256) and walks the sorted union of their M2P lists; the
 // coefficients of a block that did not accept a box are zero, so every block still receives
-// exactly the boxes its own acceptance test chose.  M = 64 channels (16 right-hand sides)
-// or 128 (32).  Both operands are split into TF32 high and low parts and the product is
-// taken as A_hi B_hi + A_hi B_lo + A_lo B_hi (3xTF32, FP32 accumulation in tensor memory).
+// exactly the boxes its own acceptance test chose.  Both operands are split into TF32 high
+// and low parts (FP32 accumulation in tensor memory): with 32 right-hand sides per unit
+// (128 channels) the product is A_hi B_hi + A_hi B_lo + A_lo B_hi (3xTF32); with 16 (64
+// channels) A_hi and A_lo are stacked into the 128 rows of one operand and two MMAs give all
+// four products.
 //
 // Two kernels per product:
 //   - tc_image_kernel writes, once per product, the split moments of every box in the
@@ -117,16 +119,19 @@ constexpr uint32_t idesc_tf32(int m, int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-// Stage geometry for order P and RC right-hand sides per unit: M = 4 RC accumulator rows.
-// With M = 64 row m sits in TMEM lane 32 (m / 16) + m % 16 (16 rows per lane quarter), with
-// M = 128 in lane m.
+// Stage geometry for order P and RC right-hand sides per unit (ROWS = 4 RC channels).
+// RC = 32: A_hi B_hi, A_hi B_lo and A_lo B_hi are three M = 128 MMAs into one accumulator.
+// RC = 16: A_hi and A_lo (adjacent in the stage) are the two halves of one M = 128 operand,
+// so two MMAs, [A_hi; A_lo] B_hi and [A_hi; A_lo] B_lo, give A_hi B in accumulator rows 0..63
+// and A_lo B in rows 64..127 (all four products); the epilogue adds both halves.  Row m of
+// an M = 128 accumulator sits in TMEM lane m.
 template <int P, int RC>
 struct TcShape {
     static constexpr int NT = n_terms(P);
     static constexpr int NKC = (NT + kKC - 1) / kKC;
     static constexpr int ROWS = 4 * RC;
-    static constexpr int RQ = ROWS / 4;                    // accumulator rows per lane quarter
-    static constexpr uint32_t IDESC = idesc_tf32(ROWS, kTcN);
+    static constexpr bool STACKED = ROWS == 64;           // hi and lo halves of one operand
+    static constexpr uint32_t IDESC = idesc_tf32(128, kTcN);
     static constexpr int A_CH = (ROWS / 8) * kChunkSBO;   // one split part of A per stage
     static constexpr int B_CH = (kTcN / 8) * kChunkSBO;   // one split part of B per stage
     static constexpr int STAGE = 2 * A_CH + 2 * B_CH;     // A_hi | A_lo | B_hi | B_lo
@@ -255,8 +260,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int rc = (int)(u - ii * nbc);
                 const int4 item = __ldg(items + ii);
                 bool ok = true;
+                int b_nx = item.y < item.z ? __ldg(&list[item.y].x) : 0;   // one box ahead
                 for (int l = item.y; l < item.z && ok; ++l) {
-                    const unsigned char *src = img + ((int64_t)__ldg(&list[l].x) * nrc + rc) * NKC * (2 * S::A_CH);
+                    const unsigned char *src = img + ((int64_t)b_nx * nrc + rc) * NKC * (2 * S::A_CH);
+                    if (l + 1 < item.z) b_nx = __ldg(&list[l + 1].x);
                     for (int kc = 0; kc < NKC; ++kc, ++seq) {
                         const int s = (int)(seq % NS);
                         if (seq >= NS &&
@@ -317,9 +324,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 const uint64_t dal = umma_desc(st + S::A_CH + off, 128, kChunkSBO);
                                 const uint64_t dbh = umma_desc(st + 2 * S::A_CH + off, 128, kChunkSBO);
                                 const uint64_t dbl = umma_desc(st + 2 * S::A_CH + S::B_CH + off, 128, kChunkSBO);
-                                tc_mma(d, dah, dbh, S::IDESC, (l == item.y && kc == 0 && ks == 0) ? 0u : 1u);
+                                const uint32_t on = (l == item.y && kc == 0 && ks == 0) ? 0u : 1u;
+                                tc_mma(d, dah, dbh, S::IDESC, on);
                                 tc_mma(d, dah, dbl, S::IDESC, 1u);
-                                tc_mma(d, dal, dbh, S::IDESC, 1u);
+                                if (!S::STACKED) tc_mma(d, dal, dbh, S::IDESC, 1u);
                             }
                             tc_commit(smem_addr(&empty_s[s]));
                         }
@@ -335,13 +343,63 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             drain_wait(smem_addr(&drain), 0u);
         }
     } else {
-        // ---- generators (one thread per target of the group), then the unit's epilogue
+        // ---- generators (one thread per target of the group); each unit's epilogue is
+        // taken once the first box of the next unit is staged, so that the MMAs keep going
         const int blk = tid / kTargetBlock;   // block of the group this thread's target is in
         int64_t seq = 0;
         int nu = 0;
-        for (int uc = 0;; ++uc) {
+        // the unit whose accumulator is still to be drained
+        bool pend = false;
+        int p_ab = 0, p_par = 0, p_b0 = 0, p_nb = 0;
+        int64_t p_tbase = 0;
+        // epilogue: warp w reads lane quarter w % 4 (accumulator rows 32 (w % 4)..) and columns
+        // 128 (w / 4)..; channel = row mod ROWS (both halves of a stacked accumulator are
+        // added); false: a wait ran out
+        auto drain_acc = [&]() -> bool {
+            const int qd = warp & 3, half = warp >> 2;
+            if (!warp_wait(smem_addr(&acc_full[p_ab]), (uint32_t)p_par, &abort_s)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if ((32 * qd) % S::ROWS < 4 * p_nb) {
+                const int m = (32 * qd + lane) % S::ROWS, j = m >> 2, cpt = m & 3;
+#pragma unroll 1
+                for (int c0 = 0; c0 < kTcN / 2; c0 += 32) {
+                    const int64_t tc = p_tbase + half * (kTcN / 2) + c0 + lane;   // this lane's column's target
+                    const int pc = tc < ntgt ? panel_of(tgt[tc].w) : -1;
+#pragma unroll
+                    for (int h16 = 0; h16 < 32; h16 += 16) {
+                        uint32_t v[16];
+                        const uint32_t addr = tmem + ((uint32_t)(32 * qd) << 16) +
+                                              (uint32_t)(p_ab * kTcN + half * (kTcN / 2) + c0 + h16);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                            "%14,%15}, [%16];"
+                            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                              "=r"(v[14]), "=r"(v[15])
+                            : "r"(addr));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int x = 0; x < 16; ++x) {
+                            const int p = __shfl_sync(0xffffffffu, pc, h16 + x);
+                            if (j < p_nb && p >= 0)
+                                atomicAdd(acc + 4 * ((int64_t)p * B + p_b0 + j) + cpt, (double)__uint_as_float(v[x]));
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) bar_arrive(smem_addr(&acc_empty[p_ab]));
+            pend = false;
+            return true;
+        };
+        bool ok = true;
+        for (int uc = 0; ok; ++uc) {
             const int slot = uc % kUnitRing;
-            if (!warp_wait(smem_addr(&ring_full[slot]), (uint32_t)(uc / kUnitRing) & 1u, &abort_s)) break;
+            if (!warp_wait(smem_addr(&ring_full[slot]), (uint32_t)(uc / kUnitRing) & 1u, &abort_s)) {
+                ok = false;
+                break;
+            }
             const int64_t u = ring[slot];
             if (u >= units) break;
             const int64_t ii = u / nbc;
@@ -351,13 +409,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int64_t ti = tbase + tid;
             const bool live = ti < ntgt;
             const float4 q = live ? tgt[ti] : tgt[0];
-            bool ok = true;
-            for (int l = item.y; l < item.z; ++l) {
-                const int2 e = __ldg(list + l);
+            // the next box's list entry and centre are loaded one box ahead
+            int2 e_nx = item.y < item.z ? __ldg(list + item.y) : make_int2(0, 0);
+            float4 c_nx = item.y < item.z ? box_c[e_nx.x] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int l = item.y; l < item.z && ok; ++l) {
+                const int2 e = e_nx;
+                const float4 c = c_nx;
+                if (l + 1 < item.z) {
+                    e_nx = __ldg(list + l + 1);
+                    c_nx = box_c[e_nx.x];
+                }
                 const bool on = live && ((e.y >> blk) & 1);   // uniform over the warp but for the tail
                 float a[NT];
                 if (on) {
-                    const float4 c = box_c[e.x];
                     constexpr MultiIndex<P> mi{};
                     const float R[3] = {q.x - c.x, q.y - c.y, q.z - c.z};
                     a[0] = rsq(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
@@ -405,51 +469,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     bar_arrive(smem_addr(&full_b[s]));
                     ++seq;
                 }
-                if (!ok) break;
+                if (ok && pend) ok = drain_acc();   // the previous unit, behind this unit's first box
             }
+            if (ok && pend) ok = drain_acc();       // the previous unit, if this one had no box
             if (!ok) break;
             if (item.y < item.z) {
-                // epilogue: warp w reads lane quarter w % 4 (rows RQ (w % 4)..) and columns
-                // 128 (w / 4).. of the unit's accumulator
-                const int ab = nu & 1, qd = warp & 3, half = warp >> 2;
-                if (!warp_wait(smem_addr(&acc_full[ab]), (uint32_t)(nu >> 1) & 1u, &abort_s)) break;
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                if (S::RQ * qd < 4 * nb) {
-                    const int m = S::RQ * qd + lane, j = lane < S::RQ ? m >> 2 : RC, cpt = m & 3;
-#pragma unroll 1
-                    for (int c0 = 0; c0 < kTcN / 2; c0 += 32) {
-                        const int64_t tc = tbase + half * (kTcN / 2) + c0 + lane;   // this lane's column's target
-                        const int pc = tc < ntgt ? panel_of(tgt[tc].w) : -1;
-#pragma unroll
-                        for (int h16 = 0; h16 < 32; h16 += 16) {
-                            uint32_t v[16];
-                            const uint32_t addr = tmem + ((uint32_t)(32 * qd) << 16) +
-                                                  (uint32_t)(ab * kTcN + half * (kTcN / 2) + c0 + h16);
-                            asm volatile(
-                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-                                "%14,%15}, [%16];"
-                                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                                  "=r"(v[14]), "=r"(v[15])
-                                : "r"(addr));
-                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                            for (int x = 0; x < 16; ++x) {
-                                const int p = __shfl_sync(0xffffffffu, pc, h16 + x);
-                                if (j < nb && p >= 0)
-                                    atomicAdd(acc + 4 * ((int64_t)p * B + b0 + j) + cpt, (double)__uint_as_float(v[x]));
-                            }
-                        }
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncwarp();
-                if (lane == 0) bar_arrive(smem_addr(&acc_empty[ab]));
+                pend = true;
+                p_ab = nu & 1;
+                p_par = (nu >> 1) & 1;
+                p_tbase = tbase;
+                p_b0 = b0;
+                p_nb = nb;
                 ++nu;
             }
             __syncwarp();
             if (lane == 0) bar_arrive(smem_addr(&ring_empty[slot]));
         }
+        if (ok && pend) drain_acc();
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
