@@ -108,6 +108,7 @@ L2_BYTES = 129 * 2 ** 20
 P2P_GEN_FLOPS = 16      # per (target, source) pair, generation of G and dG/dn (FMA = 2 flops)
 P2P_FP32_INSTR = 16     # FP32-pipe instructions per pair
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates, TF32 over BF16
 # DRAM bytes (read + write) per launch of the current kernels, from the ncu captures summarised in
 # profiles/{p2p,m2p,p2m}_fp32_sphere20480.md (dram__bytes.sum.per_second x gpu__time_duration.sum), keyed by
 # workload, kernel and treecode parameters (theta, P, Ncrit); None where no capture matches
@@ -207,6 +208,8 @@ def run_ours(args, wl, rank, world, local_rank):
     s_d = None if surf is None else torch.as_tensor(surf, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = lspr.Context(local_rank, stream.cuda_stream)
+    if args.no_tc:
+        ctx.set_tensor_cores(False)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     tune = None
     if wl.get("autotune") and wl["mode"].startswith("tree"):
@@ -353,10 +356,12 @@ def run_ours(args, wl, rank, world, local_rank):
         k = kernels["p2p"]
         k["algorithmic_tflops"] = pairs * p2p_flops(B) / (k["ms_per_launch"] * 1e-3) / 1e12
         k["pairs_per_launch"] = pairs
+    m2p_tc = B > 1 and fp32 and not args.no_tc   # the FP32 M2P of several right-hand sides runs on tcgen05
     if "m2p" in kernels:
         k = kernels["m2p"]
         k["algorithmic_tflops"] = info["n_m2p_pairs"] * kernel_targets(info) * m2p_flops(wl["P"], B) / (
             k["ms_per_launch"] * 1e-3) / 1e12
+        k["path"] = "tcgen05 (TF32 hi/lo split, FP32 accumulation)" if m2p_tc else "FP32 pipe"
     for name, flops in (("p2p_fp64", True), ("m2p_fp64", None), ("p2p_ff", True), ("m2p_ff", None)):
         if name in kernels:
             k = kernels[name]
@@ -367,6 +372,13 @@ def run_ours(args, wl, rank, world, local_rank):
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom, wl["theta"], wl["P"], wl["Ncrit"])),
                 "peak_note": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"}
+    elif dom == "m2p" and m2p_tc:
+        a = kernels[dom]["algorithmic_tflops"]
+        pk = peaks.get("bf16_tflops_sustained", 1755.8) * TF32_PER_BF16
+        roof = {"bound": "tensor", "kernel": dom, "achieved": round(a, 3), "peak": round(pk, 1), "unit": "TFLOP/s",
+                "frac": round(a / pk, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom, wl["theta"], wl["P"], wl["Ncrit"])),
+                "peak_note": "measured sustained bf16 x nominal TF32/BF16 rate (1.1/2.25); achieved counts the "
+                             "algorithmic contraction flops, not the split products"}
     elif dom in ("p2p", "m2p") and fp32:
         a = kernels[dom]["algorithmic_tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 3), "peak": round(peak_fp32, 2),
