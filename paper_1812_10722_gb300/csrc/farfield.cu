@@ -158,7 +158,10 @@ int launch_p2p(lspr_ctx *ctx, int prec, const int4 *items, int64_t nitems, doubl
         else p2p_launch<double, batch_chunk<double>(2)>(ctx, items, nitems, B, acc, st, counter);
     } else if (prec == PREC_FF) {
         if (B == 1) p2p_launch<ffloat, 1>(ctx, items, nitems, B, acc, st, counter);
-        else p2p_launch<ffloat, batch_chunk<ffloat>(2)>(ctx, items, nitems, B, acc, st, counter);
+        // float-float P2P: chunks of 2 right-hand sides (the accumulators of larger chunks cost more
+        // occupancy than regenerating G and dG/dn saves: 27.6 / 36.4 / 59.4 ms for chunks of 2 / 4 / 8
+        // at 16 right-hand sides, 20480 panels)
+        else p2p_launch<ffloat, 2>(ctx, items, nitems, B, acc, st, counter);
     } else {
         if (B == 1) p2p_launch<float, 1>(ctx, items, nitems, B, acc, st, counter);
         else p2p_launch<float, batch_chunk<float>(2)>(ctx, items, nitems, B, acc, st, counter);

@@ -179,8 +179,9 @@ int p2m_orders_ff(lspr_ctx *ctx, int B) {
 
 int m2p_orders_ff(lspr_ctx *ctx, double *acc, int *counter, int B) {
     if (ctx->tree.P < 1 || ctx->tree.P > kMaxP) return LSPR_E_ARG;
-    return B == 1 ? m2p_ff_launch<1>(ctx, acc, counter, B)
-                  : m2p_ff_launch<batch_chunk<ffloat>(2)>(ctx, acc, counter, B);
+    // chunks of 8 right-hand sides: the recurrence is shared by more of them (24.8 / 29.5 / 28.5 ms
+    // for chunks of 8 / 4 / 16 at 16 right-hand sides, 20480 panels, P = 7)
+    return B == 1 ? m2p_ff_launch<1>(ctx, acc, counter, B) : m2p_ff_launch<8>(ctx, acc, counter, B);
 }
 
 }  // namespace lspr
