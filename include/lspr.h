@@ -237,10 +237,12 @@ LSPR_API int lspr_get_timing(lspr_ctx *ctx, double *ms, int64_t *launches);
  * events cannot sit inside a graph loop.  If recording fails the context falls back
  * to host-driven cycles. */
 LSPR_API int lspr_set_graphs(lspr_ctx *ctx, int32_t enable);
-/* The FP32 M2P of several right-hand sides (B >= 2) runs on the tensor cores
- * (tcgen05, TF32 operands split into high and low parts, three products per term block,
- * FP32 accumulation in tensor memory) by default; lspr_set_tensor_cores(ctx, 0) selects the
- * FP32-pipe kernel of the same sums. */
+/* Tensor cores for the FP32 far field of several right-hand sides (B >= 2), as a mask:
+ * bit 0 (default on): the M2P contraction on tcgen05 (TF32 operands split into high and low
+ * parts, FP32 accumulation in tensor memory; about 2x the FP32-pipe kernel at 16 right-hand
+ * sides, 4x at 64); bit 1 (default off): the tree P2P on tcgen05 (same split; slower than the
+ * FP32-pipe kernel at 16 right-hand sides on GB300).  0 selects the FP32-pipe kernels of the
+ * same sums.  Bits above 1 are ignored.  LSPR_E_ARG: null context. */
 LSPR_API int lspr_set_tensor_cores(lspr_ctx *ctx, int32_t enable);
 /* Bounded waits inside device kernels that ran out since lspr_create (the tensor-core
  * M2P's pipeline barriers, about one second each): a kernel whose wait runs out stops its

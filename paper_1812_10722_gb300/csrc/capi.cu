@@ -221,7 +221,7 @@ int lspr_set_graphs(lspr_ctx *c, int32_t enable) {
 
 int lspr_set_tensor_cores(lspr_ctx *c, int32_t enable) {
     if (!c) return LSPR_E_ARG;
-    c->use_tensor_cores = enable != 0;
+    c->tensor_cores = enable & 3;
     return LSPR_OK;
 }
 

@@ -162,6 +162,8 @@ int launch_p2p(lspr_ctx *ctx, int prec, const int4 *items, int64_t nitems, doubl
         // occupancy than regenerating G and dG/dn saves: 27.6 / 36.4 / 59.4 ms for chunks of 2 / 4 / 8
         // at 16 right-hand sides, 20480 panels)
         else p2p_launch<ffloat, 2>(ctx, items, nitems, B, acc, st, counter);
+    } else if (B > 1 && (ctx->tensor_cores & 2) && items == ctx->tree.p2p_items.p) {
+        LSPR_TRY_ST(p2p_tc_launch(ctx, acc, st, counter, B));
     } else {
         if (B == 1) p2p_launch<float, 1>(ctx, items, nitems, B, acc, st, counter);
         else p2p_launch<float, batch_chunk<float>(2)>(ctx, items, nitems, B, acc, st, counter);

@@ -747,6 +747,8 @@ int p2m_orders_ff(lspr_ctx *ctx, int B);
 int m2p_orders_f32(lspr_ctx *ctx, double *acc, int *counter, int B);
 // tensor-core M2P (m2p_tc.cu): FP32 operands as 3xTF32, B >= 2; LSPR_E_STATE otherwise
 int m2p_tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B);
+// tensor-core P2P of the tree mode (p2p_tc.cu): FP32 weights as TF32 high/low parts, B >= 2
+int p2p_tc_launch(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B);
 int m2p_orders_f64(lspr_ctx *ctx, double *acc, int *counter, int B);
 int m2p_orders_ff(lspr_ctx *ctx, double *acc, int *counter, int B);
 

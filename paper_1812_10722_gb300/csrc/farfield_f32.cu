@@ -9,7 +9,7 @@ int p2m_orders_f32(lspr_ctx *ctx, int B) {
 }
 
 int m2p_orders_f32(lspr_ctx *ctx, double *acc, int *counter, int B) {
-    if (B > 1 && ctx->use_tensor_cores) {
+    if (B > 1 && (ctx->tensor_cores & 1)) {
         const int rc = m2p_tc_launch(ctx, acc, counter, B);
         if (rc != LSPR_E_STATE) return rc;
     }

@@ -42,6 +42,7 @@ constexpr double kInv4Pi = 0.079577471545947667884;   // 1 / (4 pi)
 constexpr int kTargetBlock = 64;                       // targets per interaction block (2 per lane)
 constexpr int kTcGroup = 4;        // target blocks per tensor-core M2P group (256 targets)
 constexpr int kTcGroupSeg = 32;    // boxes per tensor-core M2P work unit at most
+constexpr int kTcP2PSrc = 256;     // sources per tensor-core P2P work unit at most
 constexpr int kMaxP = 8;                               // highest Taylor order compiled
 constexpr int kMaxDepth = 10;                          // octree levels below the root (10 bits per axis)
 constexpr int kMaxNk = 32;
@@ -157,6 +158,11 @@ struct Tree {
     DArr<int4> tc_items;     // (group, list begin, list end, 0)
     DArr<int2> tc_list;      // (box id, block mask)
     int64_t n_tc_items = 0, n_tc_pairs = 0;
+    // the P2P source ranges of the same groups (tensor-core P2P): the union of the blocks'
+    // ranges cut at every range end, each piece with the mask of the blocks that sum it
+    DArr<int4> tcp_items;    // (group, interval begin, interval end, 0)
+    DArr<int4> tcp_ivl;      // (source begin, source end, block mask, 0)
+    int64_t n_tcp_items = 0, n_tcp_ivl = 0, n_tcp_sources = 0;
     DArr<int4> p2m_items;    // (leaf, source begin, source end, 0): leaves under an accepted box
     DArr<int> box_parent;    // parent box (-1 for the root)
     // moments [box][NT] x (Vre, Vim, Kre, Kim)
@@ -258,7 +264,7 @@ struct lspr_ctx {
     lspr::DArr<unsigned char> scratch[lspr::kScratchSlots];   // see lspr::Tmp
     // device-driven Arnoldi cycles (a CUDA graph per configuration, gmres_graph.cu)
     bool use_graphs = true;
-    bool use_tensor_cores = true;      // FP32 M2P of several right-hand sides on tcgen05
+    int tensor_cores = 1;              // tcgen05 for B >= 2 in FP32: bit 0 M2P, bit 1 P2P
     lspr::DArr<unsigned char> tc_img;  // split moments in tensor-core operand layout
     lspr::DArr<int> dev_err;           // bounded device waits that ran out (never reset)
     cudaStream_t gstream = nullptr;    // private recording/launch stream

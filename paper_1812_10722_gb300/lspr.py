@@ -292,9 +292,11 @@ class Context:
         """Arnoldi cycles as CUDA graph launches (default) or host-driven."""
         _check(lib().lspr_set_graphs(self._h, int(bool(enable))), "lspr_set_graphs", self._h)
 
-    def set_tensor_cores(self, enable: bool):
-        """FP32 M2P of several right-hand sides on the tensor cores (default) or the FP32 pipe."""
-        _check(lib().lspr_set_tensor_cores(self._h, int(bool(enable))), "lspr_set_tensor_cores", self._h)
+    def set_tensor_cores(self, enable):
+        """Tensor cores for the FP32 far field of several right-hand sides: True / 1 = the M2P
+        (default), 3 = M2P and P2P, False / 0 = the FP32-pipe kernels."""
+        mask = int(enable) if not isinstance(enable, bool) else int(enable)
+        _check(lib().lspr_set_tensor_cores(self._h, mask), "lspr_set_tensor_cores", self._h)
 
     def device_errors(self) -> int:
         """Bounded device waits that ran out since the context was created (0 when healthy)."""

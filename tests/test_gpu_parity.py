@@ -546,12 +546,15 @@ def test_tensor_core_m2p_matches_fp32_pipe(lspr, oracle, P, B):
         ctx.tree_build(0.5, P, 32)
         ytc = ctx.matvec(x, s, "tree_fp32")
         ytc2 = ctx.matvec(x, s, "tree_fp32")
+        ctx.set_tensor_cores(3)   # the P2P on the tensor cores too
+        ytp = ctx.matvec(x, s, "tree_fp32")
         assert ctx.device_errors() == 0
         ctx.set_tensor_cores(False)
         yfp = ctx.matvec(x, s, "tree_fp32")
         y64 = ctx.matvec(x, s, "tree_fp64")
     for b in range(B):
         assert _rel(ytc2[b], ytc[b]) < 1e-6, b
+        assert _rel(ytp[b], yfp[b]) < 1e-5, b
         assert _rel(ytc[b], y64[b]) < 1e-5, b
         assert _rel(ytc[b], yfp[b]) < 1e-5, b
     if P == 6:
@@ -562,7 +565,8 @@ def test_tensor_core_m2p_matches_fp32_pipe(lspr, oracle, P, B):
 @pytest.mark.parametrize("B", [3, 24])
 def test_tensor_core_m2p_partial_group(lspr, B):
     # 320 panels = five target blocks: the second group of four holds one block, and the
-    # targets beyond the mesh get zero coefficients and no accumulation
+    # targets beyond the mesh get zero coefficients (M2P) and kernel values (P2P) and no
+    # accumulation
     v, t = I.icosphere(2, 10.0)
     n = len(t)
     lam = I.wavelengths(350, 420, B)
@@ -572,11 +576,14 @@ def test_tensor_core_m2p_partial_group(lspr, B):
         ctx.mesh_upload(v, t)
         ctx.tree_build(0.6, 4, 16)
         ytc = ctx.matvec(x, s, "tree_fp32")
+        ctx.set_tensor_cores(3)
+        ytp = ctx.matvec(x, s, "tree_fp32")
         assert ctx.device_errors() == 0
         ctx.set_tensor_cores(False)
         yfp = ctx.matvec(x, s, "tree_fp32")
     for b in range(B):
         assert _rel(ytc[b], yfp[b]) < 1e-5, b
+        assert _rel(ytp[b], yfp[b]) < 1e-5, b
 
 
 def test_tensor_core_solve(lspr):
