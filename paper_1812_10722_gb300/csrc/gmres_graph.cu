@@ -593,7 +593,7 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
                             (uint64_t)tr.NT, (uint64_t)tr.nboxes, (uint64_t)tr.n_p2p_items,
                             (uint64_t)tr.n_m2p_items, (uint64_t)tr.n_p2m_items, (uint64_t)ctx->direct.n,
                             (uint64_t)(uintptr_t)ctx->gm_V.p, (uint64_t)ctx->num_sms, (uint64_t)me.S,
-                            (uint64_t)ctx->tensor_cores, 0, 0};
+                            (uint64_t)ctx->tensor_cores, (uint64_t)tr.n_tc_items, (uint64_t)tr.n_tcp_items};
         GraphCache *gc = nullptr;
         for (GraphCache &c : ctx->gcache)
             if (c.exec && std::equal(key, key + 24, c.key)) gc = &c;

@@ -163,6 +163,7 @@ struct Tree {
     DArr<int4> tcp_items;    // (group, interval begin, interval end, 0)
     DArr<int4> tcp_ivl;      // (source begin, source end, block mask, 0)
     int64_t n_tcp_items = 0, n_tcp_ivl = 0, n_tcp_sources = 0;
+    bool tc_built = false, tcp_built = false;   // the group lists above match the tree
     DArr<int4> p2m_items;    // (leaf, source begin, source end, 0): leaves under an accepted box
     DArr<int> box_parent;    // parent box (-1 for the root)
     // moments [box][NT] x (Vre, Vim, Kre, Kim)
@@ -316,6 +317,7 @@ int workorder_natural(lspr_ctx *ctx);
 
 // ------------------------------------------------------------ tree.cu
 int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit);
+int tree_tc_lists(lspr_ctx *ctx, bool p2p);
 // stable LSD radix sort of (keys, vals) on the context's stream (bits: key width)
 int radix_sort(lspr_ctx *ctx, unsigned *keys, int *vals, unsigned *ktmp, int *vals_tmp, int64_t n, int bits, int *hist,
                int *offs);

@@ -449,6 +449,7 @@ int tc_launch_p(lspr_ctx *ctx, double *acc, int *counter, int B) {
 
 // FP32 M2P of B >= 2 right-hand sides on the tensor cores; LSPR_E_STATE: not applicable
 int m2p_tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
+    if (!ctx->tree.tc_built) LSPR_TRY_ST(tree_tc_lists(ctx, false));
     switch (ctx->tree.P) {
     case 1: return tc_launch_p<1>(ctx, acc, counter, B);
     case 2: return tc_launch_p<2>(ctx, acc, counter, B);

@@ -358,6 +358,7 @@ int tc_p2p(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B) {
 
 // FP32 tree P2P of B >= 2 right-hand sides on the tensor cores
 int p2p_tc_launch(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B) {
+    if (!ctx->tree.tcp_built) LSPR_TRY_ST(tree_tc_lists(ctx, true));
     return B <= 16 ? tc_p2p<16>(ctx, acc, st, counter, B) : tc_p2p<32>(ctx, acc, st, counter, B);
 }
 

@@ -662,6 +662,10 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
     const bool tree = mode_tree(mode);
     const double2 eout = make_double2(eps_out_re, eps_out_im);
     const int S = me.S;   // eps_in is [B][S]
+    // the tensor-core far field's group lists before any product (a recorded Arnoldi cycle
+    // launches the kernels without the host code that would form them)
+    if (tree && mode == LSPR_TREE_FP32 && B * S > 1 && (ctx->tensor_cores & 3))
+        LSPR_TRY_ST(tree_tc_lists(ctx, (ctx->tensor_cores & 2) != 0));
     LSPR_TRY(ctx, ctx->gm_eps.ensure((size_t)B * S));
     LSPR_TRY(ctx, ctx->gm_s.ensure((size_t)B * S));
     LSPR_TRY(ctx, ctx->gm_b.ensure((size_t)B * n2));
