@@ -249,6 +249,12 @@ LSPR_API int lspr_set_tensor_cores(lspr_ctx *ctx, int32_t enable);
  * block, frees its resources and counts here, and the product it computed is incomplete.
  * Synchronises the context's stream.  LSPR_E_ARG: null pointer. */
 LSPR_API int lspr_device_errors(lspr_ctx *ctx, int32_t *count);
+/* Diagnostic of that failure path: one device thread waits, with the kernels' bounded wait, on
+ * a barrier that nothing arrives on.  result[0] = 1 if the wait reported success (a fault of
+ * the mechanism), result[1] = the abort flag it raised (1 expected), result[2] = milliseconds
+ * it waited (about 1000).  Synchronises the context's stream; the context stays usable.
+ * result: 3 int32 on the host.  LSPR_E_ARG: null pointer. */
+LSPR_API int lspr_selftest_wait_timeout(lspr_ctx *ctx, int32_t *result);
 /* Graph cycles launched and graphs recorded since lspr_create (either pointer may be null). */
 LSPR_API int lspr_graph_stats(lspr_ctx *ctx, int64_t *cycles, int64_t *recordings);
 

@@ -225,6 +225,11 @@ int lspr_set_tensor_cores(lspr_ctx *c, int32_t enable) {
     return LSPR_OK;
 }
 
+int lspr_selftest_wait_timeout(lspr_ctx *c, int32_t *result) {
+    if (!c || !result) return LSPR_E_ARG;
+    return lspr::selftest_wait_timeout(c, result);
+}
+
 int lspr_device_errors(lspr_ctx *c, int32_t *count) {
     if (!c || !count) return LSPR_E_ARG;
     *count = 0;

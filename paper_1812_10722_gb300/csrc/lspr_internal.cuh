@@ -318,6 +318,7 @@ int workorder_natural(lspr_ctx *ctx);
 // ------------------------------------------------------------ tree.cu
 int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit);
 int tree_tc_lists(lspr_ctx *ctx, bool p2p);
+int selftest_wait_timeout(lspr_ctx *ctx, int32_t *result);
 // stable LSD radix sort of (keys, vals) on the context's stream (bits: key width)
 int radix_sort(lspr_ctx *ctx, unsigned *keys, int *vals, unsigned *ktmp, int *vals_tmp, int64_t n, int bits, int *hist,
                int *offs);

@@ -88,10 +88,11 @@ def lib():
                                         ctypes.POINTER(TuneResult)]
             L.lspr_graph_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
             L.lspr_device_errors.argtypes = [_vp, ctypes.POINTER(_i32)]
+            L.lspr_selftest_wait_timeout.argtypes = [_vp, ctypes.POINTER(_i32)]
             for f in ("lspr_create", "lspr_destroy", "lspr_mesh_upload", "lspr_tree_build", "lspr_matvec",
                       "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing", "lspr_launch_count",
                       "lspr_set_graphs", "lspr_graph_stats", "lspr_autotune", "lspr_set_tensor_cores",
-                      "lspr_device_errors"):
+                      "lspr_device_errors", "lspr_selftest_wait_timeout"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -303,6 +304,12 @@ class Context:
         n = ctypes.c_int32(0)
         _check(lib().lspr_device_errors(self._h, ctypes.byref(n)), "lspr_device_errors", self._h)
         return n.value
+
+    def selftest_wait_timeout(self) -> dict:
+        """Runs one bounded device wait that cannot complete: {"succeeded", "abort", "ms"}."""
+        r = (ctypes.c_int32 * 3)()
+        _check(lib().lspr_selftest_wait_timeout(self._h, r), "lspr_selftest_wait_timeout", self._h)
+        return {"succeeded": r[0], "abort": r[1], "ms": r[2]}
 
     def graph_stats(self) -> dict:
         c, r = ctypes.c_int64(0), ctypes.c_int64(0)

@@ -586,6 +586,27 @@ def test_tensor_core_m2p_partial_group(lspr, B):
         assert _rel(ytp[b], yfp[b]) < 1e-5, b
 
 
+def test_bounded_wait_gives_up(lspr):
+    # the pipeline waits of the tensor-core kernels end after about a second when nothing
+    # arrives, raise the abort flag, and leave the context usable (a product still matches)
+    v, t = I.icosphere(2, 10.0)
+    n = len(t)
+    s = I.drude_eps(np.array([370.0, 390.0])) / I.EPS_WATER
+    x = I.random_complex(2 * n, seed=43, batch=2)
+    with lspr.Context(0) as ctx:
+        r = ctx.selftest_wait_timeout()
+        assert r["succeeded"] == 0 and r["abort"] == 1
+        assert 900 <= r["ms"] <= 5000
+        ctx.mesh_upload(v, t)
+        ctx.tree_build(0.6, 4, 16)
+        ytc = ctx.matvec(x, s, "tree_fp32")
+        assert ctx.device_errors() == 0
+        ctx.set_tensor_cores(False)
+        yfp = ctx.matvec(x, s, "tree_fp32")
+    for b in range(2):
+        assert _rel(ytc[b], yfp[b]) < 1e-5, b
+
+
 def test_tensor_core_solve(lspr):
     v, t = I.icosphere(3, 10.0)
     lam = I.wavelengths(360, 400, 12)
