@@ -20,8 +20,9 @@
 //   - m2p_tc_kernel is persistent and warp-specialised.  The terms of each (unit, box) are
 //     cut into chunks of 16, one pipeline stage each (a ring of NS stages in shared memory):
 //       warps 0-7 (one thread per target of the group) compute the coefficients a_k by the
-//         recurrence of m2p_kernel and write the split B part of each stage; at the end of a
-//         unit they drain its accumulator (tcgen05.ld) into the FP64 accumulators;
+//         recurrence of m2p_kernel and write the split B part of each stage; they drain each
+//         unit's accumulator (tcgen05.ld) into the FP64 accumulators once the next unit's
+//         first box is staged, so that the MMAs keep going meanwhile;
 //       warp 8 (one lane) fetches work units, publishes them in a small ring, and streams
 //         each stage's A part with cp.async.bulk;
 //       warp 9 (one lane) issues the MMAs of each stage once both parts are in, commits to
