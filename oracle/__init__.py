@@ -88,8 +88,10 @@ def lib():
             L.oracle_gmres_multi.restype = _i
             L.oracle_dipole_surface.argtypes = [_dp, _ip, _ip, _i64, _i, _dp, _d, _d, _d, _d, _dp, _dp]
             L.oracle_solve_multi.argtypes = [_dp, _ip, _ip, _i64, _i, _i, _i, _d, _i, _dp, _d, _d, _dp, _dp, _d,
-                                             _i, _i, _dp, _dp, _intp, _i]
+                                             _i, _i, _dp, _dp, _intp, _i, _i64, _dp, _ip]
             L.oracle_solve_multi.restype = _i
+            L.oracle_rhs_charges.argtypes = [_dp, _ip, _ip, _i64, _i, _i, _dp, _i64, _dp, _ip, _dp]
+            L.oracle_rhs_charges.restype = _i
             _lib = L
     return _lib
 
@@ -335,12 +337,42 @@ def dipole_surface(verts, tris, surf, x, surface, eps_in, eps_out, E0=(0.0, 0.0,
     return p
 
 
-def solve_multi(verts, tris, surf, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0), tol=1e-8, restart=100,
-                maxiter=1000, K=4, K_fine=19, threshold=0.5, nthreads=0):
-    """Several surfaces: RHS + GMRES + dipole and sigma_ext of surface 0 per wavelength;
-    eps_in [B,S]; returns (dipoles [B,3], sigma [B], iters [B], n_bad)."""
+def _charges(charges, charge_surf):
+    if charges is None:
+        return 0, None, None
+    q = np.ascontiguousarray(np.asarray(charges, np.float64).reshape(-1, 4))
+    qs = np.ascontiguousarray(np.asarray(charge_surf, np.int32).reshape(-1))
+    if qs.shape[0] != q.shape[0]:
+        raise ValueError("one surface index per charge")
+    return q.shape[0], q, qs
+
+
+def rhs_charges(verts, tris, surf, eps_in, charges, charge_surf):
+    """Coulomb term of point charges inside surfaces on their interior rows, [B,2n]: charge
+    (x, y, z, q) inside surface t adds q / (4 pi eps_t |c_i - r|) to row i of every panel of t
+    (Eqs. integral_eq_lspr_system, matrix_multi).  eps_in [S] or [B,S]."""
     v, t, n = _mesh(verts, tris)
     sf, S = _surf(surf, n)
+    e = _c128(np.asarray(eps_in, np.complex128).reshape(-1, S))
+    B = e.shape[0]
+    nq, q, qs = _charges(charges, charge_surf)
+    b = np.zeros((B, 2 * n), np.complex128)
+    if nq == 0:
+        return b
+    rc = lib().oracle_rhs_charges(_ptr(v), _ptr(t, _ip), _ptr(sf, _ip), n, S, B, _ptr(e.view(np.float64)), nq,
+                                  _ptr(q), _ptr(qs, _ip), _ptr(b.view(np.float64)))
+    if rc:
+        raise RuntimeError(f"oracle_rhs_charges failed ({rc})")
+    return b
+
+
+def solve_multi(verts, tris, surf, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0), tol=1e-8, restart=100,
+                maxiter=1000, K=4, K_fine=19, threshold=0.5, nthreads=0, charges=None, charge_surf=None):
+    """Several surfaces: RHS (+ point charges, rhs_charges) + GMRES + dipole and sigma_ext of
+    surface 0 per wavelength; eps_in [B,S]; returns (dipoles [B,3], sigma [B], iters [B], n_bad)."""
+    v, t, n = _mesh(verts, tris)
+    sf, S = _surf(surf, n)
+    nq, q, qs = _charges(charges, charge_surf)
     e = _c128(np.asarray(eps_in, np.complex128).reshape(-1, S))
     lam = _f64(np.atleast_1d(lambda_nm))
     B = e.shape[0]
@@ -351,5 +383,5 @@ def solve_multi(verts, tris, surf, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0
     bad = lib().oracle_solve_multi(_ptr(v), _ptr(t, _ip), _ptr(sf, _ip), n, S, K, K_fine, threshold, B,
                                    _ptr(e.view(np.float64)), e2.real, e2.imag, _ptr(_f64(E0)), _ptr(lam), tol,
                                    restart, maxiter, _ptr(dip.view(np.float64)), _ptr(sig), its.ctypes.data_as(_intp),
-                                   nthreads)
+                                   nthreads, nq, _ptr(q) if nq else None, _ptr(qs, _ip) if nq else None)
     return dip, sig, its, bad

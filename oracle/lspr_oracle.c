@@ -21,6 +21,8 @@
  *   - the operator of several closed interfaces in one host (a particle
  *     and analyte surfaces), its right-hand side and the dipole of one
  *     surface                                                    [Eqs. integral_eq_lspr_system, matrix_multi]
+ *   - the Coulomb term of point charges inside a surface on its interior
+ *     row                                                        [Eqs. integral_eq_lspr_system, matrix_multi]
  *   - complex GMRES (restarted, right block-Jacobi preconditioner) and a
  *     dense complex LU with partial pivoting for small systems  [Sec. II.D]
  *   - the dipole moment from boundary data                      [Eq. dipole_def_gauss_i_final]
@@ -492,6 +494,35 @@ int oracle_rhs_multi(const double *verts, const int32_t *tris, const int32_t *su
     return 0;
 }
 
+/* Point charges inside the surfaces [Eqs. integral_eq_lspr_system, matrix_multi: the interior
+ * row of an analyte surface Gamma_2 carries (1 / (4 pi eps_3)) sum_k q_k / |r - r_k|]: charge k
+ * (q_k at r_k, inside surface t_k) adds q_k / (4 pi eps_t |c_i - r_k|) to the interior (top) row
+ * of every panel i of surface t_k, eps_t that surface's permittivity of the wavelength.
+ * charges: [nq][4] (x, y, z, q); surf_q: [nq]; eps_in: [B][S] complex; b: [B][2n], added to. */
+int oracle_rhs_charges(const double *verts, const int32_t *tris, const int32_t *surf, int64_t n, int S, int B,
+                       const double *eps_in, int64_t nq, const double *charges, const int32_t *surf_q,
+                       double *bout)
+{
+    cplx *b = (cplx *)bout;
+    const cplx *e1 = (const cplx *)eps_in;
+    for (int64_t k = 0; k < nq; ++k)
+        if (surf_q[k] < 0 || surf_q[k] >= S) return 2;
+    for (int64_t i = 0; i < n; ++i) {
+        panel_t p;
+        make_panel(verts, tris, i, &p);
+        const int t = surf ? surf[i] : 0;
+        double phi = 0.0;
+        for (int64_t k = 0; k < nq; ++k) {
+            if (surf_q[k] != t) continue;
+            const double dx = p.c[0] - charges[4 * k], dy = p.c[1] - charges[4 * k + 1],
+                         dz = p.c[2] - charges[4 * k + 2];
+            phi += charges[4 * k + 3] / sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        for (int bb = 0; bb < B; ++bb) b[(size_t)bb * 2 * n + i] += phi / (4.0 * M_PI * e1[(size_t)bb * S + t]);
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Dense complex LU with partial pivoting (row-major A[n][n], solves in place) */
 /* ------------------------------------------------------------------------- */
@@ -801,7 +832,8 @@ int oracle_solve(const double *verts, const int32_t *tris, int64_t n, int K, int
 int oracle_solve_multi(const double *verts, const int32_t *tris, const int32_t *surf, int64_t n, int S, int K,
                        int Kf, double threshold, int B, const double *eps_in, double eps_out_re,
                        double eps_out_im, const double *E0, const double *lambda_nm, double tol, int restart,
-                       int maxiter, double *dip_out, double *sigma_out, int *iters_out, int nthreads)
+                       int maxiter, double *dip_out, double *sigma_out, int *iters_out, int nthreads,
+                       int64_t nq, const double *charges, const int32_t *surf_q)
 {
     const int64_t N2 = 2 * n;
     double *b = (double *)malloc(sizeof(double) * 2 * (size_t)N2);
@@ -813,6 +845,10 @@ int oracle_solve_multi(const double *verts, const int32_t *tris, const int32_t *
         const double *e1 = eps_in + 2 * (size_t)S * bb;
         oracle_rhs_multi(verts, tris, surf, n, S, K, Kf, threshold, 1, e1, eps_out_re, eps_out_im, E0, b,
                          nthreads);
+        if (nq > 0 && oracle_rhs_charges(verts, tris, surf, n, S, 1, e1, nq, charges, surf_q, b)) {
+            bad = B;
+            break;
+        }
         for (int t = 0; t < S; ++t) {
             cplx st = (e1[2 * t] + I * e1[2 * t + 1]) / e2;
             s[2 * t] = creal(st);
