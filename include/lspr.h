@@ -249,6 +249,15 @@ LSPR_API int lspr_set_tensor_cores(lspr_ctx *ctx, int32_t enable);
  * block, frees its resources and counts here, and the product it computed is incomplete.
  * Synchronises the context's stream.  LSPR_E_ARG: null pointer. */
 LSPR_API int lspr_device_errors(lspr_ctx *ctx, int32_t *count);
+/* Point charges inside the surfaces (Eqs. integral_eq_lspr_system, matrix_multi: the interior
+ * row of an analyte surface carries (1 / (4 pi eps_t)) sum_k q_k / |r - r_k|, r the collocation
+ * point, eps_t the surface's permittivity of each wavelength in lspr_solve).  charges: [nq][4]
+ * host doubles (x, y, z in nm, q in the units of the incident field E0 times nm^2, so that both
+ * right-hand-side terms are potentials); surf_q: [nq] host int32, the surface holding each
+ * charge.  The library copies them; they apply to every later lspr_solve until replaced, and
+ * nq = 0 removes them.  A surface index >= the mesh's surface count makes lspr_solve return
+ * LSPR_E_ARG.  LSPR_E_ARG: null context, nq < 0, null arrays with nq > 0, negative index. */
+LSPR_API int lspr_set_charges(lspr_ctx *ctx, const double *charges, int64_t nq, const int32_t *surf_q);
 /* Diagnostic of that failure path: one device thread waits, with the kernels' bounded wait, on
  * a barrier that nothing arrives on.  result[0] = 1 if the wait reported success (a fault of
  * the mechanism), result[1] = the abort flag it raised (1 expected), result[2] = milliseconds

@@ -1,9 +1,11 @@
 // C ABI entry points (declared in include/lspr.h).  Argument checking, context
 // ownership and status mapping live here; the numerical work is in mesh.cu,
 // tree.cu, farfield.cu and solve.cu.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <new>
+#include <vector>
 
 #include "lspr_internal.cuh"
 
@@ -222,6 +224,29 @@ int lspr_set_graphs(lspr_ctx *c, int32_t enable) {
 int lspr_set_tensor_cores(lspr_ctx *c, int32_t enable) {
     if (!c) return LSPR_E_ARG;
     c->tensor_cores = enable & 3;
+    return LSPR_OK;
+}
+
+int lspr_set_charges(lspr_ctx *c, const double *charges, int64_t nq, const int32_t *surf_q) {
+    if (!c || nq < 0 || (nq > 0 && (!charges || !surf_q))) return LSPR_E_ARG;
+    int mx = -1;
+    for (int64_t k = 0; k < nq; ++k) {
+        if (surf_q[k] < 0) return LSPR_E_ARG;
+        mx = std::max(mx, (int)surf_q[k]);
+    }
+    c->nq = 0;
+    c->max_charge_surf = -1;
+    if (nq == 0) return LSPR_OK;
+    std::vector<dbl4> h((size_t)nq);
+    for (int64_t k = 0; k < nq; ++k)
+        h[k] = make_dbl4(charges[4 * k], charges[4 * k + 1], charges[4 * k + 2], charges[4 * k + 3]);
+    LSPR_TRY(c, c->charges.ensure(nq));
+    LSPR_TRY(c, c->charge_surf.ensure(nq));
+    LSPR_TRY(c, cudaMemcpyAsync(c->charges.p, h.data(), sizeof(dbl4) * nq, cudaMemcpyHostToDevice, c->stream));
+    LSPR_TRY(c, cudaMemcpyAsync(c->charge_surf.p, surf_q, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, c->stream));
+    LSPR_TRY(c, cudaStreamSynchronize(c->stream));
+    c->nq = nq;
+    c->max_charge_surf = mx;
     return LSPR_OK;
 }
 

@@ -268,6 +268,12 @@ struct lspr_ctx {
     int tensor_cores = 1;              // tcgen05 for B >= 2 in FP32: bit 0 M2P, bit 1 P2P
     lspr::DArr<unsigned char> tc_img;  // split moments in tensor-core operand layout
     lspr::DArr<int> dev_err;           // bounded device waits that ran out (never reset)
+    // point charges inside the surfaces (lspr_set_charges): (x, y, z, q) and the surface of each
+    lspr::DArr<dbl4> charges;
+    lspr::DArr<int> charge_surf;
+    int64_t nq = 0;
+    int max_charge_surf = -1;
+    lspr::DArr<double> coul;           // [N] sum_k q_k / |c_i - r_k| over the charges of i's surface
     cudaStream_t gstream = nullptr;    // private recording/launch stream
     cudaEvent_t ev_g0 = nullptr, ev_g1 = nullptr;
     lspr::GraphCache gcache[2];

@@ -439,6 +439,50 @@ __global__ void rhs_kernel(int B, int S, int64_t N, const double2 *__restrict__ 
     rhs[(int64_t)b * 2 * N + N + i] = acc;
 }
 
+// Point charges inside the surfaces (Eqs. integral_eq_lspr_system, matrix_multi: the interior
+// row of a surface holding charges carries (1 / (4 pi eps_t)) sum_k q_k / |r - r_k|).
+// coul[i] = sum over the charges of panel i's surface of q_k / |c_i - r_k| (FP64; the charges
+// pass through shared memory in tiles of the block size).
+constexpr int kCoulThreads = 128;
+__global__ void __launch_bounds__(kCoulThreads)
+    coulomb_kernel(int64_t N, int64_t nq, const double *__restrict__ cx, const double *__restrict__ cy,
+                   const double *__restrict__ cz, const int *__restrict__ surf, const dbl4 *__restrict__ charges,
+                   const int *__restrict__ qsurf, double *__restrict__ coul) {
+    __shared__ dbl4 sq[kCoulThreads];
+    __shared__ int ss[kCoulThreads];
+    const int64_t i = blockIdx.x * (int64_t)kCoulThreads + threadIdx.x;
+    const bool live = i < N;
+    const double x = live ? cx[i] : 0.0, y = live ? cy[i] : 0.0, z = live ? cz[i] : 0.0;
+    const int t = live ? surf[i] : -1;
+    double phi = 0.0;
+    for (int64_t k0 = 0; k0 < nq; k0 += kCoulThreads) {
+        __syncthreads();
+        if (k0 + threadIdx.x < nq) {
+            sq[threadIdx.x] = charges[k0 + threadIdx.x];
+            ss[threadIdx.x] = qsurf[k0 + threadIdx.x];
+        }
+        __syncthreads();
+        const int cnt = (int)min((int64_t)kCoulThreads, nq - k0);
+        for (int k = 0; k < cnt; ++k) {
+            if (ss[k] != t) continue;
+            const double dx = x - sq[k].x, dy = y - sq[k].y, dz = z - sq[k].z;
+            phi += sq[k].w / sqrt(dx * dx + dy * dy + dz * dz);
+        }
+    }
+    if (live) coul[i] = phi;
+}
+
+// rhs top row of panel i += coul[i] / (4 pi eps_t), eps_t = eps_in[b][surf[i]]
+__global__ void charge_rhs_kernel(int B, int S, int64_t N, const double *__restrict__ coul,
+                                  const int *__restrict__ surf, const double2 *eps_in, double2 *rhs) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (i >= N) return;
+    const double2 e = eps_in[b * S + surf[i]];
+    const double2 f = cdiv(make_double2(coul[i] / (4.0 * M_PI), 0.0), e);
+    rhs[(int64_t)b * 2 * N + i] = cadd(rhs[(int64_t)b * 2 * N + i], f);
+}
+
 // ---------------------------------------------------------- dipole + sigma
 // dipole of surface 0 (the particle; eps_in [B][S], its permittivity eps_in[b][0])
 __global__ void dipole_partial_kernel(int B, int S, int64_t N, const int *__restrict__ surf,
@@ -691,6 +735,20 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
     LSPR_TRY_ST(layer_potentials(ctx, mode, xin, Vinc, Vinc + (size_t)S * N));
     ++ctx->n_launches;
     rhs_kernel<<<dim3(grid_for(N, 256), B), 256, 0, st>>>(B, S, N, Vinc, ctx->gm_eps.p, eout, ctx->gm_b.p);
+    if (ctx->nq > 0) {   // point charges on their surfaces' interior rows
+        if (ctx->max_charge_surf >= S) {
+            ctx->last_error = "a charge's surface index is not a surface of the mesh";
+            return LSPR_E_ARG;
+        }
+        LSPR_TRY(ctx, ctx->coul.ensure(N));
+        ++ctx->n_launches;
+        coulomb_kernel<<<grid_for(N, kCoulThreads), kCoulThreads, 0, st>>>(N, ctx->nq, me.cx.p, me.cy.p, me.cz.p,
+                                                                            me.surf.p, ctx->charges.p,
+                                                                            ctx->charge_surf.p, ctx->coul.p);
+        ++ctx->n_launches;
+        charge_rhs_kernel<<<dim3(grid_for(N, 256), B), 256, 0, st>>>(B, S, N, ctx->coul.p, me.surf.p, ctx->gm_eps.p,
+                                                                     ctx->gm_b.p);
+    }
     LSPR_TRY(ctx, cudaMemsetAsync(ctx->gm_x.p, 0, sizeof(double2) * B * n2, st));
     // ||b||
     const int nch = (int)((n2 + kChunk - 1) / kChunk);

@@ -89,10 +89,11 @@ def lib():
             L.lspr_graph_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
             L.lspr_device_errors.argtypes = [_vp, ctypes.POINTER(_i32)]
             L.lspr_selftest_wait_timeout.argtypes = [_vp, ctypes.POINTER(_i32)]
+            L.lspr_set_charges.argtypes = [_vp, _vp, _i64, _vp]
             for f in ("lspr_create", "lspr_destroy", "lspr_mesh_upload", "lspr_tree_build", "lspr_matvec",
                       "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing", "lspr_launch_count",
                       "lspr_set_graphs", "lspr_graph_stats", "lspr_autotune", "lspr_set_tensor_cores",
-                      "lspr_device_errors", "lspr_selftest_wait_timeout"):
+                      "lspr_device_errors", "lspr_selftest_wait_timeout", "lspr_set_charges"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -304,6 +305,18 @@ class Context:
         n = ctypes.c_int32(0)
         _check(lib().lspr_device_errors(self._h, ctypes.byref(n)), "lspr_device_errors", self._h)
         return n.value
+
+    def set_charges(self, charges=None, surf=None):
+        """Point charges (x, y, z, q) inside the given surfaces for later solves (None: remove)."""
+        if charges is None:
+            _check(lib().lspr_set_charges(self._h, None, 0, None), "lspr_set_charges", self._h)
+            return
+        q = np.ascontiguousarray(np.asarray(charges, np.float64).reshape(-1, 4))
+        sq = np.ascontiguousarray(np.asarray(surf, np.int32).reshape(-1))
+        if sq.shape[0] != q.shape[0]:
+            raise ValueError("one surface index per charge")
+        _check(lib().lspr_set_charges(self._h, q.ctypes.data, q.shape[0], sq.ctypes.data), "lspr_set_charges",
+               self._h)
 
     def selftest_wait_timeout(self) -> dict:
         """Runs one bounded device wait that cannot complete: {"succeeded", "abort", "ms"}."""

@@ -486,6 +486,53 @@ def test_multi_surface_solve(lspr, oracle, graphs):
     assert abs(r1.sigma_ext[0] - rt.sigma_ext[1]) / rt.sigma_ext[1] < 1e-6
 
 
+def test_point_charges_solve(lspr, oracle):
+    # charges inside the analytes add their Coulomb potential over 4 pi eps_t to the analytes'
+    # interior rows (Eqs. integral_eq_lspr_system, matrix_multi); GPU against the oracle
+    v, t, surf = _sensor_small()
+    c = v[t].mean(axis=1)
+    q1, q2 = c[surf == 1].mean(axis=0), c[surf == 2].mean(axis=0)
+    charges = np.array([[*q1, 800.0], [*(q1 + [0.3, -0.2, 0.1]), -500.0], [*(q2 + [0.0, 0.2, 0.0]), 1200.0]])
+    csurf = np.array([1, 1, 2], np.int32)
+    lam = np.array([370.0, 390.0])
+    eps = np.stack([I.drude_eps(lam), np.full(2, 2.25), np.full(2, 2.0 + 0.05j)], axis=1)
+    dref, sref, _, bad = oracle.solve_multi(v, t, surf, eps, I.EPS_WATER, lam, tol=1e-10, charges=charges,
+                                            charge_surf=csurf)
+    d0, _, _, bad0 = oracle.solve_multi(v, t, surf, eps, I.EPS_WATER, lam, tol=1e-10)
+    assert bad == 0 and bad0 == 0
+    assert np.max(np.abs(dref - d0)) > 1e-3 * np.max(np.abs(d0))   # the charges matter
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t, N_k=24, surf_id=surf)
+        ctx.set_charges(charges, csurf)
+        r = ctx.solve(eps, I.EPS_WATER, lam, tol=1e-10, mode="direct_fp64", restart=100, maxiter=2000)
+        ctx.tree_build(0.3, 8, 32)
+        rt = ctx.solve(eps, I.EPS_WATER, lam, tol=1e-8, mode="tree_fp32", refine=True, restart=60, maxiter=2000)
+        ctx.set_charges([[0.0, 0.0, 0.0, 1.0]], [3])   # no surface 3
+        with pytest.raises(lspr.LsprError):
+            ctx.solve(eps, I.EPS_WATER, lam, tol=1e-10, mode="direct_fp64", restart=100, maxiter=2000)
+        ctx.set_charges(None)
+        rn = ctx.solve(eps, I.EPS_WATER, lam, tol=1e-10, mode="direct_fp64", restart=100, maxiter=2000)
+    assert np.all(r.status == 0) and np.all(rt.status == 0) and np.all(rn.status == 0)
+    scale = np.max(np.abs(dref))
+    assert np.max(np.abs(r.dipole - dref)) < 1e-6 * scale
+    assert np.max(np.abs(r.sigma_ext - sref)) < 1e-6 * np.max(np.abs(sref))
+    assert np.max(np.abs(rt.dipole - dref)) < 1e-4 * scale
+    assert np.max(np.abs(rn.dipole - d0)) < 1e-6 * np.max(np.abs(d0))
+
+
+def test_centred_charge_leaves_the_dipole(lspr):
+    # a charge at the centre of a sphere adds a field of full symmetry: the dipole is unchanged
+    v, t = I.icosphere(3, 10.0)
+    lam = np.array([380.0])
+    eps = I.drude_eps(lam)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        a = ctx.solve(eps, I.EPS_WATER, lam, tol=1e-10, mode="direct_fp64", restart=100, maxiter=2000)
+        ctx.set_charges([[0.0, 0.0, 0.0, 5000.0]], [0])
+        b = ctx.solve(eps, I.EPS_WATER, lam, tol=1e-10, mode="direct_fp64", restart=100, maxiter=2000)
+    assert np.max(np.abs(b.dipole - a.dipole)) < 1e-8 * np.max(np.abs(a.dipole))
+
+
 def test_multi_surface_upload_errors(lspr):
     v, t, surf = _sensor_small()
     bad = surf.copy()
