@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "lspr_internal.cuh"
+#include "tc_lists.h"
 
 namespace lspr {
 
@@ -726,9 +727,7 @@ int tree_tc_lists(lspr_ctx *ctx, bool p2p) {
     const int64_t ntb = tr.ntblocks;
     if (!tr.ready) return LSPR_E_STATE;
     if (!tr.tc_built) {
-        // M2P lists of groups of kTcGroup consecutive target blocks (tensor-core M2P): per group
-        // the sorted union of its blocks' lists with the mask of accepting blocks, cut into
-        // segments of at most kTcGroupSeg boxes (host side: one pass over the pairs)
+        // M2P lists of the groups (tc_group_m2p)
         std::vector<int> hlist((size_t)tr.n_m2p_pairs);
         std::vector<int4> hitems((size_t)tr.n_m2p_items);
         if (tr.n_m2p_pairs > 0) {
@@ -736,37 +735,16 @@ int tree_tc_lists(lspr_ctx *ctx, bool p2p) {
             LSPR_TRY(ctx, cudaMemcpyAsync(hitems.data(), tr.m2p_items.p, sizeof(int4) * tr.n_m2p_items, cudaMemcpyDeviceToHost, st));
             LSPR_TRY(ctx, cudaStreamSynchronize(st));
         }
-        std::vector<int2> glist;
-        std::vector<int4> gitems;
-        {
-            const int64_t ngroups = (ntb + kTcGroup - 1) / kTcGroup;
-            std::vector<std::vector<int2>> per(ngroups);   // (box, mask) entries of each group
-            for (const int4 &it : hitems) {
-                const int64_t g = it.x / kTcGroup;
-                const int bit = 1 << (int)(it.x % kTcGroup);
-                for (int l = it.y; l < it.z; ++l) per[g].push_back(make_int2(hlist[l], bit));
-            }
-            for (int64_t g = 0; g < ngroups; ++g) {
-                std::vector<int2> &v = per[g];
-                if (v.empty()) continue;
-                std::sort(v.begin(), v.end(), [](const int2 &a, const int2 &b) { return a.x < b.x; });
-                const int64_t start = (int64_t)glist.size();
-                for (const int2 &e : v) {
-                    if ((int64_t)glist.size() > start && glist.back().x == e.x)
-                        glist.back().y |= e.y;
-                    else
-                        glist.push_back(e);
-                }
-                const int64_t n = (int64_t)glist.size() - start, k = (n + kTcGroupSeg - 1) / kTcGroupSeg;
-                for (int64_t q = 0; q < k; ++q)
-                    gitems.push_back(make_int4((int)g, (int)(start + n * q / k), (int)(start + n * (q + 1) / k), 0));
-            }
-        }
+        std::vector<TcEntry> glist;
+        std::vector<TcItem> gitems;
+        tc_group_m2p(ntb, kTcGroup, kTcGroupSeg, hlist.data(), (const int *)hitems.data(), tr.n_m2p_items, glist,
+                     gitems);
         tr.n_tc_pairs = (int64_t)glist.size();
         tr.n_tc_items = (int64_t)gitems.size();
         LSPR_TRY(ctx, tr.tc_list.ensure(std::max<size_t>(1, glist.size())));
         LSPR_TRY(ctx, tr.tc_items.ensure(std::max<size_t>(1, gitems.size())));
         if (!glist.empty()) {
+            static_assert(sizeof(TcEntry) == sizeof(int2) && sizeof(TcItem) == sizeof(int4), "device layouts");
             LSPR_TRY(ctx, cudaMemcpyAsync(tr.tc_list.p, glist.data(), sizeof(int2) * glist.size(), cudaMemcpyHostToDevice, st));
             LSPR_TRY(ctx, cudaMemcpyAsync(tr.tc_items.p, gitems.data(), sizeof(int4) * gitems.size(), cudaMemcpyHostToDevice, st));
         }
@@ -774,67 +752,17 @@ int tree_tc_lists(lspr_ctx *ctx, bool p2p) {
         tr.tc_built = true;
     }
     if (p2p && !tr.tcp_built) {
-        // P2P source ranges of the same groups: per group, the blocks' ranges are cut at every
-        // range end (a sweep over the sorted ends with one coverage count per block), pieces with
-        // the same mask that touch are merged, and the pieces are packed into work units of at
-        // most kTcP2PSrc sources (a longer piece is split)
+        // P2P source ranges of the same groups (tc_group_p2p)
         std::vector<int4> hp2p((size_t)tr.n_p2p_items);
         if (tr.n_p2p_items > 0) {
             LSPR_TRY(ctx, cudaMemcpyAsync(hp2p.data(), tr.p2p_items.p, sizeof(int4) * tr.n_p2p_items,
                                           cudaMemcpyDeviceToHost, st));
             LSPR_TRY(ctx, cudaStreamSynchronize(st));
         }
-        std::vector<int4> pivl, pitems;
-        int64_t psrc = 0;
-        {
-            const int64_t ngroups = (ntb + kTcGroup - 1) / kTcGroup;
-            std::vector<std::vector<int2>> ev(ngroups);   // (position, +-(block + 1))
-            for (const int4 &it : hp2p) {
-                const int64_t g = it.x / kTcGroup;
-                const int k = (int)(it.x % kTcGroup) + 1;
-                ev[g].push_back(make_int2(it.y, k));
-                ev[g].push_back(make_int2(it.z, -k));
-            }
-            for (int64_t g = 0; g < ngroups; ++g) {
-                std::vector<int2> &e = ev[g];
-                if (e.empty()) continue;
-                std::sort(e.begin(), e.end(), [](const int2 &a, const int2 &b) { return a.x < b.x; });
-                int cov[kTcGroup] = {0};
-                const size_t first = pivl.size();
-                for (size_t i = 0; i < e.size();) {
-                    const int pos = e[i].x;
-                    for (; i < e.size() && e[i].x == pos; ++i) cov[std::abs(e[i].y) - 1] += e[i].y > 0 ? 1 : -1;
-                    if (i == e.size()) break;
-                    int mask = 0;
-                    for (int k = 0; k < kTcGroup; ++k) mask |= cov[k] > 0 ? 1 << k : 0;
-                    const int next = e[i].x;
-                    if (!mask || next <= pos) continue;
-                    if (pivl.size() > first && pivl.back().y == pos && pivl.back().z == mask)
-                        pivl.back().y = next;
-                    else
-                        pivl.push_back(make_int4(pos, next, mask, 0));
-                }
-                // split long pieces, then pack pieces into units
-                std::vector<int4> pieces;
-                for (size_t i = first; i < pivl.size(); ++i)
-                    for (int s0 = pivl[i].x; s0 < pivl[i].y; s0 += kTcP2PSrc)
-                        pieces.push_back(make_int4(s0, std::min(pivl[i].y, s0 + kTcP2PSrc), pivl[i].z, 0));
-                pivl.resize(first);
-                int64_t u0 = (int64_t)pivl.size(), usrc = 0;
-                for (const int4 &q : pieces) {
-                    const int n = q.y - q.x;
-                    if (usrc > 0 && usrc + n > kTcP2PSrc) {
-                        pitems.push_back(make_int4((int)g, (int)u0, (int)pivl.size(), 0));
-                        u0 = (int64_t)pivl.size();
-                        usrc = 0;
-                    }
-                    pivl.push_back(q);
-                    usrc += n;
-                    psrc += n;
-                }
-                if ((int64_t)pivl.size() > u0) pitems.push_back(make_int4((int)g, (int)u0, (int)pivl.size(), 0));
-            }
-        }
+        std::vector<TcRange> pivl;
+        std::vector<TcItem> pitems;
+        static_assert(sizeof(TcRange) == sizeof(int4), "device layout");
+        const int64_t psrc = tc_group_p2p(ntb, kTcGroup, kTcP2PSrc, (const int *)hp2p.data(), tr.n_p2p_items, pivl, pitems);
         tr.n_tcp_items = (int64_t)pitems.size();
         tr.n_tcp_ivl = (int64_t)pivl.size();
         tr.n_tcp_sources = psrc;
