@@ -713,11 +713,13 @@ static void p2m_launch(lspr_ctx *ctx, int B) {
 template <typename T, int P, int NB>
 static void m2p_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     static int occ = 0;
+    static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
     if constexpr (NB > 1) {
         constexpr size_t smem = m2p_gemm_smem<T, P, NB>();
+        // a failure here shows as the launch's error, which the caller checks
+        (void)allow_smem(m2p_gemm_kernel<T, P, NB>, (int)smem, ctx->device, smem_set);
         if (occ <= 0) {
-            cudaFuncSetAttribute(m2p_gemm_kernel<T, P, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             int per_sm = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2p_gemm_kernel<T, P, NB>, kM2PGemmThreads,
                                                               smem) != cudaSuccess ||

@@ -142,16 +142,14 @@ __global__ void __launch_bounds__(kFfM2PWarps * 32)
 
 template <int NB>
 int m2p_ff_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
-    static int occ = 0, occ_smem = -1, smem_set = 0;
+    static int occ = 0, occ_smem = -1;
+    static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
     const int NT = n_terms(tr.P);
     const size_t per = ff_m2p_smem_per_warp(NT, NB);
     const int W = (int)std::max<size_t>(1, std::min<size_t>(kFfM2PWarps, (96 * 1024) / per));
     const size_t smem = per * W;
-    if (smem > (size_t)smem_set) {
-        LSPR_TRY(ctx, cudaFuncSetAttribute(m2p_ff_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        smem_set = (int)smem;
-    }
+    LSPR_TRY(ctx, allow_smem(m2p_ff_kernel<NB>, (int)smem, ctx->device, smem_set));
     if (occ_smem != (int)smem) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2p_ff_kernel<NB>, kFfM2PWarps * 32, smem) !=

@@ -322,6 +322,18 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
 int workorder_natural(lspr_ctx *ctx);
 
 // ------------------------------------------------------------ tree.cu
+// A kernel's dynamic shared memory above 48 KB is opted into on every device it runs on:
+// set[d] holds the size already allowed on device d (devices past the table set it each call).
+constexpr int kSmemDevices = 64;
+template <class K>
+inline cudaError_t allow_smem(K kernel, int bytes, int device, int *set) {
+    const bool tracked = device >= 0 && device < kSmemDevices;
+    if (tracked && set[device] >= bytes) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && tracked) set[device] = bytes;
+    return e;
+}
+
 int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit);
 int tree_tc_lists(lspr_ctx *ctx, bool p2p);
 int selftest_wait_timeout(lspr_ctx *ctx, int32_t *result);

@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 template <int P, int RC>
 int tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     using S = TcShape<P, RC>;
-    static int smem_set = 0;
+    static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
     if (tr.n_tc_items == 0) return LSPR_OK;
     const int nrc = (B + RC - 1) / RC;
@@ -424,10 +424,7 @@ int tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
         LSPR_TRY(ctx, ctx->dev_err.ensure(1));
         LSPR_TRY(ctx, cudaMemsetAsync(ctx->dev_err.p, 0, sizeof(int), ctx->stream));
     }
-    if (!smem_set) {
-        LSPR_TRY(ctx, cudaFuncSetAttribute(m2p_tc_kernel<P, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
-        smem_set = 1;
-    }
+    LSPR_TRY(ctx, allow_smem(m2p_tc_kernel<P, RC>, S::SMEM, ctx->device, smem_set));
     ++ctx->n_launches;   // the image; the caller counts the M2P launch
     const unsigned gi =
         (unsigned)std::max<int64_t>(1, std::min<int64_t>((segs + 255) / 256, 8 * std::max(1, ctx->num_sms)));

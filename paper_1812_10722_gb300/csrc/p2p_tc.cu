@@ -333,17 +333,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 template <int RC>
 int tc_p2p(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B) {
     using S = P2PShape<RC>;
-    static int smem_set = 0;
+    static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
     if (tr.n_tcp_items == 0) return LSPR_OK;
     if (!ctx->dev_err.p) {
         LSPR_TRY(ctx, ctx->dev_err.ensure(1));
         LSPR_TRY(ctx, cudaMemsetAsync(ctx->dev_err.p, 0, sizeof(int), st));
     }
-    if (!smem_set) {
-        LSPR_TRY(ctx, cudaFuncSetAttribute(p2p_tc_kernel<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
-        smem_set = 1;
-    }
+    LSPR_TRY(ctx, allow_smem(p2p_tc_kernel<RC>, S::SMEM, ctx->device, smem_set));
     const int nrc = (B + RC - 1) / RC;
     const unsigned grid =
         (unsigned)std::max<int64_t>(1, std::min<int64_t>(tr.n_tcp_items * nrc, std::max(1, ctx->num_sms)));
