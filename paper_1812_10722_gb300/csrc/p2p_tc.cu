@@ -22,7 +22,7 @@
 // Opt-in (lspr_set_tensor_cores bit 1): on this GPU the generation of the kernel tile (one
 // thread per target, 8 warps) bounds it, and a group's union of source ranges holds about
 // 1.7x the pairs of its blocks' own lists, so at 16 right-hand sides it is slower than
-// p2p_kernel (1.40 ms against 1.0 ms per product on the 20480-panel sphere).
+// p2p_kernel (1.40 ms against 0.94 ms per product on the 20480-panel sphere).
 #include "farfield.cuh"
 #include "tcgen05.cuh"
 
