@@ -1,0 +1,71 @@
+"""The bench's workloads against the benchmark configurations (mesh sizes, wavelength grids,
+media, tolerances) and its algorithmic work counts; CPU only, nothing is timed."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1812_10722_gb300 import inputs as I  # noqa: E402
+
+
+def test_default_workload_is_the_20480_panel_sphere():
+    wl = bench.WORKLOADS["sphere20480"]
+    v, t, surf = bench.workload_geometry(wl)
+    assert len(t) == 20480 and surf is None
+    r = np.linalg.norm(v, axis=1)
+    assert np.allclose(r, 10.0)
+    assert wl["lam"] == [380.0] and wl["tol"] == 1e-6 and wl["mode"] == "tree_fp32"
+    assert (wl["K"], wl["K_fine"]) == (4, 19)
+
+
+def test_sweep_workloads():
+    w16 = bench.WORKLOADS["sphere20480_sweep16"]
+    assert len(w16["lam"]) == 16 and w16["lam"][0] == 350.0 and w16["lam"][-1] == 420.0
+    w64 = bench.WORKLOADS["sphere81920_sweep64"]
+    lam = np.asarray(w64["lam"])
+    assert len(lam) == 64 and lam[0] == 350.0 and lam[-1] == 420.0
+    assert np.allclose(np.diff(lam), 70.0 / 63.0)          # uniform, endpoints included
+    assert w64["sub"] == 6 and 20 * 4 ** w64["sub"] == 81920
+    assert w64["tol"] == 1e-6 and w64["refine"]
+
+
+def test_sensor_workload():
+    wl = bench.WORKLOADS["sensor_c4"]
+    lam = np.asarray(wl["lam"])
+    assert len(lam) == 32 and lam[0] == 370.0 and lam[-1] == 400.0
+    assert wl["eps_analyte"] == 2.25 and 20 * 4 ** wl["sub"] == 81920
+    assert {a[1] for a in wl["analytes"]} == {1.0}          # 1 nm gaps on +-z
+    eps = bench.workload_eps(wl, lam[:3])
+    assert eps.shape == (3, 3)
+    assert np.allclose(eps[:, 0], I.drude_eps(lam[:3])) and np.allclose(eps[:, 1:], 2.25)
+
+
+def test_tuning_wavelengths_hold_the_resonance():
+    lam = I.wavelengths(350, 420, 64)
+    pick = bench.tuning_wavelengths(lam)
+    k = np.argmin(np.abs(I.drude_eps(lam) + 2 * I.EPS_WATER))
+    assert lam[k] in pick and lam[0] in pick and lam[-1] in pick and len(pick) <= 4
+    assert list(bench.tuning_wavelengths(lam, 1)) == [lam[k]]
+    assert list(bench.tuning_wavelengths(lam[:3])) == list(lam[:3])
+
+
+def _terms(P):
+    return [(a, b, n - a - b) for n in range(P + 1) for a in range(n, -1, -1) for b in range(n - a, -1, -1)]
+
+
+@pytest.mark.parametrize("P", [1, 5, 6, 8])
+def test_work_counts(P):
+    nt = (P + 1) * (P + 2) * (P + 3) // 6
+    assert len(_terms(P)) == nt
+    # the contraction adds 4 channels x 2 flops per term and right-hand side
+    assert bench.m2p_flops(P, 3) - bench.m2p_flops(P, 0) == 8 * nt * 3
+    # the recurrence: each term beyond the first reads its lower neighbours along every axis with
+    # a nonzero index (2 flops) and with an index >= 2 (1 flop), plus 3 to combine
+    rec = sum(2 * sum(d >= 1 for d in k) + sum(d >= 2 for d in k) + 3 for k in _terms(P)[1:])
+    assert bench.m2p_flops(P, 0) == 9 + rec
+    assert bench.p2p_flops(16) == 16 + 8 * 16
