@@ -169,7 +169,9 @@ LSPR_API int lspr_matvec(lspr_ctx *ctx, const double *x, double *y, int32_t B, c
  * correction (the update's deviation from the high-precision residual is at most the
  * FP32 operator's relative error times the previous residual); the dipole is
  * p = -eps_out * sum_j A_j (c_j dphi2s/dn_j - phi_j n_j) over the panels and
- * sigma_ext = Im(k^2 e.p / (eps_out |E0|)) / Re k with k = 2 pi sqrt(eps_out) / lambda.
+ * sigma_ext = Im(k^2 e.p / (eps_out |E0|)) / Re k with k = 2 pi sqrt(eps_out) / lambda
+ * (E0 = 0 is allowed, e.g. for the response to point charges alone: the dipole is then the
+ * result and sigma_ext, a ratio to |E0|, is not finite).
  * Returns LSPR_E_NOT_CONVERGED if any wavelength missed tol (results are still
  * written).  st may be null. */
 LSPR_API int lspr_solve(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
