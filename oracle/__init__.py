@@ -92,6 +92,9 @@ def lib():
             L.oracle_solve_multi.restype = _i
             L.oracle_rhs_charges.argtypes = [_dp, _ip, _ip, _i64, _i, _i, _dp, _i64, _dp, _ip, _dp]
             L.oracle_rhs_charges.restype = _i
+            L.oracle_solve_batch.argtypes = [_dp, _ip, _ip, _i64, _i, _i, _i, _d, _i, _dp, _d, _d, _dp, _dp, _d,
+                                             _i, _i, _dp, _dp, _intp, _dp, _i]
+            L.oracle_solve_batch.restype = _i
             _lib = L
     return _lib
 
@@ -385,3 +388,34 @@ def solve_multi(verts, tris, surf, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0
                                    restart, maxiter, _ptr(dip.view(np.float64)), _ptr(sig), its.ctypes.data_as(_intp),
                                    nthreads, nq, _ptr(q) if nq else None, _ptr(qs, _ip) if nq else None)
     return dip, sig, its, bad
+
+
+def solve_batch(verts, tris, eps_in, eps_out, lambda_nm, surf=None, E0=(0.0, 0.0, 1.0), tol=1e-8, restart=100,
+                maxiter=1000, K=4, K_fine=19, threshold=0.5, nthreads=0):
+    """The solve of ``solve`` (``surf`` None) or ``solve_multi`` for B wavelengths in lockstep, every
+    operator application shared across the wavelengths still iterating (Sec. II.D GMRES; the matrix
+    entries of Eq. layers_element are evaluated once per row for all of them).  Each wavelength's
+    result is bit for bit the one-at-a-time result.  eps_in: [B] or [B, S] complex.
+    Returns (dipoles [B,3], sigma [B], iters [B], relres [B], n_bad)."""
+    v, t, n = _mesh(verts, tris)
+    if surf is None:
+        sf, S = None, 1
+    else:
+        sf, S = _surf(surf, n)
+    lam = _f64(np.atleast_1d(lambda_nm))
+    B = len(lam)
+    e = _c128(np.asarray(eps_in, np.complex128).reshape(B, S))
+    dip = np.zeros((B, 3), np.complex128)
+    sig = np.zeros(B)
+    its = np.zeros(B, dtype=np.int32)
+    rr = np.zeros(B)
+    E = _f64(E0)
+    e2 = complex(eps_out)
+    bad = lib().oracle_solve_batch(_ptr(v), _ptr(t, _ip), _ptr(sf, _ip) if sf is not None else None, n, S, K,
+                                   K_fine, threshold, B, _ptr(e.view(np.float64)), e2.real, e2.imag, _ptr(E),
+                                   _ptr(lam), tol, restart, maxiter, _ptr(dip.view(np.float64)), _ptr(sig),
+                                   its.ctypes.data_as(_intp), _ptr(rr), nthreads)
+    if bad < 0:
+        raise RuntimeError("oracle_solve_batch: bad quadrature rule")
+    return dip, sig, its, rr, bad
+

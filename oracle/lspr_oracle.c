@@ -719,6 +719,164 @@ int oracle_gmres_multi(const double *verts, const int32_t *tris, const int32_t *
     return st;
 }
 
+/* The same GMRES for B wavelengths in lockstep, one Krylov basis per wavelength, every
+ * operator application shared by the wavelengths still iterating (apply_operator with B
+ * right-hand sides: the matrix entries are evaluated once per row for all of them).  Each
+ * wavelength takes exactly the steps of gmres_impl, in the same order, with the same
+ * per-row accumulation order of the operator, so its iterate is the one gmres_impl would
+ * produce bit for bit; only the cost is shared.  s: [B][S]; b, x: [B][2n]. */
+static int gmres_batch_impl(mesh_t *mp, int B, const cplx *s, const cplx *b, cplx *x, double tol, int restart,
+                            int maxiter, int *iters_out, double *relres_out)
+{
+    mesh_t m = *mp;
+    const int64_t n = m.n;
+    const int64_t N2 = 2 * n;
+    const int S = m.S;
+    const int mr = restart;
+    double *Vii = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const panel_t *p = &m.pan[i];
+        Vii[i] = oracle_self_V(p->v[0], p->v[1], p->v[2], p->c);
+    }
+    cplx *Vb = (cplx *)malloc(sizeof(cplx) * (size_t)N2 * (mr + 1) * B);
+    cplx *H = (cplx *)calloc((size_t)(mr + 1) * mr * B, sizeof(cplx));
+    cplx *cs = (cplx *)malloc(sizeof(cplx) * (size_t)mr * B), *sn = (cplx *)malloc(sizeof(cplx) * (size_t)mr * B);
+    cplx *g = (cplx *)malloc(sizeof(cplx) * (size_t)(mr + 1) * B), *yv = (cplx *)malloc(sizeof(cplx) * mr);
+    cplx *w = (cplx *)malloc(sizeof(cplx) * (size_t)N2 * B), *z = (cplx *)malloc(sizeof(cplx) * (size_t)N2 * B);
+    cplx *sp = (cplx *)malloc(sizeof(cplx) * (size_t)B * S);     /* packed eps ratios of the active set */
+    double *bnorm = (double *)malloc(sizeof(double) * B), *relres = (double *)malloc(sizeof(double) * B);
+    int *it = (int *)calloc(B, sizeof(int)), *state = (int *)malloc(sizeof(int) * B);   /* -1 running, 0 ok, 1 not */
+    int *jn = (int *)malloc(sizeof(int) * B), *live = (int *)malloc(sizeof(int) * B), *act = (int *)malloc(sizeof(int) * B);
+    for (int q = 0; q < B; ++q) {
+        for (int64_t i = 0; i < N2; ++i) x[(size_t)q * N2 + i] = 0.0;
+        bnorm[q] = vnorm(b + (size_t)q * N2, N2);
+        if (bnorm[q] == 0.0) bnorm[q] = 1.0;
+        relres[q] = 1.0;
+        state[q] = -1;
+    }
+    while (1) {
+        /* explicit residuals r = b - A x of the running wavelengths, one shared product */
+        int na = 0;
+        for (int q = 0; q < B; ++q)
+            if (state[q] < 0) act[na++] = q;
+        if (na == 0) break;
+        for (int a = 0; a < na; ++a) {
+            memcpy(z + (size_t)a * N2, x + (size_t)act[a] * N2, sizeof(cplx) * (size_t)N2);
+            memcpy(sp + (size_t)a * S, s + (size_t)act[a] * S, sizeof(cplx) * (size_t)S);
+        }
+        apply_operator(&m, na, sp, z, w);
+        int nl = 0;
+        for (int a = 0; a < na; ++a) {
+            const int q = act[a];
+            cplx *wq = w + (size_t)a * N2;
+            const cplx *bq = b + (size_t)q * N2;
+            for (int64_t i = 0; i < N2; ++i) wq[i] = bq[i] - wq[i];
+            const double beta = vnorm(wq, N2);
+            relres[q] = beta / bnorm[q];
+            if (relres[q] <= tol) { state[q] = 0; continue; }
+            if (it[q] >= maxiter) { state[q] = 1; continue; }
+            cplx *v0 = Vb + (size_t)q * N2 * (mr + 1);
+            for (int64_t i = 0; i < N2; ++i) v0[i] = wq[i] / beta;
+            cplx *gq = g + (size_t)q * (mr + 1);
+            for (int k = 0; k <= mr; ++k) gq[k] = 0.0;
+            gq[0] = beta;
+            jn[q] = 0;
+            live[nl++] = q;
+        }
+        if (nl == 0) continue;
+        /* Arnoldi steps; a wavelength leaves the cycle when its estimate meets tol or its
+         * step budget runs out (jn = the steps it took in this cycle) */
+        int *inner = (int *)malloc(sizeof(int) * nl);
+        for (int a = 0; a < nl; ++a) inner[a] = 1;
+        for (int j = 0; j < mr; ++j) {
+            int ns = 0;
+            for (int a = 0; a < nl; ++a) {
+                const int q = live[a];
+                if (inner[a] && it[q] < maxiter) act[ns++] = a;
+                else inner[a] = 0;
+            }
+            if (ns == 0) break;
+            for (int c = 0; c < ns; ++c) {
+                const int q = live[act[c]];
+                const cplx *vj = Vb + (size_t)q * N2 * (mr + 1) + (size_t)j * N2;
+                precond(&m, Vii, s + (size_t)q * S, vj, z + (size_t)c * N2);
+                memcpy(sp + (size_t)c * S, s + (size_t)q * S, sizeof(cplx) * (size_t)S);
+            }
+            apply_operator(&m, ns, sp, z, w);
+            for (int c = 0; c < ns; ++c) {
+                const int a = act[c], q = live[a];
+                cplx *Vq = Vb + (size_t)q * N2 * (mr + 1);
+                cplx *Hq = H + (size_t)q * (mr + 1) * mr, *csq = cs + (size_t)q * mr, *snq = sn + (size_t)q * mr;
+                cplx *gq = g + (size_t)q * (mr + 1);
+                cplx *wq = w + (size_t)c * N2, *vn = Vq + (size_t)(j + 1) * N2;
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int i = 0; i <= j; ++i) {
+                        cplx *vi = Vq + (size_t)i * N2;
+                        cplx h = 0.0;
+                        for (int64_t k = 0; k < N2; ++k) h += conj(vi[k]) * wq[k];
+                        for (int64_t k = 0; k < N2; ++k) wq[k] -= h * vi[k];
+                        Hq[i * mr + j] += h;
+                    }
+                double hn = vnorm(wq, N2);
+                Hq[(j + 1) * mr + j] = hn;
+                for (int64_t k = 0; k < N2; ++k) vn[k] = hn > 0 ? wq[k] / hn : 0.0;
+                for (int i = 0; i < j; ++i) {
+                    cplx aa = Hq[i * mr + j], c2 = Hq[(i + 1) * mr + j];
+                    Hq[i * mr + j] = csq[i] * aa + snq[i] * c2;
+                    Hq[(i + 1) * mr + j] = -conj(snq[i]) * aa + csq[i] * c2;
+                }
+                cplx aa = Hq[j * mr + j];
+                double bb = cabs(Hq[(j + 1) * mr + j]);
+                double t = sqrt(cabs(aa) * cabs(aa) + bb * bb);
+                if (cabs(aa) == 0.0) {
+                    csq[j] = 0.0;
+                    snq[j] = 1.0;
+                } else {
+                    csq[j] = cabs(aa) / t;
+                    snq[j] = (aa / cabs(aa)) * conj(Hq[(j + 1) * mr + j]) / t;
+                }
+                Hq[j * mr + j] = csq[j] * aa + snq[j] * Hq[(j + 1) * mr + j];
+                Hq[(j + 1) * mr + j] = 0.0;
+                gq[j + 1] = -conj(snq[j]) * gq[j];
+                gq[j] = csq[j] * gq[j];
+                ++it[q];
+                jn[q] = j + 1;
+                if (cabs(gq[j + 1]) / bnorm[q] <= tol) inner[a] = 0;
+            }
+        }
+        free(inner);
+        /* per wavelength: solve H y = g (upper triangular, size jn), x += M^-1 V y */
+        for (int a = 0; a < nl; ++a) {
+            const int q = live[a], jq = jn[q];
+            cplx *Vq = Vb + (size_t)q * N2 * (mr + 1);
+            cplx *Hq = H + (size_t)q * (mr + 1) * mr, *gq = g + (size_t)q * (mr + 1);
+            for (int i = jq - 1; i >= 0; --i) {
+                cplx acc = gq[i];
+                for (int k = i + 1; k < jq; ++k) acc -= Hq[i * mr + k] * yv[k];
+                yv[i] = acc / Hq[i * mr + i];
+            }
+            for (int64_t k = 0; k < N2; ++k) {
+                cplx acc = 0.0;
+                for (int i = 0; i < jq; ++i) acc += Vq[(size_t)i * N2 + k] * yv[i];
+                w[k] = acc;
+            }
+            precond(&m, Vii, s + (size_t)q * S, w, z);
+            cplx *xq = x + (size_t)q * N2;
+            for (int64_t k = 0; k < N2; ++k) xq[k] += z[k];
+            memset(Hq, 0, sizeof(cplx) * (size_t)(mr + 1) * mr);
+        }
+    }
+    int bad = 0;
+    for (int q = 0; q < B; ++q) {
+        if (state[q] != 0) ++bad;
+        if (iters_out) iters_out[q] = it[q];
+        if (relres_out) relres_out[q] = relres[q];
+    }
+    free(Vb); free(H); free(cs); free(sn); free(g); free(yv); free(w); free(z); free(sp);
+    free(bnorm); free(relres); free(it); free(state); free(jn); free(live); free(act); free(Vii);
+    return bad;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Observables                                                               */
 /* ------------------------------------------------------------------------- */
@@ -867,5 +1025,48 @@ int oracle_solve_multi(const double *verts, const int32_t *tris, const int32_t *
     free(b);
     free(x);
     free(s);
+    return bad;
+}
+
+/* The solve of oracle_solve_multi (surf may be NULL for one surface) for B wavelengths with
+ * every operator application shared across them: the right-hand sides of all wavelengths
+ * from one pass over V, then gmres_batch_impl, then each wavelength's dipole of surface 0 and
+ * sigma_ext.  Results equal oracle_solve / oracle_solve_multi wavelength by wavelength bit for
+ * bit; only the matrix-entry evaluations are shared.  eps_in: [B][S] complex.  Returns the
+ * number of wavelengths that did not converge. */
+int oracle_solve_batch(const double *verts, const int32_t *tris, const int32_t *surf, int64_t n, int S, int K,
+                       int Kf, double threshold, int B, const double *eps_in, double eps_out_re,
+                       double eps_out_im, const double *E0, const double *lambda_nm, double tol, int restart,
+                       int maxiter, double *dip_out, double *sigma_out, int *iters_out, double *relres_out,
+                       int nthreads)
+{
+    mesh_t m;
+    set_threads(nthreads);
+    int rc = mesh_init(&m, verts, tris, n, K, Kf, threshold);
+    if (rc) return -1;
+    m.surf = surf;
+    m.S = surf ? S : 1;
+    const int64_t N2 = 2 * n;
+    const cplx e2 = eps_out_re + I * eps_out_im;
+    cplx *b = (cplx *)malloc(sizeof(cplx) * (size_t)N2 * B);
+    cplx *x = (cplx *)malloc(sizeof(cplx) * (size_t)N2 * B);
+    cplx *s = (cplx *)malloc(sizeof(cplx) * (size_t)B * m.S);
+    rhs_impl(&m, B, (const cplx *)eps_in, e2, E0, b);
+    for (int q = 0; q < B * m.S; ++q) s[q] = (eps_in[2 * q] + I * eps_in[2 * q + 1]) / e2;
+    int bad = gmres_batch_impl(&m, B, s, b, x, tol, restart, maxiter, iters_out, relres_out);
+    for (int q = 0; q < B; ++q) {
+        const double *e1 = eps_in + 2 * (size_t)m.S * q;
+        const double *xq = (const double *)(x + (size_t)q * N2);
+        if (surf)
+            oracle_dipole_surface(verts, tris, surf, n, 0, xq, e1[0], e1[1], eps_out_re, eps_out_im, E0,
+                                  dip_out + 6 * q);
+        else
+            oracle_dipole(verts, tris, n, 0, n, xq, e1[0], e1[1], eps_out_re, eps_out_im, E0, dip_out + 6 * q);
+        sigma_out[q] = oracle_sigma_ext(dip_out + 6 * q, eps_out_re, eps_out_im, E0, lambda_nm[q]);
+    }
+    free(b);
+    free(x);
+    free(s);
+    mesh_free(&m);
     return bad;
 }

@@ -51,6 +51,34 @@ def sphere20480():
         gmres_iterations=int(its[0])))
 
 
+def sphere81920_sweep64():
+    """sigma_ext at four wavelengths of the 64-wavelength sweep over 350-420 nm on the 81920-panel
+    sphere: the one nearest the dipole resonance (smallest |eps + 2 eps_m|), both ends and the middle.
+    The four are solved in lockstep (oracle.solve_batch: every matrix entry is evaluated once per
+    product for all of them; each result equals the one-at-a-time solve bit for bit)."""
+    v, t = I.icosphere(6, 10.0)
+    lam_all = I.wavelengths(350.0, 420.0, 64)
+    k = int(np.argmin(np.abs(I.drude_eps(lam_all) + 2 * I.EPS_WATER)))
+    idx = sorted({k, 0, 32, 63})
+    lam = lam_all[idx]
+    ep = I.drude_eps(lam)
+    dip, sig, its, rr, bad = O.solve_batch(v, t, ep, I.EPS_WATER, lam, tol=1e-8, restart=100)
+    assert bad == 0
+    write("sphere81920_sweep64.json", dict(
+        workload="icosphere subdivision 6 (81920 triangles), R = 10 nm, Drude silver in water, 64 wavelengths "
+                 "uniform over 350-420 nm (these are four of them), E0 = z, K = 4, K_fine = 19, threshold 0.5, "
+                 "GMRES tol 1e-8, restart 100",
+        writer="tests/golden/make_golden.py (oracle only)",
+        sweep_index=[int(i) for i in idx],
+        resonance_index=k,
+        lambda_nm=[float(x) for x in lam],
+        sigma_ext_nm2=[float(s) for s in sig],
+        dipole=[[[float(z.real), float(z.imag)] for z in d] for d in dip],
+        closed_form_nm2=[O.sigma_closed_form(10.0, e, I.EPS_WATER, L) for e, L in zip(ep, lam)],
+        gmres_iterations=[int(i) for i in its],
+        relative_residual=[float(r) for r in rr]))
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["sphere1280"]
     for w in which:
