@@ -104,9 +104,11 @@ def resonance_peak(lam, sigma):
     return float(-b / (2 * a))
 
 
+METRIC = "lambda-solves/s at sigma_ext rel err <= 1e-4 vs plain FP64 (treecode GMRES)"
 L2_BYTES = 129 * 2 ** 20
-P2P_GEN_FLOPS = 16      # per (target, source) pair, generation of G and dG/dn (FMA = 2 flops)
-P2P_FP32_INSTR = 16     # FP32-pipe instructions per pair
+P2P_GEN_FLOPS = 18      # per (target, source) pair, generation of G and dG/dn: 3 sub, 3 FMA (r^2), 2 mul
+                        # (r^-3), 3 FMA (n.d), 2 scale, with FMA = 2 flops; the rsqrt goes to the SFU
+SFU_PER_CLK_SM = 16     # MUFU (rsqrt, reciprocal) results per clock per SM
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates, TF32 over BF16
 # DRAM bytes (read + write) per launch of the current kernels, from the ncu captures summarised in
@@ -129,10 +131,37 @@ def m2p_flops(P: int, B: int = 1) -> int:
     return f + 8 * len(terms) * B
 
 
+def m2p_terms(P: int) -> int:
+    """Taylor terms with |k| <= P."""
+    return (P + 1) * (P + 2) * (P + 3) // 6
+
+
 def p2p_flops(B: int = 1) -> int:
-    """Flops per (target, source) pair: G and dG/dn generated once (16), then two kernels
+    """Flops per (target, source) pair: G and dG/dn generated once (18), then two kernels
     times 2 real channels of each right-hand side (8 B)."""
     return P2P_GEN_FLOPS + 8 * B
+
+
+def m2p_tc_bound(P: int, B: int, group_box_pairs: int, peaks: dict, mhz: float) -> dict:
+    """Time bound of one tensor-core M2P launch: the largest of its coefficient generation on the
+    FP32 pipe (the recurrence for 256 targets per (group, box) and unit of 16 or 32 right-hand
+    sides), its reciprocal square roots on the SFU, and its issued MMAs on the tensor pipe
+    (M = 128 channels x N = 256 targets x K = 8 per step; 3 MMAs per step for units of 32
+    right-hand sides, 2 for units of 16)."""
+    nt = (P + 1) * (P + 2) * (P + 3) // 6
+    rc = 16 if B <= 16 else 32
+    units = (B + rc - 1) // rc
+    ksteps = sum((min(16, nt - kc) + 7) // 8 for kc in range(0, nt, 16))
+    gen = group_box_pairs * units * 256 * (m2p_flops(P, 0))
+    mufu = group_box_pairs * units * 256
+    mma = group_box_pairs * units * (3 if rc == 32 else 2) * 2 * 128 * 256 * 8 * ksteps
+    fp32_peak = fp32_peak_tflops(mhz) * 1e12
+    sfu_peak = SFU_PER_CLK_SM * 152 * mhz * 1e6
+    tf32_peak = peaks.get("bf16_tflops_sustained", 1741.2) * TF32_PER_BF16 * 1e12
+    t = {"fp32_generation": gen / fp32_peak, "sfu": mufu / sfu_peak, "tensor_mma": mma / tf32_peak}
+    return {"terms_s": t, "bound_s": max(t.values()), "limiter": max(t, key=t.get), "mma_flops": mma,
+            "generation_flops": gen, "mufu_ops": mufu, "tf32_peak_tflops": tf32_peak / 1e12,
+            "fp32_peak_tflops": fp32_peak / 1e12, "sfu_peak_tops": sfu_peak / 1e12}
 
 
 def fp32_peak_tflops(mhz: float) -> float:
@@ -284,6 +313,8 @@ def run_ours(args, wl, rank, world, local_rank):
         e1.synchronize()
         replay_ms += e0.elapsed_time(e1)
     ktime = ctx.timing()
+    krhs = ctx.timing_rhs()
+    ctx_tc = ctx.tc_info()
     ctx.set_timing(False)
     barrier()
     info = ctx.info()
@@ -294,15 +325,68 @@ def run_ours(args, wl, rank, world, local_rank):
         t_max = float(tt.item())
     value = B * args.steps * world / (t_max / 1e3)
 
-    # ---- accuracy: the same step with the plain FP64 treecode (same P, theta) and the oracle's stored value
+    # ---- accuracy and the plain baseline: the FP64 treecode (same tree) one wavelength at a time at
+    # the checked wavelengths (all of them for B <= 4; else the one nearest the resonance, both ends
+    # and the middle), each solve timed with CUDA events; the mixed-precision sigma_ext and the FP64
+    # one against each other and against the oracle's stored solves
     acc = {}
+    base = None
     if wl["mode"] == "tree_fp32":
-        # large batches: the wavelength nearest the resonance (the FP64 treecode is ~30x slower)
-        ka = [int(np.argmin(np.abs(I.drude_eps(lam) + 2 * em)))] if B > 4 else list(range(B))
-        r64 = ctx.solve(eps[ka], em, lam[ka], tol=min(wl["tol"], 1e-8), restart=wl["restart"], maxiter=2000,
-                        mode="tree_fp64")
-        acc["sigma_rel_err_vs_fp64_treecode"] = float(np.max(np.abs(sig[ka] - r64.sigma_ext) / r64.sigma_ext))
+        ka = [int(np.where(lam == x)[0][0]) for x in tuning_wavelengths(lam)] if B > 4 else list(range(B))
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        ctx.mesh_upload(v_d, t_d, wl["K"], wl["K_fine"], wl["N_k"], surf_id=s_d)
+        ctx.tree_build(wl["theta"], wl["P"], wl["Ncrit"])
+        g1.record(stream)
+        g1.synchronize()
+        t_geom = g0.elapsed_time(g1)
+        ctx.solve(eps[ka[:1]], em, lam[ka[:1]], tol=wl["tol"], restart=wl["restart"], maxiter=2000, mode="tree_fp64")
+        sig64, t64, it64 = [], [], []
+        for k in ka:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r64 = ctx.solve(eps[k:k + 1], em, lam[k:k + 1], tol=wl["tol"], restart=wl["restart"], maxiter=2000,
+                            mode="tree_fp64")
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+            sig64.append(float(r64.sigma_ext[0]))
+            it64.append(int(r64.iterations[0]))
+        sig64 = np.asarray(sig64)
+        acc["sigma_rel_err_vs_fp64_treecode"] = float(np.max(np.abs(sig[ka] - sig64) / sig64))
         acc["checked_wavelengths_nm"] = [float(lam[k]) for k in ka]
+        t_sweep = t_geom + B / len(ka) * sum(t64)
+        base = {"value": round(1e3 * B / t_sweep, 4), "unit": "lambda-solves/s",
+                "ms_per_sweep": round(t_sweep, 2), "extrapolated": B > len(ka),
+                "ratio": round(value / (1e3 * B / t_sweep), 3),
+                "sample": f"plain FP64 treecode GMRES (theta {wl['theta']}, P {wl['P']}, Ncrit {wl['Ncrit']}, tol "
+                          f"{wl['tol']}, restart {wl['restart']}, no refinement), one wavelength at a time: "
+                          f"{len(ka)} of the {B} wavelengths ({acc['checked_wavelengths_nm']}) solved and timed "
+                          f"with CUDA events ({[round(x, 1) for x in t64]} ms, {it64} Arnoldi steps); the sweep = "
+                          f"one mesh upload and tree build ({t_geom:.1f} ms) + {B}/{len(ka)} x their sum",
+                "sigma_ext_nm2": [float(x) for x in sig64]}
+    gname = os.path.join(ROOT, "tests", "golden", f"{args.workload}.json")
+    gold1 = os.path.join(ROOT, "tests", "golden", f"sphere{info['n_panels']}_l380.json")
+    if os.path.exists(gname):
+        with open(gname) as f:
+            g = json.load(f)
+        idx = [int(np.argmin(np.abs(lam - x))) for x in g["lambda_nm"]]
+        ref = np.asarray(g["sigma_ext_nm2"])
+        err = np.abs(sig[idx] - ref) / ref
+        acc["oracle"] = {"lambda_nm": [float(lam[k]) for k in idx], "sigma_rel_err": [float(e) for e in err],
+                         "max_rel_err": float(err.max()), "within_1e-4": bool(err.max() <= 1e-4),
+                         "resonance_lambda_nm": float(lam[g["resonance_index"]]),
+                         "golden": f"tests/golden/{args.workload}.json (oracle, direct FP64, tol 1e-8)"}
+        if base is not None:
+            s64 = dict(zip(acc["checked_wavelengths_nm"], base["sigma_ext_nm2"]))
+            e64 = [abs(s64[float(lam[k])] - r) / r for k, r in zip(idx, ref) if float(lam[k]) in s64]
+            if e64:
+                base["sigma_max_rel_err_vs_oracle"] = float(max(e64))
+        acc["sigma_rel_err_vs_oracle"] = float(err.max())
+    elif B == 1 and lam[0] == 380.0 and os.path.exists(gold1):
+        with open(gold1) as f:
+            g = json.load(f)
+        acc["sigma_rel_err_vs_oracle"] = float(abs(sig[0] - g["sigma_ext_nm2"]) / g["sigma_ext_nm2"])
     if wl.get("analytes"):
         # resonance shift: the same sweep on the bare sphere, peaks from parabolic fits
         vb, tb = I.icosphere(wl["sub"], wl["R"])
@@ -313,11 +397,7 @@ def run_ours(args, wl, rank, world, local_rank):
         acc["resonance"] = {"peak_nm": resonance_peak(lam, sig), "bare_sphere_peak_nm": resonance_peak(lam, rb.sigma_ext),
                             "shift_nm": resonance_peak(lam, sig) - resonance_peak(lam, rb.sigma_ext),
                             "peak_sigma_nm2": float(np.max(sig)), "bare_peak_sigma_nm2": float(np.max(rb.sigma_ext))}
-    gold = os.path.join(ROOT, "tests", "golden", f"sphere{info['n_panels']}_l380.json")
-    if B == 1 and lam[0] == 380.0 and os.path.exists(gold):
-        with open(gold) as f:
-            g = json.load(f)
-        acc["sigma_rel_err_vs_oracle"] = float(abs(sig[0] - g["sigma_ext_nm2"]) / g["sigma_ext_nm2"])
+    dev_errors = ctx.device_errors()
 
     # ---- end to end through the public API with host buffers
     barrier()
@@ -334,69 +414,85 @@ def run_ours(args, wl, rank, world, local_rank):
         0 if surf is None else surf.nbytes)
     d2h = B * (3 * 16 + 8)
 
-    # ---- roofline of the dominant kernel (CUDA events around every launch in the timed region)
+    # ---- roofline of the dominant kernel: CUDA events around every launch of the instrumented
+    # replay, in which the far-field kernels run one after another on one stream (no overlap);
+    # algorithmic work counted from the right-hand sides each timed launch carried
     peaks = load_peaks()
-    mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    mhz = peaks.get("sm_max_mhz", 2070.0)
     kernels = {}
-    matvecs_per_step = None
     for name in ("p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh", "p2p_fp64", "m2p_fp64", "p2m_fp64",
                  "weights", "p2p_ff", "m2p_ff", "p2m_ff"):
         ms, n = ktime[name]
         if n:
             kernels[name] = {"ms_total": round(ms, 4), "launches": n, "ms_per_launch": ms / n,
                              "share_of_step": round(ms / replay_ms, 4)}
+            if krhs[name]:
+                kernels[name]["rhs_per_launch"] = round(krhs[name] / n, 3)
     pairs = info["n_p2p_pairs"] if wl["mode"].startswith("tree") else info["n_panels"] * info["n_sources"]
+    tgt_box = info["n_m2p_pairs"] * kernel_targets(info)
+    fp32 = wl["mode"].endswith("fp32")
+    peak_fp32 = fp32_peak_tflops(mhz)
+    m2p_tc = B > 1 and fp32 and not args.no_tc   # the FP32 M2P of several right-hand sides runs on tcgen05
+
+    def work(name):
+        """Algorithmic flops of all timed launches of a far-field slot."""
+        n, r = kernels[name]["launches"], krhs[name]
+        if name.startswith("p2p"):
+            return pairs * (P2P_GEN_FLOPS * n + 8 * r)
+        if name.startswith("m2p"):
+            return tgt_box * (m2p_flops(wl["P"], 0) * n + 8 * m2p_terms(wl["P"]) * r)
+        return None
+
+    for name in ("p2p", "m2p", "p2p_fp64", "m2p_fp64", "p2p_ff", "m2p_ff"):
+        if name in kernels and krhs[name]:
+            k = kernels[name]
+            k["algorithmic_tflops"] = work(name) / (k["ms_total"] * 1e-3) / 1e12
+    if "p2p" in kernels:
+        kernels["p2p"]["pairs_per_launch"] = pairs
+    if "m2p" in kernels:
+        kernels["m2p"]["path"] = "tcgen05 (TF32 hi/lo split, FP32 accumulation)" if m2p_tc else "FP32 pipe"
     roof = None
-    # dominant single kernel: the far-field evaluations (the "gmres" slot groups many small
-    # vector kernels, and P2M's event time overlaps the concurrent P2P on the side stream)
     dom = max((k for k in kernels if k in ("p2p", "m2p", "p2p_fp64", "m2p_fp64", "p2p_ff", "m2p_ff")),
               key=lambda k: kernels[k]["ms_total"], default=None)
-    fp32 = wl["mode"].endswith("fp32")
-    peak_fp32 = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
-    if "p2p" in kernels:
-        k = kernels["p2p"]
-        k["algorithmic_tflops"] = pairs * p2p_flops(B) / (k["ms_per_launch"] * 1e-3) / 1e12
-        k["pairs_per_launch"] = pairs
-    m2p_tc = B > 1 and fp32 and not args.no_tc   # the FP32 M2P of several right-hand sides runs on tcgen05
-    if "m2p" in kernels:
-        k = kernels["m2p"]
-        k["algorithmic_tflops"] = info["n_m2p_pairs"] * kernel_targets(info) * m2p_flops(wl["P"], B) / (
-            k["ms_per_launch"] * 1e-3) / 1e12
-        k["path"] = "tcgen05 (TF32 hi/lo split, FP32 accumulation)" if m2p_tc else "FP32 pipe"
-    for name, flops in (("p2p_fp64", True), ("m2p_fp64", None), ("p2p_ff", True), ("m2p_ff", None)):
-        if name in kernels:
-            k = kernels[name]
-            work = pairs * p2p_flops(B) if flops else info["n_m2p_pairs"] * kernel_targets(info) * m2p_flops(wl["P"], B)
-            k["algorithmic_tflops"] = work / (k["ms_per_launch"] * 1e-3) / 1e12
+    traffic = NCU_TRAFFIC.get((args.workload, dom, wl["theta"], wl["P"], wl["Ncrit"])) if dom else None
     if dom in ("p2p_fp64", "m2p_fp64"):
         a = kernels[dom]["algorithmic_tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom, wl["theta"], wl["P"], wl["Ncrit"])),
+                "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "peak_note": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"}
     elif dom == "m2p" and m2p_tc:
-        a = kernels[dom]["algorithmic_tflops"]
-        pk = peaks.get("bf16_tflops_sustained", 1755.8) * TF32_PER_BF16
-        roof = {"bound": "tensor", "kernel": dom, "achieved": round(a, 3), "peak": round(pk, 1), "unit": "TFLOP/s",
-                "frac": round(a / pk, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom, wl["theta"], wl["P"], wl["Ncrit"])),
-                "peak_note": "measured sustained bf16 x nominal TF32/BF16 rate (1.1/2.25); achieved counts the "
-                             "algorithmic contraction flops, not the split products"}
+        # max(generation / FP32 peak, rsqrt / SFU peak, issued MMA flops / TF32 peak) per launch
+        tc = ctx_tc
+        k = kernels[dom]
+        bnd = m2p_tc_bound(wl["P"], round(krhs[dom] / k["launches"]), tc["m2p_group_boxes"], peaks, mhz)
+        t = k["ms_per_launch"] * 1e-3
+        lim = bnd["limiter"]
+        if lim == "tensor_mma":
+            a, pk, unit, bound = bnd["mma_flops"] / t / 1e12, bnd["tf32_peak_tflops"], "TFLOP/s", "tensor"
+        elif lim == "fp32_generation":
+            a, pk, unit, bound = bnd["generation_flops"] / t / 1e12, bnd["fp32_peak_tflops"], "TFLOP/s", "alu"
+        else:
+            a, pk, unit, bound = bnd["mufu_ops"] / t / 1e12, bnd["sfu_peak_tops"], "Top/s", "alu"
+        roof = {"bound": bound, "kernel": dom, "achieved": round(a, 3), "peak": round(pk, 2), "unit": unit,
+                "frac": round(bnd["bound_s"] / t, 4), "traffic": traffic,
+                "bound_terms_ms": {x: round(1e3 * y, 4) for x, y in bnd["terms_s"].items()},
+                "peak_note": "frac = max(generation flops / FP32 peak (152 SM x 128 x 2 x 2070 MHz, derived), rsqrt / "
+                             "SFU peak (16 per clock per SM), issued TF32 MMA flops / TF32 peak (measured sustained "
+                             "bf16 x nominal 1.1/2.25)) / the launch time; achieved and peak are the limiting term's"}
     elif dom in ("p2p", "m2p") and fp32:
         a = kernels[dom]["algorithmic_tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 3), "peak": round(peak_fp32, 2),
-                "unit": "TFLOP/s", "frac": round(a / peak_fp32, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom, wl["theta"], wl["P"], wl["Ncrit"])),
+                "unit": "TFLOP/s", "frac": round(a / peak_fp32, 4), "traffic": traffic,
                 "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 flops x 2070 MHz (derived, no measured FP32 peak)"}
     elif dom in ("p2p_ff", "m2p_ff"):
         a = kernels[dom]["algorithmic_tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 4), "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s (FP64-equivalent)", "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC.get((args.workload, dom, wl["theta"], wl["P"], wl["Ncrit"])),
+                "unit": "TFLOP/s (FP64-equivalent)", "frac": round(a / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "peak_note": "float-float kernel replacing FP64; peak is the nominal FP64 1.25 TFLOP/s"}
-    elif dom is not None:
-        roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": None, "traffic": None, "peak_note": "of measured"}
     g_int = pairs * (sum(mvs) / len(mvs)) / (total_ms / args.steps / 1e3)
 
     out = {
-        "metric": "lambda-solves/s at sigma_ext rel err <= 1e-4 vs plain FP64 (treecode GMRES)",
+        "metric": METRIC,
         "value": round(value, 4), "unit": "lambda-solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
@@ -416,6 +512,8 @@ def run_ours(args, wl, rank, world, local_rank):
         "gmres_iterations": iters[-1],
         "sigma_ext_nm2": float(sig[0]),
         "accuracy": acc,
+        "baseline_fp64_treecode": base,
+        "device_errors": dev_errors,
         "kernels": kernels,
         "kernel_timing": {"how": "CUDA events around every launch, instrumented replay of the timed steps "
                                  "(host-driven Arnoldi cycles, same kernels and inputs)",
@@ -438,63 +536,121 @@ def ctx_launches(ctx) -> int:
 
 
 # --------------------------------------------------------- oracle (CPU) timings
-def oracle_sample(wl, iters_hint: int, reps: int = 1):
-    """Time the oracle's matrix-free matvec at full size and extrapolate one
-    lambda-solve as (GMRES iterations + 2) matvecs (explicit residual and RHS)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_iterations(wl, n_panels: int):
+    """The oracle's own GMRES step count for the workload, from its stored golden solves: the
+    largest over the stored wavelengths (the lockstep solve of a sweep runs until its slowest
+    wavelength converges).  Returns (steps, source)."""
+    name = "sphere81920_sweep64.json" if n_panels == 81920 and len(wl["lam"]) > 1 else f"sphere{n_panels}_l380.json"
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+            its = json.load(f)["gmres_iterations"]
+        return int(max(np.atleast_1d(its))), f"tests/golden/{name}"
+    except (OSError, KeyError):
+        return 40, "no stored oracle solve for this mesh: 40 assumed"
+
+
+def oracle_block(wl, rows: int, nthreads: int = 0):
+    """Time rows [0, rows) of the oracle's product with all the workload's right-hand sides (the
+    entries of a row are evaluated once for all of them).  Returns (seconds, rows, n)."""
     import oracle
     verts, tris, surf = workload_geometry(wl)
     n = len(tris)
-    if n > 40000:
-        # too large for a full product in the time budget: the matrix entries of a block of
-        # rows (the product's cost), scaled to all n rows
-        rows = 256
+    rows = max(1, min(rows, n))
+    lam = np.asarray(wl["lam"], float)
+    if surf is not None:
+        # several surfaces: the matrix entries of the block of rows (the product's cost)
         t0 = time.perf_counter()
         oracle.entries(verts, tris, K=wl["K"], K_fine=wl["K_fine"], rows=(0, rows))
-        t_mv = (time.perf_counter() - t0) * n / rows
-        return t_mv, (iters_hint + 2) * t_mv, f"the oracle's matrix entries of {rows} of {n} rows, scaled to a product"
-    s = I.drude_eps(wl["lam"][0]) / I.EPS_WATER
-    x = I.random_complex(2 * n, seed=0)
-    times = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        oracle.matvec(verts, tris, x, s, K=wl["K"], K_fine=wl["K_fine"])
-        times.append(time.perf_counter() - t0)
-    t_mv = float(np.median(times))
-    t_solve = (iters_hint + 2) * t_mv
-    return t_mv, t_solve, "one full-size oracle matvec"
+        return time.perf_counter() - t0, rows, n
+    s = I.drude_eps(lam) / I.EPS_WATER
+    x = I.random_complex(2 * n, seed=0, batch=len(lam))
+    t0 = time.perf_counter()
+    oracle.matvec_rows(verts, tris, x, s, (0, rows), K=wl["K"], K_fine=wl["K_fine"], nthreads=nthreads)
+    return time.perf_counter() - t0, rows, n
 
 
-def oracle_iterations_hint(wl):
-    gold = os.path.join(ROOT, "tests", "golden", f"sphere{len(I.icosphere(wl['sub'], wl['R'])[1])}_l380.json")
-    try:
-        with open(gold) as f:
-            return int(json.load(f)["gmres_iterations"])
-    except OSError:
-        return 30
+def oracle_rows_for(wl, seconds: float, nthreads: int = 0) -> int:
+    """Rows of the oracle's product that take about `seconds` (calibrated on a small block)."""
+    t, r, n = oracle_block(wl, 64, nthreads)
+    return int(max(16, min(n, 64 * seconds / max(t, 1e-6))))
+
+
+def oracle_rate(wl, t_block: float, rows: int, n: int, iters: int) -> float:
+    """lambda-solves/s of the oracle's lockstep solve of the workload's B wavelengths, from the
+    time of a block of rows of its B-right-hand-side product: (iterations + 3) products (first
+    residual, one per Arnoldi step, final residual, the right-hand side's pass over V)."""
+    t_prod = t_block * n / rows
+    return len(wl["lam"]) / ((iters + 3) * t_prod)
+
+
+def oracle_baseline(wl, n_panels: int, seconds: float = 12.0) -> dict:
+    """The cpu_baseline of the GPU line: the oracle timed on all host cores and on one, on a
+    bounded block of rows of its product, extrapolated to the workload's lambda-solves/s."""
+    iters, src = oracle_iterations(wl, n_panels)
+    cores = os.cpu_count()
+    rows = oracle_rows_for(wl, seconds)
+    t_all, rows, n = oracle_block(wl, rows)
+    rows1 = max(8, rows // max(1, cores))
+    t_one, rows1, _ = oracle_block(wl, rows1, nthreads=1)
+    v_all = oracle_rate(wl, t_all, rows, n, iters)
+    v_one = oracle_rate(wl, t_one, rows1, n, iters)
+    return {"value": v_all, "unit": "lambda-solves/s", "cores": cores, "kind": "oracle",
+            "single_thread_value": v_one, "cpu_model": cpu_model(), "extrapolated": True,
+            "sample": f"rows 0..{rows} of {n} of the oracle's {len(wl['lam'])}-right-hand-side product on "
+                      f"{cores} threads ({t_all:.2f} s; {rows1} rows on one thread: {t_one:.2f} s), scaled to "
+                      f"the whole product and to ({iters} + 3) products per lockstep solve; {iters} = the "
+                      f"oracle's own step count ({src})"}
 
 
 def run_reference(args, wl):
+    """The oracle as it stands on the host cores: every step times one bounded block of rows of its
+    B-right-hand-side product (about 4 s); the lambda-solve rate is extrapolated from it."""
     import oracle
     oracle.build()
-    it = oracle_iterations_hint(wl)
+    n = len(workload_geometry(wl)[1])
+    iters, src = oracle_iterations(wl, n)
+    rows = oracle_rows_for(wl, 4.0)
     for _ in range(args.warmup):
-        oracle_sample(wl, it)
-    t = 0.0
+        oracle_block(wl, rows)
+    ts = []
     for _ in range(args.steps):
-        t_mv, t_solve, sample = oracle_sample(wl, it)
-        t += t_solve
-    value = len(wl["lam"]) * args.steps / t if len(wl["lam"]) == 1 else args.steps / t
+        t, rows, n = oracle_block(wl, rows)
+        ts.append(t)
+    t_step = float(np.mean(ts))
+    value = oracle_rate(wl, t_step, rows, n, iters)
     cores = os.cpu_count()
+    sample = (f"each step: rows 0..{rows} of {n} of the oracle's {len(wl['lam'])}-right-hand-side product on "
+              f"{cores} threads; value extrapolated to the whole product and to ({iters} + 3) products per "
+              f"lockstep solve of the {len(wl['lam'])} wavelengths ({iters} = the oracle's own step count, {src})")
     return {
-        "impl": "reference", "metric": "lambda-solves/s at sigma_ext rel err <= 1e-4 vs plain FP64 (treecode GMRES)",
-        "value": value, "unit": "lambda-solves/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (icosphere, Drude silver in water)",
-        "config": {"workload": args.workload, "panels": len(workload_geometry(wl)[1]),
-                   "wavelengths": 1, "mode": "oracle direct FP64 (plain CPU)"},
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "lambda-solves/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (icosphere, Drude silver in water)",
+        "extrapolated": True,
+        "config": {"workload": args.workload, "panels": n, "wavelengths": len(wl["lam"]),
+                   "mode": "oracle direct FP64 (plain CPU), lockstep GMRES"},
         "cpu_baseline": {"value": value, "unit": "lambda-solves/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{sample} per step, lambda-solve extrapolated as "
-                                   f"({it} GMRES iterations + 2) matvecs"},
+                         "cpu_model": cpu_model(), "extrapolated": True, "sample": sample},
         "e2e": {"value": value, "unit": "lambda-solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -582,7 +738,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sphere20480", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sphere81920_sweep64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--restart", type=int, default=None, help="override the workload's GMRES restart length")
     ap.add_argument("--matvecs", type=int, default=0, help="only run this many bare matvecs (profiling)")
@@ -621,11 +777,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     out, iters = run_ours(args, wl, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_mv, t_solve, sample = oracle_sample(wl, iters[-1])
-        out["cpu_baseline"] = {"value": 1.0 / t_solve,
-                               "unit": "lambda-solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                               "sample": f"{sample} ({t_mv:.2f} s) on the host cores; one "
-                                         f"lambda-solve extrapolated as ({iters[-1]} GMRES iterations + 2) matvecs"}
+        out["cpu_baseline"] = oracle_baseline(wl, out["config"]["panels"])
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

@@ -149,7 +149,8 @@ LSPR_API int lspr_tree_build(lspr_ctx *ctx, double theta, int32_t P, int32_t Ncr
  * (.)_t the layer potential of surface t's panels, eps_ratio [B][nsurf] complex.
  * on_device = 0: x, y, eps_ratio are host pointers; 1: device pointers.  The
  * call is complete (stream synchronised) on return.
- * Errors: LSPR_E_STATE (no mesh; tree mode without a tree), LSPR_E_ARG, LSPR_E_CUDA. */
+ * Errors: LSPR_E_STATE (no mesh; tree mode without a tree), LSPR_E_ARG, LSPR_E_CUDA,
+ * LSPR_E_TIMEOUT (a bounded device wait ran out: y is written but incomplete). */
 LSPR_API int lspr_matvec(lspr_ctx *ctx, const double *x, double *y, int32_t B, const double *eps_ratio,
                 int32_t mode, int32_t on_device);
 
@@ -173,7 +174,8 @@ LSPR_API int lspr_matvec(lspr_ctx *ctx, const double *x, double *y, int32_t B, c
  * (E0 = 0 is allowed, e.g. for the response to point charges alone: the dipole is then the
  * result and sigma_ext, a ratio to |E0|, is not finite).
  * Returns LSPR_E_NOT_CONVERGED if any wavelength missed tol (results are still
- * written).  st may be null. */
+ * written), LSPR_E_TIMEOUT if a bounded device wait ran out during the solve (results are
+ * written but not trustworthy).  st may be null. */
 LSPR_API int lspr_solve(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
                const double *lambda_nm, int32_t B, const lspr_solve_opts *o, double *dipole_out,
                double *sigma_ext_out, lspr_solve_stats *st);
@@ -217,8 +219,18 @@ LSPR_API int lspr_autotune(lspr_ctx *ctx, const double *eps_in, double eps_out_r
 LSPR_API int lspr_get_info(lspr_ctx *ctx, int64_t *n_panels, int64_t *n_sources, int64_t *n_near, int64_t *n_boxes,
                   int64_t *n_p2p_items, int64_t *n_m2p_pairs, int64_t *n_p2p_pairs);
 
+/* Sizes of the tensor-core work lists of the current tree (0 until the first product of
+ * several right-hand sides forms them; any pointer may be null): M2P work units (a group of
+ * four consecutive 64-target blocks and a stretch of its box list), (group, box) entries of
+ * the groups' united box lists, and source entries of the P2P groups' united source ranges.
+ * LSPR_E_ARG: null context. */
+LSPR_API int lspr_get_tc_info(lspr_ctx *ctx, int64_t *m2p_units, int64_t *m2p_group_boxes,
+                              int64_t *p2p_group_sources);
+
 /* Kernel timing on the context's stream while enabled (lspr_set_timing(ctx, 1) clears
- * the counters): milliseconds summed over launches and launch counts, arrays of 16:
+ * the counters).  While enabled, the treecode's P2P runs on the context's stream after
+ * P2M and M2P instead of beside them on a second stream, so that the events around each
+ * launch time that kernel alone.  Milliseconds summed over launches and launch counts, arrays of 16:
  * [0] P2P FP32, [1] M2P FP32, [2] P2M FP32, [3] near correction + block assembly,
  * [4] GMRES vector kernels, [5] tree build, [6] mesh + near precompute, [7] other,
  * [8] P2P FP64, [9] M2P FP64, [10] P2M FP64, [11] source weights,
@@ -228,6 +240,10 @@ LSPR_API int lspr_set_timing(lspr_ctx *ctx, int32_t enable);
 /* Number of CUDA kernels the context has launched since lspr_create. */
 LSPR_API int lspr_launch_count(lspr_ctx *ctx, int64_t *count);
 LSPR_API int lspr_get_timing(lspr_ctx *ctx, double *ms, int64_t *launches);
+/* Right-hand sides (channel sets: wavelengths x surfaces) summed over the timed launches of the
+ * far-field slots ([0]-[2], [8]-[10], [12]-[14]; 0 elsewhere), so that the algorithmic work of
+ * the timed launches can be counted exactly.  rhs: array of 16.  LSPR_E_ARG: null pointer. */
+LSPR_API int lspr_get_timing_rhs(lspr_ctx *ctx, int64_t *rhs);
 
 /* GMRES of lspr_solve runs each Arnoldi cycle as one CUDA graph launch: a graph
  * loop whose body is one Arnoldi step (preconditioner, product, two Gram-Schmidt
@@ -247,10 +263,20 @@ LSPR_API int lspr_set_graphs(lspr_ctx *ctx, int32_t enable);
  * same sums.  Bits above 1 are ignored.  LSPR_E_ARG: null context. */
 LSPR_API int lspr_set_tensor_cores(lspr_ctx *ctx, int32_t enable);
 /* Bounded waits inside device kernels that ran out since lspr_create (the tensor-core
- * M2P's pipeline barriers, about one second each): a kernel whose wait runs out stops its
- * block, frees its resources and counts here, and the product it computed is incomplete.
+ * far-field kernels' pipeline barriers, about one second each): a kernel whose wait runs out
+ * stops its block, drains its copies and MMAs in flight, frees its tensor memory and counts
+ * here; the product it computed is incomplete, and the lspr_matvec, lspr_solve or
+ * lspr_autotune call that launched it returns LSPR_E_TIMEOUT (results are still written).
  * Synchronises the context's stream.  LSPR_E_ARG: null pointer. */
 LSPR_API int lspr_device_errors(lspr_ctx *ctx, int32_t *count);
+/* Check of that failure path inside the real product kernels: while enabled, every launch of a
+ * tensor-core far-field kernel first waits, with the pipelines' bounded wait, on a barrier that
+ * nothing arrives on; the wait gives up after its limit (about one second) before any copy or
+ * MMA is issued, the kernel returns without doing its work, the device error count grows and
+ * the call returns LSPR_E_TIMEOUT.  No fault, trap or endless loop is involved, and the context
+ * stays usable: disable it and the next product is complete.  Synchronises the context's
+ * stream.  LSPR_E_ARG: null context. */
+LSPR_API int lspr_selftest_gate_waits(lspr_ctx *ctx, int32_t enable);
 /* Point charges inside the surfaces (Eqs. integral_eq_lspr_system, matrix_multi: the interior
  * row of an analyte surface carries (1 / (4 pi eps_t)) sum_k q_k / |r - r_k|, r the collocation
  * point, eps_t the surface's permittivity of each wavelength in lspr_solve).  charges: [nq][4]

@@ -92,6 +92,8 @@ def lib():
             L.oracle_solve_multi.restype = _i
             L.oracle_rhs_charges.argtypes = [_dp, _ip, _ip, _i64, _i, _i, _dp, _i64, _dp, _ip, _dp]
             L.oracle_rhs_charges.restype = _i
+            L.oracle_matvec_rows.argtypes = [_dp, _ip, _i64, _i, _i, _d, _i, _dp, _dp, _dp, _i64, _i64, _i]
+            L.oracle_matvec_rows.restype = _i
             L.oracle_solve_batch.argtypes = [_dp, _ip, _ip, _i64, _i, _i, _i, _d, _i, _dp, _d, _d, _dp, _dp, _d,
                                              _i, _i, _dp, _dp, _intp, _dp, _i]
             L.oracle_solve_batch.restype = _i
@@ -418,4 +420,22 @@ def solve_batch(verts, tris, eps_in, eps_out, lambda_nm, surf=None, E0=(0.0, 0.0
     if bad < 0:
         raise RuntimeError("oracle_solve_batch: bad quadrature rule")
     return dip, sig, its, rr, bad
+
+
+def matvec_rows(verts, tris, x, s, rows, K=4, K_fine=19, threshold=0.5, nthreads=0):
+    """Rows [i0, i1) (panels) of y = A(s) x (Eq. matrix_lspr), top and bottom; x [2n] or [B, 2n].
+    Returns y shaped like x with only those rows filled (the rest zero)."""
+    v, t, n = _mesh(verts, tris)
+    x = _c128(x)
+    squeeze = x.ndim == 1
+    x2 = x.reshape(-1, 2 * n)
+    B = x2.shape[0]
+    s = _c128(np.broadcast_to(np.atleast_1d(np.asarray(s, np.complex128)), (B,)))
+    y = np.zeros_like(x2)
+    i0, i1 = rows
+    rc = lib().oracle_matvec_rows(_ptr(v), _ptr(t, _ip), n, K, K_fine, threshold, B, _ptr(s.view(np.float64)),
+                                  _ptr(x2.view(np.float64)), _ptr(y.view(np.float64)), int(i0), int(i1), nthreads)
+    if rc:
+        raise RuntimeError(f"oracle_matvec_rows failed ({rc})")
+    return y[0] if squeeze else y
 

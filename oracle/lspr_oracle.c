@@ -358,7 +358,9 @@ int64_t oracle_near_pairs(const double *verts, const int32_t *tris, int64_t n, d
 /*   y_bot = phi/2 - sum_t (K phi)_t + sum_t s_t (V dphi)_t                    */
 /* (one surface: y_bot = phi/2 - K phi + s V dphi).                           */
 /* ------------------------------------------------------------------------- */
-static void apply_operator(const mesh_t *m, int B, const cplx *s, const cplx *x, cplx *y)
+/* Rows [i0, i1) of the product (the whole product: [0, n)). */
+static void apply_operator_rows(const mesh_t *m, int B, const cplx *s, const cplx *x, cplx *y, int64_t i0,
+                                int64_t i1)
 {
     const int64_t n = m->n;
     const int S = m->S;
@@ -368,7 +370,7 @@ static void apply_operator(const mesh_t *m, int B, const cplx *s, const cplx *x,
         cplx *kp = (cplx *)malloc(sizeof(cplx) * (size_t)B * S);
         cplx *vd = (cplx *)malloc(sizeof(cplx) * (size_t)B * S);
 #pragma omp for schedule(dynamic, 8)
-        for (int64_t i = 0; i < n; ++i) {
+        for (int64_t i = i0; i < i1; ++i) {
             for (int q = 0; q < B * S; ++q) kp[q] = vd[q] = 0.0;
             for (int64_t j = 0; j < n; ++j) {
                 double V, Kd;
@@ -398,6 +400,11 @@ static void apply_operator(const mesh_t *m, int B, const cplx *s, const cplx *x,
     }
 }
 
+static void apply_operator(const mesh_t *m, int B, const cplx *s, const cplx *x, cplx *y)
+{
+    apply_operator_rows(m, B, s, x, y, 0, m->n);
+}
+
 static void set_threads(int nthreads)
 {
 #ifdef _OPENMP
@@ -416,6 +423,22 @@ int oracle_matvec(const double *verts, const int32_t *tris, int64_t n, int K, in
     int rc = mesh_init(&m, verts, tris, n, K, Kf, threshold);
     if (rc) return rc;
     apply_operator(&m, B, (const cplx *)s, (const cplx *)x, (cplx *)y);
+    mesh_free(&m);
+    return 0;
+}
+
+/* Rows [i0, i1) of y[b] = A(s_b) x[b] (top and bottom rows of those panels; the other rows of y
+ * are left as they are): the product of oracle_matvec restricted to a block of panels, for
+ * timing a bounded share of it.  x, y: [B][2n]. */
+int oracle_matvec_rows(const double *verts, const int32_t *tris, int64_t n, int K, int Kf, double threshold,
+                       int B, const double *s, const double *x, double *y, int64_t i0, int64_t i1, int nthreads)
+{
+    mesh_t m;
+    if (i0 < 0 || i1 > n || i0 > i1) return -3;
+    set_threads(nthreads);
+    int rc = mesh_init(&m, verts, tris, n, K, Kf, threshold);
+    if (rc) return rc;
+    apply_operator_rows(&m, B, (const cplx *)s, (const cplx *)x, (cplx *)y, i0, i1);
     mesh_free(&m);
     return 0;
 }

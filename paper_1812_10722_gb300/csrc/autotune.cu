@@ -110,7 +110,8 @@ int lspr_autotune(lspr_ctx *c, const double *eps_in, double eps_out_re, double e
     res->ref_ms = ref_ms;
     res->candidates = n + 1;
     res->qualified = ok;
-    return LSPR_OK;
+    LSPR_TRY(c, cudaStreamSynchronize(c->stream));
+    return timeout_status(c, LSPR_OK);
 }
 
 }  // extern "C"

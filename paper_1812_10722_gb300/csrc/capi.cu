@@ -66,6 +66,22 @@ void timer_collect(lspr_ctx *ctx) {
 
 }  // namespace lspr
 
+namespace lspr {
+
+// LSPR_E_TIMEOUT if a bounded device wait ran out since the last status that reported one
+// (the stream is synchronised by the caller); otherwise rc
+int timeout_status(lspr_ctx *c, int rc) {
+    int count = 0;
+    if (cudaMemcpy(&count, c->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_status(c, cudaGetLastError(), "reading the device error count");
+    if (count == c->dev_err_seen) return rc;
+    c->dev_err_seen = count;
+    c->last_error = "a bounded device wait ran out: the product is incomplete";
+    return (rc == LSPR_OK || rc == LSPR_E_NOT_CONVERGED) ? LSPR_E_TIMEOUT : rc;
+}
+
+}  // namespace lspr
+
 using namespace lspr;
 
 extern "C" {
@@ -104,7 +120,8 @@ int lspr_create(lspr_ctx **out, int device, void *cuda_stream) {
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        c->dev_err.ensure(2) != cudaSuccess || cudaMemset(c->dev_err.p, 0, 2 * sizeof(int)) != cudaSuccess) {
         lspr_destroy(c);
         return LSPR_E_CUDA;
     }
@@ -172,7 +189,7 @@ int lspr_matvec(lspr_ctx *c, const double *x, double *y, int32_t B, const double
         LSPR_TRY(c, cudaMemcpyAsync(y, yd, sizeof(double2) * B * n2, cudaMemcpyDeviceToHost, c->stream));
     LSPR_TRY(c, cudaStreamSynchronize(c->stream));
     timer_collect(c);
-    return LSPR_OK;
+    return timeout_status(c, LSPR_OK);
 }
 
 int lspr_solve(lspr_ctx *c, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
@@ -189,6 +206,7 @@ int lspr_solve(lspr_ctx *c, const double *eps_in, double eps_out_re, double eps_
     const int64_t mv0 = c->matvec_count;
     int rc = solve_impl(c, eps_in, eps_out_re, eps_out_im, E0, lambda_nm, B, *o, dipole_out, sigma_ext_out, st);
     timer_collect(c);
+    if (cudaStreamSynchronize(c->stream) == cudaSuccess) rc = timeout_status(c, rc);
     if (st) {
         st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         st->matvecs = c->matvec_count - mv0;
@@ -206,6 +224,16 @@ int lspr_get_info(lspr_ctx *c, int64_t *n_panels, int64_t *n_sources, int64_t *n
     if (n_p2p_items) *n_p2p_items = c->tree.ready ? c->tree.n_p2p_items : 0;
     if (n_m2p_pairs) *n_m2p_pairs = c->tree.ready ? c->tree.n_m2p_pairs : 0;
     if (n_p2p_pairs) *n_p2p_pairs = c->tree.ready ? c->tree.p2p_pairs : 0;
+    return LSPR_OK;
+}
+
+int lspr_get_tc_info(lspr_ctx *c, int64_t *m2p_units, int64_t *m2p_group_boxes, int64_t *p2p_group_sources) {
+    if (!c) return LSPR_E_ARG;
+    const Tree &tr = c->tree;
+    const bool m = tr.ready && tr.tc_built, p = tr.ready && tr.tcp_built;
+    if (m2p_units) *m2p_units = m ? tr.n_tc_items : 0;
+    if (m2p_group_boxes) *m2p_group_boxes = m ? tr.n_tc_pairs : 0;
+    if (p2p_group_sources) *p2p_group_sources = p ? tr.n_tcp_sources : 0;
     return LSPR_OK;
 }
 
@@ -264,6 +292,14 @@ int lspr_device_errors(lspr_ctx *c, int32_t *count) {
     return LSPR_OK;
 }
 
+int lspr_selftest_gate_waits(lspr_ctx *c, int32_t enable) {
+    if (!c) return LSPR_E_ARG;
+    const int v = enable ? 1 : 0;
+    LSPR_TRY(c, cudaMemcpyAsync(c->dev_err.p + 1, &v, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    LSPR_TRY(c, cudaStreamSynchronize(c->stream));
+    return LSPR_OK;
+}
+
 int lspr_graph_stats(lspr_ctx *c, int64_t *cycles, int64_t *recordings) {
     if (!c) return LSPR_E_ARG;
     if (cycles) *cycles = c->graph_cycles;
@@ -278,7 +314,14 @@ int lspr_set_timing(lspr_ctx *c, int32_t enable) {
     for (int k = 0; k < kTimerSlots; ++k) {
         c->timing.ms[k] = 0;
         c->timing.launches[k] = 0;
+        c->timing.rhs[k] = 0;
     }
+    return LSPR_OK;
+}
+
+int lspr_get_timing_rhs(lspr_ctx *c, int64_t *rhs) {
+    if (!c || !rhs) return LSPR_E_ARG;
+    for (int k = 0; k < kTimerSlots; ++k) rhs[k] = c->timing.rhs[k];
     return LSPR_OK;
 }
 

@@ -169,6 +169,7 @@ int launch_p2p(lspr_ctx *ctx, int prec, const int4 *items, int64_t nitems, doubl
         else p2p_launch<float, batch_chunk<float>(2)>(ctx, items, nitems, B, acc, st, counter);
     }
     timer_end_on(ctx, slot, ev, st);
+    timer_rhs(ctx, slot, B);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
@@ -206,6 +207,7 @@ int launch_p2m(lspr_ctx *ctx, int prec, int B) {
         }
     }
     timer_end(ctx, slot, ev);
+    timer_rhs(ctx, slot, B);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }
@@ -225,6 +227,7 @@ int launch_m2p(lspr_ctx *ctx, int prec, double *acc, int *counter, int B) {
         LSPR_TRY_ST(m2p_orders_f32(ctx, acc, counter, B));
     }
     timer_end(ctx, slot, ev);
+    timer_rhs(ctx, slot, B);
     LSPR_TRY(ctx, cudaGetLastError());
     return LSPR_OK;
 }

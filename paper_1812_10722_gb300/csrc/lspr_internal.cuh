@@ -221,6 +221,7 @@ struct Timing {
     bool enabled = false;
     double ms[kTimerSlots] = {0};
     int64_t launches[kTimerSlots] = {0};
+    int64_t rhs[kTimerSlots] = {0};    // right-hand sides (channel sets) summed over the launches
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     size_t used = 0;
@@ -267,7 +268,9 @@ struct lspr_ctx {
     bool use_graphs = true;
     int tensor_cores = 1;              // tcgen05 for B >= 2 in FP32: bit 0 M2P, bit 1 P2P
     lspr::DArr<unsigned char> tc_img;  // split moments in tensor-core operand layout
-    lspr::DArr<int> dev_err;           // bounded device waits that ran out (never reset)
+    lspr::DArr<int> dev_err;           // [0] bounded device waits that ran out (never reset);
+                                       // [1] failure-path check: tensor-core kernels give up at once
+    int dev_err_seen = 0;              // [0] as last reported by a status (LSPR_E_TIMEOUT)
     // point charges inside the surfaces (lspr_set_charges): (x, y, z, q) and the surface of each
     lspr::DArr<dbl4> charges;
     lspr::DArr<int> charge_surf;
@@ -293,6 +296,9 @@ namespace lspr {
 
 // -------------------------------------------------------------- error helpers
 int cuda_status(lspr_ctx *ctx, cudaError_t e, const char *what);
+// LSPR_E_TIMEOUT in place of rc (LSPR_OK or LSPR_E_NOT_CONVERGED) when a bounded device wait ran
+// out since the last status that reported one; call with the context's stream synchronised
+int timeout_status(lspr_ctx *ctx, int rc);
 #define LSPR_TRY(ctx, expr)                                              \
     do {                                                                 \
         cudaError_t e__ = (expr);                                        \
@@ -310,6 +316,9 @@ void timer_end(lspr_ctx *ctx, int slot, cudaEvent_t ev);
 void timer_begin_on(lspr_ctx *ctx, int slot, cudaEvent_t *ev, cudaStream_t st);
 void timer_end_on(lspr_ctx *ctx, int slot, cudaEvent_t ev, cudaStream_t st);
 void timer_collect(lspr_ctx *ctx);
+inline void timer_rhs(lspr_ctx *ctx, int slot, int64_t B) {
+    if (ctx->timing.enabled) ctx->timing.rhs[slot] += B;
+}
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 

@@ -30,7 +30,9 @@
 //         (two accumulators of 256 columns alternate between units).
 // Every wait is bounded (about a second): one that runs out raises an abort flag that the
 // other roles see, the block drains its bulk copies and MMAs in flight, frees its tensor
-// memory and returns, and the context's device error count records it.
+// memory and returns, and the context's device error count (error[0]) records it.  With
+// error[1] set, thread 0 first waits on a barrier that nothing arrives on, so that the wait
+// runs out before any work is issued (the host's check of this failure path).
 #include "farfield.cuh"
 #include "tcgen05.cuh"
 
@@ -146,6 +148,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         bar_init(smem_addr(&drain), 1);
         abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // failure-path check (error[1] set by the host): a bounded wait on a barrier that nothing
+        // arrives on runs out before any copy or MMA is issued, and the block returns without work
+        if (__ldcg(error + 1)) bar_wait(smem_addr(&drain), 1u, &abort_s);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tslot)),
@@ -420,10 +425,7 @@ int tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     const int nrc = (B + RC - 1) / RC;
     const int64_t segs = tr.nboxes * nrc * S::NKC * (S::A_CH / 16);
     LSPR_TRY(ctx, ctx->tc_img.ensure((size_t)segs * 32));
-    if (!ctx->dev_err.p) {
-        LSPR_TRY(ctx, ctx->dev_err.ensure(1));
-        LSPR_TRY(ctx, cudaMemsetAsync(ctx->dev_err.p, 0, sizeof(int), ctx->stream));
-    }
+    if (!ctx->dev_err.p) return LSPR_E_STATE;
     LSPR_TRY(ctx, allow_smem(m2p_tc_kernel<P, RC>, S::SMEM, ctx->device, smem_set));
     ++ctx->n_launches;   // the image; the caller counts the M2P launch
     const unsigned gi =

@@ -104,6 +104,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         bar_init(smem_addr(&drain), 1);
         abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // failure-path check (error[1] set by the host): a bounded wait on a barrier that nothing
+        // arrives on runs out before any copy or MMA is issued, and the block returns without work
+        if (__ldcg(error + 1)) bar_wait(smem_addr(&drain), 1u, &abort_s);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tslot)),
@@ -336,10 +339,7 @@ int tc_p2p(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B) {
     static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
     if (tr.n_tcp_items == 0) return LSPR_OK;
-    if (!ctx->dev_err.p) {
-        LSPR_TRY(ctx, ctx->dev_err.ensure(1));
-        LSPR_TRY(ctx, cudaMemsetAsync(ctx->dev_err.p, 0, sizeof(int), st));
-    }
+    if (!ctx->dev_err.p) return LSPR_E_STATE;
     LSPR_TRY(ctx, allow_smem(p2p_tc_kernel<RC>, S::SMEM, ctx->device, smem_set));
     const int nrc = (B + RC - 1) / RC;
     const unsigned grid =

@@ -227,7 +227,14 @@ static int far_part(lspr_ctx *ctx, int mode, const double2 *x, int B) {
         xt = ctx->xt.p;
     }
     LSPR_TRY_ST(launch_weights(ctx, prec, x, xt, N, B, S));
-    if (tree) {
+    if (tree && ctx->timing.enabled) {
+        // kernel timing: every far-field kernel on the main stream, one after another, so that
+        // the events around a launch measure that kernel alone (no overlap, no waiting)
+        LSPR_TRY_ST(launch_p2p(ctx, prec, ctx->tree.p2p_items.p, ctx->tree.n_p2p_items, ctx->acc.p, ctx->stream,
+                               ctx->counters.p, BS));
+        LSPR_TRY_ST(launch_p2m(ctx, prec, BS));
+        LSPR_TRY_ST(launch_m2p(ctx, prec, ctx->acc.p, ctx->counters.p + 1, BS));
+    } else if (tree) {
         // P2P on the side stream overlaps P2M -> M2P on the main stream; both add into acc
         LSPR_TRY(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream));
         LSPR_TRY(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));

@@ -29,6 +29,10 @@ _lock = threading.Lock()
 _lib = None
 
 
+TIMER_NAMES = ["p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh", "other", "p2p_fp64", "m2p_fp64",
+               "p2m_fp64", "weights", "p2p_ff", "m2p_ff", "p2m_ff", "unused"]
+
+
 class LsprError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
@@ -79,6 +83,8 @@ def lib():
             L.lspr_solve.argtypes = [_vp, _vp, _d, _d, _vp, _vp, _i32, ctypes.POINTER(SolveOpts), _vp, _vp,
                                      ctypes.POINTER(SolveStats)]
             L.lspr_get_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 7
+            L.lspr_get_timing_rhs.argtypes = [_vp, _vp]
+            L.lspr_get_tc_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 3
             L.lspr_set_timing.argtypes = [_vp, _i32]
             L.lspr_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
             L.lspr_get_timing.argtypes = [_vp, _vp, _vp]
@@ -89,11 +95,13 @@ def lib():
             L.lspr_graph_stats.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
             L.lspr_device_errors.argtypes = [_vp, ctypes.POINTER(_i32)]
             L.lspr_selftest_wait_timeout.argtypes = [_vp, ctypes.POINTER(_i32)]
+            L.lspr_selftest_gate_waits.argtypes = [_vp, _i32]
             L.lspr_set_charges.argtypes = [_vp, _vp, _i64, _vp]
             for f in ("lspr_create", "lspr_destroy", "lspr_mesh_upload", "lspr_tree_build", "lspr_matvec",
                       "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing", "lspr_launch_count",
                       "lspr_set_graphs", "lspr_graph_stats", "lspr_autotune", "lspr_set_tensor_cores",
-                      "lspr_device_errors", "lspr_selftest_wait_timeout", "lspr_set_charges"):
+                      "lspr_device_errors", "lspr_selftest_wait_timeout", "lspr_selftest_gate_waits",
+                      "lspr_set_charges", "lspr_get_tc_info", "lspr_get_timing_rhs"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -270,6 +278,12 @@ class Context:
         keys = ["n_panels", "n_sources", "n_near", "n_boxes", "n_p2p_items", "n_m2p_pairs", "n_p2p_pairs"]
         return {k: v.value for k, v in zip(keys, vals)}
 
+    def tc_info(self) -> dict:
+        """Sizes of the tensor-core work lists (0 until a product of several right-hand sides)."""
+        vals = [ctypes.c_int64() for _ in range(3)]
+        _check(lib().lspr_get_tc_info(self._h, *[ctypes.byref(v) for v in vals]), "lspr_get_tc_info", self._h)
+        return dict(zip(["m2p_units", "m2p_group_boxes", "p2p_group_sources"], [v.value for v in vals]))
+
     def launch_count(self) -> int:
         n = ctypes.c_int64(0)
         _check(lib().lspr_launch_count(self._h, ctypes.byref(n)), "lspr_launch_count", self._h)
@@ -324,6 +338,11 @@ class Context:
         _check(lib().lspr_selftest_wait_timeout(self._h, r), "lspr_selftest_wait_timeout", self._h)
         return {"succeeded": r[0], "abort": r[1], "ms": r[2]}
 
+    def selftest_gate_waits(self, enable: bool):
+        """While enabled, every tensor-core far-field kernel gives up at once through its bounded
+        wait (no work done, LSPR_E_TIMEOUT from the product or solve that launched it)."""
+        _check(lib().lspr_selftest_gate_waits(self._h, int(bool(enable))), "lspr_selftest_gate_waits", self._h)
+
     def graph_stats(self) -> dict:
         c, r = ctypes.c_int64(0), ctypes.c_int64(0)
         _check(lib().lspr_graph_stats(self._h, ctypes.byref(c), ctypes.byref(r)), "lspr_graph_stats", self._h)
@@ -336,6 +355,10 @@ class Context:
         ms = np.zeros(16)
         n = np.zeros(16, np.int64)
         _check(lib().lspr_get_timing(self._h, _host_ptr(ms), _host_ptr(n)), "lspr_get_timing", self._h)
-        names = ["p2p", "m2p", "p2m", "near_assembly", "gmres", "tree", "mesh", "other", "p2p_fp64", "m2p_fp64",
-                 "p2m_fp64", "weights", "p2p_ff", "m2p_ff", "p2m_ff", "unused"]
-        return {k: (float(a), int(b)) for k, a, b in zip(names, ms, n)}
+        return {k: (float(a), int(b)) for k, a, b in zip(TIMER_NAMES, ms, n)}
+
+    def timing_rhs(self) -> dict:
+        """Right-hand sides summed over the timed launches of each far-field slot."""
+        r = np.zeros(16, np.int64)
+        _check(lib().lspr_get_timing_rhs(self._h, _host_ptr(r)), "lspr_get_timing_rhs", self._h)
+        return {k: int(v) for k, v in zip(TIMER_NAMES, r)}

@@ -13,7 +13,13 @@ import bench  # noqa: E402
 from paper_1812_10722_gb300 import inputs as I  # noqa: E402
 
 
-def test_default_workload_is_the_20480_panel_sphere():
+def test_default_workload_is_the_batched_sweep():
+    # the metric's configuration: 81920 panels, 64 wavelengths in one batched solve
+    src = open(bench.__file__).read()
+    assert 'add_argument("--workload", default="sphere81920_sweep64"' in src
+
+
+def test_single_wavelength_workload_is_the_20480_panel_sphere():
     wl = bench.WORKLOADS["sphere20480"]
     v, t, surf = bench.workload_geometry(wl)
     assert len(t) == 20480 and surf is None
@@ -68,4 +74,27 @@ def test_work_counts(P):
     # a nonzero index (2 flops) and with an index >= 2 (1 flop), plus 3 to combine
     rec = sum(2 * sum(d >= 1 for d in k) + sum(d >= 2 for d in k) + 3 for k in _terms(P)[1:])
     assert bench.m2p_flops(P, 0) == 9 + rec
-    assert bench.p2p_flops(16) == 16 + 8 * 16
+    # G and dG/dn once per pair (18 flops), then 2 kernels x 2 real channels x 2 flops per right-hand side
+    assert bench.p2p_flops(16) == 18 + 8 * 16
+    assert bench.m2p_terms(P) == nt
+
+
+def test_tensor_core_m2p_bound():
+    # the three terms of the bound scale as stated: generation and SFU with the units of 32
+    # right-hand sides, MMAs with 3 products of 2 x 128 x 256 x 8 flops per K step of 8 terms
+    pk = {"bf16_tflops_sustained": 1741.2}
+    b = bench.m2p_tc_bound(7, 64, 1000, pk, 2070.0)
+    nt = 120
+    assert b["mufu_ops"] == 1000 * 2 * 256
+    assert b["mma_flops"] == 1000 * 2 * 3 * 2 * 128 * 256 * 8 * (nt // 8)
+    assert b["generation_flops"] == 1000 * 2 * 256 * bench.m2p_flops(7, 0)
+    assert b["bound_s"] == max(b["terms_s"].values())
+    b16 = bench.m2p_tc_bound(7, 16, 1000, pk, 2070.0)
+    assert b16["mma_flops"] == 1000 * 2 * 2 * 128 * 256 * 8 * (nt // 8)
+
+
+def test_oracle_rate_model():
+    wl = bench.WORKLOADS["sphere81920_sweep64"]
+    # 64 wavelengths, a product timed on 1000 of 81920 rows in 2 s, 40 oracle steps
+    v = bench.oracle_rate(wl, 2.0, 1000, 81920, 40)
+    assert np.isclose(v, 64 / (43 * 2.0 * 81.92))

@@ -654,6 +654,35 @@ def test_bounded_wait_gives_up(lspr):
         assert _rel(ytc[b], yfp[b]) < 1e-5, b
 
 
+def test_timed_out_wait_is_a_status(lspr):
+    # the same bounded wait inside the real tensor-core M2P: with the check enabled it runs out
+    # before any work is issued, and the product and the solve report LSPR_E_TIMEOUT (6); with
+    # it disabled again, the same context gives the complete product
+    v, t = I.icosphere(2, 10.0)
+    n = len(t)
+    lam = np.array([370.0, 390.0])
+    s = I.drude_eps(lam) / I.EPS_WATER
+    x = I.random_complex(2 * n, seed=44, batch=2)
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        ctx.tree_build(0.6, 4, 16)
+        y0 = ctx.matvec(x, s, "tree_fp32")
+        assert ctx.device_errors() == 0
+        ctx.selftest_gate_waits(True)
+        with pytest.raises(lspr.LsprError) as e:
+            ctx.matvec(x, s, "tree_fp32")
+        assert e.value.status == 6
+        assert ctx.device_errors() > 0
+        with pytest.raises(lspr.LsprError) as e:
+            ctx.solve(I.drude_eps(lam), I.EPS_WATER, lam, tol=1e-8, restart=2, maxiter=2, mode="tree_fp32")
+        assert e.value.status == 6
+        ctx.selftest_gate_waits(False)
+        nerr = ctx.device_errors()
+        y1 = ctx.matvec(x, s, "tree_fp32")
+        assert ctx.device_errors() == nerr
+    assert np.array_equal(y0, y1) or _rel(y0, y1) < 1e-12
+
+
 def test_tensor_core_solve(lspr):
     v, t = I.icosphere(3, 10.0)
     lam = I.wavelengths(360, 400, 12)

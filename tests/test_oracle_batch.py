@@ -42,3 +42,19 @@ def test_batch_several_surfaces(oracle):
     d2, s2, i2, rr, bad2 = oracle.solve_batch(v, t, e, I.EPS_WATER, lam, surf=surf, tol=1e-9, restart=9)
     assert bad1 == bad2 == 0 and np.array_equal(i1, i2)
     assert np.array_equal(s1, s2) and np.array_equal(d1, d2)
+
+
+def test_row_block_of_the_product(oracle):
+    # a block of rows of the product (used to time a bounded share of it) is those rows of the
+    # whole product, bit for bit, for one and several right-hand sides
+    v, t = I.icosphere(2, 10.0)
+    n = len(t)
+    lam = np.array([360.0, 380.0, 400.0])
+    s = I.drude_eps(lam) / I.EPS_WATER
+    x = I.random_complex(2 * n, seed=3, batch=3)
+    y = oracle.matvec(v, t, x, s)
+    yr = oracle.matvec_rows(v, t, x, s, (17, 101))
+    rows = np.r_[17:101, n + 17:n + 101]
+    assert np.array_equal(yr[:, rows], y[:, rows])
+    assert not np.any(np.delete(yr, rows, axis=1))
+    assert np.array_equal(oracle.matvec_rows(v, t, x[1], s[1], (0, n)), oracle.matvec(v, t, x[1], s[1]))
