@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     constexpr int NT = S::NT, NKC = S::NKC, NS = S::NS;
     extern __shared__ __align__(128) unsigned char tc_smem[];
     __shared__ __align__(8) uint64_t full_a[NS], full_b[NS], empty_s[NS];
-    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], ring_full[kUnitRing], ring_empty[kUnitRing], drain;
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], ring_full[kUnitRing], ring_empty[kUnitRing], drain, gate;
     __shared__ int64_t ring[kUnitRing];
     __shared__ uint32_t tslot;
     __shared__ volatile int abort_s;
@@ -150,9 +150,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         // failure-path check (error[1] set by the host): a bounded wait on a barrier that nothing
         // arrives on runs out before any copy or MMA is issued, and the block returns without work
-        if (__ldcg(error + 1)) bar_wait(smem_addr(&drain), 1u, &abort_s);
+        if (__ldcg(error + 1)) {
+            bar_init(smem_addr(&gate), 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            bar_wait(smem_addr(&gate), 0u, &abort_s);   // phase 0 never completes: no arrival
+        }
     }
     if (warp == 0) {
+        __syncwarp();   // lane 0 may come from the set-up above (and its bounded check wait)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tslot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
