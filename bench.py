@@ -240,6 +240,8 @@ def run_ours(args, wl, rank, world, local_rank):
     ctx = lspr.Context(local_rank, stream.cuda_stream)
     if args.no_tc:
         ctx.set_tensor_cores(False)
+    elif args.tc is not None:
+        ctx.set_tensor_cores(args.tc)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     tune = None
     if wl.get("autotune") and wl["mode"].startswith("tree"):
@@ -666,6 +668,8 @@ def run_matvecs(args, wl):
     ctx = lspr.Context(0, torch.cuda.current_stream().cuda_stream)
     if args.no_tc:
         ctx.set_tensor_cores(False)
+    elif args.tc is not None:
+        ctx.set_tensor_cores(args.tc)
     ctx.mesh_upload(verts, tris, wl["K"], wl["K_fine"], wl["N_k"])
     mode = args.matvec_mode or wl["mode"]
     if mode.startswith("tree"):
@@ -702,6 +706,8 @@ def run_profile(args, wl):
     t_d = torch.as_tensor(tris, device="cuda")
     stream = torch.cuda.current_stream()
     ctx = lspr.Context(0, stream.cuda_stream)
+    if args.tc is not None:
+        ctx.set_tensor_cores(args.tc)
     if args.no_graphs:
         ctx.set_graphs(False)   # ncu does not profile the kernels inside a graph's loop
     if args.no_tc:
@@ -747,6 +753,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="only the steps, in an NVTX range 'timed' (profiling)")
     ap.add_argument("--no-graphs", action="store_true", help="host-driven Arnoldi cycles (profiling)")
     ap.add_argument("--no-tc", action="store_true", help="FP32 M2P on the CUDA cores, not tcgen05")
+    ap.add_argument("--tc", type=int, default=None, help="tensor-core mask for several right-hand sides (1 M2P, 3 M2P+P2P)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.restart:

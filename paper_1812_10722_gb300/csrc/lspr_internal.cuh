@@ -42,7 +42,7 @@ constexpr double kInv4Pi = 0.079577471545947667884;   // 1 / (4 pi)
 constexpr int kTargetBlock = 64;                       // targets per interaction block (2 per lane)
 constexpr int kTcGroup = 4;        // target blocks per tensor-core M2P group (256 targets)
 constexpr int kTcGroupSeg = 32;    // boxes per tensor-core M2P work unit at most
-constexpr int kTcP2PSrc = 256;     // sources per tensor-core P2P work unit at most
+constexpr int kTcP2PSrc = 2048;    // sources per tensor-core P2P work unit at most
 constexpr int kMaxP = 8;                               // highest Taylor order compiled
 constexpr int kMaxDepth = 10;                          // octree levels below the root (10 bits per axis)
 constexpr int kMaxNk = 32;

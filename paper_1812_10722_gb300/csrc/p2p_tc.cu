@@ -1,28 +1,36 @@
 // P2P of several right-hand sides on the fifth-generation tensor cores (tcgen05).
 //
-// The direct far-rule sum of a target x over sources y_s with weights w_s (per right-hand
-// side: V re, V im from the single layer, K re, K im from the double layer),
-//   D[4 j + c][x] += G(x, y_s) w_s[j].c (c = 0, 1),  dG/dn(x, y_s) w_s[j].c (c = 2, 3),
-// is a matrix product once the kernel values are laid out as an operand: K = 16 per stage,
-// columns 0..7 hold G of eight sources and columns 8..15 their dG/dn; A (the weights) has the
-// V channels in columns 0..7 and the K channels in columns 8..15 (the other half is zero), B
-// (the kernel tile, generated in registers by one thread per target) has the 256 targets of a
-// group of four target blocks as N.  The group walks the union of its blocks' P2P source
-// ranges; a target whose block does not sum a range gets zero kernel values there, and a
-// target's own panel is skipped (its exact integral is in the near correction), as in
-// p2p_kernel.  Operands are split into TF32 high and low parts: with 16 right-hand sides the
-// high and low weights are the two halves of one 128-row operand (two MMAs per K step give
-// all four products, the epilogue adds both halves), with 32 the three 3xTF32 products.
+// The direct far-rule sums of Eq. summation for a target x over sources y_s,
+//   V_j(x) = sum_s G(x, y_s) q_s[j],   K_j(x) = sum_s dG/dn(x, y_s) mu_s[j],
+// (q, mu complex per right-hand side j) are two matrix products once the kernel values of a
+// tile are laid out as operands:
+//   D_V[channel][target] += W_V[channel][source] G[source][target]
+//   D_K[channel][target] += W_K[channel][source] dG/dn[source][target]
+// with the channels (re and im of each of up to 64 right-hand sides: 128 rows) as the MMA's M,
+// the 256 targets of a group of four consecutive 64-target blocks as its N, and 8 sources per
+// pipeline stage as its K.  W_V holds only single-layer weights and W_K only double-layer ones,
+// so no operand carries structural zeros, and one kernel tile serves 64 right-hand sides.
+// The group walks the union of its blocks' P2P source ranges; a target whose block does not sum
+// a range gets zero kernel values there, and a target's own panel is skipped (its exact integral
+// is in the near correction), as in p2p_kernel.  Both operands are split into TF32 high and low
+// parts with FP32 accumulation in tensor memory: with more than 32 right-hand sides in the unit,
+// three MMAs per operand pair give W_hi G_hi + W_hi G_lo + W_lo G_hi (3xTF32); with at most 32,
+// W_hi and W_lo are the two halves of one 128-row operand and two MMAs give all four products
+// (the epilogue adds both halves).
 //
-// Roles (persistent, one CTA per SM): warps 0-7 generate both operands of every stage and
-// drain each unit's accumulator behind the next unit's first stage; warp 8 (one lane) fetches
-// work units into a small ring; warp 9 (one lane) issues the MMAs into one of two 256-column
-// TMEM accumulators.  Every wait is bounded as in the tensor-core M2P.
-//
-// Opt-in (lspr_set_tensor_cores bit 1): on this GPU the generation of the kernel tile (one
-// thread per target, 8 warps) bounds it, and a group's union of source ranges holds about
-// 1.7x the pairs of its blocks' own lists, so at 16 right-hand sides it is slower than
-// p2p_kernel (1.40 ms against 0.94 ms per product on the 20480-panel sphere).
+// Roles (persistent, one CTA per SM, both accumulators in the SM's 512 tensor-memory columns):
+//   warps 0-7 (one thread per target of the group) generate G and dG/dn of every stage in
+//     registers, split them and write the B operands; warps 0-3 also stage the split weights
+//     (the A operands) from the source weights; after the first stage of the next unit they
+//     drain the finished unit's accumulators (tcgen05.ld) into the FP64 accumulators;
+//   warp 8 (one lane) fetches work units into a small ring;
+//   warp 9 (one lane) issues the MMAs of each stage once it is written, commits to the stage's
+//     "empty" barrier and, at the end of a unit, to the accumulator barrier.
+// Every wait is bounded (about a second): one that runs out raises an abort flag that the
+// other roles see, the block drains its MMAs in flight, frees its tensor memory and returns,
+// and the context's device error count (error[0]) records it.  With error[1] set, thread 0
+// first waits on a barrier that nothing arrives on, so that the wait runs out before any work
+// is issued (the host's check of this failure path).
 #include "farfield.cuh"
 #include "tcgen05.cuh"
 
@@ -32,34 +40,32 @@ namespace {
 
 using namespace tc;
 
-constexpr int kSrc = 8;                        // sources per stage
-constexpr int kKC = 2 * kSrc;                  // K per stage: G then dG/dn of the sources
+constexpr int kSrc = 8;                        // sources per stage (the MMA's K)
+constexpr int kRC = 64;                        // right-hand sides per work unit
 constexpr int kTcN = kTcGroup * kTargetBlock;  // targets per work unit (the MMA's N)
-constexpr int kChunkSBO = (kKC / 4) * 128;     // bytes per 8-row group of a stage operand
+constexpr int kSBO = (kSrc / 4) * 128;         // bytes per 8-row group of a stage operand
 constexpr int kGenWarps = kTcN / 32;           // one thread per target
 constexpr int kProdWarp = kGenWarps, kMmaWarp = kGenWarps + 1;
 constexpr int kTcThreads = 32 * (kGenWarps + 2);
 constexpr int kUnitRing = 4;
 constexpr int kRingConsumers = kGenWarps + 1;  // lane 0 of each consumer warp
-constexpr uint32_t kTmemCols = 2 * kTcN;       // two accumulators
-static_assert(kTmemCols <= 512 && kTcN <= 256, "one MMA spans the group");
+constexpr uint32_t kTmemCols = 2 * kTcN;       // D_V in columns [0, 256), D_K in [256, 512)
+constexpr int kAPart = (128 / 8) * kSBO;       // one split part of a weight operand (128 rows)
+constexpr int kBPart = (kTcN / 8) * kSBO;      // one split part of a kernel operand (256 rows)
+// stage: W_V hi | W_V lo | W_K hi | W_K lo | G hi | G lo | dG hi | dG lo
+constexpr int kOffWV = 0, kOffWK = 2 * kAPart, kOffG = 4 * kAPart, kOffD = 4 * kAPart + 2 * kBPart;
+constexpr int kStage = 4 * kAPart + 4 * kBPart;
+constexpr int kStages = (200 * 1024) / kStage;
+constexpr int kSmem = kStages * kStage;
+constexpr uint32_t kIdesc = idesc_tf32(128, kTcN);
+static_assert(kTmemCols <= 512 && kTcN <= 256, "both accumulators fit the tensor memory");
+static_assert(kStages >= 2, "at least two stages");
+static_assert(kRC * 2 == 128, "re and im of the unit's right-hand sides fill the MMA's M");
 
-template <int RC>
-struct P2PShape {
-    static constexpr int ROWS = 4 * RC;
-    static constexpr bool STACKED = ROWS == 64;           // hi and lo weights as one operand
-    static constexpr uint32_t IDESC = idesc_tf32(128, kTcN);
-    static constexpr int A_CH = (ROWS / 8) * kChunkSBO;   // one split part of the weights
-    static constexpr int B_CH = (kTcN / 8) * kChunkSBO;   // one split part of the kernel tile
-    static constexpr int STAGE = 2 * A_CH + 2 * B_CH;     // A_hi | A_lo | B_hi | B_lo
-    static constexpr int NS = (200 * 1024) / STAGE;
-    static constexpr int SMEM = NS * STAGE;
-    static_assert(ROWS == 64 || ROWS == 128, "unit of 16 or 32 right-hand sides");
-    static_assert(kSrc * RC <= kTcN, "one weight per generating thread");
-};
-
+// byte offset of (row r, column k) inside one split part of a stage operand (K-major 8 x 16-byte
+// core matrices, no swizzle)
 __device__ __forceinline__ int core_off(int r, int k) {
-    return (r >> 3) * kChunkSBO + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+    return (r >> 3) * kSBO + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
 }
 
 __device__ __forceinline__ float4 f4_hi(const float4 v) {
@@ -69,34 +75,26 @@ __device__ __forceinline__ float4 f4_sub(const float4 a, const float4 b) {
     return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
 }
 
-template <int RC>
 __global__ void __launch_bounds__(kTcThreads, 1)
     p2p_tc_kernel(const int4 *__restrict__ items, int64_t nitems, const int4 *__restrict__ ivl, int B,
                   const float4 *__restrict__ tgt, int64_t ntgt, const float4 *__restrict__ spos,
                   const float4 *__restrict__ snrm, const float4 *__restrict__ sw, double *__restrict__ acc,
                   int *counter, int *error, const int *nact) {
-    using S = P2PShape<RC>;
-    constexpr int NS = S::NS;
     extern __shared__ __align__(128) unsigned char tc_smem[];
-    __shared__ __align__(8) uint64_t full_s[NS], empty_s[NS];
-    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], ring_full[kUnitRing], ring_empty[kUnitRing], drain, gate;
+    __shared__ __align__(8) uint64_t full_s[kStages], empty_s[kStages];
+    __shared__ __align__(8) uint64_t acc_full, acc_empty, ring_full[kUnitRing], ring_empty[kUnitRing], drain, gate;
     __shared__ int64_t ring[kUnitRing];
     __shared__ uint32_t tslot;
     __shared__ volatile int abort_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = smem_addr(tc_smem);
-    // the weight operand's structural zeros (V rows in the dG/dn columns, K rows in the G
-    // columns) are never written afterwards
-    for (int i = tid; i < S::SMEM / 16; i += kTcThreads) ((float4 *)tc_smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (tid == 0) {
-        for (int s = 0; s < NS; ++s) {
+        for (int s = 0; s < kStages; ++s) {
             bar_init(smem_addr(&full_s[s]), kTcN);   // one arrival per generating thread
             bar_init(smem_addr(&empty_s[s]), 1);     // the MMAs' commit
         }
-        for (int a = 0; a < 2; ++a) {
-            bar_init(smem_addr(&acc_full[a]), 1);
-            bar_init(smem_addr(&acc_empty[a]), kGenWarps);
-        }
+        bar_init(smem_addr(&acc_full), 1);
+        bar_init(smem_addr(&acc_empty), kGenWarps);
         for (int r = 0; r < kUnitRing; ++r) {
             bar_init(smem_addr(&ring_full[r]), 1);
             bar_init(smem_addr(&ring_empty[r]), kRingConsumers);
@@ -105,7 +103,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         // failure-path check (error[1] set by the host): a bounded wait on a barrier that nothing
-        // arrives on runs out before any copy or MMA is issued, and the block returns without work
+        // arrives on runs out before any work is issued, and the block returns without work
         if (__ldcg(error + 1)) {
             bar_init(smem_addr(&gate), 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -123,7 +121,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tslot;
     const int Bact = nact ? *nact : B;   // right-hand sides in use (the first Bact slots)
-    const int nbc = (Bact + RC - 1) / RC;
+    const int nbc = (Bact + kRC - 1) / kRC;
     const int64_t units = nitems * nbc;
 
     if (warp == kProdWarp) {
@@ -144,47 +142,55 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // ---- MMA issue: one lane
         if (lane == 0) {
             int64_t seq = 0;
-            int nu = 0;   // non-empty units so far (accumulator = nu & 1)
+            int nu = 0;   // units with stages so far
             for (int uc = 0;; ++uc) {
                 const int slot = uc % kUnitRing;
                 if (!bar_wait(smem_addr(&ring_full[slot]), (uint32_t)(uc / kUnitRing) & 1u, &abort_s)) break;
                 const int64_t u = ring[slot];
                 if (u >= units) break;
-                const int4 item = __ldg(items + u / nbc);
+                const int64_t ii = u / nbc;
+                const int nb = min(kRC, Bact - (int)(u - ii * nbc) * kRC);
+                const bool stacked = nb <= kRC / 2;
+                const int4 item = __ldg(items + ii);
                 if (item.y < item.z) {
-                    const int ab = nu & 1;
-                    if (nu >= 2 && !bar_wait(smem_addr(&acc_empty[ab]), (uint32_t)((nu >> 1) - 1) & 1u, &abort_s))
-                        break;
+                    // the accumulators are free once the previous unit is drained
+                    if (nu >= 1 && !bar_wait(smem_addr(&acc_empty), (uint32_t)((nu - 1) & 1), &abort_s)) break;
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t d = tmem + (uint32_t)(ab * kTcN);
+                    const uint32_t dv = tmem, dk = tmem + (uint32_t)kTcN;
                     bool ok = true, first = true;
                     for (int iv = item.y; iv < item.z && ok; ++iv) {
                         const int4 e = __ldg(ivl + iv);
                         for (int sb = e.x; sb < e.y; sb += kSrc, ++seq) {
-                            const int s = (int)(seq % NS);
-                            if (!bar_wait(smem_addr(&full_s[s]), (uint32_t)(seq / NS) & 1u, &abort_s)) {
+                            const int s = (int)(seq % kStages);
+                            if (!bar_wait(smem_addr(&full_s[s]), (uint32_t)(seq / kStages) & 1u, &abort_s)) {
                                 ok = false;
                                 break;
                             }
                             asm volatile("tcgen05.fence::after_thread_sync;");
-                            const uint32_t st = sbase + (uint32_t)(s * S::STAGE);
-#pragma unroll
-                            for (int ks = 0; ks < kKC / 8; ++ks) {
-                                const uint32_t off = ks * 256;   // two 16-byte column groups per K step of 8
-                                const uint64_t dah = umma_desc(st + off, 128, kChunkSBO);
-                                const uint64_t dal = umma_desc(st + S::A_CH + off, 128, kChunkSBO);
-                                const uint64_t dbh = umma_desc(st + 2 * S::A_CH + off, 128, kChunkSBO);
-                                const uint64_t dbl = umma_desc(st + 2 * S::A_CH + S::B_CH + off, 128, kChunkSBO);
-                                tc_mma(d, dah, dbh, S::IDESC, first ? 0u : 1u);
-                                first = false;
-                                tc_mma(d, dah, dbl, S::IDESC, 1u);
-                                if (!S::STACKED) tc_mma(d, dal, dbh, S::IDESC, 1u);
+                            const uint32_t st = sbase + (uint32_t)(s * kStage);
+                            const uint64_t wvh = umma_desc(st + kOffWV, 128, kSBO);
+                            const uint64_t wvl = umma_desc(st + kOffWV + kAPart, 128, kSBO);
+                            const uint64_t wkh = umma_desc(st + kOffWK, 128, kSBO);
+                            const uint64_t wkl = umma_desc(st + kOffWK + kAPart, 128, kSBO);
+                            const uint64_t gh = umma_desc(st + kOffG, 128, kSBO);
+                            const uint64_t gl = umma_desc(st + kOffG + kBPart, 128, kSBO);
+                            const uint64_t hh = umma_desc(st + kOffD, 128, kSBO);
+                            const uint64_t hl = umma_desc(st + kOffD + kBPart, 128, kSBO);
+                            const uint32_t on = first ? 0u : 1u;
+                            first = false;
+                            tc_mma(dv, wvh, gh, kIdesc, on);
+                            tc_mma(dv, wvh, gl, kIdesc, 1u);
+                            tc_mma(dk, wkh, hh, kIdesc, on);
+                            tc_mma(dk, wkh, hl, kIdesc, 1u);
+                            if (!stacked) {
+                                tc_mma(dv, wvl, gh, kIdesc, 1u);
+                                tc_mma(dk, wkl, hh, kIdesc, 1u);
                             }
                             tc_commit(smem_addr(&empty_s[s]));
                         }
                     }
                     if (!ok) break;
-                    tc_commit(smem_addr(&acc_full[ab]));
+                    tc_commit(smem_addr(&acc_full));
                     ++nu;
                 }
                 bar_arrive(smem_addr(&ring_empty[slot]));
@@ -194,50 +200,62 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             drain_wait(smem_addr(&drain), 0u);
         }
     } else {
-        // ---- generators: thread tid owns target tid of the group (row tid of the kernel tile)
-        // and, for tid < 8 RC, the weight of source tid / RC and right-hand side tid % RC
+        // ---- generators: thread tid owns target tid of the group (row tid of the kernel
+        // operands); threads 0..127 also stage the weights of one right-hand side for four
+        // sources of each stage
         const int blk = tid / kTargetBlock;
-        const int wsl = tid / RC, wj = tid % RC;
         int64_t seq = 0;
         int nu = 0;
         bool pend = false;
-        int p_ab = 0, p_par = 0, p_b0 = 0, p_nb = 0;
+        int p_nb = 0, p_b0 = 0;
+        bool p_stacked = false;
         int64_t p_tbase = 0;
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4).. (channel rows) and the 128
+        // targets from column 128 (w / 4) of both accumulators; false: a wait ran out
         auto drain_acc = [&]() -> bool {
             const int qd = warp & 3, half = warp >> 2;
-            if (!warp_wait(smem_addr(&acc_full[p_ab]), (uint32_t)p_par, &abort_s)) return false;
+            if (!warp_wait(smem_addr(&acc_full), (uint32_t)((nu - 1) & 1), &abort_s)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            if ((32 * qd) % S::ROWS < 4 * p_nb) {
-                const int m = (32 * qd + lane) % S::ROWS, j = m >> 2, cpt = m & 3;
+            const int m = 32 * qd + lane;
+            // row m: without stacking re (m < 64) / im of right-hand side m % 64; stacked: re / im
+            // of m % 32 in the high (m < 64) or the low half
+            const int j = p_stacked ? (m & 31) : (m & 63);
+            const int cpt = p_stacked ? ((m >> 5) & 1) : (m >> 6);
+            const bool row_on = j < p_nb;
+            if (__any_sync(0xffffffffu, row_on)) {
 #pragma unroll 1
                 for (int c0 = 0; c0 < kTcN / 2; c0 += 32) {
                     const int64_t tc = p_tbase + half * (kTcN / 2) + c0 + lane;   // this lane's column's target
                     const int pc = tc < ntgt ? panel_of(tgt[tc].w) : -1;
+#pragma unroll 1
+                    for (int op = 0; op < 2; ++op) {   // D_V, then D_K
 #pragma unroll
-                    for (int h16 = 0; h16 < 32; h16 += 16) {
-                        uint32_t v[16];
-                        const uint32_t addr = tmem + ((uint32_t)(32 * qd) << 16) +
-                                              (uint32_t)(p_ab * kTcN + half * (kTcN / 2) + c0 + h16);
-                        asm volatile(
-                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-                            "%14,%15}, [%16];"
-                            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                              "=r"(v[14]), "=r"(v[15])
-                            : "r"(addr));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        for (int h16 = 0; h16 < 32; h16 += 16) {
+                            uint32_t v[16];
+                            const uint32_t addr = tmem + ((uint32_t)(32 * qd) << 16) +
+                                                  (uint32_t)(op * kTcN + half * (kTcN / 2) + c0 + h16);
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                                "%14,%15}, [%16];"
+                                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                                  "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                                : "r"(addr));
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                        for (int x = 0; x < 16; ++x) {
-                            const int p = __shfl_sync(0xffffffffu, pc, h16 + x);
-                            if (j < p_nb && p >= 0)
-                                atomicAdd(acc + 4 * ((int64_t)p * B + p_b0 + j) + cpt, (double)__uint_as_float(v[x]));
+                            for (int x = 0; x < 16; ++x) {
+                                const int p = __shfl_sync(0xffffffffu, pc, h16 + x);
+                                if (row_on && p >= 0)
+                                    atomicAdd(acc + 4 * ((int64_t)p * B + p_b0 + j) + 2 * op + cpt,
+                                              (double)__uint_as_float(v[x]));
+                            }
                         }
                     }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
-            if (lane == 0) bar_arrive(smem_addr(&acc_empty[p_ab]));
+            if (lane == 0) bar_arrive(smem_addr(&acc_empty));
             pend = false;
             return true;
         };
@@ -251,19 +269,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int64_t u = ring[slot];
             if (u >= units) break;
             const int64_t ii = u / nbc;
-            const int b0 = (int)(u - ii * nbc) * RC, nb = min(RC, Bact - b0);
+            const int b0 = (int)(u - ii * nbc) * kRC, nb = min(kRC, Bact - b0);
+            const bool stacked = nb <= kRC / 2;
             const int4 item = __ldg(items + ii);
             const int64_t tbase = (int64_t)item.x * kTcN;   // first target of the group
             const int64_t ti = tbase + tid;
             const bool live = ti < ntgt;
             const float4 q = live ? tgt[ti] : tgt[0];
             const int tp = live ? panel_of(q.w) : -1;
+            // weight staging (rows of the weight operands as documented at drain_acc): right-hand
+            // side wj at the sources of columns wk..wk+3; stacked units need threads 0..63 only
+            const bool wr = tid < 128 && (!stacked || tid < 64);
+            const int wj = stacked ? (tid & 31) : (tid & 31) + 32 * (tid >> 6);
+            const int wk = stacked ? 4 * (tid >> 5) : 4 * ((tid >> 5) & 1);
             for (int iv = item.y; iv < item.z && ok; ++iv) {
                 const int4 e = __ldg(ivl + iv);
                 const bool on = live && ((e.z >> blk) & 1);   // uniform over the warp but for the tail
                 for (int sb = e.x; sb < e.y && ok; sb += kSrc) {
-                    // the kernel tile row of this target: G and dG/dn of the stage's sources
-                    // the kernel tile row of this target: G and dG/dn of the stage's sources
+                    // the kernel operand row of this target: G and dG/dn of the stage's sources
                     float g[kSrc], h[kSrc];
 #pragma unroll
                     for (int k = 0; k < kSrc; ++k) {
@@ -278,36 +301,59 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             h[k] = (dx * n.x + dy * n.y + dz * n.z) * (r * r) * r;
                         }
                     }
-                    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (tid < kSrc * RC && sb + wsl < e.y && wj < nb) w = __ldg(sw + (int64_t)(sb + wsl) * B + b0 + wj);
-                    const int s = (int)(seq % NS);
-                    if (seq >= NS && !warp_wait(smem_addr(&empty_s[s]), (uint32_t)((seq / NS) - 1) & 1u, &abort_s)) {
+                    // the weights of right-hand side wj at the four sources from column wk
+                    float4 w[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        w[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (wr && wj < nb && sb + wk + i < e.y) w[i] = __ldg(sw + (int64_t)(sb + wk + i) * B + b0 + wj);
+                    }
+                    const int s = (int)(seq % kStages);
+                    if (seq >= kStages &&
+                        !warp_wait(smem_addr(&empty_s[s]), (uint32_t)((seq / kStages) - 1) & 1u, &abort_s)) {
                         ok = false;
                         break;
                     }
-                    unsigned char *ah = tc_smem + s * S::STAGE, *al = ah + S::A_CH;
-                    unsigned char *bh = ah + 2 * S::A_CH, *bl = bh + S::B_CH;
-                    if (tid < kSrc * RC) {
-                        // V channels (rows 4 j, 4 j + 1) in the G column of the source, K channels
-                        // (rows 4 j + 2, 4 j + 3) in its dG/dn column
-                        const float v[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int off = core_off(4 * wj + c, (c < 2 ? 0 : kSrc) + wsl);
-                            const float hi = tf32_hi(v[c]);
-                            *(float *)(ah + off) = hi;
-                            *(float *)(al + off) = v[c] - hi;
+                    unsigned char *stg = tc_smem + s * kStage;
+                    if (wr) {
+                        const float4 vre = make_float4(w[0].x, w[1].x, w[2].x, w[3].x);
+                        const float4 vim = make_float4(w[0].y, w[1].y, w[2].y, w[3].y);
+                        const float4 kre = make_float4(w[0].z, w[1].z, w[2].z, w[3].z);
+                        const float4 kim = make_float4(w[0].w, w[1].w, w[2].w, w[3].w);
+                        const float4 vreh = f4_hi(vre), vimh = f4_hi(vim), kreh = f4_hi(kre), kimh = f4_hi(kim);
+                        unsigned char *av = stg + kOffWV, *ak = stg + kOffWK;
+                        if (stacked) {
+                            // rows: re hi wj, im hi 32 + wj, re lo 64 + wj, im lo 96 + wj
+                            *(float4 *)(av + core_off(wj, wk)) = vreh;
+                            *(float4 *)(av + core_off(32 + wj, wk)) = vimh;
+                            *(float4 *)(av + core_off(64 + wj, wk)) = f4_sub(vre, vreh);
+                            *(float4 *)(av + core_off(96 + wj, wk)) = f4_sub(vim, vimh);
+                            *(float4 *)(ak + core_off(wj, wk)) = kreh;
+                            *(float4 *)(ak + core_off(32 + wj, wk)) = kimh;
+                            *(float4 *)(ak + core_off(64 + wj, wk)) = f4_sub(kre, kreh);
+                            *(float4 *)(ak + core_off(96 + wj, wk)) = f4_sub(kim, kimh);
+                        } else {
+                            // rows: re wj, im 64 + wj; the high part, then the low part
+                            *(float4 *)(av + core_off(wj, wk)) = vreh;
+                            *(float4 *)(av + core_off(64 + wj, wk)) = vimh;
+                            *(float4 *)(av + kAPart + core_off(wj, wk)) = f4_sub(vre, vreh);
+                            *(float4 *)(av + kAPart + core_off(64 + wj, wk)) = f4_sub(vim, vimh);
+                            *(float4 *)(ak + core_off(wj, wk)) = kreh;
+                            *(float4 *)(ak + core_off(64 + wj, wk)) = kimh;
+                            *(float4 *)(ak + kAPart + core_off(wj, wk)) = f4_sub(kre, kreh);
+                            *(float4 *)(ak + kAPart + core_off(64 + wj, wk)) = f4_sub(kim, kimh);
                         }
                     }
+                    unsigned char *bg = stg + kOffG, *bd = stg + kOffD;
 #pragma unroll
                     for (int k4 = 0; k4 < kSrc / 4; ++k4) {
                         const float4 gv = make_float4(g[4 * k4], g[4 * k4 + 1], g[4 * k4 + 2], g[4 * k4 + 3]);
                         const float4 hv = make_float4(h[4 * k4], h[4 * k4 + 1], h[4 * k4 + 2], h[4 * k4 + 3]);
-                        const float4 gh = f4_hi(gv), hh = f4_hi(hv);
-                        *(float4 *)(bh + core_off(tid, 4 * k4)) = gh;
-                        *(float4 *)(bl + core_off(tid, 4 * k4)) = f4_sub(gv, gh);
-                        *(float4 *)(bh + core_off(tid, kSrc + 4 * k4)) = hh;
-                        *(float4 *)(bl + core_off(tid, kSrc + 4 * k4)) = f4_sub(hv, hh);
+                        const float4 gh4 = f4_hi(gv), hh4 = f4_hi(hv);
+                        *(float4 *)(bg + core_off(tid, 4 * k4)) = gh4;
+                        *(float4 *)(bg + kBPart + core_off(tid, 4 * k4)) = f4_sub(gv, gh4);
+                        *(float4 *)(bd + core_off(tid, 4 * k4)) = hh4;
+                        *(float4 *)(bd + kBPart + core_off(tid, 4 * k4)) = f4_sub(hv, hh4);
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_arrive(smem_addr(&full_s[s]));
@@ -319,11 +365,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (!ok) break;
             if (item.y < item.z) {
                 pend = true;
-                p_ab = nu & 1;
-                p_par = (nu >> 1) & 1;
                 p_tbase = tbase;
                 p_b0 = b0;
                 p_nb = nb;
+                p_stacked = stacked;
                 ++nu;
             }
             __syncwarp();
@@ -338,30 +383,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (tid == 0 && abort_s) atomicAdd(error, 1);
 }
 
-template <int RC>
-int tc_p2p(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B) {
-    using S = P2PShape<RC>;
-    static int smem_set[kSmemDevices] = {};
-    Tree &tr = ctx->tree;
-    if (tr.n_tcp_items == 0) return LSPR_OK;
-    if (!ctx->dev_err.p) return LSPR_E_STATE;
-    LSPR_TRY(ctx, allow_smem(p2p_tc_kernel<RC>, S::SMEM, ctx->device, smem_set));
-    const int nrc = (B + RC - 1) / RC;
-    const unsigned grid =
-        (unsigned)std::max<int64_t>(1, std::min<int64_t>(tr.n_tcp_items * nrc, std::max(1, ctx->num_sms)));
-    p2p_tc_kernel<RC><<<grid, kTcThreads, S::SMEM, st>>>(tr.tcp_items.p, tr.n_tcp_items, tr.tcp_ivl.p, B,
-                                                        Views<float>::tgt(ctx), ctx->mesh.N, Views<float>::spos(ctx),
-                                                        Views<float>::snrm(ctx), Views<float>::w(ctx), acc, counter,
-                                                        ctx->dev_err.p, ctx->rhs_nact);
-    return LSPR_OK;
-}
-
 }  // namespace
 
 // FP32 tree P2P of B >= 2 right-hand sides on the tensor cores
 int p2p_tc_launch(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B) {
-    if (!ctx->tree.tcp_built) LSPR_TRY_ST(tree_tc_lists(ctx, true));
-    return B <= 16 ? tc_p2p<16>(ctx, acc, st, counter, B) : tc_p2p<32>(ctx, acc, st, counter, B);
+    static int smem_set[kSmemDevices] = {};
+    Tree &tr = ctx->tree;
+    if (!tr.tcp_built) LSPR_TRY_ST(tree_tc_lists(ctx, true));
+    if (tr.n_tcp_items == 0) return LSPR_OK;
+    if (!ctx->dev_err.p) return LSPR_E_STATE;
+    LSPR_TRY(ctx, allow_smem(p2p_tc_kernel, kSmem, ctx->device, smem_set));
+    const int nrc = (B + kRC - 1) / kRC;
+    const unsigned grid =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(tr.n_tcp_items * nrc, std::max(1, ctx->num_sms)));
+    p2p_tc_kernel<<<grid, kTcThreads, kSmem, st>>>(tr.tcp_items.p, tr.n_tcp_items, tr.tcp_ivl.p, B,
+                                                  Views<float>::tgt(ctx), ctx->mesh.N, Views<float>::spos(ctx),
+                                                  Views<float>::snrm(ctx), Views<float>::w(ctx), acc, counter,
+                                                  ctx->dev_err.p, ctx->rhs_nact);
+    return LSPR_OK;
 }
 
 }  // namespace lspr

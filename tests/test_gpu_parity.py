@@ -50,6 +50,18 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def _rowmax(a, b):
+    """Largest error of one element against the largest magnitude: max_i |a_i - b_i| / max_i |b_i|."""
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def _agree(a, b, tol, what=""):
+    """a matches b in the relative L2 norm and element by element (no single row may carry an
+    error the norm would average away)."""
+    e2, ei = _rel(a, b), _rowmax(a, b)
+    assert e2 < tol and ei < tol, f"{what} relative L2 {e2:.3e}, largest element error {ei:.3e} (tol {tol:g})"
+
+
 @pytest.mark.parametrize("name", list(MESHES))
 def test_near_classification_exact(lspr, oracle, name):
     v, t = MESHES[name]()
@@ -78,7 +90,7 @@ def test_matvec_direct(lspr, oracle, name, mode, tol):
     with lspr.Context(0) as ctx:
         ctx.mesh_upload(v, t, N_k=NK.get(name, 9))
         y = ctx.matvec(x, s, mode)
-    assert _rel(y, yo) < tol
+    _agree(y, yo, tol, name)
 
 
 def test_self_integral_converges_in_Nk(lspr, oracle):
@@ -114,7 +126,7 @@ def test_matvec_tree(lspr, oracle, name, mode, ncrit):
         info = ctx.info()
         y = ctx.matvec(x, s, mode)
     assert info["n_boxes"] >= 1
-    assert _rel(y, yo) < 1e-4
+    _agree(y, yo, 1e-4, name)
 
 
 def test_tree_error_falls_with_order(lspr, oracle):
@@ -146,7 +158,7 @@ def test_batched_matvec_and_device_pointers(lspr, oracle):
         y_host = ctx.matvec(x, s, "tree_fp32")
         y_dev = ctx.matvec(torch.as_tensor(x, device="cuda"), s, "tree_fp32").cpu().numpy()
     for b in range(3):
-        assert _rel(y_host[b], yo[b]) < 1e-4
+        _agree(y_host[b], yo[b], 1e-4, b)
     # same product through device pointers; the FP32 far field accumulates with atomics
     # in a run-dependent order, so the two agree to FP32 rounding, not bit for bit
     assert _rel(y_dev, y_host) < 1e-6
@@ -265,31 +277,69 @@ def test_errors_are_status_codes(lspr):
 
 
 @pytest.mark.slow
-def test_full_size_sampled_rows_and_sigma(lspr, oracle):
-    # 20480-panel sphere, treecode P = 6, theta = 0.5, Ncrit = 300 (the benchmark's configuration)
+def _sampled_rows(oracle, v, t, x, s, blocks):
+    """The oracle's product on blocks of 64 rows (top and bottom rows of those panels)."""
+    n = len(t)
+    idx, ref = [], []
+    for i0 in blocks:
+        yo = oracle.matvec_rows(v, t, x, s, (i0, i0 + 64))
+        rows = np.r_[i0:i0 + 64, n + i0:n + i0 + 64]
+        idx.append(rows)
+        ref.append(yo[..., rows])
+    return np.concatenate(idx), np.concatenate(ref, axis=-1)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("tree", [(0.4, 5, 256), (0.5, 6, 300)])
+def test_full_size_20480_rows_and_sigma(lspr, oracle, tree):
+    # 20480-panel sphere at the tree the autotuner picks for the one-wavelength workload
+    # (theta 0.4, P 5, Ncrit 256) and at the configuration's literal one: 256 rows (four blocks
+    # of 64 across the Morton order) element by element against the oracle's rows; sigma_ext
+    # of the refined FP32 solve against the oracle's stored solve
     v, t = I.icosphere(5, 10.0)
     n = len(t)
     s = I.drude_eps(380.0) / I.EPS_WATER
     x = I.random_complex(2 * n, seed=4)
-    rows = np.random.default_rng(0).choice(n, 48, replace=False)
+    rows, yo = _sampled_rows(oracle, v, t, x, s, [0, n // 3, 2 * n // 3, n - 64])
     with lspr.Context(0) as ctx:
         ctx.mesh_upload(v, t)
-        ctx.tree_build(0.5, 6, 300)
+        ctx.tree_build(*tree)
         y = ctx.matvec(x, s, "tree_fp32")
         r = ctx.solve(I.drude_eps(380.0), I.EPS_WATER, 380.0, tol=1e-6, mode="tree_fp32", refine=True, restart=50)
-    num = den = 0.0
-    for i in rows:
-        V, K = oracle.entries(v, t, rows=(int(i), int(i) + 1))
-        kp, vd = K[0] @ x[:n], V[0] @ x[n:]
-        top = 0.5 * x[i] + kp - vd
-        bot = 0.5 * x[i] - kp + s * vd
-        num += abs(y[i] - top) ** 2 + abs(y[n + i] - bot) ** 2
-        den += abs(top) ** 2 + abs(bot) ** 2
-    assert (num / den) ** 0.5 < 1e-4
-    gold = os.path.join(GOLD, "sphere20480_l380.json")
-    if os.path.exists(gold):
-        g = _golden("sphere20480_l380.json")
-        assert abs(r.sigma_ext[0] - g["sigma_ext_nm2"]) / g["sigma_ext_nm2"] < 1e-3
+    _agree(y[rows], yo, 1e-4, tree)
+    g = _golden("sphere20480_l380.json")
+    err = abs(r.sigma_ext[0] - g["sigma_ext_nm2"]) / g["sigma_ext_nm2"]
+    # the tuned tree meets the metric's 1e-4; the literal P = 6, theta = 0.5 tree truncates
+    # at ~7e-4 (the reason the bench tunes it)
+    assert err < (1e-4 if tree == (0.4, 5, 256) else 1e-3), err
+
+
+@pytest.mark.slow
+def test_full_size_81920_sweep(lspr, oracle):
+    # the 64-wavelength sweep on the 81920-panel sphere at the tree the autotuner picks for it
+    # (theta 0.4, P 7, Ncrit 512), tensor-core far field for 64 right-hand sides: 256 rows of
+    # the 64-right-hand-side product element by element against the oracle's rows, then the
+    # batched refined solve's sigma_ext against the oracle's stored solves at four wavelengths
+    # (nearest the resonance, both ends, the middle)
+    v, t = I.icosphere(6, 10.0)
+    n = len(t)
+    lam = I.wavelengths(350, 420, 64)
+    ep = I.drude_eps(lam)
+    s = ep / I.EPS_WATER
+    x = I.random_complex(2 * n, seed=6, batch=64)
+    rows, yo = _sampled_rows(oracle, v, t, x, s, [0, n // 3, 2 * n // 3, n - 64])
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        ctx.tree_build(0.4, 7, 512)
+        y = ctx.matvec(x, s, "tree_fp32")
+        for b in range(64):
+            _agree(y[b][rows], yo[b], 1e-4, b)
+        r = ctx.solve(ep, I.EPS_WATER, lam, tol=1e-6, mode="tree_fp32", refine=True, restart=50, maxiter=2000)
+        assert ctx.device_errors() == 0
+    g = _golden("sphere81920_sweep64.json")
+    for k, ref in zip(g["sweep_index"], g["sigma_ext_nm2"]):
+        err = abs(r.sigma_ext[k] - ref) / ref
+        assert err < 1e-4, (lam[k], err)
 
 
 @pytest.mark.parametrize("mode,tol", [("direct_fp64", 1e-6), ("direct_fp32", 1e-5), ("tree_fp64", 1e-4),
@@ -308,7 +358,7 @@ def test_batched_matvec_ragged_chunks(lspr, oracle, mode, tol):
         y = ctx.matvec(x, s, mode)
         y1 = ctx.matvec(x[5], s[5], mode)
     for b in range(11):
-        assert _rel(y[b], yo[b]) < tol, b
+        _agree(y[b], yo[b], tol, b)
     # a batched column equals the single-RHS product (in FP32 modes up to FP32-level rounding:
     # several right-hand sides take the tensor-core M2P, one takes the FP32 pipe)
     assert _rel(y[5], y1) < (1e-6 if mode.endswith("fp64") else 1e-5)
@@ -460,8 +510,8 @@ def test_multi_surface_matvec(lspr, oracle, mode, tol):
         y = ctx.matvec(x, s, mode)
         y1 = ctx.matvec(x[1], s[1], mode)
     for b in range(3):
-        assert _rel(y[b], yo[b]) < tol, b
-    assert _rel(y1, yo[1]) < tol
+        _agree(y[b], yo[b], tol, b)
+    _agree(y1, yo[1], tol, "single")
 
 
 @pytest.mark.parametrize("graphs", [True, False])
@@ -576,7 +626,7 @@ def test_lossy_host_matches_oracle(lspr, oracle):
     assert np.max(np.abs(r.sigma_ext - so) / so) < 1e-6
 
 
-@pytest.mark.parametrize("P,B", [(5, 5), (6, 16), (7, 40), (8, 20), (3, 2)])
+@pytest.mark.parametrize("P,B", [(5, 5), (6, 16), (7, 40), (8, 20), (3, 2), (7, 64), (5, 70)])
 def test_tensor_core_m2p_matches_fp32_pipe(lspr, oracle, P, B):
     # 3xTF32 products on the tensor cores give the FP32-pipe M2P's sums to FP32-level rounding
     # (the low parts are truncated to TF32: ~2^-21 per product, a few 1e-6 over the sum, inside
@@ -600,13 +650,14 @@ def test_tensor_core_m2p_matches_fp32_pipe(lspr, oracle, P, B):
         yfp = ctx.matvec(x, s, "tree_fp32")
         y64 = ctx.matvec(x, s, "tree_fp64")
     for b in range(B):
-        assert _rel(ytc2[b], ytc[b]) < 1e-6, b
-        assert _rel(ytp[b], yfp[b]) < 1e-5, b
-        assert _rel(ytc[b], y64[b]) < 1e-5, b
-        assert _rel(ytc[b], yfp[b]) < 1e-5, b
+        _agree(ytc2[b], ytc[b], 1e-6, b)
+        _agree(ytp[b], yfp[b], 1e-5, b)
+        _agree(ytc[b], y64[b], 1e-5, b)
+        _agree(ytc[b], yfp[b], 1e-5, b)
     if P == 6:
         yo = oracle.matvec(v, t, x[:3], s[:3])
-        assert max(_rel(ytc[b], yo[b]) for b in range(3)) < 1e-4
+        for b in range(3):
+            _agree(ytc[b], yo[b], 1e-4, b)
 
 
 @pytest.mark.parametrize("B", [3, 24])
@@ -629,8 +680,8 @@ def test_tensor_core_m2p_partial_group(lspr, B):
         ctx.set_tensor_cores(False)
         yfp = ctx.matvec(x, s, "tree_fp32")
     for b in range(B):
-        assert _rel(ytc[b], yfp[b]) < 1e-5, b
-        assert _rel(ytp[b], yfp[b]) < 1e-5, b
+        _agree(ytc[b], yfp[b], 1e-5, b)
+        _agree(ytp[b], yfp[b], 1e-5, b)
 
 
 def test_bounded_wait_gives_up(lspr):
@@ -680,7 +731,8 @@ def test_timed_out_wait_is_a_status(lspr):
         nerr = ctx.device_errors()
         y1 = ctx.matvec(x, s, "tree_fp32")
         assert ctx.device_errors() == nerr
-    assert np.array_equal(y0, y1) or _rel(y0, y1) < 1e-12
+    # the FP32 far field accumulates with atomics in a run-dependent order
+    assert _rel(y0, y1) < 1e-6
 
 
 def test_tensor_core_solve(lspr):
