@@ -98,10 +98,9 @@ def workload_eps(wl, lam):
 
 
 def resonance_peak(lam, sigma):
-    """Wavelength of the largest sigma_ext from a parabola through the 3 samples around it."""
-    k = int(np.clip(np.argmax(sigma), 1, len(sigma) - 2))
-    a, b, _ = np.polyfit(lam[k - 1:k + 2], sigma[k - 1:k + 2], 2)
-    return float(-b / (2 * a))
+    """Wavelength of the extinction peak (reciprocal-parabola vertex, sensitivity.peak_wavelength)."""
+    from paper_1812_10722_gb300.sensitivity import peak_wavelength
+    return peak_wavelength(lam, sigma)
 
 
 METRIC = "lambda-solves/s at sigma_ext rel err <= 1e-4 vs plain FP64 (treecode GMRES)"
@@ -738,6 +737,46 @@ def run_profile(args, wl):
     return out
 
 
+def run_study(args):
+    """Resonance-shift studies (builder runs, not the timed step): "sensitivity" = the 327680-panel
+    sphere with six analytes at gaps of 0.5/1/2/4 nm on +-x, +-y, +-z, 32 wavelengths over
+    370-400 nm each; "placement" = the 81920-panel sphere with two analytes at 1 nm on +-z, +-x
+    or +-y.  Treecode parameters from the autotuner on the first geometry (one wavelength, the
+    one nearest the resonance, coarse grid)."""
+    import torch
+    from paper_1812_10722_gb300 import lspr
+    from paper_1812_10722_gb300 import sensitivity as SN
+    lam = I.wavelengths(370, 400, 32)
+    if args.study == "sensitivity":
+        geoms = SN.gap_geometries([0.5, 1.0, 2.0, 4.0], sphere_sub=7)
+        sub = 7
+    else:
+        geoms = SN.axis_geometries(1.0, sphere_sub=6)
+        sub = 6
+    ctx = lspr.Context(0, torch.cuda.current_stream().cuda_stream)
+    if args.tc is not None:
+        ctx.set_tensor_cores(args.tc)
+    name0 = next(iter(geoms))
+    v, t, surf = geoms[name0]
+    S = int(surf.max()) + 1
+    lt = tuning_wavelengths(lam, 1)
+    e = np.full((1, S), 2.25 + 0j)
+    e[:, 0] = I.drude_eps(lt)
+    ctx.mesh_upload(v, t, surf_id=surf)
+    t0 = time.perf_counter()
+    tune = ctx.autotune(e, I.EPS_WATER, lt, target_rel_err=1e-4, tol=1e-8, restart=50, mode="tree_fp32", refine=1,
+                        coarse=True)
+    tune["seconds"] = round(time.perf_counter() - t0, 2)
+    tree = (tune["theta"], tune["P"], tune["Ncrit"])
+    t0 = time.perf_counter()
+    res = SN.shift_study(ctx, geoms, lam, sub, tree=tree)
+    out = {"study": args.study, "wavelengths": [float(lam[0]), float(lam[-1]), len(lam)], "tree": tree,
+           "autotune": tune, "seconds": round(time.perf_counter() - t0, 1), "results": res,
+           "device_errors": ctx.device_errors(), "tensor_cores": args.tc}
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -753,6 +792,8 @@ def main():
     ap.add_argument("--profile", action="store_true", help="only the steps, in an NVTX range 'timed' (profiling)")
     ap.add_argument("--no-graphs", action="store_true", help="host-driven Arnoldi cycles (profiling)")
     ap.add_argument("--no-tc", action="store_true", help="FP32 M2P on the CUDA cores, not tcgen05")
+    ap.add_argument("--study", default=None, choices=["sensitivity", "placement"],
+                    help="resonance-shift study instead of the timed step (builder runs)")
     ap.add_argument("--tc", type=int, default=None, help="tensor-core mask for several right-hand sides (1 M2P, 3 M2P+P2P)")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
@@ -767,6 +808,9 @@ def main():
         wl.update(theta=float(th), P=int(P), Ncrit=int(nc), autotune=False)
     if args.matvecs:
         print(json.dumps(run_matvecs(args, wl)))
+        return
+    if args.study:
+        print(json.dumps(run_study(args)))
         return
     if args.profile:
         print(json.dumps(run_profile(args, wl)))
