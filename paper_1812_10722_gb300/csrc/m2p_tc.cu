@@ -108,10 +108,10 @@ __global__ void tc_image_kernel(int64_t nbox, int B, int nrc, const float4 *__re
             if (t < S::NT && j < Bact) x = __ldg((const float *)(mom + (box * S::NT + t) * B + j) + cpt);
             v[u] = x;
         }
-        const float4 hi = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
+        const TfPair sp = tf32_split(make_float4(v[0], v[1], v[2], v[3]));
         unsigned char *dst = img + c * (2 * S::A_CH) + 16 * e;
-        *(float4 *)dst = hi;
-        *(float4 *)(dst + S::A_CH) = make_float4(v[0] - hi.x, v[1] - hi.y, v[2] - hi.z, v[3] - hi.w);
+        *(float4 *)dst = sp.hi;
+        *(float4 *)(dst + S::A_CH) = sp.lo;
     }
 }
 
@@ -387,10 +387,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             const int t = kc * kKC + 4 * t4 + w;
                             v[w] = t < NT ? a[t < NT ? t : 0] : 0.f;
                         }
-                        const float4 hi = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
-                        *(float4 *)(bh + core_off(tid, 4 * t4)) = hi;
-                        *(float4 *)(bl + core_off(tid, 4 * t4)) =
-                            make_float4(v[0] - hi.x, v[1] - hi.y, v[2] - hi.z, v[3] - hi.w);
+                        const TfPair sp = tf32_split(make_float4(v[0], v[1], v[2], v[3]));
+                        *(float4 *)(bh + core_off(tid, 4 * t4)) = sp.hi;
+                        *(float4 *)(bl + core_off(tid, 4 * t4)) = sp.lo;
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_arrive(smem_addr(&full_b[s]));

@@ -13,8 +13,9 @@
 // The group walks the union of its blocks' P2P source ranges; a target whose block does not sum
 // a range gets zero kernel values there, and a target's own panel is skipped (its exact integral
 // is in the near correction), as in p2p_kernel.  Both operands are split into TF32 high and low
-// parts with FP32 accumulation in tensor memory: with more than 32 right-hand sides in the unit,
-// three MMAs per operand pair give W_hi G_hi + W_hi G_lo + W_lo G_hi (3xTF32); with at most 32,
+// parts (each rounded to nearest) with FP32 accumulation in tensor memory: with more than 32
+// right-hand sides in the unit, three MMAs per operand pair give W_hi G_hi + W_hi G_lo +
+// W_lo G_hi (3xTF32); with at most 32,
 // W_hi and W_lo are the two halves of one 128-row operand and two MMAs give all four products
 // (the epilogue adds both halves).
 //
@@ -66,13 +67,6 @@ static_assert(kRC * 2 == 128, "re and im of the unit's right-hand sides fill the
 // core matrices, no swizzle)
 __device__ __forceinline__ int core_off(int r, int k) {
     return (r >> 3) * kSBO + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
-}
-
-__device__ __forceinline__ float4 f4_hi(const float4 v) {
-    return make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-}
-__device__ __forceinline__ float4 f4_sub(const float4 a, const float4 b) {
-    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -320,28 +314,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const float4 vim = make_float4(w[0].y, w[1].y, w[2].y, w[3].y);
                         const float4 kre = make_float4(w[0].z, w[1].z, w[2].z, w[3].z);
                         const float4 kim = make_float4(w[0].w, w[1].w, w[2].w, w[3].w);
-                        const float4 vreh = f4_hi(vre), vimh = f4_hi(vim), kreh = f4_hi(kre), kimh = f4_hi(kim);
+                        const TfPair svr = tf32_split(vre), svi = tf32_split(vim);
+                        const TfPair skr = tf32_split(kre), ski = tf32_split(kim);
                         unsigned char *av = stg + kOffWV, *ak = stg + kOffWK;
                         if (stacked) {
                             // rows: re hi wj, im hi 32 + wj, re lo 64 + wj, im lo 96 + wj
-                            *(float4 *)(av + core_off(wj, wk)) = vreh;
-                            *(float4 *)(av + core_off(32 + wj, wk)) = vimh;
-                            *(float4 *)(av + core_off(64 + wj, wk)) = f4_sub(vre, vreh);
-                            *(float4 *)(av + core_off(96 + wj, wk)) = f4_sub(vim, vimh);
-                            *(float4 *)(ak + core_off(wj, wk)) = kreh;
-                            *(float4 *)(ak + core_off(32 + wj, wk)) = kimh;
-                            *(float4 *)(ak + core_off(64 + wj, wk)) = f4_sub(kre, kreh);
-                            *(float4 *)(ak + core_off(96 + wj, wk)) = f4_sub(kim, kimh);
+                            *(float4 *)(av + core_off(wj, wk)) = svr.hi;
+                            *(float4 *)(av + core_off(32 + wj, wk)) = svi.hi;
+                            *(float4 *)(av + core_off(64 + wj, wk)) = svr.lo;
+                            *(float4 *)(av + core_off(96 + wj, wk)) = svi.lo;
+                            *(float4 *)(ak + core_off(wj, wk)) = skr.hi;
+                            *(float4 *)(ak + core_off(32 + wj, wk)) = ski.hi;
+                            *(float4 *)(ak + core_off(64 + wj, wk)) = skr.lo;
+                            *(float4 *)(ak + core_off(96 + wj, wk)) = ski.lo;
                         } else {
                             // rows: re wj, im 64 + wj; the high part, then the low part
-                            *(float4 *)(av + core_off(wj, wk)) = vreh;
-                            *(float4 *)(av + core_off(64 + wj, wk)) = vimh;
-                            *(float4 *)(av + kAPart + core_off(wj, wk)) = f4_sub(vre, vreh);
-                            *(float4 *)(av + kAPart + core_off(64 + wj, wk)) = f4_sub(vim, vimh);
-                            *(float4 *)(ak + core_off(wj, wk)) = kreh;
-                            *(float4 *)(ak + core_off(64 + wj, wk)) = kimh;
-                            *(float4 *)(ak + kAPart + core_off(wj, wk)) = f4_sub(kre, kreh);
-                            *(float4 *)(ak + kAPart + core_off(64 + wj, wk)) = f4_sub(kim, kimh);
+                            *(float4 *)(av + core_off(wj, wk)) = svr.hi;
+                            *(float4 *)(av + core_off(64 + wj, wk)) = svi.hi;
+                            *(float4 *)(av + kAPart + core_off(wj, wk)) = svr.lo;
+                            *(float4 *)(av + kAPart + core_off(64 + wj, wk)) = svi.lo;
+                            *(float4 *)(ak + core_off(wj, wk)) = skr.hi;
+                            *(float4 *)(ak + core_off(64 + wj, wk)) = ski.hi;
+                            *(float4 *)(ak + kAPart + core_off(wj, wk)) = skr.lo;
+                            *(float4 *)(ak + kAPart + core_off(64 + wj, wk)) = ski.lo;
                         }
                     }
                     unsigned char *bg = stg + kOffG, *bd = stg + kOffD;
@@ -349,11 +344,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int k4 = 0; k4 < kSrc / 4; ++k4) {
                         const float4 gv = make_float4(g[4 * k4], g[4 * k4 + 1], g[4 * k4 + 2], g[4 * k4 + 3]);
                         const float4 hv = make_float4(h[4 * k4], h[4 * k4 + 1], h[4 * k4 + 2], h[4 * k4 + 3]);
-                        const float4 gh4 = f4_hi(gv), hh4 = f4_hi(hv);
-                        *(float4 *)(bg + core_off(tid, 4 * k4)) = gh4;
-                        *(float4 *)(bg + kBPart + core_off(tid, 4 * k4)) = f4_sub(gv, gh4);
-                        *(float4 *)(bd + core_off(tid, 4 * k4)) = hh4;
-                        *(float4 *)(bd + kBPart + core_off(tid, 4 * k4)) = f4_sub(hv, hh4);
+                        const TfPair sg = tf32_split(gv), sh = tf32_split(hv);
+                        *(float4 *)(bg + core_off(tid, 4 * k4)) = sg.hi;
+                        *(float4 *)(bg + kBPart + core_off(tid, 4 * k4)) = sg.lo;
+                        *(float4 *)(bd + core_off(tid, 4 * k4)) = sh.hi;
+                        *(float4 *)(bd + kBPart + core_off(tid, 4 * k4)) = sh.lo;
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_arrive(smem_addr(&full_s[s]));

@@ -1,6 +1,7 @@
 // tcgen05 / mbarrier building blocks of the tensor-core far-field kernels (inline PTX):
 // shared-memory matrix and instruction descriptors for K-major TF32 operands without swizzle,
-// the TF32 high/low split, bounded mbarrier waits and the MMA / commit instructions.
+// the TF32 high/low split (both parts rounded to nearest), bounded mbarrier waits and the MMA /
+// commit instructions.
 #pragma once
 #include <cstdint>
 
@@ -19,7 +20,23 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// nearest TF32 value of x (round to nearest, ties away from zero).  A split x = hi + lo with
+// hi = tf32_rn(x) and lo = tf32_rn(x - hi) leaves |x - hi - lo| <= 2^-22 |x|, unbiased; the
+// products hi*hi + hi*lo + lo*hi of two split operands then miss only lo*lo (<= 2^-22 relative)
+__device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+struct TfPair {
+    float4 hi, lo;
+};
+__device__ __forceinline__ TfPair tf32_split(const float4 v) {
+    TfPair p;
+    p.hi = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+    p.lo = make_float4(tf32_rn(v.x - p.hi.x), tf32_rn(v.y - p.hi.y), tf32_rn(v.z - p.hi.z), tf32_rn(v.w - p.hi.w));
+    return p;
+}
 
 
 __device__ __forceinline__ uint64_t now_ns() {
