@@ -172,7 +172,9 @@ LSPR_API int lspr_matvec(lspr_ctx *ctx, const double *x, double *y, int32_t B, c
  * p = -eps_out * sum_j A_j (c_j dphi2s/dn_j - phi_j n_j) over the panels and
  * sigma_ext = Im(k^2 e.p / (eps_out |E0|)) / Re k with k = 2 pi sqrt(eps_out) / lambda
  * (E0 = 0 is allowed, e.g. for the response to point charges alone: the dipole is then the
- * result and sigma_ext, a ratio to |E0|, is not finite).
+ * result and sigma_ext, a ratio to |E0|, is not finite).  The dipole is taken about the
+ * coordinate origin: when point charges give surface 0 a net charge, the exterior field has a
+ * monopole part and the dipole moment depends on that choice of origin.
  * Returns LSPR_E_NOT_CONVERGED if any wavelength missed tol (results are still
  * written), LSPR_E_TIMEOUT if a bounded device wait ran out during the solve (results are
  * written but not trustworthy).  st may be null. */
@@ -303,15 +305,20 @@ LSPR_API int lspr_graph_stats(lspr_ctx *ctx, int64_t *cycles, int64_t *recording
  * cudaMalloc/cudaFree would stall (they can synchronise the device).  The call
  * uses no cudaMalloc, cudaFree or allocating library routine: its scratch
  * (source weights and accumulators) is one fixed device array of 1.5 MiB inside
- * the library, which every GPU that loads the library keeps until exit.
+ * the library, which every GPU that loads the library's device code keeps until
+ * exit (with lazy module loading the runtime creates it at the first call's
+ * address lookup, so that first call may allocate it; later calls do not).
  *   ctx        context with an uploaded mesh of at most 16384 panels and 65536
  *              far-rule sources (larger meshes: LSPR_E_ARG)
  *   x, y       device pointers on the context's device, [2N] complex each
  *   s          eps_in / eps_out (re, im)
  * The work is queued on the context's stream and is not synchronised on return.
- * The first call on a device looks up the array's device address (make it before
- * any stream capture).  All calls on a device share the array and leave their
- * contents in it; calls that overlap on the GPU race and must be serialised.
+ * The first call on a device looks up the array's device address and caches it
+ * for that device's primary context (make it before any stream capture; the
+ * cache does not survive cudaDeviceReset).  All calls on a device share the array
+ * and leave their contents in it; calls that overlap on the GPU race and must be
+ * serialised.  A tree build does not change the product (its Morton reordering of
+ * the sources and targets is taken into account).
  * Errors: LSPR_E_ARG, LSPR_E_STATE (no mesh, or a mesh of several surfaces), LSPR_E_CUDA. */
 LSPR_API int lspr_matvec_direct_fp32_noalloc(lspr_ctx *ctx, const double *x, double *y, double s_re, double s_im);
 

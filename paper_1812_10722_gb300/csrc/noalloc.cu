@@ -7,13 +7,19 @@
 // latency-critical loops in which cudaMalloc/cudaFree would stall, since those
 // calls can synchronise the whole device.  For them this entry point does the
 // same direct FP32 product with its scratch in one file-scope device array of
-// fixed size, reserved when the library is loaded, and never calls cudaMalloc,
-// cudaFree or an allocating library routine.
+// fixed size and never calls cudaMalloc, cudaFree or an allocating library routine.
 //
 // Set-up: the first call on a device, with that device current, resolves the
 // array's device address with cudaGetSymbolAddress and caches it for the device
-// (the host-side name of the array is not a device address).  Make that first
-// call before any stream capture begins.
+// (the host-side name of the array is not a device address).  The CUDA runtime
+// creates the array when it loads this library's device code onto the device; with
+// lazy module loading (the runtime's default) that happens during this first
+// lookup, so the first call may allocate the array itself (about 1.5 MiB) and the
+// calls after it do not.  Make that first call before any stream capture begins
+// and before the phase in which the caller cannot allow allocation.  The cached
+// address belongs to the device's primary context (the one the runtime API uses):
+// it does not survive cudaDeviceReset, and a context whose stream lives in another
+// CUDA context must not use this entry point.
 //
 // Sharing: every call on a device uses the same array and leaves its contents
 // behind; each call clears the accumulators it needs before use.  Calls that
