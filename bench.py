@@ -130,6 +130,42 @@ def m2p_flops(P: int, B: int = 1) -> int:
     return f + 8 * len(terms) * B
 
 
+def p2p_tc_bound(B: int, pairs: int, stages: int, peaks: dict, mhz: float) -> dict:
+    """Time bound of one tensor-core P2P launch: the largest of its G and dG/dn generation on the
+    FP32 pipe (the blocks' own pairs, once per unit of 64 right-hand sides), its rsqrt on the SFU,
+    and its issued MMAs on the tensor pipe (per stage of 8 sources: M = 128 channels x N = 256
+    targets x K = 8, for the single and the double layer, 3 products each above 32 right-hand
+    sides in the unit, 2 at 32 or fewer)."""
+    units = [min(64, B - b0) for b0 in range(0, B, 64)]
+    gen = pairs * P2P_GEN_FLOPS * len(units)
+    mufu = pairs * len(units)
+    mma = sum(stages * 2 * (3 if nb > 32 else 2) * 2 * 128 * 256 * 8 for nb in units)
+    fp32_peak = fp32_peak_tflops(mhz) * 1e12
+    sfu_peak = SFU_PER_CLK_SM * 152 * mhz * 1e6
+    tf32_peak = peaks.get("bf16_tflops_sustained", 1741.2) * TF32_PER_BF16 * 1e12
+    t = {"fp32_generation": gen / fp32_peak, "sfu": mufu / sfu_peak, "tensor_mma": mma / tf32_peak}
+    return {"terms_s": t, "bound_s": max(t.values()), "limiter": max(t, key=t.get), "mma_flops": mma,
+            "generation_flops": gen, "mufu_ops": mufu, "tf32_peak_tflops": tf32_peak / 1e12,
+            "fp32_peak_tflops": fp32_peak / 1e12, "sfu_peak_tops": sfu_peak / 1e12}
+
+
+def tc_roofline(bnd: dict, t: float, kernel: str, traffic) -> dict:
+    """Roofline entry of a tensor-core kernel from its max-of-three bound and launch time t (s)."""
+    lim = bnd["limiter"]
+    if lim == "tensor_mma":
+        a, pk, unit, bound = bnd["mma_flops"] / t / 1e12, bnd["tf32_peak_tflops"], "TFLOP/s", "tensor"
+    elif lim == "fp32_generation":
+        a, pk, unit, bound = bnd["generation_flops"] / t / 1e12, bnd["fp32_peak_tflops"], "TFLOP/s", "alu"
+    else:
+        a, pk, unit, bound = bnd["mufu_ops"] / t / 1e12, bnd["sfu_peak_tops"], "Top/s", "alu"
+    return {"bound": bound, "kernel": kernel, "achieved": round(a, 3), "peak": round(pk, 2), "unit": unit,
+            "frac": round(bnd["bound_s"] / t, 4), "traffic": traffic,
+            "bound_terms_ms": {x: round(1e3 * y, 4) for x, y in bnd["terms_s"].items()},
+            "peak_note": "frac = max(generation flops / FP32 peak (152 SM x 128 x 2 x 2070 MHz, derived), rsqrt / "
+                         "SFU peak (16 per clock per SM), issued TF32 MMA flops / TF32 peak (measured sustained "
+                         "bf16 x nominal 1.1/2.25)) / the launch time; achieved and peak are the limiting term's"}
+
+
 def m2p_terms(P: int) -> int:
     """Taylor terms with |k| <= P."""
     return (P + 1) * (P + 2) * (P + 3) // 6
@@ -433,7 +469,8 @@ def run_ours(args, wl, rank, world, local_rank):
     tgt_box = info["n_m2p_pairs"] * kernel_targets(info)
     fp32 = wl["mode"].endswith("fp32")
     peak_fp32 = fp32_peak_tflops(mhz)
-    m2p_tc = B > 1 and fp32 and not args.no_tc   # the FP32 M2P of several right-hand sides runs on tcgen05
+    m2p_tc = B > 1 and fp32 and not args.no_tc and (args.tc is None or args.tc & 1)   # M2P of several RHS on tcgen05
+    p2p_tc = B > 1 and fp32 and not args.no_tc and ctx_tc["p2p_stages"] > 0           # P2P of several RHS on tcgen05
 
     def work(name):
         """Algorithmic flops of all timed launches of a far-field slot."""
@@ -450,6 +487,7 @@ def run_ours(args, wl, rank, world, local_rank):
             k["algorithmic_tflops"] = work(name) / (k["ms_total"] * 1e-3) / 1e12
     if "p2p" in kernels:
         kernels["p2p"]["pairs_per_launch"] = pairs
+        kernels["p2p"]["path"] = "tcgen05 (TF32 hi/lo split, FP32 accumulation)" if p2p_tc else "FP32 pipe"
     if "m2p" in kernels:
         kernels["m2p"]["path"] = "tcgen05 (TF32 hi/lo split, FP32 accumulation)" if m2p_tc else "FP32 pipe"
     roof = None
@@ -463,23 +501,13 @@ def run_ours(args, wl, rank, world, local_rank):
                 "peak_note": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"}
     elif dom == "m2p" and m2p_tc:
         # max(generation / FP32 peak, rsqrt / SFU peak, issued MMA flops / TF32 peak) per launch
-        tc = ctx_tc
         k = kernels[dom]
-        bnd = m2p_tc_bound(wl["P"], round(krhs[dom] / k["launches"]), tc["m2p_group_boxes"], peaks, mhz)
-        t = k["ms_per_launch"] * 1e-3
-        lim = bnd["limiter"]
-        if lim == "tensor_mma":
-            a, pk, unit, bound = bnd["mma_flops"] / t / 1e12, bnd["tf32_peak_tflops"], "TFLOP/s", "tensor"
-        elif lim == "fp32_generation":
-            a, pk, unit, bound = bnd["generation_flops"] / t / 1e12, bnd["fp32_peak_tflops"], "TFLOP/s", "alu"
-        else:
-            a, pk, unit, bound = bnd["mufu_ops"] / t / 1e12, bnd["sfu_peak_tops"], "Top/s", "alu"
-        roof = {"bound": bound, "kernel": dom, "achieved": round(a, 3), "peak": round(pk, 2), "unit": unit,
-                "frac": round(bnd["bound_s"] / t, 4), "traffic": traffic,
-                "bound_terms_ms": {x: round(1e3 * y, 4) for x, y in bnd["terms_s"].items()},
-                "peak_note": "frac = max(generation flops / FP32 peak (152 SM x 128 x 2 x 2070 MHz, derived), rsqrt / "
-                             "SFU peak (16 per clock per SM), issued TF32 MMA flops / TF32 peak (measured sustained "
-                             "bf16 x nominal 1.1/2.25)) / the launch time; achieved and peak are the limiting term's"}
+        bnd = m2p_tc_bound(wl["P"], round(krhs[dom] / k["launches"]), ctx_tc["m2p_group_boxes"], peaks, mhz)
+        roof = tc_roofline(bnd, k["ms_per_launch"] * 1e-3, dom, traffic)
+    elif dom == "p2p" and p2p_tc:
+        k = kernels[dom]
+        bnd = p2p_tc_bound(round(krhs[dom] / k["launches"]), pairs, ctx_tc["p2p_stages"], peaks, mhz)
+        roof = tc_roofline(bnd, k["ms_per_launch"] * 1e-3, dom, traffic)
     elif dom in ("p2p", "m2p") and fp32:
         a = kernels[dom]["algorithmic_tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(a, 3), "peak": round(peak_fp32, 2),

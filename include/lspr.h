@@ -224,10 +224,11 @@ LSPR_API int lspr_get_info(lspr_ctx *ctx, int64_t *n_panels, int64_t *n_sources,
 /* Sizes of the tensor-core work lists of the current tree (0 until the first product of
  * several right-hand sides forms them; any pointer may be null): M2P work units (a group of
  * four consecutive 64-target blocks and a stretch of its box list), (group, box) entries of
- * the groups' united box lists, and source entries of the P2P groups' united source ranges.
- * LSPR_E_ARG: null context. */
+ * the groups' united box lists, source entries of the P2P groups' united source ranges, and
+ * the P2P pipeline stages (8 sources of one range each) that one unit of right-hand sides
+ * takes.  LSPR_E_ARG: null context. */
 LSPR_API int lspr_get_tc_info(lspr_ctx *ctx, int64_t *m2p_units, int64_t *m2p_group_boxes,
-                              int64_t *p2p_group_sources);
+                              int64_t *p2p_group_sources, int64_t *p2p_stages);
 
 /* Kernel timing on the context's stream while enabled (lspr_set_timing(ctx, 1) clears
  * the counters).  While enabled, the treecode's P2P runs on the context's stream after

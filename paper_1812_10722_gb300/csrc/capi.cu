@@ -227,13 +227,15 @@ int lspr_get_info(lspr_ctx *c, int64_t *n_panels, int64_t *n_sources, int64_t *n
     return LSPR_OK;
 }
 
-int lspr_get_tc_info(lspr_ctx *c, int64_t *m2p_units, int64_t *m2p_group_boxes, int64_t *p2p_group_sources) {
+int lspr_get_tc_info(lspr_ctx *c, int64_t *m2p_units, int64_t *m2p_group_boxes, int64_t *p2p_group_sources,
+                     int64_t *p2p_stages) {
     if (!c) return LSPR_E_ARG;
     const Tree &tr = c->tree;
     const bool m = tr.ready && tr.tc_built, p = tr.ready && tr.tcp_built;
     if (m2p_units) *m2p_units = m ? tr.n_tc_items : 0;
     if (m2p_group_boxes) *m2p_group_boxes = m ? tr.n_tc_pairs : 0;
     if (p2p_group_sources) *p2p_group_sources = p ? tr.n_tcp_sources : 0;
+    if (p2p_stages) *p2p_stages = p ? tr.n_tcp_stages : 0;
     return LSPR_OK;
 }
 

@@ -162,7 +162,7 @@ struct Tree {
     // ranges cut at every range end, each piece with the mask of the blocks that sum it
     DArr<int4> tcp_items;    // (group, interval begin, interval end, 0)
     DArr<int4> tcp_ivl;      // (source begin, source end, block mask, 0)
-    int64_t n_tcp_items = 0, n_tcp_ivl = 0, n_tcp_sources = 0;
+    int64_t n_tcp_items = 0, n_tcp_ivl = 0, n_tcp_sources = 0, n_tcp_stages = 0;   // stages of 8 sources
     bool tc_built = false, tcp_built = false;   // the group lists above match the tree
     DArr<int4> p2m_items;    // (leaf, source begin, source end, 0): leaves under an accepted box
     DArr<int> box_parent;    // parent box (-1 for the root)

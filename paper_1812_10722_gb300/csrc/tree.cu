@@ -707,7 +707,7 @@ int tree_build(lspr_ctx *ctx, double theta, int P, int Ncrit) {
         LSPR_TRY(ctx, cudaMemcpyAsync(tr.p2m_items.p, p2m.data(), sizeof(int4) * p2m.size(), cudaMemcpyHostToDevice, st));
     // the group lists of the tensor-core far field are formed on first use (tree_tc_lists)
     tr.tc_built = tr.tcp_built = false;
-    tr.n_tc_items = tr.n_tc_pairs = tr.n_tcp_items = tr.n_tcp_ivl = tr.n_tcp_sources = 0;
+    tr.n_tc_items = tr.n_tc_pairs = tr.n_tcp_items = tr.n_tcp_ivl = tr.n_tcp_sources = tr.n_tcp_stages = 0;
     LSPR_TRY(ctx, tr.box_parent.ensure(nboxes));
     LSPR_TRY(ctx, cudaMemcpyAsync(tr.box_parent.p, hpar.data(), sizeof(int) * nboxes, cudaMemcpyHostToDevice, st));
     timer_end(ctx, T_TREE, ev);
@@ -766,6 +766,8 @@ int tree_tc_lists(lspr_ctx *ctx, bool p2p) {
         tr.n_tcp_items = (int64_t)pitems.size();
         tr.n_tcp_ivl = (int64_t)pivl.size();
         tr.n_tcp_sources = psrc;
+        tr.n_tcp_stages = 0;
+        for (const TcRange &r : pivl) tr.n_tcp_stages += (r.s1 - r.s0 + 7) / 8;
         LSPR_TRY(ctx, tr.tcp_items.ensure(std::max<size_t>(1, pitems.size())));
         LSPR_TRY(ctx, tr.tcp_ivl.ensure(std::max<size_t>(1, pivl.size())));
         if (!pitems.empty()) {

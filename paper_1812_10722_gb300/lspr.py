@@ -84,7 +84,7 @@ def lib():
                                      ctypes.POINTER(SolveStats)]
             L.lspr_get_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 7
             L.lspr_get_timing_rhs.argtypes = [_vp, _vp]
-            L.lspr_get_tc_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 3
+            L.lspr_get_tc_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 4
             L.lspr_set_timing.argtypes = [_vp, _i32]
             L.lspr_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
             L.lspr_get_timing.argtypes = [_vp, _vp, _vp]
@@ -280,9 +280,9 @@ class Context:
 
     def tc_info(self) -> dict:
         """Sizes of the tensor-core work lists (0 until a product of several right-hand sides)."""
-        vals = [ctypes.c_int64() for _ in range(3)]
+        vals = [ctypes.c_int64() for _ in range(4)]
         _check(lib().lspr_get_tc_info(self._h, *[ctypes.byref(v) for v in vals]), "lspr_get_tc_info", self._h)
-        return dict(zip(["m2p_units", "m2p_group_boxes", "p2p_group_sources"], [v.value for v in vals]))
+        return dict(zip(["m2p_units", "m2p_group_boxes", "p2p_group_sources", "p2p_stages"], [v.value for v in vals]))
 
     def launch_count(self) -> int:
         n = ctypes.c_int64(0)
