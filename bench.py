@@ -284,12 +284,22 @@ def run_ours(args, wl, rank, world, local_rank):
         ctx.mesh_upload(v_d, t_d, wl["K"], wl["K_fine"], wl["N_k"], surf_id=s_d)
         lt = tuning_wavelengths(lam, wl.get("tune_lams", 4))
         t0 = time.perf_counter()
+        # a batch: candidates costed from product times at the batch's size, then the restart
+        # length and the P2P path timed with full solves of the batch
         tune = ctx.autotune(workload_eps(wl, lt), em, lt, target_rel_err=1e-4, tol=min(wl["tol"], 1e-8),
                             restart=wl["restart"], mode=wl["mode"], refine=1 if wl["refine"] else 0,
-                            coarse=len(tris) > 50000)
+                            coarse=len(tris) > 50000, time_rhs=B if B > 1 else 0)
+        wl["theta"], wl["P"], wl["Ncrit"] = tune["theta"], tune["P"], tune["Ncrit"]
+        if B > 1 and wl["mode"] == "tree_fp32" and args.tc is None and not args.no_tc:
+            tune["solver"] = ctx.tune_solver(eps, em, lam, restarts=(30, 50, 80), tol=wl["tol"], maxiter=2000,
+                                             mode=wl["mode"], refine=1 if wl["refine"] else 0)
+            wl["restart"] = tune["solver"]["restart"]
         tune["seconds"] = round(time.perf_counter() - t0, 2)
         tune["wavelengths"] = [float(x) for x in lt]
-        wl["theta"], wl["P"], wl["Ncrit"] = tune["theta"], tune["P"], tune["Ncrit"]
+        if args.no_tc:
+            ctx.set_tensor_cores(False)
+        elif args.tc is not None:
+            ctx.set_tensor_cores(args.tc)
 
     def step(host: bool):
         if host:

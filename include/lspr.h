@@ -199,6 +199,13 @@ typedef struct {
     int32_t refine;          /* refinement of the timed solves (as lspr_solve_opts.refine) */
     int32_t grid;            /* 0: the full grid (60 candidates); 1: a coarse grid for large meshes
                                 (P 5..7, theta 0.4/0.5, Ncrit 256/512: 12 candidates) */
+    int32_t time_rhs;        /* 0: a candidate's cost is the time of its tuning solve; > 0: it is
+                                modelled for a batch of time_rhs right-hand sides as
+                                (reference Arnoldi steps + 4) x the time of one FP32 product of
+                                that many right-hand sides (the faster of the tensor-core P2P and
+                                the FP32-pipe P2P when time_rhs >= 2) + the time of one product of
+                                the refinement residual's mode */
+    int32_t pad_;
 } lspr_tune_opts;
 
 typedef struct {
@@ -209,11 +216,30 @@ typedef struct {
     double ref_ms;           /* solve time of the reference parameters */
     int32_t candidates;      /* candidates built and solved */
     int32_t qualified;       /* candidates within the accuracy bound */
+    int32_t tensor_cores;    /* the tensor-core mask left set (lspr_set_tensor_cores): with time_rhs,
+                                bit 1 is set iff the tensor-core P2P was the faster */
+    int32_t iterations;      /* Arnoldi steps of the reference solve (largest over the wavelengths) */
+    double product_ms;       /* time_rhs > 0: the chosen candidate's FP32 product time */
+    double residual_product_ms;   /* time_rhs > 0: its refinement-residual product time */
 } lspr_tune_result;
 
 LSPR_API int lspr_autotune(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im,
                            const double *E0, const double *lambda_nm, int32_t B, const lspr_tune_opts *o,
                            lspr_tune_result *res);
+
+/* Autotuner of the solver's execution for the current tree and a whole batch (the wavelengths
+ * that will be solved together): every pair of a GMRES restart length from restarts[0 ..
+ * n_restarts) and a P2P path (FP32 pipe; tensor cores, for B >= 2) is timed with one full solve
+ * (o->mode, o->tol, o->refine; o->restart is ignored) with CUDA events on the context's stream.
+ * The fastest pair whose wavelengths all converge is applied (its tensor-core mask is left set)
+ * and returned: *restart, *tensor_cores (the mask) and *ms (its solve time).  The tree and the
+ * accuracy are not changed (the restart length and the P2P path move sigma_ext only within the
+ * solve tolerance and the FP32-level rounding).  Errors as lspr_solve; LSPR_E_ARG for an empty
+ * or out-of-range restart list (1..512). */
+LSPR_API int lspr_tune_solver(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im,
+                              const double *E0, const double *lambda_nm, int32_t B, const lspr_solve_opts *o,
+                              const int32_t *restarts, int32_t n_restarts, int32_t *restart,
+                              int32_t *tensor_cores, double *ms);
 
 /* Sizes of the current geometry and tree (any pointer may be null):
  * panels, sources, near pairs (including self), boxes, P2P source-range items,

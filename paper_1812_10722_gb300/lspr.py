@@ -84,6 +84,8 @@ def lib():
                                      ctypes.POINTER(SolveStats)]
             L.lspr_get_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 7
             L.lspr_get_timing_rhs.argtypes = [_vp, _vp]
+            L.lspr_tune_solver.argtypes = [_vp, _vp, _d, _d, _vp, _vp, _i32, ctypes.POINTER(SolveOpts), _vp, _i32,
+                                           ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_d)]
             L.lspr_get_tc_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 4
             L.lspr_set_timing.argtypes = [_vp, _i32]
             L.lspr_launch_count.argtypes = [_vp, ctypes.POINTER(_i64)]
@@ -101,7 +103,7 @@ def lib():
                       "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing", "lspr_launch_count",
                       "lspr_set_graphs", "lspr_graph_stats", "lspr_autotune", "lspr_set_tensor_cores",
                       "lspr_device_errors", "lspr_selftest_wait_timeout", "lspr_selftest_gate_waits",
-                      "lspr_set_charges", "lspr_get_tc_info", "lspr_get_timing_rhs"):
+                      "lspr_set_charges", "lspr_get_tc_info", "lspr_get_timing_rhs", "lspr_tune_solver"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -123,13 +125,16 @@ def _host_ptr(a: np.ndarray):
 
 class TuneOpts(ctypes.Structure):
     _fields_ = [("target_rel_err", ctypes.c_double), ("tol", ctypes.c_double), ("restart", ctypes.c_int32),
-                ("mode", ctypes.c_int32), ("refine", ctypes.c_int32), ("grid", ctypes.c_int32)]
+                ("mode", ctypes.c_int32), ("refine", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("time_rhs", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("theta", ctypes.c_double), ("P", ctypes.c_int32), ("Ncrit", ctypes.c_int32),
                 ("rel_err", ctypes.c_double), ("ms", ctypes.c_double), ("ref_ms", ctypes.c_double),
-                ("candidates", ctypes.c_int32), ("qualified", ctypes.c_int32)]
+                ("candidates", ctypes.c_int32), ("qualified", ctypes.c_int32), ("tensor_cores", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("product_ms", ctypes.c_double),
+                ("residual_product_ms", ctypes.c_double)]
 
 
 @dataclass
@@ -290,19 +295,41 @@ class Context:
         return n.value
 
     def autotune(self, eps_in, eps_out, lambda_nm, E0=(0.0, 0.0, 1.0), target_rel_err=1e-4, tol=1e-6,
-                 restart=50, mode="tree_fp32", refine=1, coarse=False) -> dict:
-        """Fastest (theta, P, Ncrit) whose sigma_ext stays within target_rel_err / 2 of the
-        reference treecode solve; the chosen tree is left built."""
+                 restart=50, mode="tree_fp32", refine=1, coarse=False, time_rhs=0) -> dict:
+        """Cheapest (theta, P, Ncrit) whose sigma_ext stays within target_rel_err / 2 of the
+        reference treecode solve; the chosen tree is left built.  time_rhs > 0: the cost is
+        modelled from product times at that many right-hand sides (and the faster P2P path is
+        left set), else it is the tuning solve's time."""
         eps = np.ascontiguousarray(np.atleast_1d(np.asarray(eps_in, np.complex128)))
         lam = np.ascontiguousarray(np.atleast_1d(np.asarray(lambda_nm, np.float64)))
         e0 = np.ascontiguousarray(np.asarray(E0, np.float64))
         eo = complex(eps_out)
         o = TuneOpts(float(target_rel_err), float(tol), int(restart), MODES[mode] if isinstance(mode, str) else int(mode),
-                     int(refine), int(bool(coarse)))
+                     int(refine), int(bool(coarse)), int(time_rhs), 0)
         r = TuneResult()
         _check(lib().lspr_autotune(self._h, _host_ptr(eps), eo.real, eo.imag, _host_ptr(e0), _host_ptr(lam),
                                    len(lam), ctypes.byref(o), ctypes.byref(r)), "lspr_autotune", self._h)
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
+    def tune_solver(self, eps_in, eps_out, lambda_nm, restarts=(30, 50, 80), E0=(0.0, 0.0, 1.0), tol=1e-6,
+                    maxiter=2000, mode="tree_fp32", refine=1) -> dict:
+        """Fastest (GMRES restart, P2P path) for this batch, each timed with a full solve; the
+        chosen tensor-core mask is left set.  Returns {"restart", "tensor_cores", "ms"}."""
+        S = getattr(self, "nsurf", 1)
+        lam1 = np.atleast_1d(np.asarray(lambda_nm, np.float64))
+        ea = np.asarray(eps_in, np.complex128)
+        B = max(len(lam1), ea.size // S)
+        e = self._per_surface(ea, B)
+        lam = np.ascontiguousarray(np.broadcast_to(lam1, (B,)), dtype=np.float64)
+        E = np.ascontiguousarray(E0, dtype=np.float64)
+        rs = np.ascontiguousarray(restarts, dtype=np.int32)
+        o = SolveOpts(float(tol), 50, int(maxiter), MODES[mode] if isinstance(mode, str) else int(mode), int(refine))
+        m, tc, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+        eo = complex(eps_out)
+        _check(lib().lspr_tune_solver(self._h, _host_ptr(e), eo.real, eo.imag, _host_ptr(E), _host_ptr(lam), B,
+                                      ctypes.byref(o), _host_ptr(rs), len(rs), ctypes.byref(m), ctypes.byref(tc),
+                                      ctypes.byref(ms)), "lspr_tune_solver", self._h)
+        return {"restart": m.value, "tensor_cores": tc.value, "ms": ms.value}
 
     def set_graphs(self, enable: bool):
         """Arnoldi cycles as CUDA graph launches (default) or host-driven."""

@@ -487,6 +487,31 @@ def test_autotune_meets_sigma_bound(lspr):
     assert abs(s.sigma_ext[0] - g) / g < 1e-4
 
 
+def test_autotune_batch_cost_and_solver(lspr):
+    # batch tuning: candidates costed from product times at 24 right-hand sides (the faster P2P
+    # path left set), then the restart and P2P path timed with full solves of the batch; the
+    # chosen configuration solves the batch to the same sigma_ext as the FP64 treecode
+    v, t = I.icosphere(3, 10.0)
+    lam = I.wavelengths(355, 400, 24)
+    ep = I.drude_eps(lam)
+    lt = lam[[0, 10, 23]]
+    with lspr.Context(0) as ctx:
+        ctx.mesh_upload(v, t)
+        r = ctx.autotune(I.drude_eps(lt), I.EPS_WATER, lt, target_rel_err=1e-4, tol=1e-8, coarse=True, time_rhs=24)
+        assert r["candidates"] == 12 and r["qualified"] >= 1 and r["rel_err"] <= 5e-5
+        assert r["product_ms"] > 0 and r["residual_product_ms"] > 0 and r["iterations"] > 0
+        assert r["tensor_cores"] in (1, 3)
+        sv = ctx.tune_solver(ep, I.EPS_WATER, lam, restarts=(20, 40), tol=1e-8)
+        assert sv["restart"] in (20, 40) and sv["tensor_cores"] in (1, 3) and sv["ms"] > 0
+        a = ctx.solve(ep, I.EPS_WATER, lam, tol=1e-8, restart=sv["restart"], maxiter=3000, mode="tree_fp32",
+                      refine=True)
+        b = ctx.solve(ep, I.EPS_WATER, lam, tol=1e-8, restart=sv["restart"], maxiter=3000, mode="tree_fp64")
+        with pytest.raises(lspr.LsprError):
+            ctx.tune_solver(ep, I.EPS_WATER, lam, restarts=(0,))
+        assert ctx.device_errors() == 0
+    assert np.max(np.abs(a.sigma_ext - b.sigma_ext) / b.sigma_ext) < 1e-5
+
+
 def _sensor_small():
     # sphere (surface 0) and two analytes at 0.5 and 1 nm: cross-surface near-singular pairs
     # (the analytes' skinny panels need N_k = 24 for the semi-analytical self integral to
