@@ -287,9 +287,12 @@ LSPR_API int lspr_set_graphs(lspr_ctx *ctx, int32_t enable);
 /* Tensor cores for the FP32 far field of several right-hand sides (B >= 2), as a mask:
  * bit 0 (default on): the M2P contraction on tcgen05 (TF32 operands split into high and low
  * parts, FP32 accumulation in tensor memory; about 2x the FP32-pipe kernel at 16 right-hand
- * sides, 4x at 64); bit 1 (default off): the tree P2P on tcgen05 (same split; slower than the
- * FP32-pipe kernel at 16 right-hand sides on GB300).  0 selects the FP32-pipe kernels of the
- * same sums.  Bits above 1 are ignored.  LSPR_E_ARG: null context. */
+ * sides, 4x at 64); bit 1 (default off; lspr_tune_solver sets it where it pays): the tree P2P
+ * on tcgen05 (same split; 2.3x the FP32-pipe kernel at 64 right-hand sides) for products with
+ * at least 24 right-hand sides (channel sets) in use, the FP32-pipe P2P below that (inside a
+ * solve the count falls as wavelengths converge, and the choice is then made on the device).
+ * 0 selects the FP32-pipe kernels of the same sums.  Bits above 1 are ignored.
+ * LSPR_E_ARG: null context. */
 LSPR_API int lspr_set_tensor_cores(lspr_ctx *ctx, int32_t enable);
 /* Bounded waits inside device kernels that ran out since lspr_create (the tensor-core
  * far-field kernels' pipeline barriers, about one second each): a kernel whose wait runs out

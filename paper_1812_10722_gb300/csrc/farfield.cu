@@ -163,9 +163,19 @@ int launch_p2p(lspr_ctx *ctx, int prec, const int4 *items, int64_t nitems, doubl
         // at 16 right-hand sides, 20480 panels)
         else p2p_launch<ffloat, 2>(ctx, items, nitems, B, acc, st, counter);
     } else if (B > 1 && (ctx->tensor_cores & 2) && items == ctx->tree.p2p_items.p) {
-        LSPR_TRY_ST(p2p_tc_launch(ctx, acc, st, counter, B));
+        // the tensor-core P2P for products of at least tc_p2p_min_rhs right-hand sides in use, the
+        // FP32 pipe below: decided on the host when every slot is in use, else on the device from
+        // the count of running systems (both kernels are launched; the one not chosen returns at once)
+        const int mn = std::max(2, ctx->tc_p2p_min_rhs);
+        if (!ctx->rhs_nact) {
+            if (B >= mn) LSPR_TRY_ST(p2p_tc_launch(ctx, acc, st, counter, B, 0));
+            else p2p_launch<float, batch_chunk<float>(2)>(ctx, items, nitems, B, acc, st, counter);
+        } else {
+            LSPR_TRY_ST(p2p_tc_launch(ctx, acc, st, counter, B, mn));
+            p2p_launch<float, batch_chunk<float>(2)>(ctx, items, nitems, B, acc, st, counter, mn);
+        }
     } else {
-        if (B == 1) p2p_launch<float, 1>(ctx, items, nitems, B, acc, st, counter);
+        if (B == 1) p2p1_launch(ctx, items, nitems, acc, st, counter);
         else p2p_launch<float, batch_chunk<float>(2)>(ctx, items, nitems, B, acc, st, counter);
     }
     timer_end_on(ctx, slot, ev, st);
@@ -245,7 +255,7 @@ int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, cons
                         const float4 *spos, const float4 *snrm, const float4 *w, double *acc) {
     if (nitems == 0) return LSPR_OK;
     p2p_kernel<float, 1, false><<<grid_for(nitems, p2p_warps(1)), p2p_warps(1) * 32, 0, st>>>(
-        items, nitems, 1, 1, tgt, ntgt, spos, snrm, w, acc, nullptr, nullptr);
+        items, nitems, 1, 1, tgt, ntgt, spos, snrm, w, acc, nullptr, nullptr, 1 << 30);
     return cudaGetLastError() == cudaSuccess ? LSPR_OK : LSPR_E_CUDA;
 }
 

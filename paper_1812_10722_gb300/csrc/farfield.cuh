@@ -138,20 +138,22 @@ __device__ __forceinline__ void p2p_range(int beg, int end, int lane, int B, int
 
 // Work units: (item, right-hand-side chunk), item = (target block, source begin, source
 // end, own-panel flag); one per warp.  DYNAMIC: a persistent grid whose warps take units
-// from an atomic counter.  acc is [panel][B][4].
+// from an atomic counter.  acc is [panel][B][4].  The kernel does nothing when at least
+// skip_from right-hand sides are in use (the tensor-core P2P then takes the product).
 template <typename T, int NB, bool DYNAMIC>
 __global__ void __launch_bounds__(p2p_warps(NB) * 32)
     p2p_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B,
                const typename Vec4<T>::type *__restrict__ tgt, int64_t ntgt,
                const typename Vec4<T>::type *__restrict__ spos, const typename Vec4<T>::type *__restrict__ snrm,
                const typename Vec4<T>::type *__restrict__ sw, double *__restrict__ acc, int *counter,
-               const int *nact) {
+               const int *nact, int skip_from) {
     using T4 = typename Vec4<T>::type;
     constexpr int W = p2p_warps(NB);
     __shared__ T4 sh[W][2][32];
     __shared__ T4 shw[W][32][NB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int Bact = nact ? *nact : B;   // right-hand sides in use (the first Bact slots)
+    if (Bact >= skip_from) return;       // the tensor-core P2P takes this product
     nbc = (Bact + NB - 1) / NB;
     const int64_t units = nitems * nbc;
     int64_t it = (int64_t)blockIdx.x * W + warp;
@@ -186,6 +188,135 @@ __global__ void __launch_bounds__(p2p_warps(NB) * 32)
             if (t0 < ntgt) atomic_add4(acc + 4 * ((int64_t)tp0 * B + b0 + k), a0[k][0], a0[k][1], a0[k][2], a0[k][3]);
             if (t1 < ntgt) atomic_add4(acc + 4 * ((int64_t)tp1 * B + b0 + k), a1[k][0], a1[k][1], a1[k][2], a1[k][3]);
         }
+        if (!DYNAMIC) return;
+    }
+}
+
+// ------------------------------------------------------- P2P, one right-hand side
+// FP32 direct sums of one right-hand side with the arithmetic packed two targets at a time
+// (f32x2: FADD2 / FMUL2 / FFMA2 on target pairs).  A warp takes one work item (a 64-target block
+// and a source range); lane l of half h (h = lane / 16) holds the four targets l, l + 16, l + 32,
+// l + 48 of the block as two pairs, and the two halves take alternate sources of each staged
+// chunk of 32, so every source operand read from shared memory feeds four targets.  A source is
+// staged once per chunk with each component duplicated into both halves of a register pair
+// (position, normal, the four weight channels) and its panel id beside; at the end the halves'
+// partial sums are added with one exchange and each lane adds two targets into the FP64
+// accumulators.  The sums and the own-panel rule are those of p2p_kernel.
+constexpr int kP1Warps = 8;
+struct P1Src {   // one staged source, 96 bytes: duplicated pairs (the position negated)
+    float4 pxy;   // (-px, -px, -py, -py)
+    float4 pzn;   // (-pz, -pz, nx, nx)
+    float4 nyz;   // (ny, ny, nz, nz)
+    float4 wv;    // (w.x, w.x, w.y, w.y): single-layer weight, re and im
+    float4 wk;    // (w.z, w.z, w.w, w.w): double-layer weight, re and im
+    int pid, pad0, pad1, pad2;
+};
+
+template <bool CHECK>
+__device__ __forceinline__ void p1_range(int beg, int end, int lane, P1Src *sh, const float4 *__restrict__ spos,
+                                         const float4 *__restrict__ snrm, const float4 *__restrict__ sw,
+                                         const float2 (&qx)[2], const float2 (&qy)[2], const float2 (&qz)[2],
+                                         const int (&tp)[4], float2 (&av)[2][2], float2 (&ak)[2][2]) {
+    const int h = lane >> 4;
+    for (int base = beg; base < end; base += 32) {
+        const int s = base + lane;
+        if (s < end) {
+            const float4 p = spos[s], n = snrm[s], w = sw[s];
+            P1Src e;
+            e.pxy = make_float4(-p.x, -p.x, -p.y, -p.y);
+            e.pzn = make_float4(-p.z, -p.z, n.x, n.x);
+            e.nyz = make_float4(n.y, n.y, n.z, n.z);
+            e.wv = make_float4(w.x, w.x, w.y, w.y);
+            e.wk = make_float4(w.z, w.z, w.w, w.w);
+            e.pid = panel_of(n.w);
+            sh[lane] = e;
+        }
+        __syncwarp();
+        const int cnt = min(32, end - base);
+#pragma unroll 2
+        for (int kk = h; kk < cnt; kk += 2) {
+            const float4 a = sh[kk].pxy, b = sh[kk].pzn, c = sh[kk].nyz, wv = sh[kk].wv, wk = sh[kk].wk;
+            const float2 px = make_float2(a.x, a.y), py = make_float2(a.z, a.w), pz = make_float2(b.x, b.y);
+            const float2 nx = make_float2(b.z, b.w), ny = make_float2(c.x, c.y), nz = make_float2(c.z, c.w);
+            const float2 wvr = make_float2(wv.x, wv.y), wvi = make_float2(wv.z, wv.w);
+            const float2 wkr = make_float2(wk.x, wk.y), wki = make_float2(wk.z, wk.w);
+            const int pid = sh[kk].pid;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float2 dx = __fadd2_rn(qx[u], px), dy = __fadd2_rn(qy[u], py), dz = __fadd2_rn(qz[u], pz);
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                float r0 = rsq(r2.x), r1 = rsq(r2.y);
+                if (CHECK) {
+                    r0 = pid == tp[2 * u] ? 0.f : r0;
+                    r1 = pid == tp[2 * u + 1] ? 0.f : r1;
+                }
+                const float2 r = make_float2(r0, r1);
+                const float2 dn = __ffma2_rn(dz, nz, __ffma2_rn(dy, ny, __fmul2_rn(dx, nx)));
+                const float2 t = __fmul2_rn(__fmul2_rn(dn, __fmul2_rn(r, r)), r);
+                av[u][0] = __ffma2_rn(r, wvr, av[u][0]);
+                av[u][1] = __ffma2_rn(r, wvi, av[u][1]);
+                ak[u][0] = __ffma2_rn(t, wkr, ak[u][0]);
+                ak[u][1] = __ffma2_rn(t, wki, ak[u][1]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <bool DYNAMIC>
+__global__ void __launch_bounds__(kP1Warps * 32)
+    p2p1_kernel(const int4 *__restrict__ items, int64_t nitems, const float4 *__restrict__ tgt, int64_t ntgt,
+                const float4 *__restrict__ spos, const float4 *__restrict__ snrm, const float4 *__restrict__ sw,
+                double *__restrict__ acc, int *counter, const int *nact) {
+    __shared__ P1Src sh[kP1Warps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, l = lane & 15, h = lane >> 4;
+    if (nact && *nact < 1) return;   // no right-hand side in use
+    int64_t it = (int64_t)blockIdx.x * kP1Warps + warp;
+    while (true) {
+        if (DYNAMIC) {
+            int v = 0;
+            if (lane == 0) v = atomicAdd(counter, 1);
+            it = __shfl_sync(0xffffffffu, v, 0);
+        }
+        if (it >= nitems) return;
+        const int4 item = __ldg(items + it);
+        const int64_t t0 = (int64_t)item.x * kTargetBlock + l;
+        float4 q[4];
+        int tp[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t ti = t0 + 16 * i;
+            q[i] = ti < ntgt ? tgt[ti] : tgt[0];
+            tp[i] = panel_of(q[i].w);
+        }
+        const float2 qx[2] = {make_float2(q[0].x, q[1].x), make_float2(q[2].x, q[3].x)};
+        const float2 qy[2] = {make_float2(q[0].y, q[1].y), make_float2(q[2].y, q[3].y)};
+        const float2 qz[2] = {make_float2(q[0].z, q[1].z), make_float2(q[2].z, q[3].z)};
+        float2 av[2][2], ak[2][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) av[u][c] = ak[u][c] = make_float2(0.f, 0.f);
+        if (item.w)
+            p1_range<true>(item.y, item.z, lane, sh[warp], spos, snrm, sw, qx, qy, qz, tp, av, ak);
+        else
+            p1_range<false>(item.y, item.z, lane, sh[warp], spos, snrm, sw, qx, qy, qz, tp, av, ak);
+        // add the two halves; lanes of half h keep the pair u = h (targets l + 32 h, l + 16 + 32 h)
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                av[u][c].x += __shfl_xor_sync(0xffffffffu, av[u][c].x, 16);
+                av[u][c].y += __shfl_xor_sync(0xffffffffu, av[u][c].y, 16);
+                ak[u][c].x += __shfl_xor_sync(0xffffffffu, ak[u][c].x, 16);
+                ak[u][c].y += __shfl_xor_sync(0xffffffffu, ak[u][c].y, 16);
+            }
+        const float2 v0 = h ? av[1][0] : av[0][0], v1 = h ? av[1][1] : av[0][1];
+        const float2 k0 = h ? ak[1][0] : ak[0][0], k1 = h ? ak[1][1] : ak[0][1];
+        const int64_t ta = t0 + 32 * h, tb = ta + 16;
+        const int pa = h ? tp[2] : tp[0], pb = h ? tp[3] : tp[1];
+        if (ta < ntgt) atomic_add4(acc + 4 * (int64_t)pa, v0.x, v1.x, k0.x, k1.x);
+        if (tb < ntgt) atomic_add4(acc + 4 * (int64_t)pb, v0.y, v1.y, k0.y, k1.y);
         if (!DYNAMIC) return;
     }
 }
@@ -689,7 +820,7 @@ template <> struct Views<ffloat> {
 
 template <typename T, int NB>
 static void p2p_launch(lspr_ctx *ctx, const int4 *items, int64_t nitems, int B, double *acc, cudaStream_t st,
-                       int *counter) {
+                       int *counter, int skip_from = 1 << 30) {
     static int occ = 0;
     constexpr int W = p2p_warps(NB);
     const int nbc = (B + NB - 1) / NB;
@@ -697,7 +828,18 @@ static void p2p_launch(lspr_ctx *ctx, const int4 *items, int64_t nitems, int B, 
                                              persistent_grid(ctx, p2p_kernel<T, NB, true>, W * 32, &occ));
     p2p_kernel<T, NB, true><<<grid, W * 32, 0, st>>>(items, nitems, nbc, B, Views<T>::tgt(ctx), ctx->mesh.N,
                                                       Views<T>::spos(ctx), Views<T>::snrm(ctx), Views<T>::w(ctx),
-                                                      acc, counter, ctx->rhs_nact);
+                                                      acc, counter, ctx->rhs_nact, skip_from);
+}
+
+// the packed single-right-hand-side P2P (FP32)
+static void p2p1_launch(lspr_ctx *ctx, const int4 *items, int64_t nitems, double *acc, cudaStream_t st,
+                        int *counter) {
+    static int occ = 0;
+    const unsigned grid = std::min<unsigned>(grid_for(nitems, kP1Warps),
+                                             persistent_grid(ctx, p2p1_kernel<true>, kP1Warps * 32, &occ));
+    p2p1_kernel<true><<<grid, kP1Warps * 32, 0, st>>>(items, nitems, Views<float>::tgt(ctx), ctx->mesh.N,
+                                                       Views<float>::spos(ctx), Views<float>::snrm(ctx),
+                                                       Views<float>::w(ctx), acc, counter, ctx->rhs_nact);
 }
 
 template <typename T, int P, int NB>
@@ -769,7 +911,9 @@ int m2p_orders_f32(lspr_ctx *ctx, double *acc, int *counter, int B);
 // tensor-core M2P (m2p_tc.cu): FP32 operands as 3xTF32, B >= 2; LSPR_E_STATE otherwise
 int m2p_tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B);
 // tensor-core P2P of the tree mode (p2p_tc.cu): FP32 weights as TF32 high/low parts, B >= 2
-int p2p_tc_launch(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B);
+// min_rhs: the kernel does nothing when fewer right-hand sides are in use (the FP32-pipe P2P
+// then takes the product)
+int p2p_tc_launch(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B, int min_rhs);
 int m2p_orders_f64(lspr_ctx *ctx, double *acc, int *counter, int B);
 int m2p_orders_ff(lspr_ctx *ctx, double *acc, int *counter, int B);
 

@@ -267,6 +267,8 @@ struct lspr_ctx {
     // device-driven Arnoldi cycles (a CUDA graph per configuration, gmres_graph.cu)
     bool use_graphs = true;
     int tensor_cores = 1;              // tcgen05 for B >= 2 in FP32: bit 0 M2P, bit 1 P2P
+    int tc_p2p_min_rhs = 24;           // the tensor-core P2P takes products of at least this many
+                                       // right-hand sides in use; fewer take the FP32-pipe P2P
     lspr::DArr<unsigned char> tc_img;  // split moments in tensor-core operand layout
     lspr::DArr<int> dev_err;           // [0] bounded device waits that ran out (never reset);
                                        // [1] failure-path check: tensor-core kernels give up at once

@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     p2p_tc_kernel(const int4 *__restrict__ items, int64_t nitems, const int4 *__restrict__ ivl, int B,
                   const float4 *__restrict__ tgt, int64_t ntgt, const float4 *__restrict__ spos,
                   const float4 *__restrict__ snrm, const float4 *__restrict__ sw, double *__restrict__ acc,
-                  int *counter, int *error, const int *nact) {
+                  int *counter, int *error, const int *nact, int min_rhs) {
+    // fewer right-hand sides in use than min_rhs: the FP32-pipe P2P takes this product
+    if ((nact ? *nact : B) < min_rhs) return;
     extern __shared__ __align__(128) unsigned char tc_smem[];
     __shared__ __align__(8) uint64_t full_s[kStages], empty_s[kStages];
     __shared__ __align__(8) uint64_t acc_full, acc_empty, ring_full[kUnitRing], ring_empty[kUnitRing], drain, gate;
@@ -381,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }  // namespace
 
 // FP32 tree P2P of B >= 2 right-hand sides on the tensor cores
-int p2p_tc_launch(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B) {
+int p2p_tc_launch(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B, int min_rhs) {
     static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
     if (!tr.tcp_built) LSPR_TRY_ST(tree_tc_lists(ctx, true));
@@ -394,7 +396,7 @@ int p2p_tc_launch(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int
     p2p_tc_kernel<<<grid, kTcThreads, kSmem, st>>>(tr.tcp_items.p, tr.n_tcp_items, tr.tcp_ivl.p, B,
                                                   Views<float>::tgt(ctx), ctx->mesh.N, Views<float>::spos(ctx),
                                                   Views<float>::snrm(ctx), Views<float>::w(ctx), acc, counter,
-                                                  ctx->dev_err.p, ctx->rhs_nact);
+                                                  ctx->dev_err.p, ctx->rhs_nact, min_rhs);
     return LSPR_OK;
 }
 

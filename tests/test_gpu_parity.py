@@ -498,7 +498,7 @@ def test_autotune_batch_cost_and_solver(lspr):
     with lspr.Context(0) as ctx:
         ctx.mesh_upload(v, t)
         r = ctx.autotune(I.drude_eps(lt), I.EPS_WATER, lt, target_rel_err=1e-4, tol=1e-8, coarse=True, time_rhs=24)
-        assert r["candidates"] == 12 and r["qualified"] >= 1 and r["rel_err"] <= 5e-5
+        assert r["candidates"] == 13 and r["qualified"] >= 1 and r["rel_err"] <= 5e-5   # 12 + the reference
         assert r["product_ms"] > 0 and r["residual_product_ms"] > 0 and r["iterations"] > 0
         assert r["tensor_cores"] in (1, 3)
         sv = ctx.tune_solver(ep, I.EPS_WATER, lam, restarts=(20, 40), tol=1e-8)
