@@ -6,14 +6,20 @@
 //               the device, whether another step follows)
 //                 z = M^-1 v_j                      (v_j = w / ||w|| formed here, j > 0)
 //                 w = A z                           (the far field, near SpMV and block rows)
-//                 two classical Gram-Schmidt passes h = V^H w, w -= V h
+//                 classical Gram-Schmidt h = V^H w, w -= V h, repeated once for the systems
+//                 whose w lost more than a factor 1/sqrt(2) of its norm in the first pass
+//                 (the Daniel-Gragg-Kaufman-Stewart criterion: one repetition restores
+//                 orthogonality to working precision, and a pass that removes little
+//                 needs none)
 //                 ||w||, Givens rotation of the new Hessenberg column, residual
 //                 estimate |g_{j+1}|, per-system stop test
 //   back substitution R y = g, x += M^-1 V y
 // so the host only takes part once per cycle (explicit residual and stop decision).
 // Inner products reduce over blocks with a last-block ticket instead of a second launch.
-// The arithmetic is that of the host-driven GMRES in solve.cu: FP64 Krylov basis,
-// right 2x2 block-Jacobi preconditioner, CGS2, the same rotation convention.
+// The arithmetic is that of the host-driven GMRES in solve.cu (FP64 Krylov basis, right 2x2
+// block-Jacobi preconditioner, the same rotation convention), whose Gram-Schmidt always takes
+// the second pass (CGS2); here the second pass runs only where the criterion asks for it, which
+// removes up to half of the basis traffic that dominates a step's vector work.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -25,7 +31,8 @@ namespace lspr {
 namespace {
 
 constexpr int kT = 256;                 // threads per block of the vector kernels
-constexpr int kPer = 4;                 // elements per thread of the inner-product kernel
+constexpr int kPer = 8;                 // elements per thread of the inner-product kernel
+constexpr double kReorthEta = 0.70710678118654752;   // second pass when ||w_1|| < eta ||w_0||
 constexpr int kDotChunk = kT * kPer;    // elements per inner-product block
 constexpr int kMaxWarpsSmall = 16;      // warps of the per-system (rotation, back substitution) kernels
 
@@ -38,7 +45,8 @@ struct Arn {
     const int *surf;   // surface of each panel; s is [B][S]
     int S;
     double2 *h, *hcol, *part, *H, *sn, *g, *y;
-    double *npart, *nrm, *cs, *res;
+    double *npart, *nrm, *cs, *res, *npart0, *nrm0;
+    int *reorth;
     const double *bn, *par;
     unsigned *tick;
     int *jdev, *active, *jb, *iters;
@@ -91,13 +99,16 @@ __device__ __forceinline__ bool last_block(unsigned *t, unsigned count) {
     return last;
 }
 
-// final sum of the squared-norm partials of system b into nrm[b] (last block only)
-__device__ __forceinline__ void norm_final(const Arn &a, int b, double *sh) {
+// final sum of the squared-norm partials of system b into nrm[b] (last block only); decide:
+// the first Gram-Schmidt pass decides whether the second runs
+__device__ __forceinline__ void norm_final(const Arn &a, int b, double *sh, bool decide = false) {
     double t = 0.0;
     for (int c = threadIdx.x; c < a.nblk; c += kT) t += __ldcg(a.npart + (int64_t)b * a.nblk + c);
     t = block_sum(t, sh);
     if (threadIdx.x == 0) {
-        a.nrm[b] = sqrt(t);
+        const double r = sqrt(t);
+        a.nrm[b] = r;
+        if (decide) a.reorth[b] = !(r >= kReorthEta * __ldcg(a.nrm0 + b));
         a.tick[a.B + b] = 0;
     }
 }
@@ -173,18 +184,25 @@ __global__ void __launch_bounds__(kT) arn_precond_kernel(Arn a) {
 // hcol += h on pass 1).
 __global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
     __shared__ double2 red[kT / 32][32];
+    __shared__ double shn[kT / 32];
     const int b = blockIdx.y, chunk = blockIdx.x;
-    if (!a.active[b]) return;
+    if (!a.active[b] || (pass && !a.reorth[b])) return;
     const int nv = *a.jdev + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t base = (int64_t)chunk * kDotChunk + threadIdx.x;
     const double2 *wb = a.w + (int64_t)b * a.n2;
     const double2 *Vb = a.V + (int64_t)b * a.vstride;
     double2 wr[kPer];
+    double w2 = 0.0;
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
         const int64_t k = base + r * kT;
         wr[r] = k < a.n2 ? wb[k] : make_double2(0.0, 0.0);
+        w2 += cabs2(wr[r]);
+    }
+    if (pass == 0) {   // ||A z||^2 of this chunk, for the second-pass criterion
+        w2 = block_sum(w2, shn);
+        if (threadIdx.x == 0) a.npart0[(int64_t)b * a.nch + chunk] = w2;
     }
     double2 *pb = a.part + (int64_t)b * (a.m + 1) * a.nch;
     for (int i0 = 0; i0 < nv; i0 += 32) {
@@ -210,6 +228,12 @@ __global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
         __syncthreads();
     }
     if (!last_block(a.tick + b, a.nch)) return;
+    if (pass == 0) {
+        double t = 0.0;
+        for (int c = threadIdx.x; c < a.nch; c += kT) t += __ldcg(a.npart0 + (int64_t)b * a.nch + c);
+        t = block_sum(t, shn);
+        if (threadIdx.x == 0) a.nrm0[b] = sqrt(t);
+    }
     // rows i = warp + 8 u: lanes stride over the chunks
     for (int i0 = warp; i0 < nv; i0 += 4 * (kT / 32)) {
         double2 t[4];
@@ -234,12 +258,13 @@ __global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
     if (threadIdx.x == 0) a.tick[b] = 0;
 }
 
-// Second half of a pass: w -= sum_{i <= j} v_i h_i; with_norm (second pass): ||w||
-// into nrm[b] (partials per block, the last block sums them)
-__global__ void __launch_bounds__(kT) arn_axpy_kernel(Arn a, int with_norm) {
+// Second half of a pass: w -= sum_{i <= j} v_i h_i, then ||w|| into nrm[b] (partials per
+// block, the last block sums them); after the first pass the last block also decides whether
+// the second runs (reorth[b])
+__global__ void __launch_bounds__(kT) arn_axpy_kernel(Arn a, int pass) {
     __shared__ double sh[kT / 32];
     const int b = blockIdx.y;
-    if (!a.active[b]) return;
+    if (!a.active[b] || (pass && !a.reorth[b])) return;
     const int nv = *a.jdev + 1;
     const int64_t k = blockIdx.x * (int64_t)kT + threadIdx.x;
     const double2 *hb = a.h + (int64_t)b * (a.m + 1);
@@ -247,14 +272,14 @@ __global__ void __launch_bounds__(kT) arn_axpy_kernel(Arn a, int with_norm) {
     if (k < a.n2) {
         const double2 *Vb = a.V + (int64_t)b * a.vstride + k;
         double2 acc = a.w[(int64_t)b * a.n2 + k];
+#pragma unroll 4
         for (int i = 0; i < nv; ++i) acc = csub(acc, cmul(Vb[(int64_t)i * a.n2], hb[i]));
         a.w[(int64_t)b * a.n2 + k] = acc;
         q = cabs2(acc);
     }
-    if (!with_norm) return;
     q = block_sum(q, sh);
     if (threadIdx.x == 0) a.npart[(int64_t)b * a.nblk + blockIdx.x] = q;
-    if (last_block(a.tick + a.B + b, a.nblk)) norm_final(a, b, sh);
+    if (last_block(a.tick + a.B + b, a.nblk)) norm_final(a, b, sh, pass == 0);
 }
 
 // shared memory of the rotation kernel per warp: column (m+1), sines (m), cosines (m)
@@ -500,6 +525,9 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     LSPR_TRY(ctx, ab.part.ensure((size_t)B * (m + 1) * nch));
     LSPR_TRY(ctx, ab.npart.ensure((size_t)B * nblk));
     LSPR_TRY(ctx, ab.nrm.ensure(B));
+    LSPR_TRY(ctx, ab.npart0.ensure((size_t)B * nch));
+    LSPR_TRY(ctx, ab.nrm0.ensure(B));
+    LSPR_TRY(ctx, ab.reorth.ensure(B));
     LSPR_TRY(ctx, ab.H.ensure((size_t)B * (m + 1) * m));
     LSPR_TRY(ctx, ab.cs.ensure((size_t)B * m));
     LSPR_TRY(ctx, ab.sn.ensure((size_t)B * m));
@@ -537,6 +565,9 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     a.y = ab.y.p;
     a.npart = ab.npart.p;
     a.nrm = ab.nrm.p;
+    a.npart0 = ab.npart0.p;
+    a.nrm0 = ab.nrm0.p;
+    a.reorth = ab.reorth.p;
     a.cs = ab.cs.p;
     a.res = ab.res.p;
     a.bn = ab.bn.p;

@@ -202,6 +202,9 @@ struct ArnoldiBufs {
     DArr<double2> part;     // [B][m+1][chunks] partial inner products
     DArr<double> npart;     // [B][blocks] partial squared norms
     DArr<double> nrm;       // [B] norm of the new basis vector / of the residual
+    DArr<double> npart0;    // [B][chunks] partial squared norms of A z before orthogonalisation
+    DArr<double> nrm0;      // [B] ||A z|| before orthogonalisation
+    DArr<int> reorth;       // [B] 1: the step takes the second Gram-Schmidt pass
     DArr<double2> H;        // [B][m+1][m] rotated Hessenberg matrix (R)
     DArr<double> cs;        // [B][m] Givens cosines
     DArr<double2> sn;       // [B][m] Givens sines
