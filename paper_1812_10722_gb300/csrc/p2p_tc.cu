@@ -20,15 +20,17 @@
 // (the epilogue adds both halves).
 //
 // Roles (persistent, one CTA per SM, both accumulators in the SM's 512 tensor-memory columns):
+//   warp 8 (one lane) fetches work units into a small ring and bulk-copies every stage's inputs
+//     (the positions, normals and weights of its eight sources) into the stage;
 //   warps 0-7 (one thread per target of the group) generate G and dG/dn of every stage in
-//     registers, split them and write the B operands; warps 0-3 also stage the split weights
-//     (the A operands) from the source weights; after the first stage of the next unit they
-//     drain the finished unit's accumulators (tcgen05.ld) into the FP64 accumulators;
-//   warp 8 (one lane) fetches work units into a small ring;
+//     registers from those inputs, split them and write the B operands; warps 0-3 also write
+//     the split weights (the A operands); after the first stage of the next unit they drain the
+//     finished unit's accumulators (tcgen05.ld) into the FP64 accumulators;
 //   warp 9 (one lane) issues the MMAs of each stage once it is written, commits to the stage's
 //     "empty" barrier and, at the end of a unit, to the accumulator barrier.
 // Every wait is bounded (about a second): one that runs out raises an abort flag that the
-// other roles see, the block drains its MMAs in flight, frees its tensor memory and returns,
+// other roles see, the block drains its bulk copies and MMAs in flight, frees its tensor memory
+// and returns,
 // and the context's device error count (error[0]) records it.  With error[1] set, thread 0
 // first waits on a barrier that nothing arrives on, so that the wait runs out before any work
 // is issued (the host's check of this failure path).
@@ -53,11 +55,16 @@ constexpr int kRingConsumers = kGenWarps + 1;  // lane 0 of each consumer warp
 constexpr uint32_t kTmemCols = 2 * kTcN;       // D_V in columns [0, 256), D_K in [256, 512)
 constexpr int kAPart = (128 / 8) * kSBO;       // one split part of a weight operand (128 rows)
 constexpr int kBPart = (kTcN / 8) * kSBO;      // one split part of a kernel operand (256 rows)
-// stage: W_V hi | W_V lo | W_K hi | W_K lo | G hi | G lo | dG hi | dG lo
+// stage: W_V hi | W_V lo | W_K hi | W_K lo | G hi | G lo | dG hi | dG lo | the stage's inputs as
+// bulk-copied from global memory: source positions (8 float4), normals (8 float4), weights
+// (8 sources x 64 right-hand sides float4)
 constexpr int kOffWV = 0, kOffWK = 2 * kAPart, kOffG = 4 * kAPart, kOffD = 4 * kAPart + 2 * kBPart;
-constexpr int kStage = 4 * kAPart + 4 * kBPart;
-constexpr int kStages = (200 * 1024) / kStage;
+constexpr int kOffRaw = 4 * kAPart + 4 * kBPart;
+constexpr int kRawPos = 0, kRawNrm = kSrc * 16, kRawW = 2 * kSrc * 16;
+constexpr int kStage = kOffRaw + 2 * kSrc * 16 + kSrc * kRC * 16;
+constexpr int kStages = 4;
 constexpr int kSmem = kStages * kStage;
+static_assert(kSmem + 1024 <= 232448, "the stages and the static shared memory fit one SM");
 constexpr uint32_t kIdesc = idesc_tf32(128, kTcN);
 static_assert(kTmemCols <= 512 && kTcN <= 256, "both accumulators fit the tensor memory");
 static_assert(kStages >= 2, "at least two stages");
@@ -77,7 +84,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // fewer right-hand sides in use than min_rhs: the FP32-pipe P2P takes this product
     if ((nact ? *nact : B) < min_rhs) return;
     extern __shared__ __align__(128) unsigned char tc_smem[];
-    __shared__ __align__(8) uint64_t full_s[kStages], empty_s[kStages];
+    __shared__ __align__(8) uint64_t full_s[kStages], empty_s[kStages], raw_s[kStages];
     __shared__ __align__(8) uint64_t acc_full, acc_empty, ring_full[kUnitRing], ring_empty[kUnitRing], drain, gate;
     __shared__ int64_t ring[kUnitRing];
     __shared__ uint32_t tslot;
@@ -88,6 +95,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int s = 0; s < kStages; ++s) {
             bar_init(smem_addr(&full_s[s]), kTcN);   // one arrival per generating thread
             bar_init(smem_addr(&empty_s[s]), 1);     // the MMAs' commit
+            bar_init(smem_addr(&raw_s[s]), 1);       // the producer's expect_tx (+ the copies' bytes)
         }
         bar_init(smem_addr(&acc_full), 1);
         bar_init(smem_addr(&acc_empty), kGenWarps);
@@ -121,8 +129,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int64_t units = nitems * nbc;
 
     if (warp == kProdWarp) {
-        // ---- work units
+        // ---- work units, and the inputs of every stage by bulk copies: positions and normals
+        // of the stage's sources, their weights for the unit's right-hand sides
         if (lane == 0) {
+            int64_t seq = 0;   // stages armed so far
             for (int uc = 0;; ++uc) {
                 const int slot = uc % kUnitRing;
                 if (uc >= kUnitRing &&
@@ -132,7 +142,48 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 ring[slot] = u;
                 bar_arrive(smem_addr(&ring_full[slot]));
                 if (u >= units) break;
+                const int64_t ii = u / nbc;
+                const int b0 = (int)(u - ii * nbc) * kRC, nb = min(kRC, Bact - b0);
+                const int4 item = __ldg(items + ii);
+                bool ok = true;
+                for (int iv = item.y; iv < item.z && ok; ++iv) {
+                    const int4 e = __ldg(ivl + iv);
+                    for (int sb = e.x; sb < e.y; sb += kSrc, ++seq) {
+                        const int s = (int)(seq % kStages);
+                        if (seq >= kStages &&
+                            !bar_wait(smem_addr(&empty_s[s]), (uint32_t)((seq / kStages) - 1) & 1u, &abort_s)) {
+                            ok = false;
+                            break;
+                        }
+                        const int n = min(kSrc, e.y - sb);
+                        const uint32_t rb = smem_addr(&raw_s[s]);
+                        const uint32_t dst = sbase + (uint32_t)(s * kStage + kOffRaw);
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(rb),
+                                     "r"((uint32_t)(n * 32 + n * nb * 16))
+                                     : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                dst + kRawPos),
+                            "l"(spos + sb), "r"(n * 16), "r"(rb)
+                            : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                dst + kRawNrm),
+                            "l"(snrm + sb), "r"(n * 16), "r"(rb)
+                            : "memory");
+                        for (int k = 0; k < n; ++k)
+                            asm volatile(
+                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                    dst + kRawW + (uint32_t)(k * kRC * 16)),
+                                "l"(sw + (int64_t)(sb + k) * B + b0), "r"(nb * 16), "r"(rb)
+                                : "memory");
+                    }
+                }
+                if (!ok) break;
             }
+            // the copies of the last armed stages may still be in flight
+            for (int64_t k = seq > kStages ? seq - kStages : 0; k < seq; ++k)
+                drain_wait(smem_addr(&raw_s[k % kStages]), (uint32_t)(k / kStages) & 1u);
         }
     } else if (warp == kMmaWarp) {
         // ---- MMA issue: one lane
@@ -282,6 +333,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int4 e = __ldg(ivl + iv);
                 const bool on = live && ((e.z >> blk) & 1);   // uniform over the warp but for the tail
                 for (int sb = e.x; sb < e.y && ok; sb += kSrc) {
+                    // the stage's inputs have landed (and its operands are free: the producer
+                    // armed the copies after the stage's previous MMAs completed)
+                    const int s = (int)(seq % kStages);
+                    if (!warp_wait(smem_addr(&raw_s[s]), (uint32_t)(seq / kStages) & 1u, &abort_s)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *stg = tc_smem + s * kStage;
+                    const float4 *rpos = (const float4 *)(stg + kOffRaw + kRawPos);
+                    const float4 *rnrm = (const float4 *)(stg + kOffRaw + kRawNrm);
+                    const float4 *rw = (const float4 *)(stg + kOffRaw + kRawW);
                     // the kernel operand row of this target: G and dG/dn of the stage's sources
                     float g[kSrc], h[kSrc];
 #pragma unroll
@@ -289,7 +351,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         g[k] = 0.f;
                         h[k] = 0.f;
                         if (on && sb + k < e.y) {
-                            const float4 p = __ldg(spos + sb + k), n = __ldg(snrm + sb + k);
+                            const float4 p = rpos[k], n = rnrm[k];
                             const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
                             float r = rsq(dx * dx + dy * dy + dz * dz);
                             r = panel_of(n.w) == tp ? 0.f : r;
@@ -302,15 +364,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         w[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (wr && wj < nb && sb + wk + i < e.y) w[i] = __ldg(sw + (int64_t)(sb + wk + i) * B + b0 + wj);
+                        if (wr && wj < nb && sb + wk + i < e.y) w[i] = rw[(wk + i) * kRC + wj];
                     }
-                    const int s = (int)(seq % kStages);
-                    if (seq >= kStages &&
-                        !warp_wait(smem_addr(&empty_s[s]), (uint32_t)((seq / kStages) - 1) & 1u, &abort_s)) {
-                        ok = false;
-                        break;
-                    }
-                    unsigned char *stg = tc_smem + s * kStage;
                     if (wr) {
                         const float4 vre = make_float4(w[0].x, w[1].x, w[2].x, w[3].x);
                         const float4 vim = make_float4(w[0].y, w[1].y, w[2].y, w[3].y);
