@@ -111,11 +111,12 @@ SFU_PER_CLK_SM = 16     # MUFU (rsqrt, reciprocal) results per clock per SM
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates, TF32 over BF16
 # DRAM bytes (read + write) per launch of the current kernels, from the ncu captures summarised in
-# profiles/{p2p,m2p,p2m}_fp32_sphere20480.md (dram__bytes.sum.per_second x gpu__time_duration.sum), keyed by
-# workload, kernel and treecode parameters (theta, P, Ncrit); None where no capture matches
-# (the P2P entry was dropped when its contraction became packed FFMA2: the kernel changed since the
-# capture, so its traffic is unknown until the next one)
-NCU_TRAFFIC = {("sphere20480", "m2p", 0.4, 5, 256): 2.410e6, ("sphere20480", "p2m", 0.4, 5, 256): 5.097e6}
+# profiles/ (dram__bytes_read.sum + dram__bytes_write.sum of one launch), keyed by workload, kernel and
+# treecode parameters (theta, P, Ncrit); None where no capture of the current kernel matches
+NCU_TRAFFIC = {("sphere20480", "m2p", 0.4, 5, 256): 2.410e6,          # m2p_fp32_sphere20480.md
+               ("sphere20480", "p2m", 0.4, 5, 256): 5.097e6,          # p2m_fp32_sphere20480.md
+               ("sphere20480", "p2p", 0.4, 5, 256): 5.045e6,          # p2p1_fp32_sphere20480.md
+               ("sphere81920_sweep64", "m2p", 0.4, 7, 512): 7.869e9}  # m2p_tc_sphere81920_sweep64.md
 
 
 def m2p_flops(P: int, B: int = 1) -> int:
