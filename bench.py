@@ -781,7 +781,7 @@ def run_study(args):
     sphere with six analytes at gaps of 0.5/1/2/4 nm on +-x, +-y, +-z, 32 wavelengths over
     370-400 nm each; "placement" = the 81920-panel sphere with two analytes at 1 nm on +-z, +-x
     or +-y.  Treecode parameters from the autotuner on the first geometry (one wavelength, the
-    one nearest the resonance, coarse grid)."""
+    one nearest the resonance, coarse grid), or fixed by --tree."""
     import torch
     from paper_1812_10722_gb300 import lspr
     from paper_1812_10722_gb300 import sensitivity as SN
@@ -795,18 +795,23 @@ def run_study(args):
     ctx = lspr.Context(0, torch.cuda.current_stream().cuda_stream)
     if args.tc is not None:
         ctx.set_tensor_cores(args.tc)
-    name0 = next(iter(geoms))
-    v, t, surf = geoms[name0]
-    S = int(surf.max()) + 1
-    lt = tuning_wavelengths(lam, 1)
-    e = np.full((1, S), 2.25 + 0j)
-    e[:, 0] = I.drude_eps(lt)
-    ctx.mesh_upload(v, t, surf_id=surf)
-    t0 = time.perf_counter()
-    tune = ctx.autotune(e, I.EPS_WATER, lt, target_rel_err=1e-4, tol=1e-8, restart=50, mode="tree_fp32", refine=1,
-                        coarse=True)
-    tune["seconds"] = round(time.perf_counter() - t0, 2)
-    tree = (tune["theta"], tune["P"], tune["Ncrit"])
+    if args.tree:
+        # fixed treecode parameters (--tree), no autotuning
+        th, P, nc = args.tree.split(",")
+        tree, tune = (float(th), int(P), int(nc)), None
+    else:
+        name0 = next(iter(geoms))
+        v, t, surf = geoms[name0]
+        S = int(surf.max()) + 1
+        lt = tuning_wavelengths(lam, 1)
+        e = np.full((1, S), 2.25 + 0j)
+        e[:, 0] = I.drude_eps(lt)
+        ctx.mesh_upload(v, t, surf_id=surf)
+        t0 = time.perf_counter()
+        tune = ctx.autotune(e, I.EPS_WATER, lt, target_rel_err=1e-4, tol=1e-8, restart=50, mode="tree_fp32",
+                            refine=1, coarse=True)
+        tune["seconds"] = round(time.perf_counter() - t0, 2)
+        tree = (tune["theta"], tune["P"], tune["Ncrit"])
     t0 = time.perf_counter()
     res = SN.shift_study(ctx, geoms, lam, sub, tree=tree)
     out = {"study": args.study, "wavelengths": [float(lam[0]), float(lam[-1]), len(lam)], "tree": tree,
