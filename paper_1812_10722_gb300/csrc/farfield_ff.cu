@@ -43,27 +43,27 @@ constexpr FfTermTable make_ff_terms() {
 
 __constant__ FfTermTable c_ff_terms = make_ff_terms();
 
-constexpr int kFfM2PWarps = 8;          // warps per block at most
-constexpr int kFfM2PSmem = 200 * 1024;  // shared memory per block at most
+constexpr int kFfM2PWarps = 4;
 
-// shared memory per warp: the lanes' coefficients (NT x 32)
-__host__ __device__ inline size_t ff_m2p_smem_per_warp(int NT) { return (size_t)NT * 32 * sizeof(ffloat); }
+// shared memory per warp: the staged moments of one box (NT x NB) and the lanes'
+// coefficients (NT x 32)
+__host__ __device__ inline size_t ff_m2p_smem_per_warp(int NT, int NB) {
+    return (size_t)NT * NB * sizeof(ff4) + (size_t)NT * 32 * sizeof(ffloat);
+}
 
-// Work units and accumulation as in m2p_kernel; NT = n_terms(P) at run time; the block has as
-// many warps as their coefficient arrays fit in shared memory.  Per (target, box) the rolled
-// recurrence first writes all coefficients into the lane's column of shared memory; the
-// contraction then reads the box's moments straight from global memory (every lane reads the
-// same moment: one broadcast load per term and right-hand side), so that the shared memory holds
-// the coefficients only and more warps fit on an SM.
+// Work units and accumulation as in m2p_kernel; NT = n_terms(P) at run time, W warps of
+// the block take part (the shared memory of a warp bounds how many fit).
 template <int NB>
 __global__ void __launch_bounds__(kFfM2PWarps * 32)
-    m2p_ff_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B, int NT,
+    m2p_ff_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B, int NT, int W,
                   const ff4 *__restrict__ tgt, int64_t ntgt, const int *__restrict__ list,
                   const ff4 *__restrict__ box_c, const ff4 *__restrict__ mom, double *__restrict__ acc, int *counter,
                   const int *nact) {
     extern __shared__ __align__(16) unsigned char ff_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    ffloat *sa = (ffloat *)(ff_smem + (size_t)warp * ff_m2p_smem_per_warp(NT));   // sa[t * 32 + lane]
+    if (warp >= W) return;
+    ff4 *sm = (ff4 *)(ff_smem + (size_t)warp * ff_m2p_smem_per_warp(NT, NB));
+    ffloat *sa = (ffloat *)(sm + NT * NB);   // sa[t * 32 + lane]
     const int Bact = nact ? *nact : B;   // right-hand sides in use (the first Bact slots)
     nbc = (Bact + NB - 1) / NB;
     const int64_t units = nitems * nbc;
@@ -88,11 +88,25 @@ __global__ void __launch_bounds__(kFfM2PWarps * 32)
             for (int l = item.y; l < item.z; ++l) {
                 const int b = __ldg(list + l);
                 const ff4 c = box_c[b];
+                __syncwarp();
+                for (int q2 = lane; q2 < NT * NB; q2 += 32) {
+                    const int t = q2 / NB, j = q2 - t * NB;
+                    sm[q2] = j < nb ? mom[((int64_t)b * NT + t) * B + b0 + j] : zero4<ff4>();
+                }
+                __syncwarp();
                 const ffloat R[3] = {q.x - c.x, q.y - c.y, q.z - c.z};
                 const ffloat r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
                 const ffloat a0 = rsq(r2);
                 const ffloat ir2 = a0 * a0;
                 sa[lane] = a0;
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const ff4 m = sm[j];
+                    a[j][0] += a0 * m.x;
+                    a[j][1] += a0 * m.y;
+                    a[j][2] += a0 * m.z;
+                    a[j][3] += a0 * m.w;
+                }
 #pragma unroll 1
                 for (int t = 1; t < NT; ++t) {
                     const FfTerm &e = c_ff_terms.t[t];
@@ -102,16 +116,11 @@ __global__ void __launch_bounds__(kFfM2PWarps * 32)
                         if (e.m1[d] >= 0) s1 += R[d] * sa[e.m1[d] * 32 + lane];
                         if (e.m2[d] >= 0) s2 += sa[e.m2[d] * 32 + lane];
                     }
-                    sa[t * 32 + lane] = (ffloat(e.c1h, e.c1l) * s1 + ffloat(e.c2h, e.c2l) * s2) * ir2;
-                }
-                const ff4 *mb = mom + (int64_t)b * NT * B + b0;
-#pragma unroll 1
-                for (int t = 0; t < NT; ++t) {
-                    const ffloat at = sa[t * 32 + lane];
+                    const ffloat at = (ffloat(e.c1h, e.c1l) * s1 + ffloat(e.c2h, e.c2l) * s2) * ir2;
+                    sa[t * 32 + lane] = at;
 #pragma unroll
                     for (int j = 0; j < NB; ++j) {
-                        if (j >= nb) break;
-                        const ff4 m = mb[(int64_t)t * B + j];
+                        const ff4 m = sm[t * NB + j];
                         a[j][0] += at * m.x;
                         a[j][1] += at * m.y;
                         a[j][2] += at * m.z;
@@ -133,27 +142,28 @@ __global__ void __launch_bounds__(kFfM2PWarps * 32)
 
 template <int NB>
 int m2p_ff_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
-    static int occ = 0, occ_w = -1;
+    static int occ = 0, occ_smem = -1;
     static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
     const int NT = n_terms(tr.P);
-    const size_t per = ff_m2p_smem_per_warp(NT);
-    const int W = (int)std::max<size_t>(1, std::min<size_t>(kFfM2PWarps, kFfM2PSmem / per));
+    const size_t per = ff_m2p_smem_per_warp(NT, NB);
+    const int W = (int)std::max<size_t>(1, std::min<size_t>(kFfM2PWarps, (96 * 1024) / per));
     const size_t smem = per * W;
     LSPR_TRY(ctx, allow_smem(m2p_ff_kernel<NB>, (int)smem, ctx->device, smem_set));
-    if (occ_w != W) {
+    if (occ_smem != (int)smem) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2p_ff_kernel<NB>, W * 32, smem) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2p_ff_kernel<NB>, kFfM2PWarps * 32, smem) !=
+                cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         occ = per_sm;
-        occ_w = W;
+        occ_smem = (int)smem;
     }
     const int nbc = (B + NB - 1) / NB;
     const unsigned grid = (unsigned)std::min<int64_t>((tr.n_m2p_items * nbc + W - 1) / W,
                                                       (int64_t)occ * std::max(1, ctx->num_sms));
-    m2p_ff_kernel<NB><<<grid, W * 32, smem, ctx->stream>>>(
-        tr.m2p_items.p, tr.n_m2p_items, nbc, B, NT, Views<ffloat>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p,
+    m2p_ff_kernel<NB><<<grid, kFfM2PWarps * 32, smem, ctx->stream>>>(
+        tr.m2p_items.p, tr.n_m2p_items, nbc, B, NT, W, Views<ffloat>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p,
         Views<ffloat>::bc(ctx), Views<ffloat>::mom(ctx), acc, counter, ctx->rhs_nact);
     return LSPR_OK;
 }
