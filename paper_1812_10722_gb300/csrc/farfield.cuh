@@ -117,6 +117,20 @@ __device__ __forceinline__ void p2p_range(int beg, int end, int lane, int B, int
                     a0[k][0] = v0.x; a0[k][1] = v0.y; a0[k][2] = k0.x; a0[k][3] = k0.y;
                     a1[k][0] = v1.x; a1[k][1] = v1.y; a1[k][2] = k1.x; a1[k][3] = k1.y;
                 }
+            } else if constexpr (std::is_same<T, ffloat>::value) {
+                // float-float: products accumulated without per-step renormalisation (ff_mac)
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    const T4 w = shw[kk][k];
+                    ff_mac(a0[k][0], r0, w.x);
+                    ff_mac(a0[k][1], r0, w.y);
+                    ff_mac(a0[k][2], t0, w.z);
+                    ff_mac(a0[k][3], t0, w.w);
+                    ff_mac(a1[k][0], r1, w.x);
+                    ff_mac(a1[k][1], r1, w.y);
+                    ff_mac(a1[k][2], t1, w.z);
+                    ff_mac(a1[k][3], t1, w.w);
+                }
             } else {
 #pragma unroll
                 for (int k = 0; k < NB; ++k) {

@@ -43,99 +43,98 @@ constexpr FfTermTable make_ff_terms() {
 
 __constant__ FfTermTable c_ff_terms = make_ff_terms();
 
-constexpr int kFfM2PWarps = 4;
-
-// shared memory per warp: the staged moments of one box (NT x NB) and the lanes'
-// coefficients (NT x 32)
-__host__ __device__ inline size_t ff_m2p_smem_per_warp(int NT, int NB) {
-    return (size_t)NT * NB * sizeof(ff4) + (size_t)NT * 32 * sizeof(ffloat);
+// Shared memory of a block: the staged moments of one box for its chunk of right-hand sides
+// (NT x NB, shared by the block's two warps) and each warp's coefficients (2 x NT x 32)
+__host__ __device__ inline size_t ff_m2p_smem(int NT, int NB) {
+    return (size_t)NT * NB * sizeof(ff4) + 2 * (size_t)NT * 32 * sizeof(ffloat);
 }
 
-// Work units and accumulation as in m2p_kernel; NT = n_terms(P) at run time, W warps of
-// the block take part (the shared memory of a warp bounds how many fit).
+// Work units and accumulation as in m2p_kernel; NT = n_terms(P) at run time.  A block of two
+// warps takes a unit: warp h the targets 32 h .. 32 h + 31 of the 64-target block, both on the
+// same boxes, so each box's moments are staged once for the two.  The recurrence is rolled
+// (each lane's coefficients live in its column of the warp's array), and the contraction
+// accumulates with ff_mac.
 template <int NB>
-__global__ void __launch_bounds__(kFfM2PWarps * 32)
-    m2p_ff_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B, int NT, int W,
+__global__ void __launch_bounds__(64)
+    m2p_ff_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B, int NT,
                   const ff4 *__restrict__ tgt, int64_t ntgt, const int *__restrict__ list,
                   const ff4 *__restrict__ box_c, const ff4 *__restrict__ mom, double *__restrict__ acc, int *counter,
                   const int *nact) {
     extern __shared__ __align__(16) unsigned char ff_smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp >= W) return;
-    ff4 *sm = (ff4 *)(ff_smem + (size_t)warp * ff_m2p_smem_per_warp(NT, NB));
-    ffloat *sa = (ffloat *)(sm + NT * NB);   // sa[t * 32 + lane]
+    __shared__ int64_t unit;
+    const int h = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    ff4 *sm = (ff4 *)ff_smem;
+    ffloat *sa = (ffloat *)(sm + NT * NB) + (size_t)h * NT * 32;   // sa[t * 32 + lane]
     const int Bact = nact ? *nact : B;   // right-hand sides in use (the first Bact slots)
     nbc = (Bact + NB - 1) / NB;
     const int64_t units = nitems * nbc;
     while (true) {
-        int v = 0;
-        if (lane == 0) v = atomicAdd(counter, 1);
-        const int64_t it = __shfl_sync(0xffffffffu, v, 0);
+        if (threadIdx.x == 0) unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t it = unit;
+        __syncthreads();   // every thread has read the unit before thread 0 takes the next one
         if (it >= units) return;
         const int64_t ii = it / nbc;
         const int b0 = (int)(it - ii * nbc) * NB, nb = min(NB, Bact - b0);
         const int4 item = __ldg(items + ii);
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            const int64_t ti = (int64_t)item.x * kTargetBlock + lane + 32 * h;
-            const ff4 q = ti < ntgt ? tgt[ti] : tgt[0];
-            ffloat a[NB][4];
+        const int64_t ti = (int64_t)item.x * kTargetBlock + lane + 32 * h;
+        const ff4 q = ti < ntgt ? tgt[ti] : tgt[0];
+        ffloat a[NB][4];
 #pragma unroll
-            for (int j = 0; j < NB; ++j)
+        for (int j = 0; j < NB; ++j)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) a[j][c] = ffloat(0.f, 0.f);
+            for (int c = 0; c < 4; ++c) a[j][c] = ffloat(0.f, 0.f);
 #pragma unroll 1
-            for (int l = item.y; l < item.z; ++l) {
-                const int b = __ldg(list + l);
-                const ff4 c = box_c[b];
-                __syncwarp();
-                for (int q2 = lane; q2 < NT * NB; q2 += 32) {
-                    const int t = q2 / NB, j = q2 - t * NB;
-                    sm[q2] = j < nb ? mom[((int64_t)b * NT + t) * B + b0 + j] : zero4<ff4>();
+        for (int l = item.y; l < item.z; ++l) {
+            const int b = __ldg(list + l);
+            const ff4 c = box_c[b];
+            __syncthreads();   // the previous box's moments are no longer read
+            for (int q2 = threadIdx.x; q2 < NT * NB; q2 += 64) {
+                const int t = q2 / NB, j = q2 - t * NB;
+                sm[q2] = j < nb ? mom[((int64_t)b * NT + t) * B + b0 + j] : zero4<ff4>();
+            }
+            __syncthreads();
+            const ffloat R[3] = {q.x - c.x, q.y - c.y, q.z - c.z};
+            const ffloat r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+            const ffloat a0 = rsq(r2);
+            const ffloat ir2 = a0 * a0;
+            sa[lane] = a0;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                const ff4 m = sm[j];
+                ff_mac(a[j][0], a0, m.x);
+                ff_mac(a[j][1], a0, m.y);
+                ff_mac(a[j][2], a0, m.z);
+                ff_mac(a[j][3], a0, m.w);
+            }
+#pragma unroll 1
+            for (int t = 1; t < NT; ++t) {
+                const FfTerm &e = c_ff_terms.t[t];
+                ffloat s1(0.f, 0.f), s2(0.f, 0.f);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (e.m1[d] >= 0) s1 += R[d] * sa[e.m1[d] * 32 + lane];
+                    if (e.m2[d] >= 0) s2 += sa[e.m2[d] * 32 + lane];
                 }
-                __syncwarp();
-                const ffloat R[3] = {q.x - c.x, q.y - c.y, q.z - c.z};
-                const ffloat r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
-                const ffloat a0 = rsq(r2);
-                const ffloat ir2 = a0 * a0;
-                sa[lane] = a0;
+                const ffloat at = (ffloat(e.c1h, e.c1l) * s1 + ffloat(e.c2h, e.c2l) * s2) * ir2;
+                sa[t * 32 + lane] = at;
 #pragma unroll
                 for (int j = 0; j < NB; ++j) {
-                    const ff4 m = sm[j];
-                    a[j][0] += a0 * m.x;
-                    a[j][1] += a0 * m.y;
-                    a[j][2] += a0 * m.z;
-                    a[j][3] += a0 * m.w;
-                }
-#pragma unroll 1
-                for (int t = 1; t < NT; ++t) {
-                    const FfTerm &e = c_ff_terms.t[t];
-                    ffloat s1(0.f, 0.f), s2(0.f, 0.f);
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        if (e.m1[d] >= 0) s1 += R[d] * sa[e.m1[d] * 32 + lane];
-                        if (e.m2[d] >= 0) s2 += sa[e.m2[d] * 32 + lane];
-                    }
-                    const ffloat at = (ffloat(e.c1h, e.c1l) * s1 + ffloat(e.c2h, e.c2l) * s2) * ir2;
-                    sa[t * 32 + lane] = at;
-#pragma unroll
-                    for (int j = 0; j < NB; ++j) {
-                        const ff4 m = sm[t * NB + j];
-                        a[j][0] += at * m.x;
-                        a[j][1] += at * m.y;
-                        a[j][2] += at * m.z;
-                        a[j][3] += at * m.w;
-                    }
+                    const ff4 m = sm[t * NB + j];
+                    ff_mac(a[j][0], at, m.x);
+                    ff_mac(a[j][1], at, m.y);
+                    ff_mac(a[j][2], at, m.z);
+                    ff_mac(a[j][3], at, m.w);
                 }
             }
-            if (ti < ntgt) {
-                const int64_t tp = panel_of(q.w);
+        }
+        if (ti < ntgt) {
+            const int64_t tp = panel_of(q.w);
 #pragma unroll
-                for (int j = 0; j < NB; ++j)
-                    if (j < nb)
-                        atomic_add4(acc + 4 * (tp * B + b0 + j), (double)a[j][0], (double)a[j][1], (double)a[j][2],
-                                    (double)a[j][3]);
-            }
+            for (int j = 0; j < NB; ++j)
+                if (j < nb)
+                    atomic_add4(acc + 4 * (tp * B + b0 + j), (double)a[j][0], (double)a[j][1], (double)a[j][2],
+                                (double)a[j][3]);
         }
     }
 }
@@ -146,24 +145,21 @@ int m2p_ff_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
     const int NT = n_terms(tr.P);
-    const size_t per = ff_m2p_smem_per_warp(NT, NB);
-    const int W = (int)std::max<size_t>(1, std::min<size_t>(kFfM2PWarps, (96 * 1024) / per));
-    const size_t smem = per * W;
+    const size_t smem = ff_m2p_smem(NT, NB);
     LSPR_TRY(ctx, allow_smem(m2p_ff_kernel<NB>, (int)smem, ctx->device, smem_set));
     if (occ_smem != (int)smem) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2p_ff_kernel<NB>, kFfM2PWarps * 32, smem) !=
-                cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2p_ff_kernel<NB>, 64, smem) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;
         occ = per_sm;
         occ_smem = (int)smem;
     }
     const int nbc = (B + NB - 1) / NB;
-    const unsigned grid = (unsigned)std::min<int64_t>((tr.n_m2p_items * nbc + W - 1) / W,
-                                                      (int64_t)occ * std::max(1, ctx->num_sms));
-    m2p_ff_kernel<NB><<<grid, kFfM2PWarps * 32, smem, ctx->stream>>>(
-        tr.m2p_items.p, tr.n_m2p_items, nbc, B, NT, W, Views<ffloat>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p,
+    const unsigned grid =
+        (unsigned)std::min<int64_t>(tr.n_m2p_items * nbc, (int64_t)occ * std::max(1, ctx->num_sms));
+    m2p_ff_kernel<NB><<<grid, 64, smem, ctx->stream>>>(
+        tr.m2p_items.p, tr.n_m2p_items, nbc, B, NT, Views<ffloat>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p,
         Views<ffloat>::bc(ctx), Views<ffloat>::mom(ctx), acc, counter, ctx->rhs_nact);
     return LSPR_OK;
 }
