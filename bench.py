@@ -558,8 +558,8 @@ def run_ours(args, wl, rank, world, local_rank):
         "kernels": kernels,
         "kernel_timing": {"how": "CUDA events around every launch, instrumented replay of the first "
                                  f"{replay_steps} timed steps (far-field kernels one after another on one "
-                                 "stream; host-driven Arnoldi cycles, which multiply every right-hand side "
-                                 "in every step; same kernels and inputs)",
+                                 "stream; Arnoldi cycles launched from the host instead of a graph loop: "
+                                 "same kernels and inputs)",
                           "replay_ms_per_step": round(replay_ms / replay_steps, 3)},
         "arnoldi_graphs": graph_stats,
         "tree": {"boxes": info["n_boxes"], "p2p_pairs_per_matvec": info["n_p2p_pairs"],

@@ -163,7 +163,8 @@ LSPR_API int lspr_matvec(lspr_ctx *ctx, const double *x, double *y, int32_t B, c
  *   dipole_out [B][3] complex, sigma_ext_out [B] (nm^2): caller-allocated.
  * The right-hand side V((eps_out-eps_in)/eps_out dphi_inc/dn), dphi_inc/dn = -E0.n,
  * is formed with the operator of the matvec mode of `o` (FP64 accumulation in every
- * mode); GMRES (right 2x2 block-Jacobi preconditioner, FP64 Krylov basis) runs in
+ * mode); GMRES (right 2x2 block-Jacobi preconditioner; Krylov basis and Gram-Schmidt in
+ * float-float, ~48 significant bits, rotations and solution in FP64) runs in
  * that mode, and with o->refine in an FP32 mode the residual of a refinement cycle
  * is formed with the float-float (refine 1) or FP64 (refine 2) operator of the same
  * kind, or, once it is below 1e3 tol ||b||, updated with the FP32 product of the last
@@ -280,9 +281,10 @@ LSPR_API int lspr_get_timing_rhs(lspr_ctx *ctx, int64_t *rhs);
  * per restart cycle instead of once per step.  The graph of a configuration (buffer
  * sizes, mode, B, restart) is recorded on first use and reused, also across mesh and
  * tree rebuilds of the same sizes.  lspr_set_graphs(ctx, 0) selects host-driven cycles
- * (same arithmetic); kernel timing (lspr_set_timing) also uses them, since timing
- * events cannot sit inside a graph loop.  If recording fails the context falls back
- * to host-driven cycles. */
+ * (the same kernels launched by the host, which reads the loop condition after each
+ * step); kernel timing (lspr_set_timing) also uses them, since timing events cannot sit
+ * inside a graph loop.  If recording fails the context falls back to host-driven
+ * cycles. */
 LSPR_API int lspr_set_graphs(lspr_ctx *ctx, int32_t enable);
 /* Tensor cores for the FP32 far field of several right-hand sides (B >= 2), as a mask:
  * bit 0 (default on): the M2P contraction on tcgen05 (TF32 operands split into high and low

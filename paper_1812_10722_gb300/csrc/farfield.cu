@@ -69,6 +69,31 @@ __global__ void weights_kernel(int64_t Ns, int64_t N, int B, int S, const dbl4 *
     w[g] = o;
 }
 
+// The same for FP32 products of several right-hand sides from the FP32 transposed copy
+// xt [2N][B], in FP32 arithmetic (the weights feed FP32 kernels; FP64 arithmetic would run
+// at 1/64 of the FP32 rate on this GPU)
+__global__ void weights_f32t_kernel(int64_t Ns, int64_t N, int B, int S, const float4 *__restrict__ spos32,
+                                    const int *__restrict__ src_panel, const int *__restrict__ surf,
+                                    const float2 *__restrict__ xt, float4 *__restrict__ w, const int *map,
+                                    const int *nact) {
+    const int BS = B * S;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= Ns * BS) return;
+    const int64_t s = g / BS;
+    const int slot = (int)(g - s * BS);
+    if (nact && slot >= *nact) return;
+    const int p = src_panel[s];
+    const int k = slot / S, t = slot - k * S;
+    const int b = map ? map[k] : k;
+    if (S > 1 && surf[p] != t) {
+        w[g] = zero4<float4>();
+        return;
+    }
+    const float wa = spos32[s].w * (float)kInv4Pi;
+    const float2 phi = xt[(int64_t)p * B + b], dphi = xt[(N + p) * B + b];
+    w[g] = make_float4(wa * dphi.x, wa * dphi.y, wa * phi.x, wa * phi.y);
+}
+
 // item.w = 1 iff some source of [item.y, item.z) belongs to a panel of the item's target block
 __global__ void item_flags_kernel(int4 *items, int64_t nitems, const int *__restrict__ src_tblock) {
     const int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -95,7 +120,8 @@ __global__ void to_ff_kernel(int64_t n, const dbl4 *__restrict__ a, ff4 *__restr
 }
 
 // --------------------------------------------------------------- launchers
-int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt, int64_t N, int B, int S) {
+int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt, int64_t N, int B, int S,
+                   const float2 *xtf) {
     const int64_t Ns = ctx->mesh.Ns;
     const int BS = B * S;
     const unsigned grid = grid_for(Ns * BS, 256);
@@ -110,6 +136,11 @@ int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt,
         LSPR_TRY(ctx, ctx->w_ff.ensure(Ns * BS));
         weights_kernel<ff4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, S, ctx->wo.spos64.p, ctx->wo.src_panel.p, ctx->mesh.surf.p, x, xt,
                                                            ctx->w_ff.p, ctx->rhs_map, ctx->rhs_nact);
+    } else if (xtf) {
+        LSPR_TRY(ctx, ctx->w32.ensure(Ns * BS));
+        weights_f32t_kernel<<<grid, 256, 0, ctx->stream>>>(Ns, N, B, S, ctx->wo.spos32.p, ctx->wo.src_panel.p,
+                                                           ctx->mesh.surf.p, xtf, ctx->w32.p, ctx->rhs_map,
+                                                           ctx->rhs_nact);
     } else {
         LSPR_TRY(ctx, ctx->w32.ensure(Ns * BS));
         weights_kernel<float4><<<grid, 256, 0, ctx->stream>>>(Ns, N, B, S, ctx->wo.spos64.p, ctx->wo.src_panel.p, ctx->mesh.surf.p, x, xt,

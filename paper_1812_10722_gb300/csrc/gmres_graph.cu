@@ -1,9 +1,9 @@
-// Restarted GMRES(m) (Sec. II.D-E: complex GMRES) with device-driven Arnoldi cycles.
+// Restarted GMRES(m) (Sec. II.D-E: complex GMRES) for B systems in lockstep.
 //
-// One cycle of B systems in lockstep is one CUDA graph launch:
+// One Arnoldi cycle:
 //   init        v_0 = r / beta, g = beta e_1
-//   while node  (the body is one Arnoldi step; the last kernel of the body decides, on
-//               the device, whether another step follows)
+//   loop        (the body is one Arnoldi step; its last kernel decides, on the device,
+//               whether another step follows)
 //                 z = M^-1 v_j                      (v_j = w / ||w|| formed here, j > 0)
 //                 w = A z                           (the far field, near SpMV and block rows)
 //                 classical Gram-Schmidt h = V^H w, w -= V h, repeated once for the systems
@@ -14,17 +14,25 @@
 //                 ||w||, Givens rotation of the new Hessenberg column, residual
 //                 estimate |g_{j+1}|, per-system stop test
 //   back substitution R y = g, x += M^-1 V y
-// so the host only takes part once per cycle (explicit residual and stop decision).
-// Inner products reduce over blocks with a last-block ticket instead of a second launch.
-// The arithmetic is that of the host-driven GMRES in solve.cu (FP64 Krylov basis, right 2x2
-// block-Jacobi preconditioner, the same rotation convention), whose Gram-Schmidt always takes
-// the second pass (CGS2); here the second pass runs only where the criterion asks for it, which
-// removes up to half of the basis traffic that dominates a step's vector work.
+// The cycle is recorded once as a CUDA graph whose loop is a conditional WHILE node, so the
+// host only takes part once per cycle (explicit residual and stop decision).  Without graphs
+// (or with per-kernel timing) the host launches the same kernels itself and reads the loop
+// condition after every step.  Inner products reduce over blocks with a last-block ticket
+// instead of a second launch.
+//
+// Precision.  The Krylov basis, the Gram-Schmidt coefficients and the vector being
+// orthogonalised are float-float (hi + lo FP32 pairs, ~48 significant bits): on this GPU the
+// FP64 pipe runs at 1/64 of the FP32 rate, and the Gram-Schmidt passes (8 FP64 multiply-adds
+// per basis entry and pass) would be bound by it at ~3x the time of reading the basis from
+// memory.  In float-float they are bound by the basis traffic.  A basis entry takes 16 bytes
+// as in FP64.  The rotations, the small triangular solve, norms' final sums, the residual and
+// the solution stay FP64.
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "cplx.cuh"
+#include "ffloat.cuh"
 #include "lspr_internal.cuh"
 
 namespace lspr {
@@ -36,15 +44,72 @@ constexpr double kReorthEta = 0.70710678118654752;   // second pass when ||w_1||
 constexpr int kDotChunk = kT * kPer;    // elements per inner-product block
 constexpr int kMaxWarpsSmall = 16;      // warps of the per-system (rotation, back substitution) kernels
 
+// one complex entry in float-float: re = rh + rl, im = ih + il
+struct __align__(16) cff {
+    float rh, ih, rl, il;
+};
+static_assert(sizeof(cff) == sizeof(float4), "a basis entry is one 16-byte word");
+
+__device__ __forceinline__ cff to_cff(double2 v) {
+    const float rh = (float)v.x, ih = (float)v.y;
+    return {rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih)};
+}
+__device__ __forceinline__ double2 to_d2(const cff &v) {
+    return make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+}
+__device__ __forceinline__ ffloat re_of(const cff &v) { return ffloat(v.rh, v.rl); }
+__device__ __forceinline__ ffloat im_of(const cff &v) { return ffloat(v.ih, v.il); }
+
+// hi + lo renormalised (|lo| <= ulp(hi)/2) after unnormalised accumulation
+__device__ __forceinline__ ffloat ff_norm(const ffloat &x) {
+    ffloat r;
+    ff_two_sum(x.hi, x.lo, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ cff pack(const ffloat &re, const ffloat &im) {
+    const ffloat r = ff_norm(re), i = ff_norm(im);
+    return {r.hi, i.hi, r.lo, i.lo};
+}
+
+// (sr, si) += conj(v) w
+__device__ __forceinline__ void cff_conj_mac(ffloat &sr, ffloat &si, const cff &v, const cff &w) {
+    const ffloat vr = re_of(v), vi = im_of(v), wr = re_of(w), wi = im_of(w);
+    ff_mac(sr, vr, wr);
+    ff_mac(sr, vi, wi);
+    ff_mac(si, vr, wi);
+    ff_mac(si, -vi, wr);
+}
+// (ar, ai) += v h, or -= v h with SUB
+template <bool SUB>
+__device__ __forceinline__ void cff_mac(ffloat &ar, ffloat &ai, const cff &v, const cff &h) {
+    const ffloat vr = SUB ? -re_of(v) : re_of(v), vi = SUB ? -im_of(v) : im_of(v);
+    const ffloat hr = re_of(h), hi = im_of(h);
+    ff_mac(ar, vr, hr);
+    ff_mac(ar, -vi, hi);
+    ff_mac(ai, vr, hi);
+    ff_mac(ai, vi, hr);
+}
+// |v|^2 added to s
+__device__ __forceinline__ void cff_abs2_mac(ffloat &s, const ffloat &re, const ffloat &im) {
+    ff_mac(s, re, re);
+    ff_mac(s, im, im);
+}
+
 struct Arn {
     int B, m, nch, nblk;
     int64_t N, n2, vstride;
-    double2 *V, *w, *z, *x;
+    cff *V;              // [B][m+1][2N] Krylov basis
+    double2 *w;          // [B][2N] A z (FP64 from the operator; float-float in place once the
+                         // first Gram-Schmidt pass has read it)
+    double2 *z, *x;
     const double2 *b, *s;
-    const double *Vself;
-    const int *surf;   // surface of each panel; s is [B][S]
+    const double *vinv;  // [N] 1 / V_ii (preconditioner)
+    const double2 *pq;   // [B][S] 1 / (1 + s) (preconditioner)
+    const int *surf;     // surface of each panel; s is [B][S]
     int S;
     double2 *h, *hcol, *part, *H, *sn, *g, *y;
+    cff *hff, *yff;      // [B][m+1] Gram-Schmidt coefficients, [B][m] update coefficients
+    ffloat *ninv;        // [B] 1 / ||w||
     double *npart, *nrm, *cs, *res, *npart0, *nrm0;
     int *reorth;
     const double *bn, *par;
@@ -52,8 +117,11 @@ struct Arn {
     int *jdev, *active, *jb, *iters;
     int *rmap;   // [2B + 2]: slot -> system, system -> slot (-1: not running), running count,
                  // channel sets in use (running count x surfaces)
+    int *go;     // host-driven cycles: the loop condition (nullptr inside a graph)
     cudaGraphConditionalHandle cond;
 };
+
+__device__ __forceinline__ cff *wff(const Arn &a, int b) { return (cff *)(a.w + (int64_t)b * a.n2); }
 
 // packs the running systems into the first slots (single thread)
 __device__ __forceinline__ void pack_running(const Arn &a) {
@@ -78,6 +146,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 __device__ __forceinline__ double2 warp_sum2(double2 v) { return make_double2(warp_sum(v.x), warp_sum(v.y)); }
 
+__device__ __forceinline__ ffloat shfl_xor(const ffloat &v, int o) {
+    return ffloat(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+__device__ __forceinline__ ffloat ff_warp_sum(ffloat v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = v + shfl_xor(v, o);
+    return v;
+}
+
 // sum over a block of kT threads, valid in warp 0
 __device__ __forceinline__ double block_sum(double v, double *sh) {
     v = warp_sum(v);
@@ -85,6 +162,17 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x < 32) t = warp_sum(threadIdx.x < kT / 32 ? sh[threadIdx.x] : 0.0);
+    return t;
+}
+// float-float partial sums of a block: warps reduce in float-float, warp 0 sums the kT/32
+// warp results in FP64 (valid in thread 0)
+__device__ __forceinline__ double block_sum_ff(const ffloat &v, double *sh) {
+    const ffloat s = ff_warp_sum(ff_norm(v));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)s;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < kT / 32; ++q) t += sh[q];
     return t;
 }
 
@@ -99,8 +187,8 @@ __device__ __forceinline__ bool last_block(unsigned *t, unsigned count) {
     return last;
 }
 
-// final sum of the squared-norm partials of system b into nrm[b] (last block only); decide:
-// the first Gram-Schmidt pass decides whether the second runs
+// final sum of the squared-norm partials of system b into nrm[b] and 1/nrm[b] (last block
+// only); decide: the first Gram-Schmidt pass decides whether the second runs
 __device__ __forceinline__ void norm_final(const Arn &a, int b, double *sh, bool decide = false) {
     double t = 0.0;
     for (int c = threadIdx.x; c < a.nblk; c += kT) t += __ldcg(a.npart + (int64_t)b * a.nblk + c);
@@ -108,9 +196,20 @@ __device__ __forceinline__ void norm_final(const Arn &a, int b, double *sh, bool
     if (threadIdx.x == 0) {
         const double r = sqrt(t);
         a.nrm[b] = r;
+        a.ninv[b] = ffloat(r > 0 ? 1.0 / r : 0.0);
         if (decide) a.reorth[b] = !(r >= kReorthEta * __ldcg(a.nrm0 + b));
         a.tick[a.B + b] = 0;
     }
+}
+
+// Right preconditioner of panel i (inverse of the diagonal 2x2 block of the operator,
+// [[1/2 + K_ii, -V_ii], [1/2 - K_ii, s V_ii]] with K_ii = 0):
+//   o0 = 2 (s u0 + u1) / (1 + s),  o1 = (u1 - u0) / (V_ii (1 + s))
+// with pq = 1 / (1 + s) and vinv = 1 / V_ii formed once per solve (no division per entry)
+__device__ __forceinline__ void precond(double vinv, double2 q, double2 s, double2 u0, double2 u1, double2 &o0,
+                                        double2 &o1) {
+    o0 = cscale(cmul(q, cadd(cmul(s, u0), u1)), 2.0);
+    o1 = cscale(cmul(q, csub(u1, u0)), vinv);
 }
 
 // w = A x - b (w holds A x on entry; x_zero: x = 0 and w = -b), nrm[b] = ||w||
@@ -136,7 +235,7 @@ __global__ void __launch_bounds__(kT) arn_init_kernel(Arn a) {
     const int b = blockIdx.y;
     const int64_t k = blockIdx.x * (int64_t)kT + threadIdx.x;
     const bool act = a.active[b] != 0;
-    if (act && k < a.n2) a.V[(int64_t)b * a.vstride + k] = cscale(a.w[(int64_t)b * a.n2 + k], -1.0 / a.nrm[b]);
+    if (act && k < a.n2) a.V[(int64_t)b * a.vstride + k] = to_cff(cscale(a.w[(int64_t)b * a.n2 + k], -1.0 / a.nrm[b]));
     if (blockIdx.x == 0) {
         for (int i = threadIdx.x; i <= a.m; i += kT)
             a.g[(int64_t)b * (a.m + 1) + i] = make_double2(i == 0 && act ? a.nrm[b] : 0.0, 0.0);
@@ -152,36 +251,37 @@ __global__ void __launch_bounds__(kT) arn_init_kernel(Arn a) {
     }
 }
 
-// v_j = w / ||w|| (j > 0; v_0 comes from the init kernel), z = M^-1 v_j
+// v_j = w / ||w|| (j > 0, w float-float; v_0 comes from the init kernel), z = M^-1 v_j
 __global__ void __launch_bounds__(kT) arn_precond_kernel(Arn a) {
     const int b = blockIdx.y;
     const int64_t t = blockIdx.x * (int64_t)kT + threadIdx.x;
     if (t >= a.N || !a.active[b]) return;
     const int j = *a.jdev;
-    double2 *Vj = a.V + (int64_t)b * a.vstride + (int64_t)j * a.n2;
-    double2 u0, u1;
+    cff *Vj = a.V + (int64_t)b * a.vstride + (int64_t)j * a.n2;
+    cff v0, v1;
     if (j == 0) {
-        u0 = Vj[t];
-        u1 = Vj[a.N + t];
+        v0 = Vj[t];
+        v1 = Vj[a.N + t];
     } else {
-        const double d = a.nrm[b];
-        const double inv = d > 0 ? 1.0 / d : 0.0;
-        const double2 *wb = a.w + (int64_t)b * a.n2;
-        u0 = cscale(wb[t], inv);
-        u1 = cscale(wb[a.N + t], inv);
-        Vj[t] = u0;
-        Vj[a.N + t] = u1;
+        const ffloat inv = a.ninv[b];
+        const cff *wb = wff(a, b);
+        const cff w0 = wb[t], w1 = wb[a.N + t];
+        v0 = pack(re_of(w0) * inv, im_of(w0) * inv);
+        v1 = pack(re_of(w1) * inv, im_of(w1) * inv);
+        Vj[t] = v0;
+        Vj[a.N + t] = v1;
     }
     double2 o0, o1;
-    block_jacobi(a.Vself[t], a.s[b * a.S + a.surf[t]], u0, u1, o0, o1);
+    precond(a.vinv[t], a.pq[b * a.S + a.surf[t]], a.s[b * a.S + a.surf[t]], to_d2(v0), to_d2(v1), o0, o1);
     a.z[(int64_t)b * a.n2 + t] = o0;
     a.z[(int64_t)b * a.n2 + a.N + t] = o1;
 }
 
 // One classical Gram-Schmidt pass, first half: h_i = <v_i, w> for i <= j.  Each block
-// forms the partial products of its chunk for every basis vector; the last block of the
-// system sums the chunks into h and into the Hessenberg column (hcol = h on pass 0,
-// hcol += h on pass 1).
+// forms the partial products of its chunk for every basis vector (float-float in the
+// threads and warps, FP64 across warps and blocks); the last block of the system sums the
+// chunks into h (FP64 and float-float) and into the Hessenberg column (hcol = h on pass 0,
+// hcol += h on pass 1).  Pass 0 converts w to float-float in place and forms ||w||.
 __global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
     __shared__ double2 red[kT / 32][32];
     __shared__ double shn[kT / 32];
@@ -190,33 +290,42 @@ __global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
     const int nv = *a.jdev + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t base = (int64_t)chunk * kDotChunk + threadIdx.x;
-    const double2 *wb = a.w + (int64_t)b * a.n2;
-    const double2 *Vb = a.V + (int64_t)b * a.vstride;
-    double2 wr[kPer];
-    double w2 = 0.0;
+    cff *wb = wff(a, b);
+    const cff *Vb = a.V + (int64_t)b * a.vstride;
+    cff wr[kPer];
+    ffloat w2(0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
         const int64_t k = base + r * kT;
-        wr[r] = k < a.n2 ? wb[k] : make_double2(0.0, 0.0);
-        w2 += cabs2(wr[r]);
+        wr[r] = {0.f, 0.f, 0.f, 0.f};
+        if (k < a.n2) {
+            if (pass == 0) {
+                wr[r] = to_cff(a.w[(int64_t)b * a.n2 + k]);
+                wb[k] = wr[r];
+            } else {
+                wr[r] = wb[k];
+            }
+        }
+        if (pass == 0) cff_abs2_mac(w2, re_of(wr[r]), im_of(wr[r]));
     }
     if (pass == 0) {   // ||A z||^2 of this chunk, for the second-pass criterion
-        w2 = block_sum(w2, shn);
-        if (threadIdx.x == 0) a.npart0[(int64_t)b * a.nch + chunk] = w2;
+        const double t = block_sum_ff(w2, shn);
+        if (threadIdx.x == 0) a.npart0[(int64_t)b * a.nch + chunk] = t;
     }
     double2 *pb = a.part + (int64_t)b * (a.m + 1) * a.nch;
     for (int i0 = 0; i0 < nv; i0 += 32) {
         const int cnt = min(32, nv - i0);
         for (int ii = 0; ii < cnt; ++ii) {
-            const double2 *v = Vb + (int64_t)(i0 + ii) * a.n2;
-            double2 s = make_double2(0.0, 0.0);
+            const cff *v = Vb + (int64_t)(i0 + ii) * a.n2;
+            ffloat sr(0.f, 0.f), si(0.f, 0.f);
 #pragma unroll
             for (int r = 0; r < kPer; ++r) {
                 const int64_t k = base + r * kT;
-                if (k < a.n2) s = cadd(s, cconjmul(v[k], wr[r]));
+                if (k < a.n2) cff_conj_mac(sr, si, v[k], wr[r]);
             }
-            s = warp_sum2(s);
-            if (lane == 0) red[warp][ii] = s;
+            sr = ff_warp_sum(ff_norm(sr));
+            si = ff_warp_sum(ff_norm(si));
+            if (lane == 0) red[warp][ii] = make_double2((double)sr, (double)si);
         }
         __syncthreads();
         if (threadIdx.x < cnt) {
@@ -250,6 +359,7 @@ __global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
             const double2 sum = warp_sum2(t[u]);
             if (lane == 0 && i < nv) {
                 a.h[(int64_t)b * (a.m + 1) + i] = sum;
+                a.hff[(int64_t)b * (a.m + 1) + i] = to_cff(sum);
                 double2 &e = a.hcol[(int64_t)b * (a.m + 1) + i];
                 e = pass ? cadd(e, sum) : sum;
             }
@@ -258,27 +368,32 @@ __global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
     if (threadIdx.x == 0) a.tick[b] = 0;
 }
 
-// Second half of a pass: w -= sum_{i <= j} v_i h_i, then ||w|| into nrm[b] (partials per
-// block, the last block sums them); after the first pass the last block also decides whether
-// the second runs (reorth[b])
+// Second half of a pass: w -= sum_{i <= j} v_i h_i (float-float), then ||w|| into nrm[b]
+// (partials per block, the last block sums them); after the first pass the last block also
+// decides whether the second runs (reorth[b])
 __global__ void __launch_bounds__(kT) arn_axpy_kernel(Arn a, int pass) {
     __shared__ double sh[kT / 32];
+    __shared__ cff hs[kMaxRestart + 1];
     const int b = blockIdx.y;
     if (!a.active[b] || (pass && !a.reorth[b])) return;
     const int nv = *a.jdev + 1;
+    for (int i = threadIdx.x; i < nv; i += kT) hs[i] = a.hff[(int64_t)b * (a.m + 1) + i];
+    __syncthreads();
     const int64_t k = blockIdx.x * (int64_t)kT + threadIdx.x;
-    const double2 *hb = a.h + (int64_t)b * (a.m + 1);
-    double q = 0.0;
+    ffloat q(0.f, 0.f);
     if (k < a.n2) {
-        const double2 *Vb = a.V + (int64_t)b * a.vstride + k;
-        double2 acc = a.w[(int64_t)b * a.n2 + k];
+        const cff *Vb = a.V + (int64_t)b * a.vstride + k;
+        cff *wk = wff(a, b) + k;
+        const cff w0 = *wk;
+        ffloat ar = re_of(w0), ai = im_of(w0);
 #pragma unroll 4
-        for (int i = 0; i < nv; ++i) acc = csub(acc, cmul(Vb[(int64_t)i * a.n2], hb[i]));
-        a.w[(int64_t)b * a.n2 + k] = acc;
-        q = cabs2(acc);
+        for (int i = 0; i < nv; ++i) cff_mac<true>(ar, ai, Vb[(int64_t)i * a.n2], hs[i]);
+        const cff w1 = pack(ar, ai);
+        *wk = w1;
+        cff_abs2_mac(q, re_of(w1), im_of(w1));
     }
-    q = block_sum(q, sh);
-    if (threadIdx.x == 0) a.npart[(int64_t)b * a.nblk + blockIdx.x] = q;
+    const double t = block_sum_ff(q, sh);
+    if (threadIdx.x == 0) a.npart[(int64_t)b * a.nblk + blockIdx.x] = t;
     if (last_block(a.tick + a.B + b, a.nblk)) norm_final(a, b, sh, pass == 0);
 }
 
@@ -288,8 +403,8 @@ inline size_t tail_smem_per_warp(int m) { return (size_t)(3 * m + 1) * sizeof(do
 // End of an Arnoldi step, one warp per system: the new Hessenberg column (hcol, ||w||)
 // is rotated by the previous Givens rotations, a new rotation zeroes its subdiagonal,
 // g is rotated, |g_{j+1}| is the residual estimate and decides whether the system keeps
-// running.  The block then advances j and sets the loop condition: another step runs
-// while a system is running and j < m.
+// running.  The block then advances j and sets the loop condition (the graph's, or the flag
+// the host reads): another step runs while a system is running and j < m.
 __global__ void arn_tail_kernel(Arn a) {
     extern __shared__ double2 dsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -351,11 +466,15 @@ __global__ void arn_tail_kernel(Arn a) {
     if (threadIdx.x == 0) {
         pack_running(a);
         *a.jdev = j + 1;
-        cudaGraphSetConditional(a.cond, (go && j + 1 < m) ? 1u : 0u);
+        const unsigned more = (go && j + 1 < m) ? 1u : 0u;
+        if (a.go)
+            *a.go = (int)more;
+        else
+            cudaGraphSetConditional(a.cond, more);
     }
 }
 
-// R y = g by back substitution (one warp per system), y into a.y
+// R y = g by back substitution (one warp per system), y into a.y (FP64) and a.yff
 __global__ void arn_backsub_kernel(Arn a) {
     extern __shared__ double2 ysm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -371,29 +490,43 @@ __global__ void arn_backsub_kernel(Arn a) {
             if (lane == 0) ys[i] = cdiv(csub(gb[i], s), Hb[(int64_t)i * m + i]);
             __syncwarp();
         }
-        for (int i = lane; i < n; i += 32) a.y[(int64_t)b * m + i] = ys[i];
+        for (int i = lane; i < n; i += 32) {
+            a.y[(int64_t)b * m + i] = ys[i];
+            a.yff[(int64_t)b * m + i] = to_cff(ys[i]);
+        }
         __syncwarp();
     }
 }
 
-// x += M^-1 sum_{i < jb} v_i y_i
+// x += M^-1 sum_{i < jb} v_i y_i (the sum in float-float)
 __global__ void __launch_bounds__(kT) arn_update_kernel(Arn a) {
     const int b = blockIdx.y;
     const int64_t t = blockIdx.x * (int64_t)kT + threadIdx.x;
     const int n = a.jb[b];
     if (t >= a.N || n == 0) return;
-    const double2 *Vb = a.V + (int64_t)b * a.vstride, *yb = a.y + (int64_t)b * a.m;
-    double2 u0 = make_double2(0.0, 0.0), u1 = make_double2(0.0, 0.0);
+    const cff *Vb = a.V + (int64_t)b * a.vstride;
+    const cff *yb = a.yff + (int64_t)b * a.m;
+    ffloat r0(0.f, 0.f), i0(0.f, 0.f), r1(0.f, 0.f), i1(0.f, 0.f);
     for (int i = 0; i < n; ++i) {
-        const double2 yi = yb[i];
-        u0 = cadd(u0, cmul(Vb[(int64_t)i * a.n2 + t], yi));
-        u1 = cadd(u1, cmul(Vb[(int64_t)i * a.n2 + a.N + t], yi));
+        const cff yi = yb[i];
+        cff_mac<false>(r0, i0, Vb[(int64_t)i * a.n2 + t], yi);
+        cff_mac<false>(r1, i1, Vb[(int64_t)i * a.n2 + a.N + t], yi);
     }
+    const double2 u0 = make_double2((double)r0, (double)i0), u1 = make_double2((double)r1, (double)i1);
     double2 o0, o1;
-    block_jacobi(a.Vself[t], a.s[b * a.S + a.surf[t]], u0, u1, o0, o1);
+    const int q = b * a.S + a.surf[t];
+    precond(a.vinv[t], a.pq[q], a.s[q], u0, u1, o0, o1);
     double2 *xb = a.x + (int64_t)b * a.n2;
     xb[t] = cadd(xb[t], o0);
     xb[a.N + t] = cadd(xb[a.N + t], o1);
+}
+
+// preconditioner constants of a solve: vinv = 1 / V_ii, pq = 1 / (1 + s)
+__global__ void arn_precond_setup_kernel(int64_t N, int BS, const double *Vself, const double2 *s, double *vinv,
+                                         double2 *pq) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < N) vinv[t] = 1.0 / Vself[t];
+    if (t < BS) pq[t] = cdiv(make_double2(1.0, 0.0), make_double2(1.0 + s[t].x, s[t].y));
 }
 
 int small_kernel_warps(int B, int m) {
@@ -435,6 +568,7 @@ int capture_cycle(lspr_ctx *ctx, int mode, const Arn &a0, GraphCache &gc) {
     CAP_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
     Arn a = a0;
     a.cond = h;
+    a.go = nullptr;
     ctx->stream = cs;
     // head: v_0 and the cycle state
     CAP_TRY(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
@@ -500,16 +634,69 @@ int capture_cycle(lspr_ctx *ctx, int mode, const Arn &a0, GraphCache &gc) {
     return LSPR_OK;
 }
 
+// One Arnoldi cycle launched from the host, without a graph: the kernels of the recorded
+// cycle in the same order, the loop condition read back after every step.  With per-kernel
+// timing the vector kernels are timed under T_GMRES (the operator's under their own slots).
+// Launches are counted as they happen; products are counted by the caller per running
+// system, as for a recorded cycle.
+int host_cycle(lspr_ctx *ctx, int mode, const Arn &a0, int *go_d) {
+    cudaStream_t st = ctx->stream;
+    Arn a = a0;
+    a.go = go_d;
+    a.cond = 0;
+    const int64_t mv0 = ctx->matvec_count;
+    const int nw = small_kernel_warps(a.B, a.m);
+    const dim3 gv(grid_for(a.n2, kT), a.B), gN(grid_for(a.N, kT), a.B);
+    cudaEvent_t ev;
+    timer_begin(ctx, T_GMRES, &ev);
+    arn_init_kernel<<<gv, kT, 0, st>>>(a);
+    ++ctx->n_launches;
+    timer_end(ctx, T_GMRES, ev);
+    int more = 1;
+    while (more) {
+        timer_begin(ctx, T_GMRES, &ev);
+        arn_precond_kernel<<<gN, kT, 0, st>>>(a);
+        ++ctx->n_launches;
+        timer_end(ctx, T_GMRES, ev);
+        ctx->rhs_map = a.rmap;
+        ctx->rhs_inv = a.rmap + a.B;
+        ctx->rhs_nact = a.rmap + 2 * a.B + 1;
+        const int rc = apply_operator(ctx, mode, a.z, a.w, a.s, a.B);
+        ctx->rhs_map = ctx->rhs_inv = ctx->rhs_nact = nullptr;
+        LSPR_TRY_ST(rc);
+        timer_begin(ctx, T_GMRES, &ev);
+        for (int pass = 0; pass < 2; ++pass) {
+            arn_dot_kernel<<<dim3(a.nch, a.B), kT, 0, st>>>(a, pass);
+            arn_axpy_kernel<<<gv, kT, 0, st>>>(a, pass);
+            ctx->n_launches += 2;
+        }
+        arn_tail_kernel<<<1, 32 * nw, nw * tail_smem_per_warp(a.m), st>>>(a);
+        ++ctx->n_launches;
+        timer_end(ctx, T_GMRES, ev);
+        LSPR_TRY(ctx, cudaGetLastError());
+        LSPR_TRY(ctx, cudaMemcpyAsync(&more, go_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    }
+    timer_begin(ctx, T_GMRES, &ev);
+    arn_backsub_kernel<<<1, 32 * nw, nw * a.m * sizeof(double2), st>>>(a);
+    arn_update_kernel<<<gN, kT, 0, st>>>(a);
+    ctx->n_launches += 2;
+    timer_end(ctx, T_GMRES, ev);
+    LSPR_TRY(ctx, cudaGetLastError());
+    ctx->matvec_count = mv0;
+    return LSPR_OK;
+}
+
 }  // namespace
 
 int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double tol, const double2 *s_d,
                       const double2 *b_d, double2 *x_d, bool x_zero, bool trust_estimate, std::vector<int> &iters,
                       std::vector<double> &relres, const std::vector<double> &bnorm) {
-    if (!ctx->use_graphs || ctx->timing.enabled || B < 1 || m < 1) return LSPR_E_STATE;
+    if (B < 1 || m < 1 || m > kMaxRestart) return LSPR_E_ARG;
     const Mesh &me = ctx->mesh;
     const int64_t N = me.N, n2 = 2 * N;
     cudaStream_t st = ctx->stream;
-    if (!ctx->gstream) {
+    if (ctx->use_graphs && !ctx->timing.enabled && !ctx->gstream) {
         LSPR_TRY(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
         LSPR_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_g0, cudaEventDisableTiming));
         LSPR_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_g1, cudaEventDisableTiming));
@@ -539,6 +726,12 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     LSPR_TRY(ctx, ab.tick.ensure(2 * (size_t)B));
     LSPR_TRY(ctx, ab.ctl.ensure(1 + 3 * (size_t)B));
     LSPR_TRY(ctx, ab.rmap.ensure(2 * (size_t)B + 2));
+    LSPR_TRY(ctx, ab.hff.ensure((size_t)B * (m + 1)));
+    LSPR_TRY(ctx, ab.yff.ensure((size_t)B * m));
+    LSPR_TRY(ctx, ab.ninv.ensure(B));
+    LSPR_TRY(ctx, ab.vinv.ensure(N));
+    LSPR_TRY(ctx, ab.pq.ensure((size_t)B * me.S));
+    LSPR_TRY(ctx, ab.go.ensure(1));
     Arn a;
     a.B = B;
     a.m = m;
@@ -547,13 +740,14 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     a.N = N;
     a.n2 = n2;
     a.vstride = vstride;
-    a.V = ctx->gm_V.p;
+    a.V = (cff *)ctx->gm_V.p;
     a.w = ctx->gm_w.p;
     a.z = ctx->gm_z.p;
     a.x = x_d;
     a.b = b_d;
     a.s = s_d;
-    a.Vself = me.Vself.p;
+    a.vinv = ab.vinv.p;
+    a.pq = ab.pq.p;
     a.surf = me.surf.p;
     a.S = me.S;
     a.h = ab.h.p;
@@ -578,6 +772,10 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     a.jb = ab.ctl.p + 1 + B;
     a.iters = ab.ctl.p + 1 + 2 * B;
     a.rmap = ab.rmap.p;
+    a.hff = (cff *)ab.hff.p;
+    a.yff = (cff *)ab.yff.p;
+    a.ninv = (ffloat *)ab.ninv.p;
+    a.go = nullptr;
     a.cond = 0;
     // per-call parameters live in device memory, so one recorded graph serves every call
     const double par[2] = {tol, (double)std::max(1, maxiter)};
@@ -585,6 +783,9 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     LSPR_TRY(ctx, cudaMemcpyAsync(ab.par.p, par, sizeof(par), cudaMemcpyHostToDevice, st));
     LSPR_TRY(ctx, cudaMemsetAsync(ab.ctl.p, 0, sizeof(int) * (1 + 3 * (size_t)B), st));
     LSPR_TRY(ctx, cudaMemsetAsync(ab.tick.p, 0, sizeof(unsigned) * 2 * (size_t)B, st));
+    ++ctx->n_launches;
+    arn_precond_setup_kernel<<<grid_for(std::max<int64_t>(N, (int64_t)B * me.S), kT), kT, 0, st>>>(
+        N, B * me.S, me.Vself.p, s_d, ab.vinv.p, ab.pq.p);
     for (int b = 0; b < B; ++b) {
         iters[b] = 0;
         relres[b] = 1.0;
@@ -626,9 +827,10 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
                             (uint64_t)(uintptr_t)ctx->gm_V.p, (uint64_t)ctx->num_sms, (uint64_t)me.S,
                             (uint64_t)ctx->tensor_cores, (uint64_t)tr.n_tc_items, (uint64_t)tr.n_tcp_items};
         GraphCache *gc = nullptr;
+        const bool graphs = ctx->use_graphs && !ctx->timing.enabled;
         for (GraphCache &c : ctx->gcache)
-            if (c.exec && std::equal(key, key + 24, c.key)) gc = &c;
-        if (!gc) {
+            if (graphs && c.exec && std::equal(key, key + 24, c.key)) gc = &c;
+        if (graphs && !gc) {
             gc = &ctx->gcache[0];
             for (GraphCache &c : ctx->gcache)
                 if (c.use < gc->use) gc = &c;
@@ -636,25 +838,32 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
             if (skip_mv) LSPR_TRY_ST(apply_operator(ctx, mode, b_d, a.z, s_d, B));
             LSPR_TRY(ctx, cudaStreamSynchronize(st));
             if (capture_cycle(ctx, mode, a, *gc) != LSPR_OK) {
-                ctx->use_graphs = false;   // the caller falls back to host-driven cycles
-                return LSPR_E_STATE;
+                ctx->use_graphs = false;   // host-driven cycles from now on
+                gc = nullptr;
             }
-            ++ctx->graph_recordings;
-            key[0] = g_alloc_generation.load();   // buffers the recording itself sized
-            std::copy(key, key + 24, gc->key);
+            if (gc) {
+                ++ctx->graph_recordings;
+                key[0] = g_alloc_generation.load();   // buffers the recording itself sized
+                std::copy(key, key + 24, gc->key);
+            }
         }
-        gc->use = ++clock;
-        LSPR_TRY(ctx, cudaEventRecord(ctx->ev_g0, st));
-        LSPR_TRY(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_g0, 0));
-        LSPR_TRY(ctx, cudaGraphLaunch(gc->exec, ctx->gstream));
-        LSPR_TRY(ctx, cudaEventRecord(ctx->ev_g1, ctx->gstream));
-        LSPR_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_g1, 0));
+        if (gc) {
+            gc->use = ++clock;
+            LSPR_TRY(ctx, cudaEventRecord(ctx->ev_g0, st));
+            LSPR_TRY(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->ev_g0, 0));
+            LSPR_TRY(ctx, cudaGraphLaunch(gc->exec, ctx->gstream));
+            LSPR_TRY(ctx, cudaEventRecord(ctx->ev_g1, ctx->gstream));
+            LSPR_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_g1, 0));
+        }
+        if (!gc) LSPR_TRY_ST(host_cycle(ctx, mode, a, ab.go.p));
         LSPR_TRY(ctx, cudaMemcpyAsync(ctl.data(), ab.ctl.p, sizeof(int) * ctl.size(), cudaMemcpyDeviceToHost, st));
         LSPR_TRY(ctx, cudaMemcpyAsync(est.data(), a.res, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
         LSPR_TRY(ctx, cudaStreamSynchronize(st));
-        ++ctx->graph_cycles;
         const int steps = ctl[0];
-        ctx->n_launches += gc->outer + gc->per_step * steps;
+        if (gc) {
+            ++ctx->graph_cycles;
+            ctx->n_launches += gc->outer + gc->per_step * steps;
+        }
         bool all_met = true;
         for (int b = 0; b < B; ++b) {
             ctx->matvec_count += ctl[1 + 2 * B + b] - iters[b];   // products of the running systems only

@@ -121,6 +121,7 @@ struct Mesh {
     DArr<int64_t> near_ptr;               // [N+1]
     DArr<int> near_col;                   // [nnz]
     DArr<double> near_dV, near_dK;        // [nnz]
+    DArr<float2> near_f32;                // [nnz] (dV, dK) in FP32, for FP32 products
     int64_t nnz = 0;
 };
 
@@ -216,6 +217,12 @@ struct ArnoldiBufs {
     DArr<unsigned> tick;    // [2B] last-block tickets
     DArr<int> ctl;          // [1 + 3B] current column j, active[B], jb[B], iters[B]
     DArr<int> rmap;         // [2B + 2] running systems packed first: slot -> b, b -> slot, count, sets
+    DArr<float4> hff;       // [B][m+1]  h in float-float (re.hi, im.hi, re.lo, im.lo)
+    DArr<float4> yff;       // [B][m]    update coefficients in float-float
+    DArr<float2> ninv;      // [B] 1 / ||w|| in float-float
+    DArr<double> vinv;      // [N] 1 / V_ii (preconditioner)
+    DArr<double2> pq;       // [B][S] 1 / (1 + s) (preconditioner)
+    DArr<int> go;           // host-driven cycles: the loop condition
 };
 
 constexpr int kTimerSlots = 16;
@@ -256,13 +263,13 @@ struct lspr_ctx {
     lspr::DArr<ff4> w_ff;
     lspr::DArr<double2> xbuf, ybuf;    // staging for host matvec
     lspr::DArr<double2> xt;            // [2N][B] transposed right-hand sides of a product
+    lspr::DArr<float2> xtf;            // [2N][B] the same in FP32 (FP32 products)
     lspr::DArr<double2> sbuf;
     // solver scratch
-    lspr::DArr<double2> gm_V, gm_w, gm_z, gm_x, gm_b, gm_r;
-    lspr::DArr<double2> gm_H, gm_cs, gm_sn, gm_g, gm_y, gm_h, gm_part;
-    lspr::DArr<double> gm_norm, gm_bnorm, gm_dpart;
+    lspr::DArr<float4> gm_V;   // Krylov basis, float-float complex entries
+    lspr::DArr<double2> gm_w, gm_z, gm_x, gm_b, gm_r;
+    lspr::DArr<double> gm_bnorm, gm_dpart;
     lspr::DArr<double2> gm_s, gm_vinc, gm_eps;
-    lspr::DArr<int> gm_active;
     lspr::DArr<double> gm_out;         // dipole + sigma results
     lspr::DArr<double2> gm_dx;         // refinement correction
     lspr::DArr<double> gm_dippart, gm_lambda;
@@ -379,7 +386,10 @@ int launch_ff_boxes(lspr_ctx *ctx);
 int launch_item_flags(lspr_ctx *ctx, int4 *items, int64_t nitems);
 // xt: x transposed to [2N][B] (B > 1), or null
 // S > 1 surfaces: B x S channel sets, weights of set (b, t) masked to the sources of surface t
-int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt, int64_t N, int B, int S);
+// x [B][2N]; xt: its transposed FP64 copy [2N][B] or null; xtf: its transposed FP32 copy
+// (FP32 products of several right-hand sides) or null
+int launch_weights(lspr_ctx *ctx, int prec, const double2 *x, const double2 *xt, int64_t N, int B, int S,
+                   const float2 *xtf = nullptr);
 int launch_weights_fp32_raw(cudaStream_t st, int64_t Ns, int64_t N, const dbl4 *spos64, const int *src_panel,
                             const double2 *x, float4 *w);
 int launch_p2p_fp32_raw(cudaStream_t st, const int4 *items, int64_t nitems, const float4 *tgt, int64_t ntgt,
@@ -396,13 +406,15 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
                lspr_solve_stats *st);
 
 // ------------------------------------------------------------ gmres_graph.cu
+constexpr int kMaxRestart = 512;   // longest Arnoldi cycle (restart length m)
 // Restarted GMRES(m) for B systems A(s_b) x_b = b_b whose Arnoldi cycles each run as one
-// CUDA graph launch (a device-side loop over the steps).  x_zero: x holds zeros on entry
+// CUDA graph launch (a device-side loop over the steps), or host-driven launches of the
+// same kernels without graphs or with per-kernel timing.  x_zero: x holds zeros on entry
 // (the first residual is b without a matrix-vector product).  trust_estimate: return
 // after a cycle whose recurrence residual estimates meet tol, without the explicit
 // residual (for inner solves whose caller forms the residual itself).  iters/relres
 // receive the steps taken and the last relative residual (explicit or estimated) per
-// system.  Returns LSPR_E_STATE when graphs cannot be used (the caller falls back).
+// system.
 int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double tol, const double2 *s_d,
                       const double2 *b_d, double2 *x_d, bool x_zero, bool trust_estimate, std::vector<int> &iters,
                       std::vector<double> &relres, const std::vector<double> &bnorm);

@@ -380,6 +380,14 @@ __global__ void scan_kernel(const int64_t *in, int64_t n, int64_t *out) {
     if (t == blockDim.x - 1) out[n] = part[t];
 }
 
+// FP32 copies (dV, dK) of the near-field corrections, read by the FP32 products of several
+// right-hand sides
+__global__ void near_f32_kernel(int64_t nnz, const double *__restrict__ dV, const double *__restrict__ dK,
+                                float2 *__restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < nnz) out[e] = make_float2((float)dV[e], (float)dK[e]);
+}
+
 // Per near pair: dV, dK = (K_fine rule - far rule) over panel j seen from c_i,
 // and for the self entry V_ii (the far-field kernels skip a panel's own nodes).
 __global__ void near_values_kernel(int64_t nnz, const int *row, const int *col, const double *__restrict__ verts,
@@ -599,6 +607,9 @@ int mesh_build(lspr_ctx *ctx, const double *verts, int64_t nv, const int *tris, 
     near_values_kernel<<<grid_for(m.nnz, 128), 128, 0, st>>>(m.nnz, rowidx.p, m.near_col.p, m.verts.p, m.tris.p,
                                                              m.cx.p, m.cy.p, m.cz.p, m.nx.p, m.ny.p, m.nz.p, m.area.p,
                                                              m.Vself.p, m.K, m.Kf, m.near_dV.p, m.near_dK.p);
+    LSPR_TRY(ctx, m.near_f32.ensure(m.nnz));
+    ++ctx->n_launches;
+    near_f32_kernel<<<grid_for(m.nnz, 256), 256, 0, st>>>(m.nnz, m.near_dV.p, m.near_dK.p, m.near_f32.p);
     LSPR_TRY(ctx, cudaGetLastError());
     timer_end(ctx, T_MESH, ev);
     LSPR_TRY(ctx, cudaStreamSynchronize(st));

@@ -2,11 +2,9 @@
 //   assemble_kernel   near-singular / singular correction (CSR SpMV, FP64) fused with
 //                     the 2x2 block operator of Eq. matrix_lspr:
 //                       y_top = phi/2 + K phi - V dphi,  y_bot = phi/2 - K phi + s V dphi
-//   GMRES             B independent complex systems in lockstep (Sec. II.D-E:
-//                     complex GMRES), right 2x2 block-Jacobi preconditioner
-//                     [[1/2 + K_ii, -V_ii], [1/2 - K_ii, s V_ii]] with K_ii = 0,
-//                     classical Gram-Schmidt applied twice, Givens rotations,
-//                     FP64 Krylov basis whatever the matvec precision
+//   solve             right-hand side, the GMRES of gmres_graph.cu (B complex systems in
+//                     lockstep, Sec. II.D-E), iterative refinement with a float-float or
+//                     FP64 residual
 //   dipole / sigma    p = -eps_out sum_j A_j (c_j dphi2s/dn_j - phi_j n_j),
 //                     dphi2s/dn = s dphi1s/dn - ((eps_out - eps_in)/eps_out) dphi_inc/dn,
 //                     sigma = Im(k^2 e.p / (eps_out |E0|)) / Re k, k = 2 pi sqrt(eps_out)/lambda
@@ -89,7 +87,10 @@ __global__ void assemble_kernel(int64_t N, int B, const double *__restrict__ acc
 // Several right-hand sides: x [B][2N] is transposed to xt [2N][B] once per product, so
 // that the gathers of the near-field SpMV and of the source weights read the B values of
 // a panel contiguously (32 x 32 tiles through shared memory, both sides coalesced).
-__global__ void transpose_kernel(int B, int64_t n2, const double2 *__restrict__ x, double2 *__restrict__ xt) {
+__device__ __forceinline__ void put(double2 &o, double2 v) { o = v; }
+__device__ __forceinline__ void put(float2 &o, double2 v) { o = make_float2((float)v.x, (float)v.y); }
+template <class T>
+__global__ void transpose_kernel(int B, int64_t n2, const double2 *__restrict__ x, T *__restrict__ xt) {
     __shared__ double2 tile[32][33];
     const int64_t k0 = (int64_t)blockIdx.x * 32;
     const int b0 = blockIdx.y * 32;
@@ -102,7 +103,7 @@ __global__ void transpose_kernel(int B, int64_t n2, const double2 *__restrict__ 
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {   // rows k, columns b
         const int64_t k = k0 + r;
         const int b = b0 + threadIdx.x;
-        if (b < B && k < n2) xt[k * B + b] = tile[threadIdx.x][r];
+        if (b < B && k < n2) put(xt[k * B + b], tile[threadIdx.x][r]);
     }
 }
 
@@ -139,6 +140,43 @@ __global__ void assemble_rhs_kernel(int64_t N, int B, int L, const double *__res
         double2 *yb = y + (int64_t)b * 2 * N;
         yb[i] = make_double2(0.5 * ph.x + K.x - V.x, 0.5 * ph.y + K.y - V.y);
         yb[N + i] = make_double2(0.5 * ph.x - K.x + sv.x, 0.5 * ph.y - K.y + sv.y);
+    }
+}
+
+// The same for FP32 products, in FP32 arithmetic from the FP32 transposed copy and the FP32
+// near values (the far field of this mode is FP32; FP64 arithmetic would run at 1/64 of the
+// FP32 rate on this GPU and bound the kernel)
+__global__ void assemble_rhs_f32_kernel(int64_t N, int B, int L, const double *__restrict__ acc,
+                                        const int64_t *__restrict__ ptr, const int *__restrict__ col,
+                                        const float2 *__restrict__ dVK, const float2 *__restrict__ xt,
+                                        const double2 *s, double2 *y, const int *inv) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = g / L;
+    const int r = (int)(g - i * L);
+    if (i >= N) return;
+    const int64_t e0 = ptr[i], e1 = ptr[i + 1];
+    for (int b = r; b < B; b += L) {
+        const int slot = inv ? inv[b] : b;
+        if (slot < 0) continue;   // converged system: row left untouched
+        float vr = 0.f, vi = 0.f, kr = 0.f, ki = 0.f;
+        for (int64_t e = e0; e < e1; ++e) {
+            const int64_t j = col[e];
+            const float2 c = dVK[e];
+            const float2 ph = xt[j * B + b], dp = xt[(N + j) * B + b];
+            vr = fmaf(c.x, dp.x, vr);
+            vi = fmaf(c.x, dp.y, vi);
+            kr = fmaf(c.y, ph.x, kr);
+            ki = fmaf(c.y, ph.y, ki);
+        }
+        const double *ai = acc + 4 * (i * B + slot);
+        const float Vr = (float)ai[0] + vr, Vi = (float)ai[1] + vi;
+        const float Kr = (float)ai[2] + kr, Ki = (float)ai[3] + ki;
+        const float2 ph = xt[i * B + b];
+        const float sr = (float)s[b].x, si = (float)s[b].y;
+        const float svr = sr * Vr - si * Vi, svi = sr * Vi + si * Vr;
+        double2 *yb = y + (int64_t)b * 2 * N;
+        yb[i] = make_double2(0.5f * ph.x + Kr - Vr, 0.5f * ph.y + Ki - Vi);
+        yb[N + i] = make_double2(0.5f * ph.x - Kr + svr, 0.5f * ph.y - Ki + svi);
     }
 }
 
@@ -219,14 +257,20 @@ static int far_part(lspr_ctx *ctx, int mode, const double2 *x, int B) {
     LSPR_TRY(ctx, cudaMemsetAsync(ctx->acc.p, 0, sizeof(double) * 4 * N * BS, ctx->stream));
     LSPR_TRY(ctx, cudaMemsetAsync(ctx->counters.p, 0, sizeof(int) * 8, ctx->stream));
     const double2 *xt = nullptr;
-    if (B > 1) {
+    const float2 *xtf = nullptr;
+    const dim3 tg(grid_for(2 * N, 32), grid_for(B, 32)), tb(32, 8);
+    if (B > 1 && prec == PREC_F32) {
+        LSPR_TRY(ctx, ctx->xtf.ensure((size_t)B * 2 * N));
+        ++ctx->n_launches;
+        transpose_kernel<float2><<<tg, tb, 0, ctx->stream>>>(B, 2 * N, x, ctx->xtf.p);
+        xtf = ctx->xtf.p;
+    } else if (B > 1) {
         LSPR_TRY(ctx, ctx->xt.ensure((size_t)B * 2 * N));
         ++ctx->n_launches;
-        transpose_kernel<<<dim3(grid_for(2 * N, 32), grid_for(B, 32)), dim3(32, 8), 0, ctx->stream>>>(B, 2 * N, x,
-                                                                                                   ctx->xt.p);
+        transpose_kernel<double2><<<tg, tb, 0, ctx->stream>>>(B, 2 * N, x, ctx->xt.p);
         xt = ctx->xt.p;
     }
-    LSPR_TRY_ST(launch_weights(ctx, prec, x, xt, N, B, S));
+    LSPR_TRY_ST(launch_weights(ctx, prec, x, xt, N, B, S, xtf));
     if (tree && ctx->timing.enabled) {
         // kernel timing: every far-field kernel on the main stream, one after another, so that
         // the events around a launch measure that kernel alone (no overlap, no waiting)
@@ -270,9 +314,13 @@ int apply_operator(lspr_ctx *ctx, int mode, const double2 *x, double2 *y, const 
     } else {
         int L = 1;
         while (L < B && L < 32) L *= 2;
-        assemble_rhs_kernel<<<grid_for(N * L, 256), 256, 0, ctx->stream>>>(N, B, L, ctx->acc.p, m.near_ptr.p,
-                                                                          m.near_col.p, m.near_dV.p, m.near_dK.p,
-                                                                          ctx->xt.p, s, y, ctx->rhs_inv);
+        if (mode_prec(mode) == PREC_F32)
+            assemble_rhs_f32_kernel<<<grid_for(N * L, 256), 256, 0, ctx->stream>>>(
+                N, B, L, ctx->acc.p, m.near_ptr.p, m.near_col.p, m.near_f32.p, ctx->xtf.p, s, y, ctx->rhs_inv);
+        else
+            assemble_rhs_kernel<<<grid_for(N * L, 256), 256, 0, ctx->stream>>>(N, B, L, ctx->acc.p, m.near_ptr.p,
+                                                                              m.near_col.p, m.near_dV.p, m.near_dK.p,
+                                                                              ctx->xt.p, s, y, ctx->rhs_inv);
     }
     timer_end(ctx, T_NEAR, ev);
     LSPR_TRY(ctx, cudaGetLastError());
@@ -299,64 +347,6 @@ int layer_potentials(lspr_ctx *ctx, int mode, const double2 *x, double2 *Vd, dou
 constexpr int kRedThreads = 256;
 constexpr int kChunk = 1024;   // elements per partial-sum block
 
-// right preconditioner: out = M^-1 in, per panel 2x2 block with the s of the panel's surface
-// (s is [B][S])
-__global__ void precond_kernel(int B, int64_t N, const double *__restrict__ Vself, const double2 *__restrict__ s,
-                               int S, const int *__restrict__ surf, const double2 *in, int64_t in_stride, double2 *out,
-                               const int *active) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int b = blockIdx.y;
-    if (t >= N || b >= B || (active && !active[b])) return;
-    double2 o0, o1;
-    block_jacobi(Vself[t], s[b * S + surf[t]], in[b * in_stride + t], in[b * in_stride + N + t], o0, o1);
-    out[b * 2 * N + t] = o0;
-    out[b * 2 * N + N + t] = o1;
-}
-
-// part[b][i][chunk] = sum_k conj(V[b][i][k]) w[b][k]
-__global__ void dot_partial_kernel(int B, int64_t n2, int nv, const double2 *__restrict__ V, int64_t vstride_b,
-                                   const double2 *__restrict__ w, double2 *part, int nchunks, const int *active) {
-    __shared__ double2 red[kRedThreads];
-    const int chunk = blockIdx.x, i = blockIdx.y, b = blockIdx.z;
-    if (active && !active[b]) return;
-    const double2 *v = V + b * vstride_b + (int64_t)i * n2;
-    const double2 *ww = w + (int64_t)b * n2;
-    double2 s = make_double2(0, 0);
-    const int64_t beg = (int64_t)chunk * kChunk, end = min(n2, beg + kChunk);
-    for (int64_t k = beg + threadIdx.x; k < end; k += blockDim.x) s = cadd(s, cconjmul(v[k], ww[k]));
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + o]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[((int64_t)b * nv + i) * nchunks + chunk] = red[0];
-}
-
-// h[b][i] = sum of partials; hcol[b][i] = h (first pass) or += h (second pass): the
-// Hessenberg column of this Arnoldi step, contiguous for the copy to the host
-__global__ void dot_final_kernel(int B, int nv, int nchunks, const double2 *part, double2 *h, double2 *hcol, int m,
-                                 int accumulate, const int *active) {
-    const int i = threadIdx.x + blockIdx.x * blockDim.x, b = blockIdx.y;
-    if (i >= nv || (active && !active[b])) return;
-    double2 s = make_double2(0, 0);
-    for (int c = 0; c < nchunks; ++c) s = cadd(s, part[((int64_t)b * nv + i) * nchunks + c]);
-    h[b * (m + 1) + i] = s;
-    double2 &e = hcol[b * (m + 1) + i];
-    e = accumulate ? cadd(e, s) : s;
-}
-
-// w[b] -= sum_i V[b][i] h[b][i]
-__global__ void axpy_basis_kernel(int B, int64_t n2, int nv, const double2 *__restrict__ V, int64_t vstride_b,
-                                  const double2 *__restrict__ h, int m, double2 *w, const int *active) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int b = blockIdx.y;
-    if (k >= n2 || (active && !active[b])) return;
-    double2 acc = w[(int64_t)b * n2 + k];
-    for (int i = 0; i < nv; ++i) acc = csub(acc, cmul(V[b * vstride_b + (int64_t)i * n2 + k], h[b * (m + 1) + i]));
-    w[(int64_t)b * n2 + k] = acc;
-}
-
 __global__ void norm_partial_kernel(int B, int64_t n2, const double2 *__restrict__ w, int64_t wstride, double *part,
                                     int nchunks, const int *active) {
     __shared__ double red[kRedThreads];
@@ -380,38 +370,6 @@ __global__ void norm_final_kernel(int B, int nchunks, const double *part, double
     double s = 0;
     for (int c = 0; c < nchunks; ++c) s += part[(int64_t)b * nchunks + c];
     out[b] = sqrt(s);
-}
-
-// v = w / nrm (nrm > 0), optionally records H[b][j+1][j] = nrm and starts g = (nrm, 0, ...)
-__global__ void scale_kernel(int B, int64_t n2, const double2 *w, int64_t wstride, double2 *v, int64_t vstride,
-                             const double *nrm, const int *active) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int b = blockIdx.y;
-    if (k >= n2 || (active && !active[b])) return;
-    const double d = nrm[b];
-    v[b * vstride + k] = d > 0 ? cscale(w[b * wstride + k], 1.0 / d) : make_double2(0, 0);
-}
-
-constexpr int kMaxRestart = 512;
-
-// z[b] = sum_{i < jb} V[b][i] y[b][i]
-__global__ void combine_kernel(int B, int64_t n2, const double2 *__restrict__ V, int64_t vstride_b,
-                               const double2 *__restrict__ y, int m, const int *jb, double2 *z) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int b = blockIdx.y;
-    if (k >= n2) return;
-    double2 acc = make_double2(0, 0);
-    for (int i = 0; i < jb[b]; ++i) acc = cadd(acc, cmul(V[b * vstride_b + (int64_t)i * n2 + k], y[(int64_t)b * m + i]));
-    z[(int64_t)b * n2 + k] = acc;
-}
-
-// v_0 = -(A x - b) / beta
-__global__ void init_basis_kernel(int B, int64_t n2, const double2 *w, double2 *V, int64_t vstride, const double *nrm,
-                                  const int *active) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int b = blockIdx.y;
-    if (k >= n2 || (active && !active[b])) return;
-    V[b * vstride + k] = cscale(w[(int64_t)b * n2 + k], -1.0 / nrm[b]);
 }
 
 __global__ void add_kernel(int B, int64_t n2, double2 *x, const double2 *d, double sign) {
@@ -549,160 +507,6 @@ __global__ void dipole_final_kernel(int B, int nchunks, const double *part, doub
 }
 
 // ------------------------------------------------------------------ driver
-// Restarted GMRES(m) for B systems in lockstep.  The device holds the Krylov basis and
-// does every O(N) operation (preconditioner, matvec, two classical Gram-Schmidt passes,
-// norm, scaling); after each step the new Hessenberg column (m + 2 complex values per
-// system) is copied to the host, which applies the Givens rotations in FP64, tracks the
-// residual estimate |g_{j+1}| and, at the end of a cycle, solves the small triangular
-// system for the update coefficients.
-static int gmres_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double tol, const double2 *s_d,
-                       const double2 *b_d, double2 *x_d, std::vector<int> &iters, std::vector<double> &relres,
-                       const std::vector<double> &bnorm) {
-    typedef std::complex<double> cd;
-    const Mesh &me = ctx->mesh;
-    const int64_t N = me.N, n2 = 2 * N;
-    cudaStream_t st = ctx->stream;
-    const int nch = (int)((n2 + kChunk - 1) / kChunk);
-    const int64_t vstride = (int64_t)(m + 1) * n2;
-    LSPR_TRY(ctx, ctx->gm_V.ensure((size_t)B * vstride));
-    LSPR_TRY(ctx, ctx->gm_w.ensure((size_t)B * n2));
-    LSPR_TRY(ctx, ctx->gm_z.ensure((size_t)B * n2));
-    LSPR_TRY(ctx, ctx->gm_y.ensure((size_t)B * m));
-    LSPR_TRY(ctx, ctx->gm_h.ensure((size_t)2 * B * (m + 1)));   // per-pass h, then the column
-    LSPR_TRY(ctx, ctx->gm_part.ensure((size_t)B * (m + 1) * nch));
-    LSPR_TRY(ctx, ctx->gm_dpart.ensure((size_t)B * nch));
-    LSPR_TRY(ctx, ctx->gm_norm.ensure((size_t)2 * B));
-    LSPR_TRY(ctx, ctx->gm_active.ensure((size_t)2 * B));
-    double2 *V = ctx->gm_V.p, *w = ctx->gm_w.p, *z = ctx->gm_z.p;
-    double2 *hpass = ctx->gm_h.p, *hcol = ctx->gm_h.p + (size_t)B * (m + 1);
-    double *nrm = ctx->gm_norm.p;
-    int *active = ctx->gm_active.p, *jb_d = ctx->gm_active.p + B;
-    const dim3 gv(grid_for(n2, 256), B), gN(grid_for(N, 256), B);
-    std::vector<int> act(B, 1), jb(B, 0);
-    std::vector<cd> H((size_t)B * (m + 1) * m), cs((size_t)B * m), sn((size_t)B * m), g((size_t)B * (m + 1));
-    std::vector<cd> col((size_t)B * (m + 1)), y((size_t)B * m);
-    std::vector<double> hn(B);
-    for (int b = 0; b < B; ++b) { iters[b] = 0; relres[b] = 1.0; }
-    cudaEvent_t ev;
-    while (true) {
-        // explicit residual r = b - A x for the systems still running
-        LSPR_TRY_ST(apply_operator(ctx, mode, x_d, w, s_d, B));
-        timer_begin(ctx, T_GMRES, &ev);
-        ++ctx->n_launches;
-        add_kernel<<<gv, 256, 0, st>>>(B, n2, w, b_d, -1.0);                  // w = A x - b
-        ++ctx->n_launches;
-        norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, w, n2, ctx->gm_dpart.p, nch, nullptr);
-        ++ctx->n_launches;
-        norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, nrm, nullptr);
-        timer_end(ctx, T_GMRES, ev);
-        std::vector<double> beta(B);
-        LSPR_TRY(ctx, cudaMemcpyAsync(beta.data(), nrm, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
-        LSPR_TRY(ctx, cudaStreamSynchronize(st));
-        bool any = false;
-        for (int b = 0; b < B; ++b) {
-            relres[b] = beta[b] / bnorm[b];
-            act[b] = relres[b] > tol && iters[b] < maxiter && std::isfinite(relres[b]);
-            any = any || act[b];
-        }
-        if (!any) break;
-        LSPR_TRY(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-        // v0 = -(A x - b) / beta, g = (beta, 0, ...)
-        std::fill(g.begin(), g.end(), cd(0, 0));
-        for (int b = 0; b < B; ++b) g[(size_t)b * (m + 1)] = cd(beta[b], 0);
-        ++ctx->n_launches;
-        init_basis_kernel<<<gv, 256, 0, st>>>(B, n2, w, V, vstride, nrm, active);
-        for (int b = 0; b < B; ++b) jb[b] = 0;
-        for (int j = 0; j < m; ++j) {
-            // z = M^-1 v_j ; w = A z
-            timer_begin(ctx, T_GMRES, &ev);
-            ++ctx->n_launches;
-            precond_kernel<<<gN, 256, 0, st>>>(B, N, me.Vself.p, s_d, me.S, me.surf.p, V + (int64_t)j * n2, vstride, z,
-                                                active);
-            timer_end(ctx, T_GMRES, ev);
-            LSPR_TRY_ST(apply_operator(ctx, mode, z, w, s_d, B));
-            timer_begin(ctx, T_GMRES, &ev);
-            for (int pass = 0; pass < 2; ++pass) {
-                ++ctx->n_launches;
-                dot_partial_kernel<<<dim3(nch, j + 1, B), kRedThreads, 0, st>>>(B, n2, j + 1, V, vstride, w,
-                                                                                  ctx->gm_part.p, nch, active);
-                ++ctx->n_launches;
-                dot_final_kernel<<<dim3(grid_for(j + 1, 64), B), 64, 0, st>>>(B, j + 1, nch, ctx->gm_part.p, hpass,
-                                                                               hcol, m, pass, active);
-                ++ctx->n_launches;
-                axpy_basis_kernel<<<gv, 256, 0, st>>>(B, n2, j + 1, V, vstride, hpass, m, w, active);
-            }
-            ++ctx->n_launches;
-            norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, w, n2, ctx->gm_dpart.p, nch, active);
-            ++ctx->n_launches;
-            norm_final_kernel<<<grid_for(B, 64), 64, 0, st>>>(B, nch, ctx->gm_dpart.p, nrm, active);
-            ++ctx->n_launches;
-            scale_kernel<<<gv, 256, 0, st>>>(B, n2, w, n2, V + (int64_t)(j + 1) * n2, vstride, nrm, active);
-            timer_end(ctx, T_GMRES, ev);
-            LSPR_TRY(ctx, cudaGetLastError());
-            LSPR_TRY(ctx, cudaMemcpyAsync(col.data(), hcol, sizeof(double2) * B * (m + 1), cudaMemcpyDeviceToHost, st));
-            LSPR_TRY(ctx, cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
-            LSPR_TRY(ctx, cudaStreamSynchronize(st));
-            bool any_left = false;
-            for (int b = 0; b < B; ++b) {
-                if (!act[b]) continue;
-                cd *Hb = &H[(size_t)b * (m + 1) * m], *c = &cs[(size_t)b * m], *sg = &sn[(size_t)b * m];
-                cd *gb = &g[(size_t)b * (m + 1)];
-                for (int i = 0; i <= j; ++i) Hb[(size_t)i * m + j] = col[(size_t)b * (m + 1) + i];
-                Hb[(size_t)(j + 1) * m + j] = cd(hn[b], 0);
-                for (int i = 0; i < j; ++i) {   // previous rotations on column j
-                    const cd a0 = Hb[(size_t)i * m + j], d0 = Hb[(size_t)(i + 1) * m + j];
-                    Hb[(size_t)i * m + j] = c[i] * a0 + sg[i] * d0;
-                    Hb[(size_t)(i + 1) * m + j] = -std::conj(sg[i]) * a0 + c[i] * d0;
-                }
-                const cd a0 = Hb[(size_t)j * m + j], d0 = Hb[(size_t)(j + 1) * m + j];
-                const double aa = std::abs(a0), t = std::sqrt(aa * aa + std::norm(d0));
-                if (aa == 0.0) {
-                    c[j] = 0.0;
-                    sg[j] = 1.0;
-                } else {
-                    c[j] = aa / t;
-                    sg[j] = (a0 / aa) * std::conj(d0) / t;
-                }
-                Hb[(size_t)j * m + j] = c[j] * a0 + sg[j] * d0;
-                Hb[(size_t)(j + 1) * m + j] = 0.0;
-                gb[j + 1] = -std::conj(sg[j]) * gb[j];
-                gb[j] = c[j] * gb[j];
-                const double res = std::abs(gb[j + 1]);
-                jb[b] = j + 1;
-                ++iters[b];
-                if (res / bnorm[b] <= tol || iters[b] >= maxiter || !std::isfinite(res)) act[b] = 0;
-                any_left = any_left || act[b];
-            }
-            if (!any_left) break;
-            LSPR_TRY(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-        }
-        // y = R^-1 g (back substitution on the host), x += M^-1 V y
-        for (int b = 0; b < B; ++b) {
-            const cd *Hb = &H[(size_t)b * (m + 1) * m], *gb = &g[(size_t)b * (m + 1)];
-            cd *yb = &y[(size_t)b * m];
-            for (int i = jb[b] - 1; i >= 0; --i) {
-                cd acc = gb[i];
-                for (int k = i + 1; k < jb[b]; ++k) acc -= Hb[(size_t)i * m + k] * yb[k];
-                yb[i] = acc / Hb[(size_t)i * m + i];
-            }
-        }
-        LSPR_TRY(ctx, cudaMemcpyAsync(jb_d, jb.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-        LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_y.p, y.data(), sizeof(double2) * B * m, cudaMemcpyHostToDevice, st));
-        timer_begin(ctx, T_GMRES, &ev);
-        ++ctx->n_launches;
-        combine_kernel<<<gv, 256, 0, st>>>(B, n2, V, vstride, ctx->gm_y.p, m, jb_d, w);
-        ++ctx->n_launches;
-        precond_kernel<<<gN, 256, 0, st>>>(B, N, me.Vself.p, s_d, me.S, me.surf.p, w, n2, z, nullptr);
-        ++ctx->n_launches;
-        add_kernel<<<gv, 256, 0, st>>>(B, n2, x_d, z, 1.0);
-        timer_end(ctx, T_GMRES, ev);
-        LSPR_TRY(ctx, cudaGetLastError());
-        // the host vectors y, jb must outlive the copies above
-        LSPR_TRY(ctx, cudaStreamSynchronize(st));
-    }
-    return LSPR_OK;
-}
-
 int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double eps_out_im, const double *E0,
                const double *lambda_nm, int B, const lspr_solve_opts &o, double *dipole_out, double *sigma_out,
                lspr_solve_stats *stt) {
@@ -777,12 +581,8 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
     const int m = std::max(1, std::min(o.restart, kMaxRestart));
     const bool refine = o.refine && (mode == LSPR_TREE_FP32 || mode == LSPR_DIRECT_FP32);
     if (!refine) {
-        int rc = gmres_graph_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p, true,
-                                   false, iters, relres, bnorm);
-        if (rc == LSPR_E_STATE)
-            rc = gmres_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p, iters, relres,
-                             bnorm);
-        LSPR_TRY_ST(rc);
+        LSPR_TRY_ST(gmres_graph_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p,
+                                      true, false, iters, relres, bnorm));
     } else {
         // Iterative refinement: the residual r = b - A x is formed with a high-precision
         // operator of the same kind (tree or direct); the correction solves A d = r with the
@@ -844,12 +644,8 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
             LSPR_TRY(ctx, cudaMemsetAsync(dx.p, 0, sizeof(double2) * B * n2, st));
             // the caller forms the next residual itself: the inner solve may stop on its
             // recurrence estimate
-            int rc = gmres_graph_solve(ctx, mode, B, m, std::max(1, o.maxiter - used), inner, ctx->gm_s.p,
-                                       ctx->gm_r.p, dx.p, true, true, it2, rr2, rnorm);
-            if (rc == LSPR_E_STATE)
-                rc = gmres_solve(ctx, mode, B, m, std::max(1, o.maxiter - used), inner, ctx->gm_s.p, ctx->gm_r.p,
-                                 dx.p, it2, rr2, rnorm);
-            LSPR_TRY_ST(rc);
+            LSPR_TRY_ST(gmres_graph_solve(ctx, mode, B, m, std::max(1, o.maxiter - used), inner, ctx->gm_s.p,
+                                          ctx->gm_r.p, dx.p, true, true, it2, rr2, rnorm));
             ++ctx->n_launches;
             add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_x.p, dx.p, 1.0);
             int mx = 0;

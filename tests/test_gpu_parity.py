@@ -455,9 +455,10 @@ def test_graph_cycles_match_host_cycles(lspr, mode, refine, B, restart):
     assert np.max(np.abs(g.sigma_ext - h.sigma_ext) / np.abs(h.sigma_ext)) < 1e-7
     # repeat: FP32 atomics make the far field's summation order vary from run to run
     assert np.max(np.abs(g2.sigma_ext - g.sigma_ext) / np.abs(g.sigma_ext)) < 1e-7
-    if not refine:   # same arithmetic and stopping rule; across restarts the atomics' summation
-        # order may move the stopping step by a few
-        assert np.all(np.abs(g.iterations - h.iterations) <= 3)
+    if not refine:   # same kernels and stopping rule; the atomics' summation order varies from
+        # run to run (host-driven runs alone differ), and where the explicit residual at a restart
+        # lands within rounding of tol one run stops and the other takes part of another cycle
+        assert np.all(np.abs(g.iterations - h.iterations) <= restart)
 
 
 def test_graph_cycles_respect_iteration_limit(lspr):
