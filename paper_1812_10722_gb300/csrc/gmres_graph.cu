@@ -652,7 +652,12 @@ int host_cycle(lspr_ctx *ctx, int mode, const Arn &a0, int *go_d) {
     arn_init_kernel<<<gv, kT, 0, st>>>(a);
     ++ctx->n_launches;
     timer_end(ctx, T_GMRES, ev);
-    int more = 1;
+    int more = 1, sets = a.B * a.S;
+    const bool count = ctx->timing.enabled;   // channel sets of each product, for the timing counts
+    if (count) {
+        LSPR_TRY(ctx, cudaMemcpyAsync(&sets, a.rmap + 2 * a.B + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LSPR_TRY(ctx, cudaStreamSynchronize(st));
+    }
     while (more) {
         timer_begin(ctx, T_GMRES, &ev);
         arn_precond_kernel<<<gN, kT, 0, st>>>(a);
@@ -661,8 +666,10 @@ int host_cycle(lspr_ctx *ctx, int mode, const Arn &a0, int *go_d) {
         ctx->rhs_map = a.rmap;
         ctx->rhs_inv = a.rmap + a.B;
         ctx->rhs_nact = a.rmap + 2 * a.B + 1;
+        ctx->timing_sets = count ? sets : -1;
         const int rc = apply_operator(ctx, mode, a.z, a.w, a.s, a.B);
         ctx->rhs_map = ctx->rhs_inv = ctx->rhs_nact = nullptr;
+        ctx->timing_sets = -1;
         LSPR_TRY_ST(rc);
         timer_begin(ctx, T_GMRES, &ev);
         for (int pass = 0; pass < 2; ++pass) {
@@ -675,6 +682,8 @@ int host_cycle(lspr_ctx *ctx, int mode, const Arn &a0, int *go_d) {
         timer_end(ctx, T_GMRES, ev);
         LSPR_TRY(ctx, cudaGetLastError());
         LSPR_TRY(ctx, cudaMemcpyAsync(&more, go_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (count)
+            LSPR_TRY(ctx, cudaMemcpyAsync(&sets, a.rmap + 2 * a.B + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
         LSPR_TRY(ctx, cudaStreamSynchronize(st));
     }
     timer_begin(ctx, T_GMRES, &ev);

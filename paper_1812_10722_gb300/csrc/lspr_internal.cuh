@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
@@ -272,6 +273,7 @@ struct lspr_ctx {
     lspr::DArr<double2> gm_s, gm_vinc, gm_eps;
     lspr::DArr<double> gm_out;         // dipole + sigma results
     lspr::DArr<double2> gm_dx;         // refinement correction
+    lspr::DArr<int> gm_rmap;           // [2B + 2] systems of a refinement product (packing map)
     lspr::DArr<double> gm_dippart, gm_lambda;
     lspr::DArr<unsigned char> scratch[lspr::kScratchSlots];   // see lspr::Tmp
     // device-driven Arnoldi cycles (a CUDA graph per configuration, gmres_graph.cu)
@@ -297,6 +299,7 @@ struct lspr_ctx {
     // map, system -> slot map (-1: converged), and the number of channel sets in use (running
     // systems x surfaces); the far-field kernels work on the first *rhs_nact sets only
     const int *rhs_map = nullptr, *rhs_inv = nullptr, *rhs_nact = nullptr;
+    int timing_sets = -1;   // host copy of *rhs_nact for the per-launch work count of timing
     int64_t graph_cycles = 0, graph_recordings = 0;
     // last error text
     std::string last_error;
@@ -328,8 +331,10 @@ void timer_end(lspr_ctx *ctx, int slot, cudaEvent_t ev);
 void timer_begin_on(lspr_ctx *ctx, int slot, cudaEvent_t *ev, cudaStream_t st);
 void timer_end_on(lspr_ctx *ctx, int slot, cudaEvent_t ev, cudaStream_t st);
 void timer_collect(lspr_ctx *ctx);
+// channel sets a timed far-field launch works on: the packed count when the host knows it
+// (timing_sets >= 0: host-driven Arnoldi steps and refinement products), else all B
 inline void timer_rhs(lspr_ctx *ctx, int slot, int64_t B) {
-    if (ctx->timing.enabled) ctx->timing.rhs[slot] += B;
+    if (ctx->timing.enabled) ctx->timing.rhs[slot] += ctx->timing_sets >= 0 ? std::min<int64_t>(ctx->timing_sets, B) : B;
 }
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }

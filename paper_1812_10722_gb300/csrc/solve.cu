@@ -380,6 +380,16 @@ __global__ void add_kernel(int B, int64_t n2, double2 *x, const double2 *d, doub
     x[(int64_t)b * n2 + k] = make_double2(a.x + sign * c.x, a.y + sign * c.y);
 }
 
+// r_b = b_b - y_b (update = 0) or r_b -= y_b (update = 1) for the systems with inv[b] >= 0
+__global__ void resid_combine_kernel(int B, int64_t n2, double2 *r, const double2 *bv, const double2 *y,
+                                     const int *inv, int update) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (k >= n2 || inv[b] < 0) return;
+    const int64_t o = (int64_t)b * n2 + k;
+    r[o] = update ? csub(r[o], y[o]) : csub(bv[o], y[o]);
+}
+
 // ------------------------------------------------------------------ RHS
 __global__ void dphi_inc_kernel(int64_t N, const double *nx, const double *ny, const double *nz, double E0x,
                                 double E0y, double E0z, double2 *x) {
@@ -584,17 +594,20 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
         LSPR_TRY_ST(gmres_graph_solve(ctx, mode, B, m, o.maxiter, o.tol, ctx->gm_s.p, ctx->gm_b.p, ctx->gm_x.p,
                                       true, false, iters, relres, bnorm));
     } else {
-        // Iterative refinement: the residual r = b - A x is formed with a high-precision
-        // operator of the same kind (tree or direct); the correction solves A d = r with the
-        // FP32-mode GMRES to a tolerance well above the FP32 noise floor (>= 1e-4 relative
-        // to ||r||).
+        // Iterative refinement (per system b): the residual r_b = b_b - A x_b is formed with a
+        // high-precision operator of the same kind (tree or direct); the correction solves
+        // A d_b = r_b with the FP32-mode GMRES to the relative tolerance that brings r_b to
+        // 0.3 tol ||b_b|| (between 1e-4 and 0.5 of ||r_b||; systems that met tol take no steps).
         // refine == 2: native FP64 residual; otherwise float-float (about 48 significant bits
         // at a fraction of the cost of FP64 on this GPU).
-        // Once the residual is small (||r|| <= kUpdateRatio tol ||b||), the next residual is
-        // updated instead, r <- r - A d with the FP32 operator: the update differs from the
-        // high-precision residual by (A_hi - A_32) d, whose norm is at most the FP32
-        // operator's relative error (<= 1e-5 measured bound, ~5e-7 typical) times
-        // ||A d|| ~ ||r||, i.e. <= 1e-2 tol ||b||.
+        // Once a system's residual is small (||r_b|| <= kUpdateRatio tol ||b_b||), its next
+        // residual is updated instead, r_b <- r_b - A d_b with the FP32 operator: the update
+        // differs from the high-precision residual by (A_hi - A_32) d_b, whose norm is at most
+        // the FP32 operator's relative error (<= 1e-5 measured bound, ~5e-7 typical) times
+        // ||A d_b|| ~ ||r_b||, i.e. <= 1e-2 tol ||b_b||.  The products of a cycle run on the
+        // systems that need them only (packed into the first right-hand-side slots), so that
+        // the few systems near the resonance whose first correction leaves a larger residual
+        // do not make every system pay for another high-precision product.
         constexpr double kUpdateRatio = 1e3;
         const int mode_hi = o.refine == 2 ? (tree ? LSPR_TREE_FP64 : LSPR_DIRECT_FP64)
                                           : (tree ? LSPR_TREE_FF : LSPR_DIRECT_FF);
@@ -602,9 +615,13 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
         std::vector<double> rr2(B, 1.0), rn(B, 0.0);
         DArr<double2> &dx = ctx->gm_dx;
         LSPR_TRY(ctx, dx.ensure((size_t)B * n2));
+        LSPR_TRY(ctx, ctx->gm_z.ensure((size_t)B * n2));
+        LSPR_TRY(ctx, ctx->gm_rmap.ensure(2 * (size_t)B + 2));
         const int max_cycles = 12;
         int used = 0;
-        bool updated = false;   // r already holds the updated residual of the current x
+        std::vector<char> upd(B, 0);   // r_b holds the updated residual of the current x_b
+        std::vector<char> fin(B, 0);   // system b met tol
+        std::vector<int> map(2 * (size_t)B + 2);
         auto norm_of_r = [&]() -> int {
             ++ctx->n_launches;
             norm_partial_kernel<<<dim3(nch, B), kRedThreads, 0, st>>>(B, n2, ctx->gm_r.p, n2, ctx->gm_dpart.p, nch,
@@ -616,35 +633,71 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
             LSPR_TRY(ctx, cudaStreamSynchronize(st));
             return LSPR_OK;
         };
+        // r_b = b_b - A_md xin_b (update = 0) or r_b -= A_md xin_b (update = 1) for the systems
+        // with sel[b], through gm_z; the other systems' r_b are untouched
+        auto subset_residual = [&](int md, const double2 *xin, const std::vector<char> &sel, int update) -> int {
+            int n = 0;
+            for (int b = 0; b < B; ++b) {
+                if (sel[b]) {
+                    map[n] = b;
+                    map[B + b] = n++;
+                } else {
+                    map[B + b] = -1;
+                }
+            }
+            if (n == 0) return LSPR_OK;
+            for (int q = n; q < B; ++q) map[q] = 0;
+            map[2 * B] = n;
+            map[2 * B + 1] = n * S;
+            LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_rmap.p, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice,
+                                          st));
+            ctx->rhs_map = ctx->gm_rmap.p;
+            ctx->rhs_inv = ctx->gm_rmap.p + B;
+            ctx->rhs_nact = ctx->gm_rmap.p + 2 * B + 1;
+            ctx->timing_sets = n * S;
+            const int rc = apply_operator(ctx, md, xin, ctx->gm_z.p, ctx->gm_s.p, B);
+            ctx->rhs_map = ctx->rhs_inv = ctx->rhs_nact = nullptr;
+            ctx->timing_sets = -1;
+            LSPR_TRY_ST(rc);
+            ctx->matvec_count += n - B;   // products of the selected systems only
+            ++ctx->n_launches;
+            resid_combine_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_b.p,
+                                                                             ctx->gm_z.p, ctx->gm_rmap.p + B, update);
+            LSPR_TRY(ctx, cudaGetLastError());
+            LSPR_TRY(ctx, cudaStreamSynchronize(st));   // map is reused by the next call
+            return LSPR_OK;
+        };
         for (int cycle = 0;; ++cycle) {
             if (cycle == 0) {   // x = 0: r = b
                 LSPR_TRY(ctx, cudaMemcpyAsync(ctx->gm_r.p, ctx->gm_b.p, sizeof(double2) * B * n2,
                                               cudaMemcpyDeviceToDevice, st));
                 for (int b = 0; b < B; ++b) rn[b] = bnorm[b];
-            } else if (!updated) {
-                LSPR_TRY_ST(apply_operator(ctx, mode_hi, ctx->gm_x.p, ctx->gm_r.p, ctx->gm_s.p, B));
-                ++ctx->n_launches;   // r = b - A x
-                add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_b.p, -1.0);
-                ++ctx->n_launches;
-                add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_r.p, -2.0);
+            } else {
+                std::vector<char> sel(B);
+                for (int b = 0; b < B; ++b) sel[b] = !upd[b] && !fin[b];
+                LSPR_TRY_ST(subset_residual(mode_hi, ctx->gm_x.p, sel, 0));
                 LSPR_TRY_ST(norm_of_r());
             }
-            bool done = true, small = cycle > 0;
+            bool done = true;
             double worst = 0.0;
             for (int b = 0; b < B; ++b) {
                 relres[b] = rn[b] / bnorm[b];
-                done = done && (relres[b] <= o.tol);
-                small = small && (relres[b] <= kUpdateRatio * o.tol);
+                fin[b] = relres[b] <= o.tol;
+                done = done && fin[b];
                 worst = std::max(worst, relres[b]);
             }
             if (done || cycle == max_cycles || used >= o.maxiter || !std::isfinite(worst)) break;
-            const double inner = std::min(0.5, std::max(1e-4, 0.3 * o.tol / worst));
+            // per-system inner tolerance through the reference norms: GMRES stops system b when
+            // its residual estimate is <= 1 x rnorm[b] = inner_b ||r_b||
             std::vector<double> rnorm(B);
-            for (int b = 0; b < B; ++b) rnorm[b] = rn[b] > 0 ? rn[b] : 1.0;
+            for (int b = 0; b < B; ++b) {
+                const double inner = fin[b] ? 2.0 : std::min(0.5, std::max(1e-4, 0.3 * o.tol / relres[b]));
+                rnorm[b] = rn[b] > 0 ? inner * rn[b] : 1.0;
+            }
             LSPR_TRY(ctx, cudaMemsetAsync(dx.p, 0, sizeof(double2) * B * n2, st));
             // the caller forms the next residual itself: the inner solve may stop on its
             // recurrence estimate
-            LSPR_TRY_ST(gmres_graph_solve(ctx, mode, B, m, std::max(1, o.maxiter - used), inner, ctx->gm_s.p,
+            LSPR_TRY_ST(gmres_graph_solve(ctx, mode, B, m, std::max(1, o.maxiter - used), 1.0, ctx->gm_s.p,
                                           ctx->gm_r.p, dx.p, true, true, it2, rr2, rnorm));
             ++ctx->n_launches;
             add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_x.p, dx.p, 1.0);
@@ -654,14 +707,10 @@ int solve_impl(lspr_ctx *ctx, const double *eps_in, double eps_out_re, double ep
                 mx = std::max(mx, it2[b]);
             }
             used += mx;
-            updated = small;
-            if (updated) {   // r <- r - A_32 d (gm_z is free between GMRES calls)
-                LSPR_TRY(ctx, ctx->gm_z.ensure((size_t)B * n2));
-                LSPR_TRY_ST(apply_operator(ctx, mode, dx.p, ctx->gm_z.p, ctx->gm_s.p, B));
-                ++ctx->n_launches;
-                add_kernel<<<dim3(grid_for(n2, 256), B), 256, 0, st>>>(B, n2, ctx->gm_r.p, ctx->gm_z.p, -1.0);
-                LSPR_TRY_ST(norm_of_r());
-            }
+            // r_b <- r_b - A_32 d_b for the systems whose residual was small (the next cycle forms
+            // the others' high-precision residuals and every norm)
+            for (int b = 0; b < B; ++b) upd[b] = !fin[b] && relres[b] <= kUpdateRatio * o.tol;
+            LSPR_TRY_ST(subset_residual(mode, dx.p, upd, 1));
         }
         LSPR_TRY(ctx, cudaStreamSynchronize(st));
     }
