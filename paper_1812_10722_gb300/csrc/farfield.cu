@@ -189,10 +189,7 @@ int launch_p2p(lspr_ctx *ctx, int prec, const int4 *items, int64_t nitems, doubl
         else p2p_launch<double, batch_chunk<double>(2)>(ctx, items, nitems, B, acc, st, counter);
     } else if (prec == PREC_FF) {
         if (B == 1) p2p_launch<ffloat, 1>(ctx, items, nitems, B, acc, st, counter);
-        // float-float P2P: chunks of 2 right-hand sides (the accumulators of larger chunks cost more
-        // occupancy than regenerating G and dG/dn saves: 27.6 / 36.4 / 59.4 ms for chunks of 2 / 4 / 8
-        // at 16 right-hand sides, 20480 panels)
-        else p2p_launch<ffloat, 2>(ctx, items, nitems, B, acc, st, counter);
+        else LSPR_TRY_ST(p2p_ff_multi(ctx, items, nitems, B, acc, st, counter));
     } else if (B > 1 && (ctx->tensor_cores & 2) && items == ctx->tree.p2p_items.p) {
         // the tensor-core P2P for products of at least tc_p2p_min_rhs right-hand sides in use, the
         // FP32 pipe below: decided on the host when every slot is in use, else on the device from

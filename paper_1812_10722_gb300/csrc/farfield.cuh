@@ -930,5 +930,7 @@ int m2p_tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B);
 int p2p_tc_launch(lspr_ctx *ctx, double *acc, cudaStream_t st, int *counter, int B, int min_rhs);
 int m2p_orders_f64(lspr_ctx *ctx, double *acc, int *counter, int B);
 int m2p_orders_ff(lspr_ctx *ctx, double *acc, int *counter, int B);
+// float-float P2P of B >= 2 right-hand sides (farfield_ff.cu), one target per lane
+int p2p_ff_multi(lspr_ctx *ctx, const int4 *items, int64_t nitems, int B, double *acc, cudaStream_t st, int *counter);
 
 }  // namespace lspr

@@ -12,6 +12,12 @@ namespace lspr {
 
 namespace {
 
+// right-hand sides per float-float P2P work unit: 95.9 ms per 64-right-hand-side product on the
+// 81920-panel sphere's tree (theta 0.4, P 7, Ncrit 512) against 120.6 ms for chunks of 4 and
+// 281.6 ms for the two-targets-per-lane kernel with chunks of 2; chunks of 16 spill (162
+// registers at 8)
+constexpr int kFfP2PChunk = 8;
+
 // one term k of the table: indices of k - e_d and k - 2 e_d (-1: absent) and the
 // recurrence weights -(2n-1)/n and -(n-1)/n as float-float pairs
 struct FfTerm {
@@ -164,7 +170,96 @@ int m2p_ff_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     return LSPR_OK;
 }
 
+// Float-float P2P of several right-hand sides, one target per lane: a warp takes (item, half
+// of its 64-target block, chunk of NB right-hand sides), so G and dG/dn of a pair (~170 FP32
+// instructions in float-float) serve NB right-hand sides (4 ff_mac each) instead of the two of
+// the two-targets-per-lane kernel.  Sources are staged per warp in chunks of 32 and read by
+// broadcast; sums and the own-panel rule are those of p2p_kernel.
+constexpr int kFfP2PWarps = 4;
+template <int NB>
+__global__ void __launch_bounds__(kFfP2PWarps * 32)
+    p2p_ff1_kernel(const int4 *__restrict__ items, int64_t nitems, int B, const ff4 *__restrict__ tgt, int64_t ntgt,
+                   const ff4 *__restrict__ spos, const ff4 *__restrict__ snrm, const ff4 *__restrict__ sw,
+                   double *__restrict__ acc, int *counter, const int *nact) {
+    __shared__ ff4 sh[kFfP2PWarps][2][32];
+    __shared__ ff4 shw[kFfP2PWarps][32][NB];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Bact = nact ? *nact : B;
+    const int nbc = (Bact + NB - 1) / NB;
+    const int64_t units = nitems * 2 * nbc;
+    while (true) {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(counter, 1);
+        const int64_t it = __shfl_sync(0xffffffffu, v, 0);
+        if (it >= units) return;
+        const int64_t ii = it / (2 * nbc);
+        const int rem = (int)(it - ii * 2 * nbc), h = rem / nbc;
+        const int b0 = (rem - h * nbc) * NB, nb = min(NB, Bact - b0);
+        const int4 item = __ldg(items + ii);
+        const int64_t t = (int64_t)item.x * kTargetBlock + 32 * h + lane;
+        const ff4 q = t < ntgt ? tgt[t] : tgt[0];
+        const int tp = panel_of(q.w);
+        ffloat a[NB][4];
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a[k][c] = ffloat(0.f, 0.f);
+        for (int base = item.y; base < item.z; base += 32) {
+            const int s = base + lane;
+            if (s < item.z) {
+                sh[warp][0][lane] = spos[s];
+                sh[warp][1][lane] = snrm[s];
+#pragma unroll
+                for (int k = 0; k < NB; ++k) shw[warp][lane][k] = k < nb ? sw[(int64_t)s * B + b0 + k] : zero4<ff4>();
+            }
+            __syncwarp();
+            const int cnt = min(32, item.z - base);
+#pragma unroll 2
+            for (int kk = 0; kk < cnt; ++kk) {
+                const ff4 p = sh[warp][0][kk], n = sh[warp][1][kk];
+                const ffloat dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+                ffloat r = rsq(dx * dx + dy * dy + dz * dz);
+                if (item.w && panel_of(n.w) == tp) r = ffloat(0.f, 0.f);
+                const ffloat tk = (dx * n.x + dy * n.y + dz * n.z) * (r * r) * r;
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                    const ff4 w = shw[warp][kk][k];
+                    ff_mac(a[k][0], r, w.x);
+                    ff_mac(a[k][1], r, w.y);
+                    ff_mac(a[k][2], tk, w.z);
+                    ff_mac(a[k][3], tk, w.w);
+                }
+            }
+            __syncwarp();
+        }
+        if (t < ntgt) {
+#pragma unroll
+            for (int k = 0; k < NB; ++k)
+                if (k < nb)
+                    atomic_add4(acc + 4 * ((int64_t)tp * B + b0 + k), (double)a[k][0], (double)a[k][1],
+                                (double)a[k][2], (double)a[k][3]);
+        }
+    }
+}
+
+template <int NB>
+int p2p_ff1_launch(lspr_ctx *ctx, const int4 *items, int64_t nitems, int B, double *acc, cudaStream_t st,
+                   int *counter) {
+    static int occ = 0;
+    const int nbc = (B + NB - 1) / NB;
+    const unsigned grid = std::min<unsigned>(grid_for(nitems * 2 * nbc, kFfP2PWarps),
+                                             persistent_grid(ctx, p2p_ff1_kernel<NB>, kFfP2PWarps * 32, &occ));
+    p2p_ff1_kernel<NB><<<grid, kFfP2PWarps * 32, 0, st>>>(items, nitems, B, Views<ffloat>::tgt(ctx), ctx->mesh.N,
+                                                          Views<ffloat>::spos(ctx), Views<ffloat>::snrm(ctx),
+                                                          Views<ffloat>::w(ctx), acc, counter, ctx->rhs_nact);
+    return LSPR_OK;
+}
+
 }  // namespace
+
+int p2p_ff_multi(lspr_ctx *ctx, const int4 *items, int64_t nitems, int B, double *acc, cudaStream_t st, int *counter) {
+    return p2p_ff1_launch<kFfP2PChunk>(ctx, items, nitems, B, acc, st, counter);
+}
 
 int p2m_orders_ff(lspr_ctx *ctx, int B) {
     LSPR_DISPATCH_P(p2m_launch, ffloat, B, ctx, B);
