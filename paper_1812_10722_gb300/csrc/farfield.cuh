@@ -22,6 +22,19 @@ template <> struct MomAcc<ffloat> { using type = dbl4; using scalar = double; };
 static __device__ __forceinline__ void acc_add(float *g, float v) { atomicAdd(g, v); }
 static __device__ __forceinline__ void acc_add(double *g, double v) { atomicAdd(g, v); }
 static __device__ __forceinline__ void acc_add(double *g, const ffloat &v) { atomicAdd(g, (double)v); }
+// four channels added to a 16-byte-aligned float4 of moments: one vector reduction (one L2
+// request instead of four)
+static __device__ __forceinline__ void acc_add4(float *g, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(g), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+template <typename S>
+static __device__ __forceinline__ void acc_add4(S *g, S a, S b, S c, S d) {
+    acc_add(g + 0, a);
+    acc_add(g + 1, b);
+    acc_add(g + 2, c);
+    acc_add(g + 3, d);
+}
 
 static __device__ __forceinline__ int panel_of(float w) { return __float_as_int(w); }
 static __device__ __forceinline__ int panel_of(double w) { return (int)w; }
@@ -737,10 +750,7 @@ __global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, int n
             lm[t][j] = o;
             if (own && j < nb) {
                 S *g = (S *)(mom + ((int64_t)item.x * NT + t) * B + b0 + j);
-                acc_add(g + 0, acc[j][0]);
-                acc_add(g + 1, acc[j][1]);
-                acc_add(g + 2, acc[j][2]);
-                acc_add(g + 3, acc[j][3]);
+                acc_add4(g, (S)acc[j][0], (S)acc[j][1], (S)acc[j][2], (S)acc[j][3]);
             }
         }
     }
@@ -781,10 +791,7 @@ __global__ void p2m_kernel(const int4 *__restrict__ items, int64_t nitems, int n
             for (int j = 0; j < NB; ++j) {
                 if (j >= nb) break;
                 S *g = (S *)(mom + ((int64_t)A * NT + t) * B + b0 + j);
-                acc_add(g + 0, acc[j][0]);
-                acc_add(g + 1, acc[j][1]);
-                acc_add(g + 2, acc[j][2]);
-                acc_add(g + 3, acc[j][3]);
+                acc_add4(g, (S)acc[j][0], (S)acc[j][1], (S)acc[j][2], (S)acc[j][3]);
             }
         }
     }
