@@ -42,6 +42,7 @@ constexpr int kT = 256;                 // threads per block of the vector kerne
 constexpr int kPer = 8;                 // elements per thread of the inner-product kernel
 constexpr double kReorthEta = 0.70710678118654752;   // second pass when ||w_1|| < eta ||w_0||
 constexpr int kDotChunk = kT * kPer;    // elements per inner-product block
+constexpr int kGrp = 4;                 // basis vectors per butterfly reduction of the inner products
 constexpr int kMaxWarpsSmall = 16;      // warps of the per-system (rotation, back substitution) kernels
 
 // one complex entry in float-float: re = rh + rl, im = ih + il
@@ -283,7 +284,6 @@ __global__ void __launch_bounds__(kT) arn_precond_kernel(Arn a) {
 // chunks into h (FP64 and float-float) and into the Hessenberg column (hcol = h on pass 0,
 // hcol += h on pass 1).  Pass 0 converts w to float-float in place and forms ||w||.
 __global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
-    __shared__ double2 red[kT / 32][32];
     __shared__ double shn[kT / 32];
     const int b = blockIdx.y, chunk = blockIdx.x;
     if (!a.active[b] || (pass && !a.reorth[b])) return;
@@ -312,26 +312,52 @@ __global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
         const double t = block_sum_ff(w2, shn);
         if (threadIdx.x == 0) a.npart0[(int64_t)b * a.nch + chunk] = t;
     }
+    // Vectors in groups of kGrp: the lane's partial sums of a group (re and im of each, 2 kGrp
+    // float-float values) are reduced over the warp by a butterfly that halves the values a lane
+    // keeps at each of the first three exchanges, so a group costs 18 exchanges instead of 20 per
+    // vector; lane 4 q (q = 0..7) then holds value q of the group.
+    __shared__ double red[kT / 32][32][2];
     double2 *pb = a.part + (int64_t)b * (a.m + 1) * a.nch;
     for (int i0 = 0; i0 < nv; i0 += 32) {
         const int cnt = min(32, nv - i0);
-        for (int ii = 0; ii < cnt; ++ii) {
-            const cff *v = Vb + (int64_t)(i0 + ii) * a.n2;
-            ffloat sr(0.f, 0.f), si(0.f, 0.f);
+        for (int g0 = 0; g0 < cnt; g0 += kGrp) {
+            ffloat v[2 * kGrp];
 #pragma unroll
-            for (int r = 0; r < kPer; ++r) {
-                const int64_t k = base + r * kT;
-                if (k < a.n2) cff_conj_mac(sr, si, v[k], wr[r]);
+            for (int q = 0; q < 2 * kGrp; ++q) v[q] = ffloat(0.f, 0.f);
+#pragma unroll
+            for (int g = 0; g < kGrp; ++g) {
+                if (g0 + g < cnt) {
+                    const cff *vi = Vb + (int64_t)(i0 + g0 + g) * a.n2;
+#pragma unroll
+                    for (int r = 0; r < kPer; ++r) {
+                        const int64_t k = base + r * kT;
+                        if (k < a.n2) cff_conj_mac(v[2 * g], v[2 * g + 1], vi[k], wr[r]);
+                    }
+                }
             }
-            sr = ff_warp_sum(ff_norm(sr));
-            si = ff_warp_sum(ff_norm(si));
-            if (lane == 0) red[warp][ii] = make_double2((double)sr, (double)si);
+#pragma unroll
+            for (int q = 0; q < 2 * kGrp; ++q) v[q] = ff_norm(v[q]);
+#pragma unroll
+            for (int m = 16, n = 2 * kGrp; n > 1; m >>= 1, n >>= 1) {
+                const bool up = (lane & m) != 0;
+#pragma unroll
+                for (int q = 0; q < n / 2; ++q) {
+                    const ffloat send = up ? v[q] : v[q + n / 2];
+                    const ffloat keep = up ? v[q + n / 2] : v[q];
+                    v[q] = keep + shfl_xor(send, m);
+                }
+            }
+            ffloat t = v[0];
+            t = t + shfl_xor(t, 2);
+            t = t + shfl_xor(t, 1);
+            const int q = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
+            if ((lane & 3) == 0 && g0 + (q >> 1) < cnt) red[warp][g0 + (q >> 1)][q & 1] = (double)t;
         }
         __syncthreads();
         if (threadIdx.x < cnt) {
             double2 t = make_double2(0.0, 0.0);
 #pragma unroll
-            for (int q = 0; q < kT / 32; ++q) t = cadd(t, red[q][threadIdx.x]);
+            for (int q = 0; q < kT / 32; ++q) t = cadd(t, make_double2(red[q][threadIdx.x][0], red[q][threadIdx.x][1]));
             pb[(int64_t)(i0 + threadIdx.x) * a.nch + chunk] = t;
         }
         __syncthreads();
