@@ -348,6 +348,7 @@ def run_ours(args, wl, rank, world, local_rank):
     # ---- instrumented replay of the timed steps: CUDA events around every kernel on the
     # stream it runs on.  Events cannot sit inside the graph loops of the Arnoldi cycles, so
     # timing switches the solver to host-driven cycles; the kernels and inputs are the same.
+    arn0 = ctx.arnoldi_stats()
     ctx.set_timing(True)
     replay_ms = 0.0
     replay_steps = min(args.steps, 3)   # the per-kernel table needs a few steps, not all
@@ -364,6 +365,8 @@ def run_ours(args, wl, rank, world, local_rank):
     ktime = ctx.timing()
     krhs = ctx.timing_rhs()
     ctx_tc = ctx.tc_info()
+    arn1 = ctx.arnoldi_stats()
+    arn = {k: arn1[k] - arn0[k] for k in arn0}
     # ---- the far-field kernels at the full batch: inside the solves converged wavelengths are
     # packed out, so a replayed launch carries anywhere from B down to 1 right-hand sides; the
     # roofline of a kernel is taken on 3 bare products of all B (seeded random right-hand sides,
@@ -516,6 +519,19 @@ def run_ours(args, wl, rank, world, local_rank):
         kernels["p2p"]["path"] = "tcgen05 (TF32 hi/lo split, FP32 accumulation)" if p2p_tc else "FP32 pipe"
     if "m2p" in kernels:
         kernels["m2p"]["path"] = "tcgen05 (TF32 hi/lo split, FP32 accumulation)" if m2p_tc else "FP32 pipe"
+    if "gmres" in kernels and arn["system_steps"]:
+        # basis traffic of the Arnoldi vector kernels (16 bytes per complex entry of 2N): per
+        # system-step 3 vectors (v_j, z, w read) + 2 (j + 3) for the first Gram-Schmidt pass
+        # (w converted in place, the j + 1 basis vectors read twice, w written), and 2 (j + 1) + 3
+        # for a second pass; the cycles' update (once per restart) is not counted
+        vec = 16 * 2 * len(tris)
+        gb = vec * (7 * arn["system_steps"] + 2 * arn["vectors"] + 2 * arn["vectors_second_pass"]
+                    + 3 * arn["system_steps_second_pass"]) / 1e9
+        k = kernels["gmres"]
+        k["algorithmic_gb"] = round(gb, 3)
+        k["achieved_gbs"] = round(gb / (k["ms_total"] * 1e-3), 1)
+        k["hbm_frac"] = round(k["achieved_gbs"] / peaks.get("hbm_gbs", 6800.0), 4)
+        k["arnoldi_counters"] = arn
     full = {}   # per-launch times of the far-field kernels at all B right-hand sides
     for name in ("p2p", "m2p", "p2m", "near_assembly", "weights", "p2p_fp64", "m2p_fp64", "p2m_fp64"):
         ms, n = kfull.get(name, (0.0, 0))

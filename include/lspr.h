@@ -274,6 +274,14 @@ LSPR_API int lspr_get_timing(lspr_ctx *ctx, double *ms, int64_t *launches);
  * far-field slots ([0]-[2], [8]-[10], [12]-[14]; 0 elsewhere), so that the algorithmic work of
  * the timed launches can be counted exactly.  rhs: array of 16.  LSPR_E_ARG: null pointer. */
 LSPR_API int lspr_get_timing_rhs(lspr_ctx *ctx, int64_t *rhs);
+/* Work counters of the Arnoldi steps since the context was created (GMRES, Sec. II.D-E), summed
+ * over steps and running systems: out[0] = sum of (j + 1), the basis vectors one Gram-Schmidt
+ * pass reads at step j; out[1] = system-steps; out[2] = sum of (j + 1) over the system-steps
+ * that took the second pass; out[3] = those system-steps.  The basis traffic of the vector
+ * kernels follows from them (16 bytes per complex entry).  out: array of 4.  LSPR_E_ARG: null
+ * pointer.  The counters are read from the device (the call synchronises the context's
+ * stream). */
+LSPR_API int lspr_get_arnoldi_stats(lspr_ctx *ctx, int64_t *out);
 
 /* GMRES of lspr_solve runs each Arnoldi cycle as one CUDA graph launch: a graph
  * loop whose body is one Arnoldi step (preconditioner, product, two Gram-Schmidt

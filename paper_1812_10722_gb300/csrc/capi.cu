@@ -327,6 +327,18 @@ int lspr_get_timing_rhs(lspr_ctx *c, int64_t *rhs) {
     return LSPR_OK;
 }
 
+int lspr_get_arnoldi_stats(lspr_ctx *c, int64_t *out) {
+    if (!c || !out) return LSPR_E_ARG;
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (c->arn.stats.p) {
+        cudaSetDevice(c->device);
+        LSPR_TRY(c, cudaMemcpyAsync(h, c->arn.stats.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        LSPR_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    for (int k = 0; k < 4; ++k) out[k] = (int64_t)h[k];
+    return LSPR_OK;
+}
+
 int lspr_get_timing(lspr_ctx *c, double *ms, int64_t *launches) {
     if (!c) return LSPR_E_ARG;
     timer_collect(c);

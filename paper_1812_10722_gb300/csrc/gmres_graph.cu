@@ -119,6 +119,7 @@ struct Arn {
     int *rmap;   // [2B + 2]: slot -> system, system -> slot (-1: not running), running count,
                  // channel sets in use (running count x surfaces)
     int *go;     // host-driven cycles: the loop condition (nullptr inside a graph)
+    unsigned long long *stats;   // [4] sum (j+1), system-steps, the same over second passes
     cudaGraphConditionalHandle cond;
 };
 
@@ -481,6 +482,12 @@ __global__ void arn_tail_kernel(Arn a) {
             const double r = sqrt(cabs2(gb[j + 1]));
             a.res[b] = r;
             a.jb[b] = j + 1;
+            atomicAdd(a.stats + 0, (unsigned long long)(j + 1));
+            atomicAdd(a.stats + 1, 1ull);
+            if (a.reorth[b]) {
+                atomicAdd(a.stats + 2, (unsigned long long)(j + 1));
+                atomicAdd(a.stats + 3, 1ull);
+            }
             const int it = ++a.iters[b];
             act = (r / a.bn[b] > tol) && it < maxit && isfinite(r);
             a.active[b] = act;
@@ -767,6 +774,10 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     LSPR_TRY(ctx, ab.vinv.ensure(N));
     LSPR_TRY(ctx, ab.pq.ensure((size_t)B * me.S));
     LSPR_TRY(ctx, ab.go.ensure(1));
+    if (!ab.stats.p) {
+        LSPR_TRY(ctx, ab.stats.ensure(4));
+        LSPR_TRY(ctx, cudaMemsetAsync(ab.stats.p, 0, 4 * sizeof(unsigned long long), st));
+    }
     Arn a;
     a.B = B;
     a.m = m;
@@ -811,6 +822,7 @@ int gmres_graph_solve(lspr_ctx *ctx, int mode, int B, int m, int maxiter, double
     a.yff = (cff *)ab.yff.p;
     a.ninv = (ffloat *)ab.ninv.p;
     a.go = nullptr;
+    a.stats = ab.stats.p;
     a.cond = 0;
     // per-call parameters live in device memory, so one recorded graph serves every call
     const double par[2] = {tol, (double)std::max(1, maxiter)};

@@ -224,6 +224,7 @@ struct ArnoldiBufs {
     DArr<double> vinv;      // [N] 1 / V_ii (preconditioner)
     DArr<double2> pq;       // [B][S] 1 / (1 + s) (preconditioner)
     DArr<int> go;           // host-driven cycles: the loop condition
+    DArr<unsigned long long> stats;   // [4] work counters (lspr_get_arnoldi_stats)
 };
 
 constexpr int kTimerSlots = 16;

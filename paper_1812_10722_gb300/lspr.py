@@ -84,6 +84,7 @@ def lib():
                                      ctypes.POINTER(SolveStats)]
             L.lspr_get_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 7
             L.lspr_get_timing_rhs.argtypes = [_vp, _vp]
+            L.lspr_get_arnoldi_stats.argtypes = [_vp, _vp]
             L.lspr_tune_solver.argtypes = [_vp, _vp, _d, _d, _vp, _vp, _i32, ctypes.POINTER(SolveOpts), _vp, _i32,
                                            ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_d)]
             L.lspr_get_tc_info.argtypes = [_vp] + [ctypes.POINTER(_i64)] * 4
@@ -103,7 +104,8 @@ def lib():
                       "lspr_solve", "lspr_get_info", "lspr_set_timing", "lspr_get_timing", "lspr_launch_count",
                       "lspr_set_graphs", "lspr_graph_stats", "lspr_autotune", "lspr_set_tensor_cores",
                       "lspr_device_errors", "lspr_selftest_wait_timeout", "lspr_selftest_gate_waits",
-                      "lspr_set_charges", "lspr_get_tc_info", "lspr_get_timing_rhs", "lspr_tune_solver"):
+                      "lspr_set_charges", "lspr_get_tc_info", "lspr_get_timing_rhs", "lspr_tune_solver",
+                      "lspr_get_arnoldi_stats"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -383,6 +385,13 @@ class Context:
         n = np.zeros(16, np.int64)
         _check(lib().lspr_get_timing(self._h, _host_ptr(ms), _host_ptr(n)), "lspr_get_timing", self._h)
         return {k: (float(a), int(b)) for k, a, b in zip(TIMER_NAMES, ms, n)}
+
+    def arnoldi_stats(self) -> dict:
+        """Arnoldi work counters since the context was created (lspr_get_arnoldi_stats)."""
+        r = np.zeros(4, np.int64)
+        _check(lib().lspr_get_arnoldi_stats(self._h, _host_ptr(r)), "lspr_get_arnoldi_stats", self._h)
+        return {"vectors": int(r[0]), "system_steps": int(r[1]), "vectors_second_pass": int(r[2]),
+                "system_steps_second_pass": int(r[3])}
 
     def timing_rhs(self) -> dict:
         """Right-hand sides summed over the timed launches of each far-field slot."""
