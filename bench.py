@@ -698,9 +698,17 @@ def oracle_baseline(wl, n_panels: int, seconds: float = 12.0) -> dict:
     """The cpu_baseline of the GPU line: the oracle timed on all host cores and on one, on a
     bounded block of rows of its product, extrapolated to the workload's lambda-solves/s."""
     iters, src = oracle_iterations(wl, n_panels)
-    cores = os.cpu_count()
     rows = oracle_rows_for(wl, seconds)
     t_all, rows, n = oracle_block(wl, rows)
+    if wl.get("analytes"):
+        # several surfaces: the timed block is the matrix entries of the rows, which the oracle
+        # evaluates on one thread
+        v = oracle_rate(wl, t_all, rows, n, iters)
+        return {"value": v, "unit": "lambda-solves/s", "cores": 1, "kind": "oracle", "single_thread_value": v,
+                "cpu_model": cpu_model(), "extrapolated": True,
+                "sample": f"matrix entries of rows 0..{rows} of {n} on one thread ({t_all:.2f} s), scaled to the "
+                          f"whole matrix and to ({iters} + 3) products per lockstep solve; {iters} = {src}"}
+    cores = os.cpu_count()
     rows1 = max(8, rows // max(1, cores))
     t_one, rows1, _ = oracle_block(wl, rows1, nthreads=1)
     v_all = oracle_rate(wl, t_all, rows, n, iters)

@@ -39,10 +39,9 @@ namespace lspr {
 namespace {
 
 constexpr int kT = 256;                 // threads per block of the vector kernels
-constexpr int kPer = 8;                 // elements per thread of the inner-product kernel
+constexpr int kPer = 8;                 // entries per thread of an inner-product block's chunk
 constexpr double kReorthEta = 0.70710678118654752;   // second pass when ||w_1|| < eta ||w_0||
 constexpr int kDotChunk = kT * kPer;    // elements per inner-product block
-constexpr int kGrp = 4;                 // basis vectors per butterfly reduction of the inner products
 constexpr int kMaxWarpsSmall = 16;      // warps of the per-system (rotation, back substitution) kernels
 
 // one complex entry in float-float: re = rh + rl, im = ih + il
@@ -279,90 +278,75 @@ __global__ void __launch_bounds__(kT) arn_precond_kernel(Arn a) {
     a.z[(int64_t)b * a.n2 + a.N + t] = o1;
 }
 
-// One classical Gram-Schmidt pass, first half: h_i = <v_i, w> for i <= j.  Each block
-// forms the partial products of its chunk for every basis vector (float-float in the
-// threads and warps, FP64 across warps and blocks); the last block of the system sums the
-// chunks into h (FP64 and float-float) and into the Hessenberg column (hcol = h on pass 0,
-// hcol += h on pass 1).  Pass 0 converts w to float-float in place and forms ||w||.
+// One classical Gram-Schmidt pass, first half: h_i = <v_i, w> for i <= j.  A block takes a
+// chunk of kDotChunk entries of one system: its threads stage the chunk of w in shared memory
+// (pass 0 converts w to float-float in place and forms ||w||^2 of the chunk), then warp q takes
+// the basis vectors q, q + 8, ...: its lanes stride over the chunk (64 entries each, with four
+// independent float-float accumulator pairs, so many loads are in flight) and one warp reduction
+// per vector gives the chunk's partial product.  The last block of the system sums the chunks
+// into h (FP64 and float-float) and into the Hessenberg column (hcol = h on pass 0, hcol += h on
+// pass 1).
 __global__ void __launch_bounds__(kT) arn_dot_kernel(Arn a, int pass) {
+    __shared__ cff ws[kDotChunk];
+    __shared__ double2 red[kMaxRestart + 1];
     __shared__ double shn[kT / 32];
     const int b = blockIdx.y, chunk = blockIdx.x;
     if (!a.active[b] || (pass && !a.reorth[b])) return;
     const int nv = *a.jdev + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t base = (int64_t)chunk * kDotChunk + threadIdx.x;
-    cff *wb = wff(a, b);
-    const cff *Vb = a.V + (int64_t)b * a.vstride;
-    cff wr[kPer];
+    const int64_t c0 = (int64_t)chunk * kDotChunk;
+    const int len = (int)min((int64_t)kDotChunk, a.n2 - c0);
+    cff *wb = wff(a, b) + c0;
     ffloat w2(0.f, 0.f);
-#pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-        const int64_t k = base + r * kT;
-        wr[r] = {0.f, 0.f, 0.f, 0.f};
-        if (k < a.n2) {
+    for (int e = threadIdx.x; e < kDotChunk; e += kT) {
+        cff v = {0.f, 0.f, 0.f, 0.f};
+        if (e < len) {
             if (pass == 0) {
-                wr[r] = to_cff(a.w[(int64_t)b * a.n2 + k]);
-                wb[k] = wr[r];
+                v = to_cff(a.w[(int64_t)b * a.n2 + c0 + e]);
+                wb[e] = v;
             } else {
-                wr[r] = wb[k];
+                v = wb[e];
             }
         }
-        if (pass == 0) cff_abs2_mac(w2, re_of(wr[r]), im_of(wr[r]));
+        ws[e] = v;
+        if (pass == 0) cff_abs2_mac(w2, re_of(v), im_of(v));
     }
     if (pass == 0) {   // ||A z||^2 of this chunk, for the second-pass criterion
         const double t = block_sum_ff(w2, shn);
         if (threadIdx.x == 0) a.npart0[(int64_t)b * a.nch + chunk] = t;
     }
-    // Vectors in groups of kGrp: the lane's partial sums of a group (re and im of each, 2 kGrp
-    // float-float values) are reduced over the warp by a butterfly that halves the values a lane
-    // keeps at each of the first three exchanges, so a group costs 18 exchanges instead of 20 per
-    // vector; lane 4 q (q = 0..7) then holds value q of the group.
-    __shared__ double red[kT / 32][32][2];
-    double2 *pb = a.part + (int64_t)b * (a.m + 1) * a.nch;
-    for (int i0 = 0; i0 < nv; i0 += 32) {
-        const int cnt = min(32, nv - i0);
-        for (int g0 = 0; g0 < cnt; g0 += kGrp) {
-            ffloat v[2 * kGrp];
+    __syncthreads();
+    const cff *Vb = a.V + (int64_t)b * a.vstride + c0;
+    for (int i = warp; i < nv; i += kT / 32) {
+        const cff *v = Vb + (int64_t)i * a.n2;
+        ffloat sr[4], si[4];
 #pragma unroll
-            for (int q = 0; q < 2 * kGrp; ++q) v[q] = ffloat(0.f, 0.f);
+        for (int u = 0; u < 4; ++u) sr[u] = si[u] = ffloat(0.f, 0.f);
+        if (len == kDotChunk) {
+            // eight entries per lane loaded together before they are used (more bytes in flight)
+#pragma unroll 1
+            for (int e0 = lane; e0 < kDotChunk; e0 += 256) {
+                float4 vv[8];
 #pragma unroll
-            for (int g = 0; g < kGrp; ++g) {
-                if (g0 + g < cnt) {
-                    const cff *vi = Vb + (int64_t)(i0 + g0 + g) * a.n2;
+                for (int u = 0; u < 8; ++u) vv[u] = __ldg((const float4 *)(v + e0 + 32 * u));
 #pragma unroll
-                    for (int r = 0; r < kPer; ++r) {
-                        const int64_t k = base + r * kT;
-                        if (k < a.n2) cff_conj_mac(v[2 * g], v[2 * g + 1], vi[k], wr[r]);
-                    }
+                for (int u = 0; u < 8; ++u) {
+                    const cff x = {vv[u].x, vv[u].y, vv[u].z, vv[u].w};
+                    cff_conj_mac(sr[u & 3], si[u & 3], x, ws[e0 + 32 * u]);
                 }
             }
-#pragma unroll
-            for (int q = 0; q < 2 * kGrp; ++q) v[q] = ff_norm(v[q]);
-#pragma unroll
-            for (int m = 16, n = 2 * kGrp; n > 1; m >>= 1, n >>= 1) {
-                const bool up = (lane & m) != 0;
-#pragma unroll
-                for (int q = 0; q < n / 2; ++q) {
-                    const ffloat send = up ? v[q] : v[q + n / 2];
-                    const ffloat keep = up ? v[q + n / 2] : v[q];
-                    v[q] = keep + shfl_xor(send, m);
-                }
-            }
-            ffloat t = v[0];
-            t = t + shfl_xor(t, 2);
-            t = t + shfl_xor(t, 1);
-            const int q = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
-            if ((lane & 3) == 0 && g0 + (q >> 1) < cnt) red[warp][g0 + (q >> 1)][q & 1] = (double)t;
+        } else {   // the ragged last chunk
+            for (int e = lane; e < len; e += 32) cff_conj_mac(sr[0], si[0], v[e], ws[e]);
         }
-        __syncthreads();
-        if (threadIdx.x < cnt) {
-            double2 t = make_double2(0.0, 0.0);
-#pragma unroll
-            for (int q = 0; q < kT / 32; ++q) t = cadd(t, make_double2(red[q][threadIdx.x][0], red[q][threadIdx.x][1]));
-            pb[(int64_t)(i0 + threadIdx.x) * a.nch + chunk] = t;
-        }
-        __syncthreads();
+        ffloat tr = ff_norm(sr[0]) + ff_norm(sr[1]) + (ff_norm(sr[2]) + ff_norm(sr[3]));
+        ffloat ti = ff_norm(si[0]) + ff_norm(si[1]) + (ff_norm(si[2]) + ff_norm(si[3]));
+        tr = ff_warp_sum(tr);
+        ti = ff_warp_sum(ti);
+        if (lane == 0) red[i] = make_double2((double)tr, (double)ti);
     }
+    __syncthreads();
+    double2 *pb = a.part + (int64_t)b * (a.m + 1) * a.nch;
+    for (int i = threadIdx.x; i < nv; i += kT) pb[(int64_t)i * a.nch + chunk] = red[i];
     if (!last_block(a.tick + b, a.nch)) return;
     if (pass == 0) {
         double t = 0.0;
