@@ -20,13 +20,14 @@
 // (the epilogue adds both halves).
 //
 // Roles (persistent, one CTA per SM, both accumulators in the SM's 512 tensor-memory columns):
-//   warp 8 (one lane) fetches work units into a small ring and bulk-copies every stage's inputs
+//   warp 16 (one lane) fetches work units into a small ring and bulk-copies every stage's inputs
 //     (the positions, normals and weights of its eight sources) into the stage;
-//   warps 0-7 (one thread per target of the group) generate G and dG/dn of every stage in
-//     registers from those inputs, split them and write the B operands; warps 0-3 also write
-//     the split weights (the A operands); after the first stage of the next unit they drain the
-//     finished unit's accumulators (tcgen05.ld) into the FP64 accumulators;
-//   warp 9 (one lane) issues the MMAs of each stage once it is written, commits to the stage's
+//   warps 0-15 (two threads per target of the group, four of the stage's eight sources each)
+//     generate G and dG/dn of every stage in registers from those inputs, split them and write
+//     the B operands; warps 8-11 also write the split weights (the A operands); after the first
+//     stage of the next unit they drain the finished unit's accumulators (tcgen05.ld) into the
+//     FP64 accumulators;
+//   warp 17 (one lane) issues the MMAs of each stage once it is written, commits to the stage's
 //     "empty" barrier and, at the end of a unit, to the accumulator barrier.
 // Every wait is bounded (about a second): one that runs out raises an abort flag that the
 // other roles see, the block drains its bulk copies and MMAs in flight, frees its tensor memory
@@ -47,7 +48,9 @@ constexpr int kSrc = 8;                        // sources per stage (the MMA's K
 constexpr int kRC = 64;                        // right-hand sides per work unit
 constexpr int kTcN = kTcGroup * kTargetBlock;  // targets per work unit (the MMA's N)
 constexpr int kSBO = (kSrc / 4) * 128;         // bytes per 8-row group of a stage operand
-constexpr int kGenWarps = kTcN / 32;           // one thread per target
+constexpr int kGenSplit = 2;                   // generating threads per target (4 of the 8 sources each)
+constexpr int kGenThreads = kGenSplit * kTcN;
+constexpr int kGenWarps = kGenThreads / 32;
 constexpr int kProdWarp = kGenWarps, kMmaWarp = kGenWarps + 1;
 constexpr int kTcThreads = 32 * (kGenWarps + 2);
 constexpr int kUnitRing = 4;
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t sbase = smem_addr(tc_smem);
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
-            bar_init(smem_addr(&full_s[s]), kTcN);   // one arrival per generating thread
+            bar_init(smem_addr(&full_s[s]), kGenThreads);   // one arrival per generating thread
             bar_init(smem_addr(&empty_s[s]), 1);     // the MMAs' commit
             bar_init(smem_addr(&raw_s[s]), 1);       // the producer's expect_tx (+ the copies' bytes)
         }
@@ -247,20 +250,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             drain_wait(smem_addr(&drain), 0u);
         }
     } else {
-        // ---- generators: thread tid owns target tid of the group (row tid of the kernel
-        // operands); threads 0..127 also stage the weights of one right-hand side for four
-        // sources of each stage
-        const int blk = tid / kTargetBlock;
+        // ---- generators: thread tid owns target tt = tid mod 256 of the group (row tt of the
+        // kernel operands) for the four sources 4 hf .. 4 hf + 3 of each stage, hf = tid / 256;
+        // threads 256..383 also stage the weights of one right-hand side for four sources
+        const int tt = tid & (kTcN - 1), hf = tid / kTcN, wt = tid - kTcN;
+        const int blk = tt / kTargetBlock;
         int64_t seq = 0;
         int nu = 0;
         bool pend = false;
         int p_nb = 0, p_b0 = 0;
         bool p_stacked = false;
         int64_t p_tbase = 0;
-        // epilogue: warp w reads tensor-memory lanes 32 (w % 4).. (channel rows) and the 128
-        // targets from column 128 (w / 4) of both accumulators; false: a wait ran out
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4).. (channel rows) and the 64
+        // targets from column 64 (w / 4) of both accumulators; false: a wait ran out
         auto drain_acc = [&]() -> bool {
-            const int qd = warp & 3, half = warp >> 2;
+            const int qd = warp & 3, part = warp >> 2;
             if (!warp_wait(smem_addr(&acc_full), (uint32_t)((nu - 1) & 1), &abort_s)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int m = 32 * qd + lane;
@@ -271,8 +275,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const bool row_on = j < p_nb;
             if (__any_sync(0xffffffffu, row_on)) {
 #pragma unroll 1
-                for (int c0 = 0; c0 < kTcN / 2; c0 += 32) {
-                    const int64_t tc = p_tbase + half * (kTcN / 2) + c0 + lane;   // this lane's column's target
+                for (int c0 = 0; c0 < kTcN / 4; c0 += 32) {
+                    const int64_t tc = p_tbase + part * (kTcN / 4) + c0 + lane;   // this lane's column's target
                     const int pc = tc < ntgt ? panel_of(tgt[tc].w) : -1;
 #pragma unroll 1
                     for (int op = 0; op < 2; ++op) {   // D_V, then D_K
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         for (int h16 = 0; h16 < 32; h16 += 16) {
                             uint32_t v[16];
                             const uint32_t addr = tmem + ((uint32_t)(32 * qd) << 16) +
-                                                  (uint32_t)(op * kTcN + half * (kTcN / 2) + c0 + h16);
+                                                  (uint32_t)(op * kTcN + part * (kTcN / 4) + c0 + h16);
                             asm volatile(
                                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
                                 "%14,%15}, [%16];"
@@ -320,15 +324,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const bool stacked = nb <= kRC / 2;
             const int4 item = __ldg(items + ii);
             const int64_t tbase = (int64_t)item.x * kTcN;   // first target of the group
-            const int64_t ti = tbase + tid;
+            const int64_t ti = tbase + tt;
             const bool live = ti < ntgt;
             const float4 q = live ? tgt[ti] : tgt[0];
             const int tp = live ? panel_of(q.w) : -1;
             // weight staging (rows of the weight operands as documented at drain_acc): right-hand
             // side wj at the sources of columns wk..wk+3; stacked units need threads 0..63 only
-            const bool wr = tid < 128 && (!stacked || tid < 64);
-            const int wj = stacked ? (tid & 31) : (tid & 31) + 32 * (tid >> 6);
-            const int wk = stacked ? 4 * (tid >> 5) : 4 * ((tid >> 5) & 1);
+            const bool wr = wt >= 0 && wt < 128 && (!stacked || wt < 64);
+            const int wj = stacked ? (wt & 31) : (wt & 31) + 32 * (wt >> 6);
+            const int wk = stacked ? 4 * (wt >> 5) : 4 * ((wt >> 5) & 1);
             for (int iv = item.y; iv < item.z && ok; ++iv) {
                 const int4 e = __ldg(ivl + iv);
                 const bool on = live && ((e.z >> blk) & 1);   // uniform over the warp but for the tail
@@ -344,19 +348,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const float4 *rpos = (const float4 *)(stg + kOffRaw + kRawPos);
                     const float4 *rnrm = (const float4 *)(stg + kOffRaw + kRawNrm);
                     const float4 *rw = (const float4 *)(stg + kOffRaw + kRawW);
-                    // the kernel operand row of this target: G and dG/dn of the stage's sources
-                    float g[kSrc], h[kSrc];
+                    // this thread's part of the kernel operand row of its target: G and dG/dn of
+                    // the stage's sources 4 hf .. 4 hf + 3
+                    constexpr int kPart = kSrc / kGenSplit;
+                    float g[kPart], h[kPart];
 #pragma unroll
-                    for (int k = 0; k < kSrc; ++k) {
-                        g[k] = 0.f;
-                        h[k] = 0.f;
+                    for (int kk = 0; kk < kPart; ++kk) {
+                        const int k = kPart * hf + kk;
+                        g[kk] = 0.f;
+                        h[kk] = 0.f;
                         if (on && sb + k < e.y) {
                             const float4 p = rpos[k], n = rnrm[k];
                             const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
                             float r = rsq(dx * dx + dy * dy + dz * dz);
                             r = panel_of(n.w) == tp ? 0.f : r;
-                            g[k] = r;
-                            h[k] = (dx * n.x + dy * n.y + dz * n.z) * (r * r) * r;
+                            g[kk] = r;
+                            h[kk] = (dx * n.x + dy * n.y + dz * n.z) * (r * r) * r;
                         }
                     }
                     // the weights of right-hand side wj at the four sources from column wk
@@ -397,15 +404,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         }
                     }
                     unsigned char *bg = stg + kOffG, *bd = stg + kOffD;
-#pragma unroll
-                    for (int k4 = 0; k4 < kSrc / 4; ++k4) {
-                        const float4 gv = make_float4(g[4 * k4], g[4 * k4 + 1], g[4 * k4 + 2], g[4 * k4 + 3]);
-                        const float4 hv = make_float4(h[4 * k4], h[4 * k4 + 1], h[4 * k4 + 2], h[4 * k4 + 3]);
+                    static_assert(kPart == 4, "a thread writes one 4-column slice of its row");
+                    {
+                        const float4 gv = make_float4(g[0], g[1], g[2], g[3]);
+                        const float4 hv = make_float4(h[0], h[1], h[2], h[3]);
                         const TfPair sg = tf32_split(gv), sh = tf32_split(hv);
-                        *(float4 *)(bg + core_off(tid, 4 * k4)) = sg.hi;
-                        *(float4 *)(bg + kBPart + core_off(tid, 4 * k4)) = sg.lo;
-                        *(float4 *)(bd + core_off(tid, 4 * k4)) = sh.hi;
-                        *(float4 *)(bd + kBPart + core_off(tid, 4 * k4)) = sh.lo;
+                        *(float4 *)(bg + core_off(tt, kPart * hf)) = sg.hi;
+                        *(float4 *)(bg + kBPart + core_off(tt, kPart * hf)) = sg.lo;
+                        *(float4 *)(bd + core_off(tt, kPart * hf)) = sh.hi;
+                        *(float4 *)(bd + kBPart + core_off(tt, kPart * hf)) = sh.lo;
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_arrive(smem_addr(&full_s[s]));
