@@ -114,8 +114,7 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates, TF32 over BF16
 # profiles/ (dram__bytes_read.sum + dram__bytes_write.sum of one launch), keyed by workload, kernel and
 # treecode parameters (theta, P, Ncrit); None where no capture of the current kernel matches
 NCU_TRAFFIC = {("sphere20480", "m2p", 0.4, 5, 256): 2.410e6,          # m2p_fp32_sphere20480.md
-               ("sphere20480", "p2p", 0.4, 5, 256): 5.045e6,          # p2p1_fp32_sphere20480.md
-               ("sphere81920_sweep64", "m2p", 0.4, 7, 512): 7.869e9}  # m2p_tc_sphere81920_sweep64.md
+               ("sphere20480", "p2p", 0.4, 5, 256): 5.045e6}          # p2p1_fp32_sphere20480.md
 
 
 def m2p_flops(P: int, B: int = 1) -> int:
@@ -179,17 +178,19 @@ def p2p_flops(B: int = 1) -> int:
 
 def m2p_tc_bound(P: int, B: int, group_box_pairs: int, peaks: dict, mhz: float) -> dict:
     """Time bound of one tensor-core M2P launch: the largest of its coefficient generation on the
-    FP32 pipe (the recurrence for 256 targets per (group, box) and unit of 16 or 32 right-hand
+    FP32 pipe (the recurrence for 256 targets per (group, box) and unit of 16, 32 or 64 right-hand
     sides), its reciprocal square roots on the SFU, and its issued MMAs on the tensor pipe
-    (M = 128 channels x N = 256 targets x K = 8 per step; 3 MMAs per step for units of 32
-    right-hand sides, 2 for units of 16)."""
+    (M = 128 channels x N = 256 targets x K = 8 per step; 3 MMAs per step for each A part of 32
+    right-hand sides, 2 for units of 16; above 32 right-hand sides a unit carries two A parts
+    against one set of coefficients)."""
     nt = (P + 1) * (P + 2) * (P + 3) // 6
-    rc = 16 if B <= 16 else 32
-    units = (B + rc - 1) // rc
+    rc = 16 if B <= 16 else (32 if B <= 32 else 64)
+    units = (B + rc - 1) // rc                      # coefficient generations per (group, box)
+    parts = (B + min(rc, 32) - 1) // min(rc, 32)    # A parts of 32 (or 16) right-hand sides
     ksteps = sum((min(16, nt - kc) + 7) // 8 for kc in range(0, nt, 16))
     gen = group_box_pairs * units * 256 * (m2p_flops(P, 0))
     mufu = group_box_pairs * units * 256
-    mma = group_box_pairs * units * (3 if rc == 32 else 2) * 2 * 128 * 256 * 8 * ksteps
+    mma = group_box_pairs * parts * (2 if rc == 16 else 3) * 2 * 128 * 256 * 8 * ksteps
     fp32_peak = fp32_peak_tflops(mhz) * 1e12
     sfu_peak = SFU_PER_CLK_SM * 152 * mhz * 1e6
     tf32_peak = peaks.get("bf16_tflops_sustained", 1741.2) * TF32_PER_BF16 * 1e12

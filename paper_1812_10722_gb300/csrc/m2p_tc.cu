@@ -59,19 +59,27 @@ static_assert(kTmemCols <= 512 && kTcN <= 256, "one MMA spans the group");
 // so two MMAs, [A_hi; A_lo] B_hi and [A_hi; A_lo] B_lo, give A_hi B in accumulator rows 0..63
 // and A_lo B in rows 64..127 (all four products); the epilogue adds both halves.  Row m of
 // an M = 128 accumulator sits in TMEM lane m.
+// RC = 64: two halves of 32 right-hand sides share each stage's coefficients (B): the stage
+// holds both halves' A parts, each half takes the three MMAs of RC = 32 into its own accumulator
+// (both 256-column accumulators belong to the unit), so the recurrence, the split coefficients
+// and the stage hand-overs of a (group, box) serve 64 right-hand sides.
 template <int P, int RC>
 struct TcShape {
     static constexpr int NT = n_terms(P);
     static constexpr int NKC = (NT + kKC - 1) / kKC;
-    static constexpr int ROWS = 4 * RC;
+    static constexpr int HALVES = RC == 64 ? 2 : 1;       // A parts (accumulators) per unit
+    static constexpr int HRC = RC / HALVES;               // right-hand sides per A part
+    static constexpr int ROWS = 4 * HRC;
     static constexpr bool STACKED = ROWS == 64;           // hi and lo halves of one operand
     static constexpr uint32_t IDESC = idesc_tf32(128, kTcN);
-    static constexpr int A_CH = (ROWS / 8) * kChunkSBO;   // one split part of A per stage
+    static constexpr int A_CH = (ROWS / 8) * kChunkSBO;   // one split part of one A per stage
     static constexpr int B_CH = (kTcN / 8) * kChunkSBO;   // one split part of B per stage
-    static constexpr int STAGE = 2 * A_CH + 2 * B_CH;     // A_hi | A_lo | B_hi | B_lo
+    static constexpr int OFF_B = HALVES * 2 * A_CH;       // [A_hi | A_lo] per half, then B_hi | B_lo
+    static constexpr int STAGE = OFF_B + 2 * B_CH;
     static constexpr int NS = (200 * 1024) / STAGE;
     static constexpr int SMEM = NS * STAGE;
-    static_assert(ROWS == 64 || ROWS == 128, "unit of 16 or 32 right-hand sides");
+    static_assert(ROWS == 64 || ROWS == 128, "A parts of 16 or 32 right-hand sides");
+    static_assert(HALVES == 1 || ROWS == 128, "pairs of 32-right-hand-side halves");
     static_assert(NS >= 2, "at least two stages");
 };
 
@@ -188,8 +196,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int4 item = __ldg(items + ii);
                 bool ok = true;
                 int b_nx = item.y < item.z ? __ldg(&list[item.y].x) : 0;   // one box ahead
+                // A parts present: the halves of the unit holding right-hand sides in use
+                const int nh = min(S::HALVES, (Bact - rc * RC + S::HRC - 1) / S::HRC);
                 for (int l = item.y; l < item.z && ok; ++l) {
-                    const unsigned char *src = img + ((int64_t)b_nx * nrc + rc) * NKC * (2 * S::A_CH);
+                    const unsigned char *src = img + ((int64_t)b_nx * nrc + rc * S::HALVES) * NKC * (2 * S::A_CH);
                     if (l + 1 < item.z) b_nx = __ldg(&list[l + 1].x);
                     for (int kc = 0; kc < NKC; ++kc, ++seq) {
                         const int s = (int)(seq % NS);
@@ -200,13 +210,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         }
                         const uint32_t fb = smem_addr(&full_a[s]);
                         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                                     "r"(2 * S::A_CH)
+                                     "r"((uint32_t)(nh * 2 * S::A_CH))
                                      : "memory");
-                        asm volatile(
-                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                                sbase + (uint32_t)(s * S::STAGE)),
-                            "l"(src + (int64_t)kc * 2 * S::A_CH), "r"(2 * S::A_CH), "r"(fb)
-                            : "memory");
+                        for (int h = 0; h < nh; ++h)
+                            asm volatile(
+                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                    sbase + (uint32_t)(s * S::STAGE + h * 2 * S::A_CH)),
+                                "l"(src + ((int64_t)h * NKC + kc) * 2 * S::A_CH), "r"(2 * S::A_CH), "r"(fb)
+                                : "memory");
                     }
                 }
                 if (!ok) break;
@@ -219,7 +230,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // ---- MMA issue: one lane
         if (lane == 0) {
             int64_t seq = 0;
-            int nu = 0;   // non-empty units so far (accumulator = nu & 1)
+            int nu = 0;   // non-empty units so far (accumulator = nu & 1; pairs: both, every unit)
             for (int uc = 0;; ++uc) {
                 const int slot = uc % kUnitRing;
                 if (!bar_wait(smem_addr(&ring_full[slot]), (uint32_t)(uc / kUnitRing) & 1u, &abort_s)) break;
@@ -227,11 +238,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (u >= units) break;
                 const int4 item = __ldg(items + u / nbc);
                 if (item.y < item.z) {
-                    const int ab = nu & 1;
-                    if (nu >= 2 && !bar_wait(smem_addr(&acc_empty[ab]), (uint32_t)((nu >> 1) - 1) & 1u, &abort_s))
-                        break;
+                    const int ab = S::HALVES == 2 ? 0 : (nu & 1);
+                    const bool wait = S::HALVES == 2 ? nu >= 1 : nu >= 2;
+                    const uint32_t wpar = (uint32_t)(S::HALVES == 2 ? (nu - 1) : ((nu >> 1) - 1)) & 1u;
+                    if (wait && !bar_wait(smem_addr(&acc_empty[ab]), wpar, &abort_s)) break;
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     const uint32_t d = tmem + (uint32_t)(ab * kTcN);
+                    const int rc = (int)(u % nbc);
+                    const int nh = min(S::HALVES, (Bact - rc * RC + S::HRC - 1) / S::HRC);
                     bool ok = true;
                     for (int l = item.y; l < item.z && ok; ++l) {
                         for (int kc = 0; kc < NKC; ++kc, ++seq) {
@@ -247,14 +261,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             const int ksteps = (min(kKC, NT - kc * kKC) + 7) / 8;
                             for (int ks = 0; ks < ksteps; ++ks) {
                                 const uint32_t off = ks * 256;   // two 16-byte column groups per K step of 8
-                                const uint64_t dah = umma_desc(st + off, 128, kChunkSBO);
-                                const uint64_t dal = umma_desc(st + S::A_CH + off, 128, kChunkSBO);
-                                const uint64_t dbh = umma_desc(st + 2 * S::A_CH + off, 128, kChunkSBO);
-                                const uint64_t dbl = umma_desc(st + 2 * S::A_CH + S::B_CH + off, 128, kChunkSBO);
+                                const uint64_t dbh = umma_desc(st + S::OFF_B + off, 128, kChunkSBO);
+                                const uint64_t dbl = umma_desc(st + S::OFF_B + S::B_CH + off, 128, kChunkSBO);
                                 const uint32_t on = (l == item.y && kc == 0 && ks == 0) ? 0u : 1u;
-                                tc_mma(d, dah, dbh, S::IDESC, on);
-                                tc_mma(d, dah, dbl, S::IDESC, 1u);
-                                if (!S::STACKED) tc_mma(d, dal, dbh, S::IDESC, 1u);
+                                for (int h = 0; h < nh; ++h) {   // half h into accumulator d + h kTcN
+                                    const uint32_t ah = st + (uint32_t)(h * 2 * S::A_CH);
+                                    const uint64_t dah = umma_desc(ah + off, 128, kChunkSBO);
+                                    const uint64_t dal = umma_desc(ah + S::A_CH + off, 128, kChunkSBO);
+                                    const uint32_t dh = d + (uint32_t)(h * kTcN);
+                                    tc_mma(dh, dah, dbh, S::IDESC, on);
+                                    tc_mma(dh, dah, dbl, S::IDESC, 1u);
+                                    if (!S::STACKED) tc_mma(dh, dal, dbh, S::IDESC, 1u);
+                                }
                             }
                             tc_commit(smem_addr(&empty_s[s]));
                         }
@@ -286,8 +304,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int qd = warp & 3, half = warp >> 2;
             if (!warp_wait(smem_addr(&acc_full[p_ab]), (uint32_t)p_par, &abort_s)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            if ((32 * qd) % S::ROWS < 4 * p_nb) {
+#pragma unroll 1
+            for (int hh = 0; hh < S::HALVES; ++hh) {   // the unit's A parts (accumulators)
+            const int hnb = p_nb - hh * S::HRC;          // right-hand sides of this half
+            if ((32 * qd) % S::ROWS < 4 * hnb) {
                 const int m = (32 * qd + lane) % S::ROWS, j = m >> 2, cpt = m & 3;
+                const int jb = p_b0 + hh * S::HRC + j;   // the right-hand side of row m
 #pragma unroll 1
                 for (int c0 = 0; c0 < kTcN / 2; c0 += 32) {
                     const int64_t tc = p_tbase + half * (kTcN / 2) + c0 + lane;   // this lane's column's target
@@ -296,7 +318,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int h16 = 0; h16 < 32; h16 += 16) {
                         uint32_t v[16];
                         const uint32_t addr = tmem + ((uint32_t)(32 * qd) << 16) +
-                                              (uint32_t)(p_ab * kTcN + half * (kTcN / 2) + c0 + h16);
+                                              (uint32_t)((p_ab + hh) * kTcN + half * (kTcN / 2) + c0 + h16);
                         asm volatile(
                             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
                             "%14,%15}, [%16];"
@@ -308,11 +330,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                         for (int x = 0; x < 16; ++x) {
                             const int p = __shfl_sync(0xffffffffu, pc, h16 + x);
-                            if (j < p_nb && p >= 0)
-                                atomicAdd(acc + 4 * ((int64_t)p * B + p_b0 + j) + cpt, (double)__uint_as_float(v[x]));
+                            if (j < hnb && p >= 0)
+                                atomicAdd(acc + 4 * ((int64_t)p * B + jb) + cpt, (double)__uint_as_float(v[x]));
                         }
                     }
                 }
+            }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
@@ -333,6 +356,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int b0 = (int)(u - ii * nbc) * RC, nb = min(RC, Bact - b0);
             const int4 item = __ldg(items + ii);
             const int64_t tbase = (int64_t)item.x * kTcN;   // first target of the group
+            int ustage = 0;   // stages of this unit written so far
             const int64_t ti = tbase + tid;
             const bool live = ti < ntgt;
             const float4 q = live ? tgt[ti] : tgt[0];
@@ -371,12 +395,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
 #pragma unroll
                 for (int kc = 0; kc < NKC; ++kc) {
+                    // pairs hold both accumulators per unit: the previous unit is drained before
+                    // this unit's stage NS, whose slot the MMAs of its first stage must free
+                    if (S::HALVES == 2 && pend && ustage >= NS && !(ok = drain_acc())) break;
+                    ++ustage;
                     const int s = (int)(seq % NS);
                     if (seq >= NS && !warp_wait(smem_addr(&empty_s[s]), (uint32_t)((seq / NS) - 1) & 1u, &abort_s)) {
                         ok = false;
                         break;
                     }
-                    unsigned char *bh = tc_smem + s * S::STAGE + 2 * S::A_CH, *bl = bh + S::B_CH;
+                    unsigned char *bh = tc_smem + s * S::STAGE + S::OFF_B, *bl = bh + S::B_CH;
                     // four terms per 16-byte store: the eight lanes of a quarter warp fill one
                     // core matrix, free of bank conflicts
 #pragma unroll
@@ -401,8 +429,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (!ok) break;
             if (item.y < item.z) {
                 pend = true;
-                p_ab = nu & 1;
-                p_par = (nu >> 1) & 1;
+                p_ab = S::HALVES == 2 ? 0 : (nu & 1);
+                p_par = (S::HALVES == 2 ? nu : (nu >> 1)) & 1;
                 p_tbase = tbase;
                 p_b0 = b0;
                 p_nb = nb;
@@ -426,7 +454,8 @@ int tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
     if (tr.n_tc_items == 0) return LSPR_OK;
-    const int nrc = (B + RC - 1) / RC;
+    const int nrc = (B + S::HRC - 1) / S::HRC;   // A parts of 16 or 32 right-hand sides in the image
+    const int nunit = (B + RC - 1) / RC;          // work units per group item
     const int64_t segs = tr.nboxes * nrc * S::NKC * (S::A_CH / 16);
     LSPR_TRY(ctx, ctx->tc_img.ensure((size_t)segs * 32));
     if (!ctx->dev_err.p) return LSPR_E_STATE;
@@ -434,10 +463,10 @@ int tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     ++ctx->n_launches;   // the image; the caller counts the M2P launch
     const unsigned gi =
         (unsigned)std::max<int64_t>(1, std::min<int64_t>((segs + 255) / 256, 8 * std::max(1, ctx->num_sms)));
-    tc_image_kernel<P, RC><<<gi, 256, 0, ctx->stream>>>(tr.nboxes, B, nrc, Views<float>::mom(ctx), ctx->tc_img.p,
-                                                         ctx->rhs_nact);
+    tc_image_kernel<P, S::HRC><<<gi, 256, 0, ctx->stream>>>(tr.nboxes, B, nrc, Views<float>::mom(ctx),
+                                                              ctx->tc_img.p, ctx->rhs_nact);
     const unsigned grid =
-        (unsigned)std::max<int64_t>(1, std::min<int64_t>(tr.n_tc_items * nrc, std::max(1, ctx->num_sms)));
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(tr.n_tc_items * nunit, std::max(1, ctx->num_sms)));
     m2p_tc_kernel<P, RC><<<grid, kTcThreads, S::SMEM, ctx->stream>>>(
         tr.tc_items.p, tr.n_tc_items, B, nrc, Views<float>::tgt(ctx), ctx->mesh.N, tr.tc_list.p,
         Views<float>::bc(ctx), ctx->tc_img.p, acc, counter, ctx->dev_err.p, ctx->rhs_nact);
@@ -446,7 +475,8 @@ int tc_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
 
 template <int P>
 int tc_launch_p(lspr_ctx *ctx, double *acc, int *counter, int B) {
-    return B <= 16 ? tc_launch<P, 16>(ctx, acc, counter, B) : tc_launch<P, 32>(ctx, acc, counter, B);
+    return B <= 16 ? tc_launch<P, 16>(ctx, acc, counter, B)
+                   : (B <= 32 ? tc_launch<P, 32>(ctx, acc, counter, B) : tc_launch<P, 64>(ctx, acc, counter, B));
 }
 
 }  // namespace

@@ -80,14 +80,17 @@ def test_work_counts(P):
 
 
 def test_tensor_core_m2p_bound():
-    # the three terms of the bound scale as stated: generation and SFU with the units of 32
-    # right-hand sides, MMAs with 3 products of 2 x 128 x 256 x 8 flops per K step of 8 terms
+    # the three terms of the bound scale as stated: generation and SFU once per unit (64
+    # right-hand sides above 32: two A parts against one set of coefficients), MMAs with 3
+    # products of 2 x 128 x 256 x 8 flops per K step of 8 terms and A part of 32
     pk = {"bf16_tflops_sustained": 1741.2}
     b = bench.m2p_tc_bound(7, 64, 1000, pk, 2070.0)
     nt = 120
-    assert b["mufu_ops"] == 1000 * 2 * 256
+    assert b["mufu_ops"] == 1000 * 256
     assert b["mma_flops"] == 1000 * 2 * 3 * 2 * 128 * 256 * 8 * (nt // 8)
-    assert b["generation_flops"] == 1000 * 2 * 256 * bench.m2p_flops(7, 0)
+    assert b["generation_flops"] == 1000 * 256 * bench.m2p_flops(7, 0)
+    b32 = bench.m2p_tc_bound(7, 32, 1000, pk, 2070.0)
+    assert b32["mufu_ops"] == 1000 * 256 and b32["mma_flops"] == b["mma_flops"] // 2
     assert b["bound_s"] == max(b["terms_s"].values())
     b16 = bench.m2p_tc_bound(7, 16, 1000, pk, 2070.0)
     assert b16["mma_flops"] == 1000 * 2 * 2 * 128 * 256 * 8 * (nt // 8)
