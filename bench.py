@@ -166,6 +166,15 @@ def tc_roofline(bnd: dict, t: float, kernel: str, traffic) -> dict:
                          "bf16 x nominal 1.1/2.25)) / the launch time; achieved and peak are the limiting term's"}
 
 
+def arnoldi_gb(n_panels: int, c: dict) -> float:
+    """Basis traffic (GB) of the Arnoldi vector kernels from the device work counters
+    (lspr_get_arnoldi_stats): 16 bytes per complex entry of vectors of 2N entries; per
+    system-step 7 + 2 (j + 1) vectors, and 3 + 2 (j + 1) more for a second Gram-Schmidt pass."""
+    vec = 16 * 2 * n_panels
+    return vec * (7 * c["system_steps"] + 2 * c["vectors"] + 2 * c["vectors_second_pass"]
+                  + 3 * c["system_steps_second_pass"]) / 1e9
+
+
 def m2p_terms(P: int) -> int:
     """Taylor terms with |k| <= P."""
     return (P + 1) * (P + 2) * (P + 3) // 6
@@ -525,9 +534,7 @@ def run_ours(args, wl, rank, world, local_rank):
         # system-step 3 vectors (v_j, z, w read) + 2 (j + 3) for the first Gram-Schmidt pass
         # (w converted in place, the j + 1 basis vectors read twice, w written), and 2 (j + 1) + 3
         # for a second pass; the cycles' update (once per restart) is not counted
-        vec = 16 * 2 * len(tris)
-        gb = vec * (7 * arn["system_steps"] + 2 * arn["vectors"] + 2 * arn["vectors_second_pass"]
-                    + 3 * arn["system_steps_second_pass"]) / 1e9
+        gb = arnoldi_gb(len(tris), arn)
         k = kernels["gmres"]
         k["algorithmic_gb"] = round(gb, 3)
         k["achieved_gbs"] = round(gb / (k["ms_total"] * 1e-3), 1)

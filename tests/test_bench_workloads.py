@@ -101,3 +101,16 @@ def test_oracle_rate_model():
     # 64 wavelengths, a product timed on 1000 of 81920 rows in 2 s, 40 oracle steps
     v = bench.oracle_rate(wl, 2.0, 1000, 81920, 40)
     assert np.isclose(v, 64 / (43 * 2.0 * 81.92))
+
+
+def test_arnoldi_traffic_model():
+    # one system-step at j = 0 with a second pass: 7 + 2 vectors, then 3 + 2 more (14 vectors of
+    # 2N complex entries of 16 bytes); the counters add linearly over steps
+    c = {"system_steps": 1, "vectors": 1, "vectors_second_pass": 1, "system_steps_second_pass": 1}
+    assert bench.arnoldi_gb(1000, c) == 14 * 16 * 2000 / 1e9
+    c2 = {k: 3 * v for k, v in c.items()}
+    assert abs(bench.arnoldi_gb(1000, c2) - 3 * bench.arnoldi_gb(1000, c)) < 1e-15
+    # without the second pass: 7 + 2 (j + 1) vectors at j = 4
+    c3 = {"system_steps": 1, "vectors": 5, "vectors_second_pass": 0, "system_steps_second_pass": 0}
+    assert bench.arnoldi_gb(1000, c3) == 17 * 16 * 2000 / 1e9
+
