@@ -115,7 +115,8 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates, TF32 over BF16
 # treecode parameters (theta, P, Ncrit); None where no capture of the current kernel matches
 NCU_TRAFFIC = {("sphere20480", "m2p", 0.4, 5, 256): 2.410e6,          # m2p_fp32_sphere20480.md
                ("sphere20480", "p2p", 0.4, 5, 256): 5.045e6,          # p2p1_fp32_sphere20480.md
-               ("sphere81920_sweep64", "m2p", 0.4, 7, 512): 8.883e9}  # m2p_tc_sphere81920_sweep64.md
+               ("sphere81920_sweep64", "m2p", 0.4, 7, 512): 8.883e9,  # m2p_tc_sphere81920_sweep64.md
+               ("sphere81920_sweep64", "p2p", 0.4, 7, 512): 9.805e8}  # p2p_tc_sphere81920_sweep64.md
 
 
 def m2p_flops(P: int, B: int = 1) -> int:
