@@ -18,10 +18,10 @@ namespace {
 // registers at 8)
 constexpr int kFfP2PChunk = 8;
 
-// one term k of the table: indices of k - e_d and k - 2 e_d (-1: absent) and the
-// recurrence weights -(2n-1)/n and -(n-1)/n as float-float pairs
+// one term k of the table: distances u - index(k - e_d) and u - index(k - 2 e_d) to the term's
+// own index u (0: absent), and the recurrence weights -(2n-1)/n and -(n-1)/n as float-float pairs
 struct FfTerm {
-    signed char m1[3], m2[3];
+    unsigned char d1[3], d2[3];
     short pad;
     float c1h, c1l, c2h, c2l;
 };
@@ -34,8 +34,8 @@ constexpr FfTermTable make_ff_terms() {
     constexpr MultiIndex<kMaxP> mi{};
     for (int u = 0; u < n_terms(kMaxP); ++u) {
         for (int d = 0; d < 3; ++d) {
-            tab.t[u].m1[d] = (signed char)mi.m1[u][d];
-            tab.t[u].m2[d] = (signed char)mi.m2[u][d];
+            tab.t[u].d1[d] = (unsigned char)(mi.m1[u][d] >= 0 ? u - mi.m1[u][d] : 0);
+            tab.t[u].d2[d] = (unsigned char)(mi.m2[u][d] >= 0 ? u - mi.m2[u][d] : 0);
         }
         const double n = mi.deg[u];
         const double c1 = u ? -(2.0 * n - 1.0) / n : 0.0, c2 = u ? -(n - 1.0) / n : 0.0;
@@ -46,31 +46,40 @@ constexpr FfTermTable make_ff_terms() {
     }
     return tab;
 }
+static_assert(n_terms(kMaxP) - n_terms(kMaxP - 3) <= 255, "term distances must fit the table's bytes");
 
 __constant__ FfTermTable c_ff_terms = make_ff_terms();
 
+// The recurrence of a degree-n term reads terms of degrees n-1 and n-2 only, so each lane keeps
+// its coefficients in a ring of W slots (term u in slot u mod W), W = the terms of the three
+// highest degrees P-2, P-1, P (85 instead of 120 at P = 7): every term read is among the W
+// written last.
+__host__ __device__ inline int ff_ring(int P) {
+    return P < 2 ? n_terms(P) : n_terms(P) - n_terms(P - 3);
+}
+
 // Shared memory of a block: the staged moments of one box for its chunk of right-hand sides
-// (NT x NB, shared by the block's two warps) and each warp's coefficients (2 x NT x 32)
-__host__ __device__ inline size_t ff_m2p_smem(int NT, int NB) {
-    return (size_t)NT * NB * sizeof(ff4) + 2 * (size_t)NT * 32 * sizeof(ffloat);
+// (NT x NB, shared by the block's two warps) and each warp's coefficient ring (2 x W x 32)
+__host__ __device__ inline size_t ff_m2p_smem(int NT, int W, int NB) {
+    return (size_t)NT * NB * sizeof(ff4) + 2 * (size_t)W * 32 * sizeof(ffloat);
 }
 
 // Work units and accumulation as in m2p_kernel; NT = n_terms(P) at run time.  A block of two
 // warps takes a unit: warp h the targets 32 h .. 32 h + 31 of the 64-target block, both on the
 // same boxes, so each box's moments are staged once for the two.  The recurrence is rolled
-// (each lane's coefficients live in its column of the warp's array), and the contraction
+// (each lane's coefficients live in its column of the warp's ring), and the contraction
 // accumulates with ff_mac.
 template <int NB>
 __global__ void __launch_bounds__(64)
     m2p_ff_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B, int NT,
                   const ff4 *__restrict__ tgt, int64_t ntgt, const int *__restrict__ list,
                   const ff4 *__restrict__ box_c, const ff4 *__restrict__ mom, double *__restrict__ acc, int *counter,
-                  const int *nact) {
+                  const int *nact, int W) {
     extern __shared__ __align__(16) unsigned char ff_smem[];
     __shared__ int64_t unit;
     const int h = threadIdx.x >> 5, lane = threadIdx.x & 31;
     ff4 *sm = (ff4 *)ff_smem;
-    ffloat *sa = (ffloat *)(sm + NT * NB) + (size_t)h * NT * 32;   // sa[t * 32 + lane]
+    ffloat *sa = (ffloat *)(sm + NT * NB) + (size_t)h * W * 32;   // sa[(t mod W) * 32 + lane]
     const int Bact = nact ? *nact : B;   // right-hand sides in use (the first Bact slots)
     nbc = (Bact + NB - 1) / NB;
     const int64_t units = nitems * nbc;
@@ -105,6 +114,7 @@ __global__ void __launch_bounds__(64)
             const ffloat a0 = rsq(r2);
             const ffloat ir2 = a0 * a0;
             sa[lane] = a0;
+            int su = 0;   // slot of term t
 #pragma unroll
             for (int j = 0; j < NB; ++j) {
                 const ff4 m = sm[j];
@@ -116,14 +126,21 @@ __global__ void __launch_bounds__(64)
 #pragma unroll 1
             for (int t = 1; t < NT; ++t) {
                 const FfTerm &e = c_ff_terms.t[t];
+                su = su + 1 == W ? 0 : su + 1;
                 ffloat s1(0.f, 0.f), s2(0.f, 0.f);
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    if (e.m1[d] >= 0) s1 += R[d] * sa[e.m1[d] * 32 + lane];
-                    if (e.m2[d] >= 0) s2 += sa[e.m2[d] * 32 + lane];
+                    if (e.d1[d]) {
+                        const int sl = su - e.d1[d];
+                        s1 += R[d] * sa[(sl < 0 ? sl + W : sl) * 32 + lane];
+                    }
+                    if (e.d2[d]) {
+                        const int sl = su - e.d2[d];
+                        s2 += sa[(sl < 0 ? sl + W : sl) * 32 + lane];
+                    }
                 }
                 const ffloat at = (ffloat(e.c1h, e.c1l) * s1 + ffloat(e.c2h, e.c2l) * s2) * ir2;
-                sa[t * 32 + lane] = at;
+                sa[su * 32 + lane] = at;
 #pragma unroll
                 for (int j = 0; j < NB; ++j) {
                     const ff4 m = sm[t * NB + j];
@@ -150,8 +167,8 @@ int m2p_ff_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
     static int occ = 0, occ_smem = -1;
     static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
-    const int NT = n_terms(tr.P);
-    const size_t smem = ff_m2p_smem(NT, NB);
+    const int NT = n_terms(tr.P), W = ff_ring(tr.P);
+    const size_t smem = ff_m2p_smem(NT, W, NB);
     LSPR_TRY(ctx, allow_smem(m2p_ff_kernel<NB>, (int)smem, ctx->device, smem_set));
     if (occ_smem != (int)smem) {
         int per_sm = 0;
@@ -166,7 +183,7 @@ int m2p_ff_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
         (unsigned)std::min<int64_t>(tr.n_m2p_items * nbc, (int64_t)occ * std::max(1, ctx->num_sms));
     m2p_ff_kernel<NB><<<grid, 64, smem, ctx->stream>>>(
         tr.m2p_items.p, tr.n_m2p_items, nbc, B, NT, Views<ffloat>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p,
-        Views<ffloat>::bc(ctx), Views<ffloat>::mom(ctx), acc, counter, ctx->rhs_nact);
+        Views<ffloat>::bc(ctx), Views<ffloat>::mom(ctx), acc, counter, ctx->rhs_nact, W);
     return LSPR_OK;
 }
 
