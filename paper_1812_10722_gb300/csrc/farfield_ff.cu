@@ -58,28 +58,30 @@ __host__ __device__ inline int ff_ring(int P) {
     return P < 2 ? n_terms(P) : n_terms(P) - n_terms(P - 3);
 }
 
-// Shared memory of a block: the staged moments of one box for its chunk of right-hand sides
-// (NT x NB, shared by the block's two warps) and each warp's coefficient ring (2 x W x 32)
-__host__ __device__ inline size_t ff_m2p_smem(int NT, int W, int NB) {
-    return (size_t)NT * NB * sizeof(ff4) + 2 * (size_t)W * 32 * sizeof(ffloat);
+// Shared memory of a block: one part (TP terms) of a box's staged moments for its chunk of
+// right-hand sides (TP x NB, shared by the block's two warps) and each warp's coefficient ring
+// (2 x W x 32)
+__host__ __device__ inline size_t ff_m2p_smem(int TP, int W, int NB) {
+    return (size_t)TP * NB * sizeof(ff4) + 2 * (size_t)W * 32 * sizeof(ffloat);
 }
 
 // Work units and accumulation as in m2p_kernel; NT = n_terms(P) at run time.  A block of two
 // warps takes a unit: warp h the targets 32 h .. 32 h + 31 of the 64-target block, both on the
-// same boxes, so each box's moments are staged once for the two.  The recurrence is rolled
-// (each lane's coefficients live in its column of the warp's ring), and the contraction
-// accumulates with ff_mac.
+// same boxes, so each box's moments are staged once for the two, in parts of TP terms (the
+// launcher picks TP so that more blocks fit per SM).  The recurrence is rolled (each lane's
+// coefficients live in its column of the warp's ring), and the contraction accumulates with
+// ff_mac.
 template <int NB>
 __global__ void __launch_bounds__(64)
     m2p_ff_kernel(const int4 *__restrict__ items, int64_t nitems, int nbc, int B, int NT,
                   const ff4 *__restrict__ tgt, int64_t ntgt, const int *__restrict__ list,
                   const ff4 *__restrict__ box_c, const ff4 *__restrict__ mom, double *__restrict__ acc, int *counter,
-                  const int *nact, int W) {
+                  const int *nact, int W, int TP) {
     extern __shared__ __align__(16) unsigned char ff_smem[];
     __shared__ int64_t unit;
     const int h = threadIdx.x >> 5, lane = threadIdx.x & 31;
     ff4 *sm = (ff4 *)ff_smem;
-    ffloat *sa = (ffloat *)(sm + NT * NB) + (size_t)h * W * 32;   // sa[(t mod W) * 32 + lane]
+    ffloat *sa = (ffloat *)(sm + TP * NB) + (size_t)h * W * 32;   // sa[(t mod W) * 32 + lane]
     const int Bact = nact ? *nact : B;   // right-hand sides in use (the first Bact slots)
     nbc = (Bact + NB - 1) / NB;
     const int64_t units = nitems * nbc;
@@ -103,18 +105,24 @@ __global__ void __launch_bounds__(64)
         for (int l = item.y; l < item.z; ++l) {
             const int b = __ldg(list + l);
             const ff4 c = box_c[b];
-            __syncthreads();   // the previous box's moments are no longer read
-            for (int q2 = threadIdx.x; q2 < NT * NB; q2 += 64) {
-                const int t = q2 / NB, j = q2 - t * NB;
-                sm[q2] = j < nb ? mom[((int64_t)b * NT + t) * B + b0 + j] : zero4<ff4>();
-            }
-            __syncthreads();
+            // terms t0 .. t0 + TP - 1 of the box's moments into sm (the whole block, at the same t)
+            auto stage = [&](int t0) {
+                __syncthreads();   // the previous part's moments are no longer read
+                const int nq = min(TP, NT - t0) * NB;
+                for (int q2 = threadIdx.x; q2 < nq; q2 += 64) {
+                    const int t = q2 / NB, j = q2 - t * NB;
+                    sm[q2] = j < nb ? mom[((int64_t)b * NT + t0 + t) * B + b0 + j] : zero4<ff4>();
+                }
+                __syncthreads();
+            };
+            stage(0);
             const ffloat R[3] = {q.x - c.x, q.y - c.y, q.z - c.z};
             const ffloat r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
             const ffloat a0 = rsq(r2);
             const ffloat ir2 = a0 * a0;
             sa[lane] = a0;
             int su = 0;   // slot of term t
+            int tpart = 0;   // first term of the staged part
 #pragma unroll
             for (int j = 0; j < NB; ++j) {
                 const ff4 m = sm[j];
@@ -125,6 +133,7 @@ __global__ void __launch_bounds__(64)
             }
 #pragma unroll 1
             for (int t = 1; t < NT; ++t) {
+                if (t == tpart + TP) stage(tpart = t);
                 const FfTerm &e = c_ff_terms.t[t];
                 su = su + 1 == W ? 0 : su + 1;
                 ffloat s1(0.f, 0.f), s2(0.f, 0.f);
@@ -143,7 +152,7 @@ __global__ void __launch_bounds__(64)
                 sa[su * 32 + lane] = at;
 #pragma unroll
                 for (int j = 0; j < NB; ++j) {
-                    const ff4 m = sm[t * NB + j];
+                    const ff4 m = sm[(t - tpart) * NB + j];
                     ff_mac(a[j][0], at, m.x);
                     ff_mac(a[j][1], at, m.y);
                     ff_mac(a[j][2], at, m.z);
@@ -164,26 +173,42 @@ __global__ void __launch_bounds__(64)
 
 template <int NB>
 int m2p_ff_launch(lspr_ctx *ctx, double *acc, int *counter, int B) {
-    static int occ = 0, occ_smem = -1;
+    static int occ = 0, occ_nt = -1, tp_sel = 0;
     static int smem_set[kSmemDevices] = {};
     Tree &tr = ctx->tree;
     const int NT = n_terms(tr.P), W = ff_ring(tr.P);
-    const size_t smem = ff_m2p_smem(NT, W, NB);
-    LSPR_TRY(ctx, allow_smem(m2p_ff_kernel<NB>, (int)smem, ctx->device, smem_set));
-    if (occ_smem != (int)smem) {
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2p_ff_kernel<NB>, 64, smem) != cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-        occ = per_sm;
-        occ_smem = (int)smem;
+    LSPR_TRY(ctx, allow_smem(m2p_ff_kernel<NB>, (int)ff_m2p_smem(NT, W, NB), ctx->device, smem_set));
+    if (occ_nt != NT) {
+        // the fewest parts (1 to 3) of a box's moments that give the most resident blocks per SM
+        // (P 7, 8 right-hand sides: three parts of 40 terms, 53.8 KB, four blocks instead of three)
+        occ = 0;
+        tp_sel = NT;
+        for (int parts = 1; parts <= 3; ++parts) {
+            const int tp = (NT + parts - 1) / parts;
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2p_ff_kernel<NB>, 64,
+                                                              ff_m2p_smem(tp, W, NB)) != cudaSuccess) {
+                (void)cudaGetLastError();
+                per_sm = 0;
+            }
+            if (per_sm > occ) {
+                occ = per_sm;
+                tp_sel = tp;
+            }
+        }
+        if (occ < 1) {
+            occ = 1;
+            tp_sel = NT;
+        }
+        occ_nt = NT;
     }
+    const size_t smem = ff_m2p_smem(tp_sel, W, NB);
     const int nbc = (B + NB - 1) / NB;
     const unsigned grid =
         (unsigned)std::min<int64_t>(tr.n_m2p_items * nbc, (int64_t)occ * std::max(1, ctx->num_sms));
     m2p_ff_kernel<NB><<<grid, 64, smem, ctx->stream>>>(
         tr.m2p_items.p, tr.n_m2p_items, nbc, B, NT, Views<ffloat>::tgt(ctx), ctx->mesh.N, tr.m2p_list.p,
-        Views<ffloat>::bc(ctx), Views<ffloat>::mom(ctx), acc, counter, ctx->rhs_nact, W);
+        Views<ffloat>::bc(ctx), Views<ffloat>::mom(ctx), acc, counter, ctx->rhs_nact, W, tp_sel);
     return LSPR_OK;
 }
 
