@@ -167,6 +167,21 @@ def tc_roofline(bnd: dict, t: float, kernel: str, traffic) -> dict:
                          "bf16 x nominal 1.1/2.25)) / the launch time; achieved and peak are the limiting term's"}
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over the ranks (the replicas' job time is the slowest rank's)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(B: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job lambda-solves/s: every rank solves its own B wavelengths per step."""
+    return B * steps * world / seconds
+
+
 def arnoldi_gb(n_panels: int, c: dict) -> float:
     """Basis traffic (GB) of the Arnoldi vector kernels from the device work counters
     (lspr_get_arnoldi_stats): 16 bytes per complex entry of vectors of 2N entries; per
@@ -395,12 +410,8 @@ def run_ours(args, wl, rank, world, local_rank):
     ctx.set_timing(False)
     barrier()
     info = ctx.info()
-    t_max = total_ms
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = B * args.steps * world / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, world, dev)
+    value = replica_rate(B, args.steps, world, t_max / 1e3)
 
     # ---- accuracy and the plain baseline: the FP64 treecode (same tree) one wavelength at a time at
     # the checked wavelengths (all of them for B <= 4; else the one nearest the resonance, both ends
@@ -482,11 +493,7 @@ def run_ours(args, wl, rank, world, local_rank):
     for _ in range(args.steps):
         r = step(True)
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     h2d = verts.nbytes + tris.nbytes + eps.astype(np.complex128).nbytes + lam.nbytes + 24 + (
         0 if surf is None else surf.nbytes)
     d2h = B * (3 * 16 + 8)
@@ -600,7 +607,7 @@ def run_ours(args, wl, rank, world, local_rank):
                    "K": wl["K"], "K_fine": wl["K_fine"], "N_k": wl["N_k"], "gmres_tol": wl["tol"],
                    "restart": wl["restart"], "l2": "flushed between steps (258 MiB write)",
                    "parallelism": f"replicas x{world}", "autotune": tune},
-        "e2e": {"value": round(B * args.steps * world / e2e_s, 4), "unit": "lambda-solves/s",
+        "e2e": {"value": round(replica_rate(B, args.steps, world, e2e_s), 4), "unit": "lambda-solves/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": roof,
