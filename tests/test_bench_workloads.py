@@ -114,3 +114,25 @@ def test_arnoldi_traffic_model():
     c3 = {"system_steps": 1, "vectors": 5, "vectors_second_pass": 0, "system_steps_second_pass": 0}
     assert bench.arnoldi_gb(1000, c3) == 17 * 16 * 2000 / 1e9
 
+
+
+def test_tensor_core_p2p_bound_and_roofline():
+    # one unit of 64 right-hand sides: the kernel values and the rsqrt once per pair; per stage of
+    # 8 sources, two layers x 3 products of 2 x 128 x 256 x 8 flops; a second unit of 6 right-hand
+    # sides (70 in all) repeats the generation and issues 2 products per layer
+    pk = {"bf16_tflops_sustained": 1741.2}
+    pairs, stages = 10 ** 6, 500
+    b = bench.p2p_tc_bound(64, pairs, stages, pk, 2070.0)
+    assert b["mufu_ops"] == pairs
+    assert b["generation_flops"] == pairs * bench.P2P_GEN_FLOPS
+    assert b["mma_flops"] == stages * 2 * 3 * 2 * 128 * 256 * 8
+    b70 = bench.p2p_tc_bound(70, pairs, stages, pk, 2070.0)
+    assert b70["mufu_ops"] == 2 * pairs
+    assert b70["mma_flops"] == b["mma_flops"] + stages * 2 * 2 * 2 * 128 * 256 * 8
+    # the TF32 peak is the measured sustained bf16 rate x the nominal TF32 / BF16 ratio
+    assert np.isclose(b["tf32_peak_tflops"], 1741.2 * bench.TF32_PER_BF16)
+    # the roofline entry: frac = bound / launch time, achieved and peak from the limiting term
+    assert b["limiter"] == "tensor_mma"
+    r = bench.tc_roofline(b, 2 * b["bound_s"], "p2p", None)
+    assert r["bound"] == "tensor" and r["frac"] == 0.5
+    assert np.isclose(r["achieved"], 0.5 * r["peak"], rtol=1e-3)
